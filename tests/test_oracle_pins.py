@@ -1,0 +1,539 @@
+"""Pins of the CPU oracle against facts the paper and mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: hand-worked
+examples (tests/golden), closed forms, invariants the paper states, special
+cases that reduce to an independent library routine (LAPACK, numpy sort /
+searchsorted), or brute force on tiny inputs.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1712_06326_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _grid(rng, Y, X, ch=1):
+    return rng.random((Y, X, ch)).astype(np.float32)
+
+
+# ----------------------------------------------------------------------------
+# dictionary (Sec. I: the fully known patches)
+# ----------------------------------------------------------------------------
+def test_dict_count_closed_form():
+    for (Y, X, K) in [(12, 12, 3), (20, 17, 5), (9, 9, 9), (8, 8, 9)]:
+        m = np.ones((Y, X), np.uint8)
+        d = O.dict_extract(m, K)
+        assert len(d) == max(0, X - K + 1) * max(0, Y - K + 1)
+        assert np.all(np.diff(d) > 0)  # raster order
+
+
+def test_dict_single_hole_removes_box():
+    Y, X, K = 30, 40, 5
+    m = np.ones((Y, X), np.uint8)
+    m[12, 20] = 0
+    d = O.dict_extract(m, K)
+    assert len(d) == (X - K + 1) * (Y - K + 1) - K * K
+    xs, ys = d % X, d // X
+    assert not np.any((np.abs(xs - 20) <= 2) & (np.abs(ys - 12) <= 2))
+
+
+def test_dict_3d_count():
+    m = np.ones((7, 8, 9), np.uint8)
+    d = O.dict_extract(m, 3)
+    assert len(d) == 7 * 6 * 5
+    m[3, 4, 4] = 0
+    assert len(O.dict_extract(m, 3)) == 7 * 6 * 5 - 27
+
+
+# ----------------------------------------------------------------------------
+# masked L2 cost (Sec. II after Fig. 1) and full scan (Sec. I)
+# ----------------------------------------------------------------------------
+def test_cost_closed_form_constant_offset():
+    # target - source = delta (dyadic, exact) at every known element:
+    # cost = n_known * delta^2 exactly; unknown pixels contribute 0
+    rng = np.random.default_rng(0)
+    K = 5
+    g = np.zeros((20, 20, 3), np.float32)
+    base = (rng.integers(0, 64, (K, K, 3)) / 64.0).astype(np.float32)
+    g[2:7, 2:7] = base
+    g[10:15, 11:16] = base + np.float32(0.25)
+    m = np.ones((20, 20), np.uint8)
+    t = 12 * 20 + 13
+    s = 4 * 20 + 4
+    assert O.cost64(g, m, K, t, s) == pytest.approx(K * K * 3 * 0.0625, abs=0)
+    m[10, 11] = 0
+    m[14, 15] = 0
+    assert O.cost64(g, m, K, t, s) == (K * K - 2) * 3 * 0.0625
+    w = np.array([1.0, 2.0, 4.0], np.float32)
+    assert O.cost64(g, m, K, t, s, w) == (K * K - 2) * 0.0625 * 7
+
+
+def test_cost_ignores_unknown_target_values():
+    rng = np.random.default_rng(1)
+    g = _grid(rng, 16, 16)
+    m = np.ones((16, 16), np.uint8)
+    m[6:9, 6:9] = 0
+    c1 = O.cost64(g, m, 5, 8 * 16 + 8, 3 * 16 + 12)
+    g2 = g.copy()
+    g2[6:9, 6:9] = 123.0
+    assert O.cost64(g2, m, 5, 8 * 16 + 8, 3 * 16 + 12) == c1
+
+
+def test_cost_brute_force_tiny_enumeration():
+    # tiny grid, every pair: cost >= 0, cost(p, p) = 0 for fully known p,
+    # symmetric for fully known pairs, and triangle-type bound sqrt-norm
+    rng = np.random.default_rng(2)
+    g = _grid(rng, 10, 10)
+    m = np.ones((10, 10), np.uint8)
+    d = O.dict_extract(m, 3)
+    C = np.array([[O.cost64(g, m, 3, a, b) for b in d] for a in d])
+    assert np.all(C >= 0)
+    assert np.all(np.diag(C) == 0)
+    assert np.array_equal(C, C.T)
+    S = np.sqrt(C)
+    for i in range(0, len(d), 7):
+        assert np.all(S[i][:, None] <= S[i][None, :] + S + 1e-12)
+
+
+def test_fullscan_exact_duplicate_tie_to_lowest_id():
+    rng = np.random.default_rng(3)
+    g = _grid(rng, 24, 24)
+    # plant the patch around (5,5) again around (18,16): exact duplicates
+    g[15:18, 17:20] = g[4:7, 4:7]
+    m = np.ones((24, 24), np.uint8)
+    d = O.dict_extract(m, 3)
+    t = 16 * 24 + 18
+    pick, cost = O.fullscan(g, m, 3, d, np.array([t]))
+    assert cost[0] == 0.0
+    assert d[pick[0]] == 5 * 24 + 5  # the lower-id duplicate, not the target itself
+
+
+def test_fullscan_constant_grid_picks_zero():
+    g = np.full((12, 12, 2), 0.375, np.float32)
+    m = np.ones((12, 12), np.uint8)
+    m[5:7, 5:7] = 0
+    d = O.dict_extract(m, 3)
+    pick, cost = O.fullscan(g, m, 3, d, np.array([6 * 12 + 6, 2 * 12 + 9]))
+    assert list(pick) == [0, 0] and list(cost) == [0.0, 0.0]
+
+
+def test_fullscan_planted_minimum():
+    # every source differs from the target by >= 0.5 in one element except one
+    rng = np.random.default_rng(4)
+    K = 3
+    g = (rng.integers(0, 4, (16, 16, 1)) / 4.0).astype(np.float32)
+    m = np.ones((16, 16), np.uint8)
+    d = O.dict_extract(m, K)
+    t = 8 * 16 + 8
+    costs = np.array([O.cost64(g, m, K, t, s) for s in d])
+    costs[d == t] = np.inf
+    pick, cost = O.fullscan(g, m, K, d, np.array([t]))
+    # the full scan includes the target itself (cost 0) -> pick it
+    assert d[pick[0]] == t and cost[0] == 0
+    # with the target's own patch made unknown-centred the minimum is the brute one
+    m2 = m.copy()
+    m2[8, 8] = 0
+    d2 = O.dict_extract(m, K)
+    costs2 = np.array([O.cost64(g, m2, K, t, s) for s in d2])
+    p2, c2 = O.fullscan(g, m2, K, d2, np.array([t]))
+    assert c2[0] == costs2.min() and p2[0] == int(np.argmin(costs2))
+
+
+# ----------------------------------------------------------------------------
+# subsets (Fig. 2)
+# ----------------------------------------------------------------------------
+def _gold_subsets():
+    rows = []
+    for line in open(os.path.join(GOLD, "subsets_K3.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        _, pix = line.strip().split(";")
+        rows.append([int(v) for v in pix.split(",")])
+    return np.array(rows)
+
+
+def test_subsets_hand_worked_K3():
+    assert np.array_equal(O.subsets(2, 3, 0.5, 8), _gold_subsets())
+
+
+def test_subsets_sizes_and_symmetry():
+    for K, frac, m in [(9, 0.6, 49), (11, 0.6, 73), (7, 0.6, 29), (13, 0.6, 101)]:
+        S = O.subsets(2, K, frac, 8)
+        assert S.shape == (8, m)
+        sets = [set(r) for r in S]
+        # geometric symmetry of the anchors: the set sizes are equal and each
+        # corner/edge subset maps onto its mirror under the patch's reflections
+        # up to tie-breaking (equal distance shells differ by at most the last shell)
+        for cv in range(8):
+            pts = np.array([[p % K, p // K] for p in S[cv]])
+            assert len(set(S[cv])) == m
+            assert np.all(pts >= 0) and np.all(pts < K)
+        # top-middle vs bottom-middle: mirror in y, same multiset of distances
+        def d2(anchor, p):
+            return (2 * (p % K) + 1 - anchor[0]) ** 2 + (2 * (p // K) + 1 - anchor[1]) ** 2
+        top = sorted(d2((K, 0), p) for p in S[0])
+        bot = sorted(d2((K, 2 * K), p) for p in S[2])
+        assert top == bot
+    # c = 1 covers the whole patch
+    assert np.array_equal(O.subsets(2, 5, 1.0, 8)[3], np.arange(25))
+
+
+def test_subsets_3d_corners():
+    S = O.subsets(3, 3, 1.0 / 27.0, 14)
+    # the single nearest voxel of each corner is that corner voxel
+    corners = [0, 2, 6, 8, 18, 20, 24, 26]
+    assert [int(r[0]) for r in S[:8]] == corners
+    # face middles -> face-centre voxels z-, z+, y-, y+, x-, x+
+    assert [int(r[0]) for r in S[8:]] == [4, 22, 10, 16, 12, 14]
+
+
+# ----------------------------------------------------------------------------
+# Jacobi eigen-solve and PCA (Sec. II.A)
+# ----------------------------------------------------------------------------
+def test_jacobi_2x2_closed_form():
+    for a, b, d in [(2.0, 1.0, 3.0), (1.0, -0.5, 1.0), (5.0, 1e-3, -2.0), (0.0, 1.0, 0.0)]:
+        ev, V, _ = O.jacobi(np.array([[a, b], [b, d]]))
+        mid, rad = (a + d) / 2, np.hypot((a - d) / 2, b)
+        assert sorted(ev) == pytest.approx([mid - rad, mid + rad], rel=1e-14, abs=1e-15)
+
+
+def test_jacobi_diagonal_is_fixed_point():
+    A = np.diag([3.0, -1.0, 7.5, 0.0])
+    ev, V, sw = O.jacobi(A)
+    assert list(ev) == [3.0, -1.0, 7.5, 0.0]
+    assert np.array_equal(V, np.eye(4)) and sw == 0
+
+
+@pytest.mark.parametrize("n", [3, 10, 57])
+def test_jacobi_matches_lapack(n):
+    rng = np.random.default_rng(n)
+    X = rng.normal(size=(n + 5, n))
+    A = X.T @ X / n
+    ev, V, _ = O.jacobi(A)
+    ref = np.linalg.eigvalsh(A)
+    assert np.sort(ev) == pytest.approx(ref, rel=1e-11, abs=1e-12 * ref.max())
+    assert np.abs(V.T @ V - np.eye(n)).max() < 1e-12
+    assert np.abs(A @ V - V * ev).max() < 1e-11 * ref.max()
+
+
+def test_pca_covariance_and_basis():
+    rng = np.random.default_rng(7)
+    g = _grid(rng, 30, 30, 3)
+    m = np.ones((30, 30), np.uint8)
+    K, D = 5, 4
+    d = O.dict_extract(m, K)
+    sub = O.subsets(2, K, 0.6, 8)[5]
+    B, mu, ev, cov = O.pca(g, K, d, sub, 0, D)
+    # independent gather with numpy slicing + numpy covariance (LAPACK-free)
+    xs, ys = d % 30, d // 30
+    px, py = sub % K - K // 2, sub // K - K // 2
+    X = np.stack([g[ys + py[i], xs + px[i], c] for i in range(len(sub)) for c in range(3)], 1).astype(np.float64)
+    assert np.allclose(mu, X.mean(0).astype(np.float32), rtol=0, atol=1e-7)
+    assert np.allclose(cov, np.cov(X, rowvar=False, bias=True), rtol=1e-12, atol=1e-15)
+    ref = np.linalg.eigh(cov)
+    assert ev[:D] == pytest.approx(ref[0][::-1][:D], rel=1e-11)
+    for k in range(D):
+        v = ref[1][:, ::-1][:, k]
+        v = v * np.sign(v[np.argmax(np.abs(v))])
+        assert np.abs(B[:, k] - v).max() < 1e-6
+        assert B[np.argmax(np.abs(B[:, k])), k] > 0  # sign convention
+
+
+def test_pca_sample_is_every_step_th_entry():
+    rng = np.random.default_rng(8)
+    g = _grid(rng, 20, 20)
+    m = np.ones((20, 20), np.uint8)
+    d = O.dict_extract(m, 3)
+    sub = O.subsets(2, 3, 0.6, 1)[0]
+    N = len(d)
+    S = 50
+    step = -(-N // S)
+    B1, mu1, ev1, cov1 = O.pca(g, 3, d, sub, S, 2)
+    B2, mu2, ev2, cov2 = O.pca(g, 3, d[::step], sub, 0, 2)
+    assert np.array_equal(cov1, cov2) and np.array_equal(B1, B2)
+
+
+def test_pca_rank_one_closed_form():
+    # grid linear in x and y with dyadic values (exact in FP32): every subset
+    # vector is v(centre) * (1, ..., 1) + const, so the covariance is
+    # Var(v) * 1 1^T: one eigenvalue s * Var(v), eigenvector 1/sqrt(s), rest 0
+    Y, X = 24, 24
+    yy, xx = np.mgrid[0:Y, 0:X]
+    g = ((xx + 2 * yy) / 64.0).astype(np.float32)[..., None]
+    m = np.ones((Y, X), np.uint8)
+    d = O.dict_extract(m, 5)
+    sub = O.subsets(2, 5, 0.6, 1)[0]
+    s = len(sub)
+    B, mu, ev, cov = O.pca(g, 5, d, sub, 0, 3)
+    v = ((d % X) + 2 * (d // X)) / 64.0
+    assert ev[0] == pytest.approx(s * v.var(), rel=1e-13)
+    assert abs(ev[1]) < 1e-13 * ev[0]
+    assert np.allclose(B[:, 0], 1.0 / np.sqrt(s), rtol=0, atol=1e-7)
+
+
+# ----------------------------------------------------------------------------
+# projection (Sec. II.A), quantisation and Morton keys (Sec. II.C)
+# ----------------------------------------------------------------------------
+def test_projection_matches_float64_matmul():
+    rng = np.random.default_rng(9)
+    g = _grid(rng, 25, 25, 3)
+    m = np.ones((25, 25), np.uint8)
+    K, D = 5, 6
+    d = O.dict_extract(m, K)
+    sub = O.subsets(2, K, 0.6, 8)[2]
+    B, mu, _, _ = O.pca(g, K, d, sub, 0, D)
+    y = O.project(g, K, d, sub, B, mu, D)
+    xs, ys = d % 25, d // 25
+    px, py = sub % K - K // 2, sub // K - K // 2
+    Xm = np.stack([g[ys + py[i], xs + px[i], c] for i in range(len(sub)) for c in range(3)], 1).astype(np.float64)
+    ref = (Xm - mu.astype(np.float64)) @ B.astype(np.float64)
+    assert np.abs(y - ref).max() < 1e-5
+
+
+def test_projection_selector_basis_is_exact_and_query_skips_unknown():
+    rng = np.random.default_rng(10)
+    g = _grid(rng, 12, 12)
+    m = np.ones((12, 12), np.uint8)
+    K = 3
+    sub = np.arange(9, dtype=np.int32)
+    B = np.zeros((9, 2), np.float32)
+    B[4, 0] = 1.0  # centre pixel
+    B[0, 1] = 1.0  # top-left pixel
+    mu = np.full(9, 0.5, np.float32)
+    y = O.project_query(g, m, K, 5 * 12 + 5, sub, B, mu, 2)
+    assert y[0] == np.float32(g[5, 5, 0] - np.float32(0.5))
+    assert y[1] == np.float32(g[4, 4, 0] - np.float32(0.5))
+    m[4, 4] = 0
+    y = O.project_query(g, m, K, 5 * 12 + 5, sub, B, mu, 2)
+    assert y[1] == 0.0 and y[0] == np.float32(g[5, 5, 0] - np.float32(0.5))
+
+
+def test_quantise_closed_forms():
+    y = np.array([[0.0], [1.0], [0.5], [0.25], [-3.0], [9.0]], np.float32)
+    lo, sc = O.quant_params(y[:2], 8)
+    assert lo[0] == 0.0 and sc[0] == 256.0
+    q = O.quantise(y, 8, lo, sc)[:, 0]
+    assert list(q) == [0, 255, 128, 64, 0, 255]
+    lo, sc = O.quant_params(np.zeros((3, 2), np.float32), 4)
+    assert list(sc) == [0.0, 0.0]
+    assert np.all(O.quantise(np.ones((2, 2), np.float32), 4, lo, sc) == 0)
+
+
+def test_morton_hand_worked_examples():
+    n = 0
+    for line in open(os.path.join(GOLD, "morton_examples.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        b, coords, key = line.strip().split(";")
+        q = np.array([int(v) for v in coords.split(",")], np.uint32)
+        assert O.morton(q, int(b)) == int(key), line
+        n += 1
+    assert n >= 8
+
+
+def test_morton_shift_adds_a_bit():
+    assert O.key_bits(3, 8, np.array([0, 0, 0])) == 8
+    assert O.key_bits(3, 8, np.array([0, 5, 0])) == 9
+    q = np.array([[1, 2]], np.uint32)
+    k = O.keys(q, 2, np.array([1, 1]))
+    assert int(k[0]) == O.morton(np.array([2, 3], np.uint32), 3)
+
+
+def test_paper_comparator_orders_like_morton_keys():
+    # Sec. II.C: comparing via the most significant differing bit is the same
+    # order as comparing full z-addresses
+    rng = np.random.default_rng(11)
+    for D in [1, 2, 3, 5, 8]:
+        q = rng.integers(0, 256, (300, D)).astype(np.uint32)
+        q[50:60] = q[0]  # equal points
+        k = O.keys(q, 8)
+        for _ in range(3000):
+            a, b = rng.integers(0, 300, 2)
+            assert O.zless(q[a], q[b]) == (int(k[a]) < int(k[b]))
+
+
+def test_morton_box_interval_property():
+    # Sec. II.D: every point of an axis-aligned box lies in the z-interval
+    # [z(min), z(max)] -- the property the litmax/bigmin split relies on
+    rng = np.random.default_rng(12)
+    for _ in range(50):
+        lo = rng.integers(0, 12, 2)
+        hi = lo + rng.integers(0, 5, 2)
+        zmin = O.morton(lo.astype(np.uint32), 4)
+        zmax = O.morton(hi.astype(np.uint32), 4)
+        for x in range(lo[0], hi[0] + 1):
+            for y in range(lo[1], hi[1] + 1):
+                assert zmin <= O.morton(np.array([x, y], np.uint32), 4) <= zmax
+
+
+def test_sort_and_lower_bound_against_numpy():
+    rng = np.random.default_rng(13)
+    k = rng.integers(0, 50, 5000).astype(np.uint64)
+    k[::7] = np.uint64(2 ** 63 + 5)
+    sk, si = O.sort(k)
+    ref = np.argsort(k, kind="stable")
+    assert np.array_equal(si, ref) and np.array_equal(sk, k[ref])
+    assert np.array_equal(np.sort(si), np.arange(len(k)))
+    for key in [0, 1, 17, 49, 50, 2 ** 63 + 5, 2 ** 64 - 1]:
+        assert O.lower_bound(sk, key) == int(np.searchsorted(sk, np.uint64(key), side="left"))
+
+
+def test_knn_bruteforce_against_numpy():
+    rng = np.random.default_rng(14)
+    q = rng.integers(0, 16, (400, 3)).astype(np.uint32)
+    query = np.array([7, 8, 9], np.uint32)
+    ids, dist = O.knn_bruteforce(q, query, 20)
+    d = ((q.astype(np.int64) - query.astype(np.int64)) ** 2).sum(1)
+    ref = np.lexsort((np.arange(400), d))[:20]
+    assert np.array_equal(ids, ref) and np.array_equal(dist, d[ref])
+
+
+# ----------------------------------------------------------------------------
+# SFC query (Fig. 1(b)-(d))
+# ----------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def small_rgb():
+    g, m = synth.voronoi2d(96, cfg=2, seed_sub=3)
+    ix = O.build_index(g, m, 7, 8, 6, 12, sample=0)
+    return g, m, ix
+
+
+def test_index_keys_sorted_and_permutation(small_rgb):
+    g, m, ix = small_rgb
+    for cv in range(ix["C"]):
+        assert np.all(np.diff(ix["skeys"][cv].astype(object)) >= 0)
+        assert np.array_equal(np.sort(ix["sids"][cv]), np.arange(ix["N"]))
+        assert np.array_equal(ix["keys"][cv][ix["sids"][cv]], ix["skeys"][cv])
+        eq = ix["skeys"][cv][1:] == ix["skeys"][cv][:-1]
+        assert np.all(ix["sids"][cv][1:][eq] > ix["sids"][cv][:-1][eq])
+
+
+def test_query_window_covering_dictionary_equals_fullscan(small_rgb):
+    g, m, ix = small_rgb
+    t = synth.front_targets(m, 7, cap=12, cfg=2)
+    lin = O.centres_to_lin(t, ix["ext"])
+    fp, fc = O.fullscan(g, m, 7, ix["dict"], lin)
+    for i, tl in enumerate(lin):
+        r = O.query(ix, g, m, tl, W=ix["N"])
+        assert r["pick"] == fp[i] and r["cost"] == fc[i]
+        assert np.array_equal(r["cand"], np.arange(ix["N"]))
+
+
+def test_query_dictionary_patch_finds_itself(small_rgb):
+    g, m, ix = small_rgb
+    for j in [0, 17, ix["N"] // 2, ix["N"] - 1]:
+        r = O.query(ix, g, m, ix["dict"][j], W=16)
+        assert r["cost"] == 0.0
+        assert r["pick"] <= j
+        assert ix["dict"][r["pick"]] == ix["dict"][j] or O.cost64(g, m, 7, ix["dict"][j], ix["dict"][r["pick"]]) == 0
+
+
+def test_query_candidate_set_structure(small_rgb):
+    g, m, ix = small_rgb
+    t = synth.front_targets(m, 7, cap=20, cfg=2)
+    lin = O.centres_to_lin(t, ix["ext"])
+    W = 10
+    for tl in lin:
+        r = O.query(ix, g, m, tl, W=W)
+        c = r["cand"]
+        assert len(c) <= ix["C"] * W and np.all(np.diff(c) > 0) and c.min() >= 0 and c.max() < ix["N"]
+        want = set()
+        for cv in range(ix["C"]):
+            p = O.lower_bound(ix["skeys"][cv], r["qkeys"][cv])
+            assert p == r["pos"][cv]
+            s0 = min(max(p - W // 2, 0), ix["N"] - W)
+            want |= set(ix["sids"][cv][s0:s0 + W].tolist())
+        assert set(c.tolist()) == want
+        costs = [O.cost64(g, m, 7, tl, ix["dict"][j]) for j in c]
+        assert r["cost"] == min(costs) and r["pick"] == c[int(np.argmin(costs))]
+
+
+def test_query_select_best_uses_max_coverage(small_rgb):
+    g, m, ix = small_rgb
+    t = synth.front_targets(m, 7, cap=10, cfg=2)
+    lin = O.centres_to_lin(t, ix["ext"])
+    ext = ix["ext"]
+    for tl in lin:
+        r = O.query(ix, g, m, tl, W=8, select=1)
+        x, y = tl % ext[0], tl // ext[0]
+        cov = []
+        for cv in range(ix["C"]):
+            sub = ix["subset"][cv]
+            cov.append(int(sum(m[y + p // 7 - 3, x + p % 7 - 3] for p in sub)))
+        best = int(np.argmax(cov))
+        assert r["pos"][best] >= 0 and sum(p >= 0 for p in r["pos"]) == 1
+
+
+# ----------------------------------------------------------------------------
+# fill loop (Sec. I; Fig. 1(a))
+# ----------------------------------------------------------------------------
+def test_fill_one_pixel_hole_uses_bruteforce_pick():
+    rng = np.random.default_rng(15)
+    g = _grid(rng, 20, 20)
+    m = np.ones((20, 20), np.uint8)
+    m[9, 11] = 0
+    d = O.dict_extract(m, 3)
+    out, mo, log, steps = O.inpaint(g, m, 3, mode=0)
+    assert steps == 1 and mo.all()
+    cx, cy, j = log[0]
+    # first target (confidence priority): the lowest-index centre among the
+    # front pixels with the most known pixels in their patch
+    assert (cx, cy) == (11, 8)
+    p, c = O.fullscan(g, m, 3, d, np.array([cy * 20 + cx]))
+    assert j == p[0]
+    s = d[j]
+    assert out[9, 11, 0] == g[s // 20 + 1, s % 20, 0]
+
+
+def test_fill_confidence_first_target_is_hole_corner_closed_form():
+    g, m = synth.sines2d(48, hole=(20, 28))
+    out, mo, log, steps = O.inpaint(g, m, 5, mode=0, max_steps=1)
+    # front pixels next to a corner of the square hole overlap it least; the
+    # lowest linear index among them is (x0, y0 - 1)
+    assert tuple(log[0][:2]) == (20, 19)
+
+
+def test_fill_runs_to_completion_and_replays():
+    g, m = synth.sines2d(48, hole=(20, 28))
+    out, mo, log, steps = O.inpaint(g, m, 5, mode=0)
+    assert mo.all() and 1 <= steps <= 64
+    # replaying the logged (centre, source) copies onto the input reproduces it
+    d = O.dict_extract(m, 5)
+    rg, rm = g.copy(), m.copy()
+    for cx, cy, j in log:
+        sy, sx = divmod(int(d[j]), 48)
+        for dy in range(-2, 3):
+            for dx in range(-2, 3):
+                if not rm[cy + dy, cx + dx]:
+                    rg[cy + dy, cx + dx] = g[sy + dy, sx + dx]
+                    rm[cy + dy, cx + dx] = 1
+    assert np.array_equal(rg, out) and rm.all()
+    # every filled value is a value of the original known image
+    known_vals = set(g[m.astype(bool)].ravel().tolist())
+    assert set(out[m == 0].ravel().tolist()) <= known_vals
+
+
+def test_fill_sfc_mode_with_full_windows_equals_fullscan_mode():
+    g, m = synth.voronoi2d(40, cfg=2, seed_sub=5)
+    ix = O.build_index(g, m, 5, 4, 4, 8, sample=0)
+    a = O.inpaint(g, m, 5, mode=0, max_steps=25)
+    b = O.inpaint(g, m, 5, mode=1, ix=ix, W=ix["N"], max_steps=25)
+    assert np.array_equal(a[2], b[2]) and np.array_equal(a[0], b[0])
+
+
+def test_fill_criminisi_priority_runs():
+    g, m = synth.voronoi2d(40, cfg=2, seed_sub=6)
+    out, mo, log, steps = O.inpaint(g, m, 5, mode=0, prio=1)
+    assert mo.all() and steps > 0
+
+
+def test_empty_dictionary_is_an_error():
+    g = np.zeros((6, 6, 1), np.float32)
+    m = np.zeros((6, 6), np.uint8)
+    m[0, 0] = 1
+    with pytest.raises(ValueError):
+        O.inpaint(g, m, 3)
