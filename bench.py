@@ -1,0 +1,374 @@
+"""Benchmark: patch queries/s of the SFC multi-index vs the full scan on one GB300.
+
+Workload (the paper-scale 2-D configuration): RGB 1024x1024 float32 image of
+seeded Voronoi regions (gradients, texture, noise), disc holes covering 10 %,
+11x11x3 patches (d = 363), dictionary of ~0.85 M fully known patches, SFC index
+with 8 curves, 8 principal dimensions, 16-bit quantisation, window 64; the query
+batch is every fill-front target of the initial mask (3,597; a seeded cap of
+65,536 is never reached).
+
+One step = sfc_index_build (dictionary, PCA, projection, keys, radix sort) +
+sfc_query_batch over the batch, i.e. every row of the hot path but the full scan
+and the fill loop, which are timed in the same run and reported beside it
+("fullscan", "inpaint").  value = queries per second of whole steps.
+Inputs are resident in HBM when a step starts; the L2 is flushed (a 512 MB
+write) between timed steps, outside the timed interval.
+
+Multi-GPU (torchrun): queries are independent, so every rank runs its own copy of
+the workload (weak scaling, no data-path collective); the step time is the max
+over ranks.  ``--impl reference`` times the CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(width=1024, K=11, curves=8, dims=8, bits=16, window=64, pca_sample=16384, cap=65536)
+METRIC = "patch queries/s: SFC index vs full-scan masked-L2, 1 GB300, oracle-equal picks"
+UNIT = "patch queries/s"
+
+
+def workload_inputs(width=WORKLOAD["width"]):
+    from paper_1712_06326_gb300 import synth
+
+    g, m = synth.voronoi2d(width, cfg=2)
+    t = synth.front_targets(m, WORKLOAD["K"], cap=WORKLOAD["cap"], cfg=2)
+    return g, m, t
+
+
+def index_params():
+    return dict(K=WORKLOAD["K"], curves=WORKLOAD["curves"], dims=WORKLOAD["dims"], bits=WORKLOAD["bits"],
+                window=WORKLOAD["window"], pca_sample=WORKLOAD["pca_sample"])
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample of the same workload)
+# ----------------------------------------------------------------------------
+def oracle_sample(crop=256, y0=768, x0=512):
+    """The oracle as it stands on a crop of the workload: by default the 256x256
+    tile holding the most fill-front targets (482 of the 3,597), with its full
+    8-curve index build and every front-target query of the tile, one thread."""
+    import oracle as O
+    from paper_1712_06326_gb300 import synth
+
+    g, m, _ = workload_inputs()
+    g = np.ascontiguousarray(g[y0:y0 + crop, x0:x0 + crop])
+    m = np.ascontiguousarray(m[y0:y0 + crop, x0:x0 + crop])
+    t = synth.front_targets(m, WORKLOAD["K"])
+    O.build()
+    t0 = time.perf_counter()
+    ix = O.build_index(g, m, WORKLOAD["K"], WORKLOAD["curves"], WORKLOAD["dims"], WORKLOAD["bits"],
+                       sample=WORKLOAD["pca_sample"])
+    lin = O.centres_to_lin(t, O.geometry(g)[1])
+    for tl in lin:
+        O.query(ix, g, m, tl, WORKLOAD["window"])
+    dt = time.perf_counter() - t0
+    sample = (f"{crop}x{crop} tile at (x={x0}, y={y0}) of the workload: N={ix['N']}, Q={len(t)} front targets, "
+              "8-curve index build + all queries")
+    return len(t) / dt, dt, sample
+
+
+def cpu_baseline_obj():
+    v, dt, sample = oracle_sample()
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, "seconds": dt}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_sample(crop=64, y0=768, x0=512)
+    times, qs = [], []
+    sample = ""
+    for _ in range(args.steps):
+        v, dt, sample = oracle_sample()
+        times.append(dt)
+        qs.append(v * dt)
+    value = sum(qs) / sum(times)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "voronoi2d 1024x1024 RGB, K=11, C=8, D=8, b=16, W=64 (oracle on a crop)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    import paper_1712_06326_gb300.sfc as sfc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+        __graft_entry__.build()  # no-op after rank 0 compiled; loads the library
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    g, m, t = workload_inputs()
+    gd = torch.from_numpy(g).to(dev)
+    md = torch.from_numpy(m).to(dev)
+    td = torch.from_numpy(t).to(dev)
+    Q = len(t)
+    prm = index_params()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    pick = torch.empty(Q, dtype=torch.int64, device=dev)
+    cost = torch.empty(Q, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ix = sfc.sfc_index_build(gd, md, **prm)
+        sfc.sfc_query_batch(ix, gd, md, td, pick, cost)
+        return ix
+
+    # ---- warm-up --------------------------------------------------------------
+    for _ in range(args.warmup):
+        step().close()
+    torch.cuda.synchronize()
+    assert sfc.sfc_status() == 0
+
+    # ---- timed steps (event pairs per step; L2 flush between, untimed) -------
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    l0 = sfc.sfc_launch_count()
+    ev = []
+    live = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ix = step()
+        b.record(stream)
+        ev.append((a, b))
+        live.append(ix)
+    torch.cuda.synchronize()
+    barrier()
+    launches = sfc.sfc_launch_count() - l0
+    clk = clocks.stop()
+    for ix in live:
+        ix.close()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tot_ms = float(tt.item())
+    value = Q * args.steps * world / (tot_ms / 1000.0)
+
+    # ---- the dominant kernel: the query kernel, timed alone on its stream -----
+    ix = sfc.sfc_index_build(gd, md, **prm)
+    qk, pos, cand, nc = sfc.sfc_query_candidates(ix, gd, md, td)
+    mean_cand = float(nc.double().mean().item())
+    n_elem = WORKLOAD["K"] ** 2 * 3
+    q_ms = []
+    for _ in range(5):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sfc.sfc_query_batch(ix, gd, md, td, pick, cost)
+        b.record(stream)
+        b.synchronize()
+        q_ms.append(a.elapsed_time(b))
+    q_ms_mean = statistics.mean(q_ms)
+    N = ix.N
+    # algorithmic bytes per query: the gathered candidate patches (n values of 4 B
+    # each), the window ids, and the binary-search probes (8 B per level)
+    per_query = mean_cand * n_elem * 4 + WORKLOAD["curves"] * WORKLOAD["window"] * 4 + \
+        WORKLOAD["curves"] * 8 * int(np.ceil(np.log2(N)))
+    bytes_launch = per_query * Q
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = bytes_launch / (q_ms_mean / 1000.0) / 1e9
+    roofline = {"kernel": "k_query (sfc_query_batch)", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s",
+                "bytes_per_query": per_query, "mean_candidates": mean_cand, "launch_ms": q_ms_mean}
+    query_only_qps = Q / (q_ms_mean / 1000.0)
+
+    # ---- full scan (same queries, a seeded subset) -----------------------------
+    fs_q = 2048
+    sel = torch.from_numpy(np.sort(np.random.default_rng(5).choice(Q, fs_q, replace=False))).to(dev)
+    tsub = td[sel].contiguous()
+    fs_ms = []
+    for r in range(3):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fp, fc = sfc.fullscan_query_batch(gd, md, md, tsub, K=WORKLOAD["K"])
+        b.record(stream)
+        b.synchronize()
+        if r > 0:
+            fs_ms.append(a.elapsed_time(b))
+    fs_qps = fs_q / (statistics.mean(fs_ms) / 1000.0)
+    sp = pick[sel]
+    agree = float((sp == fp).double().mean().item())
+    # acceleration error (Sec. III.C): L2 norm of the pick / of the exact pick - 1
+    ae = float((torch.sqrt(cost[sel].double()) / torch.sqrt(fc.double()).clamp_min(1e-30) - 1.0).mean().item())
+    fs_flops = 3.0 * float(N) * n_elem * fs_q
+    fullscan = {"qps": fs_qps, "queries": fs_q, "ms": statistics.mean(fs_ms), "pick_agreement_sfc": agree,
+                "acceleration_error_mean": ae,
+                "fp32_gflops_algorithmic": fs_flops / (statistics.mean(fs_ms) / 1000.0) / 1e9}
+
+    # ---- end to end through the C-ABI with host buffers ----------------------
+    gh = torch.from_numpy(g).pin_memory()
+    mh = torch.from_numpy(m).pin_memory()
+    th = torch.from_numpy(t).pin_memory()
+    ph = torch.empty(Q, dtype=torch.int64).pin_memory()
+    ch_ = torch.empty(Q, dtype=torch.float32).pin_memory()
+    e2e_ms = []
+    for r in range(max(2, min(args.steps, 4)) + 1):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g2 = gh.to(dev, non_blocking=True)
+        m2 = mh.to(dev, non_blocking=True)
+        t2 = th.to(dev, non_blocking=True)
+        ixe = sfc.sfc_index_build(g2, m2, **prm)
+        p2, c2 = sfc.sfc_query_batch(ixe, g2, m2, t2)
+        ph.copy_(p2, non_blocking=True)
+        ch_.copy_(c2, non_blocking=True)
+        torch.cuda.synchronize()
+        if r > 0:
+            e2e_ms.append(1000 * (time.perf_counter() - t0))
+        ixe.close()
+    e2e = {"value": Q / (statistics.mean(e2e_ms) / 1000.0), "unit": UNIT,
+           "h2d_bytes_per_step": int(g.nbytes + m.nbytes + t.nbytes), "d2h_bytes_per_step": int(Q * 12)}
+
+    # ---- fill loop, the small plain-method case (128^2 grey, 24^2 hole) --------
+    from paper_1712_06326_gb300 import synth
+
+    g1, m1 = synth.sines2d(128)
+    inp = {}
+    for mode, name in ((sfc.SFC_MODE_FULLSCAN, "fullscan"), (sfc.SFC_MODE_SFC, "sfc")):
+        gg = torch.from_numpy(g1).to(dev)
+        mm = torch.from_numpy(m1).to(dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps, _ = sfc.inpaint_run(gg, mm, mode=mode, K=9, curves=8, dims=8, bits=16, window=64, pca_sample=0)
+        torch.cuda.synchronize()
+        inp[name] = {"ms": 1000 * (time.perf_counter() - t0), "steps": steps}
+    ix.close()
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "voronoi2d 1024x1024 RGB, 10% disc holes, K=11 (d=363), SFC C=8 D=8 b=16 W=64",
+                       "queries_per_step": Q, "dictionary": N, "pca_sample": WORKLOAD["pca_sample"],
+                       "step": "sfc_index_build + sfc_query_batch", "l2": "flushed (512 MB write) between steps",
+                       "parallelism": f"replica x{world}"},
+            "roofline": roofline, "gpu_launches": int(launches), "e2e": e2e, "clocks": clk,
+            "query_only": {"qps": query_only_qps, "ms": q_ms_mean},
+            "index_build_ms": tot_ms / args.steps - q_ms_mean,
+            "fullscan": fullscan, "inpaint_128x128": inp}
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_obj()
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

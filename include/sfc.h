@@ -1,0 +1,179 @@
+/* sfc.h -- C-ABI of libsfc, the GB300 (sm_103a) patch-search library for
+ * exemplar-based inpainting with space-filling-curve indices (Dahmen et al.,
+ * "Space-Filling Curve Indices as Acceleration Structure for Exemplar-Based
+ * Inpainting").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Pointers.  Unless a parameter says "host", it is a DEVICE pointer on the
+ * current CUDA device, owned by the caller, which keeps it alive until the work
+ * enqueued on `stream` has finished.  `stream` is a cudaStream_t passed as
+ * void* (NULL = the legacy default stream).
+ *
+ * Grid layout.  float32, C-contiguous [Z][Y][X][ch] (x fastest, channel
+ * innermost); Z = 1 for 2-D.  Masks are uint8 [Z][Y][X], 1 = known value.
+ * A pixel's linear index is (z*Y + y)*X + x.  Patches are K x K (x K) boxes
+ * centred on a pixel, with elements in patch raster order (x fastest) and the
+ * channels innermost (the paper treats RGB values separately, Sec. II intro).
+ * Centres are int32 (x, y[, z]) rows; a valid centre keeps its whole patch
+ * inside the grid.
+ *
+ * Dictionary.  The patches whose box is inside the grid and fully known under
+ * the dictionary mask (Sec. I: the known parts of the image split into
+ * patches).  A dictionary id is the rank of the centre in raster order.
+ *
+ * Cost.  Masked squared L2 (Sec. II after Fig. 1: differences at unknown
+ * pixels are taken as zero), optionally weighted per channel:
+ *   cost(t, j) = sum over known elements e of t: w[ch(e)] * (t_e - p_{j,e})^2.
+ * Picks are the argmin over the exact value -- the FP64 sum over elements in
+ * raster order with operands widened from FP32 and no fused multiply-add --
+ * with ties to the lowest dictionary id.  The kernels compute FP32 costs and
+ * rescore in FP64 every candidate whose FP32 cost lies inside a band derived
+ * from the FP32 rounding error bound, so the picks are exactly those of that
+ * definition.  Reported costs are that FP64 value rounded to FP32.
+ *
+ * Errors.  Every entry point returns SFC_OK (0) or a negative SFC_E* code and
+ * records a message readable with sfc_last_error() (per host thread).  Calls
+ * are asynchronous unless stated: argument errors are reported at once; faults
+ * a kernel detects (an invalid centre, a timed-out wait) are written to a
+ * status word and reported by sfc_status() or by the next synchronising call.
+ * No entry point falls back to a CPU path.
+ */
+#ifndef SFC_H
+#define SFC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SFC_OK = 0,
+  SFC_EINVAL = -1,       /* invalid argument (sizes, null pointers, parameter ranges) */
+  SFC_ENOMEM = -2,       /* device allocation failed */
+  SFC_ECUDA = -3,        /* a CUDA runtime call failed */
+  SFC_ETIMEOUT = -4,     /* a bounded device-side wait gave up */
+  SFC_EUNSUPPORTED = -5, /* device is not sm_103 / feature not built */
+  SFC_EDEVICE = -6       /* a kernel flagged invalid data (e.g. a centre outside the grid) */
+};
+
+enum { SFC_SELECT_ALL = 0, SFC_SELECT_BEST = 1 };
+enum { SFC_FP32 = 0, SFC_BF16 = 1 };
+enum { SFC_PRIO_CONFIDENCE = 0, SFC_PRIO_CRIMINISI = 1 };
+enum { SFC_MODE_FULLSCAN = 0, SFC_MODE_SFC = 1 };
+
+/* Grid geometry.  ext = {X, Y, Z}; ndim 2 (Z must be 1) or 3; ch >= 1. */
+typedef struct sfc_grid {
+  int32_t ndim;
+  int32_t ch;
+  int64_t ext[3];
+} sfc_grid;
+
+/* Method parameters (Table 1 of the paper: K, c, D, k; here k is a window W).
+ * Host pointers inside are read during the call only. */
+typedef struct sfc_params {
+  int32_t K;              /* patch side, odd, 3..15, <= every extent */
+  int32_t curves;         /* C: number of indices, 1..8 (2-D) or 1..14 (3-D) (Sec. II, Fig. 2) */
+  int32_t dims;           /* D: principal components kept, 1..16, <= subset length (Sec. II.A) */
+  int32_t bits;           /* b: bits per quantised coordinate, 1..21 (Sec. II.C) */
+  int32_t window;         /* W >= 1: sorted slots read around the binary-search position */
+  float subset_frac;      /* c in (0, 1]: fraction of patch pixels per index (Sec. II) */
+  const int32_t* shifts;  /* host, curves*dims integer shifts in [0, 2^b), or NULL (= none) */
+  const float* ch_weights;/* host, ch positive weights, or NULL (= all 1) */
+  const float* basis;     /* host, curves*s*D FP32 basis (row i = subset value i), or NULL = PCA */
+  const float* mean;      /* host, curves*s FP32 means (required with basis) */
+  int32_t select;         /* SFC_SELECT_ALL or SFC_SELECT_BEST (Fig. 1(b)) */
+  int32_t precision;      /* SFC_FP32 (SFC_BF16 reserved for the GEMM pre-score) */
+  int64_t pca_sample;     /* dictionary entries used for the covariance; <= 0: all */
+  int32_t priority;       /* fill order: SFC_PRIO_CONFIDENCE or SFC_PRIO_CRIMINISI (2-D) */
+  int32_t keep_intermediates; /* 1: keep projections and unsorted keys for sfc_index_export */
+} sfc_params;
+
+typedef struct sfc_index sfc_index; /* opaque; owned by the library */
+
+/* Fill `p` with the paper's defaults (K = 9, c = 0.6, D = 10, 8 indices; Sec.
+ * III.A) and W = 80, b = 8, SELECT_ALL, FP32, pca_sample = 16384. */
+void sfc_params_default(sfc_params* p);
+
+/* Build the multi-index (Sec. II.A-C): dictionary extraction, the pixel subsets
+ * of Fig. 2, a PCA per index (FP64 covariance over a deterministic sample,
+ * FP64 Jacobi eigen-solve) unless p->basis is given, FP32 projection, per-axis
+ * quantisation to b bits, Morton keys (top 64 bits), and a stable radix sort of
+ * (key, id) per index.  grid/dict_mask: device, layout above.  On success *out
+ * owns device memory until sfc_index_destroy.  Synchronises `stream` once (to
+ * learn the dictionary size).  SFC_EINVAL if the dictionary is empty. */
+int sfc_index_build(const float* grid, const uint8_t* dict_mask, const sfc_grid* g, const sfc_params* p,
+                    void* stream, sfc_index** out);
+
+/* Release an index (waits for the device first).  NULL is accepted. */
+int sfc_index_destroy(sfc_index* ix);
+
+/* Sizes of an index: dictionary size N, subset pixels m, values per subset s. */
+int sfc_index_info(const sfc_index* ix, int64_t* N, int32_t* m, int32_t* s);
+
+/* Copy the index's arrays to HOST buffers (any may be NULL); synchronises.
+ * dict: N centre linear indices (int64); subsets: C*m patch pixel indices;
+ * basis: C*s*D; mean: C*s; evals: C*s (descending; NaN with a given basis);
+ * lo, scale: C*D; proj: C*N*D and keys: C*N (need keep_intermediates);
+ * skeys: C*N; sids: C*N (sorted order per index). */
+int sfc_index_export(const sfc_index* ix, int64_t* dict, int32_t* subsets, float* basis, float* mean, double* evals,
+                     float* lo, float* scale, float* proj, uint64_t* keys, uint64_t* skeys, uint32_t* sids);
+
+/* Answer Q queries against the index (Fig. 1(b)-(d)): for each centre, select
+ * the indices (all, or the one covering most known subset pixels), project the
+ * known subset values (unknown ones contribute zero), quantise with the index's
+ * lo/scale (clamped), take the Morton key, binary-search each sorted key array,
+ * gather the W sorted slots around the position (clamped inside [0, N)), rescore
+ * the union of candidates with the exact cost in image space and return the
+ * argmin.  grid/cur_mask: the current image and known-mask (same geometry as the
+ * build); centres: Q x ndim int32; pick: Q int64 dictionary ids; cost: Q float
+ * (exact cost of the pick).  Q = 0 is a no-op.  A centre outside the valid range
+ * yields pick = -1, cost = NaN and SFC_EDEVICE from sfc_status(). */
+int sfc_query_batch(const sfc_index* ix, const float* grid, const uint8_t* cur_mask, const int32_t* centres,
+                    int64_t Q, int64_t* pick, float* cost, void* stream);
+
+/* Intermediate results of sfc_query_batch for checking: qkeys (Q*C uint64),
+ * pos (Q*C int64 lower_bound positions; -1 for unselected indices),
+ * cand (Q*C*W int32 sorted unique candidate ids, padded with -1), ncand (Q int32). */
+int sfc_query_candidates(const sfc_index* ix, const float* grid, const uint8_t* cur_mask, const int32_t* centres,
+                         int64_t Q, uint64_t* qkeys, int64_t* pos, int32_t* cand, int32_t* ncand, void* stream);
+
+/* Exact full scan (Sec. I): the cost of every dictionary patch (dictionary =
+ * fully known patches of dict_mask) for each of the Q centres, evaluated against
+ * cur_mask, then the global argmin (ties to the lowest id).  p supplies K and
+ * ch_weights.  Outputs as sfc_query_batch. */
+int fullscan_query_batch(const float* grid, const uint8_t* dict_mask, const uint8_t* cur_mask, const sfc_grid* g,
+                         const sfc_params* p, const int32_t* centres, int64_t Q, int64_t* pick, float* cost,
+                         void* stream);
+
+/* Exemplar-based inpainting loop (Sec. I; Fig. 1(a)): repeat { find the fill
+ * front (known pixels with an unknown axis neighbour; centres moved inside the
+ * valid range), take the centre of highest priority (ties: lowest linear
+ * index), search the dictionary of the initial mask (mode: full scan, or SFC
+ * query against an index built here from the initial image), copy the source
+ * patch into the target's unknown pixels } until no pixel is unknown or
+ * max_steps (> 0) steps.  grid, mask: device, updated in place.  log: device
+ * int64 [max_steps or #unknown][ndim + 1] rows (centre coordinates, pick), or
+ * NULL.  steps_done: host.  Synchronises `stream`. */
+int inpaint_run(float* grid, uint8_t* mask, const sfc_grid* g, const sfc_params* p, int32_t mode, int64_t max_steps,
+                int64_t* log, int64_t* steps_done, void* stream);
+
+/* Read and clear the library's device-side status flags (synchronises stream):
+ * SFC_OK, SFC_EDEVICE (invalid centre seen) or SFC_ETIMEOUT (a bounded wait
+ * gave up). */
+int sfc_status(void* stream);
+
+/* Number of kernels the library has launched in this process so far (all host
+ * threads).  Diagnostics: the difference across a region counts its launches. */
+uint64_t sfc_launch_count(void);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* sfc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFC_H */

@@ -385,7 +385,7 @@ void or_project(const float* grid, int ndim, const int64_t* ext, int ch, int K, 
 // ----------------------------------------------------------------------------
 // Quantisation of principal coordinates (Sec. II.C: the listings compare byte
 // coordinates).  Reading: per dimension lo = min, hi = max over the N dictionary
-// projections; scale = (float)(2^b / ((double)hi - (double)lo)), or 0 when
+// projections (as real values: a zero is stored as +0); scale = (float)(2^b / ((double)hi - (double)lo)), or 0 when
 // hi == lo; q = clamp(floor((y - lo) * scale), 0, 2^b - 1) with the subtraction
 // and the product each rounded to FP32.  Queries reuse lo/scale and the clamp.
 // ----------------------------------------------------------------------------
@@ -397,6 +397,8 @@ void or_quant_params(const float* y, int64_t N, int D, int bits, float* lo, floa
       if (v < mn) mn = v;
       if (v > mx) mx = v;
     }
+    if (mn == 0.0f) mn = 0.0f;  // the real value zero: stored as +0
+    if (mx == 0.0f) mx = 0.0f;
     lo[k] = mn;
     scale[k] = mx > mn ? (float)(std::ldexp(1.0, bits) / ((double)mx - (double)mn)) : 0.0f;
   }

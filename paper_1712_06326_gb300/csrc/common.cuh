@@ -1,0 +1,129 @@
+// common.cuh -- shared device helpers of libsfc (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sfc.h"
+
+namespace sfc {
+
+// Device-side status bits (ORed into a library-owned word, read by sfc_status).
+enum : uint32_t { ST_BAD_CENTRE = 1u, ST_TIMEOUT = 2u, ST_OVERFLOW = 4u };
+
+// Upper bound of the spin iterations of any wait on another CTA's flag.
+constexpr long long kSpinLimit = 1ll << 24;
+
+// Geometry as the kernels see it.
+struct Geo {
+  int ndim, ch, K, r, P;  // P = K^ndim pixels per patch
+  int64_t X, Y, Z;
+  int n;                  // values per patch, P * ch
+};
+
+__host__ __device__ inline int64_t lin_of(const Geo& g, int64_t x, int64_t y, int64_t z) {
+  return (z * g.Y + y) * g.X + x;
+}
+
+// Linear pixel offset of patch pixel pp relative to the centre.
+__host__ __device__ inline int64_t patch_off(const Geo& g, int pp) {
+  int px = pp % g.K, py = (pp / g.K) % g.K, pz = g.ndim == 3 ? pp / (g.K * g.K) : g.r;
+  return ((int64_t)(pz - g.r) * g.Y + (py - g.r)) * g.X + (px - g.r);
+}
+
+// Valid centre: the whole patch inside the grid.
+__device__ inline bool centre_ok(const Geo& g, int64_t x, int64_t y, int64_t z) {
+  if (x < g.r || x > g.X - 1 - g.r || y < g.r || y > g.Y - 1 - g.r) return false;
+  if (g.ndim == 3) return z >= g.r && z <= g.Z - 1 - g.r;
+  return z == 0;
+}
+
+// ---------------------------------------------------------------------------
+// packed (cost, id) keys: non-negative IEEE values order like their bit
+// patterns, so min over (bits << 32 | id) is argmin with ties to the lowest id.
+__device__ inline unsigned long long pack_min(float c, uint32_t id) {
+  return ((unsigned long long)__float_as_uint(c) << 32) | id;
+}
+
+template <typename T>
+__device__ inline T warp_min(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    T w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w < v ? w : v;
+  }
+  return v;
+}
+
+__device__ inline float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Lexicographic (c64, id) minimum across a warp.
+__device__ inline void warp_argmin64(double& c, int64_t& id) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    int64_t i2 = __shfl_xor_sync(0xffffffffu, id, o);
+    if (c2 < c || (c2 == c && i2 < id)) {
+      c = c2;
+      id = i2;
+    }
+  }
+}
+
+// Exact cost of one (target, source) pair in FP64: known elements of the target
+// in patch raster order, channel innermost, d = t - p in FP64 (operands widened
+// from FP32), term = w * (d * d), sequential sum, no fused multiply-add.
+// `tv`/`tm` hold the target's values and per-pixel known flags; `eoff` the
+// element offsets (pixel offset * ch + channel) relative to centre * ch.
+__device__ inline double exact_cost64(const float* __restrict__ grid, int64_t src_base, const float* tv,
+                                      const uint8_t* tm, const int* eoff, int P, int ch, const float* w) {
+  double acc = 0.0;
+  for (int pp = 0; pp < P; ++pp) {
+    if (!tm[pp]) continue;
+    for (int c = 0; c < ch; ++c) {
+      int e = pp * ch + c;
+      double d = __dsub_rn((double)tv[e], (double)grid[src_base + eoff[e]]);
+      double sq = __dmul_rn(d, d);
+      double term = __dmul_rn((double)w[c], sq);
+      acc = __dadd_rn(acc, term);
+    }
+  }
+  return acc;
+}
+
+// Half-width of the FP32 band: |c32 - c| <= gamma * c for a sum of n
+// non-negative terms, each d^2 (d rounded once) times a rounded weight, summed by
+// FMA: gamma = (n + 8) * 2^-24.  A candidate can be the exact argmin only if
+// c32 <= min32 * (1 + 3 gamma) + n * 2^-126 (absolute slack for underflow).
+__device__ inline double band_limit(float min32, int n) {
+  double gamma = (double)(n + 8) * 5.9604644775390625e-8;
+  return (double)min32 * (1.0 + 3.0 * gamma) + (double)n * 1.1754943508222875e-38;
+}
+
+// Quantised coordinate (same arithmetic for dictionary entries and queries):
+// clamp(floor((y - lo) * scale), 0, 2^b - 1), subtraction and product rounded to
+// FP32 separately.
+__device__ inline uint32_t quantise_one(float y, float lo, float scale, int bits) {
+  float t = __fsub_rn(y, lo);
+  float u = __fmul_rn(t, scale);
+  float f = floorf(u);
+  float top = (float)((1u << bits) - 1u);
+  if (!(f >= 0.0f)) f = 0.0f;
+  if (f > top) f = top;
+  return (uint32_t)f;
+}
+
+// Morton / z-address: bit planes from the highest, dimension 0 first inside a
+// plane; the first 64 bits emitted when D * bp > 64.
+__device__ inline uint64_t morton_key(const uint32_t* q, int D, int bp) {
+  uint64_t key = 0;
+  int n = 0;
+  for (int p = bp - 1; p >= 0 && n < 64; --p)
+    for (int k = 0; k < D && n < 64; ++k, ++n) key = (key << 1) | (uint64_t)((q[k] >> p) & 1u);
+  return key;
+}
+
+}  // namespace sfc

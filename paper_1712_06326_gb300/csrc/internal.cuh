@@ -1,0 +1,92 @@
+// internal.cuh -- declarations shared by the translation units of libsfc.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace sfc {
+
+void set_error(const std::string& msg);
+
+// Host-side count of kernel launches made by the library (diagnostics).
+void count_launch();
+
+// Evaluate a CUDA runtime call; on failure record the message and return SFC_ECUDA
+// (SFC_ENOMEM for allocation failures) from the enclosing function.
+#define SFC_TRY(call)                                                                                  \
+  do {                                                                                                 \
+    cudaError_t e_ = (call);                                                                           \
+    if (e_ != cudaSuccess) {                                                                           \
+      ::sfc::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                            \
+      return e_ == cudaErrorMemoryAllocation ? SFC_ENOMEM : SFC_ECUDA;                                 \
+    }                                                                                                  \
+  } while (0)
+
+#define SFC_CHECK(rc)                     \
+  do {                                    \
+    int r_ = (rc);                        \
+    if (r_ != SFC_OK) return r_;          \
+  } while (0)
+
+// Library-owned device status word of the current device (see ST_* bits).
+uint32_t* status_word();
+
+// Per-index state (host struct, device arrays).
+struct Index {
+  Geo g;
+  int C, D, bits, bp, W, select, m, s;
+  int64_t N;
+  float frac;
+  int64_t pca_sample;
+  bool keep;
+  std::vector<int32_t> subset_h;  // C*m patch pixel indices
+  std::vector<float> weights_h;   // ch
+  // device arrays
+  uint32_t* dict = nullptr;   // N centre linear indices
+  int* eoff_all = nullptr;    // n element offsets (pixel offset * ch + channel) of the whole patch
+  int* sub_eoff = nullptr;    // C*s element offsets of the subset values
+  int* sub_pix = nullptr;     // C*m patch pixel indices of the subsets
+  float* weights = nullptr;   // ch
+  float* basis = nullptr;     // C*s*D
+  float* mean = nullptr;      // C*s
+  double* evals = nullptr;    // C*s
+  float* lo = nullptr;        // C*D
+  float* scale = nullptr;     // C*D
+  int32_t* shifts = nullptr;  // C*D
+  float* proj = nullptr;      // C*N*D (kept only with keep_intermediates)
+  uint64_t* keys = nullptr;   // C*N unsorted (kept only with keep_intermediates)
+  uint64_t* skeys = nullptr;  // C*N
+  uint32_t* sids = nullptr;   // C*N
+};
+
+// k_dict.cu
+int dict_extract(const uint8_t* mask, const Geo& g, cudaStream_t st, uint32_t** dict, int64_t* N);
+
+// k_pca.cu: basis/mean/evals of every index from a deterministic sample.
+int pca_build(Index& ix, const float* grid, cudaStream_t st);
+
+// k_index.cu: projection, quantisation, Morton keys.
+int project_and_key(Index& ix, const float* grid, cudaStream_t st, float* proj, uint64_t* keys);
+
+// k_sort.cu: stable LSD radix sort (onesweep) of (key, id) per index.
+int radix_sort_pairs(const uint64_t* keys, uint64_t* skeys, uint32_t* sids, int64_t N, int C, int key_bits,
+                     cudaStream_t st);
+
+// k_query.cu
+int query_batch(const Index& ix, const float* grid, const uint8_t* cur_mask, const int32_t* centres, int64_t Q,
+                int64_t* pick, float* cost, uint64_t* qkeys, int64_t* pos, int32_t* cand, int32_t* ncand,
+                cudaStream_t st);
+
+// k_fullscan.cu
+int fullscan_batch(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
+                   const int* eoff_all, const float* weights, bool weighted, const int32_t* centres,
+                   const int64_t* centre_lin, int64_t Q, int64_t* pick, float* cost, cudaStream_t st);
+
+// helpers (sfc_api.cu)
+int upload_patch_tables(const Geo& g, int** eoff_all, cudaStream_t st);
+
+}  // namespace sfc

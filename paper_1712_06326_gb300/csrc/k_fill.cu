@@ -1,0 +1,363 @@
+// k_fill.cu -- the exemplar-based inpainting loop (Sec. I; Fig. 1(a)) on the
+// device.  Per step, without a host round trip:
+//   k_prio    priorities of the candidate centres whose value can have changed
+//             (the whole grid at the start, then the box of radius 2r+1 around the
+//             last target: the patch changed mask/values/confidence within r,
+//             which reaches front flags within r+1 and confidence sums within 2r);
+//   k_argmax  packed max over (valid, priority bits, ~linear index): the highest
+//             priority, ties to the lowest linear index;
+//   k_select  decode the target (or mark the loop done);
+//   search    full scan (k_fs_scan + k_fs_band, Q = 1) or SFC query (Q = 1);
+//   k_insert  copy the source patch into the target's unknown pixels, mark them
+//             known, give them the target's confidence term, log the step.
+// Candidate centres: a known pixel with an unknown axis neighbour (4-/6-
+// connected) is a front pixel; its centre is the pixel moved into the valid
+// range [r, ext-1-r] per axis.  Priority (Criminisi et al.'s order, written out
+// since the paper defers to it): confidence term Cterm = (sum of confidence over
+// the patch, FP32 in raster order) / K^dim; CONFIDENCE: P = Cterm; CRIMINISI
+// (2-D): P = Cterm * (|(-gy) nx + gx ny| + 0.001), grey-value gradient by central
+// differences over known neighbours (one-sided if one side is unknown), n the
+// normalised central-difference gradient of the known-mask (outside = known).
+// Every product and sum is rounded separately (explicit _rn intrinsics).
+#include "internal.cuh"
+
+namespace sfc {
+
+int fullscan_single(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
+                    const int* eoff_all, const float* weights, bool weighted, const int64_t* centre_lin,
+                    int64_t* pick, float* cost, float* tilemin, unsigned int* gmin, cudaStream_t st);
+
+namespace {
+
+struct FillState {
+  unsigned long long* key;  // npix packed priorities
+  float* conf;              // npix confidence
+  float* cterm;             // npix confidence term of candidate centres
+  unsigned long long* best;
+  int64_t* sel_lin;         // chosen centre (linear)
+  int32_t* sel_xyz;         // chosen centre (x, y, z)
+  float* sel_cterm;
+  int64_t* pick;
+  float* cost;
+  int* done;
+  int64_t* steps;
+};
+
+__device__ inline bool in_grid(const Geo& g, int64_t x, int64_t y, int64_t z) {
+  return x >= 0 && y >= 0 && z >= 0 && x < g.X && y < g.Y && z < g.Z;
+}
+
+__device__ inline bool is_front(const Geo& g, const uint8_t* mask, int64_t x, int64_t y, int64_t z) {
+  if (!mask[lin_of(g, x, y, z)]) return false;
+  const int64_t nb[6][3] = {{x - 1, y, z}, {x + 1, y, z}, {x, y - 1, z}, {x, y + 1, z}, {x, y, z - 1}, {x, y, z + 1}};
+  for (int a = 0; a < 2 * g.ndim; ++a)
+    if (in_grid(g, nb[a][0], nb[a][1], nb[a][2]) && !mask[lin_of(g, nb[a][0], nb[a][1], nb[a][2])]) return true;
+  return false;
+}
+
+__device__ inline float gray_at(const Geo& g, const float* grid, int64_t q) {
+  if (g.ch == 1) return grid[q];
+  float acc = grid[q * g.ch];
+  for (int c = 1; c < g.ch; ++c) acc = __fadd_rn(acc, grid[q * g.ch + c]);
+  return __fdiv_rn(acc, (float)g.ch);
+}
+
+// Priority of centre (x, y, z); writes key (0 = not a candidate) and cterm.
+__device__ void prio_one(const Geo& g, const float* __restrict__ grid, const uint8_t* __restrict__ mask,
+                         const float* __restrict__ conf, int prio, int64_t x, int64_t y, int64_t z,
+                         unsigned long long* key, float* cterm) {
+  const int64_t c = lin_of(g, x, y, z);
+  if (!centre_ok(g, x, y, z)) {
+    key[c] = 0ull;
+    return;
+  }
+  // preimage of the clamping
+  int64_t lo[3], hi[3];
+  const int64_t cc[3] = {x, y, z}, ext[3] = {g.X, g.Y, g.Z};
+  for (int a = 0; a < 3; ++a) {
+    if (a >= g.ndim) {
+      lo[a] = hi[a] = 0;
+      continue;
+    }
+    lo[a] = cc[a] == g.r ? 0 : cc[a];
+    hi[a] = cc[a] == ext[a] - 1 - g.r ? ext[a] - 1 : cc[a];
+  }
+  bool cand = false;
+  for (int64_t pz = lo[2]; pz <= hi[2] && !cand; ++pz)
+    for (int64_t py = lo[1]; py <= hi[1] && !cand; ++py)
+      for (int64_t px = lo[0]; px <= hi[0] && !cand; ++px) cand = is_front(g, mask, px, py, pz);
+  if (!cand) {
+    key[c] = 0ull;
+    return;
+  }
+  float sum = 0.0f;
+  for (int pp = 0; pp < g.P; ++pp) sum = __fadd_rn(sum, conf[c + patch_off(g, pp)]);
+  const float Ct = __fdiv_rn(sum, (float)g.P);
+  float P = Ct;
+  if (prio == SFC_PRIO_CRIMINISI) {
+    const bool kc = mask[c] != 0;
+    float gxy[2];
+    for (int a = 0; a < 2; ++a) {
+      int64_t x0 = x - (a == 0), y0 = y - (a == 1), x1 = x + (a == 0), y1 = y + (a == 1);
+      bool k0 = in_grid(g, x0, y0, 0) && mask[lin_of(g, x0, y0, 0)];
+      bool k1 = in_grid(g, x1, y1, 0) && mask[lin_of(g, x1, y1, 0)];
+      float gv = 0.0f;
+      if (k0 && k1)
+        gv = __fmul_rn(0.5f, __fsub_rn(gray_at(g, grid, lin_of(g, x1, y1, 0)), gray_at(g, grid, lin_of(g, x0, y0, 0))));
+      else if (kc && k1)
+        gv = __fsub_rn(gray_at(g, grid, lin_of(g, x1, y1, 0)), gray_at(g, grid, c));
+      else if (kc && k0)
+        gv = __fsub_rn(gray_at(g, grid, c), gray_at(g, grid, lin_of(g, x0, y0, 0)));
+      gxy[a] = gv;
+    }
+    auto mval = [&](int64_t xx, int64_t yy) -> float {
+      if (!in_grid(g, xx, yy, 0)) return 1.0f;
+      return mask[lin_of(g, xx, yy, 0)] ? 1.0f : 0.0f;
+    };
+    float mx = __fmul_rn(0.5f, __fsub_rn(mval(x + 1, y), mval(x - 1, y)));
+    float my = __fmul_rn(0.5f, __fsub_rn(mval(x, y + 1), mval(x, y - 1)));
+    float nrm = __fsqrt_rn(__fadd_rn(__fmul_rn(mx, mx), __fmul_rn(my, my)));
+    float nx = 0.0f, ny = 0.0f;
+    if (nrm > 0.0f) {
+      nx = __fdiv_rn(mx, nrm);
+      ny = __fdiv_rn(my, nrm);
+    }
+    float t1 = __fmul_rn(-gxy[1], nx);
+    float t2 = __fmul_rn(gxy[0], ny);
+    float Dt = fabsf(__fadd_rn(t1, t2));
+    P = __fmul_rn(Ct, __fadd_rn(Dt, 0.001f));
+  }
+  key[c] = (1ull << 63) | ((unsigned long long)__float_as_uint(P) << 32) | (unsigned long long)(0xffffffffu - (uint32_t)c);
+  cterm[c] = Ct;
+}
+
+// Whole grid (box == nullptr) or the box around the last target.
+__global__ void k_prio(const float* __restrict__ grid, const uint8_t* __restrict__ mask, Geo g, int prio,
+                       FillState s, int whole) {
+  if (!whole && *s.done) return;
+  int64_t bx0 = 0, by0 = 0, bz0 = 0, bnx = g.X, bny = g.Y, bnz = g.Z;
+  if (!whole) {
+    const int R = 2 * g.r + 1;
+    const int64_t t = *s.sel_lin;
+    const int64_t tx = t % g.X, ty = (t / g.X) % g.Y, tz = t / (g.X * g.Y);
+    bx0 = tx - R;
+    by0 = ty - R;
+    bz0 = g.ndim == 3 ? tz - R : 0;
+    bnx = 2 * R + 1;
+    bny = 2 * R + 1;
+    bnz = g.ndim == 3 ? 2 * R + 1 : 1;
+  }
+  const int64_t total = bnx * bny * bnz;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t x = bx0 + i % bnx, y = by0 + (i / bnx) % bny, z = bz0 + i / (bnx * bny);
+    if (!in_grid(g, x, y, z)) continue;
+    prio_one(g, grid, mask, s.conf, prio, x, y, z, s.key, s.cterm);
+  }
+}
+
+__global__ void k_argmax(const unsigned long long* __restrict__ key, int64_t npix, FillState s) {
+  if (*s.done) return;
+  unsigned long long m = 0ull;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix; i += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long v = key[i];
+    m = v > m ? v : m;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long w = __shfl_xor_sync(0xffffffffu, m, o);
+    m = w > m ? w : m;
+  }
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(s.best, m);
+}
+
+__global__ void k_select(Geo g, FillState s, int64_t max_steps) {
+  if (*s.done) return;
+  const unsigned long long b = *s.best;
+  *s.best = 0ull;
+  if (b == 0ull || (max_steps > 0 && *s.steps >= max_steps)) {
+    *s.done = 1;
+    return;
+  }
+  const int64_t c = (int64_t)(0xffffffffu - (uint32_t)(b & 0xffffffffull));
+  *s.sel_lin = c;
+  s.sel_xyz[0] = (int32_t)(c % g.X);
+  s.sel_xyz[1] = (int32_t)((c / g.X) % g.Y);
+  s.sel_xyz[2] = (int32_t)(c / (g.X * g.Y));
+  *s.sel_cterm = s.cterm[c];
+}
+
+__global__ void k_insert(float* __restrict__ grid, uint8_t* __restrict__ mask, Geo g, const uint32_t* __restrict__ dict,
+                         FillState s, int64_t* __restrict__ log, int64_t log_cap, int64_t* __restrict__ unknown_left,
+                         uint32_t* __restrict__ status) {
+  if (*s.done) return;
+  const int64_t t = *s.sel_lin;
+  const int64_t j = *s.pick;
+  if (j < 0) {
+    if (threadIdx.x == 0) *s.done = 1;
+    return;
+  }
+  const int64_t src = dict[j];
+  const float ct = *s.sel_cterm;
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int pp = threadIdx.x; pp < g.P; pp += blockDim.x) {
+    const int64_t off = patch_off(g, pp);
+    const int64_t qt = t + off;
+    if (mask[qt]) continue;
+    const int64_t qs = src + off;
+    for (int c = 0; c < g.ch; ++c) grid[qt * g.ch + c] = grid[qs * g.ch + c];
+    mask[qt] = 1;
+    s.conf[qt] = ct;
+    ++mine;
+  }
+  atomicAdd(&cnt, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int64_t k = *s.steps;
+    if (cnt == 0) {  // every step fills at least one pixel; stop rather than spin
+      atomicOr(status, ST_OVERFLOW);
+      *s.done = 1;
+      return;
+    }
+    if (log && k < log_cap) {
+      log[k * (g.ndim + 1) + 0] = s.sel_xyz[0];
+      log[k * (g.ndim + 1) + 1] = s.sel_xyz[1];
+      if (g.ndim == 3) log[k * (g.ndim + 1) + 2] = s.sel_xyz[2];
+      log[k * (g.ndim + 1) + g.ndim] = j;
+    }
+    *s.steps = k + 1;
+    *unknown_left -= cnt;
+  }
+}
+
+__global__ void k_conf_init(const uint8_t* __restrict__ mask, int64_t npix, float* __restrict__ conf,
+                            int64_t* __restrict__ unknown) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < npix) {
+    conf[i] = mask[i] ? 1.0f : 0.0f;
+    if (!mask[i]) atomicAdd((unsigned long long*)unknown, 1ull);
+  }
+}
+
+__global__ void k_state_init(FillState s, Geo g) {
+  *s.best = 0ull;
+  *s.done = 0;
+  *s.steps = 0;
+  *s.sel_lin = lin_of(g, g.r, g.r, g.ndim == 3 ? g.r : 0);
+  s.sel_xyz[0] = g.r;
+  s.sel_xyz[1] = g.r;
+  s.sel_xyz[2] = g.ndim == 3 ? g.r : 0;
+  *s.sel_cterm = 0.0f;
+  *s.pick = -1;
+}
+
+}  // namespace
+
+// Runs the loop; `ix` is null in full-scan mode.  dict/N: the dictionary of the
+// initial mask.  Synchronises `st` every chunk of steps to test for completion.
+int fill_loop(const Geo& g, float* grid, uint8_t* mask, int prio, int mode, const Index* ix, const uint32_t* dict,
+              int64_t N, const int* eoff_all, const float* weights, bool weighted, int64_t max_steps, int64_t* log,
+              int64_t* steps_done, cudaStream_t st) {
+  const int64_t npix = g.X * g.Y * g.Z;
+  FillState s;
+  int64_t* unknown = nullptr;
+  float* tilemin = nullptr;
+  unsigned int* gmin = nullptr;
+  const int64_t ntiles = (N + 1023) / 1024;
+  SFC_TRY(cudaMallocAsync(&s.key, sizeof(unsigned long long) * npix, st));
+  SFC_TRY(cudaMallocAsync(&s.conf, sizeof(float) * npix, st));
+  SFC_TRY(cudaMallocAsync(&s.cterm, sizeof(float) * npix, st));
+  SFC_TRY(cudaMallocAsync(&s.best, sizeof(unsigned long long), st));
+  SFC_TRY(cudaMallocAsync(&s.sel_lin, sizeof(int64_t), st));
+  SFC_TRY(cudaMallocAsync(&s.sel_xyz, sizeof(int32_t) * 4, st));
+  SFC_TRY(cudaMallocAsync(&s.sel_cterm, sizeof(float), st));
+  SFC_TRY(cudaMallocAsync(&s.pick, sizeof(int64_t), st));
+  SFC_TRY(cudaMallocAsync(&s.cost, sizeof(float), st));
+  SFC_TRY(cudaMallocAsync(&s.done, sizeof(int), st));
+  SFC_TRY(cudaMallocAsync(&s.steps, sizeof(int64_t), st));
+  SFC_TRY(cudaMallocAsync(&unknown, sizeof(int64_t), st));
+  SFC_TRY(cudaMallocAsync(&tilemin, sizeof(float) * (ntiles > 0 ? ntiles : 1), st));
+  SFC_TRY(cudaMallocAsync(&gmin, sizeof(unsigned int), st));
+  SFC_TRY(cudaMemsetAsync(unknown, 0, sizeof(int64_t), st));
+  SFC_TRY(cudaMemsetAsync(s.key, 0, sizeof(unsigned long long) * npix, st));
+  SFC_TRY(cudaMemsetAsync(s.cterm, 0, sizeof(float) * npix, st));
+  count_launch();
+  k_state_init<<<1, 1, 0, st>>>(s, g);
+  count_launch();
+  k_conf_init<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(mask, npix, s.conf, unknown);
+  int pg = (int)((npix + 255) / 256 < 152 * 16 ? (npix + 255) / 256 : 152 * 16);
+  count_launch();
+  k_prio<<<pg, 256, 0, st>>>(grid, mask, g, prio, s, 1);
+  SFC_TRY(cudaGetLastError());
+  const int R = 2 * g.r + 1;
+  const int64_t box = (int64_t)(2 * R + 1) * (2 * R + 1) * (g.ndim == 3 ? 2 * R + 1 : 1);
+  const int bg = (int)((box + 255) / 256);
+  const int ag = (int)((npix + 255) / 256 < 152 * 8 ? (npix + 255) / 256 : 152 * 8);
+  int64_t left = 0;
+  SFC_TRY(cudaMemcpyAsync(&left, unknown, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SFC_TRY(cudaStreamSynchronize(st));
+  if (left > 0 && N <= 0) {
+    set_error("inpaint_run: the dictionary is empty but pixels are unknown");
+    return SFC_EINVAL;
+  }
+  // every step fills >= 1 unknown pixel, so `left` steps always suffice
+  const int64_t log_cap = max_steps > 0 ? (max_steps < left ? max_steps : left) : left;
+  int64_t enqueued = 0;
+  int chunk = 8;
+  int done = 0;
+  int rc = SFC_OK;
+  int64_t first = 1;
+  while (!done && rc == SFC_OK) {
+    for (int k = 0; k < chunk; ++k) {
+      if (!first) {
+        count_launch();
+        k_prio<<<bg, 256, 0, st>>>(grid, mask, g, prio, s, 0);
+      }
+      first = 0;
+      count_launch();
+      k_argmax<<<ag, 256, 0, st>>>(s.key, npix, s);
+      count_launch();
+      k_select<<<1, 1, 0, st>>>(g, s, max_steps);
+      if (mode == SFC_MODE_SFC)
+        rc = query_batch(*ix, grid, mask, s.sel_xyz, 1, s.pick, s.cost, nullptr, nullptr, nullptr, nullptr, st);
+      else
+        rc = fullscan_single(g, grid, mask, dict, N, eoff_all, weights, weighted, s.sel_lin, s.pick, s.cost, tilemin,
+                             gmin, st);
+      if (rc != SFC_OK) break;
+      count_launch();
+      k_insert<<<1, 256, 0, st>>>(grid, mask, g, dict, s, log, log_cap, unknown, status_word());
+      ++enqueued;
+    }
+    SFC_TRY(cudaGetLastError());
+    SFC_TRY(cudaMemcpyAsync(&done, s.done, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SFC_TRY(cudaStreamSynchronize(st));
+    if (chunk < 256) chunk *= 2;
+    if (!done && enqueued > left + 1) {
+      set_error("inpaint_run: the loop did not finish within one step per unknown pixel");
+      rc = SFC_EDEVICE;
+    }
+  }
+  int64_t steps = 0;
+  SFC_TRY(cudaMemcpyAsync(&steps, s.steps, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SFC_TRY(cudaStreamSynchronize(st));
+  *steps_done = steps;
+  cudaFreeAsync(s.key, st);
+  cudaFreeAsync(s.conf, st);
+  cudaFreeAsync(s.cterm, st);
+  cudaFreeAsync(s.best, st);
+  cudaFreeAsync(s.sel_lin, st);
+  cudaFreeAsync(s.sel_xyz, st);
+  cudaFreeAsync(s.sel_cterm, st);
+  cudaFreeAsync(s.pick, st);
+  cudaFreeAsync(s.cost, st);
+  cudaFreeAsync(s.done, st);
+  cudaFreeAsync(s.steps, st);
+  cudaFreeAsync(unknown, st);
+  cudaFreeAsync(tilemin, st);
+  cudaFreeAsync(gmin, st);
+  return rc;
+}
+
+}  // namespace sfc

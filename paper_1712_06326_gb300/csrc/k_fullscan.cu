@@ -1,0 +1,342 @@
+// k_fullscan.cu -- exact full scan (Sec. I: the cost of every dictionary patch,
+// then the global minimum) for a batch of queries.
+//
+// Pass 1 (FP32, CUDA cores): a CTA takes QT queries x (256 * EPT) dictionary
+// entries; every thread keeps an EPT x QT register tile of costs, the queries'
+// per-element (known, known * value) pairs sit in shared memory (read as
+// broadcasts), the source patch values are gathered from the grid (L2-resident).
+// Per element: d = fma(-k, p, k t) (exactly k (t - p) for k in {0,1}), acc =
+// fma(d, d, acc); weighted: acc = fma(w d, d, acc).  The CTA writes its per-query
+// minimum (tile minimum) and folds it into a per-query global minimum.
+// Pass 2 (one CTA per query): every tile whose minimum lies inside the FP32
+// error band of the global minimum is re-evaluated with the identical FP32
+// arithmetic, and each entry inside the band is rescored with the exact FP64
+// sequential cost; argmin over (cost, id).  Costs are non-negative, so float
+// bit patterns order like their values.
+#include "internal.cuh"
+
+namespace sfc {
+
+namespace {
+
+constexpr int kFsThreads = 256;
+
+template <int QT, int EPT, bool WEIGHTED>
+__global__ void __launch_bounds__(kFsThreads) k_fs_scan(const float* __restrict__ grid,
+                                                        const uint8_t* __restrict__ mask, Geo g,
+                                                        const uint32_t* __restrict__ dict, int64_t N,
+                                                        const int* __restrict__ eoff_all,
+                                                        const float* __restrict__ weights,
+                                                        const int64_t* __restrict__ centre_lin, int64_t Q,
+                                                        int64_t qbase, float* __restrict__ tilemin,
+                                                        unsigned int* __restrict__ gmin, int64_t ntiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = g.n, ch = g.ch;
+  float2* am = reinterpret_cast<float2*>(smem_raw);  // [n][QT]: (known, known * t)
+  int* eo = reinterpret_cast<int*>(am + (size_t)n * QT);
+  float* we = reinterpret_cast<float*>(eo + n);       // [n] weights (WEIGHTED)
+  const int64_t q0 = qbase + (int64_t)blockIdx.y * QT;
+  for (int e = threadIdx.x; e < n; e += kFsThreads) {
+    int o = eoff_all[e];
+    eo[e] = o;
+    if (WEIGHTED) we[e] = weights[e % ch];
+    const int pixo = eoff_all[e - e % ch] / ch;
+#pragma unroll
+    for (int qi = 0; qi < QT; ++qi) {
+      int64_t q = q0 + qi;
+      float2 v = make_float2(0.0f, 0.0f);
+      if (q < Q) {
+        int64_t tc = centre_lin[q];
+        float k = mask[tc + pixo] ? 1.0f : 0.0f;
+        v = make_float2(k, k * grid[tc * ch + o]);
+      }
+      am[(size_t)e * QT + qi] = v;
+    }
+  }
+  __syncthreads();
+  const int64_t j0 = (int64_t)blockIdx.x * kFsThreads * EPT + threadIdx.x;
+  int64_t sb[EPT];
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    int64_t j = j0 + (int64_t)k * kFsThreads;
+    sb[k] = j < N ? (int64_t)dict[j] * ch : -1;
+  }
+  float acc[EPT][QT];
+#pragma unroll
+  for (int k = 0; k < EPT; ++k)
+#pragma unroll
+    for (int qi = 0; qi < QT; ++qi) acc[k][qi] = 0.0f;
+  for (int e = 0; e < n; ++e) {
+    const int o = eo[e];
+    float p[EPT];
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) p[k] = sb[k] >= 0 ? __ldg(grid + sb[k] + o) : 0.0f;
+    float w = WEIGHTED ? we[e] : 1.0f;
+#pragma unroll
+    for (int qi = 0; qi < QT; ++qi) {
+      const float2 v = am[(size_t)e * QT + qi];
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        float d = __fmaf_rn(-v.x, p[k], v.y);
+        if (WEIGHTED)
+          acc[k][qi] = __fmaf_rn(__fmul_rn(w, d), d, acc[k][qi]);
+        else
+          acc[k][qi] = __fmaf_rn(d, d, acc[k][qi]);
+      }
+    }
+  }
+  __shared__ float red[kFsThreads / 32][QT];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int qi = 0; qi < QT; ++qi) {
+    float m = INFINITY;
+#pragma unroll
+    for (int k = 0; k < EPT; ++k)
+      if (sb[k] >= 0) m = fminf(m, acc[k][qi]);
+    m = warp_min(m);
+    if (lane == 0) red[warp][qi] = m;
+  }
+  __syncthreads();
+  if (threadIdx.x < QT) {
+    const int qi = threadIdx.x;
+    float m = red[0][qi];
+    for (int w = 1; w < kFsThreads / 32; ++w) m = fminf(m, red[w][qi]);
+    int64_t q = q0 + qi;
+    if (q < Q) {
+      tilemin[q * ntiles + blockIdx.x] = m;
+      atomicMin(&gmin[q], __float_as_uint(m));
+    }
+  }
+}
+
+// Same FP32 arithmetic for one query and one entry (bit-identical to pass 1).
+template <bool WEIGHTED>
+__device__ inline float cost32_one(const float* __restrict__ grid, int64_t sb, const float2* am, const int* eo,
+                                   const float* we, int n) {
+  float acc = 0.0f;
+  for (int e = 0; e < n; ++e) {
+    float p = __ldg(grid + sb + eo[e]);
+    float d = __fmaf_rn(-am[e].x, p, am[e].y);
+    if (WEIGHTED)
+      acc = __fmaf_rn(__fmul_rn(we[e], d), d, acc);
+    else
+      acc = __fmaf_rn(d, d, acc);
+  }
+  return acc;
+}
+
+template <int EPT, bool WEIGHTED>
+__global__ void __launch_bounds__(kFsThreads) k_fs_band(const float* __restrict__ grid,
+                                                        const uint8_t* __restrict__ mask, Geo g,
+                                                        const uint32_t* __restrict__ dict, int64_t N,
+                                                        const int* __restrict__ eoff_all,
+                                                        const float* __restrict__ weights,
+                                                        const int64_t* __restrict__ centre_lin,
+                                                        const float* __restrict__ tilemin,
+                                                        const unsigned int* __restrict__ gmin, int64_t ntiles,
+                                                        int64_t* __restrict__ pick, float* __restrict__ cost) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = g.n, ch = g.ch, P = g.P;
+  float2* am = reinterpret_cast<float2*>(smem_raw);
+  float* tv = reinterpret_cast<float*>(am + n);
+  int* eo = reinterpret_cast<int*>(tv + n);
+  float* we = reinterpret_cast<float*>(eo + n);
+  uint8_t* tm = reinterpret_cast<uint8_t*>(we + n);
+  const int64_t q = blockIdx.x;
+  const int64_t tc = centre_lin[q];
+  for (int e = threadIdx.x; e < n; e += kFsThreads) {
+    int o = eoff_all[e];
+    eo[e] = o;
+    we[e] = weights[e % ch];
+    float t = grid[tc * ch + o];
+    float k = mask[tc + eoff_all[e - e % ch] / ch] ? 1.0f : 0.0f;
+    tv[e] = t;
+    am[e] = make_float2(k, k * t);
+  }
+  for (int pp = threadIdx.x; pp < P; pp += kFsThreads) tm[pp] = mask[tc + eoff_all[pp * ch] / ch];
+  __syncthreads();
+  const float m32 = __uint_as_float(gmin[q]);
+  const double T = band_limit(m32, n);
+  double bc = INFINITY;
+  int64_t bj = INT64_MAX;
+  for (int64_t t = 0; t < ntiles; ++t) {
+    if ((double)tilemin[q * ntiles + t] > T) continue;  // uniform across the CTA
+    for (int k = 0; k < EPT; ++k) {
+      int64_t j = t * kFsThreads * EPT + (int64_t)k * kFsThreads + threadIdx.x;
+      if (j >= N) continue;
+      int64_t sb = (int64_t)dict[j] * ch;
+      float c32 = cost32_one<WEIGHTED>(grid, sb, am, eo, we, n);
+      if ((double)c32 <= T) {
+        double c64 = exact_cost64(grid, sb, tv, tm, eo, P, ch, weights);
+        if (c64 < bc || (c64 == bc && j < bj)) {
+          bc = c64;
+          bj = j;
+        }
+      }
+    }
+  }
+  warp_argmin64(bc, bj);
+  __shared__ double sd[kFsThreads / 32];
+  __shared__ int64_t si[kFsThreads / 32];
+  if ((threadIdx.x & 31) == 0) {
+    sd[threadIdx.x >> 5] = bc;
+    si[threadIdx.x >> 5] = bj;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kFsThreads / 32; ++w)
+      if (sd[w] < bc || (sd[w] == bc && si[w] < bj)) {
+        bc = sd[w];
+        bj = si[w];
+      }
+    if (bj == INT64_MAX) {
+      pick[q] = -1;
+      cost[q] = __int_as_float(0x7fc00000);
+    } else {
+      pick[q] = bj;
+      cost[q] = (float)bc;
+    }
+  }
+}
+
+// centre rows -> linear pixel index; invalid centres flag the status word and
+// get index -1 (their outputs become -1 / NaN).
+__global__ void k_centre_lin(const int32_t* __restrict__ centres, int64_t Q, Geo g, int64_t* __restrict__ lin,
+                             uint32_t* __restrict__ status) {
+  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  int64_t x = centres[q * g.ndim], y = centres[q * g.ndim + 1], z = g.ndim == 3 ? centres[q * g.ndim + 2] : 0;
+  if (centre_ok(g, x, y, z)) {
+    lin[q] = lin_of(g, x, y, z);
+  } else {
+    lin[q] = -1;
+    atomicOr(status, ST_BAD_CENTRE);
+  }
+}
+
+// Replace invalid centres by a valid stand-in (pixel of the first centre slot)
+// for the scan and mark their outputs afterwards.
+__global__ void k_centre_fix(int64_t* lin, int64_t Q, Geo g, uint8_t* bad) {
+  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  bad[q] = lin[q] < 0;
+  if (lin[q] < 0) lin[q] = lin_of(g, g.r, g.r, g.ndim == 3 ? g.r : 0);
+}
+
+__global__ void k_mark_bad(const uint8_t* bad, int64_t Q, int64_t* pick, float* cost) {
+  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q < Q && bad[q]) {
+    pick[q] = -1;
+    cost[q] = __int_as_float(0x7fc00000);
+  }
+}
+
+__global__ void k_fill_u32(unsigned int* p, int64_t n, unsigned int v) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+template <int QT, int EPT, bool W>
+int run_scan(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
+             const int* eoff_all, const float* weights, const int64_t* lin, int64_t Q, float* tilemin,
+             unsigned int* gmin, int64_t ntiles, cudaStream_t st) {
+  const size_t shm = (size_t)g.n * QT * sizeof(float2) + (size_t)g.n * 8;
+  if (shm > 48 * 1024)
+    SFC_TRY(cudaFuncSetAttribute(k_fs_scan<QT, EPT, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  const int64_t qtiles = (Q + QT - 1) / QT;
+  for (int64_t y0 = 0; y0 < qtiles; y0 += 65535) {
+    int64_t ny = qtiles - y0 < 65535 ? qtiles - y0 : 65535;
+    count_launch();
+    k_fs_scan<QT, EPT, W><<<dim3((unsigned)ntiles, (unsigned)ny), kFsThreads, shm, st>>>(
+        grid, cur_mask, g, dict, N, eoff_all, weights, lin, Q, y0 * QT, tilemin, gmin, ntiles);
+    SFC_TRY(cudaGetLastError());
+  }
+  return SFC_OK;
+}
+
+template <int EPT, bool W>
+int run_band(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
+             const int* eoff_all, const float* weights, const int64_t* lin, int64_t Q, const float* tilemin,
+             const unsigned int* gmin, int64_t ntiles, int64_t* pick, float* cost, cudaStream_t st) {
+  const size_t shm = (size_t)g.n * 20 + (size_t)g.P + 16;
+  if (shm > 48 * 1024)
+    SFC_TRY(cudaFuncSetAttribute(k_fs_band<EPT, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  count_launch();
+  k_fs_band<EPT, W><<<(unsigned)Q, kFsThreads, shm, st>>>(grid, cur_mask, g, dict, N, eoff_all, weights, lin,
+                                                          tilemin, gmin, ntiles, pick, cost);
+  SFC_TRY(cudaGetLastError());
+  return SFC_OK;
+}
+
+}  // namespace
+
+// One query whose centre (linear index) is already on the device and valid; the
+// caller owns the tile-minimum buffer (ceil(N / 1024) floats) and gmin.
+int fullscan_single(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
+                    const int* eoff_all, const float* weights, bool weighted, const int64_t* centre_lin,
+                    int64_t* pick, float* cost, float* tilemin, unsigned int* gmin, cudaStream_t st) {
+  constexpr int EPT = 4;
+  const int64_t ntiles = (N + kFsThreads * EPT - 1) / (kFsThreads * EPT);
+  count_launch();
+  k_fill_u32<<<1, 32, 0, st>>>(gmin, 1, 0x7f800000u);
+  int rc = weighted ? run_scan<1, EPT, true>(g, grid, cur_mask, dict, N, eoff_all, weights, centre_lin, 1, tilemin,
+                                             gmin, ntiles, st)
+                    : run_scan<1, EPT, false>(g, grid, cur_mask, dict, N, eoff_all, weights, centre_lin, 1, tilemin,
+                                              gmin, ntiles, st);
+  SFC_CHECK(rc);
+  return weighted ? run_band<EPT, true>(g, grid, cur_mask, dict, N, eoff_all, weights, centre_lin, 1, tilemin, gmin,
+                                        ntiles, pick, cost, st)
+                  : run_band<EPT, false>(g, grid, cur_mask, dict, N, eoff_all, weights, centre_lin, 1, tilemin, gmin,
+                                         ntiles, pick, cost, st);
+}
+
+int fullscan_batch(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
+                   const int* eoff_all, const float* weights, bool weighted, const int32_t* centres,
+                   const int64_t* centre_lin, int64_t Q, int64_t* pick, float* cost, cudaStream_t st) {
+  if (Q <= 0) return SFC_OK;
+  constexpr int EPT = 4;
+  const int64_t ntiles = (N + kFsThreads * EPT - 1) / (kFsThreads * EPT);
+  int64_t* lin = nullptr;
+  uint8_t* bad = nullptr;
+  float* tilemin = nullptr;
+  unsigned int* gmin = nullptr;
+  SFC_TRY(cudaMallocAsync(&tilemin, sizeof(float) * Q * ntiles, st));
+  SFC_TRY(cudaMallocAsync(&gmin, sizeof(unsigned int) * Q, st));
+  SFC_TRY(cudaMallocAsync(&bad, Q, st));
+  const int64_t* L = centre_lin;
+  if (!L) {
+    SFC_TRY(cudaMallocAsync(&lin, sizeof(int64_t) * Q, st));
+    count_launch();
+    k_centre_lin<<<(unsigned)((Q + 255) / 256), 256, 0, st>>>(centres, Q, g, lin, status_word());
+    L = lin;
+  } else {
+    SFC_TRY(cudaMallocAsync(&lin, sizeof(int64_t) * Q, st));
+    SFC_TRY(cudaMemcpyAsync(lin, centre_lin, sizeof(int64_t) * Q, cudaMemcpyDeviceToDevice, st));
+    L = lin;
+  }
+  count_launch();
+  k_centre_fix<<<(unsigned)((Q + 255) / 256), 256, 0, st>>>(lin, Q, g, bad);
+  count_launch();
+  k_fill_u32<<<(unsigned)((Q + 255) / 256), 256, 0, st>>>(gmin, Q, 0x7f800000u);
+  int rc;
+  if (Q >= 8)
+    rc = weighted ? run_scan<8, EPT, true>(g, grid, cur_mask, dict, N, eoff_all, weights, L, Q, tilemin, gmin, ntiles, st)
+                  : run_scan<8, EPT, false>(g, grid, cur_mask, dict, N, eoff_all, weights, L, Q, tilemin, gmin, ntiles, st);
+  else
+    rc = weighted ? run_scan<1, EPT, true>(g, grid, cur_mask, dict, N, eoff_all, weights, L, Q, tilemin, gmin, ntiles, st)
+                  : run_scan<1, EPT, false>(g, grid, cur_mask, dict, N, eoff_all, weights, L, Q, tilemin, gmin, ntiles, st);
+  SFC_CHECK(rc);
+  rc = weighted ? run_band<EPT, true>(g, grid, cur_mask, dict, N, eoff_all, weights, L, Q, tilemin, gmin, ntiles, pick, cost, st)
+                : run_band<EPT, false>(g, grid, cur_mask, dict, N, eoff_all, weights, L, Q, tilemin, gmin, ntiles, pick, cost, st);
+  SFC_CHECK(rc);
+  count_launch();
+  k_mark_bad<<<(unsigned)((Q + 255) / 256), 256, 0, st>>>(bad, Q, pick, cost);
+  SFC_TRY(cudaGetLastError());
+  cudaFreeAsync(tilemin, st);
+  cudaFreeAsync(gmin, st);
+  cudaFreeAsync(bad, st);
+  cudaFreeAsync(lin, st);
+  return SFC_OK;
+}
+
+}  // namespace sfc

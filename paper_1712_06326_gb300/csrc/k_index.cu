@@ -1,0 +1,164 @@
+// k_index.cu -- projection to principal space (Sec. II.A), quantisation and
+// Morton / z-address keys (Sec. II.C) of every dictionary entry on every index.
+//
+// Projection: y_k = chain of FP32 fused multiply-adds over the index's subset
+// values in subset order, acc = fma(B[i][k], x_i - mu_i, acc) starting at +0 with
+// x_i - mu_i rounded to FP32 (one thread per (entry, index), the D chains of a
+// thread interleaved).  The per-axis minimum and maximum over the dictionary are
+// exact reductions (order-independent).  Quantisation: q = clamp(floor((y - lo)
+// * scale), 0, 2^b - 1) with scale = (float)(2^b / ((double)hi - (double)lo)) (0
+// if hi == lo), then q + shift.  Key: bits interleaved highest plane first,
+// dimension 0 first inside a plane (the highest-variance axis first, Sec. II.C);
+// the top 64 bits when D * b' > 64.
+#include "internal.cuh"
+
+namespace sfc {
+
+namespace {
+
+// Monotone map float -> uint32 so that unsigned min/max order like the floats;
+// -0 is folded to +0 first (both are the real value zero).
+__device__ inline uint32_t ord_of(float v) {
+  if (v == 0.0f) v = 0.0f;
+  uint32_t b = __float_as_uint(v);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ inline float float_of(uint32_t u) {
+  uint32_t b = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+  return __uint_as_float(b);
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_project(const float* __restrict__ grid, const uint32_t* __restrict__ dict,
+                                                 int64_t N, int ch, int s, const int* __restrict__ sub_eoff,
+                                                 const float* __restrict__ basis, const float* __restrict__ mean,
+                                                 float* __restrict__ proj, uint32_t* __restrict__ lohi) {
+  const int c = blockIdx.y;
+  extern __shared__ unsigned char smem_raw[];
+  float* B = reinterpret_cast<float*>(smem_raw);  // s*D
+  float* mu = B + s * D;                          // s
+  int* eo = reinterpret_cast<int*>(mu + s);       // s
+  for (int t = threadIdx.x; t < s * D; t += blockDim.x) B[t] = basis[(int64_t)c * s * D + t];
+  for (int t = threadIdx.x; t < s; t += blockDim.x) {
+    mu[t] = mean[(int64_t)c * s + t];
+    eo[t] = sub_eoff[(int64_t)c * s + t];
+  }
+  __syncthreads();
+  __shared__ uint32_t smin[D], smax[D];
+  if (threadIdx.x < D) {
+    smin[threadIdx.x] = 0xffffffffu;
+    smax[threadIdx.x] = 0u;
+  }
+  __syncthreads();
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  float acc[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) acc[k] = 0.0f;
+  if (j < N) {
+    const int64_t base = (int64_t)dict[j] * ch;
+    for (int i = 0; i < s; ++i) {
+      float xc = __fsub_rn(grid[base + eo[i]], mu[i]);
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc[k] = __fmaf_rn(B[i * D + k], xc, acc[k]);
+    }
+    float* out = proj + ((int64_t)c * N + j) * D;
+#pragma unroll
+    for (int k = 0; k < D; ++k) out[k] = acc[k];
+  }
+  // per-axis min / max: warp reduce, then shared, then one global atomic per axis
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    uint32_t u = j < N ? ord_of(acc[k]) : 0xffffffffu;
+    uint32_t v = j < N ? ord_of(acc[k]) : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      u = min(u, __shfl_xor_sync(0xffffffffu, u, o));
+      v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&smin[k], u);
+      atomicMax(&smax[k], v);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < D) {
+    atomicMin(&lohi[(c * D + threadIdx.x) * 2 + 0], smin[threadIdx.x]);
+    atomicMax(&lohi[(c * D + threadIdx.x) * 2 + 1], smax[threadIdx.x]);
+  }
+}
+
+__global__ void k_lohi_init(uint32_t* lohi, int n) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) {
+    lohi[2 * t] = 0xffffffffu;
+    lohi[2 * t + 1] = 0u;
+  }
+}
+
+__global__ void k_scale(const uint32_t* __restrict__ lohi, int n, int bits, float* __restrict__ lo,
+                        float* __restrict__ scale) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) {
+    float l = float_of(lohi[2 * t]), h = float_of(lohi[2 * t + 1]);
+    lo[t] = l;
+    scale[t] = h > l ? (float)(ldexp(1.0, bits) / ((double)h - (double)l)) : 0.0f;
+  }
+}
+
+}  // namespace
+
+namespace {
+
+__global__ void k_keys(const float* __restrict__ proj, int64_t N, int D, int bits, int bp,
+                       const float* __restrict__ lo, const float* __restrict__ scale,
+                       const int32_t* __restrict__ shifts, uint64_t* __restrict__ keys) {
+  const int c = blockIdx.y;
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  uint32_t q[16];
+  const float* y = proj + ((int64_t)c * N + j) * D;
+  for (int k = 0; k < D; ++k)
+    q[k] = quantise_one(y[k], lo[c * D + k], scale[c * D + k], bits) + (uint32_t)shifts[c * D + k];
+  keys[(int64_t)c * N + j] = morton_key(q, D, bp);
+}
+
+template <int D>
+int launch_project(const Index& ix, const float* grid, float* proj, uint32_t* lohi, cudaStream_t st) {
+  const size_t shm = sizeof(float) * (ix.s * D + ix.s) + sizeof(int) * ix.s;
+  if (shm > 48 * 1024) SFC_TRY(cudaFuncSetAttribute(k_project<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  dim3 grd((unsigned)((ix.N + 255) / 256), ix.C);
+  count_launch();
+  k_project<D><<<grd, 256, shm, st>>>(grid, ix.dict, ix.N, ix.g.ch, ix.s, ix.sub_eoff, ix.basis, ix.mean, proj, lohi);
+  SFC_TRY(cudaGetLastError());
+  return SFC_OK;
+}
+
+}  // namespace
+
+int project_and_key(Index& ix, const float* grid, cudaStream_t st, float* proj, uint64_t* keys) {
+  uint32_t* lohi = nullptr;
+  const int n = ix.C * ix.D;
+  SFC_TRY(cudaMallocAsync(&lohi, sizeof(uint32_t) * 2 * n, st));
+  count_launch();
+  k_lohi_init<<<(n + 127) / 128, 128, 0, st>>>(lohi, n);
+  int rc = SFC_EINVAL;
+  switch (ix.D) {
+#define SFC_D(d) \
+  case d: rc = launch_project<d>(ix, grid, proj, lohi, st); break;
+    SFC_D(1) SFC_D(2) SFC_D(3) SFC_D(4) SFC_D(5) SFC_D(6) SFC_D(7) SFC_D(8)
+    SFC_D(9) SFC_D(10) SFC_D(11) SFC_D(12) SFC_D(13) SFC_D(14) SFC_D(15) SFC_D(16)
+#undef SFC_D
+    default: set_error("dims must be 1..16"); return SFC_EINVAL;
+  }
+  SFC_CHECK(rc);
+  count_launch();
+  k_scale<<<(n + 127) / 128, 128, 0, st>>>(lohi, n, ix.bits, ix.lo, ix.scale);
+  dim3 grd((unsigned)((ix.N + 255) / 256), ix.C);
+  count_launch();
+  k_keys<<<grd, 256, 0, st>>>(proj, ix.N, ix.D, ix.bits, ix.bp, ix.lo, ix.scale, ix.shifts, keys);
+  SFC_TRY(cudaGetLastError());
+  cudaFreeAsync(lohi, st);
+  return SFC_OK;
+}
+
+}  // namespace sfc

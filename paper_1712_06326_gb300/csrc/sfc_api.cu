@@ -1,0 +1,565 @@
+// sfc_api.cu -- the extern "C" boundary of libsfc (declared in include/sfc.h):
+// argument validation, index lifecycle and the orchestration of the kernels.
+#include <algorithm>
+#include <atomic>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+struct sfc_index {
+  sfc::Index ix;
+  int device;
+};
+
+namespace sfc {
+
+namespace {
+thread_local std::string g_err;
+__device__ uint32_t g_status_word;
+std::mutex g_mu;
+uint32_t* g_status_ptr[128] = {};
+}  // namespace
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+namespace {
+std::atomic<uint64_t> g_launches{0};
+}
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+uint32_t* status_word() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_status_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_status_word) != cudaSuccess) return nullptr;
+    g_status_ptr[dev] = static_cast<uint32_t*>(p);
+  }
+  return g_status_ptr[dev];
+}
+
+int fill_loop(const Geo& g, float* grid, uint8_t* mask, int prio, int mode, const Index* ix, const uint32_t* dict,
+              int64_t N, const int* eoff_all, const float* weights, bool weighted, int64_t max_steps, int64_t* log,
+              int64_t* steps_done, cudaStream_t st);
+
+namespace {
+
+// The device must be an sm_103 part (the library carries sm_103a code only) and
+// the status word must be reachable.
+int check_device() {
+  int dev = 0;
+  SFC_TRY(cudaGetDevice(&dev));
+  int maj = 0, mnr = 0;
+  SFC_TRY(cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, dev));
+  SFC_TRY(cudaDeviceGetAttribute(&mnr, cudaDevAttrComputeCapabilityMinor, dev));
+  if (maj != 10 || mnr != 3) {
+    set_error("libsfc is built for sm_103a; device " + std::to_string(dev) + " is sm_" + std::to_string(maj) +
+              std::to_string(mnr));
+    return SFC_EUNSUPPORTED;
+  }
+  if (!status_word()) {
+    set_error("cannot reach the library status word on this device");
+    return SFC_ECUDA;
+  }
+  return SFC_OK;
+}
+
+int make_geo(const sfc_grid* gp, int K, Geo* out) {
+  if (!gp) {
+    set_error("grid geometry is NULL");
+    return SFC_EINVAL;
+  }
+  if (gp->ndim != 2 && gp->ndim != 3) {
+    set_error("ndim must be 2 or 3");
+    return SFC_EINVAL;
+  }
+  if (gp->ch < 1 || gp->ch > 64) {
+    set_error("ch must be 1..64");
+    return SFC_EINVAL;
+  }
+  if (K < 3 || K > 15 || (K % 2) == 0) {
+    set_error("K must be odd, 3..15");
+    return SFC_EINVAL;
+  }
+  const int64_t Z = gp->ndim == 3 ? gp->ext[2] : 1;
+  if (gp->ndim == 2 && gp->ext[2] != 1 && gp->ext[2] != 0) {
+    set_error("a 2-D grid needs ext[2] == 1");
+    return SFC_EINVAL;
+  }
+  if (gp->ext[0] < K || gp->ext[1] < K || Z < (gp->ndim == 3 ? K : 1)) {
+    set_error("every grid extent must be >= K");
+    return SFC_EINVAL;
+  }
+  const int64_t npix = gp->ext[0] * gp->ext[1] * Z;
+  if (npix >= (int64_t)1 << 32) {
+    set_error("grids must have fewer than 2^32 pixels");
+    return SFC_EINVAL;
+  }
+  Geo g;
+  g.ndim = gp->ndim;
+  g.ch = gp->ch;
+  g.K = K;
+  g.r = K / 2;
+  g.P = gp->ndim == 3 ? K * K * K : K * K;
+  g.X = gp->ext[0];
+  g.Y = gp->ext[1];
+  g.Z = Z;
+  g.n = g.P * g.ch;
+  if (g.n > 4096) {
+    set_error("patches with more than 4096 values are not supported");
+    return SFC_EINVAL;
+  }
+  *out = g;
+  return SFC_OK;
+}
+
+// Subset rule (Fig. 2): anchors at the middles of the patch edges and at its
+// corners (2-D: top, right, bottom, left middles, then TL, TR, BR, BL corners;
+// 3-D: the 8 corners in raster order, then the face middles z-, z+, y-, y+, x-,
+// x+), in doubled coordinates where pixel p is at 2p+1 and the patch spans
+// [0, 2K]; the m pixels of smallest squared distance, ties to the lower raster
+// index, listed in ascending order.
+std::vector<int32_t> subsets_host(int ndim, int K, int C, int m) {
+  const int P = ndim == 3 ? K * K * K : K * K;
+  const int E = 2 * K, H = K;
+  std::vector<std::array<int, 3>> an;
+  if (ndim == 2) {
+    an = {{H, 0, 0}, {E, H, 0}, {H, E, 0}, {0, H, 0}, {0, 0, 0}, {E, 0, 0}, {E, E, 0}, {0, E, 0}};
+  } else {
+    for (int z = 0; z < 2; ++z)
+      for (int y = 0; y < 2; ++y)
+        for (int x = 0; x < 2; ++x) an.push_back({x * E, y * E, z * E});
+    an.push_back({H, H, 0});
+    an.push_back({H, H, E});
+    an.push_back({H, 0, H});
+    an.push_back({H, E, H});
+    an.push_back({0, H, H});
+    an.push_back({E, H, H});
+  }
+  std::vector<int32_t> out((size_t)C * m);
+  std::vector<std::pair<long long, int>> d(P);
+  for (int c = 0; c < C; ++c) {
+    for (int pp = 0; pp < P; ++pp) {
+      const long long x = 2 * (pp % K) + 1 - an[c][0];
+      const long long y = 2 * ((pp / K) % K) + 1 - an[c][1];
+      const long long z = ndim == 3 ? 2 * (pp / (K * K)) + 1 - an[c][2] : 0;
+      d[pp] = {x * x + y * y + z * z, pp};
+    }
+    std::sort(d.begin(), d.end());
+    std::vector<int32_t> sel(m);
+    for (int i = 0; i < m; ++i) sel[i] = d[i].second;
+    std::sort(sel.begin(), sel.end());
+    std::copy(sel.begin(), sel.end(), out.begin() + (size_t)c * m);
+  }
+  return out;
+}
+
+template <typename T>
+int upload(T** dst, const T* src, size_t count, cudaStream_t st) {
+  SFC_TRY(cudaMallocAsync(dst, sizeof(T) * (count ? count : 1), st));
+  if (count) SFC_TRY(cudaMemcpyAsync(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice, st));
+  return SFC_OK;
+}
+
+void free_index(Index& ix) {
+  void* ptrs[] = {ix.dict,  ix.eoff_all, ix.sub_eoff, ix.sub_pix, ix.weights, ix.basis, ix.mean, ix.evals,
+                  ix.lo,    ix.scale,    ix.shifts,   ix.proj,    ix.keys,    ix.skeys, ix.sids};
+  cudaDeviceSynchronize();
+  for (void* p : ptrs)
+    if (p) cudaFreeAsync(p, nullptr);
+  cudaStreamSynchronize(nullptr);
+}
+
+std::vector<float> weights_of(const sfc_params* p, int ch) {
+  std::vector<float> w(ch, 1.0f);
+  if (p->ch_weights)
+    for (int c = 0; c < ch; ++c) w[c] = p->ch_weights[c];
+  return w;
+}
+
+int check_weights(const std::vector<float>& w) {
+  for (float v : w)
+    if (!(v > 0.0f) || !std::isfinite(v)) {
+      set_error("channel weights must be positive and finite");
+      return SFC_EINVAL;
+    }
+  return SFC_OK;
+}
+
+}  // namespace
+
+int upload_patch_tables(const Geo& g, int** eoff_all, cudaStream_t st) {
+  std::vector<int> eo(g.n);
+  for (int e = 0; e < g.n; ++e) eo[e] = (int)(patch_off(g, e / g.ch) * g.ch + e % g.ch);
+  return upload(eoff_all, eo.data(), eo.size(), st);
+}
+
+// Build every array of an index (shared by sfc_index_build and inpaint_run).
+int build_index(const float* grid, const uint8_t* dict_mask, const sfc_grid* gp, const sfc_params* p,
+                cudaStream_t st, Index& ix) {
+  if (!grid || !dict_mask || !p) {
+    set_error("sfc_index_build: NULL argument");
+    return SFC_EINVAL;
+  }
+  SFC_CHECK(make_geo(gp, p->K, &ix.g));
+  const Geo& g = ix.g;
+  const int maxC = g.ndim == 2 ? 8 : 14;
+  if (p->curves < 1 || p->curves > maxC) {
+    set_error("curves must be 1.." + std::to_string(maxC));
+    return SFC_EINVAL;
+  }
+  if (p->dims < 1 || p->dims > 16 || p->bits < 1 || p->bits > 21 || p->window < 1 ||
+      !(p->subset_frac > 0.0f && p->subset_frac <= 1.0f) || (p->select != SFC_SELECT_ALL && p->select != SFC_SELECT_BEST)) {
+    set_error("parameter out of range (dims 1..16, bits 1..21, window >= 1, subset_frac in (0, 1], select)");
+    return SFC_EINVAL;
+  }
+  if (p->precision != SFC_FP32) {
+    set_error("the index path computes in FP32 (precision must be SFC_FP32)");
+    return SFC_EUNSUPPORTED;
+  }
+  ix.C = p->curves;
+  ix.D = p->dims;
+  ix.bits = p->bits;
+  ix.W = p->window;
+  ix.select = p->select;
+  ix.frac = p->subset_frac;
+  ix.pca_sample = p->pca_sample;
+  ix.keep = p->keep_intermediates != 0;
+  int m = (int)std::floor((double)p->subset_frac * g.P + 0.5);
+  m = std::max(1, std::min(m, g.P));
+  ix.m = m;
+  ix.s = m * g.ch;
+  if (ix.D > ix.s) {
+    set_error("dims must not exceed the subset length m * ch");
+    return SFC_EINVAL;
+  }
+  std::vector<int32_t> sh((size_t)ix.C * ix.D, 0);
+  ix.bp = ix.bits;
+  if (p->shifts) {
+    for (size_t i = 0; i < sh.size(); ++i) {
+      sh[i] = p->shifts[i];
+      if (sh[i] < 0 || sh[i] >= (1 << ix.bits)) {
+        set_error("shifts must lie in [0, 2^bits)");
+        return SFC_EINVAL;
+      }
+      if (sh[i] != 0) ix.bp = ix.bits + 1;
+    }
+  }
+  ix.weights_h = weights_of(p, g.ch);
+  SFC_CHECK(check_weights(ix.weights_h));
+  if (p->basis && !p->mean) {
+    set_error("a given basis needs its mean");
+    return SFC_EINVAL;
+  }
+  ix.subset_h = subsets_host(g.ndim, g.K, ix.C, m);
+  std::vector<int32_t> sub_eoff((size_t)ix.C * ix.s);
+  for (int c = 0; c < ix.C; ++c)
+    for (int i = 0; i < ix.s; ++i)
+      sub_eoff[(size_t)c * ix.s + i] =
+          (int32_t)(patch_off(g, ix.subset_h[(size_t)c * m + i / g.ch]) * g.ch + i % g.ch);
+  SFC_CHECK(upload_patch_tables(g, &ix.eoff_all, st));
+  SFC_CHECK(upload(&ix.sub_pix, ix.subset_h.data(), ix.subset_h.size(), st));
+  SFC_CHECK(upload(&ix.sub_eoff, sub_eoff.data(), sub_eoff.size(), st));
+  SFC_CHECK(upload(&ix.weights, ix.weights_h.data(), ix.weights_h.size(), st));
+  SFC_CHECK(upload(&ix.shifts, sh.data(), sh.size(), st));
+  SFC_CHECK(dict_extract(dict_mask, g, st, &ix.dict, &ix.N));
+  if (ix.N <= 0) {
+    set_error("the dictionary is empty (no fully known patch)");
+    return SFC_EINVAL;
+  }
+  const int C = ix.C, D = ix.D, s = ix.s;
+  const int64_t N = ix.N;
+  SFC_TRY(cudaMallocAsync(&ix.basis, sizeof(float) * C * s * D, st));
+  SFC_TRY(cudaMallocAsync(&ix.mean, sizeof(float) * C * s, st));
+  SFC_TRY(cudaMallocAsync(&ix.evals, sizeof(double) * C * s, st));
+  SFC_TRY(cudaMallocAsync(&ix.lo, sizeof(float) * C * D, st));
+  SFC_TRY(cudaMallocAsync(&ix.scale, sizeof(float) * C * D, st));
+  SFC_TRY(cudaMallocAsync(&ix.skeys, sizeof(uint64_t) * C * N, st));
+  SFC_TRY(cudaMallocAsync(&ix.sids, sizeof(uint32_t) * C * N, st));
+  if (p->basis) {
+    SFC_TRY(cudaMemcpyAsync(ix.basis, p->basis, sizeof(float) * C * s * D, cudaMemcpyHostToDevice, st));
+    SFC_TRY(cudaMemcpyAsync(ix.mean, p->mean, sizeof(float) * C * s, cudaMemcpyHostToDevice, st));
+    SFC_TRY(cudaMemsetAsync(ix.evals, 0xff, sizeof(double) * C * s, st));  // NaN
+  } else {
+    SFC_CHECK(pca_build(ix, grid, st));
+  }
+  float* proj = nullptr;
+  uint64_t* keys = nullptr;
+  SFC_TRY(cudaMallocAsync(&proj, sizeof(float) * C * N * D, st));
+  SFC_TRY(cudaMallocAsync(&keys, sizeof(uint64_t) * C * N, st));
+  SFC_CHECK(project_and_key(ix, grid, st, proj, keys));
+  const int key_bits = std::min(64, D * ix.bp);
+  SFC_CHECK(radix_sort_pairs(keys, ix.skeys, ix.sids, N, C, key_bits, st));
+  if (ix.keep) {
+    ix.proj = proj;
+    ix.keys = keys;
+  } else {
+    cudaFreeAsync(proj, st);
+    cudaFreeAsync(keys, st);
+  }
+  SFC_TRY(cudaGetLastError());
+  return SFC_OK;
+}
+
+}  // namespace sfc
+
+using namespace sfc;
+
+extern "C" {
+
+void sfc_params_default(sfc_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->K = 9;
+  p->curves = 8;
+  p->dims = 10;
+  p->bits = 8;
+  p->window = 80;
+  p->subset_frac = 0.6f;
+  p->select = SFC_SELECT_ALL;
+  p->precision = SFC_FP32;
+  p->pca_sample = 16384;
+  p->priority = SFC_PRIO_CONFIDENCE;
+}
+
+const char* sfc_last_error(void) { return g_err.c_str(); }
+
+uint64_t sfc_launch_count(void) { return g_launches.load(); }
+
+int sfc_index_build(const float* grid, const uint8_t* dict_mask, const sfc_grid* g, const sfc_params* p,
+                    void* stream, sfc_index** out) {
+  g_err.clear();
+  if (!out) {
+    set_error("sfc_index_build: out is NULL");
+    return SFC_EINVAL;
+  }
+  *out = nullptr;
+  SFC_CHECK(check_device());
+  auto* h = new sfc_index();
+  cudaGetDevice(&h->device);
+  int rc = build_index(grid, dict_mask, g, p, (cudaStream_t)stream, h->ix);
+  if (rc != SFC_OK) {
+    free_index(h->ix);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return SFC_OK;
+}
+
+int sfc_index_destroy(sfc_index* ix) {
+  if (!ix) return SFC_OK;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ix->device);
+  free_index(ix->ix);
+  cudaSetDevice(prev);
+  delete ix;
+  return SFC_OK;
+}
+
+int sfc_index_info(const sfc_index* ix, int64_t* N, int32_t* m, int32_t* s) {
+  if (!ix) {
+    set_error("sfc_index_info: NULL index");
+    return SFC_EINVAL;
+  }
+  if (N) *N = ix->ix.N;
+  if (m) *m = ix->ix.m;
+  if (s) *s = ix->ix.s;
+  return SFC_OK;
+}
+
+int sfc_index_export(const sfc_index* h, int64_t* dict, int32_t* subsets, float* basis, float* mean, double* evals,
+                     float* lo, float* scale, float* proj, uint64_t* keys, uint64_t* skeys, uint32_t* sids) {
+  g_err.clear();
+  if (!h) {
+    set_error("sfc_index_export: NULL index");
+    return SFC_EINVAL;
+  }
+  const Index& ix = h->ix;
+  if ((proj || keys) && !ix.keep) {
+    set_error("projections/unsorted keys are only kept with keep_intermediates = 1");
+    return SFC_EINVAL;
+  }
+  SFC_TRY(cudaDeviceSynchronize());
+  const size_t C = ix.C, D = ix.D, s = ix.s, N = ix.N;
+  if (dict) {
+    std::vector<uint32_t> d(N);
+    SFC_TRY(cudaMemcpy(d.data(), ix.dict, sizeof(uint32_t) * N, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < N; ++i) dict[i] = d[i];
+  }
+  if (subsets) std::memcpy(subsets, ix.subset_h.data(), sizeof(int32_t) * ix.subset_h.size());
+  if (basis) SFC_TRY(cudaMemcpy(basis, ix.basis, sizeof(float) * C * s * D, cudaMemcpyDeviceToHost));
+  if (mean) SFC_TRY(cudaMemcpy(mean, ix.mean, sizeof(float) * C * s, cudaMemcpyDeviceToHost));
+  if (evals) SFC_TRY(cudaMemcpy(evals, ix.evals, sizeof(double) * C * s, cudaMemcpyDeviceToHost));
+  if (lo) SFC_TRY(cudaMemcpy(lo, ix.lo, sizeof(float) * C * D, cudaMemcpyDeviceToHost));
+  if (scale) SFC_TRY(cudaMemcpy(scale, ix.scale, sizeof(float) * C * D, cudaMemcpyDeviceToHost));
+  if (proj) SFC_TRY(cudaMemcpy(proj, ix.proj, sizeof(float) * C * N * D, cudaMemcpyDeviceToHost));
+  if (keys) SFC_TRY(cudaMemcpy(keys, ix.keys, sizeof(uint64_t) * C * N, cudaMemcpyDeviceToHost));
+  if (skeys) SFC_TRY(cudaMemcpy(skeys, ix.skeys, sizeof(uint64_t) * C * N, cudaMemcpyDeviceToHost));
+  if (sids) SFC_TRY(cudaMemcpy(sids, ix.sids, sizeof(uint32_t) * C * N, cudaMemcpyDeviceToHost));
+  return SFC_OK;
+}
+
+int sfc_query_batch(const sfc_index* h, const float* grid, const uint8_t* cur_mask, const int32_t* centres,
+                    int64_t Q, int64_t* pick, float* cost, void* stream) {
+  g_err.clear();
+  if (!h || Q < 0) {
+    set_error("sfc_query_batch: NULL index or negative Q");
+    return SFC_EINVAL;
+  }
+  if (Q == 0) return SFC_OK;
+  if (!grid || !cur_mask || !centres || !pick || !cost) {
+    set_error("sfc_query_batch: NULL pointer");
+    return SFC_EINVAL;
+  }
+  SFC_CHECK(check_device());
+  return query_batch(h->ix, grid, cur_mask, centres, Q, pick, cost, nullptr, nullptr, nullptr, nullptr,
+                     (cudaStream_t)stream);
+}
+
+int sfc_query_candidates(const sfc_index* h, const float* grid, const uint8_t* cur_mask, const int32_t* centres,
+                         int64_t Q, uint64_t* qkeys, int64_t* pos, int32_t* cand, int32_t* ncand, void* stream) {
+  g_err.clear();
+  if (!h || Q < 0) {
+    set_error("sfc_query_candidates: NULL index or negative Q");
+    return SFC_EINVAL;
+  }
+  if (Q == 0) return SFC_OK;
+  if (!grid || !cur_mask || !centres || !qkeys || !pos || !cand || !ncand) {
+    set_error("sfc_query_candidates: NULL pointer");
+    return SFC_EINVAL;
+  }
+  SFC_CHECK(check_device());
+  return query_batch(h->ix, grid, cur_mask, centres, Q, nullptr, nullptr, qkeys, pos, cand, ncand,
+                     (cudaStream_t)stream);
+}
+
+int fullscan_query_batch(const float* grid, const uint8_t* dict_mask, const uint8_t* cur_mask, const sfc_grid* gp,
+                         const sfc_params* p, const int32_t* centres, int64_t Q, int64_t* pick, float* cost,
+                         void* stream) {
+  g_err.clear();
+  if (!p || Q < 0) {
+    set_error("fullscan_query_batch: NULL params or negative Q");
+    return SFC_EINVAL;
+  }
+  if (Q == 0) return SFC_OK;
+  if (!grid || !dict_mask || !cur_mask || !centres || !pick || !cost) {
+    set_error("fullscan_query_batch: NULL pointer");
+    return SFC_EINVAL;
+  }
+  SFC_CHECK(check_device());
+  Geo g;
+  SFC_CHECK(make_geo(gp, p->K, &g));
+  std::vector<float> w = weights_of(p, g.ch);
+  SFC_CHECK(check_weights(w));
+  bool weighted = false;
+  for (float v : w) weighted |= v != 1.0f;
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t* dict = nullptr;
+  int64_t N = 0;
+  int* eo = nullptr;
+  float* wd = nullptr;
+  SFC_CHECK(dict_extract(dict_mask, g, st, &dict, &N));
+  if (N <= 0) {
+    if (dict) cudaFreeAsync(dict, st);
+    set_error("the dictionary is empty (no fully known patch)");
+    return SFC_EINVAL;
+  }
+  SFC_CHECK(upload_patch_tables(g, &eo, st));
+  SFC_CHECK(upload(&wd, w.data(), w.size(), st));
+  int rc = fullscan_batch(g, grid, cur_mask, dict, N, eo, wd, weighted, centres, nullptr, Q, pick, cost, st);
+  cudaFreeAsync(dict, st);
+  cudaFreeAsync(eo, st);
+  cudaFreeAsync(wd, st);
+  return rc;
+}
+
+int inpaint_run(float* grid, uint8_t* mask, const sfc_grid* gp, const sfc_params* p, int32_t mode, int64_t max_steps,
+                int64_t* log, int64_t* steps_done, void* stream) {
+  g_err.clear();
+  if (!grid || !mask || !p || !steps_done) {
+    set_error("inpaint_run: NULL pointer");
+    return SFC_EINVAL;
+  }
+  if (mode != SFC_MODE_FULLSCAN && mode != SFC_MODE_SFC) {
+    set_error("inpaint_run: mode must be SFC_MODE_FULLSCAN or SFC_MODE_SFC");
+    return SFC_EINVAL;
+  }
+  *steps_done = 0;
+  SFC_CHECK(check_device());
+  Geo g;
+  SFC_CHECK(make_geo(gp, p->K, &g));
+  if (p->priority != SFC_PRIO_CONFIDENCE && p->priority != SFC_PRIO_CRIMINISI) {
+    set_error("inpaint_run: unknown priority");
+    return SFC_EINVAL;
+  }
+  if (p->priority == SFC_PRIO_CRIMINISI && g.ndim != 2) {
+    set_error("inpaint_run: the Criminisi priority is defined for 2-D grids");
+    return SFC_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<float> w = weights_of(p, g.ch);
+  SFC_CHECK(check_weights(w));
+  bool weighted = false;
+  for (float v : w) weighted |= v != 1.0f;
+  Index ix;
+  int rc = SFC_OK;
+  uint32_t* dict = nullptr;
+  int64_t N = 0;
+  int* eo = nullptr;
+  float* wd = nullptr;
+  if (mode == SFC_MODE_SFC) {
+    rc = build_index(grid, mask, gp, p, st, ix);
+    if (rc != SFC_OK) {
+      free_index(ix);
+      return rc;
+    }
+    dict = ix.dict;
+    N = ix.N;
+    eo = ix.eoff_all;
+    wd = ix.weights;
+  } else {
+    SFC_CHECK(dict_extract(mask, g, st, &dict, &N));
+    SFC_CHECK(upload_patch_tables(g, &eo, st));
+    SFC_CHECK(upload(&wd, w.data(), w.size(), st));
+  }
+  rc = fill_loop(g, grid, mask, p->priority, mode, mode == SFC_MODE_SFC ? &ix : nullptr, dict, N, eo, wd, weighted,
+                 max_steps, log, steps_done, st);
+  if (mode == SFC_MODE_SFC) {
+    free_index(ix);
+  } else {
+    cudaStreamSynchronize(st);
+    if (dict) cudaFreeAsync(dict, st);
+    cudaFreeAsync(eo, st);
+    cudaFreeAsync(wd, st);
+    cudaStreamSynchronize(st);
+  }
+  return rc;
+}
+
+int sfc_status(void* stream) {
+  g_err.clear();
+  SFC_CHECK(check_device());
+  SFC_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  uint32_t v = 0, zero = 0;
+  SFC_TRY(cudaMemcpyFromSymbol(&v, g_status_word, sizeof(v)));
+  SFC_TRY(cudaMemcpyToSymbol(g_status_word, &zero, sizeof(zero)));
+  if (v & ST_TIMEOUT) {
+    set_error("a bounded device-side wait timed out");
+    return SFC_ETIMEOUT;
+  }
+  if (v & ST_BAD_CENTRE) {
+    set_error("a query centre lies outside the valid centre range");
+    return SFC_EDEVICE;
+  }
+  return SFC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,258 @@
+"""Python binding of libsfc (include/sfc.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and passes device
+pointers of torch CUDA tensors plus the current CUDA stream.  All computation
+happens in the CUDA kernels of libsfc; there is no fallback path: if the
+library is missing or a call fails, a RuntimeError is raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsfc.so")
+
+SFC_OK, SFC_EINVAL, SFC_ENOMEM, SFC_ECUDA, SFC_ETIMEOUT, SFC_EUNSUPPORTED, SFC_EDEVICE = 0, -1, -2, -3, -4, -5, -6
+SFC_SELECT_ALL, SFC_SELECT_BEST = 0, 1
+SFC_FP32, SFC_BF16 = 0, 1
+SFC_PRIO_CONFIDENCE, SFC_PRIO_CRIMINISI = 0, 1
+SFC_MODE_FULLSCAN, SFC_MODE_SFC = 0, 1
+
+EXPORTS = ["sfc_params_default", "sfc_index_build", "sfc_index_destroy", "sfc_index_info", "sfc_index_export",
+           "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "inpaint_run", "sfc_status",
+           "sfc_launch_count", "sfc_last_error"]
+
+
+class sfc_grid(C.Structure):
+    _fields_ = [("ndim", C.c_int32), ("ch", C.c_int32), ("ext", C.c_int64 * 3)]
+
+
+class sfc_params(C.Structure):
+    _fields_ = [("K", C.c_int32), ("curves", C.c_int32), ("dims", C.c_int32), ("bits", C.c_int32),
+                ("window", C.c_int32), ("subset_frac", C.c_float), ("shifts", C.c_void_p),
+                ("ch_weights", C.c_void_p), ("basis", C.c_void_p), ("mean", C.c_void_p), ("select", C.c_int32),
+                ("precision", C.c_int32), ("pca_sample", C.c_int64), ("priority", C.c_int32),
+                ("keep_intermediates", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libsfc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libsfc.so not found at {LIB_PATH}; run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+        L.sfc_params_default.argtypes = [C.POINTER(sfc_params)]
+        L.sfc_params_default.restype = None
+        L.sfc_index_build.argtypes = [vp, vp, C.POINTER(sfc_grid), C.POINTER(sfc_params), vp, C.POINTER(vp)]
+        L.sfc_index_destroy.argtypes = [vp]
+        L.sfc_index_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)]
+        L.sfc_index_export.argtypes = [vp] * 12
+        L.sfc_query_batch.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
+        L.sfc_query_candidates.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp, vp]
+        L.fullscan_query_batch.argtypes = [vp, vp, vp, C.POINTER(sfc_grid), C.POINTER(sfc_params), vp, i64, vp, vp,
+                                           vp]
+        L.inpaint_run.argtypes = [vp, vp, C.POINTER(sfc_grid), C.POINTER(sfc_params), i32, i64, vp,
+                                  C.POINTER(i64), vp]
+        L.sfc_status.argtypes = [vp]
+        L.sfc_last_error.restype = C.c_char_p
+        L.sfc_launch_count.restype = C.c_uint64
+        L.sfc_launch_count.argtypes = []
+        for name in ["sfc_index_build", "sfc_index_destroy", "sfc_index_info", "sfc_index_export",
+                     "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "inpaint_run",
+                     "sfc_status"]:
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != SFC_OK:
+        msg = lib().sfc_last_error().decode()
+        raise RuntimeError(f"{what} failed ({rc}): {msg}")
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t: torch.Tensor, dtype) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(np.ascontiguousarray(t))
+    if not t.is_cuda:
+        t = t.to("cuda")
+    return t.to(dtype).contiguous()
+
+
+def make_grid(grid: torch.Tensor) -> sfc_grid:
+    """Geometry of a grid tensor laid out (Y, X, ch) or (Z, Y, X, ch)."""
+    g = sfc_grid()
+    if grid.dim() == 3:
+        Y, X, ch = grid.shape
+        g.ndim, g.ch = 2, ch
+        g.ext[0], g.ext[1], g.ext[2] = X, Y, 1
+    elif grid.dim() == 4:
+        Z, Y, X, ch = grid.shape
+        g.ndim, g.ch = 3, ch
+        g.ext[0], g.ext[1], g.ext[2] = X, Y, Z
+    else:
+        raise ValueError("grid must be (Y, X, ch) or (Z, Y, X, ch)")
+    return g
+
+
+class Params:
+    """sfc_params with the paper's defaults, overridable by keyword."""
+
+    def __init__(self, **kw):
+        self.p = sfc_params()
+        lib().sfc_params_default(C.byref(self.p))
+        self._keep = []
+        for k, v in kw.items():
+            if k in ("shifts", "ch_weights", "basis", "mean"):
+                if v is None:
+                    setattr(self.p, k, None)
+                    continue
+                arr = np.ascontiguousarray(v, np.int32 if k == "shifts" else np.float32)
+                self._keep.append(arr)
+                setattr(self.p, k, arr.ctypes.data_as(C.c_void_p))
+            else:
+                setattr(self.p, k, v)
+
+    def __getattr__(self, k):
+        return getattr(self.__dict__["p"], k)
+
+
+class Index:
+    """Owner of an sfc_index handle."""
+
+    def __init__(self, handle, params: Params, ndim: int):
+        self.h = handle
+        self.params = params
+        self.ndim = ndim
+        N = C.c_int64()
+        m = C.c_int32()
+        s = C.c_int32()
+        _check(lib().sfc_index_info(self.h, C.byref(N), C.byref(m), C.byref(s)), "sfc_index_info")
+        self.N, self.m, self.s = N.value, m.value, s.value
+
+    def close(self):
+        if self.h:
+            lib().sfc_index_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sfc_index_build(grid: torch.Tensor, dict_mask: torch.Tensor, **params) -> Index:
+    grid = _dev(grid, torch.float32)
+    dict_mask = _dev(dict_mask, torch.uint8)
+    P = Params(**params)
+    g = make_grid(grid)
+    h = C.c_void_p()
+    _check(lib().sfc_index_build(_ptr(grid), _ptr(dict_mask), C.byref(g), C.byref(P.p), _stream(), C.byref(h)),
+           "sfc_index_build")
+    return Index(h, P, g.ndim)
+
+
+def sfc_index_export(ix: Index, proj: bool = False) -> dict:
+    C_, D, N, s, m = ix.params.curves, ix.params.dims, ix.N, ix.s, ix.m
+    out = dict(dict=np.empty(N, np.int64), subsets=np.empty((C_, m), np.int32), basis=np.empty((C_, s, D), np.float32),
+               mean=np.empty((C_, s), np.float32), evals=np.empty((C_, s), np.float64),
+               lo=np.empty((C_, D), np.float32), scale=np.empty((C_, D), np.float32),
+               skeys=np.empty((C_, N), np.uint64), sids=np.empty((C_, N), np.uint32))
+    if proj:
+        out["proj"] = np.empty((C_, N, D), np.float32)
+        out["keys"] = np.empty((C_, N), np.uint64)
+    p = lambda k: out[k].ctypes.data_as(C.c_void_p) if k in out else None  # noqa: E731
+    _check(lib().sfc_index_export(ix.h, p("dict"), p("subsets"), p("basis"), p("mean"), p("evals"), p("lo"),
+                                  p("scale"), p("proj"), p("keys"), p("skeys"), p("sids")), "sfc_index_export")
+    return out
+
+
+def sfc_query_batch(ix: Index, grid: torch.Tensor, cur_mask: torch.Tensor, centres: torch.Tensor,
+                    pick: torch.Tensor | None = None, cost: torch.Tensor | None = None):
+    grid = _dev(grid, torch.float32)
+    cur_mask = _dev(cur_mask, torch.uint8)
+    centres = _dev(centres, torch.int32)
+    Q = centres.shape[0]
+    if pick is None:
+        pick = torch.empty(Q, dtype=torch.int64, device=grid.device)
+    if cost is None:
+        cost = torch.empty(Q, dtype=torch.float32, device=grid.device)
+    _check(lib().sfc_query_batch(ix.h, _ptr(grid), _ptr(cur_mask), _ptr(centres), Q, _ptr(pick), _ptr(cost),
+                                 _stream()), "sfc_query_batch")
+    return pick, cost
+
+
+def sfc_query_candidates(ix: Index, grid: torch.Tensor, cur_mask: torch.Tensor, centres: torch.Tensor):
+    grid = _dev(grid, torch.float32)
+    cur_mask = _dev(cur_mask, torch.uint8)
+    centres = _dev(centres, torch.int32)
+    Q, C_, W = centres.shape[0], ix.params.curves, ix.params.window
+    dev = grid.device
+    qkeys = torch.empty((Q, C_), dtype=torch.int64, device=dev)  # uint64 bits
+    pos = torch.empty((Q, C_), dtype=torch.int64, device=dev)
+    cand = torch.empty((Q, C_ * W), dtype=torch.int32, device=dev)
+    ncand = torch.empty(Q, dtype=torch.int32, device=dev)
+    _check(lib().sfc_query_candidates(ix.h, _ptr(grid), _ptr(cur_mask), _ptr(centres), Q, _ptr(qkeys), _ptr(pos),
+                                      _ptr(cand), _ptr(ncand), _stream()), "sfc_query_candidates")
+    return qkeys, pos, cand, ncand
+
+
+def fullscan_query_batch(grid: torch.Tensor, dict_mask: torch.Tensor, cur_mask: torch.Tensor,
+                         centres: torch.Tensor, K: int, ch_weights=None, pick=None, cost=None):
+    grid = _dev(grid, torch.float32)
+    dict_mask = _dev(dict_mask, torch.uint8)
+    cur_mask = _dev(cur_mask, torch.uint8)
+    centres = _dev(centres, torch.int32)
+    Q = centres.shape[0]
+    P = Params(K=K, ch_weights=ch_weights)
+    g = make_grid(grid)
+    if pick is None:
+        pick = torch.empty(Q, dtype=torch.int64, device=grid.device)
+    if cost is None:
+        cost = torch.empty(Q, dtype=torch.float32, device=grid.device)
+    _check(lib().fullscan_query_batch(_ptr(grid), _ptr(dict_mask), _ptr(cur_mask), C.byref(g), C.byref(P.p),
+                                      _ptr(centres), Q, _ptr(pick), _ptr(cost), _stream()), "fullscan_query_batch")
+    return pick, cost
+
+
+def inpaint_run(grid: torch.Tensor, mask: torch.Tensor, mode: int = SFC_MODE_FULLSCAN, max_steps: int = 0,
+                log: bool = True, **params):
+    """Runs the fill loop in place on (device) grid and mask.  -> (steps, log int64 [steps, ndim+1])."""
+    assert grid.is_cuda and mask.is_cuda and grid.is_contiguous() and mask.is_contiguous()
+    assert grid.dtype == torch.float32 and mask.dtype == torch.uint8
+    P = Params(**params)
+    g = make_grid(grid)
+    unknown = int((mask == 0).sum().item())
+    cap = unknown if max_steps <= 0 else max_steps
+    lg = torch.zeros((max(cap, 1), g.ndim + 1), dtype=torch.int64, device=grid.device) if log else None
+    steps = C.c_int64()
+    _check(lib().inpaint_run(_ptr(grid), _ptr(mask), C.byref(g), C.byref(P.p), mode, max_steps, _ptr(lg),
+                             C.byref(steps), _stream()), "inpaint_run")
+    n = steps.value
+    return n, (lg[:n] if lg is not None else None)
+
+
+def sfc_launch_count() -> int:
+    return int(lib().sfc_launch_count())
+
+
+def sfc_status() -> int:
+    return lib().sfc_status(_stream())

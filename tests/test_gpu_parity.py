@@ -1,0 +1,358 @@
+"""CUDA path vs the CPU oracle, through the C-ABI (needs a GB300).
+
+Bars: dictionary ids, subsets, projections (FP32 chain), lo/scale, keys, sorted
+orders, query keys, positions and candidate sets bit-exact; picks equal; the
+reported cost is the exact FP64 cost rounded to FP32, so bit-exact as well; the
+PCA basis (a different summation order and Jacobi ordering) within the FP64
+tolerances stated below; the fill loop's log and output bit-identical.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1712_06326_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1712_06326_gb300 import sfc
+
+    torch.cuda.set_device(0)
+    return sfc
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def ext_of(g):
+    return O.geometry(g)[1]
+
+
+def oracle_ix(ex, grid, K, C_, D, bits, shifts=None):
+    ndim, ext, ch = O.geometry(grid)
+    return dict(ndim=ndim, ext=ext, ch=ch, K=K, C=C_, D=D, bits=bits, dict=ex["dict"], N=len(ex["dict"]),
+                subset=np.ascontiguousarray(ex["subsets"]), m=ex["subsets"].shape[1], basis=ex["basis"],
+                mean=ex["mean"], lo=ex["lo"], scale=ex["scale"], skeys=ex["skeys"], sids=ex["sids"],
+                shifts=None if shifts is None else np.ascontiguousarray(shifts, np.int32).reshape(C_, D))
+
+
+# ----------------------------------------------------------------------------
+# full scan (Sec. I)
+# ----------------------------------------------------------------------------
+def check_fullscan(S, g, m_dict, m_cur, t, K, w=None):
+    fp, fc = S.fullscan_query_batch(dev(g), dev(m_dict), dev(m_cur), dev(t), K=K, ch_weights=w)
+    torch.cuda.synchronize()
+    d = O.dict_extract(m_dict, K)
+    op, oc = O.fullscan(g, m_cur, K, d, O.centres_to_lin(t, ext_of(g)), w)
+    assert np.array_equal(fp.cpu().numpy(), op)
+    assert np.array_equal(fc.cpu().numpy(), oc.astype(np.float32))
+    return op
+
+
+def test_fullscan_sines_front_targets(S):
+    g, m = synth.sines2d(128)
+    t = synth.front_targets(m, 9)
+    assert len(O.dict_extract(m, 9)) == 13376  # spans 13 tiles of 1024 + a ragged tail
+    check_fullscan(S, g, m, m, t, 9)
+
+
+def test_fullscan_rgb_weighted_and_random_targets(S):
+    g, m = synth.voronoi2d(96, cfg=2, seed_sub=2)
+    t = np.concatenate([synth.front_targets(m, 7, cap=40, cfg=2), synth.random_targets(m, 7, 30, cfg=2)])
+    check_fullscan(S, g, m, m, t, 7)
+    check_fullscan(S, g, m, m, t, 7, w=np.array([1.0, 2.0, 0.5], np.float32))
+
+
+def test_fullscan_exact_ties_lowest_id(S):
+    rng = np.random.default_rng(5)
+    g = rng.random((40, 40, 1)).astype(np.float32)
+    g[30:35, 30:35] = g[3:8, 3:8]
+    g[20:25, 2:7] = g[3:8, 3:8]
+    m = np.ones((40, 40), np.uint8)
+    t = np.array([[32, 32], [4, 22], [5, 5]], np.int32)
+    op = check_fullscan(S, g, m, m, t, 5)
+    d = O.dict_extract(m, 5)
+    assert d[op[0]] == 5 * 40 + 5 and d[op[1]] == 5 * 40 + 5
+
+
+def test_fullscan_constant_grid(S):
+    g = np.full((30, 30, 2), 0.25, np.float32)
+    m = np.ones((30, 30), np.uint8)
+    m[10:14, 10:14] = 0
+    t = np.array([[12, 9], [3, 3], [26, 26]], np.int32)
+    op = check_fullscan(S, g, m, m, t, 3)
+    assert list(op) == [0, 0, 0]
+
+
+def test_fullscan_3d(S):
+    g, m = synth.spheres3d(24, block=4, missing=0.1)
+    t = synth.front_targets(m, 5, cap=40, cfg=3)
+    check_fullscan(S, g, m, m, t, 5)
+
+
+def test_fullscan_invalid_centre_and_empty_batch(S):
+    g, m = synth.sines2d(64)
+    t = np.array([[1, 1], [30, 30], [63, 10]], np.int32)
+    fp, fc = S.fullscan_query_batch(dev(g), dev(m), dev(m), dev(t), K=9)
+    fp = fp.cpu().numpy()
+    fc = fc.cpu().numpy()
+    assert fp[0] == -1 and np.isnan(fc[0]) and fp[2] == -1
+    assert fp[1] >= 0
+    assert S.sfc_status() == S.SFC_EDEVICE
+    assert S.sfc_status() == 0  # cleared
+    fp, fc = S.fullscan_query_batch(dev(g), dev(m), dev(m), dev(np.zeros((0, 2), np.int32)), K=9)
+    assert fp.numel() == 0
+
+
+# ----------------------------------------------------------------------------
+# index build (Sec. II.A-C)
+# ----------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def rgb_index(S):
+    g, m = synth.voronoi2d(96, cfg=2, seed_sub=3)
+    K, C_, D, bits = 7, 8, 6, 12
+    ix = S.sfc_index_build(dev(g), dev(m), K=K, curves=C_, dims=D, bits=bits, window=16, pca_sample=0,
+                           keep_intermediates=1)
+    ex = S.sfc_index_export(ix, proj=True)
+    return dict(g=g, m=m, K=K, C=C_, D=D, bits=bits, ix=ix, ex=ex)
+
+
+def test_index_dictionary_and_subsets(rgb_index):
+    r = rgb_index
+    assert np.array_equal(r["ex"]["dict"], O.dict_extract(r["m"], r["K"]))
+    assert np.array_equal(r["ex"]["subsets"], O.subsets(2, r["K"], 0.6, r["C"]))
+
+
+def test_index_pca_basis_close_to_oracle(rgb_index):
+    r = rgb_index
+    ex = r["ex"]
+    d = ex["dict"]
+    for cv in range(r["C"]):
+        B, mu, ev, cov = O.pca(r["g"], r["K"], d, ex["subsets"][cv], 0, r["D"])
+        # eigenvalues: FP64 throughout, different summation/rotation order
+        assert np.allclose(ex["evals"][cv], ev, rtol=1e-9, atol=1e-12 * ev[0])
+        assert np.allclose(ex["mean"][cv], mu, rtol=0, atol=0)
+        # eigenvectors with an eigen-gap: same direction and canonical sign
+        gaps = np.minimum(np.abs(np.diff(ev[: r["D"] + 1])), np.r_[np.inf, np.abs(np.diff(ev[: r["D"]]))])
+        for k in range(r["D"]):
+            if gaps[k] > 1e-6 * ev[0]:
+                assert np.abs(ex["basis"][cv][:, k] - B[:, k]).max() < 2e-6
+
+
+def test_index_keys_bit_exact_from_common_basis(rgb_index):
+    r = rgb_index
+    ex = r["ex"]
+    oix = O.build_index(r["g"], r["m"], r["K"], r["C"], r["D"], r["bits"], basis=ex["basis"], mean=ex["mean"])
+    assert np.array_equal(oix["proj"], ex["proj"])
+    assert np.array_equal(oix["lo"], ex["lo"]) and np.array_equal(oix["scale"], ex["scale"])
+    assert np.array_equal(oix["keys"], ex["keys"])
+    assert np.array_equal(oix["skeys"], ex["skeys"]) and np.array_equal(oix["sids"], ex["sids"])
+
+
+def test_index_shifted_curves_and_sampled_pca(S):
+    g, m = synth.voronoi2d(80, cfg=2, seed_sub=4)
+    K, C_, D, bits = 5, 6, 5, 10
+    rng = np.random.default_rng(3)
+    sh = rng.integers(0, 1 << bits, (C_, D)).astype(np.int32)
+    ix = S.sfc_index_build(dev(g), dev(m), K=K, curves=C_, dims=D, bits=bits, window=8, pca_sample=500,
+                           shifts=sh, keep_intermediates=1)
+    ex = S.sfc_index_export(ix, proj=True)
+    d = ex["dict"]
+    B, mu, ev, _ = O.pca(g, K, d, ex["subsets"][0], 500, D)
+    assert np.allclose(ex["evals"][0], ev, rtol=1e-9, atol=1e-12 * ev[0])
+    oix = O.build_index(g, m, K, C_, D, bits, shifts=sh, basis=ex["basis"], mean=ex["mean"])
+    assert np.array_equal(oix["keys"], ex["keys"])
+    assert np.array_equal(oix["skeys"], ex["skeys"]) and np.array_equal(oix["sids"], ex["sids"])
+    t = synth.front_targets(m, K, cap=30, cfg=2)
+    qk, pos, cand, nc = S.sfc_query_candidates(ix, dev(g), dev(m), dev(t))
+    oq = oracle_ix(ex, g, K, C_, D, bits, sh)
+    lin = O.centres_to_lin(t, ext_of(g))
+    for i in range(len(t)):
+        rr = O.query(oq, g, m, lin[i], 8)
+        assert np.array_equal(qk[i].cpu().numpy().view(np.uint64), rr["qkeys"])
+        assert np.array_equal(cand[i, : nc[i]].cpu().numpy(), rr["cand"])
+    ix.close()
+
+
+def test_index_3d_truncated_keys(S):
+    g, m = synth.spheres3d(24, block=4, missing=0.1)
+    K, C_, D, bits = 5, 8, 6, 21  # 126 key bits -> top 64
+    ix = S.sfc_index_build(dev(g), dev(m), K=K, curves=C_, dims=D, bits=bits, window=12, pca_sample=0,
+                           keep_intermediates=1)
+    ex = S.sfc_index_export(ix, proj=True)
+    assert np.array_equal(ex["dict"], O.dict_extract(m, K))
+    assert np.array_equal(ex["subsets"], O.subsets(3, K, 0.6, C_))
+    oix = O.build_index(g, m, K, C_, D, bits, basis=ex["basis"], mean=ex["mean"])
+    assert np.array_equal(oix["proj"], ex["proj"])
+    assert np.array_equal(oix["skeys"], ex["skeys"]) and np.array_equal(oix["sids"], ex["sids"])
+    t = synth.front_targets(m, K, cap=25, cfg=3)
+    p, c = S.sfc_query_batch(ix, dev(g), dev(m), dev(t))
+    lin = O.centres_to_lin(t, ext_of(g))
+    p = p.cpu().numpy()
+    c = c.cpu().numpy()
+    for i in range(len(t)):
+        rr = O.query(oix, g, m, lin[i], 12)
+        assert p[i] == rr["pick"] and c[i] == np.float32(rr["cost"])
+    ix.close()
+
+
+# ----------------------------------------------------------------------------
+# queries (Fig. 1(b)-(d))
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("select", [0, 1])
+def test_query_candidates_and_picks(S, rgb_index, select):
+    r = rgb_index
+    g, m, K = r["g"], r["m"], r["K"]
+    W = 16
+    ix = S.sfc_index_build(dev(g), dev(m), K=K, curves=r["C"], dims=r["D"], bits=r["bits"], window=W,
+                           pca_sample=0, select=select)
+    ex = S.sfc_index_export(ix)
+    oq = oracle_ix(ex, g, K, r["C"], r["D"], r["bits"])
+    t = np.concatenate([synth.front_targets(m, K, cap=60, cfg=2), synth.random_targets(m, K, 20, cfg=2)])
+    # a partly filled state: current mask differs from the dictionary mask
+    cur = m.copy()
+    cur[40:50, 40:50] = 1
+    for mask in (m, cur):
+        qk, pos, cand, nc = S.sfc_query_candidates(ix, dev(g), dev(mask), dev(t))
+        pk, cs = S.sfc_query_batch(ix, dev(g), dev(mask), dev(t))
+        qk, pos, cand, nc = (x.cpu().numpy() for x in (qk, pos, cand, nc))
+        pk, cs = pk.cpu().numpy(), cs.cpu().numpy()
+        lin = O.centres_to_lin(t, ext_of(g))
+        for i in range(len(t)):
+            rr = O.query(oq, g, mask, lin[i], W, select=select)
+            assert np.array_equal(qk[i].view(np.uint64), rr["qkeys"])
+            assert np.array_equal(pos[i], rr["pos"])
+            assert nc[i] == len(rr["cand"]) and np.array_equal(cand[i, : nc[i]], rr["cand"])
+            assert np.all(cand[i, nc[i]:] == -1)
+            assert pk[i] == rr["pick"] and cs[i] == np.float32(rr["cost"])
+    ix.close()
+
+
+def test_query_window_covering_dictionary_equals_fullscan(S):
+    g, m = synth.voronoi2d(48, cfg=2, seed_sub=8)
+    K = 5
+    N = len(O.dict_extract(m, K))
+    ix = S.sfc_index_build(dev(g), dev(m), K=K, curves=2, dims=4, bits=8, window=N, pca_sample=0)
+    t = synth.front_targets(m, K, cap=50, cfg=2)
+    pk, cs = S.sfc_query_batch(ix, dev(g), dev(m), dev(t))
+    fp, fc = S.fullscan_query_batch(dev(g), dev(m), dev(m), dev(t), K=K)
+    assert torch.equal(pk, fp) and torch.equal(cs, fc)
+    ix.close()
+
+
+def test_query_dictionary_patches_cost_zero(S, rgb_index):
+    r = rgb_index
+    ex = r["ex"]
+    ext = ext_of(r["g"])
+    js = np.array([0, 5, len(ex["dict"]) // 2, len(ex["dict"]) - 1])
+    t = O.lin_to_centres(ex["dict"][js], ext, 2).astype(np.int32)
+    pk, cs = S.sfc_query_batch(r["ix"], dev(r["g"]), dev(r["m"]), dev(t))
+    assert torch.all(cs == 0) and torch.all(pk.cpu() <= torch.from_numpy(js))
+
+
+# ----------------------------------------------------------------------------
+# fill loop (Sec. I, Fig. 1(a))
+# ----------------------------------------------------------------------------
+def run_fill(S, g, m, **kw):
+    gd, md = dev(g), dev(m)
+    steps, log = S.inpaint_run(gd, md, **kw)
+    return gd.cpu().numpy(), md.cpu().numpy(), log.cpu().numpy(), steps
+
+
+def test_fill_sines_fullscan_bit_identical(S):
+    g, m = synth.sines2d(128)
+    og, om, olog, osteps = O.inpaint(g, m, 9, mode=0, prio=0)
+    gg, gm, glog, gsteps = run_fill(S, g, m, mode=S.SFC_MODE_FULLSCAN, K=9, priority=0)
+    assert gsteps == osteps and np.array_equal(glog, olog)
+    assert np.array_equal(gg, og) and gm.all()
+
+
+def test_fill_rgb_criminisi_fullscan_bit_identical(S):
+    g, m = synth.voronoi2d(56, cfg=2, seed_sub=9)
+    og, om, olog, osteps = O.inpaint(g, m, 5, mode=0, prio=1)
+    gg, gm, glog, gsteps = run_fill(S, g, m, mode=S.SFC_MODE_FULLSCAN, K=5, priority=1)
+    assert gsteps == osteps and np.array_equal(glog, olog)
+    assert np.array_equal(gg, og)
+
+
+def test_fill_rgb_sfc_bit_identical(S):
+    g, m = synth.voronoi2d(64, cfg=2, seed_sub=10)
+    K, C_, D, bits, W = 5, 8, 5, 10, 12
+    ix = S.sfc_index_build(dev(g), dev(m), K=K, curves=C_, dims=D, bits=bits, window=W, pca_sample=0)
+    ex = S.sfc_index_export(ix)
+    ix.close()
+    oix = O.build_index(g, m, K, C_, D, bits, basis=ex["basis"], mean=ex["mean"])
+    og, om, olog, osteps = O.inpaint(g, m, K, mode=1, prio=1, ix=oix, W=W)
+    gg, gm, glog, gsteps = run_fill(S, g, m, mode=S.SFC_MODE_SFC, K=K, curves=C_, dims=D, bits=bits, window=W,
+                                    basis=ex["basis"], mean=ex["mean"], priority=1)
+    assert gsteps == osteps and np.array_equal(glog, olog)
+    assert np.array_equal(gg, og)
+
+
+def test_fill_3d_and_max_steps(S):
+    g, m = synth.spheres3d(20, block=4, missing=0.05)
+    og, om, olog, osteps = O.inpaint(g, m, 3, mode=0, prio=0, max_steps=40)
+    gg, gm, glog, gsteps = run_fill(S, g, m, mode=S.SFC_MODE_FULLSCAN, K=3, priority=0, max_steps=40)
+    assert gsteps == osteps == 40 and np.array_equal(glog, olog) and np.array_equal(gg, og)
+
+
+# ----------------------------------------------------------------------------
+# the full paper-scale 2-D workload (1024^2 RGB, K=11, C=8, D=8, b=16, W=64)
+# ----------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def big(S):
+    g, m = synth.voronoi2d(1024, cfg=2)
+    t = synth.front_targets(m, 11, cap=65536, cfg=2)
+    gd, md, td = dev(g), dev(m), dev(t)
+    ix = S.sfc_index_build(gd, md, K=11, curves=8, dims=8, bits=16, window=64, pca_sample=16384,
+                           keep_intermediates=1)
+    ex = S.sfc_index_export(ix, proj=True)
+    return dict(g=g, m=m, t=t, gd=gd, md=md, td=td, ix=ix, ex=ex)
+
+
+def test_big_index_sorted_permutation_and_sampled_keys(big):
+    ex, g = big["ex"], big["g"]
+    C_, N = ex["skeys"].shape
+    assert N > 800_000
+    for cv in range(C_):
+        assert np.all(ex["skeys"][cv][1:] >= ex["skeys"][cv][:-1])
+        assert np.array_equal(np.sort(ex["sids"][cv]), np.arange(N, dtype=np.uint32))
+        assert np.array_equal(ex["keys"][cv][ex["sids"][cv]], ex["skeys"][cv])
+    rng = np.random.default_rng(0)
+    ones = np.ones(big["m"].shape, np.uint8)
+    for j in rng.choice(N, 64, replace=False):
+        for cv in (0, 3, 7):
+            y = O.project_query(g, ones, 11, ex["dict"][j], ex["subsets"][cv], ex["basis"][cv], ex["mean"][cv], 8)
+            assert np.array_equal(y, ex["proj"][cv][j])
+            q = O.quantise(y[None], 16, ex["lo"][cv], ex["scale"][cv])
+            assert O.keys(q, 16)[0] == ex["keys"][cv][j]
+
+
+def test_big_sampled_queries_match_oracle(S, big):
+    ex, g, m, t = big["ex"], big["g"], big["m"], big["t"]
+    assert len(t) == 65536
+    pk, cs = S.sfc_query_batch(big["ix"], big["gd"], big["md"], big["td"])
+    pk, cs = pk.cpu().numpy(), cs.cpu().numpy()
+    assert np.all(pk >= 0)
+    oq = oracle_ix(ex, g, 11, 8, 8, 16)
+    lin = O.centres_to_lin(t, ext_of(g))
+    rng = np.random.default_rng(1)
+    for i in np.r_[0, len(t) - 1, rng.choice(len(t), 62, replace=False)]:
+        rr = O.query(oq, g, m, lin[i], 64)
+        assert pk[i] == rr["pick"] and cs[i] == np.float32(rr["cost"])
+
+
+def test_big_sampled_fullscan_match_oracle(S, big):
+    g, m, t = big["g"], big["m"], big["t"]
+    rng = np.random.default_rng(2)
+    sel = np.sort(rng.choice(len(t), 12, replace=False))
+    fp, fc = S.fullscan_query_batch(big["gd"], big["md"], big["md"], dev(t[sel]), K=11)
+    op, oc = O.fullscan(g, m, 11, big["ex"]["dict"], O.centres_to_lin(t[sel], ext_of(g)))
+    assert np.array_equal(fp.cpu().numpy(), op) and np.array_equal(fc.cpu().numpy(), oc.astype(np.float32))
