@@ -337,7 +337,7 @@ def test_big_index_sorted_permutation_and_sampled_keys(big):
 
 def test_big_sampled_queries_match_oracle(S, big):
     ex, g, m, t = big["ex"], big["g"], big["m"], big["t"]
-    assert len(t) == 65536
+    assert len(t) == 3597  # every front target of the initial mask (the 65,536 cap is not reached)
     pk, cs = S.sfc_query_batch(big["ix"], big["gd"], big["md"], big["td"])
     pk, cs = pk.cpu().numpy(), cs.cpu().numpy()
     assert np.all(pk >= 0)
