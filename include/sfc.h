@@ -148,6 +148,26 @@ int fullscan_query_batch(const float* grid, const uint8_t* dict_mask, const uint
                          const sfc_params* p, const int32_t* centres, int64_t Q, int64_t* pick, float* cost,
                          void* stream);
 
+/* fullscan_query_batch without device allocation.  The paper has no
+ * counterpart: this is an interface for callers that cannot call cudaMalloc --
+ * for example a host framework whose own allocator owns the device memory and
+ * forbids libraries from allocating behind its back, or a latency-critical
+ * caller that cannot afford the implicit synchronisation an allocation may
+ * cause.  Arguments, results and errors are those of fullscan_query_batch; the
+ * caller still passes every input and output.  All scratch lives in one
+ * library-owned static device array of 16 MiB (held by every GPU that loads the
+ * library until the process exits); a call whose grid and batch would need more
+ * -- about 2 bytes per pixel + 4 bytes per valid centre + 13 bytes per query +
+ * 4 bytes per query per 1,024 valid centres -- is rejected with SFC_EINVAL
+ * before any device work.  The first call on a device looks up that array's
+ * device address; make that first call before any stream capture.  All calls
+ * share the array and it keeps the last call's contents, so calls that overlap
+ * on the GPU (concurrent streams or host threads) race: serialise them.
+ * Synchronises `stream` once (to learn the dictionary size). */
+int fullscan_query_batch_static(const float* grid, const uint8_t* dict_mask, const uint8_t* cur_mask,
+                                const sfc_grid* g, const sfc_params* p, const int32_t* centres, int64_t Q,
+                                int64_t* pick, float* cost, void* stream);
+
 /* Exemplar-based inpainting loop (Sec. I; Fig. 1(a)): repeat { find the fill
  * front (known pixels with an unknown axis neighbour; centres moved inside the
  * valid range), take the centre of highest priority (ties: lowest linear

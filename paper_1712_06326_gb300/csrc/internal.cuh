@@ -66,6 +66,9 @@ struct Index {
 // k_dict.cu
 int dict_extract(const uint8_t* mask, const Geo& g, cudaStream_t st, uint32_t** dict, int64_t* N);
 
+int dict_extract_into(const uint8_t* mask, const Geo& g, cudaStream_t st, uint8_t* a, uint8_t* b, uint32_t* counts,
+                      int64_t* dtotal, uint32_t* out, int64_t* N);
+
 // k_pca.cu: basis/mean/evals of every index from a deterministic sample.
 int pca_build(Index& ix, const float* grid, cudaStream_t st);
 
@@ -86,7 +89,14 @@ int fullscan_batch(const Geo& g, const float* grid, const uint8_t* cur_mask, con
                    const int* eoff_all, const float* weights, bool weighted, const int32_t* centres,
                    const int64_t* centre_lin, int64_t Q, int64_t* pick, float* cost, cudaStream_t st);
 
+int fullscan_batch_into(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
+                        const int* eoff_all, const float* weights, bool weighted, const int32_t* centres, int64_t Q,
+                        int64_t* pick, float* cost, int64_t* lin, uint8_t* bad, unsigned int* gmin, float* tilemin,
+                        cudaStream_t st);
+
 // helpers (sfc_api.cu)
 int upload_patch_tables(const Geo& g, int** eoff_all, cudaStream_t st);
+int check_device();
+int make_geo(const sfc_grid* gp, int K, Geo* out);
 
 }  // namespace sfc

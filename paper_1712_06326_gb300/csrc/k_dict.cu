@@ -151,4 +151,38 @@ int dict_extract(const uint8_t* mask, const Geo& g, cudaStream_t st, uint32_t** 
   return SFC_OK;
 }
 
+// The same extraction into caller-provided buffers (no allocation): a, b: npix
+// bytes each; counts: ceil(npix / 2048) words; dtotal: one int64; out: room for
+// every valid centre.  Synchronises `st` once to read N.
+int dict_extract_into(const uint8_t* mask, const Geo& g, cudaStream_t st, uint8_t* a, uint8_t* b, uint32_t* counts,
+                      int64_t* dtotal, uint32_t* out, int64_t* N) {
+  const int64_t npix = g.X * g.Y * g.Z;
+  const int64_t ntiles = (npix + kTile - 1) / kTile;
+  int grid = (int)((npix + 255) / 256 < 152 * 64 ? (npix + 255) / 256 : 152 * 64);
+  count_launch();
+  k_window_all<<<grid, 256, 0, st>>>(mask, a, npix, g.X, g.Y, 0, g.X, g.r);
+  count_launch();
+  k_window_all<<<grid, 256, 0, st>>>(a, b, npix, g.X, g.Y, 1, g.Y, g.r);
+  const uint8_t* flag = b;
+  if (g.ndim == 3) {
+    count_launch();
+    k_window_all<<<grid, 256, 0, st>>>(b, a, npix, g.X, g.Y, 2, g.Z, g.r);
+    flag = a;
+  }
+  count_launch();
+  k_tile_count<<<(unsigned)ntiles, 256, 0, st>>>(flag, npix, counts);
+  count_launch();
+  k_scan_counts<<<1, 1024, 0, st>>>(counts, ntiles, dtotal);
+  int64_t total = 0;
+  SFC_TRY(cudaMemcpyAsync(&total, dtotal, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SFC_TRY(cudaStreamSynchronize(st));
+  if (total > 0) {
+    count_launch();
+    k_tile_emit<<<(unsigned)ntiles, 256, 0, st>>>(flag, npix, counts, out);
+  }
+  SFC_TRY(cudaGetLastError());
+  *N = total;
+  return SFC_OK;
+}
+
 }  // namespace sfc

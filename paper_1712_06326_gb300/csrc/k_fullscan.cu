@@ -339,4 +339,37 @@ int fullscan_batch(const Geo& g, const float* grid, const uint8_t* cur_mask, con
   return SFC_OK;
 }
 
+// The batched full scan into caller-provided scratch (no allocation): lin: Q
+// int64; bad: Q bytes; gmin: Q words; tilemin: Q * ceil(N / 1024) floats.
+int fullscan_batch_into(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
+                        const int* eoff_all, const float* weights, bool weighted, const int32_t* centres, int64_t Q,
+                        int64_t* pick, float* cost, int64_t* lin, uint8_t* bad, unsigned int* gmin, float* tilemin,
+                        cudaStream_t st) {
+  if (Q <= 0) return SFC_OK;
+  constexpr int EPT = 4;
+  const int64_t ntiles = (N + kFsThreads * EPT - 1) / (kFsThreads * EPT);
+  const unsigned qb = (unsigned)((Q + 255) / 256);
+  count_launch();
+  k_centre_lin<<<qb, 256, 0, st>>>(centres, Q, g, lin, status_word());
+  count_launch();
+  k_centre_fix<<<qb, 256, 0, st>>>(lin, Q, g, bad);
+  count_launch();
+  k_fill_u32<<<qb, 256, 0, st>>>(gmin, Q, 0x7f800000u);
+  int rc;
+  if (Q >= 8)
+    rc = weighted ? run_scan<8, EPT, true>(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, st)
+                  : run_scan<8, EPT, false>(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, st);
+  else
+    rc = weighted ? run_scan<1, EPT, true>(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, st)
+                  : run_scan<1, EPT, false>(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, st);
+  SFC_CHECK(rc);
+  rc = weighted ? run_band<EPT, true>(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, pick, cost, st)
+                : run_band<EPT, false>(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, pick, cost, st);
+  SFC_CHECK(rc);
+  count_launch();
+  k_mark_bad<<<qb, 256, 0, st>>>(bad, Q, pick, cost);
+  SFC_TRY(cudaGetLastError());
+  return SFC_OK;
+}
+
 }  // namespace sfc

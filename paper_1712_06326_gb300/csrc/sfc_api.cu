@@ -48,8 +48,6 @@ int fill_loop(const Geo& g, float* grid, uint8_t* mask, int prio, int mode, cons
               int64_t N, const int* eoff_all, const float* weights, bool weighted, int64_t max_steps, int64_t* log,
               int64_t* steps_done, cudaStream_t st);
 
-namespace {
-
 // The device must be an sm_103 part (the library carries sm_103a code only) and
 // the status word must be reachable.
 int check_device() {
@@ -118,6 +116,8 @@ int make_geo(const sfc_grid* gp, int K, Geo* out) {
   *out = g;
   return SFC_OK;
 }
+
+namespace {
 
 // Subset rule (Fig. 2): anchors at the middles of the patch edges and at its
 // corners (2-D: top, right, bottom, left middles, then TL, TR, BR, BL corners;

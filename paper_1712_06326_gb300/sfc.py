@@ -23,8 +23,8 @@ SFC_PRIO_CONFIDENCE, SFC_PRIO_CRIMINISI = 0, 1
 SFC_MODE_FULLSCAN, SFC_MODE_SFC = 0, 1
 
 EXPORTS = ["sfc_params_default", "sfc_index_build", "sfc_index_destroy", "sfc_index_info", "sfc_index_export",
-           "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "inpaint_run", "sfc_status",
-           "sfc_launch_count", "sfc_last_error"]
+           "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "fullscan_query_batch_static",
+           "inpaint_run", "sfc_status", "sfc_launch_count", "sfc_last_error"]
 
 
 class sfc_grid(C.Structure):
@@ -60,6 +60,7 @@ def lib():
         L.sfc_query_candidates.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp, vp]
         L.fullscan_query_batch.argtypes = [vp, vp, vp, C.POINTER(sfc_grid), C.POINTER(sfc_params), vp, i64, vp, vp,
                                            vp]
+        L.fullscan_query_batch_static.argtypes = list(L.fullscan_query_batch.argtypes)
         L.inpaint_run.argtypes = [vp, vp, C.POINTER(sfc_grid), C.POINTER(sfc_params), i32, i64, vp,
                                   C.POINTER(i64), vp]
         L.sfc_status.argtypes = [vp]
@@ -67,8 +68,8 @@ def lib():
         L.sfc_launch_count.restype = C.c_uint64
         L.sfc_launch_count.argtypes = []
         for name in ["sfc_index_build", "sfc_index_destroy", "sfc_index_info", "sfc_index_export",
-                     "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "inpaint_run",
-                     "sfc_status"]:
+                     "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "fullscan_query_batch_static",
+                     "inpaint_run", "sfc_status"]:
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -230,6 +231,26 @@ def fullscan_query_batch(grid: torch.Tensor, dict_mask: torch.Tensor, cur_mask: 
         cost = torch.empty(Q, dtype=torch.float32, device=grid.device)
     _check(lib().fullscan_query_batch(_ptr(grid), _ptr(dict_mask), _ptr(cur_mask), C.byref(g), C.byref(P.p),
                                       _ptr(centres), Q, _ptr(pick), _ptr(cost), _stream()), "fullscan_query_batch")
+    return pick, cost
+
+
+def fullscan_query_batch_static(grid: torch.Tensor, dict_mask: torch.Tensor, cur_mask: torch.Tensor,
+                                centres: torch.Tensor, K: int, ch_weights=None, pick=None, cost=None):
+    """As fullscan_query_batch, through the entry point that allocates no device memory."""
+    grid = _dev(grid, torch.float32)
+    dict_mask = _dev(dict_mask, torch.uint8)
+    cur_mask = _dev(cur_mask, torch.uint8)
+    centres = _dev(centres, torch.int32)
+    Q = centres.shape[0]
+    P = Params(K=K, ch_weights=ch_weights)
+    g = make_grid(grid)
+    if pick is None:
+        pick = torch.empty(Q, dtype=torch.int64, device=grid.device)
+    if cost is None:
+        cost = torch.empty(Q, dtype=torch.float32, device=grid.device)
+    _check(lib().fullscan_query_batch_static(_ptr(grid), _ptr(dict_mask), _ptr(cur_mask), C.byref(g),
+                                             C.byref(P.p), _ptr(centres), Q, _ptr(pick), _ptr(cost), _stream()),
+           "fullscan_query_batch_static")
     return pick, cost
 
 
