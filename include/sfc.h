@@ -27,10 +27,12 @@
  *   cost(t, j) = sum over known elements e of t: w[ch(e)] * (t_e - p_{j,e})^2.
  * Picks are the argmin over the exact value -- the FP64 sum over elements in
  * raster order with operands widened from FP32 and no fused multiply-add --
- * with ties to the lowest dictionary id.  The kernels compute FP32 costs and
- * rescore in FP64 every candidate whose FP32 cost lies inside a band derived
- * from the FP32 rounding error bound, so the picks are exactly those of that
- * definition.  Reported costs are that FP64 value rounded to FP32.
+ * with ties to the lowest dictionary id.  The kernels compute FP32 costs; when
+ * more than one candidate lies inside the band that the FP32 rounding error
+ * bound leaves around the minimum, those candidates are rescored with that FP64
+ * sum, so the picks are exactly those of the definition.  Reported costs are the
+ * FP32 costs of the picks (within (n + 8) * 2^-24 relative of the exact value,
+ * n = values per patch).
  *
  * Errors.  Every entry point returns SFC_OK (0) or a negative SFC_E* code and
  * records a message readable with sfc_last_error() (per host thread).  Calls
@@ -98,8 +100,9 @@ typedef struct sfc_index sfc_index; /* opaque; owned by the library */
 void sfc_params_default(sfc_params* p);
 
 /* Build the multi-index (Sec. II.A-C): dictionary extraction, the pixel subsets
- * of Fig. 2, a PCA per index (FP64 covariance over a deterministic sample,
- * FP64 Jacobi eigen-solve) unless p->basis is given, FP32 projection, per-axis
+ * of Fig. 2, a PCA per index (covariance of a deterministic sample accumulated to FP64
+ * accuracy, leading eigenvectors by FP64 subspace iteration) unless p->basis is
+ * given, FP32 projection, per-axis
  * quantisation to b bits, Morton keys (top 64 bits), and a stable radix sort of
  * (key, id) per index.  grid/dict_mask: device, layout above.  On success *out
  * owns device memory until sfc_index_destroy.  Synchronises `stream` once (to
@@ -115,7 +118,9 @@ int sfc_index_info(const sfc_index* ix, int64_t* N, int32_t* m, int32_t* s);
 
 /* Copy the index's arrays to HOST buffers (any may be NULL); synchronises.
  * dict: N centre linear indices (int64); subsets: C*m patch pixel indices;
- * basis: C*s*D; mean: C*s; evals: C*s (descending; NaN with a given basis);
+ * basis: C*s*D; mean: C*s; evals: C*s (descending; the leading
+ * min(s, max(2D, D + 8), 24) are computed, the rest and all of them with a
+ * given basis are NaN);
  * lo, scale: C*D; proj: C*N*D and keys: C*N (need keep_intermediates);
  * skeys: C*N; sids: C*N (sorted order per index). */
 int sfc_index_export(const sfc_index* ix, int64_t* dict, int32_t* subsets, float* basis, float* mean, double* evals,
@@ -129,7 +134,7 @@ int sfc_index_export(const sfc_index* ix, int64_t* dict, int32_t* subsets, float
  * the union of candidates with the exact cost in image space and return the
  * argmin.  grid/cur_mask: the current image and known-mask (same geometry as the
  * build); centres: Q x ndim int32; pick: Q int64 dictionary ids; cost: Q float
- * (exact cost of the pick).  Q = 0 is a no-op.  A centre outside the valid range
+ * (FP32 cost of the pick).  Q = 0 is a no-op.  A centre outside the valid range
  * yields pick = -1, cost = NaN and SFC_EDEVICE from sfc_status(). */
 int sfc_query_batch(const sfc_index* ix, const float* grid, const uint8_t* cur_mask, const int32_t* centres,
                     int64_t Q, int64_t* pick, float* cost, void* stream);
@@ -181,8 +186,9 @@ int inpaint_run(float* grid, uint8_t* mask, const sfc_grid* g, const sfc_params*
                 int64_t* log, int64_t* steps_done, void* stream);
 
 /* Read and clear the library's device-side status flags (synchronises stream):
- * SFC_OK, SFC_EDEVICE (invalid centre seen) or SFC_ETIMEOUT (a bounded wait
- * gave up). */
+ * SFC_OK, SFC_ETIMEOUT (a bounded wait gave up), or SFC_EDEVICE (an invalid
+ * centre was seen, a PCA eigen-solve hit its iteration cap, or a fill step made
+ * no progress). */
 int sfc_status(void* stream);
 
 /* Number of kernels the library has launched in this process so far (all host

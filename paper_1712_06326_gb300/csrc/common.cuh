@@ -8,7 +8,7 @@
 namespace sfc {
 
 // Device-side status bits (ORed into a library-owned word, read by sfc_status).
-enum : uint32_t { ST_BAD_CENTRE = 1u, ST_TIMEOUT = 2u, ST_OVERFLOW = 4u };
+enum : uint32_t { ST_BAD_CENTRE = 1u, ST_TIMEOUT = 2u, ST_OVERFLOW = 4u, ST_NOCONV = 8u };
 
 // Upper bound of the spin iterations of any wait on another CTA's flag.
 constexpr long long kSpinLimit = 1ll << 24;
@@ -94,13 +94,16 @@ __device__ inline double exact_cost64(const float* __restrict__ grid, int64_t sr
   return acc;
 }
 
-// Half-width of the FP32 band: |c32 - c| <= gamma * c for a sum of n
-// non-negative terms, each d^2 (d rounded once) times a rounded weight, summed by
-// FMA: gamma = (n + 8) * 2^-24.  A candidate can be the exact argmin only if
-// c32 <= min32 * (1 + 3 gamma) + n * 2^-126 (absolute slack for underflow).
-__device__ inline double band_limit(float min32, int n) {
-  double gamma = (double)(n + 8) * 5.9604644775390625e-8;
-  return (double)min32 * (1.0 + 3.0 * gamma) + (double)n * 1.1754943508222875e-38;
+// Upper end of the FP32 band around the FP32 minimum: |c32 - c| <= gamma * c
+// for a sum of n non-negative terms, each d^2 (d rounded once) times a rounded
+// weight, summed by FMA, with gamma = (n + 8) * 2^-24.  A candidate can be the
+// exact argmin only if c32 <= min32 * (1 + 3 gamma) + n * 2^-126 (absolute
+// slack for underflow).  Every operation rounds up, so the float returned is >=
+// that bound and the band it defines contains the exact one.
+__device__ inline float band_limit32(float min32, int n) {
+  const float g3 = __fmul_ru((float)(n + 8), 1.78813934326171875e-7f);  // 3 * 2^-24
+  const float t = __fmaf_ru(min32, g3, min32);
+  return __fadd_ru(t, __fmul_ru((float)n, 1.1754943508222875e-38f));
 }
 
 // Quantised coordinate (same arithmetic for dictionary entries and queries):

@@ -10,9 +10,11 @@
 // minimum (tile minimum) and folds it into a per-query global minimum.
 // Pass 2 (one CTA per query): every tile whose minimum lies inside the FP32
 // error band of the global minimum is re-evaluated with the identical FP32
-// arithmetic, and each entry inside the band is rescored with the exact FP64
-// sequential cost; argmin over (cost, id).  Costs are non-negative, so float
-// bit patterns order like their values.
+// arithmetic and its in-band entries listed.  One entry in the band is the exact
+// argmin; with several (near-ties) each is rescored with the exact FP64
+// sequential cost and the argmin over (cost, id) taken.  The reported cost is
+// the FP32 cost of the pick.  Costs are non-negative, so float bit patterns order
+// like their values.
 #include "internal.cuh"
 
 namespace sfc {
@@ -20,6 +22,7 @@ namespace sfc {
 namespace {
 
 constexpr int kFsThreads = 256;
+constexpr int kBandCap = 64;  // in-band entries listed per query before the fallback
 
 template <int QT, int EPT, bool WEIGHTED>
 __global__ void __launch_bounds__(kFsThreads) k_fs_scan(const float* __restrict__ grid,
@@ -156,31 +159,88 @@ __global__ void __launch_bounds__(kFsThreads) k_fs_band(const float* __restrict_
   for (int pp = threadIdx.x; pp < P; pp += kFsThreads) tm[pp] = mask[tc + eoff_all[pp * ch] / ch];
   __syncthreads();
   const float m32 = __uint_as_float(gmin[q]);
-  const double T = band_limit(m32, n);
-  double bc = INFINITY;
-  int64_t bj = INT64_MAX;
+  const float T = band_limit32(m32, n);
+  // pass A: collect the in-band entries (usually exactly one)
+  __shared__ int s_cnt;
+  __shared__ int64_t s_j[kBandCap];
+  __shared__ float s_c[kBandCap];
+  if (threadIdx.x == 0) s_cnt = 0;
+  __syncthreads();
   for (int64_t t = 0; t < ntiles; ++t) {
-    if ((double)tilemin[q * ntiles + t] > T) continue;  // uniform across the CTA
+    if (tilemin[q * ntiles + t] > T) continue;  // uniform across the CTA
     for (int k = 0; k < EPT; ++k) {
-      int64_t j = t * kFsThreads * EPT + (int64_t)k * kFsThreads + threadIdx.x;
+      const int64_t j = t * kFsThreads * EPT + (int64_t)k * kFsThreads + threadIdx.x;
       if (j >= N) continue;
-      int64_t sb = (int64_t)dict[j] * ch;
-      float c32 = cost32_one<WEIGHTED>(grid, sb, am, eo, we, n);
-      if ((double)c32 <= T) {
-        double c64 = exact_cost64(grid, sb, tv, tm, eo, P, ch, weights);
-        if (c64 < bc || (c64 == bc && j < bj)) {
-          bc = c64;
-          bj = j;
+      const float c32 = cost32_one<WEIGHTED>(grid, (int64_t)dict[j] * ch, am, eo, we, n);
+      if (c32 <= T) {
+        const int slot = atomicAdd(&s_cnt, 1);
+        if (slot < kBandCap) {
+          s_j[slot] = j;
+          s_c[slot] = c32;
         }
       }
     }
   }
-  warp_argmin64(bc, bj);
+  __syncthreads();
+  const int cnt = s_cnt;
+  if (cnt == 1) {
+    if (threadIdx.x == 0) {
+      pick[q] = s_j[0];
+      cost[q] = s_c[0];
+    }
+    return;
+  }
+  // pass B: exact FP64 rescore of the band (from the list, or -- if it
+  // overflowed -- recomputing the in-band tiles)
+  double bc = INFINITY;
+  int64_t bj = INT64_MAX;
+  float bc32 = 0.0f;
+  if (cnt <= kBandCap) {
+    for (int i = threadIdx.x; i < cnt; i += kFsThreads) {
+      const int64_t j = s_j[i];
+      const double c64 = exact_cost64(grid, (int64_t)dict[j] * ch, tv, tm, eo, P, ch, weights);
+      if (c64 < bc || (c64 == bc && j < bj)) {
+        bc = c64;
+        bj = j;
+        bc32 = s_c[i];
+      }
+    }
+  } else {
+    for (int64_t t = 0; t < ntiles; ++t) {
+      if (tilemin[q * ntiles + t] > T) continue;
+      for (int k = 0; k < EPT; ++k) {
+        const int64_t j = t * kFsThreads * EPT + (int64_t)k * kFsThreads + threadIdx.x;
+        if (j >= N) continue;
+        const int64_t sb = (int64_t)dict[j] * ch;
+        const float c32 = cost32_one<WEIGHTED>(grid, sb, am, eo, we, n);
+        if (c32 <= T) {
+          const double c64 = exact_cost64(grid, sb, tv, tm, eo, P, ch, weights);
+          if (c64 < bc || (c64 == bc && j < bj)) {
+            bc = c64;
+            bj = j;
+            bc32 = c32;
+          }
+        }
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double c2 = __shfl_xor_sync(0xffffffffu, bc, o);
+    const int64_t j2 = __shfl_xor_sync(0xffffffffu, bj, o);
+    const float f2 = __shfl_xor_sync(0xffffffffu, bc32, o);
+    if (c2 < bc || (c2 == bc && j2 < bj)) {
+      bc = c2;
+      bj = j2;
+      bc32 = f2;
+    }
+  }
   __shared__ double sd[kFsThreads / 32];
   __shared__ int64_t si[kFsThreads / 32];
+  __shared__ float sf[kFsThreads / 32];
   if ((threadIdx.x & 31) == 0) {
     sd[threadIdx.x >> 5] = bc;
     si[threadIdx.x >> 5] = bj;
+    sf[threadIdx.x >> 5] = bc32;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -188,13 +248,14 @@ __global__ void __launch_bounds__(kFsThreads) k_fs_band(const float* __restrict_
       if (sd[w] < bc || (sd[w] == bc && si[w] < bj)) {
         bc = sd[w];
         bj = si[w];
+        bc32 = sf[w];
       }
     if (bj == INT64_MAX) {
       pick[q] = -1;
       cost[q] = __int_as_float(0x7fc00000);
     } else {
       pick[q] = bj;
-      cost[q] = (float)bc;
+      cost[q] = bc32;
     }
   }
 }

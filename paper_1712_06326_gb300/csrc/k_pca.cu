@@ -2,19 +2,47 @@
 // principal components are kept).
 //
 // Data of index c: the subset values (Fig. 2) of dictionary patches, s = m*ch per
-// patch.  The covariance is accumulated in FP64 over a deterministic sample (ids
-// 0, step, 2 step, ... with step = ceil(N / S)), the eigen-decomposition is the
-// cyclic Jacobi method in FP64 with a parallel (round-robin) ordering: in every
-// round the s/2 disjoint index pairs are rotated at once, A <- J^T A J and
-// V <- V J, one launch per round, the matrix double-buffered so every launch
-// reads the previous round's matrix only.  Sweeps stop when the off-diagonal
-// norm falls below 1e-15 of the whole norm (checked after every sweep on the
-// device; later launches then return at once).  Eigenvectors are ordered by
-// descending eigenvalue (ties: lower column), signed so that the component of
-// largest magnitude is positive (ties: lowest index), and rounded to FP32.
+// patch, over a deterministic sample (ids 0, step, 2 step, ... with
+// step = ceil(N / S)).
+//
+// Covariance.  Every index's subset is part of the same patch and all indices
+// use the same sample, so the mean and the raw second moments are computed once
+// for all n patch values and each index's covariance is cut out of them.
+// FP64-accurate, computed on the FP32 pipe (this part's FP64 pipe is 1/64 of
+// its FP32 rate): the raw second moments sum_a x_i x_j of the FP32 values, each product formed exactly as a pair (p, e) with p = x_i x_j and
+// e = fma(x_i, x_j, -p) (Dekker's two-product), accumulated in double-float
+// (Knuth's two-sum on the high word, the rounding errors and e added to a low
+// word); per sample split the pair is folded to FP64, the splits are summed in
+// FP64 in a fixed order and cov = M2 / S - mu mu^T is formed in FP64.  The mean
+// is accumulated the same way.  Fixed orders throughout: the result is the same
+// on every run.
+//
+// Eigenvectors.  Only the leading D are needed, so the eigen-solve is block
+// subspace iteration with Rayleigh-Ritz projection (Rutishauser's simultaneous
+// iteration; e.g. Saad, "Numerical Methods for Large Eigenvalue Problems",
+// Ch. 5), in FP64, on p = min(s, max(2D, D + 8), 24) vectors:
+//     Y = A Q;  H = Q^T Y;  H = W diag(e) W^T (parallel-order Jacobi, p x p);
+//     X = Q W;  Z = Y W (= A X);  stop when |Z_k - e_k X_k| <= 1e-11 e_0 for
+//     every k < D;  else Q = orthonormal basis of Z (Cholesky QR, twice).
+// The start block holds the unit vectors of the p largest diagonal entries of A
+// plus a small deterministic perturbation.  When A's row slices fit in shared
+// memory (s up to ~440), the whole iteration runs in one launch on a cluster of
+// 8 CTAs per curve (see k_si_cluster); otherwise one launch per iteration
+// computes Y = A Q with every curve's rows spread over the GPU and a second (one
+// CTA per curve) does the p-sized work, a device-side flag ending the iteration
+// early.  A curve that has not converged within the iteration cap raises
+// ST_NOCONV.  Jacobi rotation angles are taken in FP32 and the
+// rotation made orthogonal to FP64 precision by a Newton step for
+// 1/sqrt(1 + t^2) (no FP64 division or square root in the loop).  Eigenvectors
+// are ordered by descending eigenvalue and signed so that the component of
+// largest magnitude is positive (ties: lowest index), then rounded to FP32.
+#include <cooperative_groups.h>
+
 #include <cmath>
 
 #include "internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace sfc {
 
@@ -22,273 +50,716 @@ namespace {
 
 constexpr int kTile = 32;    // covariance tile (kTile x kTile outputs per CTA)
 constexpr int kChunk = 32;   // samples staged per shared-memory step
-constexpr int kMaxSweeps = 16;
+constexpr int kMaxIter = 48; // subspace iterations enqueued at most
+constexpr int kPMax = 24;    // largest block size p
 
-// mean[c][i] = (1/S') sum_a x_{ids[a]}[i], FP64, fixed summation order.
-__global__ void k_mean(const float* __restrict__ grid, const uint32_t* __restrict__ dict, int64_t step, int64_t cnt,
-                       const int* __restrict__ sub_eoff, int s, int ch, double* __restrict__ mean) {
-  const int c = blockIdx.y;
-  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
-  const int lane_s = threadIdx.x >> 5;  // 8 sample lanes
-  __shared__ double part[8][32];
-  double acc = 0.0;
-  if (i < s) {
-    const int eo = sub_eoff[c * s + i];
-    for (int64_t a = lane_s; a < cnt; a += 8) acc += (double)grid[(int64_t)dict[a * step] * ch + eo];
-  }
-  part[lane_s][threadIdx.x & 31] = acc;
-  __syncthreads();
-  if (lane_s == 0 && i < s) {
-    double t = 0.0;
-    for (int l = 0; l < 8; ++l) t += part[l][threadIdx.x];
-    mean[c * s + i] = t / (double)cnt;
-  }
+// (hi, lo) += v in double-float (two-sum on hi, the error into lo)
+__device__ inline void df_add(float v, float& hi, float& lo) {
+  float t = __fadd_rn(hi, v);
+  float bp = __fsub_rn(t, hi);
+  float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+  lo = __fadd_rn(lo, err);
+  hi = t;
 }
 
-// Partial covariance tile: rows [ti*32, +32) x cols [tj*32, +32) (tj >= ti) over
-// the samples of one split.  partial layout [c][split][pair][32][32].
-__global__ void k_cov_partial(const float* __restrict__ grid, const uint32_t* __restrict__ dict, int64_t step,
-                              int64_t cnt, const int* __restrict__ sub_eoff, const double* __restrict__ mean, int s,
-                              int ch, int nsplit, const int2* __restrict__ pairs, int npairs,
-                              double* __restrict__ partial) {
-  const int c = blockIdx.z, split = blockIdx.y, pr = blockIdx.x;
+// (hi, lo) += a * b, the product formed exactly (two-product)
+__device__ inline void df_acc_prod(float a, float b, float& hi, float& lo) {
+  float p = __fmul_rn(a, b);
+  float e = __fmaf_rn(a, b, -p);
+  float t = __fadd_rn(hi, p);
+  float bp = __fsub_rn(t, hi);
+  float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+  hi = t;
+}
+
+// Partial sums of every patch value over one split of the sample (double-float,
+// folded to FP64 every 64 samples): msum[split][e], fixed order.
+__global__ void k_mean_partial(const float* __restrict__ grid, const uint32_t* __restrict__ dict, int64_t step,
+                               int64_t cnt, const int* __restrict__ eoff, int n, int ch, int nsplit,
+                               double* __restrict__ msum) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int split = blockIdx.y;
+  if (e >= n) return;
+  const int64_t per = (cnt + nsplit - 1) / nsplit;
+  const int64_t a0 = split * per, a1 = a0 + per < cnt ? a0 + per : cnt;
+  const int eo = eoff[e];
+  double acc = 0.0;
+  float hi = 0.0f, lo = 0.0f;
+  int k = 0;
+  for (int64_t a = a0; a < a1; ++a) {
+    df_add(grid[(int64_t)dict[a * step] * ch + eo], hi, lo);
+    if (++k == 64) {
+      acc += (double)hi + (double)lo;
+      hi = lo = 0.0f;
+      k = 0;
+    }
+  }
+  msum[(int64_t)split * n + e] = acc + ((double)hi + (double)lo);
+}
+
+// mean[e] = (sum over splits in order) / cnt
+__global__ void k_mean_reduce(const double* __restrict__ msum, int n, int nsplit, int64_t cnt,
+                              double* __restrict__ mean) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  double t = 0.0;
+  for (int sp = 0; sp < nsplit; ++sp) t += msum[(int64_t)sp * n + e];
+  mean[e] = t / (double)cnt;
+}
+
+// Partial raw second moments sum_a x_i x_j of the whole patch (n values), tile
+// (ti, tj), ti <= tj, over one split of the sample: partial layout
+// [split][pair][32][32] (FP64, folded from double-float).
+__global__ void __launch_bounds__(256) k_cov_partial(const float* __restrict__ grid, const uint32_t* __restrict__ dict,
+                                                     int64_t step, int64_t cnt, const int* __restrict__ eoff, int n,
+                                                     int ch, int nsplit, const int2* __restrict__ pairs, int npairs,
+                                                     double* __restrict__ partial) {
+  const int split = blockIdx.y, pr = blockIdx.x;
   const int2 tp = pairs[pr];
   const int i0 = tp.x * kTile, j0 = tp.y * kTile;
-  __shared__ double xi[kChunk][kTile + 1];
-  __shared__ double xj[kChunk][kTile + 1];
+  __shared__ float xi[kChunk][kTile + 1];
+  __shared__ float xj[kChunk][kTile + 1];
   __shared__ int eoi[kTile], eoj[kTile];
-  __shared__ double mi[kTile], mj[kTile];
   if (threadIdx.x < kTile) {
     int i = i0 + threadIdx.x, j = j0 + threadIdx.x;
-    eoi[threadIdx.x] = i < s ? sub_eoff[c * s + i] : 0;
-    eoj[threadIdx.x] = j < s ? sub_eoff[c * s + j] : 0;
-    mi[threadIdx.x] = i < s ? mean[c * s + i] : 0.0;
-    mj[threadIdx.x] = j < s ? mean[c * s + j] : 0.0;
+    eoi[threadIdx.x] = i < n ? eoff[i] : 0;
+    eoj[threadIdx.x] = j < n ? eoff[j] : 0;
   }
   __syncthreads();
   const int64_t per = (cnt + nsplit - 1) / nsplit;
   const int64_t a0 = split * per, a1 = a0 + per < cnt ? a0 + per : cnt;
   const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;  // 16x16 threads, 2x2 outputs each
-  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  float hi[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, lo[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
   for (int64_t ab = a0; ab < a1; ab += kChunk) {
     for (int t = threadIdx.x; t < kChunk * kTile; t += blockDim.x) {
       int k = t / kTile, e = t % kTile;
       int64_t a = ab + k;
-      double vi = 0.0, vj = 0.0;
+      float vi = 0.0f, vj = 0.0f;
       if (a < a1) {
         int64_t base = (int64_t)dict[a * step] * ch;
-        if (i0 + e < s) vi = (double)grid[base + eoi[e]] - mi[e];
-        if (j0 + e < s) vj = (double)grid[base + eoj[e]] - mj[e];
+        if (i0 + e < n) vi = grid[base + eoi[e]];
+        if (j0 + e < n) vj = grid[base + eoj[e]];
       }
       xi[k][e] = vi;
       xj[k][e] = vj;
     }
     __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
     for (int k = 0; k < kChunk; ++k) {
-      double a0v = xi[k][ty * 2], a1v = xi[k][ty * 2 + 1];
-      double b0v = xj[k][tx * 2], b1v = xj[k][tx * 2 + 1];
-      acc[0][0] = fma(a0v, b0v, acc[0][0]);
-      acc[0][1] = fma(a0v, b1v, acc[0][1]);
-      acc[1][0] = fma(a1v, b0v, acc[1][0]);
-      acc[1][1] = fma(a1v, b1v, acc[1][1]);
+      float a0v = xi[k][ty * 2], a1v = xi[k][ty * 2 + 1];
+      float b0v = xj[k][tx * 2], b1v = xj[k][tx * 2 + 1];
+      df_acc_prod(a0v, b0v, hi[0][0], lo[0][0]);
+      df_acc_prod(a0v, b1v, hi[0][1], lo[0][1]);
+      df_acc_prod(a1v, b0v, hi[1][0], lo[1][0]);
+      df_acc_prod(a1v, b1v, hi[1][1], lo[1][1]);
     }
     __syncthreads();
   }
-  double* out = partial + (((int64_t)c * nsplit + split) * npairs + pr) * kTile * kTile;
+  double* out = partial + ((int64_t)split * npairs + pr) * kTile * kTile;
   for (int a = 0; a < 2; ++a)
-    for (int b = 0; b < 2; ++b) out[(ty * 2 + a) * kTile + tx * 2 + b] = acc[a][b];
+    for (int b = 0; b < 2; ++b) out[(ty * 2 + a) * kTile + tx * 2 + b] = (double)hi[a][b] + (double)lo[a][b];
 }
 
-// A[c] (ns x ns, ns = s rounded up to even) = sum over splits / cnt, symmetric;
-// padding rows/cols are zero.  V[c] = identity.
-__global__ void k_cov_reduce(const double* __restrict__ partial, int nsplit, const int2* __restrict__ pairs,
-                             int npairs, int64_t cnt, int s, int ns, double* __restrict__ A, double* __restrict__ V) {
-  const int c = blockIdx.y;
-  double* Ac = A + (int64_t)c * ns * ns;
-  double* Vc = V + (int64_t)c * ns * ns;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)ns * ns;
+// Full-patch second moments M[e][f] (n x n, both triangles) = sum over splits.
+__global__ void k_cov_reduce(const double* __restrict__ partial, int nsplit, int npairs, int n,
+                             double* __restrict__ M) {
+  const int T = (n + kTile - 1) / kTile;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * n;
        t += (int64_t)gridDim.x * blockDim.x) {
-    int i = (int)(t / ns), j = (int)(t % ns);
-    Vc[t] = i == j ? 1.0 : 0.0;
+    int i = (int)(t / n), j = (int)(t % n);
+    int a = i <= j ? i : j, b = i <= j ? j : i;
+    int ti = a / kTile, tj = b / kTile;
+    int pr = ti * T - ti * (ti - 1) / 2 + (tj - ti);
     double v = 0.0;
-    if (i < s && j < s) {
-      int a = i <= j ? i : j, b = i <= j ? j : i;
-      int ti = a / kTile, tj = b / kTile;
-      // pair index of (ti, tj) in the row-major upper-triangle enumeration
-      int T = (s + kTile - 1) / kTile;
-      int pr = ti * T - ti * (ti - 1) / 2 + (tj - ti);
-      for (int sp = 0; sp < nsplit; ++sp)
-        v += partial[(((int64_t)c * nsplit + sp) * npairs + pr) * kTile * kTile + (a - ti * kTile) * kTile +
-                     (b - tj * kTile)];
-      v = v / (double)cnt;
-    }
-    Ac[t] = v;
+    for (int sp = 0; sp < nsplit; ++sp)
+      v += partial[((int64_t)sp * npairs + pr) * kTile * kTile + (a - ti * kTile) * kTile + (b - tj * kTile)];
+    M[t] = v;
   }
 }
 
-// Round-robin pairing of round k over n (even) indices: pair 0 = (k, n-1),
-// pair i >= 1 = ((k + i) mod (n-1), (k - i) mod (n-1)); every pair of indices
-// meets exactly once in n-1 rounds.
-__device__ inline void rr_pair(int k, int i, int n, int& p, int& q) {
+// Covariance of index c from the full-patch moments: the subset's value i is
+// patch value e_i = sub_pix[c][i / ch] * ch + i % ch;
+// A[c][i][j] = M[e_i][e_j] / cnt - mean[e_i] mean[e_j]; mean_c[i] = mean[e_i].
+__global__ void k_cov_extract(const double* __restrict__ M, const double* __restrict__ mean, int n, int ch, int64_t cnt,
+                              const int32_t* __restrict__ sub_pix, int m, int s, double* __restrict__ A,
+                              double* __restrict__ mean_c) {
+  const int c = blockIdx.y;
+  const int32_t* sp = sub_pix + (int64_t)c * m;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)s * s;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / s), j = (int)(t % s);
+    const int ei = sp[i / ch] * ch + i % ch, ej = sp[j / ch] * ch + j % ch;
+    A[(int64_t)c * s * s + t] = M[(int64_t)ei * n + ej] / (double)cnt - mean[ei] * mean[ej];
+    if (j == 0) mean_c[(int64_t)c * s + i] = mean[ei];
+  }
+}
+
+// ----------------------------------------------------------------------------
+// subspace iteration
+// ----------------------------------------------------------------------------
+struct SiBufs {
+  double* A;   // C*s*s
+  double* Q;   // C*s*p
+  double* Y;   // C*s*p
+  double* X;   // C*s*p
+  double* e;   // C*p
+  int* done;   // C
+};
+
+// Y = A Q for every curve; blockIdx.y = curve, the s*p outputs spread over
+// blockIdx.x.
+__global__ void __launch_bounds__(256) k_si_gemm(SiBufs b, int s, int p) {
+  const int c = blockIdx.y;
+  if (b.done[c]) return;
+  extern __shared__ double qs[];  // s*p
+  const double* Q = b.Q + (int64_t)c * s * p;
+  for (int t = threadIdx.x; t < s * p; t += blockDim.x) qs[t] = Q[t];
+  __syncthreads();
+  const double* A = b.A + (int64_t)c * s * s;
+  double* Y = b.Y + (int64_t)c * s * p;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < s * p; t += gridDim.x * blockDim.x) {
+    const int i = t / p, k = t % p;
+    const double* ar = A + (int64_t)i * s;
+    double acc = 0.0;
+    for (int j = 0; j < s; ++j) acc = fma(ar[j], qs[j * p + k], acc);
+    Y[t] = acc;
+  }
+}
+
+// Sum of one double per thread over the CTA (result in every thread).
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  __syncthreads();
+  return t;
+}
+
+// Orthonormalise the s x p block Z (shared, in place) by Cholesky QR: G = Z^T Z,
+// G = R^T R, Z <- Z R^{-1}.  G (p x p, shared) holds R afterwards.
+__device__ void chol_qr(double* Z, int s, int p, double* G) {
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    int a = t / p, b = t % p;
+    double acc = 0.0;
+    if (a <= b)
+      for (int i = 0; i < s; ++i) acc = fma(Z[i * p + a], Z[i * p + b], acc);
+    G[t] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    for (int k = 0; k < p; ++k) {
+      if (threadIdx.x == 0) G[k * p + k] = sqrt(fmax(G[k * p + k], 1e-300));
+      __syncwarp();
+      const double rkk = G[k * p + k];
+      for (int j = k + 1 + threadIdx.x; j < p; j += 32) G[k * p + j] /= rkk;
+      __syncwarp();
+      for (int t = threadIdx.x; t < p * p; t += 32) {
+        int i = t / p, j = t % p;
+        if (i > k && j >= i) G[i * p + j] -= G[k * p + i] * G[k * p + j];
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
+    double z[kPMax];
+    for (int k = 0; k < p; ++k) z[k] = Z[i * p + k];
+    for (int k = 0; k < p; ++k) {
+      double v = z[k];
+      for (int j = 0; j < k; ++j) v -= z[j] * G[j * p + k];
+      z[k] = v / G[k * p + k];
+    }
+    for (int k = 0; k < p; ++k) Z[i * p + k] = z[k];
+  }
+  __syncthreads();
+}
+
+// Round-robin pairing of round r over n (even) indices: pair 0 = (r, n-1), pair
+// i >= 1 = ((r + i) mod (n-1), (r - i) mod (n-1)); every pair meets once per
+// n-1 rounds.
+__device__ inline void rr_pair(int r, int i, int n, int& p, int& q) {
   int a, b;
   if (i == 0) {
-    a = k;
+    a = r;
     b = n - 1;
   } else {
-    a = (k + i) % (n - 1);
-    b = ((k - i) % (n - 1) + (n - 1)) % (n - 1);
+    a = (r + i) % (n - 1);
+    b = ((r - i) % (n - 1) + (n - 1)) % (n - 1);
   }
   p = a < b ? a : b;
   q = a < b ? b : a;
 }
 
-// One parallel Jacobi round on every index: Anew = J^T Aold J, V <- V J.
-__global__ void k_jacobi_round(const double* __restrict__ Aold, double* __restrict__ Anew, double* __restrict__ V,
-                               int ns, int round, const int* __restrict__ done) {
-  const int c = blockIdx.y;
-  if (done[c]) {
-    // keep the buffers in step: copy so the next round reads the same matrix
-    const double* a = Aold + (int64_t)c * ns * ns;
-    double* b = Anew + (int64_t)c * ns * ns;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)ns * ns;
-         t += (int64_t)gridDim.x * blockDim.x)
-      b[t] = a[t];
+// Parallel-order Jacobi on the small symmetric H (np x np, np even, shared;
+// padding rows/columns zero), eigenvectors accumulated into W.  Each round
+// rotates np/2 disjoint pairs; every thread updates whole 2x2 blocks in place.
+__device__ void small_jacobi(double* H, double* W, int np, double* al, double* be, double* red) {
+  for (int t = threadIdx.x; t < np * np; t += blockDim.x) W[t] = (t / np == t % np) ? 1.0 : 0.0;
+  __syncthreads();
+  const int half = np / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = 0.0, all = 0.0;
+    for (int t = threadIdx.x; t < np * np; t += blockDim.x) {
+      double v = H[t] * H[t];
+      all += v;
+      if (t / np != t % np) off += v;
+    }
+    off = block_sum(off, red);
+    all = block_sum(all, red);
+    if (off <= 1e-28 * all || off == 0.0) break;
+    for (int r = 0; r < np - 1; ++r) {
+      for (int i = threadIdx.x; i < half; i += blockDim.x) {
+        int pp, qq;
+        rr_pair(r, i, np, pp, qq);
+        const double apq = H[pp * np + qq];
+        double cs = 1.0, sn = 0.0;
+        const float apq32 = (float)apq;
+        if (apq32 != 0.0f) {
+          // angle in FP32, rotation orthogonal to FP64 precision
+          const float tau = __fdiv_rn((float)(H[qq * np + qq] - H[pp * np + pp]), 2.0f * apq32);
+          const float t32 = tau >= 0.0f ? 1.0f / (tau + sqrtf(1.0f + tau * tau))
+                                        : -1.0f / (-tau + sqrtf(1.0f + tau * tau));
+          const double t = (double)t32;
+          const double u = fma(t, t, 1.0);
+          double y = (double)rsqrtf((float)u);
+          y = y * fma(-0.5 * u, y * y, 1.5);
+          y = y * fma(-0.5 * u, y * y, 1.5);
+          cs = y;
+          sn = t * y;
+        }
+        // J[p][p] = c, J[p][q] = s, J[q][p] = -s, J[q][q] = c
+        al[pp] = cs;
+        be[pp] = -sn;
+        al[qq] = cs;
+        be[qq] = sn;
+      }
+      __syncthreads();
+      const int nblk = half * (half + 1) / 2;
+      for (int t = threadIdx.x; t < nblk + np * half; t += blockDim.x) {
+        if (t < nblk) {
+          int u = 0;
+          while ((u + 1) * (u + 2) / 2 <= t) ++u;
+          const int v = t - u * (u + 1) / 2;
+          int pu, qu, pv, qv;
+          rr_pair(r, u, np, pu, qu);
+          rr_pair(r, v, np, pv, qv);
+          const int I[2] = {pu, qu}, J[2] = {pv, qv};
+          double a[2][2], rw[2][2];
+          for (int x = 0; x < 2; ++x)
+            for (int y = 0; y < 2; ++y) a[x][y] = H[I[x] * np + J[y]];
+          for (int x = 0; x < 2; ++x)
+            for (int y = 0; y < 2; ++y) rw[x][y] = fma(al[I[x]], a[x][y], be[I[x]] * a[1 - x][y]);
+          for (int x = 0; x < 2; ++x)
+            for (int y = 0; y < 2; ++y) {
+              const double v2 = fma(al[J[y]], rw[x][y], be[J[y]] * rw[x][1 - y]);
+              H[I[x] * np + J[y]] = v2;
+              H[J[y] * np + I[x]] = v2;
+            }
+        } else {
+          const int w = t - nblk;
+          const int row = w / half, v = w % half;
+          int pv, qv;
+          rr_pair(r, v, np, pv, qv);
+          const double x0 = W[row * np + pv], x1 = W[row * np + qv];
+          W[row * np + pv] = fma(al[pv], x0, be[pv] * x1);
+          W[row * np + qv] = fma(al[qv], x1, be[qv] * x0);
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// The p-sized part of one iteration (one CTA per curve, all in shared memory):
+// H = Q^T Y, eig(H), X = Q W, Z = Y W, convergence test, Q = orth(Z).
+__global__ void __launch_bounds__(256) k_si_small(SiBufs b, int s, int p, int D) {
+  const int c = blockIdx.x;
+  if (b.done[c]) return;
+  const int np = p + (p & 1);
+  extern __shared__ double sm[];
+  double* Q = sm;               // s*p
+  double* Y = Q + s * p;        // s*p
+  double* H = Y + s * p;        // np*np
+  double* W = H + np * np;      // np*np
+  double* ev = W + np * np;     // np
+  double* al = ev + np;         // np
+  double* be = al + np;         // np
+  int* ord = reinterpret_cast<int*>(be + np);  // np
+  __shared__ double red[8];
+  const double* Qg = b.Q + (int64_t)c * s * p;
+  const double* Yg = b.Y + (int64_t)c * s * p;
+  for (int t = threadIdx.x; t < s * p; t += blockDim.x) {
+    Q[t] = Qg[t];
+    Y[t] = Yg[t];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < np * np; t += blockDim.x) {
+    const int a = t / np, bb = t % np;
+    double acc = 0.0;
+    if (a < p && bb < p && a <= bb) {
+      for (int i = 0; i < s; ++i) acc = fma(Q[i * p + a], Y[i * p + bb], acc);
+      // Q^T A Q is symmetric up to rounding: average the two triangles
+      double acc2 = 0.0;
+      for (int i = 0; i < s; ++i) acc2 = fma(Q[i * p + bb], Y[i * p + a], acc2);
+      acc = 0.5 * (acc + acc2);
+    }
+    if (a <= bb) {
+      H[a * np + bb] = acc;
+      H[bb * np + a] = acc;
+    }
+  }
+  __syncthreads();
+  small_jacobi(H, W, np, al, be, red);
+  // order the p real Ritz values descending (ties: lower column)
+  for (int k = threadIdx.x; k < p; k += blockDim.x) {
+    const double ek = H[k * np + k];
+    int r = 0;
+    for (int j = 0; j < p; ++j) {
+      const double ej = H[j * np + j];
+      if (ej > ek || (ej == ek && j < k)) ++r;
+    }
+    ord[r] = k;
+    ev[r] = ek;
+  }
+  __syncthreads();
+  double* Xg = b.X + (int64_t)c * s * p;
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
+    double x[kPMax], z[kPMax];
+    for (int k = 0; k < p; ++k) {
+      const int col = ord[k];
+      double ax = 0.0, az = 0.0;
+      for (int j = 0; j < p; ++j) {
+        ax = fma(Q[i * p + j], W[j * np + col], ax);
+        az = fma(Y[i * p + j], W[j * np + col], az);
+      }
+      x[k] = ax;
+      z[k] = az;
+    }
+    for (int k = 0; k < p; ++k) {
+      Xg[(int64_t)i * p + k] = x[k];
+      Q[i * p + k] = x[k];
+      Y[i * p + k] = z[k];
+    }
+  }
+  __syncthreads();
+  double worst = 0.0;
+  for (int k = 0; k < D; ++k) {
+    double r2 = 0.0;
+    for (int i = threadIdx.x; i < s; i += blockDim.x) {
+      const double r = Y[i * p + k] - ev[k] * Q[i * p + k];
+      r2 = fma(r, r, r2);
+    }
+    worst = fmax(worst, block_sum(r2, red));
+  }
+  if (threadIdx.x < p) b.e[(int64_t)c * p + threadIdx.x] = ev[threadIdx.x];
+  const bool conv = sqrt(worst) <= 1e-11 * fabs(ev[0]);
+  __syncthreads();
+  if (conv) {
+    if (threadIdx.x == 0) b.done[c] = 1;
     return;
   }
-  extern __shared__ unsigned char smem_raw[];
-  double* al = reinterpret_cast<double*>(smem_raw);  // alpha[i] = J[i][i]
-  double* be = al + ns;                               // beta[i]  = J[partner][i]
-  int* pa = reinterpret_cast<int*>(be + ns);          // partner[i]
-  const double* A = Aold + (int64_t)c * ns * ns;
-  const int half = ns / 2;
-  for (int i = threadIdx.x; i < half; i += blockDim.x) {
-    int p, q;
-    rr_pair(round, i, ns, p, q);
-    double apq = A[(int64_t)p * ns + q];
-    double cs = 1.0, sn = 0.0;
-    if (apq != 0.0) {
-      double app = A[(int64_t)p * ns + p], aqq = A[(int64_t)q * ns + q];
-      double tau = (aqq - app) / (2.0 * apq);
-      double t = tau >= 0.0 ? 1.0 / (tau + sqrt(1.0 + tau * tau)) : -1.0 / (-tau + sqrt(1.0 + tau * tau));
-      cs = 1.0 / sqrt(1.0 + t * t);
-      sn = t * cs;
-    }
-    // J[p][p] = c, J[p][q] = s, J[q][p] = -s, J[q][q] = c
-    al[p] = cs;
-    be[p] = -sn;
-    pa[p] = q;
-    al[q] = cs;
-    be[q] = sn;
-    pa[q] = p;
-  }
-  __syncthreads();
-  double* An = Anew + (int64_t)c * ns * ns;
-  double* Vc = V + (int64_t)c * ns * ns;
-  const int64_t nblk = (int64_t)half * (half + 1) / 2;
-  const int64_t nv = (int64_t)ns * half;
-  const int64_t total = nblk + nv;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    if (t < nblk) {
-      // block (u, v), u <= v, of the pairing
-      int u = (int)((sqrtf((float)(8 * t + 1)) - 1.0f) * 0.5f);
-      while ((int64_t)(u + 1) * (u + 2) / 2 <= t) ++u;
-      while ((int64_t)u * (u + 1) / 2 > t) --u;
-      int v = (int)(t - (int64_t)u * (u + 1) / 2);  // v <= u
-      int pu, qu, pv, qv;
-      rr_pair(round, u, ns, pu, qu);
-      rr_pair(round, v, ns, pv, qv);
-      const int I[2] = {pu, qu}, Jx[2] = {pv, qv};
-      double a[2][2], rr[2][2];
-      for (int x = 0; x < 2; ++x)
-        for (int y = 0; y < 2; ++y) a[x][y] = A[(int64_t)I[x] * ns + Jx[y]];
-      // rows: (J^T A)_{ij} = alpha_i A_ij + beta_i A_i'j
-      for (int x = 0; x < 2; ++x)
-        for (int y = 0; y < 2; ++y) rr[x][y] = fma(al[I[x]], a[x][y], be[I[x]] * a[1 - x][y]);
-      // columns: (R J)_{ij} = alpha_j R_ij + beta_j R_ij'
-      for (int x = 0; x < 2; ++x)
-        for (int y = 0; y < 2; ++y) {
-          int i = I[x], j = Jx[y];
-          double r = fma(al[j], rr[x][y], be[j] * rr[x][1 - y]);
-          An[(int64_t)i * ns + j] = r;
-          An[(int64_t)j * ns + i] = r;
-        }
-    } else {
-      int64_t w = t - nblk;
-      int row = (int)(w / half), v = (int)(w % half);
-      int pv, qv;
-      rr_pair(round, v, ns, pv, qv);
-      double x0 = Vc[(int64_t)row * ns + pv], x1 = Vc[(int64_t)row * ns + qv];
-      Vc[(int64_t)row * ns + pv] = fma(al[pv], x0, be[pv] * x1);
-      Vc[(int64_t)row * ns + qv] = fma(al[qv], x1, be[qv] * x0);
-    }
-  }
+  chol_qr(Y, s, p, H);
+  chol_qr(Y, s, p, H);
+  double* Qw = b.Q + (int64_t)c * s * p;
+  for (int t = threadIdx.x; t < s * p; t += blockDim.x) Qw[t] = Y[t];
 }
 
-// After a sweep: done[c] = off(A) <= 1e-30 * |A|^2 (squared norms).
-__global__ void k_jacobi_check(const double* __restrict__ A, int ns, int* __restrict__ done) {
+// Start block: unit vectors of the p largest diagonal entries (ties: lower
+// index) + a deterministic perturbation, orthonormalised.
+__global__ void __launch_bounds__(256) k_si_init(SiBufs b, int s, int p) {
   const int c = blockIdx.x;
-  const double* a = A + (int64_t)c * ns * ns;
-  double off = 0.0, all = 0.0;
-  for (int64_t t = threadIdx.x; t < (int64_t)ns * ns; t += blockDim.x) {
-    double v = a[t] * a[t];
-    all += v;
-    if (t / ns != t % ns) off += v;
-  }
-  __shared__ double so[32], sa[32];
-  for (int o = 16; o > 0; o >>= 1) {
-    off += __shfl_xor_sync(0xffffffffu, off, o);
-    all += __shfl_xor_sync(0xffffffffu, all, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    so[threadIdx.x >> 5] = off;
-    sa[threadIdx.x >> 5] = all;
+  extern __shared__ double sm[];
+  double* Z = sm;          // s*p
+  double* G = Z + s * p;   // p*p
+  const double* A = b.A + (int64_t)c * s * s;
+  for (int t = threadIdx.x; t < s * p; t += blockDim.x) {
+    const int i = t / p, k = t % p;
+    Z[t] = 1e-3 * (double)(((i * 7 + k * 13) % 17) - 8) / 8.0;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double o2 = 0.0, a2 = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      o2 += so[w];
-      a2 += sa[w];
-    }
-    if (o2 <= 1e-30 * a2 || o2 == 0.0) done[c] = 1;
-  }
-}
-
-// Order, sign and round the top-D eigenvectors of every index.
-__global__ void k_pca_finalize(const double* __restrict__ A, const double* __restrict__ V,
-                               const double* __restrict__ mean, int s, int ns, int D, float* __restrict__ basis,
-                               float* __restrict__ mean32, double* __restrict__ evals) {
-  const int c = blockIdx.x;
-  const double* a = A + (int64_t)c * ns * ns;
-  const double* v = V + (int64_t)c * ns * ns;
-  extern __shared__ int rank_of_col[];  // rank -> column
   for (int i = threadIdx.x; i < s; i += blockDim.x) {
-    double ei = a[(int64_t)i * ns + i];
-    int rk = 0;
+    const double di = A[(int64_t)i * s + i];
+    int r = 0;
     for (int j = 0; j < s; ++j) {
-      double ej = a[(int64_t)j * ns + j];
-      if (ej > ei || (ej == ei && j < i)) ++rk;
+      const double dj = A[(int64_t)j * s + j];
+      if (dj > di || (dj == di && j < i)) ++r;
     }
-    rank_of_col[rk] = i;
-    evals[(int64_t)c * s + rk] = ei;
-    mean32[(int64_t)c * s + i] = (float)mean[(int64_t)c * s + i];
+    if (r < p) Z[i * p + r] += 1.0;
   }
   __syncthreads();
+  chol_qr(Z, s, p, G);
+  chol_qr(Z, s, p, G);
+  double* Qg = b.Q + (int64_t)c * s * p;
+  for (int t = threadIdx.x; t < s * p; t += blockDim.x) Qg[t] = Z[t];
+  if (threadIdx.x == 0) b.done[c] = 0;
+}
+
+// Top-D Ritz vectors -> FP32 basis with the sign convention; evals: the p Ritz
+// values then NaN; mean rounded to FP32.
+__global__ void k_pca_finalize(SiBufs b, const double* __restrict__ mean, int s, int p, int D,
+                               float* __restrict__ basis, float* __restrict__ mean32, double* __restrict__ evals,
+                               uint32_t* __restrict__ status) {
+  const int c = blockIdx.x;
+  const double* X = b.X + (int64_t)c * s * p;
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
+    mean32[(int64_t)c * s + i] = (float)mean[(int64_t)c * s + i];
+    evals[(int64_t)c * s + i] = i < p ? b.e[(int64_t)c * p + i] : __longlong_as_double(0x7ff8000000000000ll);
+  }
   for (int k = threadIdx.x; k < D; k += blockDim.x) {
-    int col = rank_of_col[k];
     int imax = 0;
     double vmax = -1.0;
     for (int i = 0; i < s; ++i) {
-      double x = fabs(v[(int64_t)i * ns + col]);
+      const double x = fabs(X[(int64_t)i * p + k]);
       if (x > vmax) {
         vmax = x;
         imax = i;
       }
     }
-    double sg = v[(int64_t)imax * ns + col] < 0.0 ? -1.0 : 1.0;
-    for (int i = 0; i < s; ++i) basis[((int64_t)c * s + i) * D + k] = (float)(sg * v[(int64_t)i * ns + col]);
+    const double sg = X[(int64_t)imax * p + k] < 0.0 ? -1.0 : 1.0;
+    for (int i = 0; i < s; ++i) basis[((int64_t)c * s + i) * D + k] = (float)(sg * X[(int64_t)i * p + k]);
   }
+  if (threadIdx.x == 0 && !b.done[c]) atomicOr(status, ST_NOCONV);
+}
+
+// ----------------------------------------------------------------------------
+// the same iteration in one launch per build: a thread-block cluster of kCS CTAs
+// per curve, A's rows split over the CTAs (in shared memory), partial p x p
+// products reduced through distributed shared memory in rank order (every CTA
+// ends with the same sums), the Q slices all-gathered the same way, hardware
+// cluster barriers between phases.  Rayleigh-Ritz and the convergence test run
+// every kRR-th iteration (the subspace converges at the same rate without it).
+// ----------------------------------------------------------------------------
+constexpr int kCS = 8;
+constexpr int kRR = 4;
+constexpr int kMaxIterCl = 64;
+
+// 1/sqrt(x) to FP64 accuracy from an FP32 seed (two Newton steps, FMAs only)
+__device__ inline double rsqrt64(double x) {
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  return y * fma(-0.5 * x, y * y, 1.5);
+}
+
+struct ClShm {
+  double* As;   // rp x s  (this CTA's rows of A)
+  double* Qf;   // s x p   (full Q)
+  double* Ys;   // rp x p
+  double* Zs;   // rp x p
+  double* part; // np x np (partial sums exchanged through DSMEM)
+  double* Hf;   // np x np
+  double* Wf;   // np x np
+  double* ev;   // np
+  double* al;   // np
+  double* be;   // np
+  int* ord;     // np
+};
+
+// every CTA: out[t] = sum over ranks (in order) of part[t], t < len
+__device__ void cl_allreduce(cg::cluster_group& cl, double* part, double* out, int len) {
+  cl.sync();
+  for (int t = threadIdx.x; t < len; t += blockDim.x) {
+    double acc = 0.0;
+    for (int rk = 0; rk < kCS; ++rk) acc += cl.map_shared_rank(part, rk)[t];
+    out[t] = acc;
+  }
+  cl.sync();
+}
+
+// Q rows [r0, r1) := orthonormal basis rows of the distributed block Z (rows
+// [r0, r1) here): Cholesky QR, the Gram matrix reduced over the cluster, the
+// factor computed redundantly (identically) in every CTA; then all-gather Q.
+__device__ void cl_cholqr(cg::cluster_group& cl, ClShm& m, int nr, int r0, int s, int p, int rp) {
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    const int a = t / p, b = t % p;
+    double acc = 0.0;
+    if (a <= b)
+      for (int i = 0; i < nr; ++i) acc = fma(m.Zs[i * p + a], m.Zs[i * p + b], acc);
+    m.part[t] = acc;
+  }
+  cl_allreduce(cl, m.part, m.Hf, p * p);
+  double* G = m.Hf;
+  if (threadIdx.x < 32) {
+    for (int k = 0; k < p; ++k) {
+      const double gkk = G[k * p + k];
+      const double y = gkk > 1e-30 ? rsqrt64(gkk) : 0.0;  // a null direction stays a zero column
+      __syncwarp();
+      if (threadIdx.x == 0) {
+        G[k * p + k] = y;  // store 1 / R_kk on the diagonal
+      }
+      for (int j = k + 1 + threadIdx.x; j < p; j += 32) G[k * p + j] *= y;
+      __syncwarp();
+      for (int t = threadIdx.x; t < p * p; t += 32) {
+        const int i = t / p, j = t % p;
+        if (i > k && j >= i) G[i * p + j] = fma(-G[k * p + i], G[k * p + j], G[i * p + j]);
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+    double z[kPMax];
+    for (int k = 0; k < p; ++k) z[k] = m.Zs[i * p + k];
+    for (int k = 0; k < p; ++k) {
+      double v = z[k];
+      for (int j = 0; j < k; ++j) v = fma(-z[j], G[j * p + k], v);
+      z[k] = v * G[k * p + k];
+    }
+    for (int k = 0; k < p; ++k) {
+      m.Zs[i * p + k] = z[k];
+      m.Qf[(r0 + i) * p + k] = z[k];
+    }
+  }
+  cl.sync();
+  const int me = (int)cl.block_rank();
+  for (int t = threadIdx.x; t < s * p; t += blockDim.x) {
+    const int rk = (t / p) / rp;
+    if (rk != me) m.Qf[t] = cl.map_shared_rank(m.Qf, rk)[t];
+  }
+  cl.sync();
+}
+
+__global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int D) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int c = blockIdx.x / kCS;
+  const int me = (int)cl.block_rank();
+  const int rp = (s + kCS - 1) / kCS;
+  const int r0 = me * rp < s ? me * rp : s;
+  const int r1 = r0 + rp < s ? r0 + rp : s;
+  const int nr = r1 - r0;
+  const int np = p + (p & 1);
+  extern __shared__ double sm[];
+  ClShm m;
+  m.As = sm;
+  m.Qf = m.As + rp * s;
+  m.Ys = m.Qf + s * p;
+  m.Zs = m.Ys + rp * p;
+  m.part = m.Zs + rp * p;
+  m.Hf = m.part + np * np;
+  m.Wf = m.Hf + np * np;
+  m.ev = m.Wf + np * np;
+  m.al = m.ev + np;
+  m.be = m.al + np;
+  m.ord = reinterpret_cast<int*>(m.be + np);
+  __shared__ double red[8];
+  const double* A = b.A + (int64_t)c * s * s;
+  for (int t = threadIdx.x; t < nr * s; t += blockDim.x) m.As[t] = A[(int64_t)r0 * s + t];
+  // start block rows: unit vectors of the p largest diagonal entries + perturbation
+  for (int t = threadIdx.x; t < nr * p; t += blockDim.x) {
+    const int i = r0 + t / p, k = t % p;
+    m.Zs[t] = 1e-3 * (double)(((i * 7 + k * 13) % 17) - 8) / 8.0;
+  }
+  __syncthreads();
+  for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    const double di = A[(int64_t)i * s + i];
+    int r = 0;
+    for (int j = 0; j < s; ++j) {
+      const double dj = A[(int64_t)j * s + j];
+      if (dj > di || (dj == di && j < i)) ++r;
+    }
+    if (r < p) m.Zs[(i - r0) * p + r] += 1.0;
+  }
+  __syncthreads();
+  cl_cholqr(cl, m, nr, r0, s, p, rp);
+  cl_cholqr(cl, m, nr, r0, s, p, rp);
+  bool conv = false;
+  for (int it = 0; it < kMaxIterCl && !conv; ++it) {
+    // Y = A Q (this CTA's rows)
+    for (int t = threadIdx.x; t < nr * p; t += blockDim.x) {
+      const int i = t / p, k = t % p;
+      const double* ar = m.As + i * s;
+      double acc = 0.0;
+      for (int j = 0; j < s; ++j) acc = fma(ar[j], m.Qf[j * p + k], acc);
+      m.Ys[t] = acc;
+    }
+    __syncthreads();
+    const bool rr = (it % kRR) == kRR - 1 || it == kMaxIterCl - 1;
+    if (rr) {
+      // H = Q^T A Q (upper triangle, mirrored), reduced over the cluster
+      for (int t = threadIdx.x; t < np * np; t += blockDim.x) {
+        const int a = t / np, bb = t % np;
+        double acc = 0.0;
+        if (a < p && bb < p && a <= bb)
+          for (int i = 0; i < nr; ++i) acc = fma(m.Qf[(r0 + i) * p + a], m.Ys[i * p + bb], acc);
+        m.part[t] = acc;
+      }
+      cl_allreduce(cl, m.part, m.Hf, np * np);
+      for (int t = threadIdx.x; t < np * np; t += blockDim.x) {
+        const int a = t / np, bb = t % np;
+        if (a > bb) m.Hf[t] = m.Hf[bb * np + a];
+      }
+      __syncthreads();
+      small_jacobi(m.Hf, m.Wf, np, m.al, m.be, red);
+      for (int k = threadIdx.x; k < p; k += blockDim.x) {
+        const double ek = m.Hf[k * np + k];
+        int r = 0;
+        for (int j = 0; j < p; ++j) {
+          const double ej = m.Hf[j * np + j];
+          if (ej > ek || (ej == ek && j < k)) ++r;
+        }
+        m.ord[r] = k;
+        m.ev[r] = ek;
+      }
+      __syncthreads();
+      // X = Q W, Z = Y W (this CTA's rows); residual partial sums for k < D
+      double* Xg = b.X + (int64_t)c * s * p;
+      for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+        double x[kPMax], z[kPMax];
+        for (int k = 0; k < p; ++k) {
+          const int col = m.ord[k];
+          double ax = 0.0, az = 0.0;
+          for (int j = 0; j < p; ++j) {
+            ax = fma(m.Qf[(r0 + i) * p + j], m.Wf[j * np + col], ax);
+            az = fma(m.Ys[i * p + j], m.Wf[j * np + col], az);
+          }
+          x[k] = ax;
+          z[k] = az;
+        }
+        for (int k = 0; k < p; ++k) {
+          Xg[(int64_t)(r0 + i) * p + k] = x[k];
+          m.Zs[i * p + k] = z[k];
+        }
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < np * np; t += blockDim.x) m.part[t] = 0.0;
+      __syncthreads();
+      for (int k = 0; k < D; ++k) {
+        double r2 = 0.0;
+        for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+          const double r = fma(-m.ev[k], Xg[(int64_t)(r0 + i) * p + k], m.Zs[i * p + k]);
+          r2 = fma(r, r, r2);
+        }
+        r2 = block_sum(r2, red);
+        if (threadIdx.x == 0) m.part[k] = r2;
+      }
+      cl_allreduce(cl, m.part, m.Hf, D);
+      double worst = 0.0;
+      for (int k = 0; k < D; ++k) worst = fmax(worst, m.Hf[k]);
+      conv = worst <= 1e-22 * m.ev[0] * m.ev[0];
+      if (conv || it == kMaxIterCl - 1) {
+        if (me == 0 && threadIdx.x < p) b.e[(int64_t)c * p + threadIdx.x] = m.ev[threadIdx.x];
+        if (me == 0 && threadIdx.x == 0) b.done[c] = conv ? 1 : 0;
+        break;
+      }
+    } else {
+      for (int t = threadIdx.x; t < nr * p; t += blockDim.x) m.Zs[t] = m.Ys[t];
+      __syncthreads();
+    }
+    cl_cholqr(cl, m, nr, r0, s, p, rp);
+    cl_cholqr(cl, m, nr, r0, s, p, rp);
+  }
+  cl.sync();  // no CTA leaves while others may still read its shared memory
+}
+
+size_t cluster_shm_bytes(int s, int p) {
+  const int rp = (s + kCS - 1) / kCS;
+  const int np = p + (p & 1);
+  return sizeof(double) * ((size_t)rp * s + (size_t)s * p + 2 * (size_t)rp * p + 3 * (size_t)np * np + 3 * np) +
+         sizeof(int) * np;
 }
 
 }  // namespace
@@ -299,64 +770,106 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
   const int64_t S = (ix.pca_sample <= 0 || ix.pca_sample >= N) ? N : ix.pca_sample;
   const int64_t step = (N + S - 1) / S;
   const int64_t cnt = (N + step - 1) / step;
-  const int ns = (s + 1) & ~1;
-  const int T = (s + kTile - 1) / kTile;
+  int p = 2 * D > D + 8 ? 2 * D : D + 8;
+  if (p > kPMax) p = kPMax;
+  if (p > s) p = s;
+  const int np = p + (p & 1);
+  const int n = ix.g.n;
+  const int T = (n + kTile - 1) / kTile;
   std::vector<int2> pairs_h;
   for (int i = 0; i < T; ++i)
     for (int j = i; j < T; ++j) pairs_h.push_back(make_int2(i, j));
   const int npairs = (int)pairs_h.size();
-  int nsplit = (int)((cnt + 1023) / 1024);
+  int nsplit = (int)((cnt + 511) / 512);
   if (nsplit > 64) nsplit = 64;
   if (nsplit < 1) nsplit = 1;
 
-  double *mean = nullptr, *partial = nullptr, *A0 = nullptr, *A1 = nullptr, *V = nullptr;
+  double *mean = nullptr, *mean_c = nullptr, *msum = nullptr, *partial = nullptr, *M = nullptr;
   int2* pairs = nullptr;
-  int* done = nullptr;
-  SFC_TRY(cudaMallocAsync(&mean, sizeof(double) * C * s, st));
-  SFC_TRY(cudaMallocAsync(&partial, sizeof(double) * C * nsplit * npairs * kTile * kTile, st));
-  SFC_TRY(cudaMallocAsync(&A0, sizeof(double) * C * ns * ns, st));
-  SFC_TRY(cudaMallocAsync(&A1, sizeof(double) * C * ns * ns, st));
-  SFC_TRY(cudaMallocAsync(&V, sizeof(double) * C * ns * ns, st));
+  SiBufs b;
+  SFC_TRY(cudaMallocAsync(&mean, sizeof(double) * n, st));
+  SFC_TRY(cudaMallocAsync(&mean_c, sizeof(double) * C * s, st));
+  SFC_TRY(cudaMallocAsync(&msum, sizeof(double) * nsplit * n, st));
+  SFC_TRY(cudaMallocAsync(&partial, sizeof(double) * nsplit * npairs * kTile * kTile, st));
+  SFC_TRY(cudaMallocAsync(&M, sizeof(double) * n * n, st));
   SFC_TRY(cudaMallocAsync(&pairs, sizeof(int2) * npairs, st));
-  SFC_TRY(cudaMallocAsync(&done, sizeof(int) * C, st));
+  SFC_TRY(cudaMallocAsync(&b.A, sizeof(double) * C * s * s, st));
+  SFC_TRY(cudaMallocAsync(&b.Q, sizeof(double) * C * s * p, st));
+  SFC_TRY(cudaMallocAsync(&b.Y, sizeof(double) * C * s * p, st));
+  SFC_TRY(cudaMallocAsync(&b.X, sizeof(double) * C * s * p, st));
+  SFC_TRY(cudaMallocAsync(&b.e, sizeof(double) * C * p, st));
+  SFC_TRY(cudaMallocAsync(&b.done, sizeof(int) * C, st));
   SFC_TRY(cudaMemcpyAsync(pairs, pairs_h.data(), sizeof(int2) * npairs, cudaMemcpyHostToDevice, st));
-  SFC_TRY(cudaMemsetAsync(done, 0, sizeof(int) * C, st));
 
   count_launch();
-  k_mean<<<dim3((s + 31) / 32, C), 256, 0, st>>>(grid, ix.dict, step, cnt, ix.sub_eoff, s, ix.g.ch, mean);
+  k_mean_partial<<<dim3((n + 127) / 128, nsplit), 128, 0, st>>>(grid, ix.dict, step, cnt, ix.eoff_all, n, ix.g.ch,
+                                                                  nsplit, msum);
   count_launch();
-  k_cov_partial<<<dim3(npairs, nsplit, C), 256, 0, st>>>(grid, ix.dict, step, cnt, ix.sub_eoff, mean, s, ix.g.ch,
-                                                          nsplit, pairs, npairs, partial);
+  k_mean_reduce<<<(n + 127) / 128, 128, 0, st>>>(msum, n, nsplit, cnt, mean);
   count_launch();
-  k_cov_reduce<<<dim3(64, C), 256, 0, st>>>(partial, nsplit, pairs, npairs, cnt, s, ns, A0, V);
+  k_cov_partial<<<dim3(npairs, nsplit), 256, 0, st>>>(grid, ix.dict, step, cnt, ix.eoff_all, n, ix.g.ch, nsplit,
+                                                      pairs, npairs, partial);
+  count_launch();
+  k_cov_reduce<<<128, 256, 0, st>>>(partial, nsplit, npairs, n, M);
+  count_launch();
+  k_cov_extract<<<dim3(64, C), 256, 0, st>>>(M, mean, n, ix.g.ch, cnt, ix.sub_pix, ix.m, s, b.A, mean_c);
   SFC_TRY(cudaGetLastError());
 
-  const size_t shm = sizeof(double) * 2 * ns + sizeof(int) * ns;
-  int ctas = 152 / C;
-  if (ctas < 4) ctas = 4;
-  double *Ain = A0, *Aout = A1;
-  for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
-    for (int r = 0; r < ns - 1; ++r) {
-      count_launch();
-      k_jacobi_round<<<dim3(ctas, C), 256, shm, st>>>(Ain, Aout, V, ns, r, done);
-      double* t = Ain;
-      Ain = Aout;
-      Aout = t;
-    }
+  const size_t shm_init = sizeof(double) * ((size_t)s * p + (size_t)p * p);
+  const size_t shm_small = sizeof(double) * (2 * (size_t)s * p + 2 * (size_t)np * np + 3 * np) + sizeof(int) * np;
+  const size_t shm_gemm = sizeof(double) * (size_t)s * p;
+  if (shm_init > 48 * 1024)
+    SFC_TRY(cudaFuncSetAttribute(k_si_init, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_init));
+  if (shm_small > 48 * 1024)
+    SFC_TRY(cudaFuncSetAttribute(k_si_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_small));
+  if (shm_gemm > 48 * 1024)
+    SFC_TRY(cudaFuncSetAttribute(k_si_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_gemm));
+  const size_t shm_cl = cluster_shm_bytes(s, p);
+  if (shm_cl <= 200 * 1024) {
+    SFC_TRY(cudaFuncSetAttribute(k_si_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_cl));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C * kCS);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = shm_cl;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kCS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     count_launch();
-    k_jacobi_check<<<C, 256, 0, st>>>(Ain, ns, done);
+    SFC_TRY(cudaLaunchKernelEx(&cfg, k_si_cluster, b, s, p, D));
+  } else {
+    count_launch();
+    k_si_init<<<C, 256, shm_init, st>>>(b, s, p);
+  int gx = (s * p + 255) / 256;
+  const int per_curve = 152 / C > 0 ? 152 / C : 1;
+  if (gx > per_curve) gx = per_curve;
+    for (int it = 0; it < kMaxIter; ++it) {
+      count_launch();
+      k_si_gemm<<<dim3(gx, C), 256, shm_gemm, st>>>(b, s, p);
+      count_launch();
+      k_si_small<<<C, 256, shm_small, st>>>(b, s, p, D);
+    }
   }
   SFC_TRY(cudaGetLastError());
   count_launch();
-  k_pca_finalize<<<C, 256, sizeof(int) * s, st>>>(Ain, V, mean, s, ns, D, ix.basis, ix.mean, ix.evals);
+  k_pca_finalize<<<C, 256, 0, st>>>(b, mean_c, s, p, D, ix.basis, ix.mean, ix.evals, status_word());
   SFC_TRY(cudaGetLastError());
   cudaFreeAsync(mean, st);
+  cudaFreeAsync(mean_c, st);
+  cudaFreeAsync(msum, st);
+  cudaFreeAsync(M, st);
   cudaFreeAsync(partial, st);
-  cudaFreeAsync(A0, st);
-  cudaFreeAsync(A1, st);
-  cudaFreeAsync(V, st);
   cudaFreeAsync(pairs, st);
-  cudaFreeAsync(done, st);
+  cudaFreeAsync(b.A, st);
+  cudaFreeAsync(b.Q, st);
+  cudaFreeAsync(b.Y, st);
+  cudaFreeAsync(b.X, st);
+  cudaFreeAsync(b.e, st);
+  cudaFreeAsync(b.done, st);
   return SFC_OK;
 }
 

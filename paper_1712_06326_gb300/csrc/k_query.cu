@@ -13,9 +13,10 @@
 //  5. filter-and-refine (Fig. 1(d)): FP32 masked-L2 cost of every candidate, one
 //     warp per candidate, each lane holding its patch elements' known flag,
 //     target value and grid offset in registers, gathered reads of the source
-//     patch rows, warp-shuffle sum; block minimum; every candidate inside the
-//     FP32 error band is rescored with the exact FP64 sequential cost; argmin
-//     over (cost, id).
+//     patch rows, warp-shuffle sum; block minimum; a single candidate inside
+//     the FP32 error band is the exact argmin, several (near-ties) are rescored
+//     with the exact FP64 sequential cost and the argmin over (cost, id) taken.
+//     The reported cost is the FP32 cost of the pick.
 #include "internal.cuh"
 
 namespace sfc {
@@ -308,40 +309,60 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   __syncthreads();
   float m32 = s_redf[0];
   for (int w = 1; w < kQWarps; ++w) m32 = fminf(m32, s_redf[w]);
-  const double T = band_limit(m32, n);
-  // --- FP64 band rescore, argmin over (cost, id) ------------------------------
+  const float T = band_limit32(m32, n);
+  // --- band: a single member is the exact argmin; otherwise rescore in FP64 ---
+  int nband = 0, mine = -1;
+  for (int ci = tid; ci < ncand; ci += kQThreads)
+    if (c32[ci] <= T) {
+      ++nband;
+      mine = ci;
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nband += __shfl_xor_sync(0xffffffffu, nband, o);
+  if (lane == 0) s_part[warp] = (uint32_t)nband;
+  __syncthreads();
+  int total = 0;
+  for (int w = 0; w < kQWarps; ++w) total += (int)s_part[w];
+  if (total == 1) {
+    if (mine >= 0) {
+      a.pick[q] = ucand[mine];
+      a.cost[q] = c32[mine];
+    }
+    return;
+  }
   double bc = INFINITY;
-  int64_t bj = INT64_MAX;
+  int64_t bi = INT64_MAX;  // candidate slot; slots are in ascending id order
   for (int ci = tid; ci < ncand; ci += kQThreads) {
-    if ((double)c32[ci] <= T) {
+    if (c32[ci] <= T) {
       const uint32_t j = ucand[ci];
-      double c64 = exact_cost64(a.grid, (int64_t)a.dict[j] * ch, tv, tm, eo, P, ch, a.weights);
-      if (c64 < bc || (c64 == bc && (int64_t)j < bj)) {
+      const double c64 = exact_cost64(a.grid, (int64_t)a.dict[j] * ch, tv, tm, eo, P, ch, a.weights);
+      if (c64 < bc || (c64 == bc && ci < bi)) {
         bc = c64;
-        bj = j;
+        bi = ci;
       }
     }
   }
-  warp_argmin64(bc, bj);
+  warp_argmin64(bc, bi);
+  __syncthreads();
   if (lane == 0) {
     s_redd[warp] = bc;
-    s_redi[warp] = bj;
+    s_redi[warp] = bi;
   }
   __syncthreads();
   if (tid == 0) {
     double c = s_redd[0];
-    int64_t j = s_redi[0];
+    int64_t i = s_redi[0];
     for (int w = 1; w < kQWarps; ++w)
-      if (s_redd[w] < c || (s_redd[w] == c && s_redi[w] < j)) {
+      if (s_redd[w] < c || (s_redd[w] == c && s_redi[w] < i)) {
         c = s_redd[w];
-        j = s_redi[w];
+        i = s_redi[w];
       }
-    if (ncand == 0) {
+    if (ncand == 0 || i == INT64_MAX) {
       a.pick[q] = -1;
       a.cost[q] = __int_as_float(0x7fc00000);
     } else {
-      a.pick[q] = j;
-      a.cost[q] = (float)c;
+      a.pick[q] = ucand[i];
+      a.cost[q] = c32[i];
     }
   }
 }

@@ -555,6 +555,14 @@ int sfc_status(void* stream) {
     set_error("a bounded device-side wait timed out");
     return SFC_ETIMEOUT;
   }
+  if (v & ST_NOCONV) {
+    set_error("a PCA eigen-solve stopped before its residual test passed (basis less accurate)");
+    return SFC_EDEVICE;
+  }
+  if (v & ST_OVERFLOW) {
+    set_error("the fill loop stopped: a step filled no pixel");
+    return SFC_EDEVICE;
+  }
   if (v & ST_BAD_CENTRE) {
     set_error("a query centre lies outside the valid centre range");
     return SFC_EDEVICE;

@@ -2,8 +2,8 @@
 
 Bars: dictionary ids, subsets, projections (FP32 chain), lo/scale, keys, sorted
 orders, query keys, positions and candidate sets bit-exact; picks equal; the
-reported cost is the exact FP64 cost rounded to FP32, so bit-exact as well; the
-PCA basis (a different summation order and Jacobi ordering) within the FP64
+reported cost (the FP32 cost of the pick) within COST_RTOL of the oracle's exact
+FP64 cost; the PCA basis (another summation order and eigen-solver) within the
 tolerances stated below; the fill loop's log and output bit-identical.
 """
 import numpy as np
@@ -14,6 +14,15 @@ import oracle as O
 from paper_1712_06326_gb300 import synth
 
 pytestmark = pytest.mark.gpu
+
+# FP32 cost vs exact cost: the target's bar (1e-5 relative); zero stays zero
+COST_RTOL = 1e-5
+
+
+def cost_close(gpu, exact):
+    gpu = np.asarray(gpu, np.float64)
+    exact = np.asarray(exact, np.float64)
+    return np.all(np.abs(gpu - exact) <= COST_RTOL * np.abs(exact)) and np.all((gpu == 0) == (exact == 0))
 
 
 @pytest.fixture(scope="module")
@@ -52,7 +61,7 @@ def check_fullscan(S, g, m_dict, m_cur, t, K, w=None):
     d = O.dict_extract(m_dict, K)
     op, oc = O.fullscan(g, m_cur, K, d, O.centres_to_lin(t, ext_of(g)), w)
     assert np.array_equal(fp.cpu().numpy(), op)
-    assert np.array_equal(fc.cpu().numpy(), oc.astype(np.float32))
+    assert cost_close(fc.cpu().numpy(), oc)
     return op
 
 
@@ -121,6 +130,7 @@ def rgb_index(S):
     ix = S.sfc_index_build(dev(g), dev(m), K=K, curves=C_, dims=D, bits=bits, window=16, pca_sample=0,
                            keep_intermediates=1)
     ex = S.sfc_index_export(ix, proj=True)
+    assert S.sfc_status() == 0  # the eigen-solve converged on every index
     return dict(g=g, m=m, K=K, C=C_, D=D, bits=bits, ix=ix, ex=ex)
 
 
@@ -137,8 +147,9 @@ def test_index_pca_basis_close_to_oracle(rgb_index):
     for cv in range(r["C"]):
         B, mu, ev, cov = O.pca(r["g"], r["K"], d, ex["subsets"][cv], 0, r["D"])
         # eigenvalues: FP64 throughout, different summation/rotation order
-        assert np.allclose(ex["evals"][cv], ev, rtol=1e-9, atol=1e-12 * ev[0])
-        assert np.allclose(ex["mean"][cv], mu, rtol=0, atol=0)
+        D = r["D"]
+        assert np.allclose(ex["evals"][cv][:D], ev[:D], rtol=1e-9, atol=1e-12 * ev[0])
+        assert np.all(np.abs(ex["mean"][cv] - mu) <= np.spacing(np.abs(mu)))
         # eigenvectors with an eigen-gap: same direction and canonical sign
         gaps = np.minimum(np.abs(np.diff(ev[: r["D"] + 1])), np.r_[np.inf, np.abs(np.diff(ev[: r["D"]]))])
         for k in range(r["D"]):
@@ -166,7 +177,7 @@ def test_index_shifted_curves_and_sampled_pca(S):
     ex = S.sfc_index_export(ix, proj=True)
     d = ex["dict"]
     B, mu, ev, _ = O.pca(g, K, d, ex["subsets"][0], 500, D)
-    assert np.allclose(ex["evals"][0], ev, rtol=1e-9, atol=1e-12 * ev[0])
+    assert np.allclose(ex["evals"][0][:D], ev[:D], rtol=1e-9, atol=1e-12 * ev[0])
     oix = O.build_index(g, m, K, C_, D, bits, shifts=sh, basis=ex["basis"], mean=ex["mean"])
     assert np.array_equal(oix["keys"], ex["keys"])
     assert np.array_equal(oix["skeys"], ex["skeys"]) and np.array_equal(oix["sids"], ex["sids"])
@@ -199,7 +210,7 @@ def test_index_3d_truncated_keys(S):
     c = c.cpu().numpy()
     for i in range(len(t)):
         rr = O.query(oix, g, m, lin[i], 12)
-        assert p[i] == rr["pick"] and c[i] == np.float32(rr["cost"])
+        assert p[i] == rr["pick"] and cost_close(c[i], rr["cost"])
     ix.close()
 
 
@@ -231,7 +242,7 @@ def test_query_candidates_and_picks(S, rgb_index, select):
             assert np.array_equal(pos[i], rr["pos"])
             assert nc[i] == len(rr["cand"]) and np.array_equal(cand[i, : nc[i]], rr["cand"])
             assert np.all(cand[i, nc[i]:] == -1)
-            assert pk[i] == rr["pick"] and cs[i] == np.float32(rr["cost"])
+            assert pk[i] == rr["pick"] and cost_close(cs[i], rr["cost"])
     ix.close()
 
 
@@ -243,7 +254,40 @@ def test_query_window_covering_dictionary_equals_fullscan(S):
     t = synth.front_targets(m, K, cap=50, cfg=2)
     pk, cs = S.sfc_query_batch(ix, dev(g), dev(m), dev(t))
     fp, fc = S.fullscan_query_batch(dev(g), dev(m), dev(m), dev(t), K=K)
-    assert torch.equal(pk, fp) and torch.equal(cs, fc)
+    assert torch.equal(pk, fp) and cost_close(cs.cpu().numpy(), fc.cpu().numpy())
+    ix.close()
+
+
+def test_query_exact_ties_and_constant_grid(S):
+    # several exact duplicates in the window: the FP64 band pass must return the
+    # lowest id; a constant grid ties every candidate at cost 0
+    rng = np.random.default_rng(9)
+    g = rng.random((40, 40, 1)).astype(np.float32)
+    for (y, x) in [(30, 30), (20, 2), (2, 30)]:
+        g[y:y + 5, x:x + 5] = g[3:8, 3:8]
+    m = np.ones((40, 40), np.uint8)
+    N = len(O.dict_extract(m, 5))
+    ix = S.sfc_index_build(dev(g), dev(m), K=5, curves=2, dims=3, bits=8, window=N, pca_sample=0)
+    S.sfc_status()  # white-noise data has no eigen-gap: a PCA cap warning is expected here
+    t = np.array([[32, 32], [4, 22], [5, 5], [20, 20]], np.int32)
+    pk, cs = S.sfc_query_batch(ix, dev(g), dev(m), dev(t))
+    d = O.dict_extract(m, 5)
+    pk = pk.cpu().numpy()
+    # copies centred at (5,5), (32,32), (4,22), (32,4): the last has the lowest
+    # raster rank (row 4), so it is the pick for all three duplicate targets
+    assert all(d[pk[i]] == 4 * 40 + 32 for i in range(3))
+    op, oc = O.fullscan(g, m, 5, d, O.centres_to_lin(t, ext_of(g)))
+    assert np.array_equal(pk, op) and cost_close(cs.cpu().numpy(), oc)
+    ix.close()
+    gc = np.full((24, 24, 3), 0.5, np.float32)
+    mc = np.ones((24, 24), np.uint8)
+    ix = S.sfc_index_build(dev(gc), dev(mc), K=3, curves=4, dims=2, bits=4, window=16, pca_sample=0)
+    pk, cs = S.sfc_query_batch(ix, dev(gc), dev(mc), dev(np.array([[10, 10], [1, 1]], np.int32)))
+    ex = S.sfc_index_export(ix)
+    oq = oracle_ix(ex, gc, 3, 4, 2, 4)
+    for i, c in enumerate([(10, 10), (1, 1)]):
+        rr = O.query(oq, gc, mc, c[1] * 24 + c[0], 16)
+        assert pk[i].item() == rr["pick"] and cs[i].item() == 0.0
     ix.close()
 
 
@@ -314,6 +358,7 @@ def big(S):
     ix = S.sfc_index_build(gd, md, K=11, curves=8, dims=8, bits=16, window=64, pca_sample=16384,
                            keep_intermediates=1)
     ex = S.sfc_index_export(ix, proj=True)
+    assert S.sfc_status() == 0
     return dict(g=g, m=m, t=t, gd=gd, md=md, td=td, ix=ix, ex=ex)
 
 
@@ -346,7 +391,7 @@ def test_big_sampled_queries_match_oracle(S, big):
     rng = np.random.default_rng(1)
     for i in np.r_[0, len(t) - 1, rng.choice(len(t), 62, replace=False)]:
         rr = O.query(oq, g, m, lin[i], 64)
-        assert pk[i] == rr["pick"] and cs[i] == np.float32(rr["cost"])
+        assert pk[i] == rr["pick"] and cost_close(cs[i], rr["cost"])
 
 
 def test_big_sampled_fullscan_match_oracle(S, big):
@@ -355,4 +400,4 @@ def test_big_sampled_fullscan_match_oracle(S, big):
     sel = np.sort(rng.choice(len(t), 12, replace=False))
     fp, fc = S.fullscan_query_batch(big["gd"], big["md"], big["md"], dev(t[sel]), K=11)
     op, oc = O.fullscan(g, m, 11, big["ex"]["dict"], O.centres_to_lin(t[sel], ext_of(g)))
-    assert np.array_equal(fp.cpu().numpy(), op) and np.array_equal(fc.cpu().numpy(), oc.astype(np.float32))
+    assert np.array_equal(fp.cpu().numpy(), op) and cost_close(fc.cpu().numpy(), oc)

@@ -58,6 +58,7 @@ def test_static_scratch_full_scan_matches_allocating_entry_point(S):
     w2 = np.array([1.0, 2.0, 0.5], np.float32)
     # two calls in a row on different grids, then the first again
     cases = [(g1, m1, t1, 9, None), (g2, m2, t2, 7, w2), (g1, m1, t1, 9, None)]
+    S.sfc_status()  # the status word is process-wide: drop flags left by earlier calls
     for g, m, t, K, w in cases:
         sp, sc = _call_static(S, g, m, t, K, w)
         rp, rc = S.fullscan_query_batch(torch.from_numpy(g).cuda(), torch.from_numpy(m).cuda(),
