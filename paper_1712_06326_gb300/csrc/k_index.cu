@@ -3,8 +3,8 @@
 //
 // Projection: y_k = chain of FP32 fused multiply-adds over the index's subset
 // values in subset order, acc = fma(B[i][k], x_i - mu_i, acc) starting at +0 with
-// x_i - mu_i rounded to FP32 (one thread per (entry, index), the D chains of a
-// thread interleaved).  The per-axis minimum and maximum over the dictionary are
+// x_i - mu_i rounded to FP32 (a thread runs the D chains of 4 entries of one
+// index, interleaved).  The per-axis minimum and maximum over the dictionary are
 // exact reductions (order-independent).  Quantisation: q = clamp(floor((y - lo)
 // * scale), 0, 2^b - 1) with scale = (float)(2^b / ((double)hi - (double)lo)) (0
 // if hi == lo), then q + shift.  Key: bits interleaved highest plane first,
@@ -28,6 +28,8 @@ __device__ inline float float_of(uint32_t u) {
   return __uint_as_float(b);
 }
 
+constexpr int kPE = 4;  // dictionary entries per thread (they share the basis reads)
+
 template <int D>
 __global__ void __launch_bounds__(256) k_project(const float* __restrict__ grid, const uint32_t* __restrict__ dict,
                                                  int64_t N, int ch, int s, const int* __restrict__ sub_eoff,
@@ -43,33 +45,59 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ grid,
     mu[t] = mean[(int64_t)c * s + t];
     eo[t] = sub_eoff[(int64_t)c * s + t];
   }
-  __syncthreads();
   __shared__ uint32_t smin[D], smax[D];
   if (threadIdx.x < D) {
     smin[threadIdx.x] = 0xffffffffu;
     smax[threadIdx.x] = 0u;
   }
   __syncthreads();
-  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  float acc[D];
+  // entries j0 + q * 256, q < kPE: for every subset value the warp's loads of one
+  // q are 32 consecutive centres (coalesced), and one basis row serves kPE chains
+  const int64_t j0 = (int64_t)blockIdx.x * blockDim.x * kPE + threadIdx.x;
+  int64_t base[kPE];
+  bool ok[kPE];
 #pragma unroll
-  for (int k = 0; k < D; ++k) acc[k] = 0.0f;
-  if (j < N) {
-    const int64_t base = (int64_t)dict[j] * ch;
-    for (int i = 0; i < s; ++i) {
-      float xc = __fsub_rn(grid[base + eo[i]], mu[i]);
-#pragma unroll
-      for (int k = 0; k < D; ++k) acc[k] = __fmaf_rn(B[i * D + k], xc, acc[k]);
-    }
-    float* out = proj + ((int64_t)c * N + j) * D;
-#pragma unroll
-    for (int k = 0; k < D; ++k) out[k] = acc[k];
+  for (int q = 0; q < kPE; ++q) {
+    const int64_t j = j0 + (int64_t)q * blockDim.x;
+    ok[q] = j < N;
+    base[q] = ok[q] ? (int64_t)dict[j] * ch : 0;
   }
+  float acc[kPE][D];
+#pragma unroll
+  for (int q = 0; q < kPE; ++q)
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc[q][k] = 0.0f;
+  for (int i = 0; i < s; ++i) {
+    const int o = eo[i];
+    const float m = mu[i];
+    float xc[kPE];
+#pragma unroll
+    for (int q = 0; q < kPE; ++q) xc[q] = __fsub_rn(ok[q] ? grid[base[q] + o] : 0.0f, m);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const float b = B[i * D + k];
+#pragma unroll
+      for (int q = 0; q < kPE; ++q) acc[q][k] = __fmaf_rn(b, xc[q], acc[q][k]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kPE; ++q)
+    if (ok[q]) {
+      float* out = proj + ((int64_t)c * N + j0 + (int64_t)q * blockDim.x) * D;
+#pragma unroll
+      for (int k = 0; k < D; ++k) out[k] = acc[q][k];
+    }
   // per-axis min / max: warp reduce, then shared, then one global atomic per axis
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    uint32_t u = j < N ? ord_of(acc[k]) : 0xffffffffu;
-    uint32_t v = j < N ? ord_of(acc[k]) : 0u;
+    uint32_t u = 0xffffffffu, v = 0u;
+#pragma unroll
+    for (int q = 0; q < kPE; ++q)
+      if (ok[q]) {
+        const uint32_t w = ord_of(acc[q][k]);
+        u = min(u, w);
+        v = max(v, w);
+      }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       u = min(u, __shfl_xor_sync(0xffffffffu, u, o));
@@ -126,7 +154,7 @@ template <int D>
 int launch_project(const Index& ix, const float* grid, float* proj, uint32_t* lohi, cudaStream_t st) {
   const size_t shm = sizeof(float) * (ix.s * D + ix.s) + sizeof(int) * ix.s;
   if (shm > 48 * 1024) SFC_TRY(cudaFuncSetAttribute(k_project<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-  dim3 grd((unsigned)((ix.N + 255) / 256), ix.C);
+  dim3 grd((unsigned)((ix.N + 256 * kPE - 1) / (256 * kPE)), ix.C);
   count_launch();
   k_project<D><<<grd, 256, shm, st>>>(grid, ix.dict, ix.N, ix.g.ch, ix.s, ix.sub_eoff, ix.basis, ix.mean, proj, lohi);
   SFC_TRY(cudaGetLastError());

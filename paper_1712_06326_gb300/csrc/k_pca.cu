@@ -26,8 +26,8 @@
 //     every k < D;  else Q = orthonormal basis of Z (Cholesky QR, twice).
 // The start block holds the unit vectors of the p largest diagonal entries of A
 // plus a small deterministic perturbation.  When A's row slices fit in shared
-// memory (s up to ~440), the whole iteration runs in one launch on a cluster of
-// 8 CTAs per curve (see k_si_cluster); otherwise one launch per iteration
+// memory, the whole iteration runs in one launch on a cluster of 16 CTAs per
+// curve (8 where 16-CTA clusters cannot be scheduled; see k_si_cluster); otherwise one launch per iteration
 // computes Y = A Q with every curve's rows spread over the GPU and a second (one
 // CTA per curve) does the p-sized work, a device-side flag ending the iteration
 // early.  A curve that has not converged within the iteration cap raises
@@ -526,14 +526,13 @@ __global__ void k_pca_finalize(SiBufs b, const double* __restrict__ mean, int s,
 }
 
 // ----------------------------------------------------------------------------
-// the same iteration in one launch per build: a thread-block cluster of kCS CTAs
+// the same iteration in one launch per build: a thread-block cluster of CS CTAs
 // per curve, A's rows split over the CTAs (in shared memory), partial p x p
 // products reduced through distributed shared memory in rank order (every CTA
 // ends with the same sums), the Q slices all-gathered the same way, hardware
 // cluster barriers between phases.  Rayleigh-Ritz and the convergence test run
 // every kRR-th iteration (the subspace converges at the same rate without it).
 // ----------------------------------------------------------------------------
-constexpr int kCS = 8;
 constexpr int kRR = 4;
 constexpr int kMaxIterCl = 64;
 
@@ -560,11 +559,12 @@ struct ClShm {
 };
 
 // every CTA: out[t] = sum over ranks (in order) of part[t], t < len
+template <int CS>
 __device__ void cl_allreduce(cg::cluster_group& cl, double* part, double* out, int len) {
   cl.sync();
   for (int t = threadIdx.x; t < len; t += blockDim.x) {
     double acc = 0.0;
-    for (int rk = 0; rk < kCS; ++rk) acc += cl.map_shared_rank(part, rk)[t];
+    for (int rk = 0; rk < CS; ++rk) acc += cl.map_shared_rank(part, rk)[t];
     out[t] = acc;
   }
   cl.sync();
@@ -573,6 +573,7 @@ __device__ void cl_allreduce(cg::cluster_group& cl, double* part, double* out, i
 // Q rows [r0, r1) := orthonormal basis rows of the distributed block Z (rows
 // [r0, r1) here): Cholesky QR, the Gram matrix reduced over the cluster, the
 // factor computed redundantly (identically) in every CTA; then all-gather Q.
+template <int CS>
 __device__ void cl_cholqr(cg::cluster_group& cl, ClShm& m, int nr, int r0, int s, int p, int rp) {
   for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
     const int a = t / p, b = t % p;
@@ -581,7 +582,7 @@ __device__ void cl_cholqr(cg::cluster_group& cl, ClShm& m, int nr, int r0, int s
       for (int i = 0; i < nr; ++i) acc = fma(m.Zs[i * p + a], m.Zs[i * p + b], acc);
     m.part[t] = acc;
   }
-  cl_allreduce(cl, m.part, m.Hf, p * p);
+  cl_allreduce<CS>(cl, m.part, m.Hf, p * p);
   double* G = m.Hf;
   if (threadIdx.x < 32) {
     for (int k = 0; k < p; ++k) {
@@ -623,11 +624,12 @@ __device__ void cl_cholqr(cg::cluster_group& cl, ClShm& m, int nr, int r0, int s
   cl.sync();
 }
 
+template <int CS>
 __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int D) {
   cg::cluster_group cl = cg::this_cluster();
-  const int c = blockIdx.x / kCS;
+  const int c = blockIdx.x / CS;
   const int me = (int)cl.block_rank();
-  const int rp = (s + kCS - 1) / kCS;
+  const int rp = (s + CS - 1) / CS;
   const int r0 = me * rp < s ? me * rp : s;
   const int r1 = r0 + rp < s ? r0 + rp : s;
   const int nr = r1 - r0;
@@ -664,8 +666,8 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
     if (r < p) m.Zs[(i - r0) * p + r] += 1.0;
   }
   __syncthreads();
-  cl_cholqr(cl, m, nr, r0, s, p, rp);
-  cl_cholqr(cl, m, nr, r0, s, p, rp);
+  cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
+  cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
   bool conv = false;
   for (int it = 0; it < kMaxIterCl && !conv; ++it) {
     // Y = A Q (this CTA's rows)
@@ -687,7 +689,7 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
           for (int i = 0; i < nr; ++i) acc = fma(m.Qf[(r0 + i) * p + a], m.Ys[i * p + bb], acc);
         m.part[t] = acc;
       }
-      cl_allreduce(cl, m.part, m.Hf, np * np);
+      cl_allreduce<CS>(cl, m.part, m.Hf, np * np);
       for (int t = threadIdx.x; t < np * np; t += blockDim.x) {
         const int a = t / np, bb = t % np;
         if (a > bb) m.Hf[t] = m.Hf[bb * np + a];
@@ -736,7 +738,7 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
         r2 = block_sum(r2, red);
         if (threadIdx.x == 0) m.part[k] = r2;
       }
-      cl_allreduce(cl, m.part, m.Hf, D);
+      cl_allreduce<CS>(cl, m.part, m.Hf, D);
       double worst = 0.0;
       for (int k = 0; k < D; ++k) worst = fmax(worst, m.Hf[k]);
       conv = worst <= 1e-22 * m.ev[0] * m.ev[0];
@@ -749,14 +751,16 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
       for (int t = threadIdx.x; t < nr * p; t += blockDim.x) m.Zs[t] = m.Ys[t];
       __syncthreads();
     }
-    cl_cholqr(cl, m, nr, r0, s, p, rp);
-    cl_cholqr(cl, m, nr, r0, s, p, rp);
+    // two passes while the block is far from the eigen-directions; afterwards
+    // Z = A Q has nearly orthogonal columns and one pass is accurate to rounding
+    cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
+    if (it < 3) cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
   }
   cl.sync();  // no CTA leaves while others may still read its shared memory
 }
 
-size_t cluster_shm_bytes(int s, int p) {
-  const int rp = (s + kCS - 1) / kCS;
+size_t cluster_shm_bytes(int s, int p, int CS) {
+  const int rp = (s + CS - 1) / CS;
   const int np = p + (p & 1);
   return sizeof(double) * ((size_t)rp * s + (size_t)s * p + 2 * (size_t)rp * p + 3 * (size_t)np * np + 3 * np) +
          sizeof(int) * np;
@@ -824,23 +828,56 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
     SFC_TRY(cudaFuncSetAttribute(k_si_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_small));
   if (shm_gemm > 48 * 1024)
     SFC_TRY(cudaFuncSetAttribute(k_si_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_gemm));
-  const size_t shm_cl = cluster_shm_bytes(s, p);
-  if (shm_cl <= 200 * 1024) {
-    SFC_TRY(cudaFuncSetAttribute(k_si_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_cl));
+  // cluster path: 16 CTAs per curve when such clusters can be scheduled, else 8
+  int cs = 0;
+  size_t shm_cl = 0;
+  for (int cand : {16, 8}) {
+    const size_t need = cluster_shm_bytes(s, p, cand);
+    if (need > 200 * 1024) continue;
+    const void* fn = cand == 16 ? (const void*)k_si_cluster<16> : (const void*)k_si_cluster<8>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need) != cudaSuccess) continue;
+    if (cand == 16 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t q = {};
+    q.gridDim = dim3(C * cand);
+    q.blockDim = dim3(256);
+    q.dynamicSmemBytes = need;
+    cudaLaunchAttribute qa[1];
+    qa[0].id = cudaLaunchAttributeClusterDimension;
+    qa[0].val.clusterDim.x = cand;
+    qa[0].val.clusterDim.y = 1;
+    qa[0].val.clusterDim.z = 1;
+    q.attrs = qa;
+    q.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &q) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    cs = cand;
+    shm_cl = need;
+    break;
+  }
+  if (cs) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(C * kCS);
+    cfg.gridDim = dim3(C * cs);
     cfg.blockDim = dim3(256);
     cfg.dynamicSmemBytes = shm_cl;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kCS;
+    attr[0].val.clusterDim.x = cs;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     count_launch();
-    SFC_TRY(cudaLaunchKernelEx(&cfg, k_si_cluster, b, s, p, D));
+    if (cs == 16)
+      SFC_TRY(cudaLaunchKernelEx(&cfg, k_si_cluster<16>, b, s, p, D));
+    else
+      SFC_TRY(cudaLaunchKernelEx(&cfg, k_si_cluster<8>, b, s, p, D));
   } else {
     count_launch();
     k_si_init<<<C, 256, shm_init, st>>>(b, s, p);
