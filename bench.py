@@ -35,6 +35,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(width=1024, K=11, curves=8, dims=8, bits=16, window=64, pca_sample=16384, cap=65536)
+# DRAM bytes (read + write) per launch from one ncu capture of `python bench.py
+# --steps 1 --warmup 1` (profiles/); None once the kernel changed since.
+TRAFFIC = {"k_query": 21.63e6, "k_si_cluster": None}
+FP64_PEAK_TFLOPS = 1.25
 METRIC = "patch queries/s: SFC index vs full-scan masked-L2, 1 GB300, oracle-equal picks"
 UNIT = "patch queries/s"
 
@@ -105,6 +109,26 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+# ----------------------------------------------------------------------------
+# multi-rank aggregation: every rank runs its own copy of the workload (the
+# queries are independent), the job time is the slowest rank's
+# ----------------------------------------------------------------------------
+def max_over_ranks(ms: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(queries_per_step: int, steps: int, world: int, job_ms: float) -> float:
+    """Queries answered by all ranks / the slowest rank's time (weak scaling)."""
+    return queries_per_step * steps * world / (job_ms / 1000.0)
 
 
 # ----------------------------------------------------------------------------
@@ -221,6 +245,7 @@ def main():
     # ---- timed steps (event pairs per step; L2 flush between, untimed) -------
     clocks = Clocks(local)
     clocks.start()
+    sfc.sfc_trace(True)
     barrier()
     torch.cuda.synchronize()
     l0 = sfc.sfc_launch_count()
@@ -241,13 +266,12 @@ def main():
     clk = clocks.stop()
     for ix in live:
         ix.close()
+    trace = sfc.sfc_trace_read()  # phase events recorded on the build stream
+    sfc.sfc_trace(False)
+    phases_ms = {k: v / max(trace["builds"], 1) for k, v in trace["ms"].items()}
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tot_ms = float(tt.item())
-    value = Q * args.steps * world / (tot_ms / 1000.0)
+    tot_ms = max_over_ranks(sum(step_ms), dev)
+    value = whole_job_rate(Q, args.steps, world, tot_ms)
 
     # ---- the dominant kernel: the query kernel, timed alone on its stream -----
     ix = sfc.sfc_index_build(gd, md, **prm)
@@ -277,11 +301,21 @@ def main():
     except (OSError, ValueError):
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = bytes_launch / (q_ms_mean / 1000.0) / 1e9
-    roofline = {"kernel": "k_query (sfc_query_batch)", "bound": "hbm", "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s",
-                "bytes_per_query": per_query, "mean_candidates": mean_cand, "launch_ms": q_ms_mean}
+    q_roof = {"kernel": "k_query (sfc_query_batch)", "bound": "hbm",
+              "achieved": bytes_launch / (q_ms_mean / 1000.0) / 1e9, "peak": hbm, "unit": "GB/s",
+              "traffic": TRAFFIC.get("k_query"),
+              "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s",
+              "bytes_per_query": per_query, "mean_candidates": mean_cand, "launch_ms": q_ms_mean}
+    q_roof["frac"] = q_roof["achieved"] / q_roof["peak"]
+    eig_ms = phases_ms["eigen"]
+    eig_tf = trace["eig_flops"] / max(trace["builds"], 1) / (eig_ms / 1000.0) / 1e12 if eig_ms > 0 else 0.0
+    e_roof = {"kernel": "k_si_cluster (eigen-solve in sfc_index_build)", "bound": "alu", "achieved": eig_tf,
+              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": eig_tf / FP64_PEAK_TFLOPS,
+              "traffic": TRAFFIC.get("k_si_cluster"), "peak_source": "nominal FP64 1.25 TFLOP/s (no measured FP64 peak)",
+              "launch_ms": eig_ms, "flops_per_launch": trace["eig_flops"] / max(trace["builds"], 1)}
+    # the dominant kernel of a step: the eigen-solve or the query kernel, by measured time
+    roofline = e_roof if eig_ms >= q_ms_mean else q_roof
+    roofline["others"] = [q_roof if roofline is e_roof else e_roof]
     query_only_qps = Q / (q_ms_mean / 1000.0)
 
     # ---- full scan (same queries, a seeded subset) -----------------------------
@@ -358,7 +392,7 @@ def main():
                        "parallelism": f"replica x{world}"},
             "roofline": roofline, "gpu_launches": int(launches), "e2e": e2e, "clocks": clk,
             "query_only": {"qps": query_only_qps, "ms": q_ms_mean},
-            "index_build_ms": tot_ms / args.steps - q_ms_mean,
+            "index_build_ms": tot_ms / args.steps - q_ms_mean, "phases_ms": phases_ms,
             "fullscan": fullscan, "inpaint_128x128": inp}
     if rank == 0:
         if not args.no_cpu_baseline:

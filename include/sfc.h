@@ -195,6 +195,21 @@ int sfc_status(void* stream);
  * threads).  Diagnostics: the difference across a region counts its launches. */
 uint64_t sfc_launch_count(void);
 
+/* Phase tracing of sfc_index_build (diagnostics; the paper reports only wall
+ * times).  sfc_trace(1) enables it and clears the accumulators, sfc_trace(0)
+ * disables it.  While enabled, every build records CUDA events on its stream
+ * around its phases; when that index is destroyed (the device is idle then) the
+ * phase durations are added to the accumulators.  sfc_trace_read copies to HOST
+ * ms[SFC_TRACE_PHASES] the summed milliseconds of the phases -- dictionary,
+ * moments (mean + covariance), eigen-solve, basis finalisation,
+ * projection + keys, sort -- and *builds the number of builds summed, and
+ * *eig_flops the summed algorithmic FP64 flops of the eigen-solves
+ * (per index and iteration 2 s^2 p + 4 s p^2, s = subset length, p = block
+ * size).  Any output may be NULL. */
+enum { SFC_TRACE_PHASES = 6 };
+int sfc_trace(int on);
+int sfc_trace_read(double* ms, int64_t* builds, double* eig_flops);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* sfc_last_error(void);
 

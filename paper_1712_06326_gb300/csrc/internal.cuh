@@ -35,6 +35,15 @@ void count_launch();
 // Library-owned device status word of the current device (see ST_* bits).
 uint32_t* status_word();
 
+// Stream-ordered allocation from the library's own memory pool on the current
+// device (created on first use; it keeps freed memory for reuse instead of
+// returning it to the driver at every synchronisation).
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st);
+template <typename T>
+inline cudaError_t pmalloc(T** p, size_t bytes, cudaStream_t st) {
+  return pool_malloc(reinterpret_cast<void**>(p), bytes, st);
+}
+
 // Per-index state (host struct, device arrays).
 struct Index {
   Geo g;
@@ -61,7 +70,15 @@ struct Index {
   uint64_t* keys = nullptr;   // C*N unsorted (kept only with keep_intermediates)
   uint64_t* skeys = nullptr;  // C*N
   uint32_t* sids = nullptr;   // C*N
+  // tracing (sfc_trace): phase events of the build and the eigen-solve iterations
+  cudaEvent_t ev[SFC_TRACE_PHASES + 1] = {};
+  bool traced = false;
+  int p_block = 0;             // subspace block size
+  int* eig_iters = nullptr;    // C (device): iterations used per index
 };
+
+// Record phase boundary k of a traced build (no-op otherwise).
+void trace_mark(Index& ix, int k, cudaStream_t st);
 
 // k_dict.cu
 int dict_extract(const uint8_t* mask, const Geo& g, cudaStream_t st, uint32_t** dict, int64_t* N);

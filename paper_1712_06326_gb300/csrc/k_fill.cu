@@ -266,20 +266,20 @@ int fill_loop(const Geo& g, float* grid, uint8_t* mask, int prio, int mode, cons
   float* tilemin = nullptr;
   unsigned int* gmin = nullptr;
   const int64_t ntiles = (N + 1023) / 1024;
-  SFC_TRY(cudaMallocAsync(&s.key, sizeof(unsigned long long) * npix, st));
-  SFC_TRY(cudaMallocAsync(&s.conf, sizeof(float) * npix, st));
-  SFC_TRY(cudaMallocAsync(&s.cterm, sizeof(float) * npix, st));
-  SFC_TRY(cudaMallocAsync(&s.best, sizeof(unsigned long long), st));
-  SFC_TRY(cudaMallocAsync(&s.sel_lin, sizeof(int64_t), st));
-  SFC_TRY(cudaMallocAsync(&s.sel_xyz, sizeof(int32_t) * 4, st));
-  SFC_TRY(cudaMallocAsync(&s.sel_cterm, sizeof(float), st));
-  SFC_TRY(cudaMallocAsync(&s.pick, sizeof(int64_t), st));
-  SFC_TRY(cudaMallocAsync(&s.cost, sizeof(float), st));
-  SFC_TRY(cudaMallocAsync(&s.done, sizeof(int), st));
-  SFC_TRY(cudaMallocAsync(&s.steps, sizeof(int64_t), st));
-  SFC_TRY(cudaMallocAsync(&unknown, sizeof(int64_t), st));
-  SFC_TRY(cudaMallocAsync(&tilemin, sizeof(float) * (ntiles > 0 ? ntiles : 1), st));
-  SFC_TRY(cudaMallocAsync(&gmin, sizeof(unsigned int), st));
+  SFC_TRY(pmalloc(&s.key, sizeof(unsigned long long) * npix, st));
+  SFC_TRY(pmalloc(&s.conf, sizeof(float) * npix, st));
+  SFC_TRY(pmalloc(&s.cterm, sizeof(float) * npix, st));
+  SFC_TRY(pmalloc(&s.best, sizeof(unsigned long long), st));
+  SFC_TRY(pmalloc(&s.sel_lin, sizeof(int64_t), st));
+  SFC_TRY(pmalloc(&s.sel_xyz, sizeof(int32_t) * 4, st));
+  SFC_TRY(pmalloc(&s.sel_cterm, sizeof(float), st));
+  SFC_TRY(pmalloc(&s.pick, sizeof(int64_t), st));
+  SFC_TRY(pmalloc(&s.cost, sizeof(float), st));
+  SFC_TRY(pmalloc(&s.done, sizeof(int), st));
+  SFC_TRY(pmalloc(&s.steps, sizeof(int64_t), st));
+  SFC_TRY(pmalloc(&unknown, sizeof(int64_t), st));
+  SFC_TRY(pmalloc(&tilemin, sizeof(float) * (ntiles > 0 ? ntiles : 1), st));
+  SFC_TRY(pmalloc(&gmin, sizeof(unsigned int), st));
   SFC_TRY(cudaMemsetAsync(unknown, 0, sizeof(int64_t), st));
   SFC_TRY(cudaMemsetAsync(s.key, 0, sizeof(unsigned long long) * npix, st));
   SFC_TRY(cudaMemsetAsync(s.cterm, 0, sizeof(float) * npix, st));

@@ -361,17 +361,17 @@ int fullscan_batch(const Geo& g, const float* grid, const uint8_t* cur_mask, con
   uint8_t* bad = nullptr;
   float* tilemin = nullptr;
   unsigned int* gmin = nullptr;
-  SFC_TRY(cudaMallocAsync(&tilemin, sizeof(float) * Q * ntiles, st));
-  SFC_TRY(cudaMallocAsync(&gmin, sizeof(unsigned int) * Q, st));
-  SFC_TRY(cudaMallocAsync(&bad, Q, st));
+  SFC_TRY(pmalloc(&tilemin, sizeof(float) * Q * ntiles, st));
+  SFC_TRY(pmalloc(&gmin, sizeof(unsigned int) * Q, st));
+  SFC_TRY(pmalloc(&bad, Q, st));
   const int64_t* L = centre_lin;
   if (!L) {
-    SFC_TRY(cudaMallocAsync(&lin, sizeof(int64_t) * Q, st));
+    SFC_TRY(pmalloc(&lin, sizeof(int64_t) * Q, st));
     count_launch();
     k_centre_lin<<<(unsigned)((Q + 255) / 256), 256, 0, st>>>(centres, Q, g, lin, status_word());
     L = lin;
   } else {
-    SFC_TRY(cudaMallocAsync(&lin, sizeof(int64_t) * Q, st));
+    SFC_TRY(pmalloc(&lin, sizeof(int64_t) * Q, st));
     SFC_TRY(cudaMemcpyAsync(lin, centre_lin, sizeof(int64_t) * Q, cudaMemcpyDeviceToDevice, st));
     L = lin;
   }

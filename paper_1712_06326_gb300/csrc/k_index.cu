@@ -166,7 +166,7 @@ int launch_project(const Index& ix, const float* grid, float* proj, uint32_t* lo
 int project_and_key(Index& ix, const float* grid, cudaStream_t st, float* proj, uint64_t* keys) {
   uint32_t* lohi = nullptr;
   const int n = ix.C * ix.D;
-  SFC_TRY(cudaMallocAsync(&lohi, sizeof(uint32_t) * 2 * n, st));
+  SFC_TRY(pmalloc(&lohi, sizeof(uint32_t) * 2 * n, st));
   count_launch();
   k_lohi_init<<<(n + 127) / 128, 128, 0, st>>>(lohi, n);
   int rc = SFC_EINVAL;

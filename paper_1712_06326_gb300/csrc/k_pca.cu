@@ -205,6 +205,7 @@ struct SiBufs {
   double* X;   // C*s*p
   double* e;   // C*p
   int* done;   // C
+  int* iters;  // C: iterations used (tracing)
 };
 
 // Y = A Q for every curve; blockIdx.y = curve, the s*p outputs spread over
@@ -379,6 +380,7 @@ __device__ void small_jacobi(double* H, double* W, int np, double* al, double* b
 __global__ void __launch_bounds__(256) k_si_small(SiBufs b, int s, int p, int D) {
   const int c = blockIdx.x;
   if (b.done[c]) return;
+  if (threadIdx.x == 0) b.iters[c] += 1;
   const int np = p + (p & 1);
   extern __shared__ double sm[];
   double* Q = sm;               // s*p
@@ -495,7 +497,10 @@ __global__ void __launch_bounds__(256) k_si_init(SiBufs b, int s, int p) {
   chol_qr(Z, s, p, G);
   double* Qg = b.Q + (int64_t)c * s * p;
   for (int t = threadIdx.x; t < s * p; t += blockDim.x) Qg[t] = Z[t];
-  if (threadIdx.x == 0) b.done[c] = 0;
+  if (threadIdx.x == 0) {
+    b.done[c] = 0;
+    b.iters[c] = 0;
+  }
 }
 
 // Top-D Ritz vectors -> FP32 basis with the sign convention; evals: the p Ritz
@@ -544,14 +549,136 @@ __device__ inline double rsqrt64(double x) {
   return y * fma(-0.5 * x, y * y, 1.5);
 }
 
+// Eigen-decomposition of the small symmetric H (np x np, shared, FP64) for the
+// cluster path: cyclic Jacobi in FP32 (cheap on this part), then two steps of
+// Ogita & Aishima's iterative refinement in FP64 ("Iterative refinement for
+// symmetric eigenvalue decomposition", 2018): with X the current eigenvector
+// matrix, R = I - X^T X, S = X^T H X, l_i = S_ii / (1 - R_ii),
+// E_ij = (S_ij + l_j R_ij) / (l_j - l_i) (i != j; R_ij / 2 when l_i, l_j are too
+// close), E_ii = R_ii / 2, X <- X + X E.  Each step squares the error, so two
+// steps take the FP32 result to FP64 accuracy; all FP64 work is dense
+// np x np products spread over the CTA.  On exit W holds X and ev the l_i.
+__device__ void small_eig_refined(const double* H, double* W, double* ev, int np, float* H32, float* W32,
+                                  double* T1, double* T2, double* red) {
+  // FP32 cyclic Jacobi (one warp; np <= 24)
+  for (int t = threadIdx.x; t < np * np; t += blockDim.x) {
+    H32[t] = (float)H[t];
+    W32[t] = (t / np == t % np) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int sweep = 0; sweep < 12; ++sweep) {
+      float off = 0.0f, all = 0.0f;
+      for (int t = lane; t < np * np; t += 32) {
+        const float v = H32[t] * H32[t];
+        all += v;
+        if (t / np != t % np) off += v;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        off += __shfl_xor_sync(0xffffffffu, off, o);
+        all += __shfl_xor_sync(0xffffffffu, all, o);
+      }
+      if (off <= 1e-13f * all) break;  // FP32 accuracy reached; FP64 refinement follows
+      for (int pp = 0; pp < np - 1; ++pp)
+        for (int q = pp + 1; q < np; ++q) {
+          const float apq = H32[pp * np + q];
+          if (apq == 0.0f) continue;
+          const float tau = (H32[q * np + q] - H32[pp * np + pp]) / (2.0f * apq);
+          const float tt = tau >= 0.0f ? 1.0f / (tau + sqrtf(1.0f + tau * tau)) : -1.0f / (-tau + sqrtf(1.0f + tau * tau));
+          const float cs = rsqrtf(1.0f + tt * tt), sn = tt * cs;
+          __syncwarp();
+          if (lane < np) {
+            const int k = lane;
+            const float hkp = H32[k * np + pp], hkq = H32[k * np + q];
+            H32[k * np + pp] = cs * hkp - sn * hkq;
+            H32[k * np + q] = sn * hkp + cs * hkq;
+          }
+          __syncwarp();
+          if (lane < np) {
+            const int k = lane;
+            const float hpk = H32[pp * np + k], hqk = H32[q * np + k];
+            H32[pp * np + k] = cs * hpk - sn * hqk;
+            H32[q * np + k] = sn * hpk + cs * hqk;
+            const float wkp = W32[k * np + pp], wkq = W32[k * np + q];
+            W32[k * np + pp] = cs * wkp - sn * wkq;
+            W32[k * np + q] = sn * wkp + cs * wkq;
+          }
+          __syncwarp();
+        }
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < np * np; t += blockDim.x) W[t] = (double)W32[t];
+  __syncthreads();
+  for (int step = 0; step < 2; ++step) {
+    // T1 = H X
+    for (int t = threadIdx.x; t < np * np; t += blockDim.x) {
+      const int i = t / np, j = t % np;
+      double a0 = 0.0, a1 = 0.0;
+      for (int k = 0; k < np; k += 2) {
+        a0 = fma(H[i * np + k], W[k * np + j], a0);
+        if (k + 1 < np) a1 = fma(H[i * np + k + 1], W[(k + 1) * np + j], a1);
+      }
+      T1[t] = a0 + a1;
+    }
+    __syncthreads();
+    // T2 = S = X^T H X (upper, mirrored) ; red-free R = I - X^T X into H32 space (as double in T1 later)
+    for (int t = threadIdx.x; t < np * np; t += blockDim.x) {
+      const int i = t / np, j = t % np;
+      double sv = 0.0, rv = 0.0;
+      for (int k = 0; k < np; ++k) {
+        sv = fma(W[k * np + i], T1[k * np + j], sv);
+        rv = fma(W[k * np + i], W[k * np + j], rv);
+      }
+      T2[t] = sv;
+      // keep R_ij in the float scratch's double view is not possible; stash in ev-sized rows below
+      reinterpret_cast<double*>(H32)[t] = (i == j ? 1.0 : 0.0) - rv;
+    }
+    __syncthreads();
+    const double* R = reinterpret_cast<const double*>(H32);
+    for (int i = threadIdx.x; i < np; i += blockDim.x) ev[i] = T2[i * np + i] / (1.0 - R[i * np + i]);
+    __syncthreads();
+    // E into T1, then W <- W + W E
+    double smax = 0.0;
+    for (int i = 0; i < np; ++i) smax = fmax(smax, fabs(ev[i]));
+    for (int t = threadIdx.x; t < np * np; t += blockDim.x) {
+      const int i = t / np, j = t % np;
+      double e;
+      if (i == j) {
+        e = 0.5 * R[t];
+      } else {
+        const double d = ev[j] - ev[i];
+        e = fabs(d) > 1e-13 * smax ? (T2[t] + ev[j] * R[t]) / d : 0.5 * R[t];
+      }
+      T1[t] = e;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < np * np; t += blockDim.x) {
+      const int i = t / np, j = t % np;
+      double a = W[t];
+      for (int k = 0; k < np; ++k) a = fma(W[i * np + k], T1[k * np + j], a);
+      T2[t] = a;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < np * np; t += blockDim.x) W[t] = T2[t];
+    __syncthreads();
+  }
+}
+
 struct ClShm {
   double* As;   // rp x s  (this CTA's rows of A)
   double* Qf;   // s x p   (full Q)
   double* Ys;   // rp x p
   double* Zs;   // rp x p
+  double* Xs;   // rp x p
   double* part; // np x np (partial sums exchanged through DSMEM)
   double* Hf;   // np x np
   double* Wf;   // np x np
+  double* T1;   // np x np
+  double* T2;   // np x np
+  double* Rv;   // np x np (as doubles; float scratch of the FP32 Jacobi aliases it)
+  float* W32;   // np x np
   double* ev;   // np
   double* al;   // np
   double* be;   // np
@@ -563,8 +690,12 @@ template <int CS>
 __device__ void cl_allreduce(cg::cluster_group& cl, double* part, double* out, int len) {
   cl.sync();
   for (int t = threadIdx.x; t < len; t += blockDim.x) {
+    double v[CS];
+#pragma unroll
+    for (int rk = 0; rk < CS; ++rk) v[rk] = cl.map_shared_rank(part, rk)[t];
     double acc = 0.0;
-    for (int rk = 0; rk < CS; ++rk) acc += cl.map_shared_rank(part, rk)[t];
+#pragma unroll
+    for (int rk = 0; rk < CS; ++rk) acc += v[rk];
     out[t] = acc;
   }
   cl.sync();
@@ -602,21 +733,34 @@ __device__ void cl_cholqr(cg::cluster_group& cl, ClShm& m, int nr, int r0, int s
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < nr; i += blockDim.x) {
-    double z[kPMax];
-    for (int k = 0; k < p; ++k) z[k] = m.Zs[i * p + k];
-    for (int k = 0; k < p; ++k) {
-      double v = z[k];
-      for (int j = 0; j < k; ++j) v = fma(-z[j], G[j * p + k], v);
-      z[k] = v * G[k * p + k];
-    }
-    for (int k = 0; k < p; ++k) {
-      m.Zs[i * p + k] = z[k];
-      m.Qf[(r0 + i) * p + k] = z[k];
+  // Rinv (upper) in Hf's lower triangle region is in use: build it in part[]
+  double* Ri = m.part;
+  if (threadIdx.x < p) {
+    const int j = threadIdx.x;  // column j of R^{-1}, back substitution
+    for (int i = p - 1; i >= 0; --i) {
+      double v = 0.0;
+      if (i == j) v = 1.0;
+      if (i < j)
+        for (int k = i + 1; k <= j; ++k) v = fma(-G[i * p + k], Ri[k * p + j], v);
+      Ri[i * p + j] = i <= j ? v * G[i * p + i] : 0.0;  // G[i][i] holds 1 / R_ii
     }
   }
+  __syncthreads();
+  // Q rows = Z rows R^{-1}, one (row, column) per thread
+  for (int t = threadIdx.x; t < nr * p; t += blockDim.x) {
+    const int i = t / p, k = t % p;
+    double a0 = 0.0, a1 = 0.0;
+    for (int j = 0; j <= k; j += 2) {
+      a0 = fma(m.Zs[i * p + j], Ri[j * p + k], a0);
+      if (j + 1 <= k) a1 = fma(m.Zs[i * p + j + 1], Ri[(j + 1) * p + k], a1);
+    }
+    m.Qf[(r0 + i) * p + k] = a0 + a1;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nr * p; t += blockDim.x) m.Zs[t] = m.Qf[(r0 + t / p) * p + t % p];
   cl.sync();
   const int me = (int)cl.block_rank();
+#pragma unroll 4
   for (int t = threadIdx.x; t < s * p; t += blockDim.x) {
     const int rk = (t / p) / rp;
     if (rk != me) m.Qf[t] = cl.map_shared_rank(m.Qf, rk)[t];
@@ -640,10 +784,15 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
   m.Qf = m.As + rp * s;
   m.Ys = m.Qf + s * p;
   m.Zs = m.Ys + rp * p;
-  m.part = m.Zs + rp * p;
+  m.Xs = m.Zs + rp * p;
+  m.part = m.Xs + rp * p;
   m.Hf = m.part + np * np;
   m.Wf = m.Hf + np * np;
-  m.ev = m.Wf + np * np;
+  m.T1 = m.Wf + np * np;
+  m.T2 = m.T1 + np * np;
+  m.Rv = m.T2 + np * np;
+  m.W32 = reinterpret_cast<float*>(m.Rv + np * np);
+  m.ev = reinterpret_cast<double*>(m.W32 + np * np + 2);
   m.al = m.ev + np;
   m.be = m.al + np;
   m.ord = reinterpret_cast<int*>(m.be + np);
@@ -674,9 +823,16 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
     for (int t = threadIdx.x; t < nr * p; t += blockDim.x) {
       const int i = t / p, k = t % p;
       const double* ar = m.As + i * s;
-      double acc = 0.0;
-      for (int j = 0; j < s; ++j) acc = fma(ar[j], m.Qf[j * p + k], acc);
-      m.Ys[t] = acc;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int j = 0;
+      for (; j + 3 < s; j += 4) {
+        a0 = fma(ar[j], m.Qf[j * p + k], a0);
+        a1 = fma(ar[j + 1], m.Qf[(j + 1) * p + k], a1);
+        a2 = fma(ar[j + 2], m.Qf[(j + 2) * p + k], a2);
+        a3 = fma(ar[j + 3], m.Qf[(j + 3) * p + k], a3);
+      }
+      for (; j < s; ++j) a0 = fma(ar[j], m.Qf[j * p + k], a0);
+      m.Ys[t] = (a0 + a1) + (a2 + a3);
     }
     __syncthreads();
     const bool rr = (it % kRR) == kRR - 1 || it == kMaxIterCl - 1;
@@ -695,48 +851,47 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
         if (a > bb) m.Hf[t] = m.Hf[bb * np + a];
       }
       __syncthreads();
-      small_jacobi(m.Hf, m.Wf, np, m.al, m.be, red);
+      small_eig_refined(m.Hf, m.Wf, m.ev, np, reinterpret_cast<float*>(m.Rv), m.W32, m.T1, m.T2, red);
+      // order the p Ritz values descending (ties: lower column); padding column excluded
       for (int k = threadIdx.x; k < p; k += blockDim.x) {
-        const double ek = m.Hf[k * np + k];
+        const double ek = m.ev[k];
         int r = 0;
         for (int j = 0; j < p; ++j) {
-          const double ej = m.Hf[j * np + j];
+          const double ej = m.ev[j];
           if (ej > ek || (ej == ek && j < k)) ++r;
         }
         m.ord[r] = k;
-        m.ev[r] = ek;
+        m.al[r] = ek;
       }
       __syncthreads();
-      // X = Q W, Z = Y W (this CTA's rows); residual partial sums for k < D
+      for (int k = threadIdx.x; k < p; k += blockDim.x) m.ev[k] = m.al[k];
+      __syncthreads();
+      // X = Q W, Z = Y W (this CTA's rows), one (row, column) per thread
       double* Xg = b.X + (int64_t)c * s * p;
-      for (int i = threadIdx.x; i < nr; i += blockDim.x) {
-        double x[kPMax], z[kPMax];
-        for (int k = 0; k < p; ++k) {
-          const int col = m.ord[k];
-          double ax = 0.0, az = 0.0;
-          for (int j = 0; j < p; ++j) {
-            ax = fma(m.Qf[(r0 + i) * p + j], m.Wf[j * np + col], ax);
-            az = fma(m.Ys[i * p + j], m.Wf[j * np + col], az);
-          }
-          x[k] = ax;
-          z[k] = az;
+      for (int t = threadIdx.x; t < nr * p; t += blockDim.x) {
+        const int i = t / p, k = t % p, col = m.ord[k];
+        double ax = 0.0, az = 0.0;
+        for (int j = 0; j < p; ++j) {
+          ax = fma(m.Qf[(r0 + i) * p + j], m.Wf[j * np + col], ax);
+          az = fma(m.Ys[i * p + j], m.Wf[j * np + col], az);
         }
-        for (int k = 0; k < p; ++k) {
-          Xg[(int64_t)(r0 + i) * p + k] = x[k];
-          m.Zs[i * p + k] = z[k];
-        }
+        m.Xs[t] = ax;
+        m.Zs[t] = az;
+        Xg[(int64_t)(r0 + i) * p + k] = ax;
       }
       __syncthreads();
+      // residual partial sums |Z_k - e_k X_k|^2 of this CTA's rows, k < D
       for (int t = threadIdx.x; t < np * np; t += blockDim.x) m.part[t] = 0.0;
+      for (int t = threadIdx.x; t < nr * p; t += blockDim.x) {
+        const int k = t % p;
+        const double r = fma(-m.ev[k], m.Xs[t], m.Zs[t]);
+        m.Ys[t] = r * r;  // Y is not needed after Z = Y W
+      }
       __syncthreads();
-      for (int k = 0; k < D; ++k) {
-        double r2 = 0.0;
-        for (int i = threadIdx.x; i < nr; i += blockDim.x) {
-          const double r = fma(-m.ev[k], Xg[(int64_t)(r0 + i) * p + k], m.Zs[i * p + k]);
-          r2 = fma(r, r, r2);
-        }
-        r2 = block_sum(r2, red);
-        if (threadIdx.x == 0) m.part[k] = r2;
+      if (threadIdx.x < D) {
+        double acc = 0.0;
+        for (int i = 0; i < nr; ++i) acc += m.Ys[i * p + threadIdx.x];
+        m.part[threadIdx.x] = acc;
       }
       cl_allreduce<CS>(cl, m.part, m.Hf, D);
       double worst = 0.0;
@@ -744,7 +899,10 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
       conv = worst <= 1e-22 * m.ev[0] * m.ev[0];
       if (conv || it == kMaxIterCl - 1) {
         if (me == 0 && threadIdx.x < p) b.e[(int64_t)c * p + threadIdx.x] = m.ev[threadIdx.x];
-        if (me == 0 && threadIdx.x == 0) b.done[c] = conv ? 1 : 0;
+        if (me == 0 && threadIdx.x == 0) {
+          b.done[c] = conv ? 1 : 0;
+          b.iters[c] = it + 1;
+        }
         break;
       }
     } else {
@@ -762,8 +920,10 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
 size_t cluster_shm_bytes(int s, int p, int CS) {
   const int rp = (s + CS - 1) / CS;
   const int np = p + (p & 1);
-  return sizeof(double) * ((size_t)rp * s + (size_t)s * p + 2 * (size_t)rp * p + 3 * (size_t)np * np + 3 * np) +
-         sizeof(int) * np;
+  // As, Qf, Ys, Zs, Xs, part, Hf, Wf, T1, T2, Rv (doubles); W32 (floats) + pad;
+  // ev, al, be (doubles); ord (ints)
+  return sizeof(double) * ((size_t)rp * s + (size_t)s * p + 3 * (size_t)rp * p + 6 * (size_t)np * np + 3 * np) +
+         sizeof(float) * ((size_t)np * np + 2) + sizeof(int) * np;
 }
 
 }  // namespace
@@ -791,18 +951,20 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
   double *mean = nullptr, *mean_c = nullptr, *msum = nullptr, *partial = nullptr, *M = nullptr;
   int2* pairs = nullptr;
   SiBufs b;
-  SFC_TRY(cudaMallocAsync(&mean, sizeof(double) * n, st));
-  SFC_TRY(cudaMallocAsync(&mean_c, sizeof(double) * C * s, st));
-  SFC_TRY(cudaMallocAsync(&msum, sizeof(double) * nsplit * n, st));
-  SFC_TRY(cudaMallocAsync(&partial, sizeof(double) * nsplit * npairs * kTile * kTile, st));
-  SFC_TRY(cudaMallocAsync(&M, sizeof(double) * n * n, st));
-  SFC_TRY(cudaMallocAsync(&pairs, sizeof(int2) * npairs, st));
-  SFC_TRY(cudaMallocAsync(&b.A, sizeof(double) * C * s * s, st));
-  SFC_TRY(cudaMallocAsync(&b.Q, sizeof(double) * C * s * p, st));
-  SFC_TRY(cudaMallocAsync(&b.Y, sizeof(double) * C * s * p, st));
-  SFC_TRY(cudaMallocAsync(&b.X, sizeof(double) * C * s * p, st));
-  SFC_TRY(cudaMallocAsync(&b.e, sizeof(double) * C * p, st));
-  SFC_TRY(cudaMallocAsync(&b.done, sizeof(int) * C, st));
+  SFC_TRY(pmalloc(&mean, sizeof(double) * n, st));
+  SFC_TRY(pmalloc(&mean_c, sizeof(double) * C * s, st));
+  SFC_TRY(pmalloc(&msum, sizeof(double) * nsplit * n, st));
+  SFC_TRY(pmalloc(&partial, sizeof(double) * nsplit * npairs * kTile * kTile, st));
+  SFC_TRY(pmalloc(&M, sizeof(double) * n * n, st));
+  SFC_TRY(pmalloc(&pairs, sizeof(int2) * npairs, st));
+  SFC_TRY(pmalloc(&b.A, sizeof(double) * C * s * s, st));
+  SFC_TRY(pmalloc(&b.Q, sizeof(double) * C * s * p, st));
+  SFC_TRY(pmalloc(&b.Y, sizeof(double) * C * s * p, st));
+  SFC_TRY(pmalloc(&b.X, sizeof(double) * C * s * p, st));
+  SFC_TRY(pmalloc(&b.e, sizeof(double) * C * p, st));
+  SFC_TRY(pmalloc(&b.done, sizeof(int) * C, st));
+  b.iters = ix.eig_iters;
+  SFC_TRY(cudaMemsetAsync(b.iters, 0, sizeof(int) * C, st));
   SFC_TRY(cudaMemcpyAsync(pairs, pairs_h.data(), sizeof(int2) * npairs, cudaMemcpyHostToDevice, st));
 
   count_launch();
@@ -818,6 +980,8 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
   count_launch();
   k_cov_extract<<<dim3(64, C), 256, 0, st>>>(M, mean, n, ix.g.ch, cnt, ix.sub_pix, ix.m, s, b.A, mean_c);
   SFC_TRY(cudaGetLastError());
+  trace_mark(ix, 2, st);
+  ix.p_block = p;
 
   const size_t shm_init = sizeof(double) * ((size_t)s * p + (size_t)p * p);
   const size_t shm_small = sizeof(double) * (2 * (size_t)s * p + 2 * (size_t)np * np + 3 * np) + sizeof(int) * np;
@@ -892,6 +1056,7 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
     }
   }
   SFC_TRY(cudaGetLastError());
+  trace_mark(ix, 3, st);
   count_launch();
   k_pca_finalize<<<C, 256, 0, st>>>(b, mean_c, s, p, D, ix.basis, ix.mean, ix.evals, status_word());
   SFC_TRY(cudaGetLastError());

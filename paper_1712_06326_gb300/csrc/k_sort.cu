@@ -214,11 +214,11 @@ int radix_sort_pairs(const uint64_t* keys, uint64_t* skeys, uint32_t* sids, int6
   uint64_t* tk = nullptr;
   uint32_t* tv = nullptr;
   const size_t status_words = (size_t)npass * C * ntiles * 256;
-  SFC_TRY(cudaMallocAsync(&hist, sizeof(uint32_t) * C * 8 * 256, st));
-  SFC_TRY(cudaMallocAsync(&status, sizeof(uint32_t) * status_words, st));
-  SFC_TRY(cudaMallocAsync(&ctr, sizeof(uint32_t) * npass * C, st));
-  SFC_TRY(cudaMallocAsync(&tk, sizeof(uint64_t) * C * N, st));
-  SFC_TRY(cudaMallocAsync(&tv, sizeof(uint32_t) * C * N, st));
+  SFC_TRY(pmalloc(&hist, sizeof(uint32_t) * C * 8 * 256, st));
+  SFC_TRY(pmalloc(&status, sizeof(uint32_t) * status_words, st));
+  SFC_TRY(pmalloc(&ctr, sizeof(uint32_t) * npass * C, st));
+  SFC_TRY(pmalloc(&tk, sizeof(uint64_t) * C * N, st));
+  SFC_TRY(pmalloc(&tv, sizeof(uint32_t) * C * N, st));
   SFC_TRY(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * C * 8 * 256, st));
   SFC_TRY(cudaMemsetAsync(status, 0, sizeof(uint32_t) * status_words, st));
   SFC_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t) * npass * C, st));
@@ -231,7 +231,7 @@ int radix_sort_pairs(const uint64_t* keys, uint64_t* skeys, uint32_t* sids, int6
   SFC_TRY(cudaGetLastError());
   // hist is laid out [C][8][256]; pass p needs the [C][256] slice of every index
   uint32_t* goffs = nullptr;
-  SFC_TRY(cudaMallocAsync(&goffs, sizeof(uint32_t) * npass * C * 256, st));
+  SFC_TRY(pmalloc(&goffs, sizeof(uint32_t) * npass * C * 256, st));
   for (int p = 0; p < npass; ++p)
     SFC_TRY(cudaMemcpy2DAsync(goffs + (size_t)p * C * 256, 256 * sizeof(uint32_t), hist + (size_t)p * 256,
                               8 * 256 * sizeof(uint32_t), 256 * sizeof(uint32_t), C, cudaMemcpyDeviceToDevice, st));

@@ -28,6 +28,44 @@ uint32_t* g_status_ptr[128] = {};
 void set_error(const std::string& msg) { g_err = msg; }
 
 namespace {
+struct TraceAcc {
+  bool on = false;
+  double ms[SFC_TRACE_PHASES] = {};
+  int64_t builds = 0;
+  double eig_flops = 0.0;
+} g_trace;
+std::mutex g_trace_mu;
+}  // namespace
+
+void trace_mark(Index& ix, int k, cudaStream_t st) {
+  if (ix.traced && ix.ev[k]) cudaEventRecord(ix.ev[k], st);
+}
+
+// Fold a finished traced build into the accumulators (device idle).
+static void trace_fold(Index& ix) {
+  if (!ix.traced) return;
+  float t[SFC_TRACE_PHASES] = {};
+  bool ok = true;
+  for (int k = 0; k < SFC_TRACE_PHASES && ok; ++k) ok = cudaEventElapsedTime(&t[k], ix.ev[k], ix.ev[k + 1]) == cudaSuccess;
+  std::vector<int> it(ix.C, 0);
+  if (ok && ix.eig_iters) ok = cudaMemcpy(it.data(), ix.eig_iters, sizeof(int) * ix.C, cudaMemcpyDeviceToHost) == cudaSuccess;
+  cudaGetLastError();
+  if (ok) {
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    for (int k = 0; k < SFC_TRACE_PHASES; ++k) g_trace.ms[k] += t[k];
+    g_trace.builds += 1;
+    const double s = ix.s, p = ix.p_block;
+    for (int c = 0; c < ix.C; ++c) g_trace.eig_flops += it[c] * (2.0 * s * s * p + 4.0 * s * p * p);
+  }
+  for (auto& e : ix.ev)
+    if (e) {
+      cudaEventDestroy(e);
+      e = nullptr;
+    }
+  ix.traced = false;
+}
+
+namespace {
 std::atomic<uint64_t> g_launches{0};
 }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -42,6 +80,39 @@ uint32_t* status_word() {
     g_status_ptr[dev] = static_cast<uint32_t*>(p);
   }
   return g_status_ptr[dev];
+}
+
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[128] = {};
+bool g_pool_tried[128] = {};
+}  // namespace
+
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaMemPool_t pool = nullptr;
+  if (dev >= 0 && dev < 128) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool_tried[dev]) {
+      g_pool_tried[dev] = true;
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      if (cudaMemPoolCreate(&g_pool[dev], &props) == cudaSuccess) {
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+      } else {
+        g_pool[dev] = nullptr;
+        cudaGetLastError();
+      }
+    }
+    pool = g_pool[dev];
+  }
+  if (pool) return cudaMallocFromPoolAsync(p, bytes, pool, st);
+  return cudaMallocAsync(p, bytes, st);
 }
 
 int fill_loop(const Geo& g, float* grid, uint8_t* mask, int prio, int mode, const Index* ix, const uint32_t* dict,
@@ -162,12 +233,14 @@ std::vector<int32_t> subsets_host(int ndim, int K, int C, int m) {
 
 template <typename T>
 int upload(T** dst, const T* src, size_t count, cudaStream_t st) {
-  SFC_TRY(cudaMallocAsync(dst, sizeof(T) * (count ? count : 1), st));
+  SFC_TRY(pmalloc(dst, sizeof(T) * (count ? count : 1), st));
   if (count) SFC_TRY(cudaMemcpyAsync(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice, st));
   return SFC_OK;
 }
 
 void free_index(Index& ix) {
+  cudaDeviceSynchronize();
+  trace_fold(ix);
   void* ptrs[] = {ix.dict,  ix.eoff_all, ix.sub_eoff, ix.sub_pix, ix.weights, ix.basis, ix.mean, ix.evals,
                   ix.lo,    ix.scale,    ix.shifts,   ix.proj,    ix.keys,    ix.skeys, ix.sids};
   cudaDeviceSynchronize();
@@ -268,34 +341,50 @@ int build_index(const float* grid, const uint8_t* dict_mask, const sfc_grid* gp,
   SFC_CHECK(upload(&ix.sub_eoff, sub_eoff.data(), sub_eoff.size(), st));
   SFC_CHECK(upload(&ix.weights, ix.weights_h.data(), ix.weights_h.size(), st));
   SFC_CHECK(upload(&ix.shifts, sh.data(), sh.size(), st));
+  {
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    ix.traced = g_trace.on;
+  }
+  if (ix.traced) {
+    for (auto& e : ix.ev) SFC_TRY(cudaEventCreate(&e));
+    trace_mark(ix, 0, st);
+  }
+  SFC_TRY(pmalloc(&ix.eig_iters, sizeof(int) * ix.C, st));
+  SFC_TRY(cudaMemsetAsync(ix.eig_iters, 0, sizeof(int) * ix.C, st));
   SFC_CHECK(dict_extract(dict_mask, g, st, &ix.dict, &ix.N));
+  trace_mark(ix, 1, st);
   if (ix.N <= 0) {
     set_error("the dictionary is empty (no fully known patch)");
     return SFC_EINVAL;
   }
   const int C = ix.C, D = ix.D, s = ix.s;
   const int64_t N = ix.N;
-  SFC_TRY(cudaMallocAsync(&ix.basis, sizeof(float) * C * s * D, st));
-  SFC_TRY(cudaMallocAsync(&ix.mean, sizeof(float) * C * s, st));
-  SFC_TRY(cudaMallocAsync(&ix.evals, sizeof(double) * C * s, st));
-  SFC_TRY(cudaMallocAsync(&ix.lo, sizeof(float) * C * D, st));
-  SFC_TRY(cudaMallocAsync(&ix.scale, sizeof(float) * C * D, st));
-  SFC_TRY(cudaMallocAsync(&ix.skeys, sizeof(uint64_t) * C * N, st));
-  SFC_TRY(cudaMallocAsync(&ix.sids, sizeof(uint32_t) * C * N, st));
+  SFC_TRY(pmalloc(&ix.basis, sizeof(float) * C * s * D, st));
+  SFC_TRY(pmalloc(&ix.mean, sizeof(float) * C * s, st));
+  SFC_TRY(pmalloc(&ix.evals, sizeof(double) * C * s, st));
+  SFC_TRY(pmalloc(&ix.lo, sizeof(float) * C * D, st));
+  SFC_TRY(pmalloc(&ix.scale, sizeof(float) * C * D, st));
+  SFC_TRY(pmalloc(&ix.skeys, sizeof(uint64_t) * C * N, st));
+  SFC_TRY(pmalloc(&ix.sids, sizeof(uint32_t) * C * N, st));
   if (p->basis) {
     SFC_TRY(cudaMemcpyAsync(ix.basis, p->basis, sizeof(float) * C * s * D, cudaMemcpyHostToDevice, st));
     SFC_TRY(cudaMemcpyAsync(ix.mean, p->mean, sizeof(float) * C * s, cudaMemcpyHostToDevice, st));
     SFC_TRY(cudaMemsetAsync(ix.evals, 0xff, sizeof(double) * C * s, st));  // NaN
+    trace_mark(ix, 2, st);
+    trace_mark(ix, 3, st);
   } else {
     SFC_CHECK(pca_build(ix, grid, st));
   }
+  trace_mark(ix, 4, st);
   float* proj = nullptr;
   uint64_t* keys = nullptr;
-  SFC_TRY(cudaMallocAsync(&proj, sizeof(float) * C * N * D, st));
-  SFC_TRY(cudaMallocAsync(&keys, sizeof(uint64_t) * C * N, st));
+  SFC_TRY(pmalloc(&proj, sizeof(float) * C * N * D, st));
+  SFC_TRY(pmalloc(&keys, sizeof(uint64_t) * C * N, st));
   SFC_CHECK(project_and_key(ix, grid, st, proj, keys));
+  trace_mark(ix, 5, st);
   const int key_bits = std::min(64, D * ix.bp);
   SFC_CHECK(radix_sort_pairs(keys, ix.skeys, ix.sids, N, C, key_bits, st));
+  trace_mark(ix, 6, st);
   if (ix.keep) {
     ix.proj = proj;
     ix.keys = keys;
@@ -331,6 +420,22 @@ void sfc_params_default(sfc_params* p) {
 const char* sfc_last_error(void) { return g_err.c_str(); }
 
 uint64_t sfc_launch_count(void) { return g_launches.load(); }
+
+int sfc_trace(int on) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  g_trace = TraceAcc();
+  g_trace.on = on != 0;
+  return SFC_OK;
+}
+
+int sfc_trace_read(double* ms, int64_t* builds, double* eig_flops) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  if (ms)
+    for (int k = 0; k < SFC_TRACE_PHASES; ++k) ms[k] = g_trace.ms[k];
+  if (builds) *builds = g_trace.builds;
+  if (eig_flops) *eig_flops = g_trace.eig_flops;
+  return SFC_OK;
+}
 
 int sfc_index_build(const float* grid, const uint8_t* dict_mask, const sfc_grid* g, const sfc_params* p,
                     void* stream, sfc_index** out) {

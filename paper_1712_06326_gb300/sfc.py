@@ -24,7 +24,8 @@ SFC_MODE_FULLSCAN, SFC_MODE_SFC = 0, 1
 
 EXPORTS = ["sfc_params_default", "sfc_index_build", "sfc_index_destroy", "sfc_index_info", "sfc_index_export",
            "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "fullscan_query_batch_static",
-           "inpaint_run", "sfc_status", "sfc_launch_count", "sfc_last_error"]
+           "inpaint_run", "sfc_status", "sfc_launch_count", "sfc_trace", "sfc_trace_read", "sfc_last_error"]
+TRACE_PHASES = ("dictionary", "moments", "eigen", "finalize", "project_keys", "sort")
 
 
 class sfc_grid(C.Structure):
@@ -67,6 +68,10 @@ def lib():
         L.sfc_last_error.restype = C.c_char_p
         L.sfc_launch_count.restype = C.c_uint64
         L.sfc_launch_count.argtypes = []
+        L.sfc_trace.argtypes = [C.c_int]
+        L.sfc_trace.restype = C.c_int
+        L.sfc_trace_read.argtypes = [vp, vp, vp]
+        L.sfc_trace_read.restype = C.c_int
         for name in ["sfc_index_build", "sfc_index_destroy", "sfc_index_info", "sfc_index_export",
                      "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "fullscan_query_batch_static",
                      "inpaint_run", "sfc_status"]:
@@ -273,6 +278,19 @@ def inpaint_run(grid: torch.Tensor, mask: torch.Tensor, mode: int = SFC_MODE_FUL
 
 def sfc_launch_count() -> int:
     return int(lib().sfc_launch_count())
+
+
+def sfc_trace(on: bool) -> None:
+    _check(lib().sfc_trace(1 if on else 0), "sfc_trace")
+
+
+def sfc_trace_read() -> dict:
+    ms = np.zeros(len(TRACE_PHASES), np.float64)
+    builds = np.zeros(1, np.int64)
+    fl = np.zeros(1, np.float64)
+    _check(lib().sfc_trace_read(ms.ctypes.data_as(C.c_void_p), builds.ctypes.data_as(C.c_void_p),
+                                fl.ctypes.data_as(C.c_void_p)), "sfc_trace_read")
+    return dict(ms=dict(zip(TRACE_PHASES, ms.tolist())), builds=int(builds[0]), eig_flops=float(fl[0]))
 
 
 def sfc_status() -> int:
