@@ -62,7 +62,7 @@ enum {
 };
 
 enum { SFC_SELECT_ALL = 0, SFC_SELECT_BEST = 1 };
-enum { SFC_FP32 = 0, SFC_BF16 = 1 };
+enum { SFC_FP32 = 0, SFC_BF16 = 1, SFC_FP16 = 2 };
 enum { SFC_PRIO_CONFIDENCE = 0, SFC_PRIO_CRIMINISI = 1 };
 enum { SFC_MODE_FULLSCAN = 0, SFC_MODE_SFC = 1 };
 
@@ -87,7 +87,7 @@ typedef struct sfc_params {
   const float* basis;     /* host, curves*s*D FP32 basis (row i = subset value i), or NULL = PCA */
   const float* mean;      /* host, curves*s FP32 means (required with basis) */
   int32_t select;         /* SFC_SELECT_ALL or SFC_SELECT_BEST (Fig. 1(b)) */
-  int32_t precision;      /* SFC_FP32 (SFC_BF16 reserved for the GEMM pre-score) */
+  int32_t precision;      /* SFC_FP32; fullscan_query_batch also takes SFC_FP16 (tensor-core pre-score) */
   int64_t pca_sample;     /* dictionary entries used for the covariance; <= 0: all */
   int32_t priority;       /* fill order: SFC_PRIO_CONFIDENCE or SFC_PRIO_CRIMINISI (2-D) */
   int32_t keep_intermediates; /* 1: keep projections and unsorted keys for sfc_index_export */
@@ -152,6 +152,24 @@ int sfc_query_candidates(const sfc_index* ix, const float* grid, const uint8_t* 
 int fullscan_query_batch(const float* grid, const uint8_t* dict_mask, const uint8_t* cur_mask, const sfc_grid* g,
                          const sfc_params* p, const int32_t* centres, int64_t Q, int64_t* pick, float* cost,
                          void* stream);
+
+/* With p->precision == SFC_FP16, fullscan_query_batch computes the pre-score
+ * s(q, j) = sum m w (p'^2 - 2 t' p') (the cost minus a per-query constant,
+ * values centred per channel) as a tensor-core GEMM (tcgen05; FP16 operands
+ * split into high and low parts, FP32 accumulation), keeps per query the
+ * minimum of every 256-entry dictionary tile, and rescores exactly (FP32 +
+ * FP64 band, as above) every tile whose minimum lies within twice the pre-score
+ * error bound E_q of the smallest: the tile of the exact argmin always
+ * qualifies, so picks and costs are those of the FP32 path.  E_q bounds the
+ * operand splitting (3.01 u16^2 sum|a b|) and the FP32 accumulation
+ * (8 K' u32 sum|a b|, K' = 6 n), with |p'| bounded by the grid's per-channel
+ * range.  Values must satisfy |value - channel mean| < 128 (else SFC_EINVAL).
+ *
+ * Checking entry point: all Q x N pre-scores into `scores` (device, Q*N floats,
+ * row-major) and E_q into `bound` (device, Q doubles); *N_out (host) gets N. */
+int sfc_tc_prescores(const float* grid, const uint8_t* dict_mask, const uint8_t* cur_mask, const sfc_grid* g,
+                     const sfc_params* p, const int32_t* centres, int64_t Q, float* scores, double* bound,
+                     int64_t* N_out, void* stream);
 
 /* fullscan_query_batch without device allocation.  The paper has no
  * counterpart: this is an interface for callers that cannot call cudaMalloc --

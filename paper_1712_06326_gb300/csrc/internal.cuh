@@ -106,6 +106,13 @@ int fullscan_batch(const Geo& g, const float* grid, const uint8_t* cur_mask, con
                    const int* eoff_all, const float* weights, bool weighted, const int32_t* centres,
                    const int64_t* centre_lin, int64_t Q, int64_t* pick, float* cost, cudaStream_t st);
 
+int fullscan_batch_tc(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
+                      const int* eoff_all, const float* weights, bool weighted, const int32_t* centres, int64_t Q,
+                      int64_t* pick, float* cost, int* nsel, cudaStream_t st);
+int tc_prescores_all(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
+                     const int* eoff_all, const float* weights, const int32_t* centres, int64_t Q, float* scores,
+                     double* bound, cudaStream_t st);
+
 int fullscan_batch_into(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
                         const int* eoff_all, const float* weights, bool weighted, const int32_t* centres, int64_t Q,
                         int64_t* pick, float* cost, int64_t* lin, uint8_t* bad, unsigned int* gmin, float* tilemin,

@@ -260,6 +260,164 @@ __global__ void __launch_bounds__(kFsThreads) k_fs_band(const float* __restrict_
   }
 }
 
+// Exact pass after the tensor-core pre-score: every 256-entry tile whose
+// pre-score minimum lies within 2 E_q of the smallest one can hold the exact
+// argmin (|s_hat - s| <= E_q for every entry); the entries of those tiles are
+// scored with the FP32 cost of k_fs_band, then the usual band / FP64 decision.
+template <bool WEIGHTED>
+__global__ void __launch_bounds__(kFsThreads) k_tc_select(const float* __restrict__ grid,
+                                                          const uint8_t* __restrict__ mask, Geo g,
+                                                          const uint32_t* __restrict__ dict, int64_t N,
+                                                          const int* __restrict__ eoff_all,
+                                                          const float* __restrict__ weights,
+                                                          const int64_t* __restrict__ centre_lin,
+                                                          const float* __restrict__ tilemin, int ntiles,
+                                                          const double* __restrict__ bound,
+                                                          int64_t* __restrict__ pick, float* __restrict__ cost,
+                                                          int* __restrict__ nsel) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = g.n, ch = g.ch, P = g.P;
+  float2* am = reinterpret_cast<float2*>(smem_raw);
+  float* tv = reinterpret_cast<float*>(am + n);
+  int* eo = reinterpret_cast<int*>(tv + n);
+  float* we = reinterpret_cast<float*>(eo + n);
+  uint8_t* tm = reinterpret_cast<uint8_t*>(we + n);
+  __shared__ float red[kFsThreads / 32];
+  __shared__ int s_cnt, s_nsel;
+  __shared__ int64_t s_j[kBandCap];
+  __shared__ float s_c[kBandCap];
+  const int64_t q = blockIdx.x;
+  const int64_t tc = centre_lin[q];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < n; e += kFsThreads) {
+    const int o = eoff_all[e];
+    eo[e] = o;
+    we[e] = weights[e % ch];
+    const float t = grid[tc * ch + o];
+    const float k = mask[tc + eoff_all[e - e % ch] / ch] ? 1.0f : 0.0f;
+    tv[e] = t;
+    am[e] = make_float2(k, k * t);
+  }
+  for (int pp = threadIdx.x; pp < P; pp += kFsThreads) tm[pp] = mask[tc + eoff_all[pp * ch] / ch];
+  // smallest tile minimum
+  float mh = INFINITY;
+  for (int t = threadIdx.x; t < ntiles; t += kFsThreads) mh = fminf(mh, tilemin[q * ntiles + t]);
+  mh = warp_min(mh);
+  if (lane == 0) red[warp] = mh;
+  if (threadIdx.x == 0) {
+    s_cnt = 0;
+    s_nsel = 0;
+  }
+  __syncthreads();
+  mh = red[0];
+  for (int w = 1; w < kFsThreads / 32; ++w) mh = fminf(mh, red[w]);
+  const double thr = (double)mh + 2.0001 * bound[q] + 1e-30;
+  __syncthreads();
+  // pass A: the FP32 minimum over the selected tiles
+  float mymin = INFINITY;
+  int mysel = 0;
+  for (int t = 0; t < ntiles; ++t) {
+    if ((double)tilemin[q * ntiles + t] > thr) continue;  // uniform across the CTA
+    ++mysel;
+    const int64_t j = (int64_t)t * kFsThreads + threadIdx.x;
+    if (j < N) mymin = fminf(mymin, cost32_one<WEIGHTED>(grid, (int64_t)dict[j] * ch, am, eo, we, n));
+  }
+  mymin = warp_min(mymin);
+  if (lane == 0) red[warp] = mymin;
+  __syncthreads();
+  float m32 = red[0];
+  for (int w = 1; w < kFsThreads / 32; ++w) m32 = fminf(m32, red[w]);
+  if (threadIdx.x == 0 && nsel) nsel[q] = mysel;
+  const float T = band_limit32(m32, n);
+  // pass B: the band members (usually one)
+  for (int t = 0; t < ntiles; ++t) {
+    if ((double)tilemin[q * ntiles + t] > thr) continue;
+    const int64_t j = (int64_t)t * kFsThreads + threadIdx.x;
+    if (j >= N) continue;
+    const float c32 = cost32_one<WEIGHTED>(grid, (int64_t)dict[j] * ch, am, eo, we, n);
+    if (c32 <= T) {
+      const int slot = atomicAdd(&s_cnt, 1);
+      if (slot < kBandCap) {
+        s_j[slot] = j;
+        s_c[slot] = c32;
+      }
+    }
+  }
+  __syncthreads();
+  const int cnt = s_cnt;
+  if (cnt == 1) {
+    if (threadIdx.x == 0) {
+      pick[q] = s_j[0];
+      cost[q] = s_c[0];
+    }
+    return;
+  }
+  double bc = INFINITY;
+  int64_t bj = INT64_MAX;
+  float bc32 = 0.0f;
+  if (cnt <= kBandCap) {
+    for (int i = threadIdx.x; i < cnt; i += kFsThreads) {
+      const int64_t j = s_j[i];
+      const double c64 = exact_cost64(grid, (int64_t)dict[j] * ch, tv, tm, eo, P, ch, weights);
+      if (c64 < bc || (c64 == bc && j < bj)) {
+        bc = c64;
+        bj = j;
+        bc32 = s_c[i];
+      }
+    }
+  } else {
+    for (int t = 0; t < ntiles; ++t) {
+      if ((double)tilemin[q * ntiles + t] > thr) continue;
+      const int64_t j = (int64_t)t * kFsThreads + threadIdx.x;
+      if (j >= N) continue;
+      const int64_t sb = (int64_t)dict[j] * ch;
+      const float c32 = cost32_one<WEIGHTED>(grid, sb, am, eo, we, n);
+      if (c32 <= T) {
+        const double c64 = exact_cost64(grid, sb, tv, tm, eo, P, ch, weights);
+        if (c64 < bc || (c64 == bc && j < bj)) {
+          bc = c64;
+          bj = j;
+          bc32 = c32;
+        }
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double c2 = __shfl_xor_sync(0xffffffffu, bc, o);
+    const int64_t j2 = __shfl_xor_sync(0xffffffffu, bj, o);
+    const float f2 = __shfl_xor_sync(0xffffffffu, bc32, o);
+    if (c2 < bc || (c2 == bc && j2 < bj)) {
+      bc = c2;
+      bj = j2;
+      bc32 = f2;
+    }
+  }
+  __shared__ double sd[kFsThreads / 32];
+  __shared__ int64_t si[kFsThreads / 32];
+  __shared__ float sf[kFsThreads / 32];
+  if (lane == 0) {
+    sd[warp] = bc;
+    si[warp] = bj;
+    sf[warp] = bc32;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kFsThreads / 32; ++w)
+      if (sd[w] < bc || (sd[w] == bc && si[w] < bj)) {
+        bc = sd[w];
+        bj = si[w];
+        bc32 = sf[w];
+      }
+    if (bj == INT64_MAX) {
+      pick[q] = -1;
+      cost[q] = __int_as_float(0x7fc00000);
+    } else {
+      pick[q] = bj;
+      cost[q] = bc32;
+    }
+  }
+}
+
 // centre rows -> linear pixel index; invalid centres flag the status word and
 // get index -1 (their outputs become -1 / NaN).
 __global__ void k_centre_lin(const int32_t* __restrict__ centres, int64_t Q, Geo g, int64_t* __restrict__ lin,
@@ -349,6 +507,81 @@ int fullscan_single(const Geo& g, const float* grid, const uint8_t* cur_mask, co
                                         ntiles, pick, cost, st)
                   : run_band<EPT, false>(g, grid, cur_mask, dict, N, eoff_all, weights, centre_lin, 1, tilemin, gmin,
                                          ntiles, pick, cost, st);
+}
+
+int tc_prescore(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
+                const int* eoff_all, const float* weights, const int64_t* centre_lin, int64_t Q, float* tilemin,
+                float* scores, double* bound, cudaStream_t st);
+int tc_tiles(int64_t N);
+
+// The full scan with the tensor-core pre-score (precision SFC_FP16): pre-score
+// tile minima, then the exact pass over the tiles that can hold the argmin.
+// nsel (optional, device, Q ints) receives the number of tiles rescored.
+int fullscan_batch_tc(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
+                      const int* eoff_all, const float* weights, bool weighted, const int32_t* centres, int64_t Q,
+                      int64_t* pick, float* cost, int* nsel, cudaStream_t st) {
+  if (Q <= 0) return SFC_OK;
+  const int ntiles = tc_tiles(N);
+  int64_t* lin = nullptr;
+  uint8_t* bad = nullptr;
+  float* tilemin = nullptr;
+  double* bound = nullptr;
+  SFC_TRY(pmalloc(&lin, sizeof(int64_t) * Q, st));
+  SFC_TRY(pmalloc(&bad, Q, st));
+  SFC_TRY(pmalloc(&tilemin, sizeof(float) * Q * ntiles, st));
+  SFC_TRY(pmalloc(&bound, sizeof(double) * Q, st));
+  const unsigned qb = (unsigned)((Q + 255) / 256);
+  count_launch();
+  k_centre_lin<<<qb, 256, 0, st>>>(centres, Q, g, lin, status_word());
+  count_launch();
+  k_centre_fix<<<qb, 256, 0, st>>>(lin, Q, g, bad);
+  SFC_CHECK(tc_prescore(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, nullptr, bound, st));
+  const size_t shm = (size_t)g.n * 20 + (size_t)g.P + 16;
+  if (weighted) {
+    if (shm > 48 * 1024)
+      SFC_TRY(cudaFuncSetAttribute(k_tc_select<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    count_launch();
+    k_tc_select<true><<<(unsigned)Q, kFsThreads, shm, st>>>(grid, cur_mask, g, dict, N, eoff_all, weights, lin,
+                                                             tilemin, ntiles, bound, pick, cost, nsel);
+  } else {
+    if (shm > 48 * 1024)
+      SFC_TRY(cudaFuncSetAttribute(k_tc_select<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    count_launch();
+    k_tc_select<false><<<(unsigned)Q, kFsThreads, shm, st>>>(grid, cur_mask, g, dict, N, eoff_all, weights, lin,
+                                                              tilemin, ntiles, bound, pick, cost, nsel);
+  }
+  count_launch();
+  k_mark_bad<<<qb, 256, 0, st>>>(bad, Q, pick, cost);
+  SFC_TRY(cudaGetLastError());
+  cudaFreeAsync(lin, st);
+  cudaFreeAsync(bad, st);
+  cudaFreeAsync(tilemin, st);
+  cudaFreeAsync(bound, st);
+  return SFC_OK;
+}
+
+// All Q x N pre-scores (checking): scores (device, Q*N), bound (device, Q).
+int tc_prescores_all(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
+                     const int* eoff_all, const float* weights, const int32_t* centres, int64_t Q, float* scores,
+                     double* bound, cudaStream_t st) {
+  if (Q <= 0) return SFC_OK;
+  const int ntiles = tc_tiles(N);
+  int64_t* lin = nullptr;
+  uint8_t* bad = nullptr;
+  float* tilemin = nullptr;
+  SFC_TRY(pmalloc(&lin, sizeof(int64_t) * Q, st));
+  SFC_TRY(pmalloc(&bad, Q, st));
+  SFC_TRY(pmalloc(&tilemin, sizeof(float) * Q * ntiles, st));
+  const unsigned qb = (unsigned)((Q + 255) / 256);
+  count_launch();
+  k_centre_lin<<<qb, 256, 0, st>>>(centres, Q, g, lin, status_word());
+  count_launch();
+  k_centre_fix<<<qb, 256, 0, st>>>(lin, Q, g, bad);
+  SFC_CHECK(tc_prescore(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, scores, bound, st));
+  cudaFreeAsync(lin, st);
+  cudaFreeAsync(bad, st);
+  cudaFreeAsync(tilemin, st);
+  return SFC_OK;
 }
 
 int fullscan_batch(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,

@@ -1,0 +1,521 @@
+// k_tc.cu -- the full scan's pre-score as a tensor-core GEMM (tcgen05, sm_103a).
+//
+// The masked cost expands as cost(q, j) = sum m w t'^2 - 2 sum m w t' p'_j +
+// sum m w p'_j^2 (values centred per channel), so the pre-score
+//     s(q, j) = sum_e [ (-2 m w t')_e p'_je + (m w)_e (p'_je)^2 ]
+// is a dot product of a query row a(q) = [-2 m w t' ; m w] with a dictionary row
+// b(j) = [p' ; p'^2] and differs from the cost by a per-query constant: a GEMM
+// when many queries share the dictionary.  FP16 operands with FP32 accumulation;
+// every operand is split into a high and a low FP16 part and the three leading
+// products (hi*hi, hi*lo, lo*hi) are concatenated along K, so the operand
+// rounding error is ~3 u16^2 of sum |a b| and the FP32 accumulation dominates.
+//
+// Kernel structure (one 128 x 256 output tile per CTA): warp 0 issues TMA loads
+// (128-byte swizzle) of the A and B K-slices into a 4-stage shared-memory ring;
+// warp 1 allocates 256 TMEM columns and issues tcgen05.mma (M = 128, N = 256,
+// K = 16) from one thread, committing each stage back to its "empty" barrier;
+// warps 2-5 wait for the last commit, read their 32 TMEM lanes each with
+// tcgen05.ld and write the minimum pre-score of their row over the tile's valid
+// columns.  Every wait is bounded: on timeout the CTA raises ST_TIMEOUT and a
+// launch-wide abort flag (CTAs that start later skip their tile), drains what it
+// issued (again bounded), frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace sfc {
+
+namespace {
+
+constexpr int kBM = 128, kBN = 256, kBK = 64, kStages = 4;
+constexpr int kTcThreads = 192;
+constexpr uint32_t kStageA = kBM * kBK * 2, kStageB = kBN * kBK * 2;  // bytes
+constexpr long long kWaitLimit = 1ll << 22;  // polls (>= 0.1 s with the back-off)
+
+__device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// bounded wait for the phase with the given parity; false on timeout
+__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < kWaitLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (it > 64) __nanosleep(32);
+  }
+  return false;
+}
+
+__device__ inline void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile stored with the 128-byte
+// swizzle (rows of 64 FP16 = 128 B, 8-row groups 1024 B apart).
+__device__ inline uint64_t smem_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);  // start address, 16-byte units
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for this layout), 16 B
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                   // descriptor version of this architecture
+  d |= (uint64_t)2 << 61;                   // layout: 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: D = F32, A = B = F16, both K-major, N = 256, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(kBN >> 3) << 17) |
+                            ((uint32_t)(kBM >> 4) << 24);
+
+__device__ inline void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc));
+}
+__device__ inline void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+struct TcArgs {
+  int64_t Q, N;        // real rows of A / B
+  int kblocks;         // K' / 64
+  int ntiles;          // ceil(N / 256)
+  int n_base;          // first dictionary tile of this launch
+  float* tilemin;      // [Q][ntiles]
+  float* scores;       // optional [Q][N] (checking only)
+  uint32_t* status;
+  int* abort_all;      // set by a CTA that timed out; later CTAs skip their tile
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const __grid_constant__ CUtensorMap mapA,
+                                                           const __grid_constant__ CUtensorMap mapB, TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte aligned stage buffers (the swizzle pattern repeats every 1024 B)
+  unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = base;                              // kStages * kStageA
+  unsigned char* sB = base + kStages * kStageA;          // kStages * kStageB
+  __shared__ uint64_t full_bar[kStages], empty_bar[kStages], done_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag, s_issued, s_consumed;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m_tile = blockIdx.x, n_tile = a.n_base + (int)blockIdx.y;
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = *(volatile int*)a.abort_all;
+  __syncthreads();
+  if (s_skip) return;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    s_issued = 0;
+    s_consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(256));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+
+  int issued_tma = 0, issued_mma = 0;
+  if (warp == 0 && lane == 0) {
+    // producer: K-block kb goes to stage kb % kStages
+    for (int kb = 0; kb < a.kblocks; ++kb) {
+      const int s = kb % kStages;
+      if (kb >= kStages && !mbar_wait(&empty_bar[s], ((kb / kStages) - 1) & 1)) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      if (*(volatile int*)&abort_flag) break;
+      mbar_expect_tx(&full_bar[s], kStageA + kStageB);
+      tma_load_2d(sA + s * kStageA, &mapA, kb * kBK, m_tile * kBM, &full_bar[s]);
+      tma_load_2d(sB + s * kStageB, &mapB, kb * kBK, n_tile * kBN, &full_bar[s]);
+      ++issued_tma;
+    }
+    s_issued = issued_tma;
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    for (int kb = 0; kb < a.kblocks; ++kb) {
+      const int s = kb % kStages;
+      if (!mbar_wait(&full_bar[s], (kb / kStages) & 1) || *(volatile int*)&abort_flag) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t a0 = smem_u32(sA + s * kStageA), b0 = smem_u32(sB + s * kStageB);
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk) {
+        // a K step of 16 FP16 = 32 bytes inside the 128-byte swizzled rows
+        tc_mma(tmem, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), (kb | kk) ? 1u : 0u);
+      }
+      tc_commit(&empty_bar[s]);
+      ++issued_mma;
+    }
+    s_consumed = issued_mma;
+    tc_commit(&done_bar);  // arrives when every MMA issued above has completed
+  }
+  __syncwarp();
+  // epilogue warps 2..5: TMEM lanes 32 * (warp % 4) ..
+  if (warp >= 2) {
+    // warp-uniform outcome (tcgen05.ld below is a whole-warp instruction)
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0));
+    if (!ok) atomicExch(&abort_flag, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int quarter = warp & 3;
+    const int64_t row = (int64_t)m_tile * kBM + quarter * 32 + lane;
+    float mn = INFINITY;
+    const int64_t col0 = (int64_t)n_tile * kBN;
+    if (ok) {
+#pragma unroll 1
+      for (int c = 0; c < kBN; c += 32) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+              "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+              "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int64_t col = col0 + c + i;
+          const float v = __uint_as_float(r[i]);
+          if (col < a.N) {
+            mn = fminf(mn, v);
+            if (a.scores && row < a.Q) a.scores[row * a.N + col] = v;
+          }
+        }
+      }
+      if (row < a.Q) a.tilemin[row * a.ntiles + n_tile] = mn;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (abort_flag && threadIdx.x == 0) {
+    // drain the TMA loads issued but not consumed (bounded); the MMAs issued
+    // were covered by the done barrier the epilogue waited on
+    atomicOr(a.status, ST_TIMEOUT);
+    atomicExch(a.abort_all, 1);
+    for (int kb = s_consumed; kb < s_issued; ++kb) mbar_wait(&full_bar[kb % kStages], (kb / kStages) & 1);
+  }
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+  }
+}
+
+// ----------------------------------------------------------------------------
+// operand rows
+// ----------------------------------------------------------------------------
+__device__ inline void split16(float v, __half& hi, __half& lo) {
+  hi = __float2half_rn(v);
+  lo = __float2half_rn(v - __half2float(hi));
+}
+
+// A row of query q: K' = 6n layout [a1h a2h | a1h a2h | a1l a2l] (each part n
+// values; a1 = -2 m w t', a2 = m w), zero padding to Kp.  bound[q] = E_q, a
+// bound of |s_hat(q, j) - s(q, j)| valid for every dictionary row j, from
+// |p'| <= pmax[c]:
+//   M = sum_e m (|a1| pmax + |a2| pmax^2),  S = sum_e m (|a1| + |a2| + pmax + pmax^2)
+//   E_q = 3.01 u16^2 M        (hi/lo splitting: the dropped lo*lo term and the
+//                              rounding of the lo parts, relative)
+//       + 2^-24 S + 2^-47 n   (FP16 subnormal spacing of the lo parts, absolute)
+//       + (8 K' (1 + 3 u16) + 4) u32 M
+//                             (FP32 accumulation over K' products, eight times
+//                              the sequential bound to cover blocked and
+//                              truncating accumulation; plus the FP32 rounding
+//                              of the centred operands)
+// Unknown pixels contribute nothing: their a parts are exactly zero.
+__global__ void k_tc_prep_A(const float* __restrict__ grid, const uint8_t* __restrict__ mask, Geo g,
+                            const int64_t* __restrict__ centre_lin, int64_t Q, const int* __restrict__ eoff,
+                            const float* __restrict__ w, const float* __restrict__ mu, const float* __restrict__ pmax,
+                            int Kp, __half* __restrict__ A, double* __restrict__ bound) {
+  const int64_t q = blockIdx.x;
+  const int n = g.n, ch = g.ch;
+  __shared__ double red[2][8];
+  double msum = 0.0, ssum = 0.0;
+  __half* row = A + q * Kp;
+  for (int e = 6 * n + threadIdx.x; e < Kp; e += blockDim.x) row[e] = __float2half_rn(0.0f);
+  if (q < Q) {
+    const int64_t tc = centre_lin[q];
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int c = e % ch;
+      const float k = mask[tc + eoff[e - c] / ch] ? 1.0f : 0.0f;
+      const float tp = grid[tc * ch + eoff[e]] - mu[c];
+      const float a1 = -2.0f * k * w[c] * tp, a2 = k * w[c];
+      __half a1h, a1l, a2h, a2l;
+      split16(a1, a1h, a1l);
+      split16(a2, a2h, a2l);
+      row[e] = a1h;
+      row[n + e] = a2h;
+      row[2 * n + e] = a1h;
+      row[3 * n + e] = a2h;
+      row[4 * n + e] = a1l;
+      row[5 * n + e] = a2l;
+      if (k != 0.0f) {
+        const double pm = pmax[c];
+        msum += (double)fabsf(a1) * pm + (double)fabsf(a2) * pm * pm;
+        ssum += (double)fabsf(a1) + (double)fabsf(a2) + pm + pm * pm;
+      }
+    }
+  } else {
+    for (int e = threadIdx.x; e < 6 * n; e += blockDim.x) row[e] = __float2half_rn(0.0f);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    msum += __shfl_xor_sync(0xffffffffu, msum, o);
+    ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = msum;
+    red[1][threadIdx.x >> 5] = ssum;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && q < Q) {
+    double m = 0.0, sa = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      m += red[0][i];
+      sa += red[1][i];
+    }
+    const double u16 = 4.8828125e-4, u32 = 5.9604644775390625e-8;
+    const double Kq = 6.0 * n;
+    bound[q] = 3.01 * u16 * u16 * m + 0x1p-24 * sa + 0x1p-47 * n + (8.0 * Kq * (1.0 + 3.0 * u16) + 4.0) * u32 * m;
+  }
+}
+
+// B row of dictionary entry j: [b1h b2h | b1l b2l | b1h b2h] with b1 = p',
+// b2 = p'^2; one block per row, zero rows past N.
+__global__ void k_tc_prep_B(const float* __restrict__ grid, const uint32_t* __restrict__ dict, int64_t N,
+                            int64_t Npad, Geo g, const int* __restrict__ eoff, const float* __restrict__ mu, int Kp,
+                            __half* __restrict__ B) {
+  const int n = g.n, ch = g.ch;
+  for (int64_t j = blockIdx.x; j < Npad; j += gridDim.x) {
+    __half* row = B + j * Kp;
+    if (j < N) {
+      const int64_t sb = (int64_t)dict[j] * ch;
+      for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const float p = grid[sb + eoff[e]] - mu[e % ch];
+        __half h1, l1, h2, l2;
+        split16(p, h1, l1);
+        split16(p * p, h2, l2);
+        row[e] = h1;
+        row[n + e] = h2;
+        row[2 * n + e] = l1;
+        row[3 * n + e] = l2;
+        row[4 * n + e] = h1;
+        row[5 * n + e] = h2;
+      }
+      for (int e = 6 * n + threadIdx.x; e < Kp; e += blockDim.x) row[e] = __float2half_rn(0.0f);
+    } else {
+      for (int e = threadIdx.x; e < Kp; e += blockDim.x) row[e] = __float2half_rn(0.0f);
+    }
+  }
+}
+
+// per-channel minimum and maximum of the grid (order-preserving integer codes)
+__device__ inline unsigned f2ord(float v) {
+  const unsigned u = __float_as_uint(v);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__global__ void k_tc_range(const float* __restrict__ grid, int64_t npix, int ch, unsigned* __restrict__ lo,
+                           unsigned* __restrict__ hi) {
+  for (int c = 0; c < ch; ++c) {
+    unsigned l = 0xFFFFFFFFu, h = 0u;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix; i += (int64_t)gridDim.x * blockDim.x) {
+      const unsigned o = f2ord(grid[i * ch + c]);
+      l = min(l, o);
+      h = max(h, o);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      l = min(l, __shfl_xor_sync(0xffffffffu, l, o));
+      h = max(h, __shfl_xor_sync(0xffffffffu, h, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&lo[c], l);
+      atomicMax(&hi[c], h);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// host side: tensor maps through the driver entry point (no libcuda link)
+// ----------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+int make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols, uint32_t box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is not available");
+    return SFC_EUNSUPPORTED;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return SFC_ECUDA;
+  }
+  return SFC_OK;
+}
+
+}  // namespace
+
+// Pre-scores of Q queries against the N dictionary entries on the tensor cores.
+// Outputs tilemin [Q][ceil(N/256)] (and, when `scores` is non-null, all Q x N
+// pre-scores) and bound[Q]; the per-query constant sum m w t'^2 is not included.
+int tc_prescore(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
+                const int* eoff_all, const float* weights, const int64_t* centre_lin, int64_t Q, float* tilemin,
+                float* scores, double* bound, cudaStream_t st) {
+  const int n = g.n;
+  const int Kp = ((6 * n + kBK - 1) / kBK) * kBK;
+  const int64_t Qpad = ((Q + kBM - 1) / kBM) * kBM, Npad = ((N + kBN - 1) / kBN) * kBN;
+  const int ntiles = (int)(Npad / kBN);
+  const int64_t npix = g.X * g.Y * g.Z;
+  __half *A = nullptr, *B = nullptr;
+  unsigned* rng = nullptr;
+  float* cent = nullptr;
+  SFC_TRY(pmalloc(&rng, sizeof(unsigned) * 2 * g.ch, st));
+  SFC_TRY(pmalloc(&cent, sizeof(float) * 2 * g.ch, st));
+  SFC_TRY(cudaMemsetAsync(rng, 0xFF, sizeof(unsigned) * g.ch, st));
+  SFC_TRY(cudaMemsetAsync(rng + g.ch, 0, sizeof(unsigned) * g.ch, st));
+  count_launch();
+  k_tc_range<<<256, 256, 0, st>>>(grid, npix, g.ch, rng, rng + g.ch);
+  SFC_TRY(cudaGetLastError());
+  {
+    // centring at the channel mid-range (smallest max |value - mu|), and the
+    // range check of the FP16 operands (largest finite 65504): |p'| < 128 so
+    // p'^2 < 16384, and |2 w t'| and w below 30000
+    std::vector<unsigned> rh(2 * g.ch);
+    std::vector<float> wh(g.ch), ch_h(2 * g.ch);
+    SFC_TRY(cudaMemcpyAsync(rh.data(), rng, sizeof(unsigned) * 2 * g.ch, cudaMemcpyDeviceToHost, st));
+    SFC_TRY(cudaMemcpyAsync(wh.data(), weights, sizeof(float) * g.ch, cudaMemcpyDeviceToHost, st));
+    SFC_TRY(cudaStreamSynchronize(st));
+    auto ord2f = [](unsigned o) {
+      const unsigned u = (o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o;
+      float f;
+      std::memcpy(&f, &u, sizeof(float));
+      return f;
+    };
+    bool ok = true;
+    for (int c = 0; c < g.ch; ++c) {
+      const float lo = ord2f(rh[c]), hi = ord2f(rh[g.ch + c]);
+      const float m = 0.5f * lo + 0.5f * hi;
+      const float pm = std::fmax(std::fabs(hi - m), std::fabs(lo - m));
+      ch_h[c] = m;
+      ch_h[g.ch + c] = pm;
+      ok = ok && std::isfinite(lo) && std::isfinite(hi) && pm < 128.0f && wh[c] < 30000.0f &&
+           2.0f * wh[c] * pm < 30000.0f;
+    }
+    if (!ok) {
+      cudaFreeAsync(rng, st);
+      cudaFreeAsync(cent, st);
+      set_error("grid values or weights out of range for the FP16 tensor-core pre-score (need finite values, "
+                "max |value - mid-range| < 128, weights and 2 w |value - mid-range| < 30000; use SFC_FP32)");
+      return SFC_EINVAL;
+    }
+    SFC_TRY(cudaMemcpyAsync(cent, ch_h.data(), sizeof(float) * 2 * g.ch, cudaMemcpyHostToDevice, st));
+  }
+  const float* mu = cent;
+  const float* pmax = cent + g.ch;
+  SFC_TRY(pmalloc(&A, sizeof(__half) * Qpad * Kp, st));
+  SFC_TRY(pmalloc(&B, sizeof(__half) * Npad * Kp, st));
+  count_launch();
+  k_tc_prep_A<<<(unsigned)Qpad, 256, 0, st>>>(grid, cur_mask, g, centre_lin, Q, eoff_all, weights, mu, pmax, Kp,
+                                               A, bound);
+  count_launch();
+  k_tc_prep_B<<<(unsigned)std::min<int64_t>(Npad, 152 * 64), 128, 0, st>>>(grid, dict, N, Npad, g, eoff_all, mu, Kp,
+                                                                            B);
+  SFC_TRY(cudaGetLastError());
+  CUtensorMap mapA, mapB;
+  SFC_CHECK(make_map(&mapA, A, Qpad, Kp, kBM));
+  SFC_CHECK(make_map(&mapB, B, Npad, Kp, kBN));
+  int* abort_all = nullptr;
+  SFC_TRY(pmalloc(&abort_all, sizeof(int), st));
+  SFC_TRY(cudaMemsetAsync(abort_all, 0, sizeof(int), st));
+  TcArgs a;
+  a.abort_all = abort_all;
+  a.Q = Q;
+  a.N = N;
+  a.kblocks = Kp / kBK;
+  a.ntiles = ntiles;
+  a.tilemin = tilemin;
+  a.scores = scores;
+  a.status = status_word();
+  const size_t shm = (size_t)kStages * (kStageA + kStageB) + 1024;
+  SFC_TRY(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  // the dictionary tiles on grid y (at most 65535 per launch); the query tiles
+  // of one dictionary tile are neighbours in launch order, so its B tile is
+  // read from HBM once and from L2 after that
+  for (int nb = 0; nb < ntiles; nb += 65535) {
+    a.n_base = nb;
+    const int ny = std::min(ntiles - nb, 65535);
+    count_launch();
+    k_tc_gemm<<<dim3((unsigned)(Qpad / kBM), (unsigned)ny), kTcThreads, shm, st>>>(mapA, mapB, a);
+    SFC_TRY(cudaGetLastError());
+  }
+  cudaFreeAsync(A, st);
+  cudaFreeAsync(B, st);
+  cudaFreeAsync(rng, st);
+  cudaFreeAsync(cent, st);
+  cudaFreeAsync(abort_all, st);
+  return SFC_OK;
+}
+
+int tc_tiles(int64_t N) { return (int)((N + kBN - 1) / kBN); }
+
+}  // namespace sfc

@@ -579,7 +579,53 @@ int fullscan_query_batch(const float* grid, const uint8_t* dict_mask, const uint
   }
   SFC_CHECK(upload_patch_tables(g, &eo, st));
   SFC_CHECK(upload(&wd, w.data(), w.size(), st));
-  int rc = fullscan_batch(g, grid, cur_mask, dict, N, eo, wd, weighted, centres, nullptr, Q, pick, cost, st);
+  int rc;
+  if (p->precision == SFC_FP16)
+    rc = fullscan_batch_tc(g, grid, cur_mask, dict, N, eo, wd, weighted, centres, Q, pick, cost, nullptr, st);
+  else if (p->precision == SFC_FP32)
+    rc = fullscan_batch(g, grid, cur_mask, dict, N, eo, wd, weighted, centres, nullptr, Q, pick, cost, st);
+  else {
+    set_error("fullscan_query_batch: precision must be SFC_FP32 or SFC_FP16");
+    rc = SFC_EUNSUPPORTED;
+  }
+  cudaFreeAsync(dict, st);
+  cudaFreeAsync(eo, st);
+  cudaFreeAsync(wd, st);
+  return rc;
+}
+
+int sfc_tc_prescores(const float* grid, const uint8_t* dict_mask, const uint8_t* cur_mask, const sfc_grid* gp,
+                     const sfc_params* p, const int32_t* centres, int64_t Q, float* scores, double* bound,
+                     int64_t* N_out, void* stream) {
+  g_err.clear();
+  if (!p || Q < 0 || !N_out) {
+    set_error("sfc_tc_prescores: NULL params/N_out or negative Q");
+    return SFC_EINVAL;
+  }
+  if (!grid || !dict_mask || !cur_mask || (Q > 0 && (!centres || !scores || !bound))) {
+    set_error("sfc_tc_prescores: NULL pointer");
+    return SFC_EINVAL;
+  }
+  SFC_CHECK(check_device());
+  Geo g;
+  SFC_CHECK(make_geo(gp, p->K, &g));
+  std::vector<float> w = weights_of(p, g.ch);
+  SFC_CHECK(check_weights(w));
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t* dict = nullptr;
+  int64_t N = 0;
+  int* eo = nullptr;
+  float* wd = nullptr;
+  SFC_CHECK(dict_extract(dict_mask, g, st, &dict, &N));
+  *N_out = N;
+  if (N <= 0) {
+    if (dict) cudaFreeAsync(dict, st);
+    set_error("the dictionary is empty (no fully known patch)");
+    return SFC_EINVAL;
+  }
+  SFC_CHECK(upload_patch_tables(g, &eo, st));
+  SFC_CHECK(upload(&wd, w.data(), w.size(), st));
+  int rc = tc_prescores_all(g, grid, cur_mask, dict, N, eo, wd, centres, Q, scores, bound, st);
   cudaFreeAsync(dict, st);
   cudaFreeAsync(eo, st);
   cudaFreeAsync(wd, st);

@@ -18,13 +18,13 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsfc.so")
 
 SFC_OK, SFC_EINVAL, SFC_ENOMEM, SFC_ECUDA, SFC_ETIMEOUT, SFC_EUNSUPPORTED, SFC_EDEVICE = 0, -1, -2, -3, -4, -5, -6
 SFC_SELECT_ALL, SFC_SELECT_BEST = 0, 1
-SFC_FP32, SFC_BF16 = 0, 1
+SFC_FP32, SFC_BF16, SFC_FP16 = 0, 1, 2
 SFC_PRIO_CONFIDENCE, SFC_PRIO_CRIMINISI = 0, 1
 SFC_MODE_FULLSCAN, SFC_MODE_SFC = 0, 1
 
 EXPORTS = ["sfc_params_default", "sfc_index_build", "sfc_index_destroy", "sfc_index_info", "sfc_index_export",
            "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "fullscan_query_batch_static",
-           "inpaint_run", "sfc_status", "sfc_launch_count", "sfc_trace", "sfc_trace_read", "sfc_last_error"]
+           "sfc_tc_prescores", "inpaint_run", "sfc_status", "sfc_launch_count", "sfc_trace", "sfc_trace_read", "sfc_last_error"]
 TRACE_PHASES = ("dictionary", "moments", "eigen", "finalize", "project_keys", "sort")
 
 
@@ -62,6 +62,8 @@ def lib():
         L.fullscan_query_batch.argtypes = [vp, vp, vp, C.POINTER(sfc_grid), C.POINTER(sfc_params), vp, i64, vp, vp,
                                            vp]
         L.fullscan_query_batch_static.argtypes = list(L.fullscan_query_batch.argtypes)
+        L.sfc_tc_prescores.argtypes = [vp, vp, vp, C.POINTER(sfc_grid), C.POINTER(sfc_params), vp, i64, vp, vp,
+                                       C.POINTER(i64), vp]
         L.inpaint_run.argtypes = [vp, vp, C.POINTER(sfc_grid), C.POINTER(sfc_params), i32, i64, vp,
                                   C.POINTER(i64), vp]
         L.sfc_status.argtypes = [vp]
@@ -74,7 +76,7 @@ def lib():
         L.sfc_trace_read.restype = C.c_int
         for name in ["sfc_index_build", "sfc_index_destroy", "sfc_index_info", "sfc_index_export",
                      "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "fullscan_query_batch_static",
-                     "inpaint_run", "sfc_status"]:
+                     "sfc_tc_prescores", "inpaint_run", "sfc_status"]:
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -222,13 +224,14 @@ def sfc_query_candidates(ix: Index, grid: torch.Tensor, cur_mask: torch.Tensor, 
 
 
 def fullscan_query_batch(grid: torch.Tensor, dict_mask: torch.Tensor, cur_mask: torch.Tensor,
-                         centres: torch.Tensor, K: int, ch_weights=None, pick=None, cost=None):
+                         centres: torch.Tensor, K: int, ch_weights=None, pick=None, cost=None,
+                         precision: int = SFC_FP32):
     grid = _dev(grid, torch.float32)
     dict_mask = _dev(dict_mask, torch.uint8)
     cur_mask = _dev(cur_mask, torch.uint8)
     centres = _dev(centres, torch.int32)
     Q = centres.shape[0]
-    P = Params(K=K, ch_weights=ch_weights)
+    P = Params(K=K, ch_weights=ch_weights, precision=precision)
     g = make_grid(grid)
     if pick is None:
         pick = torch.empty(Q, dtype=torch.int64, device=grid.device)
@@ -237,6 +240,26 @@ def fullscan_query_batch(grid: torch.Tensor, dict_mask: torch.Tensor, cur_mask: 
     _check(lib().fullscan_query_batch(_ptr(grid), _ptr(dict_mask), _ptr(cur_mask), C.byref(g), C.byref(P.p),
                                       _ptr(centres), Q, _ptr(pick), _ptr(cost), _stream()), "fullscan_query_batch")
     return pick, cost
+
+
+def sfc_tc_prescores(grid: torch.Tensor, dict_mask: torch.Tensor, cur_mask: torch.Tensor, centres: torch.Tensor,
+                     K: int, N: int, ch_weights=None):
+    """All tensor-core pre-scores (Q x N) and their bounds E_q, for checking."""
+    grid = _dev(grid, torch.float32)
+    dict_mask = _dev(dict_mask, torch.uint8)
+    cur_mask = _dev(cur_mask, torch.uint8)
+    centres = _dev(centres, torch.int32)
+    Q = centres.shape[0]
+    P = Params(K=K, ch_weights=ch_weights, precision=SFC_FP16)
+    g = make_grid(grid)
+    scores = torch.empty((Q, N), dtype=torch.float32, device=grid.device)
+    bound = torch.empty(Q, dtype=torch.float64, device=grid.device)
+    n_out = C.c_int64()
+    _check(lib().sfc_tc_prescores(_ptr(grid), _ptr(dict_mask), _ptr(cur_mask), C.byref(g), C.byref(P.p),
+                                  _ptr(centres), Q, _ptr(scores), _ptr(bound), C.byref(n_out), _stream()),
+           "sfc_tc_prescores")
+    assert n_out.value == N
+    return scores, bound
 
 
 def fullscan_query_batch_static(grid: torch.Tensor, dict_mask: torch.Tensor, cur_mask: torch.Tensor,
