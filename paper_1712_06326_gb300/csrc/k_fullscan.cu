@@ -260,10 +260,17 @@ __global__ void __launch_bounds__(kFsThreads) k_fs_band(const float* __restrict_
   }
 }
 
-// Exact pass after the tensor-core pre-score: every 256-entry tile whose
-// pre-score minimum lies within 2 E_q of the smallest one can hold the exact
-// argmin (|s_hat - s| <= E_q for every entry); the entries of those tiles are
-// scored with the FP32 cost of k_fs_band, then the usual band / FP64 decision.
+// Exact pass after the tensor-core pre-score: a group of 32 dictionary entries
+// can hold the exact argmin only if its pre-score minimum lies within 2 E_q of
+// the smallest one (|s_hat - s| <= E_q for every entry).  One CTA per query;
+// warp w takes the selected groups of the 1024-entry chunks w, w + 8, ...; each
+// lane scores one entry of a group with the FP32 cost of k_fs_band and keeps
+// the entries within the FP32 band of its own running minimum (at most
+// kLaneCands, pruned as the minimum falls; more sends the query through a
+// second pass).  The band of the CTA's minimum is a subset of what the lanes
+// kept, so the usual band / FP64 decision follows.
+constexpr int kLaneCands = 4;
+
 template <bool WEIGHTED>
 __global__ void __launch_bounds__(kFsThreads) k_tc_select(const float* __restrict__ grid,
                                                           const uint8_t* __restrict__ mask, Geo g,
@@ -271,7 +278,7 @@ __global__ void __launch_bounds__(kFsThreads) k_tc_select(const float* __restric
                                                           const int* __restrict__ eoff_all,
                                                           const float* __restrict__ weights,
                                                           const int64_t* __restrict__ centre_lin,
-                                                          const float* __restrict__ tilemin, int ntiles,
+                                                          const float* __restrict__ submin, int64_t nsub,
                                                           const double* __restrict__ bound,
                                                           int64_t* __restrict__ pick, float* __restrict__ cost,
                                                           int* __restrict__ nsel) {
@@ -283,7 +290,7 @@ __global__ void __launch_bounds__(kFsThreads) k_tc_select(const float* __restric
   float* we = reinterpret_cast<float*>(eo + n);
   uint8_t* tm = reinterpret_cast<uint8_t*>(we + n);
   __shared__ float red[kFsThreads / 32];
-  __shared__ int s_cnt, s_nsel;
+  __shared__ int s_cnt, s_nsel, s_over;
   __shared__ int64_t s_j[kBandCap];
   __shared__ float s_c[kBandCap];
   const int64_t q = blockIdx.x;
@@ -299,49 +306,98 @@ __global__ void __launch_bounds__(kFsThreads) k_tc_select(const float* __restric
     am[e] = make_float2(k, k * t);
   }
   for (int pp = threadIdx.x; pp < P; pp += kFsThreads) tm[pp] = mask[tc + eoff_all[pp * ch] / ch];
-  // smallest tile minimum
+  // smallest group minimum
+  const int64_t ngrp = (N + 31) / 32;
+  const float* sm = submin + q * nsub;
   float mh = INFINITY;
-  for (int t = threadIdx.x; t < ntiles; t += kFsThreads) mh = fminf(mh, tilemin[q * ntiles + t]);
+  for (int64_t t = threadIdx.x; t < ngrp; t += kFsThreads) mh = fminf(mh, sm[t]);
   mh = warp_min(mh);
   if (lane == 0) red[warp] = mh;
   if (threadIdx.x == 0) {
     s_cnt = 0;
     s_nsel = 0;
+    s_over = 0;
   }
   __syncthreads();
   mh = red[0];
   for (int w = 1; w < kFsThreads / 32; ++w) mh = fminf(mh, red[w]);
   const double thr = (double)mh + 2.0001 * bound[q] + 1e-30;
   __syncthreads();
-  // pass A: the FP32 minimum over the selected tiles
-  float mymin = INFINITY;
-  int mysel = 0;
-  for (int t = 0; t < ntiles; ++t) {
-    if ((double)tilemin[q * ntiles + t] > thr) continue;  // uniform across the CTA
-    ++mysel;
-    const int64_t j = (int64_t)t * kFsThreads + threadIdx.x;
-    if (j < N) mymin = fminf(mymin, cost32_one<WEIGHTED>(grid, (int64_t)dict[j] * ch, am, eo, we, n));
+  // fn(j) for every entry j < N of every selected group of this warp's chunks
+  auto each_selected = [&](auto&& fn) {
+    for (int64_t base = (int64_t)warp * 32; base < ngrp; base += kFsThreads) {
+      const int64_t gi = base + lane;
+      unsigned bal = __ballot_sync(0xffffffffu, gi < ngrp && (double)sm[gi] <= thr);
+      while (bal) {
+        const int b = __ffs(bal) - 1;
+        bal &= bal - 1;
+        const int64_t j = (base + b) * 32 + lane;
+        fn(j);
+      }
+    }
+  };
+  // single pass: running minimum and the entries within its band
+  float mt = INFINITY;
+  float cc[kLaneCands];
+  int64_t cj[kLaneCands];
+#pragma unroll
+  for (int i = 0; i < kLaneCands; ++i) {
+    cc[i] = INFINITY;
+    cj[i] = -1;
   }
-  mymin = warp_min(mymin);
-  if (lane == 0) red[warp] = mymin;
+  bool over = false;
+  int mysel = 0;
+  each_selected([&](int64_t j) {
+    ++mysel;
+    if (j >= N) return;
+    const float c = cost32_one<WEIGHTED>(grid, (int64_t)dict[j] * ch, am, eo, we, n);
+    if (c < mt) {
+      mt = c;
+      const float T = band_limit32(mt, n);
+#pragma unroll
+      for (int i = 0; i < kLaneCands; ++i)
+        if (cc[i] > T) cc[i] = INFINITY;
+    }
+    if (c <= band_limit32(mt, n)) {
+      bool placed = false;
+#pragma unroll
+      for (int i = 0; i < kLaneCands; ++i)
+        if (!placed && cc[i] == INFINITY) {
+          cc[i] = c;
+          cj[i] = j;
+          placed = true;
+        }
+      over |= !placed;
+    }
+  });
+  mt = warp_min(mt);
+  if (lane == 0) {
+    red[warp] = mt;
+    atomicAdd(&s_nsel, mysel);
+  }
+  if (over) s_over = 1;
   __syncthreads();
   float m32 = red[0];
   for (int w = 1; w < kFsThreads / 32; ++w) m32 = fminf(m32, red[w]);
-  if (threadIdx.x == 0 && nsel) nsel[q] = mysel;
+  if (threadIdx.x == 0 && nsel) nsel[q] = s_nsel;
   const float T = band_limit32(m32, n);
-  // pass B: the band members (usually one)
-  for (int t = 0; t < ntiles; ++t) {
-    if ((double)tilemin[q * ntiles + t] > thr) continue;
-    const int64_t j = (int64_t)t * kFsThreads + threadIdx.x;
-    if (j >= N) continue;
-    const float c32 = cost32_one<WEIGHTED>(grid, (int64_t)dict[j] * ch, am, eo, we, n);
-    if (c32 <= T) {
-      const int slot = atomicAdd(&s_cnt, 1);
-      if (slot < kBandCap) {
-        s_j[slot] = j;
-        s_c[slot] = c32;
-      }
+  auto push = [&](int64_t j, float c) {
+    const int slot = atomicAdd(&s_cnt, 1);
+    if (slot < kBandCap) {
+      s_j[slot] = j;
+      s_c[slot] = c;
     }
+  };
+  if (!s_over) {
+#pragma unroll
+    for (int i = 0; i < kLaneCands; ++i)
+      if (cc[i] <= T) push(cj[i], cc[i]);
+  } else {
+    each_selected([&](int64_t j) {
+      if (j >= N) return;
+      const float c = cost32_one<WEIGHTED>(grid, (int64_t)dict[j] * ch, am, eo, we, n);
+      if (c <= T) push(j, c);
+    });
   }
   __syncthreads();
   const int cnt = s_cnt;
@@ -355,32 +411,22 @@ __global__ void __launch_bounds__(kFsThreads) k_tc_select(const float* __restric
   double bc = INFINITY;
   int64_t bj = INT64_MAX;
   float bc32 = 0.0f;
+  auto consider = [&](int64_t j, float c32) {
+    const double c64 = exact_cost64(grid, (int64_t)dict[j] * ch, tv, tm, eo, P, ch, weights);
+    if (c64 < bc || (c64 == bc && j < bj)) {
+      bc = c64;
+      bj = j;
+      bc32 = c32;
+    }
+  };
   if (cnt <= kBandCap) {
-    for (int i = threadIdx.x; i < cnt; i += kFsThreads) {
-      const int64_t j = s_j[i];
-      const double c64 = exact_cost64(grid, (int64_t)dict[j] * ch, tv, tm, eo, P, ch, weights);
-      if (c64 < bc || (c64 == bc && j < bj)) {
-        bc = c64;
-        bj = j;
-        bc32 = s_c[i];
-      }
-    }
+    for (int i = threadIdx.x; i < cnt; i += kFsThreads) consider(s_j[i], s_c[i]);
   } else {
-    for (int t = 0; t < ntiles; ++t) {
-      if ((double)tilemin[q * ntiles + t] > thr) continue;
-      const int64_t j = (int64_t)t * kFsThreads + threadIdx.x;
-      if (j >= N) continue;
-      const int64_t sb = (int64_t)dict[j] * ch;
-      const float c32 = cost32_one<WEIGHTED>(grid, sb, am, eo, we, n);
-      if (c32 <= T) {
-        const double c64 = exact_cost64(grid, sb, tv, tm, eo, P, ch, weights);
-        if (c64 < bc || (c64 == bc && j < bj)) {
-          bc = c64;
-          bj = j;
-          bc32 = c32;
-        }
-      }
-    }
+    each_selected([&](int64_t j) {
+      if (j >= N) return;
+      const float c = cost32_one<WEIGHTED>(grid, (int64_t)dict[j] * ch, am, eo, we, n);
+      if (c <= T) consider(j, c);
+    });
   }
   for (int o = 16; o > 0; o >>= 1) {
     const double c2 = __shfl_xor_sync(0xffffffffu, bc, o);
@@ -510,25 +556,26 @@ int fullscan_single(const Geo& g, const float* grid, const uint8_t* cur_mask, co
 }
 
 int tc_prescore(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
-                const int* eoff_all, const float* weights, const int64_t* centre_lin, int64_t Q, float* tilemin,
+                const int* eoff_all, const float* weights, const int64_t* centre_lin, int64_t Q, float* submin,
                 float* scores, double* bound, cudaStream_t st);
-int tc_tiles(int64_t N);
+int64_t tc_subs(int64_t N);
 
 // The full scan with the tensor-core pre-score (precision SFC_FP16): pre-score
-// tile minima, then the exact pass over the tiles that can hold the argmin.
-// nsel (optional, device, Q ints) receives the number of tiles rescored.
+// minima of 32-entry groups, then the exact pass over the groups that can hold
+// the argmin.  nsel (optional, device, Q ints) receives the number of groups
+// rescored.
 int fullscan_batch_tc(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
                       const int* eoff_all, const float* weights, bool weighted, const int32_t* centres, int64_t Q,
                       int64_t* pick, float* cost, int* nsel, cudaStream_t st) {
   if (Q <= 0) return SFC_OK;
-  const int ntiles = tc_tiles(N);
+  const int64_t nsub = tc_subs(N);
   int64_t* lin = nullptr;
   uint8_t* bad = nullptr;
   float* tilemin = nullptr;
   double* bound = nullptr;
   SFC_TRY(pmalloc(&lin, sizeof(int64_t) * Q, st));
   SFC_TRY(pmalloc(&bad, Q, st));
-  SFC_TRY(pmalloc(&tilemin, sizeof(float) * Q * ntiles, st));
+  SFC_TRY(pmalloc(&tilemin, sizeof(float) * Q * nsub, st));
   SFC_TRY(pmalloc(&bound, sizeof(double) * Q, st));
   const unsigned qb = (unsigned)((Q + 255) / 256);
   count_launch();
@@ -542,13 +589,13 @@ int fullscan_batch_tc(const Geo& g, const float* grid, const uint8_t* cur_mask, 
       SFC_TRY(cudaFuncSetAttribute(k_tc_select<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     count_launch();
     k_tc_select<true><<<(unsigned)Q, kFsThreads, shm, st>>>(grid, cur_mask, g, dict, N, eoff_all, weights, lin,
-                                                             tilemin, ntiles, bound, pick, cost, nsel);
+                                                             tilemin, nsub, bound, pick, cost, nsel);
   } else {
     if (shm > 48 * 1024)
       SFC_TRY(cudaFuncSetAttribute(k_tc_select<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     count_launch();
     k_tc_select<false><<<(unsigned)Q, kFsThreads, shm, st>>>(grid, cur_mask, g, dict, N, eoff_all, weights, lin,
-                                                              tilemin, ntiles, bound, pick, cost, nsel);
+                                                              tilemin, nsub, bound, pick, cost, nsel);
   }
   count_launch();
   k_mark_bad<<<qb, 256, 0, st>>>(bad, Q, pick, cost);
@@ -565,13 +612,13 @@ int tc_prescores_all(const Geo& g, const float* grid, const uint8_t* cur_mask, c
                      const int* eoff_all, const float* weights, const int32_t* centres, int64_t Q, float* scores,
                      double* bound, cudaStream_t st) {
   if (Q <= 0) return SFC_OK;
-  const int ntiles = tc_tiles(N);
+  const int64_t nsub = tc_subs(N);
   int64_t* lin = nullptr;
   uint8_t* bad = nullptr;
   float* tilemin = nullptr;
   SFC_TRY(pmalloc(&lin, sizeof(int64_t) * Q, st));
   SFC_TRY(pmalloc(&bad, Q, st));
-  SFC_TRY(pmalloc(&tilemin, sizeof(float) * Q * ntiles, st));
+  SFC_TRY(pmalloc(&tilemin, sizeof(float) * Q * nsub, st));
   const unsigned qb = (unsigned)((Q + 255) / 256);
   count_launch();
   k_centre_lin<<<qb, 256, 0, st>>>(centres, Q, g, lin, status_word());

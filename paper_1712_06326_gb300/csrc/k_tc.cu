@@ -7,18 +7,23 @@
 // b(j) = [p' ; p'^2] and differs from the cost by a per-query constant: a GEMM
 // when many queries share the dictionary.  FP16 operands with FP32 accumulation;
 // every operand is split into a high and a low FP16 part and the three leading
-// products (hi*hi, hi*lo, lo*hi) are concatenated along K, so the operand
-// rounding error is ~3 u16^2 of sum |a b| and the FP32 accumulation dominates.
+// products are laid out along K as [lo*hi | hi*lo | hi*hi], six parts of n8
+// (n rounded up to 8) values each: the small products are accumulated first,
+// while the accumulator is still small, and the hi*hi products are shared
+// between two TMEM accumulators (K-blocks before / after kb_split) that the
+// epilogue adds, which keeps the accumulation error bound near 8 (2 n8 / 2) u32
+// of the products' magnitude.
 //
 // Kernel structure (one 128 x 256 output tile per CTA): warp 0 issues TMA loads
 // (128-byte swizzle) of the A and B K-slices into a 4-stage shared-memory ring;
-// warp 1 allocates 256 TMEM columns and issues tcgen05.mma (M = 128, N = 256,
+// warp 1 allocates 512 TMEM columns and issues tcgen05.mma (M = 128, N = 256,
 // K = 16) from one thread, committing each stage back to its "empty" barrier;
 // warps 2-5 wait for the last commit, read their 32 TMEM lanes each with
-// tcgen05.ld and write the minimum pre-score of their row over the tile's valid
-// columns.  Every wait is bounded: on timeout the CTA raises ST_TIMEOUT and a
-// launch-wide abort flag (CTAs that start later skip their tile), drains what it
-// issued (again bounded), frees its TMEM and returns.
+// tcgen05.ld, add the two accumulators and write the minimum pre-score of their
+// row over every 32 columns (valid columns only).  Every wait is bounded: on
+// timeout the CTA raises ST_TIMEOUT and a launch-wide abort flag (CTAs that
+// start later skip their tile), drains what it issued (again bounded), frees its
+// TMEM and returns.
 #include <cuda.h>
 #include <cuda_fp16.h>
 
@@ -98,12 +103,25 @@ __device__ inline void tc_commit(uint64_t* bar) {
                : "memory");
 }
 
+// 32 consecutive TMEM columns of this thread's lane (32x32b shape, 32 registers)
+__device__ inline void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
 struct TcArgs {
   int64_t Q, N;        // real rows of A / B
-  int kblocks;         // K' / 64
-  int ntiles;          // ceil(N / 256)
+  int kblocks;         // Kp / 64
+  int kb_split;        // first K-block of the second accumulator (== kblocks: none)
   int n_base;          // first dictionary tile of this launch
-  float* tilemin;      // [Q][ntiles]
+  int64_t nsub;        // 32-column groups per query row of submin (8 per tile)
+  float* submin;       // [Q][nsub] minimum over each 32 dictionary entries
   float* scores;       // optional [Q][N] (checking only)
   uint32_t* status;
   int* abort_all;      // set by a CTA that timed out; later CTAs skip their tile
@@ -139,7 +157,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const __grid_constant
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"(256));
+                 "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -173,10 +191,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const __grid_constant
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t a0 = smem_u32(sA + s * kStageA), b0 = smem_u32(sB + s * kStageB);
+      const bool second = kb >= a.kb_split;
+      const uint32_t d = tmem + (second ? 256u : 0u);
+      const bool first_block = kb == 0 || kb == a.kb_split;
 #pragma unroll
       for (int kk = 0; kk < kBK / 16; ++kk) {
         // a K step of 16 FP16 = 32 bytes inside the 128-byte swizzled rows
-        tc_mma(tmem, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), (kb | kk) ? 1u : 0u);
+        tc_mma(d, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), (first_block && kk == 0) ? 0u : 1u);
       }
       tc_commit(&empty_bar[s]);
       ++issued_mma;
@@ -193,34 +214,34 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const __grid_constant
     asm volatile("tcgen05.fence::after_thread_sync;");
     const int quarter = warp & 3;
     const int64_t row = (int64_t)m_tile * kBM + quarter * 32 + lane;
-    float mn = INFINITY;
     const int64_t col0 = (int64_t)n_tile * kBN;
+    const bool two = a.kb_split < a.kblocks;
     if (ok) {
-#pragma unroll 1
+      float mins[kBN / 32];
+#pragma unroll
       for (int c = 0; c < kBN; c += 32) {
-        uint32_t r[32];
+        uint32_t r[32], r2[32];
         const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-              "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-              "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-            : "r"(taddr));
+        tmem_ld32(taddr, r);
+        if (two) tmem_ld32(taddr + 256u, r2);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float mn = INFINITY;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const int64_t col = col0 + c + i;
-          const float v = __uint_as_float(r[i]);
+          const float v = two ? __fadd_rn(__uint_as_float(r[i]), __uint_as_float(r2[i])) : __uint_as_float(r[i]);
           if (col < a.N) {
             mn = fminf(mn, v);
             if (a.scores && row < a.Q) a.scores[row * a.N + col] = v;
           }
         }
+        mins[c / 32] = mn;
       }
-      if (row < a.Q) a.tilemin[row * a.ntiles + n_tile] = mn;
+      if (row < a.Q) {
+        float4* dst = reinterpret_cast<float4*>(a.submin + row * a.nsub + (int64_t)n_tile * (kBN / 32));
+        dst[0] = make_float4(mins[0], mins[1], mins[2], mins[3]);
+        dst[1] = make_float4(mins[4], mins[5], mins[6], mins[7]);
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -235,7 +256,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const __grid_constant
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
   }
 }
 
@@ -247,102 +268,151 @@ __device__ inline void split16(float v, __half& hi, __half& lo) {
   lo = __float2half_rn(v - __half2float(hi));
 }
 
-// A row of query q: K' = 6n layout [a1h a2h | a1h a2h | a1l a2l] (each part n
-// values; a1 = -2 m w t', a2 = m w), zero padding to Kp.  bound[q] = E_q, a
-// bound of |s_hat(q, j) - s(q, j)| valid for every dictionary row j, from
-// |p'| <= pmax[c]:
-//   M = sum_e m (|a1| pmax + |a2| pmax^2),  S = sum_e m (|a1| + |a2| + pmax + pmax^2)
-//   E_q = 3.01 u16^2 M        (hi/lo splitting: the dropped lo*lo term and the
-//                              rounding of the lo parts, relative)
-//       + 2^-24 S + 2^-47 n   (FP16 subnormal spacing of the lo parts, absolute)
-//       + (8 K' (1 + 3 u16) + 4) u32 M
-//                             (FP32 accumulation over K' products, eight times
-//                              the sequential bound to cover blocked and
-//                              truncating accumulation; plus the FP32 rounding
-//                              of the centred operands)
-// Unknown pixels contribute nothing: their a parts are exactly zero.
+// Layout of K (n8 = n rounded up to 8; part stride n8, zeros past n in each
+// part and past 6 n8 up to Kp):
+//   A row of query q:      [a1l a2l | a1h a2h | a1h a2h]   a1 = -2 m w t', a2 = m w
+//   B row of entry j:      [b1h b2h | b1l b2l | b1h b2h]   b1 = p', b2 = p'^2
+// so parts 0-3 hold the small cross products lo*hi and hi*lo, parts 4-5 the
+// hi*hi products.  K-blocks [0, kb_split) accumulate in TMEM columns 0..255,
+// the rest in columns 256..511.
+struct TcLayout {
+  int n8, Kp, kblocks, kb_split;
+};
+inline TcLayout tc_layout(int n) {
+  TcLayout L;
+  L.n8 = (n + 7) / 8 * 8;
+  L.Kp = (6 * L.n8 + kBK - 1) / kBK * kBK;
+  L.kblocks = L.Kp / kBK;
+  // the two accumulators take about half of the hi*hi products each
+  L.kb_split = std::min(L.kblocks, (5 * L.n8 + kBK / 2) / kBK);
+  if (L.kb_split < 1) L.kb_split = L.kblocks;
+  return L;
+}
+
+// bound[q] = E_q >= |s_hat(q, j) - s(q, j)| for every dictionary row j, with
+// |p'| <= pmax[c], u16 = 2^-11, u32 = 2^-24:
+//  * operand splitting: a = ah + al + da with |da| <= u16^2 |a| + 2^-25 (the
+//    low part may be an FP16 subnormal); dropping al*bl and the da, db terms
+//    costs <= 3.01 u16^2 M + 2^-24 S + 2^-47 n, where
+//      M = sum_e m (|a1| pmax + |a2| pmax^2),  S = sum_e m (|a1| + |a2| + pmax + pmax^2);
+//  * FP32 rounding of the centred operands (t - mu, w t', p - mu, p'^2):
+//    <= 4 u32 M;
+//  * accumulation: eight times the sequential FP32 bound (covers blocked and
+//    truncating accumulation), per accumulator r: steps before the hi*hi
+//    part (l_r of them) see partial sums <= SL = 2.02 u16 M + 2^-24 S (all
+//    small products), the h_r steps from there on <= SL + H_r (H_r: the hi*hi
+//    mass that accumulator holds, from the actual |a| and pmax); plus one
+//    rounding of acc0 + acc1:
+//      8 u32 sum_r [ l_r SL + h_r (SL + H_r) ] + 1.01 u32 (SL + H_0 + H_1).
+// Steps count every K position (padding included), as the hardware's blocked
+// accumulation rounds per instruction, not per nonzero product.
 __global__ void k_tc_prep_A(const float* __restrict__ grid, const uint8_t* __restrict__ mask, Geo g,
                             const int64_t* __restrict__ centre_lin, int64_t Q, const int* __restrict__ eoff,
                             const float* __restrict__ w, const float* __restrict__ mu, const float* __restrict__ pmax,
-                            int Kp, __half* __restrict__ A, double* __restrict__ bound) {
+                            TcLayout L, __half* __restrict__ A, double* __restrict__ bound) {
   const int64_t q = blockIdx.x;
-  const int n = g.n, ch = g.ch;
-  __shared__ double red[2][8];
-  double msum = 0.0, ssum = 0.0;
-  __half* row = A + q * Kp;
-  for (int e = 6 * n + threadIdx.x; e < Kp; e += blockDim.x) row[e] = __float2half_rn(0.0f);
-  if (q < Q) {
-    const int64_t tc = centre_lin[q];
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+  const int n = g.n, ch = g.ch, n8 = L.n8, Ks = L.kb_split * kBK;
+  __shared__ double red[4][8];
+  double msum = 0.0, ssum = 0.0, h0 = 0.0, h1 = 0.0;
+  __half* row = A + q * L.Kp;
+  const __half z = __float2half_rn(0.0f);
+  for (int e = 6 * n8 + threadIdx.x; e < L.Kp; e += blockDim.x) row[e] = z;
+  const int64_t tc = q < Q ? centre_lin[q] : 0;
+  for (int e = threadIdx.x; e < n8; e += blockDim.x) {
+    __half a1h = z, a1l = z, a2h = z, a2l = z;
+    if (q < Q && e < n) {
       const int c = e % ch;
       const float k = mask[tc + eoff[e - c] / ch] ? 1.0f : 0.0f;
       const float tp = grid[tc * ch + eoff[e]] - mu[c];
       const float a1 = -2.0f * k * w[c] * tp, a2 = k * w[c];
-      __half a1h, a1l, a2h, a2l;
       split16(a1, a1h, a1l);
       split16(a2, a2h, a2l);
-      row[e] = a1h;
-      row[n + e] = a2h;
-      row[2 * n + e] = a1h;
-      row[3 * n + e] = a2h;
-      row[4 * n + e] = a1l;
-      row[5 * n + e] = a2l;
       if (k != 0.0f) {
         const double pm = pmax[c];
-        msum += (double)fabsf(a1) * pm + (double)fabsf(a2) * pm * pm;
+        const double m1 = (double)fabsf(a1) * pm, m2 = (double)fabsf(a2) * pm * pm;
+        msum += m1 + m2;
         ssum += (double)fabsf(a1) + (double)fabsf(a2) + pm + pm * pm;
+        // hi*hi masses (|ah| <= |a| (1 + u16), |bh| <= pmax (1 + u16)) by accumulator
+        const double f = 1.0009770;  // > (1 + 2^-11)^2
+        if (4 * n8 + e < Ks) h0 += f * m1; else h1 += f * m1;
+        if (5 * n8 + e < Ks) h0 += f * m2; else h1 += f * m2;
       }
     }
-  } else {
-    for (int e = threadIdx.x; e < 6 * n; e += blockDim.x) row[e] = __float2half_rn(0.0f);
+    row[e] = a1l;
+    row[n8 + e] = a2l;
+    row[2 * n8 + e] = a1h;
+    row[3 * n8 + e] = a2h;
+    row[4 * n8 + e] = a1h;
+    row[5 * n8 + e] = a2h;
   }
   for (int o = 16; o > 0; o >>= 1) {
     msum += __shfl_xor_sync(0xffffffffu, msum, o);
     ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
+    h0 += __shfl_xor_sync(0xffffffffu, h0, o);
+    h1 += __shfl_xor_sync(0xffffffffu, h1, o);
   }
   if ((threadIdx.x & 31) == 0) {
     red[0][threadIdx.x >> 5] = msum;
     red[1][threadIdx.x >> 5] = ssum;
+    red[2][threadIdx.x >> 5] = h0;
+    red[3][threadIdx.x >> 5] = h1;
   }
   __syncthreads();
   if (threadIdx.x == 0 && q < Q) {
-    double m = 0.0, sa = 0.0;
+    double M = 0.0, Sa = 0.0, H0 = 0.0, H1 = 0.0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-      m += red[0][i];
-      sa += red[1][i];
+      M += red[0][i];
+      Sa += red[1][i];
+      H0 += red[2][i];
+      H1 += red[3][i];
     }
-    const double u16 = 4.8828125e-4, u32 = 5.9604644775390625e-8;
-    const double Kq = 6.0 * n;
-    bound[q] = 3.01 * u16 * u16 * m + 0x1p-24 * sa + 0x1p-47 * n + (8.0 * Kq * (1.0 + 3.0 * u16) + 4.0) * u32 * m;
+    const double u16 = 0x1p-11, u32 = 0x1p-24;
+    const double SL = 2.02 * u16 * M + 0x1p-24 * Sa;
+    const int K4 = 4 * n8;
+    const double l0 = min(Ks, K4), h0n = max(0, Ks - K4);
+    const double l1 = max(0, K4 - Ks), h1n = L.Kp - max(Ks, K4);
+    const double acc = 8.0 * u32 * (l0 * SL + h0n * (SL + H0) + l1 * SL + h1n * (SL + H1)) +
+                       1.01 * u32 * (SL + H0 + H1);
+    bound[q] = 3.01 * u16 * u16 * M + 0x1p-24 * Sa + 0x1p-47 * n + 4.0 * u32 * M + acc;
   }
 }
 
-// B row of dictionary entry j: [b1h b2h | b1l b2l | b1h b2h] with b1 = p',
-// b2 = p'^2; one block per row, zero rows past N.
+// B rows: one thread per 8 consecutive elements of one row (six 16-byte
+// stores), or per 8 zeros of the tail [6 n8, Kp).
 __global__ void k_tc_prep_B(const float* __restrict__ grid, const uint32_t* __restrict__ dict, int64_t N,
-                            int64_t Npad, Geo g, const int* __restrict__ eoff, const float* __restrict__ mu, int Kp,
-                            __half* __restrict__ B) {
-  const int n = g.n, ch = g.ch;
-  for (int64_t j = blockIdx.x; j < Npad; j += gridDim.x) {
-    __half* row = B + j * Kp;
-    if (j < N) {
-      const int64_t sb = (int64_t)dict[j] * ch;
-      for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        const float p = grid[sb + eoff[e]] - mu[e % ch];
-        __half h1, l1, h2, l2;
-        split16(p, h1, l1);
-        split16(p * p, h2, l2);
-        row[e] = h1;
-        row[n + e] = h2;
-        row[2 * n + e] = l1;
-        row[3 * n + e] = l2;
-        row[4 * n + e] = h1;
-        row[5 * n + e] = h2;
-      }
-      for (int e = 6 * n + threadIdx.x; e < Kp; e += blockDim.x) row[e] = __float2half_rn(0.0f);
-    } else {
-      for (int e = threadIdx.x; e < Kp; e += blockDim.x) row[e] = __float2half_rn(0.0f);
+                            int64_t Npad, Geo g, const int* __restrict__ eoff, const float* __restrict__ mu,
+                            TcLayout L, __half* __restrict__ B) {
+  const int n = g.n, ch = g.ch, n8 = L.n8;
+  const int G = n8 / 8, Zg = (L.Kp - 6 * n8) / 8, per = G + Zg;
+  const int64_t total = Npad * per;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = t / per;
+    const int gg = (int)(t - j * per);
+    __half* row = B + j * L.Kp;
+    if (gg >= G) {
+      reinterpret_cast<uint4*>(row + 6 * n8)[gg - G] = make_uint4(0u, 0u, 0u, 0u);
+      continue;
     }
+    __align__(16) __half h1[8], l1[8], h2[8], l2[8];
+    const int64_t sb = j < N ? (int64_t)dict[j] * ch : 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int e = gg * 8 + i;
+      float p = 0.0f;
+      if (j < N && e < n) p = grid[sb + eoff[e]] - mu[e % ch];
+      split16(p, h1[i], l1[i]);
+      split16(p * p, h2[i], l2[i]);
+    }
+    const uint4 vh1 = *reinterpret_cast<const uint4*>(h1), vl1 = *reinterpret_cast<const uint4*>(l1);
+    const uint4 vh2 = *reinterpret_cast<const uint4*>(h2), vl2 = *reinterpret_cast<const uint4*>(l2);
+    uint4* r = reinterpret_cast<uint4*>(row) + gg;
+    const int ps = n8 / 8;  // part stride in 16-byte units
+    r[0] = vh1;
+    r[ps] = vh2;
+    r[2 * ps] = vl1;
+    r[3 * ps] = vl2;
+    r[4 * ps] = vh1;
+    r[5 * ps] = vh2;
   }
 }
 
@@ -416,13 +486,15 @@ int make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols, uint
 }  // namespace
 
 // Pre-scores of Q queries against the N dictionary entries on the tensor cores.
-// Outputs tilemin [Q][ceil(N/256)] (and, when `scores` is non-null, all Q x N
-// pre-scores) and bound[Q]; the per-query constant sum m w t'^2 is not included.
+// Outputs submin [Q][tc_subs(N)] -- the minimum over each 32 consecutive
+// dictionary entries (groups past N are not written) -- bound[Q] and, when
+// `scores` is non-null, all Q x N pre-scores; the per-query constant
+// sum m w t'^2 is not included.
 int tc_prescore(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
-                const int* eoff_all, const float* weights, const int64_t* centre_lin, int64_t Q, float* tilemin,
+                const int* eoff_all, const float* weights, const int64_t* centre_lin, int64_t Q, float* submin,
                 float* scores, double* bound, cudaStream_t st) {
-  const int n = g.n;
-  const int Kp = ((6 * n + kBK - 1) / kBK) * kBK;
+  const TcLayout L = tc_layout(g.n);
+  const int Kp = L.Kp;
   const int64_t Qpad = ((Q + kBM - 1) / kBM) * kBM, Npad = ((N + kBN - 1) / kBN) * kBN;
   const int ntiles = (int)(Npad / kBN);
   const int64_t npix = g.X * g.Y * g.Z;
@@ -475,11 +547,10 @@ int tc_prescore(const Geo& g, const float* grid, const uint8_t* cur_mask, const 
   SFC_TRY(pmalloc(&A, sizeof(__half) * Qpad * Kp, st));
   SFC_TRY(pmalloc(&B, sizeof(__half) * Npad * Kp, st));
   count_launch();
-  k_tc_prep_A<<<(unsigned)Qpad, 256, 0, st>>>(grid, cur_mask, g, centre_lin, Q, eoff_all, weights, mu, pmax, Kp,
+  k_tc_prep_A<<<(unsigned)Qpad, 256, 0, st>>>(grid, cur_mask, g, centre_lin, Q, eoff_all, weights, mu, pmax, L,
                                                A, bound);
   count_launch();
-  k_tc_prep_B<<<(unsigned)std::min<int64_t>(Npad, 152 * 64), 128, 0, st>>>(grid, dict, N, Npad, g, eoff_all, mu, Kp,
-                                                                            B);
+  k_tc_prep_B<<<152 * 32, 256, 0, st>>>(grid, dict, N, Npad, g, eoff_all, mu, L, B);
   SFC_TRY(cudaGetLastError());
   CUtensorMap mapA, mapB;
   SFC_CHECK(make_map(&mapA, A, Qpad, Kp, kBM));
@@ -491,9 +562,10 @@ int tc_prescore(const Geo& g, const float* grid, const uint8_t* cur_mask, const 
   a.abort_all = abort_all;
   a.Q = Q;
   a.N = N;
-  a.kblocks = Kp / kBK;
-  a.ntiles = ntiles;
-  a.tilemin = tilemin;
+  a.kblocks = L.kblocks;
+  a.kb_split = L.kb_split;
+  a.nsub = (int64_t)ntiles * (kBN / 32);
+  a.submin = submin;
   a.scores = scores;
   a.status = status_word();
   const size_t shm = (size_t)kStages * (kStageA + kStageB) + 1024;
@@ -516,6 +588,7 @@ int tc_prescore(const Geo& g, const float* grid, const uint8_t* cur_mask, const 
   return SFC_OK;
 }
 
-int tc_tiles(int64_t N) { return (int)((N + kBN - 1) / kBN); }
+// 32-entry groups per query row of submin (a multiple of 8)
+int64_t tc_subs(int64_t N) { return (N + kBN - 1) / kBN * (kBN / 32); }
 
 }  // namespace sfc
