@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = dict(width=1024, K=11, curves=8, dims=8, bits=16, window=64, pca_sample=16384, cap=65536)
 # DRAM bytes (read + write) per launch from one ncu capture of `python bench.py
 # --steps 1 --warmup 1` (profiles/); None once the kernel changed since.
-TRAFFIC = {"k_query": 21.63e6, "k_si_cluster": None}
+TRAFFIC = {"k_query": 21.63e6, "k_si_cluster": None, "k_tc_gemm": None}
 FP64_PEAK_TFLOPS = 1.25
 METRIC = "patch queries/s: SFC index vs full-scan masked-L2, 1 GB300, oracle-equal picks"
 UNIT = "patch queries/s"
@@ -342,6 +342,38 @@ def main():
     fullscan = {"qps": fs_qps, "queries": fs_q, "ms": statistics.mean(fs_ms), "pick_agreement_sfc": agree,
                 "acceleration_error_mean": ae,
                 "fp32_gflops_algorithmic": fs_flops / (statistics.mean(fs_ms) / 1000.0) / 1e9}
+
+    # ---- the same full scan with the tensor-core pre-score (SFC_FP16) ---------
+    tc_ms = []
+    for r in range(3):
+        if r == 1:
+            sfc.sfc_trace(True)
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        hp, hc = sfc.fullscan_query_batch(gd, md, md, tsub, K=WORKLOAD["K"], precision=sfc.SFC_FP16)
+        b.record(stream)
+        b.synchronize()
+        if r > 0:
+            tc_ms.append(a.elapsed_time(b))
+    tct = sfc.sfc_trace_tc_read()
+    sfc.sfc_trace(False)
+    same = bool(torch.equal(hp, fp) and torch.equal(hc.view(torch.int32), fc.view(torch.int32)))
+    calls = max(tct["calls"], 1)
+    gemm_ms = tct["ms"]["gemm"] / calls
+    gemm_flops = tct["gemm_flops"] / calls
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    tc_roof = {"kernel": "k_tc_gemm (fullscan_query_batch, SFC_FP16)", "bound": "tensor",
+               "achieved": gemm_flops / (gemm_ms / 1000.0) / 1e12 if gemm_ms > 0 else 0.0, "peak": bf16,
+               "unit": "TFLOP/s", "traffic": TRAFFIC.get("k_tc_gemm"),
+               "peak_source": ("MEASURED_PEAKS.json bf16_tflops (FP16 and BF16 run at one rate)" if peaks
+                               else "fallback 1900 TFLOP/s"),
+               "flops_per_launch": gemm_flops, "launch_ms": gemm_ms}
+    tc_roof["frac"] = tc_roof["achieved"] / tc_roof["peak"]
+    fullscan["fp16_tensor"] = {"qps": fs_q / (statistics.mean(tc_ms) / 1000.0), "ms": statistics.mean(tc_ms),
+                               "picks_and_costs_equal_fp32": same,
+                               "phases_ms": {k: v / calls for k, v in tct["ms"].items()}, "roofline": tc_roof}
 
     # ---- end to end through the C-ABI with host buffers ----------------------
     gh = torch.from_numpy(g).pin_memory()

@@ -228,6 +228,15 @@ enum { SFC_TRACE_PHASES = 6 };
 int sfc_trace(int on);
 int sfc_trace_read(double* ms, int64_t* builds, double* eig_flops);
 
+/* While tracing is enabled, every fullscan_query_batch with SFC_FP16 also
+ * records events around its phases -- operands (dictionary, centring, A and B
+ * rows), pre-score GEMM, exact pass -- and waits for the last one before it
+ * returns.  sfc_trace_tc_read copies to HOST ms[SFC_TRACE_TC_PHASES] their
+ * summed milliseconds, *calls the number of calls summed and *gemm_flops the
+ * summed algorithmic GEMM flops (per call 2 Q N 6 n).  Any output may be NULL. */
+enum { SFC_TRACE_TC_PHASES = 3 };
+int sfc_trace_tc_read(double* ms, int64_t* calls, double* gemm_flops);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* sfc_last_error(void);
 

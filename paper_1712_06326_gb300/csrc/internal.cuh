@@ -79,6 +79,12 @@ struct Index {
 
 // Record phase boundary k of a traced build (no-op otherwise).
 void trace_mark(Index& ix, int k, cudaStream_t st);
+// Tracing of one tensor-core full scan on this host thread (no-ops unless
+// tracing is on): begin records boundary 0, mark boundary k (1..3), end waits
+// for the last one and adds the phase times and the GEMM's flops.
+void tc_trace_begin(cudaStream_t st);
+void tc_trace_mark(int k, cudaStream_t st);
+void tc_trace_end(double gemm_flops);
 
 // k_dict.cu
 int dict_extract(const uint8_t* mask, const Geo& g, cudaStream_t st, uint32_t** dict, int64_t* N);

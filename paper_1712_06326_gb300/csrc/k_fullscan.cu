@@ -600,10 +600,12 @@ int fullscan_batch_tc(const Geo& g, const float* grid, const uint8_t* cur_mask, 
   count_launch();
   k_mark_bad<<<qb, 256, 0, st>>>(bad, Q, pick, cost);
   SFC_TRY(cudaGetLastError());
+  tc_trace_mark(3, st);
   cudaFreeAsync(lin, st);
   cudaFreeAsync(bad, st);
   cudaFreeAsync(tilemin, st);
   cudaFreeAsync(bound, st);
+  tc_trace_end(2.0 * (double)Q * (double)N * 6.0 * g.n);
   return SFC_OK;
 }
 

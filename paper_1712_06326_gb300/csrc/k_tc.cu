@@ -573,6 +573,7 @@ int tc_prescore(const Geo& g, const float* grid, const uint8_t* cur_mask, const 
   // the dictionary tiles on grid y (at most 65535 per launch); the query tiles
   // of one dictionary tile are neighbours in launch order, so its B tile is
   // read from HBM once and from L2 after that
+  tc_trace_mark(1, st);
   for (int nb = 0; nb < ntiles; nb += 65535) {
     a.n_base = nb;
     const int ny = std::min(ntiles - nb, 65535);
@@ -580,6 +581,7 @@ int tc_prescore(const Geo& g, const float* grid, const uint8_t* cur_mask, const 
     k_tc_gemm<<<dim3((unsigned)(Qpad / kBM), (unsigned)ny), kTcThreads, shm, st>>>(mapA, mapB, a);
     SFC_TRY(cudaGetLastError());
   }
+  tc_trace_mark(2, st);
   cudaFreeAsync(A, st);
   cudaFreeAsync(B, st);
   cudaFreeAsync(rng, st);

@@ -33,9 +33,49 @@ struct TraceAcc {
   double ms[SFC_TRACE_PHASES] = {};
   int64_t builds = 0;
   double eig_flops = 0.0;
+  double tc_ms[SFC_TRACE_TC_PHASES] = {};
+  int64_t tc_calls = 0;
+  double tc_flops = 0.0;
 } g_trace;
 std::mutex g_trace_mu;
+// events of the tensor-core full scan in flight on this host thread
+thread_local cudaEvent_t g_tc_ev[SFC_TRACE_TC_PHASES + 1] = {};
+thread_local bool g_tc_active = false;
 }  // namespace
+
+void tc_trace_begin(cudaStream_t st) {
+  {
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    g_tc_active = g_trace.on;
+  }
+  if (!g_tc_active) return;
+  for (auto& e : g_tc_ev)
+    if (!e && cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      g_tc_active = false;
+      return;
+    }
+  cudaEventRecord(g_tc_ev[0], st);
+}
+
+void tc_trace_mark(int k, cudaStream_t st) {
+  if (g_tc_active) cudaEventRecord(g_tc_ev[k], st);
+}
+
+void tc_trace_end(double gemm_flops) {
+  if (!g_tc_active) return;
+  g_tc_active = false;
+  float t[SFC_TRACE_TC_PHASES] = {};
+  bool ok = cudaEventSynchronize(g_tc_ev[SFC_TRACE_TC_PHASES]) == cudaSuccess;
+  for (int k = 0; k < SFC_TRACE_TC_PHASES && ok; ++k)
+    ok = cudaEventElapsedTime(&t[k], g_tc_ev[k], g_tc_ev[k + 1]) == cudaSuccess;
+  cudaGetLastError();
+  if (!ok) return;
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  for (int k = 0; k < SFC_TRACE_TC_PHASES; ++k) g_trace.tc_ms[k] += t[k];
+  g_trace.tc_calls += 1;
+  g_trace.tc_flops += gemm_flops;
+}
 
 void trace_mark(Index& ix, int k, cudaStream_t st) {
   if (ix.traced && ix.ev[k]) cudaEventRecord(ix.ev[k], st);
@@ -428,6 +468,15 @@ int sfc_trace(int on) {
   return SFC_OK;
 }
 
+int sfc_trace_tc_read(double* ms, int64_t* calls, double* gemm_flops) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  if (ms)
+    for (int k = 0; k < SFC_TRACE_TC_PHASES; ++k) ms[k] = g_trace.tc_ms[k];
+  if (calls) *calls = g_trace.tc_calls;
+  if (gemm_flops) *gemm_flops = g_trace.tc_flops;
+  return SFC_OK;
+}
+
 int sfc_trace_read(double* ms, int64_t* builds, double* eig_flops) {
   std::lock_guard<std::mutex> lk(g_trace_mu);
   if (ms)
@@ -566,7 +615,13 @@ int fullscan_query_batch(const float* grid, const uint8_t* dict_mask, const uint
   SFC_CHECK(check_weights(w));
   bool weighted = false;
   for (float v : w) weighted |= v != 1.0f;
+  if (p->precision != SFC_FP32 && p->precision != SFC_FP16) {
+    set_error("fullscan_query_batch: precision must be SFC_FP32 or SFC_FP16");
+    return SFC_EUNSUPPORTED;
+  }
+  const bool tc = p->precision == SFC_FP16;
   cudaStream_t st = (cudaStream_t)stream;
+  if (tc) tc_trace_begin(st);
   uint32_t* dict = nullptr;
   int64_t N = 0;
   int* eo = nullptr;
@@ -579,15 +634,8 @@ int fullscan_query_batch(const float* grid, const uint8_t* dict_mask, const uint
   }
   SFC_CHECK(upload_patch_tables(g, &eo, st));
   SFC_CHECK(upload(&wd, w.data(), w.size(), st));
-  int rc;
-  if (p->precision == SFC_FP16)
-    rc = fullscan_batch_tc(g, grid, cur_mask, dict, N, eo, wd, weighted, centres, Q, pick, cost, nullptr, st);
-  else if (p->precision == SFC_FP32)
-    rc = fullscan_batch(g, grid, cur_mask, dict, N, eo, wd, weighted, centres, nullptr, Q, pick, cost, st);
-  else {
-    set_error("fullscan_query_batch: precision must be SFC_FP32 or SFC_FP16");
-    rc = SFC_EUNSUPPORTED;
-  }
+  const int rc = tc ? fullscan_batch_tc(g, grid, cur_mask, dict, N, eo, wd, weighted, centres, Q, pick, cost, nullptr, st)
+                    : fullscan_batch(g, grid, cur_mask, dict, N, eo, wd, weighted, centres, nullptr, Q, pick, cost, st);
   cudaFreeAsync(dict, st);
   cudaFreeAsync(eo, st);
   cudaFreeAsync(wd, st);

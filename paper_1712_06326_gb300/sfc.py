@@ -24,7 +24,8 @@ SFC_MODE_FULLSCAN, SFC_MODE_SFC = 0, 1
 
 EXPORTS = ["sfc_params_default", "sfc_index_build", "sfc_index_destroy", "sfc_index_info", "sfc_index_export",
            "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "fullscan_query_batch_static",
-           "sfc_tc_prescores", "inpaint_run", "sfc_status", "sfc_launch_count", "sfc_trace", "sfc_trace_read", "sfc_last_error"]
+           "sfc_tc_prescores", "inpaint_run", "sfc_status", "sfc_launch_count", "sfc_trace", "sfc_trace_read", "sfc_trace_tc_read",
+           "sfc_last_error"]
 TRACE_PHASES = ("dictionary", "moments", "eigen", "finalize", "project_keys", "sort")
 
 
@@ -74,6 +75,8 @@ def lib():
         L.sfc_trace.restype = C.c_int
         L.sfc_trace_read.argtypes = [vp, vp, vp]
         L.sfc_trace_read.restype = C.c_int
+        L.sfc_trace_tc_read.argtypes = [vp, vp, vp]
+        L.sfc_trace_tc_read.restype = C.c_int
         for name in ["sfc_index_build", "sfc_index_destroy", "sfc_index_info", "sfc_index_export",
                      "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "fullscan_query_batch_static",
                      "sfc_tc_prescores", "inpaint_run", "sfc_status"]:
@@ -314,6 +317,18 @@ def sfc_trace_read() -> dict:
     _check(lib().sfc_trace_read(ms.ctypes.data_as(C.c_void_p), builds.ctypes.data_as(C.c_void_p),
                                 fl.ctypes.data_as(C.c_void_p)), "sfc_trace_read")
     return dict(ms=dict(zip(TRACE_PHASES, ms.tolist())), builds=int(builds[0]), eig_flops=float(fl[0]))
+
+
+TRACE_TC_PHASES = ("operands", "gemm", "exact")
+
+
+def sfc_trace_tc_read() -> dict:
+    ms = np.zeros(len(TRACE_TC_PHASES), np.float64)
+    calls = np.zeros(1, np.int64)
+    fl = np.zeros(1, np.float64)
+    _check(lib().sfc_trace_tc_read(ms.ctypes.data_as(C.c_void_p), calls.ctypes.data_as(C.c_void_p),
+                                   fl.ctypes.data_as(C.c_void_p)), "sfc_trace_tc_read")
+    return dict(ms=dict(zip(TRACE_TC_PHASES, ms.tolist())), calls=int(calls[0]), gemm_flops=float(fl[0]))
 
 
 def sfc_status() -> int:
