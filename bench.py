@@ -186,6 +186,32 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------------
+def run_profile_fp16(width: int, queries: int):
+    """The full scan with the tensor-core pre-score on a smaller or equal case,
+    for ncu (front targets of the initial mask, topped up with seeded uniform
+    centres to QUERIES)."""
+    import torch
+
+    import __graft_entry__
+    import paper_1712_06326_gb300.sfc as sfc
+    from paper_1712_06326_gb300 import synth
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    g, m = synth.voronoi2d(width, cfg=2)
+    t = synth.front_targets(m, WORKLOAD["K"], cap=WORKLOAD["cap"], cfg=2)
+    if len(t) < queries:
+        t = np.concatenate([t, synth.random_targets(m, WORKLOAD["K"], queries - len(t), cfg=2)])
+    t = np.ascontiguousarray(t[:queries])
+    gd, md, td = (torch.from_numpy(a).cuda() for a in (g, m, t))
+    for _ in range(2):
+        p, c = sfc.fullscan_query_batch(gd, md, md, td, K=WORKLOAD["K"], precision=sfc.SFC_FP16)
+    torch.cuda.synchronize()
+    st = sfc.sfc_status()
+    print(json.dumps({"profile_fp16": {"width": width, "queries": int(len(t)), "status": st}}))
+    return 0 if st == 0 else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -193,9 +219,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-fp16", nargs=2, type=int, metavar=("WIDTH", "QUERIES"),
+                    help="profiling case only: two tensor-core full scans (SFC_FP16) of QUERIES targets on a "
+                         "WIDTH^2 voronoi2d grid, K=11; prints one line, no timing")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_fp16:
+        return run_profile_fp16(*args.profile_fp16)
 
     import torch
     import torch.distributed as dist

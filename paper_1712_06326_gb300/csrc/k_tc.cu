@@ -11,8 +11,8 @@
 // (n rounded up to 8) values each: the small products are accumulated first,
 // while the accumulator is still small, and the hi*hi products are shared
 // between two TMEM accumulators (K-blocks before / after kb_split) that the
-// epilogue adds, which keeps the accumulation error bound near 8 (2 n8 / 2) u32
-// of the products' magnitude.
+// epilogue adds; the certified bound charges each product for the K positions
+// that follow it in its accumulator (see k_tc_prep_A).
 //
 // Kernel structure (one 128 x 256 output tile per CTA): warp 0 issues TMA loads
 // (128-byte swizzle) of the A and B K-slices into a 4-stage shared-memory ring;
@@ -119,37 +119,42 @@ struct TcArgs {
   int64_t Q, N;        // real rows of A / B
   int kblocks;         // Kp / 64
   int kb_split;        // first K-block of the second accumulator (== kblocks: none)
-  int n_base;          // first dictionary tile of this launch
+  int64_t mtiles;      // 128-row query tiles
+  int64_t tiles;       // mtiles * ceil(N / 256)
   int64_t nsub;        // 32-column groups per query row of submin (8 per tile)
   float* submin;       // [Q][nsub] minimum over each 32 dictionary entries
   float* scores;       // optional [Q][N] (checking only)
   uint32_t* status;
-  int* abort_all;      // set by a CTA that timed out; later CTAs skip their tile
+  int* abort_all;      // set by a CTA that timed out; the others stop at their next tile
 };
 
+// Persistent: CTA b takes the tiles b, b + gridDim.x, ...; tile t covers query
+// rows 128 (t % mtiles) .. and dictionary entries 256 (t / mtiles) .., so CTAs
+// running at the same time share dictionary tiles (read from HBM once, then
+// from L2).  The stage ring and its phases run on across tiles, so the
+// producer prefetches the next tile while the epilogue drains the current one;
+// the MMA issuer waits for the epilogue to release the accumulators.
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const __grid_constant__ CUtensorMap mapA,
                                                            const __grid_constant__ CUtensorMap mapB, TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned stage buffers (the swizzle pattern repeats every 1024 B)
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sA = base;                              // kStages * kStageA
-  unsigned char* sB = base + kStages * kStageA;          // kStages * kStageB
-  __shared__ uint64_t full_bar[kStages], empty_bar[kStages], done_bar;
+  unsigned char* sA = base;                      // kStages * kStageA
+  unsigned char* sB = base + kStages * kStageA;  // kStages * kStageB
+  __shared__ uint64_t full_bar[kStages], empty_bar[kStages], acc_full, acc_empty, final_bar;
   __shared__ uint32_t tmem_base;
-  __shared__ int abort_flag, s_issued, s_consumed;
+  __shared__ int abort_flag;
+  __shared__ long long s_issued, s_consumed;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m_tile = blockIdx.x, n_tile = a.n_base + (int)blockIdx.y;
-  __shared__ int s_skip;
-  if (threadIdx.x == 0) s_skip = *(volatile int*)a.abort_all;
-  __syncthreads();
-  if (s_skip) return;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    mbar_init(&done_bar, 1);
+    mbar_init(&acc_full, 1);
+    mbar_init(&acc_empty, 4);  // one arrival per epilogue warp
+    mbar_init(&final_bar, 1);
     abort_flag = 0;
     s_issued = 0;
     s_consumed = 0;
@@ -164,59 +169,88 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const __grid_constant
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
+  // stop_here: this CTA's flag (shared memory, checked per K-block); stop: also
+  // the launch-wide flag (a global load, checked once per tile)
+  auto stop_here = [&]() { return *(volatile int*)&abort_flag != 0; };
+  auto stop = [&]() { return stop_here() || *(volatile int*)a.abort_all != 0; };
+  auto fail = [&]() {
+    atomicExch(&abort_flag, 1);
+    atomicExch(a.abort_all, 1);
+  };
 
-  int issued_tma = 0, issued_mma = 0;
   if (warp == 0 && lane == 0) {
-    // producer: K-block kb goes to stage kb % kStages
-    for (int kb = 0; kb < a.kblocks; ++kb) {
-      const int s = kb % kStages;
-      if (kb >= kStages && !mbar_wait(&empty_bar[s], ((kb / kStages) - 1) & 1)) {
-        atomicExch(&abort_flag, 1);
-        break;
+    // producer: ring position it -> stage it % kStages, phase (it / kStages) & 1
+    long long it = 0;
+    for (int64_t t = blockIdx.x; t < a.tiles && !stop(); t += gridDim.x) {
+      const int m_tile = (int)(t % a.mtiles), n_tile = (int)(t / a.mtiles);
+      for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
+        const int s = (int)(it % kStages);
+        if (it >= kStages && !mbar_wait(&empty_bar[s], (uint32_t)((it / kStages) - 1) & 1)) {
+          fail();
+          break;
+        }
+        if (stop_here()) break;
+        mbar_expect_tx(&full_bar[s], kStageA + kStageB);
+        tma_load_2d(sA + s * kStageA, &mapA, kb * kBK, m_tile * kBM, &full_bar[s]);
+        tma_load_2d(sB + s * kStageB, &mapB, kb * kBK, n_tile * kBN, &full_bar[s]);
+        s_issued = it + 1;
       }
-      if (*(volatile int*)&abort_flag) break;
-      mbar_expect_tx(&full_bar[s], kStageA + kStageB);
-      tma_load_2d(sA + s * kStageA, &mapA, kb * kBK, m_tile * kBM, &full_bar[s]);
-      tma_load_2d(sB + s * kStageB, &mapB, kb * kBK, n_tile * kBN, &full_bar[s]);
-      ++issued_tma;
     }
-    s_issued = issued_tma;
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
-    for (int kb = 0; kb < a.kblocks; ++kb) {
-      const int s = kb % kStages;
-      if (!mbar_wait(&full_bar[s], (kb / kStages) & 1) || *(volatile int*)&abort_flag) {
-        atomicExch(&abort_flag, 1);
+    long long it = 0;
+    int local = 0;
+    for (int64_t t = blockIdx.x; t < a.tiles && !stop(); t += gridDim.x, ++local) {
+      if (local > 0 && !mbar_wait(&acc_empty, (uint32_t)(local - 1) & 1)) {
+        fail();
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t a0 = smem_u32(sA + s * kStageA), b0 = smem_u32(sB + s * kStageB);
-      const bool second = kb >= a.kb_split;
-      const uint32_t d = tmem + (second ? 256u : 0u);
-      const bool first_block = kb == 0 || kb == a.kb_split;
+      bool ok = true;
+      for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
+        const int s = (int)(it % kStages);
+        if (!mbar_wait(&full_bar[s], (uint32_t)(it / kStages) & 1) || stop_here()) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t a0 = smem_u32(sA + s * kStageA), b0 = smem_u32(sB + s * kStageB);
+        const bool second = kb >= a.kb_split;
+        const uint32_t d = tmem + (second ? 256u : 0u);
+        const bool first_block = kb == 0 || kb == a.kb_split;
 #pragma unroll
-      for (int kk = 0; kk < kBK / 16; ++kk) {
-        // a K step of 16 FP16 = 32 bytes inside the 128-byte swizzled rows
-        tc_mma(d, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), (first_block && kk == 0) ? 0u : 1u);
+        for (int kk = 0; kk < kBK / 16; ++kk) {
+          // a K step of 16 FP16 = 32 bytes inside the 128-byte swizzled rows
+          tc_mma(d, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32),
+                 (first_block && kk == 0) ? 0u : 1u);
+        }
+        tc_commit(&empty_bar[s]);
+        s_consumed = it + 1;
       }
-      tc_commit(&empty_bar[s]);
-      ++issued_mma;
+      if (!ok) {
+        fail();
+        break;
+      }
+      tc_commit(&acc_full);  // arrives when this tile's MMAs have completed
     }
-    s_consumed = issued_mma;
-    tc_commit(&done_bar);  // arrives when every MMA issued above has completed
-  }
-  __syncwarp();
-  // epilogue warps 2..5: TMEM lanes 32 * (warp % 4) ..
-  if (warp >= 2) {
-    // warp-uniform outcome (tcgen05.ld below is a whole-warp instruction)
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0));
-    if (!ok) atomicExch(&abort_flag, 1);
-    asm volatile("tcgen05.fence::after_thread_sync;");
+    tc_commit(&final_bar);  // every MMA issued above has completed
+    if (!mbar_wait(&final_bar, 0)) fail();
+  } else if (warp >= 2) {
+    // epilogue warps 2..5: TMEM lanes 32 * (warp % 4) ..
     const int quarter = warp & 3;
-    const int64_t row = (int64_t)m_tile * kBM + quarter * 32 + lane;
-    const int64_t col0 = (int64_t)n_tile * kBN;
     const bool two = a.kb_split < a.kblocks;
-    if (ok) {
+    int local = 0;
+    for (int64_t t = blockIdx.x; t < a.tiles; t += gridDim.x, ++local) {
+      const int m_tile = (int)(t % a.mtiles), n_tile = (int)(t / a.mtiles);
+      // warp-uniform outcome (tcgen05.ld below is a whole-warp instruction)
+      const bool ok = __all_sync(0xffffffffu, !stop() && mbar_wait(&acc_full, (uint32_t)local & 1));
+      if (!ok) {
+        if (lane == 0) fail();
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int64_t row = (int64_t)m_tile * kBM + quarter * 32 + lane;
+      const int64_t col0 = (int64_t)n_tile * kBN;
       float mins[kBN / 32];
 #pragma unroll
       for (int c = 0; c < kBN; c += 32) {
@@ -237,6 +271,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const __grid_constant
         }
         mins[c / 32] = mn;
       }
+      // the accumulators are free once every lane's loads are done
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty)) : "memory");
       if (row < a.Q) {
         float4* dst = reinterpret_cast<float4*>(a.submin + row * a.nsub + (int64_t)n_tile * (kBN / 32));
         dst[0] = make_float4(mins[0], mins[1], mins[2], mins[3]);
@@ -244,14 +282,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const __grid_constant
       }
     }
   }
+  __syncwarp();
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (abort_flag && threadIdx.x == 0) {
-    // drain the TMA loads issued but not consumed (bounded); the MMAs issued
-    // were covered by the done barrier the epilogue waited on
-    atomicOr(a.status, ST_TIMEOUT);
-    atomicExch(a.abort_all, 1);
-    for (int kb = s_consumed; kb < s_issued; ++kb) mbar_wait(&full_bar[kb % kStages], (kb / kStages) & 1);
+  if (threadIdx.x == 0) {
+    if (abort_flag) atomicOr(a.status, ST_TIMEOUT);
+    // after a stop (here or in another CTA): drain the TMA loads issued but
+    // not consumed (bounded) before the shared memory is released
+    for (long long it = s_consumed; it < s_issued; ++it)
+      mbar_wait(&full_bar[it % kStages], (uint32_t)(it / kStages) & 1);
   }
   __syncthreads();
   if (warp == 1) {
@@ -297,15 +336,13 @@ inline TcLayout tc_layout(int n) {
 //      M = sum_e m (|a1| pmax + |a2| pmax^2),  S = sum_e m (|a1| + |a2| + pmax + pmax^2);
 //  * FP32 rounding of the centred operands (t - mu, w t', p - mu, p'^2):
 //    <= 4 u32 M;
-//  * accumulation: eight times the sequential FP32 bound (covers blocked and
-//    truncating accumulation), per accumulator r: steps before the hi*hi
-//    part (l_r of them) see partial sums <= SL = 2.02 u16 M + 2^-24 S (all
-//    small products), the h_r steps from there on <= SL + H_r (H_r: the hi*hi
-//    mass that accumulator holds, from the actual |a| and pmax); plus one
-//    rounding of acc0 + acc1:
-//      8 u32 sum_r [ l_r SL + h_r (SL + H_r) ] + 1.01 u32 (SL + H_0 + H_1).
-// Steps count every K position (padding included), as the hardware's blocked
-// accumulation rounds per instruction, not per nonzero product.
+//  * accumulation: the sequential FP32 bound sum_k u32 |S_k| (S_k the partial
+//    sums of one accumulator) is at most u32 sum_i mu_i rem_i, where mu_i bounds
+//    the i-th product (from the actual FP16 pieces of a and pmax) and rem_i is
+//    the number of K positions from i to the end of its accumulator (padding
+//    included: the hardware rounds per instruction, not per nonzero product);
+//    taken eight times (blocked, truncating accumulation), plus one rounding of
+//    acc0 + acc1:   8 u32 T + 1.01 u32 sum_i mu_i,   T = sum_i mu_i rem_i.
 __global__ void k_tc_prep_A(const float* __restrict__ grid, const uint8_t* __restrict__ mask, Geo g,
                             const int64_t* __restrict__ centre_lin, int64_t Q, const int* __restrict__ eoff,
                             const float* __restrict__ w, const float* __restrict__ mu, const float* __restrict__ pmax,
@@ -313,11 +350,13 @@ __global__ void k_tc_prep_A(const float* __restrict__ grid, const uint8_t* __res
   const int64_t q = blockIdx.x;
   const int n = g.n, ch = g.ch, n8 = L.n8, Ks = L.kb_split * kBK;
   __shared__ double red[4][8];
-  double msum = 0.0, ssum = 0.0, h0 = 0.0, h1 = 0.0;
+  double msum = 0.0, ssum = 0.0, tri = 0.0, mass = 0.0;
   __half* row = A + q * L.Kp;
   const __half z = __float2half_rn(0.0f);
   for (int e = 6 * n8 + threadIdx.x; e < L.Kp; e += blockDim.x) row[e] = z;
   const int64_t tc = q < Q ? centre_lin[q] : 0;
+  // K positions from k to the end of k's accumulator
+  auto rem = [&](int k) { return (double)((k < Ks ? Ks : L.Kp) - k); };
   for (int e = threadIdx.x; e < n8; e += blockDim.x) {
     __half a1h = z, a1l = z, a2h = z, a2l = z;
     if (q < Q && e < n) {
@@ -328,14 +367,19 @@ __global__ void k_tc_prep_A(const float* __restrict__ grid, const uint8_t* __res
       split16(a1, a1h, a1l);
       split16(a2, a2h, a2l);
       if (k != 0.0f) {
-        const double pm = pmax[c];
-        const double m1 = (double)fabsf(a1) * pm, m2 = (double)fabsf(a2) * pm * pm;
-        msum += m1 + m2;
-        ssum += (double)fabsf(a1) + (double)fabsf(a2) + pm + pm * pm;
-        // hi*hi masses (|ah| <= |a| (1 + u16), |bh| <= pmax (1 + u16)) by accumulator
-        const double f = 1.0009770;  // > (1 + 2^-11)^2
-        if (4 * n8 + e < Ks) h0 += f * m1; else h1 += f * m1;
-        if (5 * n8 + e < Ks) h0 += f * m2; else h1 += f * m2;
+        const double pm = pmax[c], pm2 = pm * pm;
+        msum += (double)fabsf(a1) * pm + (double)fabsf(a2) * pm2;
+        ssum += (double)fabsf(a1) + (double)fabsf(a2) + pm + pm2;
+        // product bounds: |bh| <= b (1 + u16), |bl| <= u16 b + 2^-25 for b in {pmax, pmax^2}
+        const double u16 = 0x1p-11, up = 1.0 + u16;
+        const double h1 = fabs((double)__half2float(a1h)), l1 = fabs((double)__half2float(a1l));
+        const double h2 = fabs((double)__half2float(a2h)), l2 = fabs((double)__half2float(a2l));
+        const double m0 = l1 * pm * up, m1 = l2 * pm2 * up;
+        const double m2 = h1 * (u16 * pm + 0x1p-25), m3 = h2 * (u16 * pm2 + 0x1p-25);
+        const double m4 = h1 * pm * up, m5 = h2 * pm2 * up;
+        tri += m0 * rem(e) + m1 * rem(n8 + e) + m2 * rem(2 * n8 + e) + m3 * rem(3 * n8 + e) +
+               m4 * rem(4 * n8 + e) + m5 * rem(5 * n8 + e);
+        mass += m0 + m1 + m2 + m3 + m4 + m5;
       }
     }
     row[e] = a1l;
@@ -348,32 +392,27 @@ __global__ void k_tc_prep_A(const float* __restrict__ grid, const uint8_t* __res
   for (int o = 16; o > 0; o >>= 1) {
     msum += __shfl_xor_sync(0xffffffffu, msum, o);
     ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
-    h0 += __shfl_xor_sync(0xffffffffu, h0, o);
-    h1 += __shfl_xor_sync(0xffffffffu, h1, o);
+    tri += __shfl_xor_sync(0xffffffffu, tri, o);
+    mass += __shfl_xor_sync(0xffffffffu, mass, o);
   }
   if ((threadIdx.x & 31) == 0) {
     red[0][threadIdx.x >> 5] = msum;
     red[1][threadIdx.x >> 5] = ssum;
-    red[2][threadIdx.x >> 5] = h0;
-    red[3][threadIdx.x >> 5] = h1;
+    red[2][threadIdx.x >> 5] = tri;
+    red[3][threadIdx.x >> 5] = mass;
   }
   __syncthreads();
   if (threadIdx.x == 0 && q < Q) {
-    double M = 0.0, Sa = 0.0, H0 = 0.0, H1 = 0.0;
+    double M = 0.0, Sa = 0.0, T = 0.0, Ms = 0.0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
       M += red[0][i];
       Sa += red[1][i];
-      H0 += red[2][i];
-      H1 += red[3][i];
+      T += red[2][i];
+      Ms += red[3][i];
     }
     const double u16 = 0x1p-11, u32 = 0x1p-24;
-    const double SL = 2.02 * u16 * M + 0x1p-24 * Sa;
-    const int K4 = 4 * n8;
-    const double l0 = min(Ks, K4), h0n = max(0, Ks - K4);
-    const double l1 = max(0, K4 - Ks), h1n = L.Kp - max(Ks, K4);
-    const double acc = 8.0 * u32 * (l0 * SL + h0n * (SL + H0) + l1 * SL + h1n * (SL + H1)) +
-                       1.01 * u32 * (SL + H0 + H1);
-    bound[q] = 3.01 * u16 * u16 * M + 0x1p-24 * Sa + 0x1p-47 * n + 4.0 * u32 * M + acc;
+    // (the double sums above carry relative errors ~1e-16, far inside the slack)
+    bound[q] = 3.01 * u16 * u16 * M + 0x1p-24 * Sa + 0x1p-47 * n + 4.0 * u32 * M + 8.0 * u32 * T + 1.01 * u32 * Ms;
   }
 }
 
@@ -564,23 +603,22 @@ int tc_prescore(const Geo& g, const float* grid, const uint8_t* cur_mask, const 
   a.N = N;
   a.kblocks = L.kblocks;
   a.kb_split = L.kb_split;
+  a.mtiles = Qpad / kBM;
+  a.tiles = a.mtiles * ntiles;
   a.nsub = (int64_t)ntiles * (kBN / 32);
   a.submin = submin;
   a.scores = scores;
   a.status = status_word();
   const size_t shm = (size_t)kStages * (kStageA + kStageB) + 1024;
   SFC_TRY(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-  // the dictionary tiles on grid y (at most 65535 per launch); the query tiles
-  // of one dictionary tile are neighbours in launch order, so its B tile is
-  // read from HBM once and from L2 after that
+  int dev = 0, sms = 0;
+  SFC_TRY(cudaGetDevice(&dev));
+  SFC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned grid_x = (unsigned)std::min<int64_t>(a.tiles, std::max(sms, 1));
   tc_trace_mark(1, st);
-  for (int nb = 0; nb < ntiles; nb += 65535) {
-    a.n_base = nb;
-    const int ny = std::min(ntiles - nb, 65535);
-    count_launch();
-    k_tc_gemm<<<dim3((unsigned)(Qpad / kBM), (unsigned)ny), kTcThreads, shm, st>>>(mapA, mapB, a);
-    SFC_TRY(cudaGetLastError());
-  }
+  count_launch();
+  k_tc_gemm<<<grid_x, kTcThreads, shm, st>>>(mapA, mapB, a);
+  SFC_TRY(cudaGetLastError());
   tc_trace_mark(2, st);
   cudaFreeAsync(A, st);
   cudaFreeAsync(B, st);
