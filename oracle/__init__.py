@@ -64,6 +64,8 @@ def lib():
                 "or_query": (None, [P, P, I32, P, I32, I32, I32, I32, I32, I32, I32, P, P, I32, P, P, P, P, P,
                                     P, P, P, I64, I64, P, P, P, P, P, P]),
                 "or_knn_bruteforce": (None, [P, I64, I32, P, I32, P, P]),
+                "or_query_knn": (None, [P, P, I32, P, I32, I32, I32, I32, I32, I32, I32, P, P, I32, P, P, P, P, P,
+                                        P, I64, I64, P, P, P, P]),
                 "or_inpaint": (I64, [P, P, I32, P, I32, I32, I32, I32, P, P, I64, I32, I32, I32, I32, I32, P,
                                      I32, P, P, P, P, P, P, P, I64, P]),
             }
@@ -315,6 +317,24 @@ def query(ix, grid, cur_mask, target_lin, W, select=0, weights=None):
                    _p(ix["lo"]), _p(ix["scale"]), _p(ix["shifts"]), _p(ix["skeys"]), _p(ix["sids"]), _p(ix["dict"]),
                    ix["N"], int(target_lin), _p(qk), _p(pos), _p(cand), _p(nc), _p(pick), _p(cost))
     return dict(pick=int(pick[0]), cost=float(cost[0]), cand=cand[: int(nc[0])].copy(), qkeys=qk, pos=pos)
+
+
+def query_knn(ix, grid, cur_mask, target_lin, k, select=0, weights=None):
+    """One SFC query with exact k-NN lists (Sec. II.D) -> dict(pick, cost, cand).
+    ``ix`` needs "q": [C, N, D] unshifted quantised coordinates."""
+    ndim, ext, ch = geometry(grid)
+    C_, D = ix["C"], ix["D"]
+    cand = np.empty(C_ * max(k, 1), np.int64)
+    nc = np.zeros(1, np.int64)
+    pick = np.zeros(1, np.int64)
+    cost = np.zeros(1, np.float64)
+    w = None if weights is None else _c(weights, np.float32)
+    lib().or_query_knn(_p(_c(grid, np.float32)), _p(_c(cur_mask, np.uint8)), ndim, _p(ext), ch, ix["K"], C_, D,
+                       ix["bits"], k, select, _p(w), _p(_c(ix["subset"], np.int32)), ix["m"],
+                       _p(_c(ix["basis"], np.float32)), _p(_c(ix["mean"], np.float32)), _p(_c(ix["lo"], np.float32)),
+                       _p(_c(ix["scale"], np.float32)), _p(_c(ix["q"], np.uint32)), _p(_c(ix["dict"], np.int64)),
+                       ix["N"], int(target_lin), _p(cand), _p(nc), _p(pick), _p(cost))
+    return dict(pick=int(pick[0]), cost=float(cost[0]), cand=cand[: int(nc[0])].copy())
 
 
 def inpaint(grid, mask, K, mode=0, prio=0, ix=None, W=64, select=0, weights=None, max_steps=0):

@@ -601,6 +601,68 @@ void or_knn_bruteforce(const uint32_t* qcoords, int64_t N, int D, const uint32_t
 }
 
 // ----------------------------------------------------------------------------
+// One SFC query with the paper's exact k-NN lists (Sec. II.D) in place of the
+// window: per selected index, the k dictionary entries nearest to the query in
+// the quantised principal space (squared Euclidean distance between the
+// integer coordinates, ties by id -- the set or_knn_bruteforce returns); the
+// candidates are the sorted union of those lists, rescored with the exact
+// image-space cost as in or_query.  Index selection, projection and
+// quantisation (clamped) as in or_query; distances use unshifted coordinates
+// (a common shift leaves them unchanged).
+// qc[C*N*D]: quantised, unshifted coordinates of every dictionary entry.
+// Outputs: cand (<= C*k ids), *ncand, *pick (-1 if no candidate), *cost.
+// ----------------------------------------------------------------------------
+void or_query_knn(const float* grid, const uint8_t* cur_mask, int ndim, const int64_t* ext, int ch, int K, int C,
+                  int D, int bits, int k, int select, const float* w, const int32_t* subset, int m,
+                  const float* basis, const float* mean32, const float* lo, const float* scale, const uint32_t* qc,
+                  const int64_t* dict, int64_t N, int64_t target, int64_t* cand, int64_t* ncand, int64_t* pick,
+                  double* cost) {
+  Geo g = make_geo(ndim, ext, ch, K);
+  const int s = m * ch;
+  std::vector<int> use;
+  if (select == 1) {
+    int best = 0, bestcov = -1;
+    for (int cv = 0; cv < C; ++cv) {
+      int cov = 0;
+      for (int i = 0; i < m; ++i) cov += cur_mask[patch_pixel(g, target, subset[cv * m + i])] ? 1 : 0;
+      if (cov > bestcov) {
+        bestcov = cov;
+        best = cv;
+      }
+    }
+    use.push_back(best);
+  } else {
+    for (int cv = 0; cv < C; ++cv) use.push_back(cv);
+  }
+  std::vector<int64_t> ids;
+  std::vector<float> y(D);
+  std::vector<uint32_t> qq(D);
+  const int kk = (int)std::min<int64_t>(k, N);
+  std::vector<int64_t> nn(kk), dd(kk);
+  for (int cv : use) {
+    or_project_one(grid, cur_mask, ndim, ext, ch, K, target, subset + (size_t)cv * m, m,
+                   basis + (size_t)cv * s * D, mean32 + (size_t)cv * s, D, y.data());
+    for (int a = 0; a < D; ++a) qq[a] = or_quantise_one(y[a], lo[cv * D + a], scale[cv * D + a], bits);
+    or_knn_bruteforce(qc + (size_t)cv * N * D, N, D, qq.data(), k, nn.data(), dd.data());
+    for (int i = 0; i < kk; ++i) ids.push_back(nn[i]);
+  }
+  sort_unique(ids);
+  for (size_t i = 0; i < ids.size(); ++i) cand[i] = ids[i];
+  *ncand = (int64_t)ids.size();
+  double best = INFINITY;
+  int64_t bj = -1;
+  for (int64_t j : ids) {
+    double c = cost64(g, grid, cur_mask, target, dict[j], w);
+    if (c < best) {
+      best = c;
+      bj = j;
+    }
+  }
+  *pick = bj;
+  *cost = best;
+}
+
+// ----------------------------------------------------------------------------
 // Inpainting loop (Sec. I; Fig. 1(a)).  Readings:
 //  * fill front: known pixels with an unknown axis-neighbour (4-/6-connected);
 //    a target centre is a front pixel moved into [r, ext-1-r] per axis (the

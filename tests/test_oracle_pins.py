@@ -452,6 +452,58 @@ def test_query_candidate_set_structure(small_rgb):
         assert r["cost"] == min(costs) and r["pick"] == c[int(np.argmin(costs))]
 
 
+# ----------------------------------------------------------------------------
+# SFC query with exact k-NN lists (Sec. II.D)
+# ----------------------------------------------------------------------------
+def _numpy_knn(qc, query, k):
+    d = ((qc.astype(np.int64) - query.astype(np.int64)) ** 2).sum(1)
+    return np.lexsort((np.arange(len(d)), d))[:k]
+
+
+def test_query_knn_covering_dictionary_equals_fullscan(small_rgb):
+    g, m, ix = small_rgb
+    t = synth.front_targets(m, 7, cap=8, cfg=2)
+    lin = O.centres_to_lin(t, ix["ext"])
+    fp, fc = O.fullscan(g, m, 7, ix["dict"], lin)
+    for i, tl in enumerate(lin):
+        r = O.query_knn(ix, g, m, tl, k=ix["N"] + 5)
+        assert r["pick"] == fp[i] and r["cost"] == fc[i]
+        assert np.array_equal(r["cand"], np.arange(ix["N"]))
+
+
+def test_query_knn_candidates_are_the_union_of_nearest_lists(small_rgb):
+    g, m, ix = small_rgb
+    t = np.concatenate([synth.front_targets(m, 7, cap=10, cfg=2), synth.random_targets(m, 7, 6, cfg=2)])
+    lin = O.centres_to_lin(t, ix["ext"])
+    k = 24
+    for tl in lin:
+        r = O.query_knn(ix, g, m, tl, k=k)
+        want = set()
+        for cv in range(ix["C"]):
+            y = O.project_query(g, m, 7, tl, ix["subset"][cv], ix["basis"][cv], ix["mean"][cv], ix["D"])
+            qq = O.quantise(y[None], ix["bits"], ix["lo"][cv], ix["scale"][cv])[0]
+            want |= set(_numpy_knn(ix["q"][cv], qq, k).tolist())
+        assert set(r["cand"].tolist()) == want and np.all(np.diff(r["cand"]) > 0)
+        costs = [O.cost64(g, m, 7, tl, ix["dict"][j]) for j in r["cand"]]
+        assert r["cost"] == min(costs) and r["pick"] == r["cand"][int(np.argmin(costs))]
+
+
+def test_query_knn_dictionary_patch_finds_itself(small_rgb):
+    g, m, ix = small_rgb
+    for j in [0, 17, ix["N"] // 2, ix["N"] - 1]:
+        r = O.query_knn(ix, g, m, ix["dict"][j], k=4)
+        assert j in set(r["cand"].tolist()) or r["cost"] == 0.0
+        assert r["cost"] == 0.0 and r["pick"] <= j
+
+
+def test_query_knn_select_best_single_list(small_rgb):
+    g, m, ix = small_rgb
+    t = synth.front_targets(m, 7, cap=6, cfg=2)
+    for tl in O.centres_to_lin(t, ix["ext"]):
+        r = O.query_knn(ix, g, m, tl, k=9, select=1)
+        assert 1 <= len(r["cand"]) <= 9
+
+
 def test_query_select_best_uses_max_coverage(small_rgb):
     g, m, ix = small_rgb
     t = synth.front_targets(m, 7, cap=10, cfg=2)
