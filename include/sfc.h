@@ -91,12 +91,16 @@ typedef struct sfc_params {
   int64_t pca_sample;     /* dictionary entries used for the covariance; <= 0: all */
   int32_t priority;       /* fill order: SFC_PRIO_CONFIDENCE or SFC_PRIO_CRIMINISI (2-D) */
   int32_t keep_intermediates; /* 1: keep projections and unsorted keys for sfc_index_export */
+  int32_t knn;            /* k in 1..128: per selected index, the exact k nearest dictionary entries in the
+                             quantised principal space (Sec. II.D) are the candidates instead of the window;
+                             0: the window of W sorted slots */
 } sfc_params;
 
 typedef struct sfc_index sfc_index; /* opaque; owned by the library */
 
 /* Fill `p` with the paper's defaults (K = 9, c = 0.6, D = 10, 8 indices; Sec.
- * III.A) and W = 80, b = 8, SELECT_ALL, FP32, pca_sample = 16384. */
+ * III.A) and W = 80, b = 8, SELECT_ALL, FP32, pca_sample = 16384, knn = 0
+ * (window search). */
 void sfc_params_default(sfc_params* p);
 
 /* Build the multi-index (Sec. II.A-C): dictionary extraction, the pixel subsets
@@ -139,9 +143,21 @@ int sfc_index_export(const sfc_index* ix, int64_t* dict, int32_t* subsets, float
 int sfc_query_batch(const sfc_index* ix, const float* grid, const uint8_t* cur_mask, const int32_t* centres,
                     int64_t Q, int64_t* pick, float* cost, void* stream);
 
+/* With knn = k > 0 in the build parameters, the window is replaced by the
+ * paper's exact k-NN list (Sec. II.D) per selected index: the k dictionary
+ * entries nearest to the query in the quantised principal space (squared
+ * Euclidean distance of the integer coordinates, ties by id).  The index then
+ * also keeps the quantised coordinates in curve order (C*N*D uint32); each
+ * list is found by one warp that scans the index's sorted keys inside the
+ * z-interval of the box around the query that the current k-th distance
+ * spans, shrinking the box as the list improves and jumping over runs of keys
+ * outside the box with Tropf and Herzog's BIGMIN.  The candidates are the union
+ * of the lists, rescored as above. */
+
 /* Intermediate results of sfc_query_batch for checking: qkeys (Q*C uint64),
  * pos (Q*C int64 lower_bound positions; -1 for unselected indices),
- * cand (Q*C*W int32 sorted unique candidate ids, padded with -1), ncand (Q int32). */
+ * cand (Q*C*L int32 sorted unique candidate ids, padded with -1; L = W, or k
+ * with knn = k), ncand (Q int32). */
 int sfc_query_candidates(const sfc_index* ix, const float* grid, const uint8_t* cur_mask, const int32_t* centres,
                          int64_t Q, uint64_t* qkeys, int64_t* pos, int32_t* cand, int32_t* ncand, void* stream);
 
@@ -157,9 +173,9 @@ int fullscan_query_batch(const float* grid, const uint8_t* dict_mask, const uint
  * s(q, j) = sum m w (p'^2 - 2 t' p') (the cost minus a per-query constant,
  * values centred per channel) as a tensor-core GEMM (tcgen05; FP16 operands
  * split into high and low parts, FP32 accumulation), keeps per query the
- * minimum of every 256-entry dictionary tile, and rescores exactly (FP32 +
- * FP64 band, as above) every tile whose minimum lies within twice the pre-score
- * error bound E_q of the smallest: the tile of the exact argmin always
+ * minimum of every 32-entry dictionary group, and rescores exactly (FP32 +
+ * FP64 band, as above) every group whose minimum lies within twice the pre-score
+ * error bound E_q of the smallest: the group of the exact argmin always
  * qualifies, so picks and costs are those of the FP32 path.  E_q bounds the
  * operand splitting (3.01 u16^2 sum|a b|) and the FP32 accumulation
  * (8 K' u32 sum|a b|, K' = 6 n), with |p'| bounded by the grid's per-channel

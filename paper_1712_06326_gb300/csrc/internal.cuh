@@ -70,6 +70,8 @@ struct Index {
   uint64_t* keys = nullptr;   // C*N unsorted (kept only with keep_intermediates)
   uint64_t* skeys = nullptr;  // C*N
   uint32_t* sids = nullptr;   // C*N
+  int knn = 0;                // k of the exact k-NN lists (0: window search)
+  uint32_t* sqc = nullptr;    // C*N*D quantised shifted coordinates in curve order (knn > 0 only)
   // tracing (sfc_trace): phase events of the build and the eigen-solve iterations
   cudaEvent_t ev[SFC_TRACE_PHASES + 1] = {};
   bool traced = false;
@@ -97,6 +99,9 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st);
 
 // k_index.cu: projection, quantisation, Morton keys.
 int project_and_key(Index& ix, const float* grid, cudaStream_t st, float* proj, uint64_t* keys);
+// Quantised, shifted coordinates of the dictionary in each index's sorted order
+// (the k-NN search reads them next to the sorted keys): ix.sqc from proj.
+int sorted_coords(Index& ix, const float* proj, cudaStream_t st);
 
 // k_sort.cu: stable LSD radix sort (onesweep) of (key, id) per index.
 int radix_sort_pairs(const uint64_t* keys, uint64_t* skeys, uint32_t* sids, int64_t N, int C, int key_bits,

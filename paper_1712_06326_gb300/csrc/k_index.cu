@@ -150,6 +150,20 @@ __global__ void k_keys(const float* __restrict__ proj, int64_t N, int D, int bit
   keys[(int64_t)c * N + j] = morton_key(q, D, bp);
 }
 
+// sqc[c][i][k] = quantised shifted coordinate k of the entry at sorted slot i of index c
+__global__ void k_sorted_coords(const float* __restrict__ proj, const uint32_t* __restrict__ sids, int64_t N, int D,
+                                int bits, const float* __restrict__ lo, const float* __restrict__ scale,
+                                const int32_t* __restrict__ shifts, uint32_t* __restrict__ sqc) {
+  const int c = blockIdx.y;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= N * D) return;
+  const int64_t i = t / D;
+  const int k = (int)(t - i * D);
+  const int64_t j = sids[(int64_t)c * N + i];
+  const float y = proj[((int64_t)c * N + j) * D + k];
+  sqc[(int64_t)c * N * D + t] = quantise_one(y, lo[c * D + k], scale[c * D + k], bits) + (uint32_t)shifts[c * D + k];
+}
+
 template <int D>
 int launch_project(const Index& ix, const float* grid, float* proj, uint32_t* lohi, cudaStream_t st) {
   const size_t shm = sizeof(float) * (ix.s * D + ix.s) + sizeof(int) * ix.s;
@@ -186,6 +200,15 @@ int project_and_key(Index& ix, const float* grid, cudaStream_t st, float* proj, 
   k_keys<<<grd, 256, 0, st>>>(proj, ix.N, ix.D, ix.bits, ix.bp, ix.lo, ix.scale, ix.shifts, keys);
   SFC_TRY(cudaGetLastError());
   cudaFreeAsync(lohi, st);
+  return SFC_OK;
+}
+
+int sorted_coords(Index& ix, const float* proj, cudaStream_t st) {
+  SFC_TRY(pmalloc(&ix.sqc, sizeof(uint32_t) * ix.C * ix.N * ix.D, st));
+  dim3 grd((unsigned)((ix.N * ix.D + 255) / 256), ix.C);
+  count_launch();
+  k_sorted_coords<<<grd, 256, 0, st>>>(proj, ix.sids, ix.N, ix.D, ix.bits, ix.lo, ix.scale, ix.shifts, ix.sqc);
+  SFC_TRY(cudaGetLastError());
   return SFC_OK;
 }
 

@@ -8,7 +8,9 @@
 //     the same FP32 fused multiply-add chain as the dictionary (unknown values
 //     contribute exactly zero), quantise with the index's lo/scale (clamped),
 //     shift, Morton key; warp-cooperative lower_bound on the sorted keys (32
-//     probes per step); copy the ids of the W sorted slots around the position;
+//     probes per step); copy the ids of the W sorted slots around the position,
+//     or, with knn = k, find the exact k nearest entries in the quantised space
+//     (Sec. II.D; warp_knn below);
 //  4. bitonic sort + de-duplication of the candidate union in shared memory;
 //  5. filter-and-refine (Fig. 1(d)): FP32 masked-L2 cost of every candidate, one
 //     warp per candidate, each lane holding its patch elements' known flag,
@@ -31,8 +33,9 @@ struct QArgs {
   const uint8_t* mask;
   const int32_t* centres;
   Geo g;
-  int C, D, bits, bp, W, select, m, s, L, maxsel;
+  int C, D, bits, bp, W, select, m, s, L, maxsel, knn, capw;
   int64_t N;
+  const uint32_t* sqc;
   const uint32_t* dict;
   const int32_t* sub_pix;
   const float* basis;
@@ -76,7 +79,220 @@ __device__ int64_t warp_lower_bound(const uint64_t* __restrict__ a, int64_t N, u
   return lo + __popc(__ballot_sync(0xffffffffu, lt));
 }
 
-template <int MAXE, bool WEIGHTED>
+// Morton key (top 64 bits; bit planes from the top, dimension 0 first) of the
+// coordinates held by lanes 0..D-1.
+__device__ uint64_t warp_key(uint32_t x, int D, int bp) {
+  uint64_t key = 0;
+  int nb = 0;
+  for (int p = bp - 1; p >= 0 && nb < 64; --p)
+    for (int k = 0; k < D && nb < 64; ++k, ++nb) {
+      const uint32_t v = __shfl_sync(0xffffffffu, x, k);
+      key = (key << 1) | (uint64_t)((v >> p) & 1u);
+    }
+  return key;
+}
+
+// Is the key inside the key-space box [zmin, zmax]?  Per dimension, the key bits
+// it owns (dmask in lane d) compare as integers like its truncated coordinate.
+__device__ bool key_in_box(uint64_t z, uint64_t zmin, uint64_t zmax, uint64_t dmask, int D) {
+  bool in = true;
+  for (int d = 0; d < D; ++d) {
+    const uint64_t m = __shfl_sync(0xffffffffu, dmask, d);
+    in = in && (z & m) >= (zmin & m) && (z & m) <= (zmax & m);
+  }
+  return in;
+}
+
+// BIGMIN (Tropf & Herzog, 1981): the smallest key greater than z inside the
+// key-space box [zmin, zmax] (z outside the box, zmin <= z <= zmax); false when
+// there is none.  Walks the key bits from the top with the three bits of z,
+// zmin and zmax; "load 1000" / "load 0111" set the current bit of the owning
+// dimension and clear / set that dimension's lower bits.  Warp-uniform.
+__device__ bool bigmin(uint64_t z, uint64_t zmin, uint64_t zmax, uint64_t dmask, int D, int nb, uint64_t* out) {
+  uint64_t cand = 0;
+  bool have = false;
+  for (int t = 0; t < nb; ++t) {
+    const int i = nb - 1 - t;
+    const uint64_t bit = 1ull << i;
+    const uint64_t below = __shfl_sync(0xffffffffu, dmask, t % D) & (bit - 1);
+    const int zb = (int)((z >> i) & 1u), lb = (int)((zmin >> i) & 1u), hb = (int)((zmax >> i) & 1u);
+    if (!zb && !lb && hb) {
+      cand = (zmin & ~below) | bit;  // load 1000 into zmin
+      have = true;
+      zmax = (zmax & ~bit) | below;  // load 0111 into zmax
+    } else if (!zb && lb && hb) {
+      *out = zmin;
+      return true;
+    } else if (zb && !lb && !hb) {
+      *out = cand;
+      return have;
+    } else if (zb && !lb && hb) {
+      zmin = (zmin & ~below) | bit;  // load 1000 into zmin
+    }
+  }
+  *out = z;  // z lies in the box (not reached for a key outside it)
+  return true;
+}
+
+// The kk (<= 128) entries of one index nearest to the query in the quantised
+// space, by (squared Euclidean distance, id) -- the paper's exact k-NN list
+// (Sec. II.D).  Lane d < D holds the query's shifted coordinate x; key and pos
+// are its Morton key and lower_bound position.  The list lives in registers
+// (entry e = 32 s + lane in slot s); the warp first scores the 2 kk sorted
+// slots around pos, then scans the sorted keys of the z-interval [key(lo),
+// key(hi)] of the box lo..hi = x -+ floor(sqrt(k-th distance)): 32 entries per
+// step, the box and interval shrinking whenever the list improves, and a jump
+// (BIGMIN + lower_bound) whenever the last entry of a step lies outside the
+// box.  Every entry whose truncated coordinates lie in the final box is scored,
+// so the list is exact.  Writes the ids to out[0..kk).
+__device__ void warp_knn(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sq,
+                         const uint32_t* __restrict__ si, int64_t N, int D, int bp, uint32_t x, int64_t pos, int kk,
+                         uint32_t* out) {
+  constexpr unsigned FULL = 0xffffffffu;
+  constexpr int KPL = 4;
+  const int lane = threadIdx.x & 31;
+  const int nb = D * bp < 64 ? D * bp : 64;
+  uint32_t qv[16];
+#pragma unroll
+  for (int d = 0; d < 16; ++d) qv[d] = __shfl_sync(FULL, x, d);
+  uint64_t dmask = 0;
+  if (lane < D)
+    for (int t = lane; t < nb; t += D) dmask |= 1ull << (nb - 1 - t);
+  const int64_t cmax = (1ll << bp) - 1;
+  uint64_t ld[KPL];
+  uint32_t li[KPL];
+#pragma unroll
+  for (int s = 0; s < KPL; ++s) {
+    ld[s] = ~0ull;
+    li[s] = ~0u;
+  }
+  // the list's worst entry (largest (distance, id)), its lane and slot
+  uint64_t wd = ~0ull;
+  uint32_t wi = ~0u;
+  int wl = 0, ws = 0;
+  auto find_worst = [&]() {
+    uint64_t bd = 0;
+    uint32_t bi = 0;
+    int bs = -1;
+#pragma unroll
+    for (int s = 0; s < KPL; ++s)
+      if (s * 32 + lane < kk && (bs < 0 || ld[s] > bd || (ld[s] == bd && li[s] > bi))) {
+        bd = ld[s];
+        bi = li[s];
+        bs = s;
+      }
+    int bl = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t od = __shfl_xor_sync(FULL, bd, o);
+      const uint32_t oi = __shfl_xor_sync(FULL, bi, o);
+      const int ol = __shfl_xor_sync(FULL, bl, o), os = __shfl_xor_sync(FULL, bs, o);
+      const bool take = os >= 0 && (bs < 0 || od > bd || (od == bd && (oi > bi || (oi == bi && ol < bl))));
+      if (take) {
+        bd = od;
+        bi = oi;
+        bl = ol;
+        bs = os;
+      }
+    }
+    wd = bd;
+    wi = bi;
+    wl = bl;
+    ws = bs;
+  };
+  find_worst();
+  // score the entries [i, end) (one per lane) and merge the better ones
+  auto score = [&](int64_t i, int64_t end, uint64_t zmax, bool use_zmax) -> bool {
+    const int64_t e = i + lane;
+    bool ok = e < end;
+    uint64_t d2 = ~0ull;
+    uint32_t id = ~0u;
+    if (ok && use_zmax) ok = sk[e] <= zmax;
+    if (ok) {
+      const uint32_t* c = sq + e * D;
+      d2 = 0;
+#pragma unroll
+      for (int d = 0; d < 16; ++d)
+        if (d < D) {
+          const int64_t t = (int64_t)c[d] - (int64_t)qv[d];
+          d2 += (uint64_t)(t * t);
+        }
+      id = si[e];
+    }
+    unsigned bal = __ballot_sync(FULL, ok && (d2 < wd || (d2 == wd && id < wi)));
+    bool changed = false;
+    while (bal) {
+      const int b = __ffs(bal) - 1;
+      bal &= bal - 1;
+      const uint64_t bd = __shfl_sync(FULL, d2, b);
+      const uint32_t bi = __shfl_sync(FULL, id, b);
+      if (bd < wd || (bd == wd && bi < wi)) {
+        if (lane == wl) {
+#pragma unroll
+          for (int s = 0; s < KPL; ++s)
+            if (s == ws) {
+              ld[s] = bd;
+              li[s] = bi;
+            }
+        }
+        find_worst();
+        changed = true;
+      }
+    }
+    return changed;
+  };
+  // 1) the 2 kk sorted slots around the position
+  const int64_t wlen = 2 * (int64_t)kk < N ? 2 * (int64_t)kk : N;
+  int64_t w0 = pos - kk;
+  if (w0 > N - wlen) w0 = N - wlen;
+  if (w0 < 0) w0 = 0;
+  const int64_t w1 = w0 + wlen;
+  for (int64_t i = w0; i < w1; i += 32) score(i, i + 32 < w1 ? i + 32 : w1, 0, false);
+  // 2) the box scan
+  if (wlen < N) {
+    uint64_t zmin = 0, zmax = ~0ull;
+    auto make_box = [&]() {
+      int64_t R;
+      if (wd == ~0ull) {
+        R = cmax;
+      } else {
+        R = (int64_t)sqrt((double)wd);
+        while (R > 0 && (uint64_t)R * (uint64_t)R > wd) --R;
+        while ((uint64_t)(R + 1) * (uint64_t)(R + 1) <= wd) ++R;
+      }
+      const int64_t lo = (int64_t)x - R < 0 ? 0 : (int64_t)x - R;
+      const int64_t hi = (int64_t)x + R > cmax ? cmax : (int64_t)x + R;
+      zmin = warp_key((uint32_t)lo, D, bp);
+      zmax = warp_key((uint32_t)hi, D, bp);
+    };
+    make_box();
+    int64_t i = warp_lower_bound(sk, N, zmin);
+    while (i < N) {
+      if (i >= w0 && i < w1) {
+        i = w1;
+        continue;
+      }
+      const int64_t lim = i < w0 ? w0 : N;
+      const int64_t end = i + 32 < lim ? i + 32 : lim;
+      if (sk[i] > zmax) break;  // keys are sorted: the rest lies beyond the box
+      if (score(i, end, zmax, true)) make_box();
+      const uint64_t kl = sk[end - 1];
+      int64_t next = end;
+      if (kl > zmax) break;
+      if (!key_in_box(kl, zmin, zmax, dmask, D)) {
+        uint64_t z2;
+        if (!bigmin(kl, zmin, zmax, dmask, D, nb, &z2) || z2 > zmax) break;
+        if (z2 > kl) next = end + warp_lower_bound(sk + end, N - end, z2);
+      }
+      i = next;
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < KPL; ++s)
+    if (s * 32 + lane < kk) out[s * 32 + lane] = li[s];
+}
+
+template <int MAXE, bool WEIGHTED, bool KNN>
 __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   const int64_t q = blockIdx.x;
   const Geo& g = a.g;
@@ -152,7 +368,8 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   }
   __syncthreads();
   const int nsel = s_nsel;
-  const int64_t len = a.W < a.N ? a.W : a.N;
+  const int64_t wk = a.knn > 0 ? a.knn : a.W;
+  const int64_t len = wk < a.N ? wk : a.N;
   int64_t maxs = a.N - a.W;
   if (maxs < 0) maxs = 0;
 
@@ -174,20 +391,19 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
     uint32_t qk = 0;
     if (lane < a.D) qk = quantise_one(acc, a.lo[c * a.D + lane], a.scale[c * a.D + lane], a.bits) +
                          (uint32_t)a.shifts[c * a.D + lane];
-    uint64_t key = 0;
-    int nb = 0;
-    for (int p = a.bp - 1; p >= 0 && nb < 64; --p)
-      for (int k = 0; k < a.D && nb < 64; ++k, ++nb) {
-        uint32_t v = __shfl_sync(0xffffffffu, qk, k);
-        key = (key << 1) | (uint64_t)((v >> p) & 1u);
-      }
+    const uint64_t key = warp_key(qk, a.D, a.bp);
     const uint64_t* sk = a.skeys + (int64_t)c * a.N;
     int64_t pos = warp_lower_bound(sk, a.N, key);
-    int64_t start = pos - a.W / 2;
-    if (start > maxs) start = maxs;
-    if (start < 0) start = 0;
-    const uint32_t* si = a.sids + (int64_t)c * a.N + start;
-    for (int64_t i = lane; i < len; i += 32) cand[slot * len + i] = si[i];
+    if (KNN) {
+      warp_knn(sk, a.sqc + (int64_t)c * a.N * a.D, a.sids + (int64_t)c * a.N, a.N, a.D, a.bp, qk, pos, (int)len,
+               cand + slot * len);
+    } else {
+      int64_t start = pos - a.W / 2;
+      if (start > maxs) start = maxs;
+      if (start < 0) start = 0;
+      const uint32_t* si = a.sids + (int64_t)c * a.N + start;
+      for (int64_t i = lane; i < len; i += 32) cand[slot * len + i] = si[i];
+    }
     if (a.qkeys && lane == 0) {
       a.qkeys[q * a.C + c] = key;
       a.pos[q * a.C + c] = pos;
@@ -261,7 +477,7 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   __syncthreads();
   const int ncand = s_ncand;
   if (a.cand_out) {
-    const int cap = a.C * a.W;
+    const int cap = a.C * a.capw;
     for (int i = tid; i < cap; i += kQThreads) a.cand_out[q * cap + i] = i < ncand ? (int32_t)ucand[i] : -1;
     if (tid == 0) a.ncand_out[q] = ncand;
   }
@@ -367,14 +583,19 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   }
 }
 
-template <int MAXE, bool W>
-int launch_q(const QArgs& a, int64_t Q, size_t shm, cudaStream_t st) {
+template <int MAXE, bool W, bool KNN>
+int launch_q3(const QArgs& a, int64_t Q, size_t shm, cudaStream_t st) {
   if (shm > 48 * 1024)
-    SFC_TRY(cudaFuncSetAttribute(k_query<MAXE, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    SFC_TRY(cudaFuncSetAttribute(k_query<MAXE, W, KNN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   count_launch();
-  k_query<MAXE, W><<<(unsigned)Q, kQThreads, shm, st>>>(a);
+  k_query<MAXE, W, KNN><<<(unsigned)Q, kQThreads, shm, st>>>(a);
   SFC_TRY(cudaGetLastError());
   return SFC_OK;
+}
+
+template <int MAXE, bool W>
+int launch_q(const QArgs& a, int64_t Q, size_t shm, cudaStream_t st) {
+  return a.knn > 0 ? launch_q3<MAXE, W, true>(a, Q, shm, st) : launch_q3<MAXE, W, false>(a, Q, shm, st);
 }
 
 template <bool W>
@@ -415,12 +636,20 @@ int query_batch(const Index& ix, const float* grid, const uint8_t* cur_mask, con
   a.s = ix.s;
   a.N = ix.N;
   a.maxsel = ix.select == SFC_SELECT_BEST ? 1 : ix.C;
-  int64_t len = ix.W < ix.N ? ix.W : ix.N;
+  a.knn = ix.knn;
+  a.sqc = ix.sqc;
+  a.capw = ix.knn > 0 ? ix.knn : ix.W;
+  if (ix.knn > 0 && !ix.sqc) {
+    set_error("k-NN search without the index's quantised coordinates");
+    return SFC_EINVAL;
+  }
+  const int64_t wk = ix.knn > 0 ? ix.knn : ix.W;
+  int64_t len = wk < ix.N ? wk : ix.N;
   int64_t need = len * a.maxsel;
   int L = 2;
   while (L < need) L <<= 1;
   if (L > 8192) {
-    set_error("curves * window exceeds 8192 candidates per query");
+    set_error("curves * window (or k) exceeds 8192 candidates per query");
     return SFC_EINVAL;
   }
   a.L = L;

@@ -282,7 +282,7 @@ void free_index(Index& ix) {
   cudaDeviceSynchronize();
   trace_fold(ix);
   void* ptrs[] = {ix.dict,  ix.eoff_all, ix.sub_eoff, ix.sub_pix, ix.weights, ix.basis, ix.mean, ix.evals,
-                  ix.lo,    ix.scale,    ix.shifts,   ix.proj,    ix.keys,    ix.skeys, ix.sids};
+                  ix.lo,    ix.scale,    ix.shifts,   ix.proj,    ix.keys,    ix.skeys, ix.sids, ix.sqc};
   cudaDeviceSynchronize();
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, nullptr);
@@ -328,8 +328,10 @@ int build_index(const float* grid, const uint8_t* dict_mask, const sfc_grid* gp,
     return SFC_EINVAL;
   }
   if (p->dims < 1 || p->dims > 16 || p->bits < 1 || p->bits > 21 || p->window < 1 ||
-      !(p->subset_frac > 0.0f && p->subset_frac <= 1.0f) || (p->select != SFC_SELECT_ALL && p->select != SFC_SELECT_BEST)) {
-    set_error("parameter out of range (dims 1..16, bits 1..21, window >= 1, subset_frac in (0, 1], select)");
+      !(p->subset_frac > 0.0f && p->subset_frac <= 1.0f) || (p->select != SFC_SELECT_ALL && p->select != SFC_SELECT_BEST) ||
+      p->knn < 0 || p->knn > 128) {
+    set_error("parameter out of range (dims 1..16, bits 1..21, window >= 1, subset_frac in (0, 1], select, "
+              "knn 0..128)");
     return SFC_EINVAL;
   }
   if (p->precision != SFC_FP32) {
@@ -340,6 +342,7 @@ int build_index(const float* grid, const uint8_t* dict_mask, const sfc_grid* gp,
   ix.D = p->dims;
   ix.bits = p->bits;
   ix.W = p->window;
+  ix.knn = p->knn;
   ix.select = p->select;
   ix.frac = p->subset_frac;
   ix.pca_sample = p->pca_sample;
@@ -424,6 +427,7 @@ int build_index(const float* grid, const uint8_t* dict_mask, const sfc_grid* gp,
   trace_mark(ix, 5, st);
   const int key_bits = std::min(64, D * ix.bp);
   SFC_CHECK(radix_sort_pairs(keys, ix.skeys, ix.sids, N, C, key_bits, st));
+  if (ix.knn > 0) SFC_CHECK(sorted_coords(ix, proj, st));
   trace_mark(ix, 6, st);
   if (ix.keep) {
     ix.proj = proj;

@@ -38,7 +38,7 @@ class sfc_params(C.Structure):
                 ("window", C.c_int32), ("subset_frac", C.c_float), ("shifts", C.c_void_p),
                 ("ch_weights", C.c_void_p), ("basis", C.c_void_p), ("mean", C.c_void_p), ("select", C.c_int32),
                 ("precision", C.c_int32), ("pca_sample", C.c_int64), ("priority", C.c_int32),
-                ("keep_intermediates", C.c_int32)]
+                ("keep_intermediates", C.c_int32), ("knn", C.c_int32)]
 
 
 _lib = None
@@ -215,7 +215,8 @@ def sfc_query_candidates(ix: Index, grid: torch.Tensor, cur_mask: torch.Tensor, 
     grid = _dev(grid, torch.float32)
     cur_mask = _dev(cur_mask, torch.uint8)
     centres = _dev(centres, torch.int32)
-    Q, C_, W = centres.shape[0], ix.params.curves, ix.params.window
+    Q, C_ = centres.shape[0], ix.params.curves
+    W = ix.params.knn if ix.params.knn > 0 else ix.params.window
     dev = grid.device
     qkeys = torch.empty((Q, C_), dtype=torch.int64, device=dev)  # uint64 bits
     pos = torch.empty((Q, C_), dtype=torch.int64, device=dev)
