@@ -406,6 +406,30 @@ def main():
                                "picks_and_costs_equal_fp32": same,
                                "phases_ms": {k: v / calls for k, v in tct["ms"].items()}, "roofline": tc_roof}
 
+    # ---- the paper's exact k-NN lists (Sec. II.D, k = 80) instead of windows ---
+    knn_prm = dict(prm, knn=80)
+    kn_ms, kq_ms = [], []
+    for r in range(3):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        mid = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ixk = sfc.sfc_index_build(gd, md, **knn_prm)
+        mid.record(stream)
+        kp, kc = sfc.sfc_query_batch(ixk, gd, md, td)
+        b.record(stream)
+        b.synchronize()
+        if r > 0:
+            kn_ms.append(a.elapsed_time(b))
+            kq_ms.append(mid.elapsed_time(b))
+        ixk.close()
+    kagree = float((kp[sel] == fp).double().mean().item())
+    kae = float((torch.sqrt(kc[sel].double()) / torch.sqrt(fc.double()).clamp_min(1e-30) - 1.0).mean().item())
+    sfc_knn = {"k": 80, "qps": Q / (statistics.mean(kn_ms) / 1000.0), "ms_per_step": statistics.mean(kn_ms),
+               "query_ms": statistics.mean(kq_ms), "query_only_qps": Q / (statistics.mean(kq_ms) / 1000.0),
+               "pick_agreement_fullscan": kagree, "acceleration_error_mean": kae}
+
     # ---- end to end through the C-ABI with host buffers ----------------------
     gh = torch.from_numpy(g).pin_memory()
     mh = torch.from_numpy(m).pin_memory()
@@ -437,13 +461,17 @@ def main():
     g1, m1 = synth.sines2d(128)
     inp = {}
     for mode, name in ((sfc.SFC_MODE_FULLSCAN, "fullscan"), (sfc.SFC_MODE_SFC, "sfc")):
-        gg = torch.from_numpy(g1).to(dev)
-        mm = torch.from_numpy(m1).to(dev)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        steps, _ = sfc.inpaint_run(gg, mm, mode=mode, K=9, curves=8, dims=8, bits=16, window=64, pca_sample=0)
-        torch.cuda.synchronize()
-        inp[name] = {"ms": 1000 * (time.perf_counter() - t0), "steps": steps}
+        times = []
+        for r in range(3):  # the first run loads the fill kernels: untimed
+            gg = torch.from_numpy(g1).to(dev)
+            mm = torch.from_numpy(m1).to(dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            steps, _ = sfc.inpaint_run(gg, mm, mode=mode, K=9, curves=8, dims=8, bits=16, window=64, pca_sample=0)
+            torch.cuda.synchronize()
+            if r > 0:
+                times.append(1000 * (time.perf_counter() - t0))
+        inp[name] = {"ms": statistics.mean(times), "steps": steps}
     ix.close()
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -456,7 +484,7 @@ def main():
             "roofline": roofline, "gpu_launches": int(launches), "e2e": e2e, "clocks": clk,
             "query_only": {"qps": query_only_qps, "ms": q_ms_mean},
             "index_build_ms": tot_ms / args.steps - q_ms_mean, "phases_ms": phases_ms,
-            "fullscan": fullscan, "inpaint_128x128": inp}
+            "fullscan": fullscan, "sfc_knn": sfc_knn, "inpaint_128x128": inp}
     if rank == 0:
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_obj()

@@ -92,62 +92,47 @@ __device__ uint64_t warp_key(uint32_t x, int D, int bp) {
   return key;
 }
 
-// Is the key inside the key-space box [zmin, zmax]?  Per dimension, the key bits
-// it owns (dmask in lane d) compare as integers like its truncated coordinate.
-__device__ bool key_in_box(uint64_t z, uint64_t zmin, uint64_t zmax, uint64_t dmask, int D) {
-  bool in = true;
-  for (int d = 0; d < D; ++d) {
-    const uint64_t m = __shfl_sync(0xffffffffu, dmask, d);
-    in = in && (z & m) >= (zmin & m) && (z & m) <= (zmax & m);
+// Bits of v at the positions set in m, the highest first (a software pext).
+__device__ inline uint32_t extract_bits(uint64_t v, uint64_t m) {
+  uint32_t r = 0;
+  while (m) {
+    const int i = 63 - __clzll((long long)m);
+    r = (r << 1) | (uint32_t)((v >> i) & 1u);
+    m &= ~(1ull << i);
   }
-  return in;
+  return r;
 }
 
-// BIGMIN (Tropf & Herzog, 1981): the smallest key greater than z inside the
-// key-space box [zmin, zmax] (z outside the box, zmin <= z <= zmax); false when
-// there is none.  Walks the key bits from the top with the three bits of z,
-// zmin and zmax; "load 1000" / "load 0111" set the current bit of the owning
-// dimension and clear / set that dimension's lower bits.  Warp-uniform.
-__device__ bool bigmin(uint64_t z, uint64_t zmin, uint64_t zmax, uint64_t dmask, int D, int nb, uint64_t* out) {
-  uint64_t cand = 0;
-  bool have = false;
-  for (int t = 0; t < nb; ++t) {
-    const int i = nb - 1 - t;
-    const uint64_t bit = 1ull << i;
-    const uint64_t below = __shfl_sync(0xffffffffu, dmask, t % D) & (bit - 1);
-    const int zb = (int)((z >> i) & 1u), lb = (int)((zmin >> i) & 1u), hb = (int)((zmax >> i) & 1u);
-    if (!zb && !lb && hb) {
-      cand = (zmin & ~below) | bit;  // load 1000 into zmin
-      have = true;
-      zmax = (zmax & ~bit) | below;  // load 0111 into zmax
-    } else if (!zb && lb && hb) {
-      *out = zmin;
-      return true;
-    } else if (zb && !lb && !hb) {
-      *out = cand;
-      return have;
-    } else if (zb && !lb && hb) {
-      zmin = (zmin & ~below) | bit;  // load 1000 into zmin
-    }
-  }
-  *out = z;  // z lies in the box (not reached for a key outside it)
-  return true;
+// One pending region of the k-NN traversal: the key-space box [zmin, zmax] and
+// the slots [a, b) of the sorted array whose keys lie in [zmin, zmax].
+struct KnnRegion {
+  uint64_t zmin, zmax;
+  int64_t a, b;
+};
+constexpr int kKnnStack = 66;  // depth <= key bits + 1
+constexpr int kKnnLeaf = 2048;  // mu: regions of at most this many slots are scanned (measured best of 32..8192)
+
+// First slot in [0, n) whose key is > key.
+__device__ inline int64_t warp_upper_bound(const uint64_t* __restrict__ a, int64_t n, uint64_t key) {
+  return key == ~0ull ? n : warp_lower_bound(a, n, key + 1);
 }
 
 // The kk (<= 128) entries of one index nearest to the query in the quantised
-// space, by (squared Euclidean distance, id) -- the paper's exact k-NN list
-// (Sec. II.D).  Lane d < D holds the query's shifted coordinate x; key and pos
-// are its Morton key and lower_bound position.  The list lives in registers
-// (entry e = 32 s + lane in slot s); the warp first scores the 2 kk sorted
-// slots around pos, then scans the sorted keys of the z-interval [key(lo),
-// key(hi)] of the box lo..hi = x -+ floor(sqrt(k-th distance)): 32 entries per
-// step, the box and interval shrinking whenever the list improves, and a jump
-// (BIGMIN + lower_bound) whenever the last entry of a step lies outside the
-// box.  Every entry whose truncated coordinates lie in the final box is scored,
-// so the list is exact.  Writes the ids to out[0..kk).
+// space, by (squared Euclidean distance, id) -- the paper's exact k-NN list,
+// found with its outside-in search (Sec. II.D, Fig. 3): a region of the key
+// space (an axis-aligned box of truncated coordinates, i.e. a z-interval) is
+// split where the most significant bit of its corners differs, into the
+// halves [min, litmax] and [bigmin, max]; their slot ranges come from binary
+// searches inside the parent's range; the half nearer to the query is
+// visited first, and a half whose box lies farther from the query than the
+// current k-th entry is culled; regions of at most kKnnLeaf slots (or a single
+// cell) are scanned entry by entry.  Lane d < D holds the query's shifted
+// coordinate x.  The list lives in registers (entry e = 32 s + lane in slot s);
+// the region stack (kKnnStack entries) in shared memory.  Writes the ids to
+// out[0..kk).
 __device__ void warp_knn(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sq,
-                         const uint32_t* __restrict__ si, int64_t N, int D, int bp, uint32_t x, int64_t pos, int kk,
-                         uint32_t* out) {
+                         const uint32_t* __restrict__ si, int64_t N, int D, int bp, uint32_t x, int kk,
+                         uint32_t* out, KnnRegion* stk) {
   constexpr unsigned FULL = 0xffffffffu;
   constexpr int KPL = 4;
   const int lane = threadIdx.x & 31;
@@ -155,10 +140,15 @@ __device__ void warp_knn(const uint64_t* __restrict__ sk, const uint32_t* __rest
   uint32_t qv[16];
 #pragma unroll
   for (int d = 0; d < 16; ++d) qv[d] = __shfl_sync(FULL, x, d);
+  // lane d < D: the key bits of dimension d, and how many coordinate bits lie below them
   uint64_t dmask = 0;
+  int kept = 0;
   if (lane < D)
-    for (int t = lane; t < nb; t += D) dmask |= 1ull << (nb - 1 - t);
-  const int64_t cmax = (1ll << bp) - 1;
+    for (int t = lane; t < nb; t += D) {
+      dmask |= 1ull << (nb - 1 - t);
+      ++kept;
+    }
+  const int low = bp - kept;
   uint64_t ld[KPL];
   uint32_t li[KPL];
 #pragma unroll
@@ -201,26 +191,37 @@ __device__ void warp_knn(const uint64_t* __restrict__ sk, const uint32_t* __rest
     ws = bs;
   };
   find_worst();
-  // score the entries [i, end) (one per lane) and merge the better ones
-  auto score = [&](int64_t i, int64_t end, uint64_t zmax, bool use_zmax) -> bool {
+  // score the slots [i, end) (one per lane) and merge the better entries
+  auto score = [&](int64_t i, int64_t end) {
     const int64_t e = i + lane;
-    bool ok = e < end;
+    const bool ok = e < end;
     uint64_t d2 = ~0ull;
     uint32_t id = ~0u;
-    if (ok && use_zmax) ok = sk[e] <= zmax;
     if (ok) {
+      // coordinates < 2^22: 32-bit differences, 32 x 32 -> 64-bit squares
+      auto sq_diff = [](uint32_t c, uint32_t q) {
+        const int t = (int)(c - q);
+        return (uint64_t)((long long)t * t);
+      };
       const uint32_t* c = sq + e * D;
       d2 = 0;
+      if ((D & 3) == 0) {
+        const uint4* c4 = reinterpret_cast<const uint4*>(c);  // rows of 4 D words: 16-byte aligned
 #pragma unroll
-      for (int d = 0; d < 16; ++d)
-        if (d < D) {
-          const int64_t t = (int64_t)c[d] - (int64_t)qv[d];
-          d2 += (uint64_t)(t * t);
-        }
+        for (int v = 0; v < 4; ++v)
+          if (4 * v < D) {
+            const uint4 w = __ldg(c4 + v);
+            d2 += sq_diff(w.x, qv[4 * v]) + sq_diff(w.y, qv[4 * v + 1]) + sq_diff(w.z, qv[4 * v + 2]) +
+                  sq_diff(w.w, qv[4 * v + 3]);
+          }
+      } else {
+#pragma unroll
+        for (int d = 0; d < 16; ++d)
+          if (d < D) d2 += sq_diff(__ldg(c + d), qv[d]);
+      }
       id = si[e];
     }
     unsigned bal = __ballot_sync(FULL, ok && (d2 < wd || (d2 == wd && id < wi)));
-    bool changed = false;
     while (bal) {
       const int b = __ffs(bal) - 1;
       bal &= bal - 1;
@@ -236,56 +237,55 @@ __device__ void warp_knn(const uint64_t* __restrict__ sk, const uint32_t* __rest
             }
         }
         find_worst();
-        changed = true;
       }
     }
-    return changed;
   };
-  // 1) the 2 kk sorted slots around the position
-  const int64_t wlen = 2 * (int64_t)kk < N ? 2 * (int64_t)kk : N;
-  int64_t w0 = pos - kk;
-  if (w0 > N - wlen) w0 = N - wlen;
-  if (w0 < 0) w0 = 0;
-  const int64_t w1 = w0 + wlen;
-  for (int64_t i = w0; i < w1; i += 32) score(i, i + 32 < w1 ? i + 32 : w1, 0, false);
-  // 2) the box scan
-  if (wlen < N) {
-    uint64_t zmin = 0, zmax = ~0ull;
-    auto make_box = [&]() {
-      int64_t R;
-      if (wd == ~0ull) {
-        R = cmax;
-      } else {
-        R = (int64_t)sqrt((double)wd);
-        while (R > 0 && (uint64_t)R * (uint64_t)R > wd) --R;
-        while ((uint64_t)(R + 1) * (uint64_t)(R + 1) <= wd) ++R;
-      }
-      const int64_t lo = (int64_t)x - R < 0 ? 0 : (int64_t)x - R;
-      const int64_t hi = (int64_t)x + R > cmax ? cmax : (int64_t)x + R;
-      zmin = warp_key((uint32_t)lo, D, bp);
-      zmax = warp_key((uint32_t)hi, D, bp);
-    };
-    make_box();
-    int64_t i = warp_lower_bound(sk, N, zmin);
-    while (i < N) {
-      if (i >= w0 && i < w1) {
-        i = w1;
-        continue;
-      }
-      const int64_t lim = i < w0 ? w0 : N;
-      const int64_t end = i + 32 < lim ? i + 32 : lim;
-      if (sk[i] > zmax) break;  // keys are sorted: the rest lies beyond the box
-      if (score(i, end, zmax, true)) make_box();
-      const uint64_t kl = sk[end - 1];
-      int64_t next = end;
-      if (kl > zmax) break;
-      if (!key_in_box(kl, zmin, zmax, dmask, D)) {
-        uint64_t z2;
-        if (!bigmin(kl, zmin, zmax, dmask, D, nb, &z2) || z2 > zmax) break;
-        if (z2 > kl) next = end + warp_lower_bound(sk + end, N - end, z2);
-      }
-      i = next;
+  // squared distance from the query to the box [zmin, zmax] (warp-uniform)
+  auto box_dist = [&](uint64_t zmin, uint64_t zmax) -> uint64_t {
+    uint64_t dd = 0;
+    if (lane < D) {
+      const int64_t lo = (int64_t)extract_bits(zmin, dmask) << low;
+      const int64_t hi = ((int64_t)extract_bits(zmax, dmask) << low) | ((1ll << low) - 1);
+      const int64_t xq = (int64_t)x;
+      const int64_t t = xq < lo ? lo - xq : (xq > hi ? xq - hi : 0);
+      dd = (uint64_t)(t * t);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dd += __shfl_xor_sync(FULL, dd, o);
+    return dd;
+  };
+  int sp = 0;
+  if (lane == 0) stk[0] = KnnRegion{0ull, nb == 64 ? ~0ull : ((1ull << nb) - 1), 0, N};
+  sp = 1;
+  __syncwarp();
+  while (sp > 0) {
+    const KnnRegion r = stk[--sp];
+    __syncwarp();
+    if (r.b <= r.a) continue;
+    if (wd != ~0ull && box_dist(r.zmin, r.zmax) > wd) continue;  // culled
+    if (r.b - r.a <= kKnnLeaf || r.zmin == r.zmax || sp + 2 > kKnnStack) {
+      for (int64_t i = r.a; i < r.b; i += 32) score(i, i + 32 < r.b ? i + 32 : r.b);
+      continue;
+    }
+    // split where the corners' most significant bit differs
+    const int i = 63 - __clzll((long long)(r.zmin ^ r.zmax));
+    const int d = (nb - 1 - i) % D;
+    const uint64_t bit = 1ull << i;
+    const uint64_t below = __shfl_sync(FULL, dmask, d) & (bit - 1);
+    const uint64_t litmax = (r.zmax & ~bit) | below;
+    const uint64_t bigmin = (r.zmin & ~below) | bit;
+    const int64_t ml = r.a + warp_upper_bound(sk + r.a, r.b - r.a, litmax);
+    const int64_t mr = ml + warp_lower_bound(sk + ml, r.b - ml, bigmin);
+    const KnnRegion L{r.zmin, litmax, r.a, ml}, R{bigmin, r.zmax, mr, r.b};
+    const uint64_t dl = box_dist(L.zmin, L.zmax), dr = box_dist(R.zmin, R.zmax);
+    const bool left_first = dl <= dr;
+    if (lane == 0) {
+      // the far half below the near one on the stack
+      stk[sp] = left_first ? R : L;
+      stk[sp + 1] = left_first ? L : R;
+    }
+    sp += 2;
+    __syncwarp();
   }
 #pragma unroll
   for (int s = 0; s < KPL; ++s)
@@ -305,6 +305,8 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   uint32_t* ucand = cand + a.L;                            // L
   float* c32 = reinterpret_cast<float*>(ucand + a.L);      // L
   uint8_t* tm = reinterpret_cast<uint8_t*>(c32 + a.L);     // P
+  // k-NN region stacks, one per warp (k-NN mode only), 16-byte aligned after tm
+  KnnRegion* knn_stack = reinterpret_cast<KnnRegion*>(tm + ((g.P + 15) & ~15));
   __shared__ int s_sel[16];
   __shared__ int s_cov[16];
   __shared__ int s_nsel, s_ncand, s_bad;
@@ -395,8 +397,8 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
     const uint64_t* sk = a.skeys + (int64_t)c * a.N;
     int64_t pos = warp_lower_bound(sk, a.N, key);
     if (KNN) {
-      warp_knn(sk, a.sqc + (int64_t)c * a.N * a.D, a.sids + (int64_t)c * a.N, a.N, a.D, a.bp, qk, pos, (int)len,
-               cand + slot * len);
+      warp_knn(sk, a.sqc + (int64_t)c * a.N * a.D, a.sids + (int64_t)c * a.N, a.N, a.D, a.bp, qk, (int)len,
+               cand + slot * len, knn_stack + warp * kKnnStack);
     } else {
       int64_t start = pos - a.W / 2;
       if (start > maxs) start = maxs;
@@ -671,7 +673,8 @@ int query_batch(const Index& ix, const float* grid, const uint8_t* cur_mask, con
   a.cand_out = cand;
   a.ncand_out = ncand;
   a.status = status_word();
-  const size_t shm = (size_t)ix.g.n * 8 + (size_t)L * 12 + (((size_t)ix.g.P + 15) & ~(size_t)15);
+  const size_t shm = (size_t)ix.g.n * 8 + (size_t)L * 12 + (((size_t)ix.g.P + 15) & ~(size_t)15) +
+                     (ix.knn > 0 ? sizeof(KnnRegion) * kKnnStack * kQWarps : 0);
   bool weighted = false;
   for (float w : ix.weights_h) weighted |= (w != 1.0f);
   return weighted ? dispatch_q<true>(a, Q, shm, st) : dispatch_q<false>(a, Q, shm, st);

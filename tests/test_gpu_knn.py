@@ -113,3 +113,12 @@ def test_knn_ties_and_constant_grid(S):
     m[10:14, 10:14] = 0
     t = np.array([[12, 9], [3, 3], [36, 36]], np.int32)
     run_case(S, g, m, t, 3, 2, 2, 8, 7)  # all coordinates equal: the lists are the lowest ids
+
+
+def test_knn_deep_recursion_256(S):
+    """N ~ 55k: regions split many levels below the root before the leaf scans
+    (leaves hold at most 2,048 slots)."""
+    g, m = synth.voronoi2d(256, cfg=2, seed_sub=8)
+    t = np.concatenate([synth.front_targets(m, 9, cap=24, cfg=2), synth.random_targets(m, 9, 8, cfg=2)])
+    oix = run_case(S, g, m, t, 9, 8, 8, 16, 80)
+    assert oix["N"] > 40_000
