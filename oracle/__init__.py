@@ -58,6 +58,10 @@ def lib():
                 "or_morton": (C.c_uint64, [P, I32, I32]),
                 "or_key_bits": (I32, [I32, I32, P]),
                 "or_keys": (None, [P, I64, I32, I32, P, P]),
+                "or_keys_curve": (None, [P, I64, I32, I32, P, I32, P]),
+                "or_hilbert": (C.c_uint64, [P, I32, I32]),
+                "or_query_curve": (None, [P, P, I32, P, I32, I32, I32, I32, I32, I32, I32, P, P, I32, P, P, P, P,
+                                          P, I32, P, P, P, I64, I64, P, P, P, P, P, P]),
                 "or_zless": (I32, [P, P, I32]),
                 "or_sort": (None, [P, I64, P, P]),
                 "or_lower_bound": (I64, [P, I64, C.c_uint64]),
@@ -226,12 +230,18 @@ def key_bits(D, bits, shift=None) -> int:
     return int(lib().or_key_bits(D, bits, _p(sh)))
 
 
-def keys(q, bits, shift=None):
+def keys(q, bits, shift=None, curve=0):
+    """Curve keys of quantised points: curve 0 = Morton (Sec. II.C), 1 = Hilbert."""
     N, D = q.shape
     out = np.empty(N, np.uint64)
     sh = None if shift is None else _c(shift, np.int32)
-    lib().or_keys(_p(_c(q, np.uint32)), N, D, bits, _p(sh), _p(out))
+    lib().or_keys_curve(_p(_c(q, np.uint32)), N, D, bits, _p(sh), curve, _p(out))
     return out
+
+
+def hilbert(q, bp) -> int:
+    q = _c(q, np.uint32)
+    return int(lib().or_hilbert(_p(q), len(q), bp))
 
 
 def zless(a, b) -> bool:
@@ -264,7 +274,7 @@ def knn_bruteforce(qcoords, query, k):
 # ----------------------------------------------------------------------------
 # Index (Sec. II.A-C) and query (Fig. 1) built from the functions above
 # ----------------------------------------------------------------------------
-def build_index(grid, mask, K, C_, D, bits, frac=0.6, sample=1 << 20, shifts=None, basis=None, mean=None):
+def build_index(grid, mask, K, C_, D, bits, frac=0.6, sample=1 << 20, shifts=None, basis=None, mean=None, curve=0):
     """All arrays of the multi-index.  ``basis``/``mean`` ([C, s, D] / [C, s]) may
     be given to build from a common basis (e.g. one exported from the GPU);
     otherwise the oracle's own PCA is used."""
@@ -295,10 +305,11 @@ def build_index(grid, mask, K, C_, D, bits, frac=0.6, sample=1 << 20, shifts=Non
         Y[cv] = project(grid, K, dct, sub[cv], B[cv], MU[cv], D)
         LO[cv], SC[cv] = quant_params(Y[cv], bits)
         Q[cv] = quantise(Y[cv], bits, LO[cv], SC[cv])
-        KEYS[cv] = keys(Q[cv], bits, None if sh is None else sh[cv])
+        KEYS[cv] = keys(Q[cv], bits, None if sh is None else sh[cv], curve)
         SK[cv], SI[cv] = sort(KEYS[cv])
     return dict(ndim=ndim, ext=ext, ch=ch, K=K, C=C_, D=D, bits=bits, dict=dct, N=N, subset=sub, m=m, basis=B,
-                mean=MU, evals=EV, proj=Y, lo=LO, scale=SC, q=Q, keys=KEYS, skeys=SK, sids=SI, shifts=sh)
+                mean=MU, evals=EV, proj=Y, lo=LO, scale=SC, q=Q, keys=KEYS, skeys=SK, sids=SI, shifts=sh,
+                curve=curve)
 
 
 def query(ix, grid, cur_mask, target_lin, W, select=0, weights=None):
@@ -312,10 +323,11 @@ def query(ix, grid, cur_mask, target_lin, W, select=0, weights=None):
     pick = np.zeros(1, np.int64)
     cost = np.zeros(1, np.float64)
     w = None if weights is None else _c(weights, np.float32)
-    lib().or_query(_p(_c(grid, np.float32)), _p(_c(cur_mask, np.uint8)), ndim, _p(ext), ch, ix["K"], C_, D,
-                   ix["bits"], W, select, _p(w), _p(ix["subset"]), ix["m"], _p(ix["basis"]), _p(ix["mean"]),
-                   _p(ix["lo"]), _p(ix["scale"]), _p(ix["shifts"]), _p(ix["skeys"]), _p(ix["sids"]), _p(ix["dict"]),
-                   ix["N"], int(target_lin), _p(qk), _p(pos), _p(cand), _p(nc), _p(pick), _p(cost))
+    lib().or_query_curve(_p(_c(grid, np.float32)), _p(_c(cur_mask, np.uint8)), ndim, _p(ext), ch, ix["K"], C_, D,
+                         ix["bits"], W, select, _p(w), _p(ix["subset"]), ix["m"], _p(ix["basis"]), _p(ix["mean"]),
+                         _p(ix["lo"]), _p(ix["scale"]), _p(ix["shifts"]), int(ix.get("curve", 0)), _p(ix["skeys"]),
+                         _p(ix["sids"]), _p(ix["dict"]), ix["N"], int(target_lin), _p(qk), _p(pos), _p(cand),
+                         _p(nc), _p(pick), _p(cost))
     return dict(pick=int(pick[0]), cost=float(cost[0]), cand=cand[: int(nc[0])].copy(), qkeys=qk, pos=pos)
 
 

@@ -438,6 +438,44 @@ uint64_t or_morton(const uint32_t* q, int D, int bp) {
   return key;
 }
 
+// ----------------------------------------------------------------------------
+// Hilbert keys (the alternative curve of the 3-D configuration; not in the
+// paper, which uses the z-curve): Skilling's transpose method ("Programming the
+// Hilbert curve", AIP Conf. Proc. 707, 2004).  The D coordinates of bp bits are
+// turned in place into the "transposed" Hilbert index -- the index whose bits,
+// read plane by plane from the top with dimension 0 first, are the Hilbert
+// position -- by (1) walking the bit planes from the top: below the current
+// plane, either invert the low bits of coordinate 0 (the current bit of
+// coordinate i is set) or swap the low bits of coordinates 0 and i (it is
+// clear), which undoes the rotations and reflections of the sub-cubes; (2) a
+// Gray code across the dimensions (each coordinate xor the previous one); (3)
+// xor every coordinate with the mask collecting, per plane, whether the last
+// coordinate's bit there is set (as the low-bit mask of that plane).  The key is
+// then interleaved exactly like the Morton key (or_morton).
+// ----------------------------------------------------------------------------
+uint64_t or_hilbert(const uint32_t* q, int D, int bp) {
+  std::vector<uint32_t> x(q, q + D);
+  const uint32_t top = 1u << (bp - 1);
+  for (uint32_t plane = top; plane > 1; plane >>= 1) {
+    const uint32_t low = plane - 1;
+    for (int i = 0; i < D; ++i) {
+      if (x[i] & plane) {
+        x[0] ^= low;
+      } else {
+        const uint32_t diff = (x[0] ^ x[i]) & low;
+        x[0] ^= diff;
+        x[i] ^= diff;
+      }
+    }
+  }
+  for (int i = 1; i < D; ++i) x[i] ^= x[i - 1];
+  uint32_t flip = 0;
+  for (uint32_t plane = top; plane > 1; plane >>= 1)
+    if (x[D - 1] & plane) flip ^= plane - 1;
+  for (int i = 0; i < D; ++i) x[i] ^= flip;
+  return or_morton(x.data(), D, bp);
+}
+
 int or_key_bits(int D, int bits, const int32_t* shift) {
   int bp = bits;
   if (shift)
@@ -446,13 +484,22 @@ int or_key_bits(int D, int bits, const int32_t* shift) {
   return bp;
 }
 
-void or_keys(const uint32_t* q, int64_t N, int D, int bits, const int32_t* shift, uint64_t* keys) {
+// curve: 0 = Morton (z-curve, Sec. II.C), 1 = Hilbert (or_hilbert)
+uint64_t or_curve_key(const uint32_t* q, int D, int bp, int curve) {
+  return curve == 1 ? or_hilbert(q, D, bp) : or_morton(q, D, bp);
+}
+
+void or_keys_curve(const uint32_t* q, int64_t N, int D, int bits, const int32_t* shift, int curve, uint64_t* keys) {
   int bp = or_key_bits(D, bits, shift);
   std::vector<uint32_t> t(D);
   for (int64_t j = 0; j < N; ++j) {
     for (int k = 0; k < D; ++k) t[k] = q[(size_t)j * D + k] + (uint32_t)(shift ? shift[k] : 0);
-    keys[j] = or_morton(t.data(), D, bp);
+    keys[j] = or_curve_key(t.data(), D, bp, curve);
   }
+}
+
+void or_keys(const uint32_t* q, int64_t N, int D, int bits, const int32_t* shift, uint64_t* keys) {
+  or_keys_curve(q, N, D, bits, shift, 0, keys);
 }
 
 // The paper's comparator (Sec. II.C listing), with its two typos fixed (the
@@ -514,11 +561,29 @@ int64_t or_lower_bound(const uint64_t* skeys, int64_t N, uint64_t key) {
 // Outputs: qkeys[C], pos[C] (0 / -1 for unselected indices), cand (<= C*W ids),
 // *ncand, *pick (-1 if there is no candidate), *cost.
 // ----------------------------------------------------------------------------
+void or_query_curve(const float* grid, const uint8_t* cur_mask, int ndim, const int64_t* ext, int ch, int K, int C,
+                    int D, int bits, int W, int select, const float* w, const int32_t* subset, int m,
+                    const float* basis, const float* mean32, const float* lo, const float* scale,
+                    const int32_t* shift, int curve, const uint64_t* skeys, const uint32_t* sids, const int64_t* dict,
+                    int64_t N, int64_t target, uint64_t* qkeys, int64_t* pos, int64_t* cand, int64_t* ncand,
+                    int64_t* pick, double* cost);
+
 void or_query(const float* grid, const uint8_t* cur_mask, int ndim, const int64_t* ext, int ch, int K, int C,
               int D, int bits, int W, int select, const float* w, const int32_t* subset, int m, const float* basis,
               const float* mean32, const float* lo, const float* scale, const int32_t* shift, const uint64_t* skeys,
               const uint32_t* sids, const int64_t* dict, int64_t N, int64_t target, uint64_t* qkeys, int64_t* pos,
               int64_t* cand, int64_t* ncand, int64_t* pick, double* cost) {
+  or_query_curve(grid, cur_mask, ndim, ext, ch, K, C, D, bits, W, select, w, subset, m, basis, mean32, lo, scale,
+                 shift, 0, skeys, sids, dict, N, target, qkeys, pos, cand, ncand, pick, cost);
+}
+
+// The same query on indices keyed by `curve` (0 Morton, 1 Hilbert).
+void or_query_curve(const float* grid, const uint8_t* cur_mask, int ndim, const int64_t* ext, int ch, int K, int C,
+                    int D, int bits, int W, int select, const float* w, const int32_t* subset, int m,
+                    const float* basis, const float* mean32, const float* lo, const float* scale,
+                    const int32_t* shift, int curve, const uint64_t* skeys, const uint32_t* sids, const int64_t* dict,
+                    int64_t N, int64_t target, uint64_t* qkeys, int64_t* pos, int64_t* cand, int64_t* ncand,
+                    int64_t* pick, double* cost) {
   Geo g = make_geo(ndim, ext, ch, K);
   const int s = m * ch;
   std::vector<int> use;
@@ -549,7 +614,7 @@ void or_query(const float* grid, const uint8_t* cur_mask, int ndim, const int64_
     const int32_t* sh = shift ? shift + (size_t)cv * D : nullptr;
     for (int k = 0; k < D; ++k)
       qq[k] = or_quantise_one(y[k], lo[cv * D + k], scale[cv * D + k], bits) + (uint32_t)(sh ? sh[k] : 0);
-    uint64_t key = or_morton(qq.data(), D, or_key_bits(D, bits, sh));
+    uint64_t key = or_curve_key(qq.data(), D, or_key_bits(D, bits, sh), curve);
     qkeys[cv] = key;
     int64_t p = or_lower_bound(skeys + (size_t)cv * N, N, key);
     pos[cv] = p;

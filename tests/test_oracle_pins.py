@@ -453,6 +453,52 @@ def test_query_candidate_set_structure(small_rgb):
 
 
 # ----------------------------------------------------------------------------
+# Hilbert keys (Skilling's transpose method): pinned by the curve's defining
+# properties, not by a second implementation
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("D,b", [(2, 1), (2, 3), (3, 2), (4, 2), (2, 5), (5, 2), (3, 3)])
+def test_hilbert_is_a_unit_step_bijection(D, b):
+    side = 1 << b
+    cells = np.stack(np.meshgrid(*[np.arange(side)] * D, indexing="ij"), -1).reshape(-1, D).astype(np.uint32)
+    k = np.array([O.hilbert(c, b) for c in cells], dtype=np.uint64)
+    assert len(np.unique(k)) == len(cells) and int(k.max()) == len(cells) - 1
+    assert O.hilbert(np.zeros(D, np.uint32), b) == 0
+    order = cells[np.argsort(k)].astype(np.int64)
+    step = np.abs(np.diff(order, axis=0))
+    # consecutive positions on the curve are neighbouring cells: one coordinate moves by one
+    assert np.all(step.sum(1) == 1) and np.all(step.max(1) == 1)
+
+
+def test_hilbert_nesting_and_top64_truncation():
+    rng = np.random.default_rng(21)
+    for _ in range(200):
+        x = rng.integers(0, 1 << 17, 4).astype(np.uint32)
+        # the cell of x one level up is visited as one block: H_17(x) / 2^4 = H_16(x >> 1);
+        # D * b = 68 > 64, so the key of x is exactly that quotient
+        assert O.hilbert(x, 17) == O.hilbert(x >> 1, 16)
+        y = rng.integers(0, 1 << 8, 6).astype(np.uint32)
+        assert O.hilbert(y, 8) >> 6 == O.hilbert(y >> 1, 7)
+    # keys() with curve 1 applies the shifts and b + 1 bits like the Morton keys
+    q = rng.integers(0, 1 << 8, (50, 3)).astype(np.uint32)
+    sh = np.array([3, 0, 200], np.int32)
+    want = [O.hilbert(r + sh.astype(np.uint32), 9) for r in q]
+    assert np.array_equal(O.keys(q, 8, sh, curve=1), np.array(want, np.uint64))
+
+
+def test_hilbert_query_window_covering_dictionary_equals_fullscan():
+    g, m = synth.voronoi2d(64, cfg=2, seed_sub=9)
+    ix = O.build_index(g, m, 7, 4, 6, 10, sample=0, curve=1)
+    for cv in range(4):
+        assert np.all(np.diff(ix["skeys"][cv].astype(object)) >= 0)
+    t = synth.front_targets(m, 7, cap=10, cfg=2)
+    lin = O.centres_to_lin(t, ix["ext"])
+    fp, fc = O.fullscan(g, m, 7, ix["dict"], lin)
+    for i, tl in enumerate(lin):
+        r = O.query(ix, g, m, tl, W=ix["N"])
+        assert r["pick"] == fp[i] and r["cost"] == fc[i]
+
+
+# ----------------------------------------------------------------------------
 # SFC query with exact k-NN lists (Sec. II.D)
 # ----------------------------------------------------------------------------
 def _numpy_knn(qc, query, k):
