@@ -65,6 +65,11 @@ enum { SFC_SELECT_ALL = 0, SFC_SELECT_BEST = 1 };
 enum { SFC_FP32 = 0, SFC_BF16 = 1, SFC_FP16 = 2 };
 enum { SFC_PRIO_CONFIDENCE = 0, SFC_PRIO_CRIMINISI = 1 };
 enum { SFC_MODE_FULLSCAN = 0, SFC_MODE_SFC = 1 };
+/* Curve of the index keys: the z-curve of the paper (Sec. II.C), or the
+ * Hilbert curve (Skilling's transpose method, "Programming the Hilbert curve",
+ * 2004: the coordinates are transformed to the transposed Hilbert index, then
+ * interleaved like the Morton key and cut to the top 64 bits the same way). */
+enum { SFC_CURVE_MORTON = 0, SFC_CURVE_HILBERT = 1 };
 
 /* Grid geometry.  ext = {X, Y, Z}; ndim 2 (Z must be 1) or 3; ch >= 1. */
 typedef struct sfc_grid {
@@ -94,6 +99,7 @@ typedef struct sfc_params {
   int32_t knn;            /* k in 1..128: per selected index, the exact k nearest dictionary entries in the
                              quantised principal space (Sec. II.D) are the candidates instead of the window;
                              0: the window of W sorted slots */
+  int32_t curve;          /* SFC_CURVE_MORTON (default) or SFC_CURVE_HILBERT (window search only) */
 } sfc_params;
 
 typedef struct sfc_index sfc_index; /* opaque; owned by the library */

@@ -129,4 +129,33 @@ __device__ inline uint64_t morton_key(const uint32_t* q, int D, int bp) {
   return key;
 }
 
+// Hilbert key (Skilling 2004, transpose method): the coordinates q[0..D) of bp
+// bits are rewritten into the transposed Hilbert index -- from the top bit
+// plane down, coordinate 0's bits below the plane are inverted where
+// coordinate i has the plane's bit, else exchanged with coordinate i's (undoing
+// the sub-cube rotations and reflections); then a Gray code across the
+// coordinates and a final xor with the low-bit masks of the planes where the
+// last coordinate is set -- and interleaved as morton_key does.  q is modified.
+__device__ inline uint64_t hilbert_key(uint32_t* q, int D, int bp) {
+  const uint32_t top = 1u << (bp - 1);
+  for (uint32_t plane = top; plane > 1; plane >>= 1) {
+    const uint32_t low = plane - 1;
+    for (int i = 0; i < D; ++i) {
+      if (q[i] & plane) {
+        q[0] ^= low;
+      } else {
+        const uint32_t t = (q[0] ^ q[i]) & low;
+        q[0] ^= t;
+        q[i] ^= t;
+      }
+    }
+  }
+  for (int i = 1; i < D; ++i) q[i] ^= q[i - 1];
+  uint32_t mask = 0;
+  for (uint32_t plane = top; plane > 1; plane >>= 1)
+    if (q[D - 1] & plane) mask ^= plane - 1;
+  for (int i = 0; i < D; ++i) q[i] ^= mask;
+  return morton_key(q, D, bp);
+}
+
 }  // namespace sfc

@@ -71,6 +71,7 @@ struct Index {
   uint64_t* skeys = nullptr;  // C*N
   uint32_t* sids = nullptr;   // C*N
   int knn = 0;                // k of the exact k-NN lists (0: window search)
+  int curve = SFC_CURVE_MORTON;
   uint32_t* sqc = nullptr;    // C*N*D quantised shifted coordinates in curve order (knn > 0 only)
   // tracing (sfc_trace): phase events of the build and the eigen-solve iterations
   cudaEvent_t ev[SFC_TRACE_PHASES + 1] = {};

@@ -137,7 +137,7 @@ __global__ void k_scale(const uint32_t* __restrict__ lohi, int n, int bits, floa
 
 namespace {
 
-__global__ void k_keys(const float* __restrict__ proj, int64_t N, int D, int bits, int bp,
+__global__ void k_keys(const float* __restrict__ proj, int64_t N, int D, int bits, int bp, int curve,
                        const float* __restrict__ lo, const float* __restrict__ scale,
                        const int32_t* __restrict__ shifts, uint64_t* __restrict__ keys) {
   const int c = blockIdx.y;
@@ -147,7 +147,7 @@ __global__ void k_keys(const float* __restrict__ proj, int64_t N, int D, int bit
   const float* y = proj + ((int64_t)c * N + j) * D;
   for (int k = 0; k < D; ++k)
     q[k] = quantise_one(y[k], lo[c * D + k], scale[c * D + k], bits) + (uint32_t)shifts[c * D + k];
-  keys[(int64_t)c * N + j] = morton_key(q, D, bp);
+  keys[(int64_t)c * N + j] = curve == SFC_CURVE_HILBERT ? hilbert_key(q, D, bp) : morton_key(q, D, bp);
 }
 
 // sqc[c][i][k] = quantised shifted coordinate k of the entry at sorted slot i of index c
@@ -197,7 +197,7 @@ int project_and_key(Index& ix, const float* grid, cudaStream_t st, float* proj, 
   k_scale<<<(n + 127) / 128, 128, 0, st>>>(lohi, n, ix.bits, ix.lo, ix.scale);
   dim3 grd((unsigned)((ix.N + 255) / 256), ix.C);
   count_launch();
-  k_keys<<<grd, 256, 0, st>>>(proj, ix.N, ix.D, ix.bits, ix.bp, ix.lo, ix.scale, ix.shifts, keys);
+  k_keys<<<grd, 256, 0, st>>>(proj, ix.N, ix.D, ix.bits, ix.bp, ix.curve, ix.lo, ix.scale, ix.shifts, keys);
   SFC_TRY(cudaGetLastError());
   cudaFreeAsync(lohi, st);
   return SFC_OK;

@@ -33,7 +33,7 @@ struct QArgs {
   const uint8_t* mask;
   const int32_t* centres;
   Geo g;
-  int C, D, bits, bp, W, select, m, s, L, maxsel, knn, capw;
+  int C, D, bits, bp, W, select, m, s, L, maxsel, knn, capw, curve;
   int64_t N;
   const uint32_t* sqc;
   const uint32_t* dict;
@@ -393,7 +393,15 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
     uint32_t qk = 0;
     if (lane < a.D) qk = quantise_one(acc, a.lo[c * a.D + lane], a.scale[c * a.D + lane], a.bits) +
                          (uint32_t)a.shifts[c * a.D + lane];
-    const uint64_t key = warp_key(qk, a.D, a.bp);
+    uint64_t key;
+    if (a.curve == SFC_CURVE_HILBERT) {
+      uint32_t xq[16];
+#pragma unroll
+      for (int d = 0; d < 16; ++d) xq[d] = __shfl_sync(0xffffffffu, qk, d);
+      key = hilbert_key(xq, a.D, a.bp);  // every lane, identically
+    } else {
+      key = warp_key(qk, a.D, a.bp);
+    }
     const uint64_t* sk = a.skeys + (int64_t)c * a.N;
     int64_t pos = warp_lower_bound(sk, a.N, key);
     if (KNN) {
@@ -639,6 +647,7 @@ int query_batch(const Index& ix, const float* grid, const uint8_t* cur_mask, con
   a.N = ix.N;
   a.maxsel = ix.select == SFC_SELECT_BEST ? 1 : ix.C;
   a.knn = ix.knn;
+  a.curve = ix.curve;
   a.sqc = ix.sqc;
   a.capw = ix.knn > 0 ? ix.knn : ix.W;
   if (ix.knn > 0 && !ix.sqc) {

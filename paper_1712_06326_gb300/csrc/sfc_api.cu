@@ -329,10 +329,14 @@ int build_index(const float* grid, const uint8_t* dict_mask, const sfc_grid* gp,
   }
   if (p->dims < 1 || p->dims > 16 || p->bits < 1 || p->bits > 21 || p->window < 1 ||
       !(p->subset_frac > 0.0f && p->subset_frac <= 1.0f) || (p->select != SFC_SELECT_ALL && p->select != SFC_SELECT_BEST) ||
-      p->knn < 0 || p->knn > 128) {
+      p->knn < 0 || p->knn > 128 || (p->curve != SFC_CURVE_MORTON && p->curve != SFC_CURVE_HILBERT)) {
     set_error("parameter out of range (dims 1..16, bits 1..21, window >= 1, subset_frac in (0, 1], select, "
-              "knn 0..128)");
+              "knn 0..128, curve)");
     return SFC_EINVAL;
+  }
+  if (p->knn > 0 && p->curve != SFC_CURVE_MORTON) {
+    set_error("the k-NN search (knn > 0) runs on the z-curve (SFC_CURVE_MORTON) only");
+    return SFC_EUNSUPPORTED;
   }
   if (p->precision != SFC_FP32) {
     set_error("the index path computes in FP32 (precision must be SFC_FP32)");
@@ -343,6 +347,7 @@ int build_index(const float* grid, const uint8_t* dict_mask, const sfc_grid* gp,
   ix.bits = p->bits;
   ix.W = p->window;
   ix.knn = p->knn;
+  ix.curve = p->curve;
   ix.select = p->select;
   ix.frac = p->subset_frac;
   ix.pca_sample = p->pca_sample;

@@ -21,6 +21,7 @@ SFC_SELECT_ALL, SFC_SELECT_BEST = 0, 1
 SFC_FP32, SFC_BF16, SFC_FP16 = 0, 1, 2
 SFC_PRIO_CONFIDENCE, SFC_PRIO_CRIMINISI = 0, 1
 SFC_MODE_FULLSCAN, SFC_MODE_SFC = 0, 1
+SFC_CURVE_MORTON, SFC_CURVE_HILBERT = 0, 1
 
 EXPORTS = ["sfc_params_default", "sfc_index_build", "sfc_index_destroy", "sfc_index_info", "sfc_index_export",
            "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "fullscan_query_batch_static",
@@ -38,7 +39,7 @@ class sfc_params(C.Structure):
                 ("window", C.c_int32), ("subset_frac", C.c_float), ("shifts", C.c_void_p),
                 ("ch_weights", C.c_void_p), ("basis", C.c_void_p), ("mean", C.c_void_p), ("select", C.c_int32),
                 ("precision", C.c_int32), ("pca_sample", C.c_int64), ("priority", C.c_int32),
-                ("keep_intermediates", C.c_int32), ("knn", C.c_int32)]
+                ("keep_intermediates", C.c_int32), ("knn", C.c_int32), ("curve", C.c_int32)]
 
 
 _lib = None
