@@ -430,6 +430,26 @@ def main():
                "query_ms": statistics.mean(kq_ms), "query_only_qps": Q / (statistics.mean(kq_ms) / 1000.0),
                "pick_agreement_fullscan": kagree, "acceleration_error_mean": kae}
 
+    # ---- the same step on Hilbert-curve keys (window W) -----------------------
+    hil_prm = dict(prm, curve=sfc.SFC_CURVE_HILBERT)
+    hl_ms = []
+    for r in range(4):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ixh = sfc.sfc_index_build(gd, md, **hil_prm)
+        hp_, hc_ = sfc.sfc_query_batch(ixh, gd, md, td)
+        b.record(stream)
+        b.synchronize()
+        if r > 0:
+            hl_ms.append(a.elapsed_time(b))
+        ixh.close()
+    sfc_hilbert = {"qps": Q / (statistics.mean(hl_ms) / 1000.0), "ms_per_step": statistics.mean(hl_ms),
+                   "pick_agreement_fullscan": float((hp_[sel] == fp).double().mean().item()),
+                   "acceleration_error_mean": float((torch.sqrt(hc_[sel].double()) /
+                                                     torch.sqrt(fc.double()).clamp_min(1e-30) - 1.0).mean().item())}
+
     # ---- end to end through the C-ABI with host buffers ----------------------
     gh = torch.from_numpy(g).pin_memory()
     mh = torch.from_numpy(m).pin_memory()
@@ -484,7 +504,7 @@ def main():
             "roofline": roofline, "gpu_launches": int(launches), "e2e": e2e, "clocks": clk,
             "query_only": {"qps": query_only_qps, "ms": q_ms_mean},
             "index_build_ms": tot_ms / args.steps - q_ms_mean, "phases_ms": phases_ms,
-            "fullscan": fullscan, "sfc_knn": sfc_knn, "inpaint_128x128": inp}
+            "fullscan": fullscan, "sfc_knn": sfc_knn, "sfc_hilbert": sfc_hilbert, "inpaint_128x128": inp}
     if rank == 0:
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_obj()
