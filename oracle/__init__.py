@@ -46,8 +46,8 @@ def lib():
             L = C.CDLL(build())
             sig = {
                 "or_dict_extract": (I64, [P, I32, P, I32, P, I64]),
-                "or_cost64": (C.c_double, [P, P, I32, P, I32, I32, I64, I64, P]),
-                "or_fullscan": (None, [P, P, I32, P, I32, I32, P, I64, P, I64, P, P, P]),
+                "or_cost64": (C.c_double, [P, P, I32, P, I32, I32, I64, I64, P, I32]),
+                "or_fullscan": (None, [P, P, I32, P, I32, I32, P, I64, P, I64, P, P, P, I32]),
                 "or_subsets": (I32, [I32, I32, C.c_double, I32, P, P]),
                 "or_jacobi": (I32, [P, I32, P, P, I32]),
                 "or_pca": (I32, [P, I32, P, I32, I32, P, I64, P, I32, I64, I32, P, P, P, P]),
@@ -61,7 +61,7 @@ def lib():
                 "or_keys_curve": (None, [P, I64, I32, I32, P, I32, P]),
                 "or_hilbert": (C.c_uint64, [P, I32, I32]),
                 "or_query_curve": (None, [P, P, I32, P, I32, I32, I32, I32, I32, I32, I32, P, P, I32, P, P, P, P,
-                                          P, I32, P, P, P, I64, I64, P, P, P, P, P, P]),
+                                          P, I32, P, P, P, I64, I64, P, P, P, P, P, P, I32]),
                 "or_zless": (I32, [P, P, I32]),
                 "or_sort": (None, [P, I64, P, P]),
                 "or_lower_bound": (I64, [P, I64, C.c_uint64]),
@@ -69,9 +69,9 @@ def lib():
                                     P, P, P, I64, I64, P, P, P, P, P, P]),
                 "or_knn_bruteforce": (None, [P, I64, I32, P, I32, P, P]),
                 "or_query_knn": (None, [P, P, I32, P, I32, I32, I32, I32, I32, I32, I32, P, P, I32, P, P, P, P, P,
-                                        P, I64, I64, P, P, P, P]),
+                                        P, I64, I64, P, P, P, P, I32]),
                 "or_inpaint": (I64, [P, P, I32, P, I32, I32, I32, I32, P, P, I64, I32, I32, I32, I32, I32, P,
-                                     I32, P, P, P, P, P, P, P, I64, P]),
+                                     I32, P, P, P, P, P, P, P, I64, P, I32]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -131,14 +131,14 @@ def dict_extract(mask: np.ndarray, K: int) -> np.ndarray:
     return out
 
 
-def cost64(grid, cur_mask, K, target_lin, source_lin, weights=None) -> float:
+def cost64(grid, cur_mask, K, target_lin, source_lin, weights=None, norm=0) -> float:
     ndim, ext, ch = geometry(grid)
     w = None if weights is None else _c(weights, np.float32)
     return lib().or_cost64(_p(_c(grid, np.float32)), _p(_c(cur_mask, np.uint8)), ndim, _p(ext), ch, K,
-                           int(target_lin), int(source_lin), _p(w))
+                           int(target_lin), int(source_lin), _p(w), int(norm))
 
 
-def fullscan(grid, cur_mask, K, dict_lin, targets_lin, weights=None):
+def fullscan(grid, cur_mask, K, dict_lin, targets_lin, weights=None, norm=0):
     """Full scan + global argmin, ties to the lowest id (Sec. I).  -> (pick int64[Q], cost float64[Q])."""
     ndim, ext, ch = geometry(grid)
     g = _c(grid, np.float32)
@@ -148,7 +148,8 @@ def fullscan(grid, cur_mask, K, dict_lin, targets_lin, weights=None):
     w = None if weights is None else _c(weights, np.float32)
     pick = np.empty(len(t), np.int64)
     cost = np.empty(len(t), np.float64)
-    lib().or_fullscan(_p(g), _p(m), ndim, _p(ext), ch, K, _p(d), len(d), _p(t), len(t), _p(w), _p(pick), _p(cost))
+    lib().or_fullscan(_p(g), _p(m), ndim, _p(ext), ch, K, _p(d), len(d), _p(t), len(t), _p(w), _p(pick), _p(cost),
+                      norm)
     return pick, cost
 
 
@@ -312,7 +313,7 @@ def build_index(grid, mask, K, C_, D, bits, frac=0.6, sample=1 << 20, shifts=Non
                 curve=curve)
 
 
-def query(ix, grid, cur_mask, target_lin, W, select=0, weights=None):
+def query(ix, grid, cur_mask, target_lin, W, select=0, weights=None, norm=0):
     """One SFC query (Fig. 1(b)-(d)) -> dict(pick, cost, cand, qkeys, pos)."""
     ndim, ext, ch = geometry(grid)
     C_, D = ix["C"], ix["D"]
@@ -327,11 +328,11 @@ def query(ix, grid, cur_mask, target_lin, W, select=0, weights=None):
                          ix["bits"], W, select, _p(w), _p(ix["subset"]), ix["m"], _p(ix["basis"]), _p(ix["mean"]),
                          _p(ix["lo"]), _p(ix["scale"]), _p(ix["shifts"]), int(ix.get("curve", 0)), _p(ix["skeys"]),
                          _p(ix["sids"]), _p(ix["dict"]), ix["N"], int(target_lin), _p(qk), _p(pos), _p(cand),
-                         _p(nc), _p(pick), _p(cost))
+                         _p(nc), _p(pick), _p(cost), int(norm))
     return dict(pick=int(pick[0]), cost=float(cost[0]), cand=cand[: int(nc[0])].copy(), qkeys=qk, pos=pos)
 
 
-def query_knn(ix, grid, cur_mask, target_lin, k, select=0, weights=None):
+def query_knn(ix, grid, cur_mask, target_lin, k, select=0, weights=None, norm=0):
     """One SFC query with exact k-NN lists (Sec. II.D) -> dict(pick, cost, cand).
     ``ix`` needs "q": [C, N, D] unshifted quantised coordinates."""
     ndim, ext, ch = geometry(grid)
@@ -345,11 +346,11 @@ def query_knn(ix, grid, cur_mask, target_lin, k, select=0, weights=None):
                        ix["bits"], k, select, _p(w), _p(_c(ix["subset"], np.int32)), ix["m"],
                        _p(_c(ix["basis"], np.float32)), _p(_c(ix["mean"], np.float32)), _p(_c(ix["lo"], np.float32)),
                        _p(_c(ix["scale"], np.float32)), _p(_c(ix["q"], np.uint32)), _p(_c(ix["dict"], np.int64)),
-                       ix["N"], int(target_lin), _p(cand), _p(nc), _p(pick), _p(cost))
+                       ix["N"], int(target_lin), _p(cand), _p(nc), _p(pick), _p(cost), int(norm))
     return dict(pick=int(pick[0]), cost=float(cost[0]), cand=cand[: int(nc[0])].copy())
 
 
-def inpaint(grid, mask, K, mode=0, prio=0, ix=None, W=64, select=0, weights=None, max_steps=0):
+def inpaint(grid, mask, K, mode=0, prio=0, ix=None, W=64, select=0, weights=None, max_steps=0, norm=0):
     """Fill loop (Sec. I, Fig. 1(a)); works on copies.  mode 0 = full scan,
     1 = SFC (needs ``ix``).  -> (grid, mask, log int64 [steps, ndim+1], steps)."""
     ndim, ext, ch = geometry(grid)
@@ -366,7 +367,7 @@ def inpaint(grid, mask, K, mode=0, prio=0, ix=None, W=64, select=0, weights=None
         args = [ix["C"], ix["D"], ix["bits"], W, select, _p(ix["subset"]), ix["m"], _p(ix["basis"]),
                 _p(ix["mean"]), _p(ix["lo"]), _p(ix["scale"]), _p(ix["shifts"]), _p(ix["skeys"]), _p(ix["sids"])]
     steps = lib().or_inpaint(_p(g), _p(m), ndim, _p(ext), ch, K, mode, prio, _p(w), _p(_c(dct, np.int64)), len(dct),
-                             *args, int(max_steps), _p(log))
+                             *args, int(max_steps), _p(log), int(norm))
     if steps < 0:
         raise ValueError(f"oracle inpaint failed ({steps})")
     return g, m, log[:steps].copy(), int(steps)

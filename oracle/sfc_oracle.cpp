@@ -94,8 +94,10 @@ inline bool centre_valid(const Geo& g, int64_t x, int64_t y, int64_t z) {
 // Masked L2 cost in FP64 (Sec. II after Fig. 1: differences at unknown pixels are
 // taken as zero).  Reading: the squared form (same argmin as the norm); elements
 // summed one by one in patch raster order, channel innermost; operands widened
-// from FP32; term = w_ch * (d * d); no fused multiply-add.
-double cost64(const Geo& g, const float* grid, const uint8_t* cur_mask, int64_t t, int64_t s, const float* w) {
+// from FP32; term = w_ch * (d * d); no fused multiply-add.  norm == 1: the L1
+// norm of Sec. III.K instead, term = w_ch * |d|, same order.
+double cost64(const Geo& g, const float* grid, const uint8_t* cur_mask, int64_t t, int64_t s, const float* w,
+              int norm) {
   double acc = 0.0;
   for (int pp = 0; pp < g.P; ++pp) {
     int64_t qt = patch_pixel(g, t, pp);
@@ -103,9 +105,9 @@ double cost64(const Geo& g, const float* grid, const uint8_t* cur_mask, int64_t 
     int64_t qs = patch_pixel(g, s, pp);
     for (int c = 0; c < g.ch; ++c) {
       double d = (double)grid[qt * g.ch + c] - (double)grid[qs * g.ch + c];
-      double sq = d * d;
+      double term = norm == 1 ? std::fabs(d) : d * d;
       double wc = w ? (double)w[c] : 1.0;
-      acc = acc + wc * sq;
+      acc = acc + wc * term;
     }
   }
   return acc;
@@ -144,11 +146,11 @@ int64_t or_dict_extract(const uint8_t* mask, int ndim, const int64_t* ext, int K
   return n;
 }
 
-// Exact cost of one (target, source) pair, exposed for tests.
+// Exact cost of one (target, source) pair, exposed for tests (norm: 0 = L2, 1 = L1).
 double or_cost64(const float* grid, const uint8_t* cur_mask, int ndim, const int64_t* ext, int ch, int K,
-                 int64_t target, int64_t source, const float* w) {
+                 int64_t target, int64_t source, const float* w, int norm) {
   Geo g = make_geo(ndim, ext, ch, K);
-  return cost64(g, grid, cur_mask, target, source, w);
+  return cost64(g, grid, cur_mask, target, source, w, norm);
 }
 
 // ----------------------------------------------------------------------------
@@ -157,13 +159,13 @@ double or_cost64(const float* grid, const uint8_t* cur_mask, int ndim, const int
 // ----------------------------------------------------------------------------
 void or_fullscan(const float* grid, const uint8_t* cur_mask, int ndim, const int64_t* ext, int ch, int K,
                  const int64_t* dict, int64_t N, const int64_t* targets, int64_t Q, const float* w, int64_t* pick,
-                 double* cost) {
+                 double* cost, int norm) {
   Geo g = make_geo(ndim, ext, ch, K);
   for (int64_t q = 0; q < Q; ++q) {
     double best = INFINITY;
     int64_t bj = -1;
     for (int64_t j = 0; j < N; ++j) {
-      double c = cost64(g, grid, cur_mask, targets[q], dict[j], w);
+      double c = cost64(g, grid, cur_mask, targets[q], dict[j], w, norm);
       if (c < best) {
         best = c;
         bj = j;
@@ -566,7 +568,7 @@ void or_query_curve(const float* grid, const uint8_t* cur_mask, int ndim, const 
                     const float* basis, const float* mean32, const float* lo, const float* scale,
                     const int32_t* shift, int curve, const uint64_t* skeys, const uint32_t* sids, const int64_t* dict,
                     int64_t N, int64_t target, uint64_t* qkeys, int64_t* pos, int64_t* cand, int64_t* ncand,
-                    int64_t* pick, double* cost);
+                    int64_t* pick, double* cost, int norm);
 
 void or_query(const float* grid, const uint8_t* cur_mask, int ndim, const int64_t* ext, int ch, int K, int C,
               int D, int bits, int W, int select, const float* w, const int32_t* subset, int m, const float* basis,
@@ -574,16 +576,17 @@ void or_query(const float* grid, const uint8_t* cur_mask, int ndim, const int64_
               const uint32_t* sids, const int64_t* dict, int64_t N, int64_t target, uint64_t* qkeys, int64_t* pos,
               int64_t* cand, int64_t* ncand, int64_t* pick, double* cost) {
   or_query_curve(grid, cur_mask, ndim, ext, ch, K, C, D, bits, W, select, w, subset, m, basis, mean32, lo, scale,
-                 shift, 0, skeys, sids, dict, N, target, qkeys, pos, cand, ncand, pick, cost);
+                 shift, 0, skeys, sids, dict, N, target, qkeys, pos, cand, ncand, pick, cost, 0);
 }
 
-// The same query on indices keyed by `curve` (0 Morton, 1 Hilbert).
+// The same query on indices keyed by `curve` (0 Morton, 1 Hilbert), with the
+// cost norm `norm` (0 L2, 1 L1).
 void or_query_curve(const float* grid, const uint8_t* cur_mask, int ndim, const int64_t* ext, int ch, int K, int C,
                     int D, int bits, int W, int select, const float* w, const int32_t* subset, int m,
                     const float* basis, const float* mean32, const float* lo, const float* scale,
                     const int32_t* shift, int curve, const uint64_t* skeys, const uint32_t* sids, const int64_t* dict,
                     int64_t N, int64_t target, uint64_t* qkeys, int64_t* pos, int64_t* cand, int64_t* ncand,
-                    int64_t* pick, double* cost) {
+                    int64_t* pick, double* cost, int norm) {
   Geo g = make_geo(ndim, ext, ch, K);
   const int s = m * ch;
   std::vector<int> use;
@@ -631,7 +634,7 @@ void or_query_curve(const float* grid, const uint8_t* cur_mask, int ndim, const 
   double best = INFINITY;
   int64_t bj = -1;
   for (int64_t j : ids) {
-    double c = cost64(g, grid, cur_mask, target, dict[j], w);
+    double c = cost64(g, grid, cur_mask, target, dict[j], w, norm);
     if (c < best) {
       best = c;
       bj = j;
@@ -681,7 +684,7 @@ void or_query_knn(const float* grid, const uint8_t* cur_mask, int ndim, const in
                   int D, int bits, int k, int select, const float* w, const int32_t* subset, int m,
                   const float* basis, const float* mean32, const float* lo, const float* scale, const uint32_t* qc,
                   const int64_t* dict, int64_t N, int64_t target, int64_t* cand, int64_t* ncand, int64_t* pick,
-                  double* cost) {
+                  double* cost, int norm) {
   Geo g = make_geo(ndim, ext, ch, K);
   const int s = m * ch;
   std::vector<int> use;
@@ -717,7 +720,7 @@ void or_query_knn(const float* grid, const uint8_t* cur_mask, int ndim, const in
   double best = INFINITY;
   int64_t bj = -1;
   for (int64_t j : ids) {
-    double c = cost64(g, grid, cur_mask, target, dict[j], w);
+    double c = cost64(g, grid, cur_mask, target, dict[j], w, norm);
     if (c < best) {
       best = c;
       bj = j;
@@ -748,6 +751,7 @@ void or_query_knn(const float* grid, const uint8_t* cur_mask, int ndim, const in
 //  * stop when no pixel is unknown, or after max_steps (> 0).
 // log (may be NULL) receives per step ndim centre coordinates then the pick id.
 // confidence (optional in/out, npix floats): NULL = start from the mask.
+// norm: the cost of the search (0 L2, 1 L1, as cost64).
 // Returns the number of steps; -1 when the dictionary is empty and pixels are
 // unknown; -2 for an unsupported priority.
 // ----------------------------------------------------------------------------
@@ -755,7 +759,7 @@ int64_t or_inpaint(float* grid, uint8_t* mask, int ndim, const int64_t* ext, int
                    const float* w, const int64_t* dict, int64_t N, int C, int D, int bits, int W, int select,
                    const int32_t* subset, int m, const float* basis, const float* mean32, const float* lo,
                    const float* scale, const int32_t* shift, const uint64_t* skeys, const uint32_t* sids,
-                   int64_t max_steps, int64_t* log) {
+                   int64_t max_steps, int64_t* log, int norm) {
   Geo g = make_geo(ndim, ext, ch, K);
   const int64_t npix = g.X * g.Y * g.Z;
   if (prio == 1 && ndim != 2) return -2;
@@ -859,11 +863,12 @@ int64_t or_inpaint(float* grid, uint8_t* mask, int ndim, const int64_t* ext, int
     int64_t j;
     double cst;
     if (mode == 0) {
-      or_fullscan(grid, mask, ndim, ext, ch, K, dict, N, &bestc, 1, w, &j, &cst);
+      or_fullscan(grid, mask, ndim, ext, ch, K, dict, N, &bestc, 1, w, &j, &cst, norm);
     } else {
       int64_t nc;
-      or_query(grid, mask, ndim, ext, ch, K, C, D, bits, W, select, w, subset, m, basis, mean32, lo, scale, shift,
-               skeys, sids, dict, N, bestc, qkeys.data(), pos.data(), cand.data(), &nc, &j, &cst);
+      or_query_curve(grid, mask, ndim, ext, ch, K, C, D, bits, W, select, w, subset, m, basis, mean32, lo, scale,
+                     shift, 0, skeys, sids, dict, N, bestc, qkeys.data(), pos.data(), cand.data(), &nc, &j, &cst,
+                     norm);
     }
     int64_t src = dict[j];
     for (int pp = 0; pp < g.P; ++pp) {

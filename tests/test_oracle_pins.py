@@ -99,6 +99,78 @@ def test_cost_brute_force_tiny_enumeration():
         assert np.all(S[i][:, None] <= S[i][None, :] + S + 1e-12)
 
 
+# ----------------------------------------------------------------------------
+# L1 cost (Sec. III.K)
+# ----------------------------------------------------------------------------
+def test_l1_cost_closed_form_constant_offset():
+    # target - source = +-delta (dyadic) at every known element: L1 = n_known w delta
+    rng = np.random.default_rng(30)
+    K = 5
+    g = np.zeros((20, 20, 3), np.float32)
+    base = (rng.integers(0, 64, (K, K, 3)) / 64.0).astype(np.float32)
+    sign = np.where(rng.random((K, K, 3)) < 0.5, -1.0, 1.0).astype(np.float32)
+    g[2:7, 2:7] = base
+    g[10:15, 11:16] = base + np.float32(0.25) * sign
+    m = np.ones((20, 20), np.uint8)
+    t, s_ = 12 * 20 + 13, 4 * 20 + 4
+    assert O.cost64(g, m, K, t, s_, norm=1) == K * K * 3 * 0.25
+    m[10, 11] = 0
+    m[14, 15] = 0
+    w = np.array([1.0, 2.0, 4.0], np.float32)
+    assert O.cost64(g, m, K, t, s_, w, norm=1) == (K * K - 2) * 0.25 * 7
+    assert O.cost64(g, m, K, t, s_, w) == (K * K - 2) * 0.0625 * 7  # L2 unchanged
+
+
+def test_l1_fullscan_against_numpy_brute_force():
+    rng = np.random.default_rng(31)
+    g = rng.random((14, 15, 2)).astype(np.float32)
+    m = np.ones((14, 15), np.uint8)
+    m[5:8, 6:9] = 0
+    K, r = 3, 1
+    d = O.dict_extract(m, K)
+    w = np.array([0.5, 3.0], np.float32)
+    t = np.array([[6, 4], [9, 7], [2, 2], [13, 12]], np.int64)
+    lin = O.centres_to_lin(t, O.geometry(g)[1])
+    p, c = O.fullscan(g, m, K, d, lin, w, norm=1)
+    X = g.shape[1]
+    for i, tl in enumerate(lin):
+        ty, tx = divmod(int(tl), X)
+        T = g[ty - r:ty + r + 1, tx - r:tx + r + 1].astype(np.float64)
+        km = m[ty - r:ty + r + 1, tx - r:tx + r + 1].astype(np.float64)[..., None]
+        costs = []
+        for j in d:
+            sy, sx = divmod(int(j), X)
+            P = g[sy - r:sy + r + 1, sx - r:sx + r + 1].astype(np.float64)
+            costs.append(float((np.abs(T - P) * km * w.astype(np.float64)).sum()))
+        costs = np.array(costs)
+        assert p[i] == int(np.argmin(costs))  # first minimum = lowest id
+        assert abs(c[i] - costs.min()) <= 1e-12 * max(1.0, costs.min())
+
+
+def test_l1_is_a_metric_on_known_patches():
+    rng = np.random.default_rng(32)
+    g = _grid(rng, 10, 10)
+    m = np.ones((10, 10), np.uint8)
+    d = O.dict_extract(m, 3)
+    C = np.array([[O.cost64(g, m, 3, a, b, norm=1) for b in d] for a in d])
+    assert np.all(np.diag(C) == 0) and np.array_equal(C, C.T) and np.all(C >= 0)
+    for i in range(0, len(d), 7):
+        assert np.all(C[i][:, None] <= C[i][None, :] + C + 1e-12)
+
+
+def test_l1_fill_one_pixel_hole_uses_bruteforce_pick():
+    rng = np.random.default_rng(33)
+    g = _grid(rng, 20, 20)
+    m = np.ones((20, 20), np.uint8)
+    m[9, 11] = 0
+    d = O.dict_extract(m, 3)
+    out, mo, log, steps = O.inpaint(g, m, 3, mode=0, norm=1)
+    assert steps == 1 and mo.all()
+    cx, cy, j = log[0]
+    p, c = O.fullscan(g, m, 3, d, np.array([cy * 20 + cx]), norm=1)
+    assert j == p[0]
+
+
 def test_fullscan_exact_duplicate_tie_to_lowest_id():
     rng = np.random.default_rng(3)
     g = _grid(rng, 24, 24)
