@@ -70,6 +70,11 @@ enum { SFC_MODE_FULLSCAN = 0, SFC_MODE_SFC = 1 };
  * 2004: the coordinates are transformed to the transposed Hilbert index, then
  * interleaved like the Morton key and cut to the top 64 bits the same way). */
 enum { SFC_CURVE_MORTON = 0, SFC_CURVE_HILBERT = 1 };
+/* Cost of a (target, source) pair over the target's known elements: the
+ * squared L2 norm sum w (t - p)^2 (Sec. II) or the L1 norm sum w |t - p|
+ * (Sec. III.K).  The exact pick is the argmin of the FP64 sum (terms in patch
+ * raster order, channel innermost); FP32 costs are within (n + 8) 2^-24 of it. */
+enum { SFC_COST_L2 = 0, SFC_COST_L1 = 1 };
 
 /* Grid geometry.  ext = {X, Y, Z}; ndim 2 (Z must be 1) or 3; ch >= 1. */
 typedef struct sfc_grid {
@@ -100,6 +105,8 @@ typedef struct sfc_params {
                              quantised principal space (Sec. II.D) are the candidates instead of the window;
                              0: the window of W sorted slots */
   int32_t curve;          /* SFC_CURVE_MORTON (default) or SFC_CURVE_HILBERT (window search only) */
+  int32_t cost;           /* SFC_COST_L2 (default) or SFC_COST_L1; full scan, queries and fill loop
+                             (SFC_FP16 takes L2 only) */
 } sfc_params;
 
 typedef struct sfc_index sfc_index; /* opaque; owned by the library */

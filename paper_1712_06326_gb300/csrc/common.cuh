@@ -79,14 +79,15 @@ __device__ inline void warp_argmin64(double& c, int64_t& id) {
 // `tv`/`tm` hold the target's values and per-pixel known flags; `eoff` the
 // element offsets (pixel offset * ch + channel) relative to centre * ch.
 __device__ inline double exact_cost64(const float* __restrict__ grid, int64_t src_base, const float* tv,
-                                      const uint8_t* tm, const int* eoff, int P, int ch, const float* w) {
+                                      const uint8_t* tm, const int* eoff, int P, int ch, const float* w,
+                                      bool l1 = false) {
   double acc = 0.0;
   for (int pp = 0; pp < P; ++pp) {
     if (!tm[pp]) continue;
     for (int c = 0; c < ch; ++c) {
       int e = pp * ch + c;
       double d = __dsub_rn((double)tv[e], (double)grid[src_base + eoff[e]]);
-      double sq = __dmul_rn(d, d);
+      double sq = l1 ? fabs(d) : __dmul_rn(d, d);  // L1 (Sec. III.K): |d|
       double term = __dmul_rn((double)w[c], sq);
       acc = __dadd_rn(acc, term);
     }
@@ -95,8 +96,8 @@ __device__ inline double exact_cost64(const float* __restrict__ grid, int64_t sr
 }
 
 // Upper end of the FP32 band around the FP32 minimum: |c32 - c| <= gamma * c
-// for a sum of n non-negative terms, each d^2 (d rounded once) times a rounded
-// weight, summed by FMA, with gamma = (n + 8) * 2^-24.  A candidate can be the
+// for a sum of n non-negative terms, each d^2 or |d| (d rounded once) times a
+// rounded weight, summed by FMA or addition, with gamma = (n + 8) * 2^-24.  A candidate can be the
 // exact argmin only if c32 <= min32 * (1 + 3 gamma) + n * 2^-126 (absolute
 // slack for underflow).  Every operation rounds up, so the float returned is >=
 // that bound and the band it defines contains the exact one.

@@ -72,6 +72,7 @@ struct Index {
   uint32_t* sids = nullptr;   // C*N
   int knn = 0;                // k of the exact k-NN lists (0: window search)
   int curve = SFC_CURVE_MORTON;
+  bool l1 = false;            // rescore with the L1 norm (Sec. III.K)
   uint32_t* sqc = nullptr;    // C*N*D quantised shifted coordinates in curve order (knn > 0 only)
   // tracing (sfc_trace): phase events of the build and the eigen-solve iterations
   cudaEvent_t ev[SFC_TRACE_PHASES + 1] = {};
@@ -114,8 +115,9 @@ int query_batch(const Index& ix, const float* grid, const uint8_t* cur_mask, con
                 cudaStream_t st);
 
 // k_fullscan.cu
+// cm (cost mode): bit 0 = channel weights other than 1, bit 1 = L1 norm (Sec. III.K).
 int fullscan_batch(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
-                   const int* eoff_all, const float* weights, bool weighted, const int32_t* centres,
+                   const int* eoff_all, const float* weights, int cm, const int32_t* centres,
                    const int64_t* centre_lin, int64_t Q, int64_t* pick, float* cost, cudaStream_t st);
 
 int fullscan_batch_tc(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
@@ -126,7 +128,7 @@ int tc_prescores_all(const Geo& g, const float* grid, const uint8_t* cur_mask, c
                      double* bound, cudaStream_t st);
 
 int fullscan_batch_into(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
-                        const int* eoff_all, const float* weights, bool weighted, const int32_t* centres, int64_t Q,
+                        const int* eoff_all, const float* weights, int cm, const int32_t* centres, int64_t Q,
                         int64_t* pick, float* cost, int64_t* lin, uint8_t* bad, unsigned int* gmin, float* tilemin,
                         cudaStream_t st);
 

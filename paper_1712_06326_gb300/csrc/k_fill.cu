@@ -24,7 +24,7 @@
 namespace sfc {
 
 int fullscan_single(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
-                    const int* eoff_all, const float* weights, bool weighted, const int64_t* centre_lin,
+                    const int* eoff_all, const float* weights, int cm, const int64_t* centre_lin,
                     int64_t* pick, float* cost, float* tilemin, unsigned int* gmin, cudaStream_t st);
 
 namespace {
@@ -258,7 +258,7 @@ __global__ void k_state_init(FillState s, Geo g) {
 // Runs the loop; `ix` is null in full-scan mode.  dict/N: the dictionary of the
 // initial mask.  Synchronises `st` every chunk of steps to test for completion.
 int fill_loop(const Geo& g, float* grid, uint8_t* mask, int prio, int mode, const Index* ix, const uint32_t* dict,
-              int64_t N, const int* eoff_all, const float* weights, bool weighted, int64_t max_steps, int64_t* log,
+              int64_t N, const int* eoff_all, const float* weights, int cm, int64_t max_steps, int64_t* log,
               int64_t* steps_done, cudaStream_t st) {
   const int64_t npix = g.X * g.Y * g.Z;
   FillState s;
@@ -323,7 +323,7 @@ int fill_loop(const Geo& g, float* grid, uint8_t* mask, int prio, int mode, cons
       if (mode == SFC_MODE_SFC)
         rc = query_batch(*ix, grid, mask, s.sel_xyz, 1, s.pick, s.cost, nullptr, nullptr, nullptr, nullptr, st);
       else
-        rc = fullscan_single(g, grid, mask, dict, N, eoff_all, weights, weighted, s.sel_lin, s.pick, s.cost, tilemin,
+        rc = fullscan_single(g, grid, mask, dict, N, eoff_all, weights, cm, s.sel_lin, s.pick, s.cost, tilemin,
                              gmin, st);
       if (rc != SFC_OK) break;
       count_launch();

@@ -24,7 +24,17 @@ namespace {
 constexpr int kFsThreads = 256;
 constexpr int kBandCap = 64;  // in-band entries listed per query before the fallback
 
-template <int QT, int EPT, bool WEIGHTED>
+// CM (cost mode): bit 0 = channel weights, bit 1 = L1 norm (Sec. III.K) instead of
+// the squared L2 norm.  One accumulation step of the FP32 cost for the
+// difference d: w d^2 or d^2 by FMA (L2), w |d| by FMA or + |d| (L1).
+template <int CM>
+__device__ __forceinline__ float cost_step(float acc, float d, float w) {
+  if (CM & 2) return (CM & 1) ? __fmaf_rn(w, fabsf(d), acc) : __fadd_rn(acc, fabsf(d));
+  return (CM & 1) ? __fmaf_rn(__fmul_rn(w, d), d, acc) : __fmaf_rn(d, d, acc);
+}
+
+// CM (cost mode): bit 0 = channel weights, bit 1 = L1 norm.
+template <int QT, int EPT, int CM>
 __global__ void __launch_bounds__(kFsThreads) k_fs_scan(const float* __restrict__ grid,
                                                         const uint8_t* __restrict__ mask, Geo g,
                                                         const uint32_t* __restrict__ dict, int64_t N,
@@ -42,7 +52,7 @@ __global__ void __launch_bounds__(kFsThreads) k_fs_scan(const float* __restrict_
   for (int e = threadIdx.x; e < n; e += kFsThreads) {
     int o = eoff_all[e];
     eo[e] = o;
-    if (WEIGHTED) we[e] = weights[e % ch];
+    if (CM & 1) we[e] = weights[e % ch];
     const int pixo = eoff_all[e - e % ch] / ch;
 #pragma unroll
     for (int qi = 0; qi < QT; ++qi) {
@@ -74,17 +84,14 @@ __global__ void __launch_bounds__(kFsThreads) k_fs_scan(const float* __restrict_
     float p[EPT];
 #pragma unroll
     for (int k = 0; k < EPT; ++k) p[k] = sb[k] >= 0 ? __ldg(grid + sb[k] + o) : 0.0f;
-    float w = WEIGHTED ? we[e] : 1.0f;
+    float w = (CM & 1) ? we[e] : 1.0f;
 #pragma unroll
     for (int qi = 0; qi < QT; ++qi) {
       const float2 v = am[(size_t)e * QT + qi];
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
         float d = __fmaf_rn(-v.x, p[k], v.y);
-        if (WEIGHTED)
-          acc[k][qi] = __fmaf_rn(__fmul_rn(w, d), d, acc[k][qi]);
-        else
-          acc[k][qi] = __fmaf_rn(d, d, acc[k][qi]);
+        acc[k][qi] = cost_step<CM>(acc[k][qi], d, w);
       }
     }
   }
@@ -113,22 +120,19 @@ __global__ void __launch_bounds__(kFsThreads) k_fs_scan(const float* __restrict_
 }
 
 // Same FP32 arithmetic for one query and one entry (bit-identical to pass 1).
-template <bool WEIGHTED>
+template <int CM>
 __device__ inline float cost32_one(const float* __restrict__ grid, int64_t sb, const float2* am, const int* eo,
                                    const float* we, int n) {
   float acc = 0.0f;
   for (int e = 0; e < n; ++e) {
     float p = __ldg(grid + sb + eo[e]);
     float d = __fmaf_rn(-am[e].x, p, am[e].y);
-    if (WEIGHTED)
-      acc = __fmaf_rn(__fmul_rn(we[e], d), d, acc);
-    else
-      acc = __fmaf_rn(d, d, acc);
+    acc = cost_step<CM>(acc, d, (CM & 1) ? we[e] : 1.0f);
   }
   return acc;
 }
 
-template <int EPT, bool WEIGHTED>
+template <int EPT, int CM>
 __global__ void __launch_bounds__(kFsThreads) k_fs_band(const float* __restrict__ grid,
                                                         const uint8_t* __restrict__ mask, Geo g,
                                                         const uint32_t* __restrict__ dict, int64_t N,
@@ -171,7 +175,7 @@ __global__ void __launch_bounds__(kFsThreads) k_fs_band(const float* __restrict_
     for (int k = 0; k < EPT; ++k) {
       const int64_t j = t * kFsThreads * EPT + (int64_t)k * kFsThreads + threadIdx.x;
       if (j >= N) continue;
-      const float c32 = cost32_one<WEIGHTED>(grid, (int64_t)dict[j] * ch, am, eo, we, n);
+      const float c32 = cost32_one<CM>(grid, (int64_t)dict[j] * ch, am, eo, we, n);
       if (c32 <= T) {
         const int slot = atomicAdd(&s_cnt, 1);
         if (slot < kBandCap) {
@@ -198,7 +202,7 @@ __global__ void __launch_bounds__(kFsThreads) k_fs_band(const float* __restrict_
   if (cnt <= kBandCap) {
     for (int i = threadIdx.x; i < cnt; i += kFsThreads) {
       const int64_t j = s_j[i];
-      const double c64 = exact_cost64(grid, (int64_t)dict[j] * ch, tv, tm, eo, P, ch, weights);
+      const double c64 = exact_cost64(grid, (int64_t)dict[j] * ch, tv, tm, eo, P, ch, weights, (CM & 2) != 0);
       if (c64 < bc || (c64 == bc && j < bj)) {
         bc = c64;
         bj = j;
@@ -212,9 +216,9 @@ __global__ void __launch_bounds__(kFsThreads) k_fs_band(const float* __restrict_
         const int64_t j = t * kFsThreads * EPT + (int64_t)k * kFsThreads + threadIdx.x;
         if (j >= N) continue;
         const int64_t sb = (int64_t)dict[j] * ch;
-        const float c32 = cost32_one<WEIGHTED>(grid, sb, am, eo, we, n);
+        const float c32 = cost32_one<CM>(grid, sb, am, eo, we, n);
         if (c32 <= T) {
-          const double c64 = exact_cost64(grid, sb, tv, tm, eo, P, ch, weights);
+          const double c64 = exact_cost64(grid, sb, tv, tm, eo, P, ch, weights, (CM & 2) != 0);
           if (c64 < bc || (c64 == bc && j < bj)) {
             bc = c64;
             bj = j;
@@ -350,7 +354,7 @@ __global__ void __launch_bounds__(kFsThreads) k_tc_select(const float* __restric
   each_selected([&](int64_t j) {
     ++mysel;
     if (j >= N) return;
-    const float c = cost32_one<WEIGHTED>(grid, (int64_t)dict[j] * ch, am, eo, we, n);
+    const float c = cost32_one<WEIGHTED ? 1 : 0>(grid, (int64_t)dict[j] * ch, am, eo, we, n);
     if (c < mt) {
       mt = c;
       const float T = band_limit32(mt, n);
@@ -395,7 +399,7 @@ __global__ void __launch_bounds__(kFsThreads) k_tc_select(const float* __restric
   } else {
     each_selected([&](int64_t j) {
       if (j >= N) return;
-      const float c = cost32_one<WEIGHTED>(grid, (int64_t)dict[j] * ch, am, eo, we, n);
+      const float c = cost32_one<WEIGHTED ? 1 : 0>(grid, (int64_t)dict[j] * ch, am, eo, we, n);
       if (c <= T) push(j, c);
     });
   }
@@ -424,7 +428,7 @@ __global__ void __launch_bounds__(kFsThreads) k_tc_select(const float* __restric
   } else {
     each_selected([&](int64_t j) {
       if (j >= N) return;
-      const float c = cost32_one<WEIGHTED>(grid, (int64_t)dict[j] * ch, am, eo, we, n);
+      const float c = cost32_one<WEIGHTED ? 1 : 0>(grid, (int64_t)dict[j] * ch, am, eo, we, n);
       if (c <= T) consider(j, c);
     });
   }
@@ -501,7 +505,7 @@ __global__ void k_fill_u32(unsigned int* p, int64_t n, unsigned int v) {
   if (i < n) p[i] = v;
 }
 
-template <int QT, int EPT, bool W>
+template <int QT, int EPT, int W>
 int run_scan(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
              const int* eoff_all, const float* weights, const int64_t* lin, int64_t Q, float* tilemin,
              unsigned int* gmin, int64_t ntiles, cudaStream_t st) {
@@ -519,7 +523,7 @@ int run_scan(const Geo& g, const float* grid, const uint8_t* cur_mask, const uin
   return SFC_OK;
 }
 
-template <int EPT, bool W>
+template <int EPT, int W>
 int run_band(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
              const int* eoff_all, const float* weights, const int64_t* lin, int64_t Q, const float* tilemin,
              const unsigned int* gmin, int64_t ntiles, int64_t* pick, float* cost, cudaStream_t st) {
@@ -533,26 +537,47 @@ int run_band(const Geo& g, const float* grid, const uint8_t* cur_mask, const uin
   return SFC_OK;
 }
 
+// Cost-mode dispatch (cm: bit 0 weights, bit 1 L1) of the scan and band passes.
+template <int QT, int EPT>
+int scan_cm(int cm, const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
+            const int* eoff_all, const float* weights, const int64_t* lin, int64_t Q, float* tilemin,
+            unsigned int* gmin, int64_t ntiles, cudaStream_t st) {
+  switch (cm & 3) {
+    case 0: return run_scan<QT, EPT, 0>(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, st);
+    case 1: return run_scan<QT, EPT, 1>(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, st);
+    case 2: return run_scan<QT, EPT, 2>(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, st);
+    default: return run_scan<QT, EPT, 3>(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, st);
+  }
+}
+
+template <int EPT>
+int band_cm(int cm, const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
+            const int* eoff_all, const float* weights, const int64_t* lin, int64_t Q, const float* tilemin,
+            const unsigned int* gmin, int64_t ntiles, int64_t* pick, float* cost, cudaStream_t st) {
+  switch (cm & 3) {
+    case 0: return run_band<EPT, 0>(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, pick, cost, st);
+    case 1: return run_band<EPT, 1>(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, pick, cost, st);
+    case 2: return run_band<EPT, 2>(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, pick, cost, st);
+    default: return run_band<EPT, 3>(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, pick, cost, st);
+  }
+}
+
 }  // namespace
 
 // One query whose centre (linear index) is already on the device and valid; the
 // caller owns the tile-minimum buffer (ceil(N / 1024) floats) and gmin.
 int fullscan_single(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
-                    const int* eoff_all, const float* weights, bool weighted, const int64_t* centre_lin,
+                    const int* eoff_all, const float* weights, int cm, const int64_t* centre_lin,
                     int64_t* pick, float* cost, float* tilemin, unsigned int* gmin, cudaStream_t st) {
   constexpr int EPT = 4;
   const int64_t ntiles = (N + kFsThreads * EPT - 1) / (kFsThreads * EPT);
   count_launch();
   k_fill_u32<<<1, 32, 0, st>>>(gmin, 1, 0x7f800000u);
-  int rc = weighted ? run_scan<1, EPT, true>(g, grid, cur_mask, dict, N, eoff_all, weights, centre_lin, 1, tilemin,
-                                             gmin, ntiles, st)
-                    : run_scan<1, EPT, false>(g, grid, cur_mask, dict, N, eoff_all, weights, centre_lin, 1, tilemin,
-                                              gmin, ntiles, st);
+  const int rc = scan_cm<1, EPT>(cm, g, grid, cur_mask, dict, N, eoff_all, weights, centre_lin, 1, tilemin, gmin,
+                                 ntiles, st);
   SFC_CHECK(rc);
-  return weighted ? run_band<EPT, true>(g, grid, cur_mask, dict, N, eoff_all, weights, centre_lin, 1, tilemin, gmin,
-                                        ntiles, pick, cost, st)
-                  : run_band<EPT, false>(g, grid, cur_mask, dict, N, eoff_all, weights, centre_lin, 1, tilemin, gmin,
-                                         ntiles, pick, cost, st);
+  return band_cm<EPT>(cm, g, grid, cur_mask, dict, N, eoff_all, weights, centre_lin, 1, tilemin, gmin, ntiles, pick,
+                      cost, st);
 }
 
 int tc_prescore(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
@@ -634,7 +659,7 @@ int tc_prescores_all(const Geo& g, const float* grid, const uint8_t* cur_mask, c
 }
 
 int fullscan_batch(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
-                   const int* eoff_all, const float* weights, bool weighted, const int32_t* centres,
+                   const int* eoff_all, const float* weights, int cm, const int32_t* centres,
                    const int64_t* centre_lin, int64_t Q, int64_t* pick, float* cost, cudaStream_t st) {
   if (Q <= 0) return SFC_OK;
   constexpr int EPT = 4;
@@ -661,16 +686,10 @@ int fullscan_batch(const Geo& g, const float* grid, const uint8_t* cur_mask, con
   k_centre_fix<<<(unsigned)((Q + 255) / 256), 256, 0, st>>>(lin, Q, g, bad);
   count_launch();
   k_fill_u32<<<(unsigned)((Q + 255) / 256), 256, 0, st>>>(gmin, Q, 0x7f800000u);
-  int rc;
-  if (Q >= 8)
-    rc = weighted ? run_scan<8, EPT, true>(g, grid, cur_mask, dict, N, eoff_all, weights, L, Q, tilemin, gmin, ntiles, st)
-                  : run_scan<8, EPT, false>(g, grid, cur_mask, dict, N, eoff_all, weights, L, Q, tilemin, gmin, ntiles, st);
-  else
-    rc = weighted ? run_scan<1, EPT, true>(g, grid, cur_mask, dict, N, eoff_all, weights, L, Q, tilemin, gmin, ntiles, st)
-                  : run_scan<1, EPT, false>(g, grid, cur_mask, dict, N, eoff_all, weights, L, Q, tilemin, gmin, ntiles, st);
+  int rc = Q >= 8 ? scan_cm<8, EPT>(cm, g, grid, cur_mask, dict, N, eoff_all, weights, L, Q, tilemin, gmin, ntiles, st)
+                   : scan_cm<1, EPT>(cm, g, grid, cur_mask, dict, N, eoff_all, weights, L, Q, tilemin, gmin, ntiles, st);
   SFC_CHECK(rc);
-  rc = weighted ? run_band<EPT, true>(g, grid, cur_mask, dict, N, eoff_all, weights, L, Q, tilemin, gmin, ntiles, pick, cost, st)
-                : run_band<EPT, false>(g, grid, cur_mask, dict, N, eoff_all, weights, L, Q, tilemin, gmin, ntiles, pick, cost, st);
+  rc = band_cm<EPT>(cm, g, grid, cur_mask, dict, N, eoff_all, weights, L, Q, tilemin, gmin, ntiles, pick, cost, st);
   SFC_CHECK(rc);
   count_launch();
   k_mark_bad<<<(unsigned)((Q + 255) / 256), 256, 0, st>>>(bad, Q, pick, cost);
@@ -685,7 +704,7 @@ int fullscan_batch(const Geo& g, const float* grid, const uint8_t* cur_mask, con
 // The batched full scan into caller-provided scratch (no allocation): lin: Q
 // int64; bad: Q bytes; gmin: Q words; tilemin: Q * ceil(N / 1024) floats.
 int fullscan_batch_into(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
-                        const int* eoff_all, const float* weights, bool weighted, const int32_t* centres, int64_t Q,
+                        const int* eoff_all, const float* weights, int cm, const int32_t* centres, int64_t Q,
                         int64_t* pick, float* cost, int64_t* lin, uint8_t* bad, unsigned int* gmin, float* tilemin,
                         cudaStream_t st) {
   if (Q <= 0) return SFC_OK;
@@ -698,16 +717,10 @@ int fullscan_batch_into(const Geo& g, const float* grid, const uint8_t* cur_mask
   k_centre_fix<<<qb, 256, 0, st>>>(lin, Q, g, bad);
   count_launch();
   k_fill_u32<<<qb, 256, 0, st>>>(gmin, Q, 0x7f800000u);
-  int rc;
-  if (Q >= 8)
-    rc = weighted ? run_scan<8, EPT, true>(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, st)
-                  : run_scan<8, EPT, false>(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, st);
-  else
-    rc = weighted ? run_scan<1, EPT, true>(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, st)
-                  : run_scan<1, EPT, false>(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, st);
+  int rc = Q >= 8 ? scan_cm<8, EPT>(cm, g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, st)
+                   : scan_cm<1, EPT>(cm, g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, st);
   SFC_CHECK(rc);
-  rc = weighted ? run_band<EPT, true>(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, pick, cost, st)
-                : run_band<EPT, false>(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, pick, cost, st);
+  rc = band_cm<EPT>(cm, g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, pick, cost, st);
   SFC_CHECK(rc);
   count_launch();
   k_mark_bad<<<qb, 256, 0, st>>>(bad, Q, pick, cost);

@@ -88,6 +88,11 @@ extern "C" int fullscan_query_batch_static(const float* grid, const uint8_t* dic
       }
       weighted |= v != 1.0f;
     }
+  if (p->cost != SFC_COST_L2 && p->cost != SFC_COST_L1) {
+    set_error("cost must be SFC_COST_L2 or SFC_COST_L1");
+    return SFC_EINVAL;
+  }
+  const int cm = (weighted ? 1 : 0) | (p->cost == SFC_COST_L1 ? 2 : 0);
   // scratch layout (every piece 256-byte aligned), sized by the largest
   // possible dictionary (every valid centre)
   const int64_t npix = g.X * g.Y * g.Z;
@@ -127,7 +132,7 @@ extern "C" int fullscan_query_batch_static(const float* grid, const uint8_t* dic
     set_error("the dictionary is empty (no fully known patch)");
     return SFC_EINVAL;
   }
-  return fullscan_batch_into(g, grid, cur_mask, dict, N, eo, w, weighted, centres, Q, pick, cost,
+  return fullscan_batch_into(g, grid, cur_mask, dict, N, eo, w, cm, centres, Q, pick, cost,
                              reinterpret_cast<int64_t*>(base + o_lin), base + o_bad,
                              reinterpret_cast<unsigned int*>(base + o_gmin), reinterpret_cast<float*>(base + o_tm),
                              st);

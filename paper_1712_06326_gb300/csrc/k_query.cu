@@ -33,7 +33,7 @@ struct QArgs {
   const uint8_t* mask;
   const int32_t* centres;
   Geo g;
-  int C, D, bits, bp, W, select, m, s, L, maxsel, knn, capw, curve;
+  int C, D, bits, bp, W, select, m, s, L, maxsel, knn, capw, curve, l1;
   int64_t N;
   const uint32_t* sqc;
   const uint32_t* dict;
@@ -521,7 +521,9 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
       if (lane + 32 * t < n) {
         float p = __ldg(a.grid + sb + eor[t]);
         float d = __fmaf_rn(-am[t], p, mt[t]);
-        if (WEIGHTED)
+        if (a.l1)  // L1 norm (Sec. III.K): w |d|
+          acc = WEIGHTED ? __fmaf_rn(wv[t], fabsf(d), acc) : __fadd_rn(acc, fabsf(d));
+        else if (WEIGHTED)
           acc = __fmaf_rn(__fmul_rn(wv[t], d), d, acc);
         else
           acc = __fmaf_rn(d, d, acc);
@@ -561,7 +563,7 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   for (int ci = tid; ci < ncand; ci += kQThreads) {
     if (c32[ci] <= T) {
       const uint32_t j = ucand[ci];
-      const double c64 = exact_cost64(a.grid, (int64_t)a.dict[j] * ch, tv, tm, eo, P, ch, a.weights);
+      const double c64 = exact_cost64(a.grid, (int64_t)a.dict[j] * ch, tv, tm, eo, P, ch, a.weights, a.l1 != 0);
       if (c64 < bc || (c64 == bc && ci < bi)) {
         bc = c64;
         bi = ci;
@@ -648,6 +650,7 @@ int query_batch(const Index& ix, const float* grid, const uint8_t* cur_mask, con
   a.maxsel = ix.select == SFC_SELECT_BEST ? 1 : ix.C;
   a.knn = ix.knn;
   a.curve = ix.curve;
+  a.l1 = ix.l1 ? 1 : 0;
   a.sqc = ix.sqc;
   a.capw = ix.knn > 0 ? ix.knn : ix.W;
   if (ix.knn > 0 && !ix.sqc) {

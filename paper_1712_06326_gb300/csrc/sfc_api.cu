@@ -156,7 +156,7 @@ cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st) {
 }
 
 int fill_loop(const Geo& g, float* grid, uint8_t* mask, int prio, int mode, const Index* ix, const uint32_t* dict,
-              int64_t N, const int* eoff_all, const float* weights, bool weighted, int64_t max_steps, int64_t* log,
+              int64_t N, const int* eoff_all, const float* weights, int cm, int64_t max_steps, int64_t* log,
               int64_t* steps_done, cudaStream_t st);
 
 // The device must be an sm_103 part (the library carries sm_103a code only) and
@@ -334,6 +334,10 @@ int build_index(const float* grid, const uint8_t* dict_mask, const sfc_grid* gp,
               "knn 0..128, curve)");
     return SFC_EINVAL;
   }
+  if (p->cost != SFC_COST_L2 && p->cost != SFC_COST_L1) {
+    set_error("cost must be SFC_COST_L2 or SFC_COST_L1");
+    return SFC_EINVAL;
+  }
   if (p->knn > 0 && p->curve != SFC_CURVE_MORTON) {
     set_error("the k-NN search (knn > 0) runs on the z-curve (SFC_CURVE_MORTON) only");
     return SFC_EUNSUPPORTED;
@@ -348,6 +352,7 @@ int build_index(const float* grid, const uint8_t* dict_mask, const sfc_grid* gp,
   ix.W = p->window;
   ix.knn = p->knn;
   ix.curve = p->curve;
+  ix.l1 = p->cost == SFC_COST_L1;
   ix.select = p->select;
   ix.frac = p->subset_frac;
   ix.pca_sample = p->pca_sample;
@@ -628,6 +633,15 @@ int fullscan_query_batch(const float* grid, const uint8_t* dict_mask, const uint
     set_error("fullscan_query_batch: precision must be SFC_FP32 or SFC_FP16");
     return SFC_EUNSUPPORTED;
   }
+  if (p->cost != SFC_COST_L2 && p->cost != SFC_COST_L1) {
+    set_error("cost must be SFC_COST_L2 or SFC_COST_L1");
+    return SFC_EINVAL;
+  }
+  if (p->precision == SFC_FP16 && p->cost != SFC_COST_L2) {
+    set_error("the tensor-core pre-score (SFC_FP16) is an L2 expansion; use SFC_FP32 with SFC_COST_L1");
+    return SFC_EUNSUPPORTED;
+  }
+  const int cm = (weighted ? 1 : 0) | (p->cost == SFC_COST_L1 ? 2 : 0);
   const bool tc = p->precision == SFC_FP16;
   cudaStream_t st = (cudaStream_t)stream;
   if (tc) tc_trace_begin(st);
@@ -644,7 +658,7 @@ int fullscan_query_batch(const float* grid, const uint8_t* dict_mask, const uint
   SFC_CHECK(upload_patch_tables(g, &eo, st));
   SFC_CHECK(upload(&wd, w.data(), w.size(), st));
   const int rc = tc ? fullscan_batch_tc(g, grid, cur_mask, dict, N, eo, wd, weighted, centres, Q, pick, cost, nullptr, st)
-                    : fullscan_batch(g, grid, cur_mask, dict, N, eo, wd, weighted, centres, nullptr, Q, pick, cost, st);
+                    : fullscan_batch(g, grid, cur_mask, dict, N, eo, wd, cm, centres, nullptr, Q, pick, cost, st);
   cudaFreeAsync(dict, st);
   cudaFreeAsync(eo, st);
   cudaFreeAsync(wd, st);
@@ -717,6 +731,11 @@ int inpaint_run(float* grid, uint8_t* mask, const sfc_grid* gp, const sfc_params
   SFC_CHECK(check_weights(w));
   bool weighted = false;
   for (float v : w) weighted |= v != 1.0f;
+  if (p->cost != SFC_COST_L2 && p->cost != SFC_COST_L1) {
+    set_error("cost must be SFC_COST_L2 or SFC_COST_L1");
+    return SFC_EINVAL;
+  }
+  const int cm = (weighted ? 1 : 0) | (p->cost == SFC_COST_L1 ? 2 : 0);
   Index ix;
   int rc = SFC_OK;
   uint32_t* dict = nullptr;
@@ -738,7 +757,7 @@ int inpaint_run(float* grid, uint8_t* mask, const sfc_grid* gp, const sfc_params
     SFC_CHECK(upload_patch_tables(g, &eo, st));
     SFC_CHECK(upload(&wd, w.data(), w.size(), st));
   }
-  rc = fill_loop(g, grid, mask, p->priority, mode, mode == SFC_MODE_SFC ? &ix : nullptr, dict, N, eo, wd, weighted,
+  rc = fill_loop(g, grid, mask, p->priority, mode, mode == SFC_MODE_SFC ? &ix : nullptr, dict, N, eo, wd, cm,
                  max_steps, log, steps_done, st);
   if (mode == SFC_MODE_SFC) {
     free_index(ix);

@@ -22,6 +22,7 @@ SFC_FP32, SFC_BF16, SFC_FP16 = 0, 1, 2
 SFC_PRIO_CONFIDENCE, SFC_PRIO_CRIMINISI = 0, 1
 SFC_MODE_FULLSCAN, SFC_MODE_SFC = 0, 1
 SFC_CURVE_MORTON, SFC_CURVE_HILBERT = 0, 1
+SFC_COST_L2, SFC_COST_L1 = 0, 1
 
 EXPORTS = ["sfc_params_default", "sfc_index_build", "sfc_index_destroy", "sfc_index_info", "sfc_index_export",
            "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "fullscan_query_batch_static",
@@ -39,7 +40,8 @@ class sfc_params(C.Structure):
                 ("window", C.c_int32), ("subset_frac", C.c_float), ("shifts", C.c_void_p),
                 ("ch_weights", C.c_void_p), ("basis", C.c_void_p), ("mean", C.c_void_p), ("select", C.c_int32),
                 ("precision", C.c_int32), ("pca_sample", C.c_int64), ("priority", C.c_int32),
-                ("keep_intermediates", C.c_int32), ("knn", C.c_int32), ("curve", C.c_int32)]
+                ("keep_intermediates", C.c_int32), ("knn", C.c_int32), ("curve", C.c_int32),
+                ("cost", C.c_int32)]
 
 
 _lib = None
@@ -230,13 +232,13 @@ def sfc_query_candidates(ix: Index, grid: torch.Tensor, cur_mask: torch.Tensor, 
 
 def fullscan_query_batch(grid: torch.Tensor, dict_mask: torch.Tensor, cur_mask: torch.Tensor,
                          centres: torch.Tensor, K: int, ch_weights=None, pick=None, cost=None,
-                         precision: int = SFC_FP32):
+                         precision: int = SFC_FP32, norm: int = SFC_COST_L2):
     grid = _dev(grid, torch.float32)
     dict_mask = _dev(dict_mask, torch.uint8)
     cur_mask = _dev(cur_mask, torch.uint8)
     centres = _dev(centres, torch.int32)
     Q = centres.shape[0]
-    P = Params(K=K, ch_weights=ch_weights, precision=precision)
+    P = Params(K=K, ch_weights=ch_weights, precision=precision, cost=norm)
     g = make_grid(grid)
     if pick is None:
         pick = torch.empty(Q, dtype=torch.int64, device=grid.device)
