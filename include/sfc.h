@@ -251,8 +251,8 @@ uint64_t sfc_launch_count(void);
  * moments (mean + covariance), eigen-solve, basis finalisation,
  * projection + keys, sort -- and *builds the number of builds summed, and
  * *eig_flops the summed algorithmic FP64 flops of the eigen-solves
- * (per index and iteration 2 s^2 p + 4 s p^2, s = subset length, p = block
- * size).  Any output may be NULL. */
+ * (per index: 2 s^2 p per product of the covariance with the block and 4 s p^2
+ * per orthonormalisation, s = subset length, p = block size).  Any output may be NULL. */
 enum { SFC_TRACE_PHASES = 6 };
 int sfc_trace(int on);
 int sfc_trace_read(double* ms, int64_t* builds, double* eig_flops);

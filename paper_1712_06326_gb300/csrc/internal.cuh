@@ -78,7 +78,8 @@ struct Index {
   cudaEvent_t ev[SFC_TRACE_PHASES + 1] = {};
   bool traced = false;
   int p_block = 0;             // subspace block size
-  int* eig_iters = nullptr;    // C (device): iterations used per index
+  int* eig_iters = nullptr;    // C (device): products A Q computed per index
+  int eig_per_orth = 1;        // products per orthonormalisation (2 on the cluster path)
 };
 
 // Record phase boundary k of a traced build (no-op otherwise).

@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ grid,
   for (int q = 0; q < kPE; ++q)
 #pragma unroll
     for (int k = 0; k < D; ++k) acc[q][k] = 0.0f;
+#pragma unroll 2
   for (int i = 0; i < s; ++i) {
     const int o = eo[i];
     const float m = mu[i];

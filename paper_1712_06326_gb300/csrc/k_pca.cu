@@ -538,7 +538,7 @@ __global__ void k_pca_finalize(SiBufs b, const double* __restrict__ mean, int s,
 // cluster barriers between phases.  Rayleigh-Ritz and the convergence test run
 // every kRR-th iteration (the subspace converges at the same rate without it).
 // ----------------------------------------------------------------------------
-constexpr int kRR = 4;
+constexpr int kRR = 2;  // Rayleigh-Ritz every kRR iterations (of two products each)
 constexpr int kMaxIterCl = 64;
 
 // 1/sqrt(x) to FP64 accuracy from an FP32 seed (two Newton steps, FMAs only)
@@ -550,7 +550,7 @@ __device__ inline double rsqrt64(double x) {
 }
 
 // Eigen-decomposition of the small symmetric H (np x np, shared, FP64) for the
-// cluster path: cyclic Jacobi in FP32 (cheap on this part), then two steps of
+// cluster path: parallel Jacobi in FP32 (cheap on this part), then two steps of
 // Ogita & Aishima's iterative refinement in FP64 ("Iterative refinement for
 // symmetric eigenvalue decomposition", 2018): with X the current eigenvector
 // matrix, R = I - X^T X, S = X^T H X, l_i = S_ii / (1 - R_ii),
@@ -567,7 +567,14 @@ __device__ void small_eig_refined(const double* H, double* W, double* ev, int np
   }
   __syncthreads();
   if (threadIdx.x < 32) {
+    // parallel Jacobi (round-robin ordering): each round rotates np / 2
+    // disjoint pairs at once -- the angles from the matrix at the start of the
+    // round, then all column rotations, then all row rotations (J^T H J with J
+    // the product of the pairs' rotations); np - 1 rounds make a sweep
     const int lane = threadIdx.x;
+    const int half = np / 2;
+    __shared__ int jp[12], jq[12];
+    __shared__ float jc[12], js[12];
     for (int sweep = 0; sweep < 12; ++sweep) {
       float off = 0.0f, all = 0.0f;
       for (int t = lane; t < np * np; t += 32) {
@@ -579,33 +586,61 @@ __device__ void small_eig_refined(const double* H, double* W, double* ev, int np
         off += __shfl_xor_sync(0xffffffffu, off, o);
         all += __shfl_xor_sync(0xffffffffu, all, o);
       }
-      if (off <= 1e-13f * all) break;  // FP32 accuracy reached; FP64 refinement follows
-      for (int pp = 0; pp < np - 1; ++pp)
-        for (int q = pp + 1; q < np; ++q) {
+      // off-diagonal norm 1e-5 of the whole: the FP64 refinement below squares
+      // the error twice, well past FP64 accuracy
+      if (off <= 1e-10f * all) break;
+      for (int r = 0; r < np - 1; ++r) {
+        if (lane < half) {
+          // pair lane of round r: (0, 1 + r) for lane 0, else two players
+          // rotating around the fixed player 0
+          int a, b;
+          if (lane == 0) {
+            a = 0;
+            b = 1 + r;
+          } else {
+            a = 1 + (r + lane) % (np - 1);
+            b = 1 + (r - lane + np - 1) % (np - 1);
+          }
+          const int pp = a < b ? a : b, q = a < b ? b : a;
           const float apq = H32[pp * np + q];
-          if (apq == 0.0f) continue;
-          const float tau = (H32[q * np + q] - H32[pp * np + pp]) / (2.0f * apq);
-          const float tt = tau >= 0.0f ? 1.0f / (tau + sqrtf(1.0f + tau * tau)) : -1.0f / (-tau + sqrtf(1.0f + tau * tau));
-          const float cs = rsqrtf(1.0f + tt * tt), sn = tt * cs;
-          __syncwarp();
-          if (lane < np) {
-            const int k = lane;
-            const float hkp = H32[k * np + pp], hkq = H32[k * np + q];
-            H32[k * np + pp] = cs * hkp - sn * hkq;
-            H32[k * np + q] = sn * hkp + cs * hkq;
+          float cs = 1.0f, sn = 0.0f;
+          if (apq != 0.0f) {
+            const float tau = (H32[q * np + q] - H32[pp * np + pp]) / (2.0f * apq);
+            const float tt =
+                tau >= 0.0f ? 1.0f / (tau + sqrtf(1.0f + tau * tau)) : -1.0f / (-tau + sqrtf(1.0f + tau * tau));
+            cs = rsqrtf(1.0f + tt * tt);
+            sn = tt * cs;
           }
-          __syncwarp();
-          if (lane < np) {
-            const int k = lane;
-            const float hpk = H32[pp * np + k], hqk = H32[q * np + k];
-            H32[pp * np + k] = cs * hpk - sn * hqk;
-            H32[q * np + k] = sn * hpk + cs * hqk;
-            const float wkp = W32[k * np + pp], wkq = W32[k * np + q];
-            W32[k * np + pp] = cs * wkp - sn * wkq;
-            W32[k * np + q] = sn * wkp + cs * wkq;
-          }
-          __syncwarp();
+          jp[lane] = pp;
+          jq[lane] = q;
+          jc[lane] = cs;
+          js[lane] = sn;
         }
+        __syncwarp();
+        // columns pp, q of every row k (and of W)
+        for (int t = lane; t < half * np; t += 32) {
+          const int l = t / np, k = t % np;
+          const int pp = jp[l], q = jq[l];
+          const float cs = jc[l], sn = js[l];
+          const float hkp = H32[k * np + pp], hkq = H32[k * np + q];
+          H32[k * np + pp] = cs * hkp - sn * hkq;
+          H32[k * np + q] = sn * hkp + cs * hkq;
+          const float wkp = W32[k * np + pp], wkq = W32[k * np + q];
+          W32[k * np + pp] = cs * wkp - sn * wkq;
+          W32[k * np + q] = sn * wkp + cs * wkq;
+        }
+        __syncwarp();
+        // rows pp, q
+        for (int t = lane; t < half * np; t += 32) {
+          const int l = t / np, k = t % np;
+          const int pp = jp[l], q = jq[l];
+          const float cs = jc[l], sn = js[l];
+          const float hpk = H32[pp * np + k], hqk = H32[q * np + k];
+          H32[pp * np + k] = cs * hpk - sn * hqk;
+          H32[q * np + k] = sn * hpk + cs * hqk;
+        }
+        __syncwarp();
+      }
     }
   }
   __syncthreads();
@@ -768,6 +803,38 @@ __device__ void cl_cholqr(cg::cluster_group& cl, ClShm& m, int nr, int r0, int s
   cl.sync();
 }
 
+// every CTA: Qf (s x p) := the block whose rows [r0, r0 + nr) are Zs here
+template <int CS>
+__device__ void cl_allgather_rows(cg::cluster_group& cl, ClShm& m, int nr, int r0, int s, int p, int rp) {
+  for (int t = threadIdx.x; t < nr * p; t += blockDim.x) m.Qf[(r0 + t / p) * p + t % p] = m.Zs[t];
+  cl.sync();
+  const int me = (int)cl.block_rank();
+#pragma unroll 4
+  for (int t = threadIdx.x; t < s * p; t += blockDim.x) {
+    const int rk = (t / p) / rp;
+    if (rk != me) m.Qf[t] = cl.map_shared_rank(m.Qf, rk)[t];
+  }
+  cl.sync();
+}
+
+// Zs := rows [r0, r0 + nr) of A Qf
+__device__ inline void local_rows_times(const ClShm& m, int nr, int s, int p, double* out) {
+  for (int t = threadIdx.x; t < nr * p; t += blockDim.x) {
+    const int i = t / p, k = t % p;
+    const double* ar = m.As + i * s;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int j = 0;
+    for (; j + 3 < s; j += 4) {
+      a0 = fma(ar[j], m.Qf[j * p + k], a0);
+      a1 = fma(ar[j + 1], m.Qf[(j + 1) * p + k], a1);
+      a2 = fma(ar[j + 2], m.Qf[(j + 2) * p + k], a2);
+      a3 = fma(ar[j + 3], m.Qf[(j + 3) * p + k], a3);
+    }
+    for (; j < s; ++j) a0 = fma(ar[j], m.Qf[j * p + k], a0);
+    out[t] = (a0 + a1) + (a2 + a3);
+  }
+}
+
 template <int CS>
 __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int D) {
   cg::cluster_group cl = cg::this_cluster();
@@ -820,20 +887,7 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
   bool conv = false;
   for (int it = 0; it < kMaxIterCl && !conv; ++it) {
     // Y = A Q (this CTA's rows)
-    for (int t = threadIdx.x; t < nr * p; t += blockDim.x) {
-      const int i = t / p, k = t % p;
-      const double* ar = m.As + i * s;
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-      int j = 0;
-      for (; j + 3 < s; j += 4) {
-        a0 = fma(ar[j], m.Qf[j * p + k], a0);
-        a1 = fma(ar[j + 1], m.Qf[(j + 1) * p + k], a1);
-        a2 = fma(ar[j + 2], m.Qf[(j + 2) * p + k], a2);
-        a3 = fma(ar[j + 3], m.Qf[(j + 3) * p + k], a3);
-      }
-      for (; j < s; ++j) a0 = fma(ar[j], m.Qf[j * p + k], a0);
-      m.Ys[t] = (a0 + a1) + (a2 + a3);
-    }
+    local_rows_times(m, nr, s, p, m.Ys);
     __syncthreads();
     const bool rr = (it % kRR) == kRR - 1 || it == kMaxIterCl - 1;
     if (rr) {
@@ -901,7 +955,7 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
         if (me == 0 && threadIdx.x < p) b.e[(int64_t)c * p + threadIdx.x] = m.ev[threadIdx.x];
         if (me == 0 && threadIdx.x == 0) {
           b.done[c] = conv ? 1 : 0;
-          b.iters[c] = it + 1;
+          b.iters[c] = 2 * it + 1;  // products with A (the last iteration stops after its first)
         }
         break;
       }
@@ -909,8 +963,15 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
       for (int t = threadIdx.x; t < nr * p; t += blockDim.x) m.Zs[t] = m.Ys[t];
       __syncthreads();
     }
+    // a second product before orthonormalising: Z = A^2 Q (A^2 X after a
+    // Rayleigh-Ritz step), which squares the convergence factor per Cholesky QR;
+    // the block's condition stays near (l_1 / l_p)^2, inside CholeskyQR2's reach
+    __syncthreads();
+    cl_allgather_rows<CS>(cl, m, nr, r0, s, p, rp);
+    local_rows_times(m, nr, s, p, m.Zs);
+    __syncthreads();
     // two passes while the block is far from the eigen-directions; afterwards
-    // Z = A Q has nearly orthogonal columns and one pass is accurate to rounding
+    // Z has nearly orthogonal columns and one pass is accurate to rounding
     cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
     if (it < 3) cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
   }
@@ -1037,6 +1098,7 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    ix.eig_per_orth = 2;
     count_launch();
     if (cs == 16)
       SFC_TRY(cudaLaunchKernelEx(&cfg, k_si_cluster<16>, b, s, p, D));

@@ -95,7 +95,9 @@ static void trace_fold(Index& ix) {
     for (int k = 0; k < SFC_TRACE_PHASES; ++k) g_trace.ms[k] += t[k];
     g_trace.builds += 1;
     const double s = ix.s, p = ix.p_block;
-    for (int c = 0; c < ix.C; ++c) g_trace.eig_flops += it[c] * (2.0 * s * s * p + 4.0 * s * p * p);
+    // per product A Q: 2 s^2 p; per orthonormalisation (Gram + Q = Z R^-1): 4 s p^2
+    for (int c = 0; c < ix.C; ++c)
+      g_trace.eig_flops += it[c] * 2.0 * s * s * p + std::ceil((double)it[c] / ix.eig_per_orth) * 4.0 * s * p * p;
   }
   for (auto& e : ix.ev)
     if (e) {
