@@ -68,6 +68,9 @@ def lib():
                 "or_query": (None, [P, P, I32, P, I32, I32, I32, I32, I32, I32, I32, P, P, I32, P, P, P, P, P,
                                     P, P, P, I64, I64, P, P, P, P, P, P]),
                 "or_knn_bruteforce": (None, [P, I64, I32, P, I32, P, P]),
+                "or_cost64_2": (C.c_double, [P, P, I32, P, P, P, I32, I32, I64, I64, P, I32]),
+                "or_query_dict": (None, [P, P, P, P, P, I32, I32, I32, I32, I32, I32, I32, I32, P, P, I32, P, P, P,
+                                         P, P, I32, P, P, P, I64, I64, P, P, P, P, I32]),
                 "or_query_knn": (None, [P, P, I32, P, I32, I32, I32, I32, I32, I32, I32, P, P, I32, P, P, P, P, P,
                                         P, I64, I64, P, P, P, P, I32]),
                 "or_inpaint": (I64, [P, P, I32, P, I32, I32, I32, I32, P, P, I64, I32, I32, I32, I32, I32, P,
@@ -330,6 +333,38 @@ def query(ix, grid, cur_mask, target_lin, W, select=0, weights=None, norm=0):
                          _p(ix["sids"]), _p(ix["dict"]), ix["N"], int(target_lin), _p(qk), _p(pos), _p(cand),
                          _p(nc), _p(pick), _p(cost), int(norm))
     return dict(pick=int(pick[0]), cost=float(cost[0]), cand=cand[: int(nc[0])].copy(), qkeys=qk, pos=pos)
+
+
+def cost64_2(tgrid, tmask, dgrid, K, target_lin, source_lin, weights=None, norm=0) -> float:
+    """cost64 with the target patch from tgrid/tmask and the source patch from dgrid."""
+    ndim, text, ch = geometry(tgrid)
+    _, dext, dch = geometry(dgrid)
+    assert dch == ch
+    w = None if weights is None else _c(weights, np.float32)
+    return lib().or_cost64_2(_p(_c(tgrid, np.float32)), _p(_c(tmask, np.uint8)), ndim, _p(text),
+                             _p(_c(dgrid, np.float32)), _p(dext), ch, K, int(target_lin), int(source_lin), _p(w),
+                             int(norm))
+
+
+def query_dict(ix, dict_grid, grid, cur_mask, target_lin, W, select=0, weights=None, norm=0):
+    """SFC query of a target in (grid, cur_mask) against an index whose dictionary
+    patches are in dict_grid -> dict(pick, cost, cand)."""
+    ndim, text, ch = geometry(grid)
+    _, dext, _ = geometry(dict_grid)
+    C_, D = ix["C"], ix["D"]
+    cand = np.empty(C_ * max(W, 1), np.int64)
+    nc = np.zeros(1, np.int64)
+    pick = np.zeros(1, np.int64)
+    cost = np.zeros(1, np.float64)
+    w = None if weights is None else _c(weights, np.float32)
+    lib().or_query_dict(_p(_c(dict_grid, np.float32)), _p(dext), _p(_c(grid, np.float32)),
+                        _p(_c(cur_mask, np.uint8)), _p(text), ndim, ch, ix["K"], C_, D, ix["bits"], W, select,
+                        _p(w), _p(_c(ix["subset"], np.int32)), ix["m"], _p(_c(ix["basis"], np.float32)),
+                        _p(_c(ix["mean"], np.float32)), _p(_c(ix["lo"], np.float32)), _p(_c(ix["scale"], np.float32)),
+                        _p(ix["shifts"]), int(ix.get("curve", 0)), _p(ix["skeys"]), _p(ix["sids"]),
+                        _p(_c(ix["dict"], np.int64)), ix["N"], int(target_lin), _p(cand), _p(nc), _p(pick), _p(cost),
+                        int(norm))
+    return dict(pick=int(pick[0]), cost=float(cost[0]), cand=cand[: int(nc[0])].copy())
 
 
 def query_knn(ix, grid, cur_mask, target_lin, k, select=0, weights=None, norm=0):

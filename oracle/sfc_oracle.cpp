@@ -731,6 +731,96 @@ void or_query_knn(const float* grid, const uint8_t* cur_mask, int ndim, const in
 }
 
 // ----------------------------------------------------------------------------
+// Queries against an index built on another grid (a stored dictionary, Sec.
+// II.H: the index is built once and reused): the target patch lives in tgrid /
+// tmask (geometry gt), the dictionary patches in dgrid (geometry gd, the
+// index's); same channels and patch size.  cost64_2 is cost64 with the two
+// patches taken from different grids (same element order and arithmetic).
+// ----------------------------------------------------------------------------
+double cost64_2(const Geo& gt, const float* tgrid, const uint8_t* tmask, int64_t t, const Geo& gd,
+                const float* dgrid, int64_t s, const float* w, int norm) {
+  double acc = 0.0;
+  for (int pp = 0; pp < gt.P; ++pp) {
+    int64_t qt = patch_pixel(gt, t, pp);
+    if (!tmask[qt]) continue;
+    int64_t qs = patch_pixel(gd, s, pp);
+    for (int c = 0; c < gt.ch; ++c) {
+      double d = (double)tgrid[qt * gt.ch + c] - (double)dgrid[qs * gd.ch + c];
+      double term = norm == 1 ? std::fabs(d) : d * d;
+      double wc = w ? (double)w[c] : 1.0;
+      acc = acc + wc * term;
+    }
+  }
+  return acc;
+}
+
+double or_cost64_2(const float* tgrid, const uint8_t* tmask, int tndim, const int64_t* text, const float* dgrid,
+                   const int64_t* dext, int ch, int K, int64_t target, int64_t source, const float* w, int norm) {
+  Geo gt = make_geo(tndim, text, ch, K), gd = make_geo(tndim, dext, ch, K);
+  return cost64_2(gt, tgrid, tmask, target, gd, dgrid, source, w, norm);
+}
+
+// or_query_curve with the target in (tgrid, tmask, text) and the dictionary
+// patches in (dgrid, dext); `target` is a linear pixel index of the target grid.
+void or_query_dict(const float* dgrid, const int64_t* dext, const float* tgrid, const uint8_t* tmask,
+                   const int64_t* text, int ndim, int ch, int K, int C, int D, int bits, int W, int select,
+                   const float* w, const int32_t* subset, int m, const float* basis, const float* mean32,
+                   const float* lo, const float* scale, const int32_t* shift, int curve, const uint64_t* skeys,
+                   const uint32_t* sids, const int64_t* dict, int64_t N, int64_t target, int64_t* cand,
+                   int64_t* ncand, int64_t* pick, double* cost, int norm) {
+  Geo gt = make_geo(ndim, text, ch, K), gd = make_geo(ndim, dext, ch, K);
+  const int s = m * ch;
+  std::vector<int> use;
+  if (select == 1) {
+    int best = 0, bestcov = -1;
+    for (int cv = 0; cv < C; ++cv) {
+      int cov = 0;
+      for (int i = 0; i < m; ++i) cov += tmask[patch_pixel(gt, target, subset[cv * m + i])] ? 1 : 0;
+      if (cov > bestcov) {
+        bestcov = cov;
+        best = cv;
+      }
+    }
+    use.push_back(best);
+  } else {
+    for (int cv = 0; cv < C; ++cv) use.push_back(cv);
+  }
+  std::vector<int64_t> ids;
+  std::vector<float> y(D);
+  std::vector<uint32_t> qq(D);
+  for (int cv : use) {
+    // the projection of the target's known subset values (or_project_one on the target grid)
+    or_project_one(tgrid, tmask, ndim, text, ch, K, target, subset + (size_t)cv * m, m, basis + (size_t)cv * s * D,
+                   mean32 + (size_t)cv * s, D, y.data());
+    const int32_t* sh = shift ? shift + (size_t)cv * D : nullptr;
+    for (int k = 0; k < D; ++k)
+      qq[k] = or_quantise_one(y[k], lo[cv * D + k], scale[cv * D + k], bits) + (uint32_t)(sh ? sh[k] : 0);
+    const uint64_t key = or_curve_key(qq.data(), D, or_key_bits(D, bits, sh), curve);
+    const int64_t p = or_lower_bound(skeys + (size_t)cv * N, N, key);
+    const int64_t len = W < N ? W : N;
+    int64_t start = p - W / 2;
+    const int64_t maxs = N - W > 0 ? N - W : 0;
+    if (start > maxs) start = maxs;
+    if (start < 0) start = 0;
+    for (int64_t i = start; i < start + len; ++i) ids.push_back(sids[(size_t)cv * N + i]);
+  }
+  sort_unique(ids);
+  for (size_t i = 0; i < ids.size(); ++i) cand[i] = ids[i];
+  *ncand = (int64_t)ids.size();
+  double best = INFINITY;
+  int64_t bj = -1;
+  for (int64_t j : ids) {
+    double c = cost64_2(gt, tgrid, tmask, target, gd, dgrid, dict[j], w, norm);
+    if (c < best) {
+      best = c;
+      bj = j;
+    }
+  }
+  *pick = bj;
+  *cost = best;
+}
+
+// ----------------------------------------------------------------------------
 // Inpainting loop (Sec. I; Fig. 1(a)).  Readings:
 //  * fill front: known pixels with an unknown axis-neighbour (4-/6-connected);
 //    a target centre is a front pixel moved into [r, ext-1-r] per axis (the

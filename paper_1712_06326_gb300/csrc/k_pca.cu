@@ -617,9 +617,10 @@ __device__ void small_eig_refined(const double* H, double* W, double* ev, int np
           js[lane] = sn;
         }
         __syncwarp();
-        // columns pp, q of every row k (and of W)
+        // columns pp, q of every row k (and of W); consecutive lanes take
+        // different pairs of one row, so their words sit in different banks
         for (int t = lane; t < half * np; t += 32) {
-          const int l = t / np, k = t % np;
+          const int l = t % half, k = t / half;
           const int pp = jp[l], q = jq[l];
           const float cs = jc[l], sn = js[l];
           const float hkp = H32[k * np + pp], hkq = H32[k * np + q];

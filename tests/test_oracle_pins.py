@@ -571,6 +571,50 @@ def test_hilbert_query_window_covering_dictionary_equals_fullscan():
 
 
 # ----------------------------------------------------------------------------
+# queries against an index built on another grid (a stored dictionary)
+# ----------------------------------------------------------------------------
+def test_cost64_2_same_grid_and_numpy():
+    rng = np.random.default_rng(40)
+    a = rng.random((20, 24, 3)).astype(np.float32)
+    b = rng.random((17, 30, 3)).astype(np.float32)
+    mb = (rng.random((17, 30)) < 0.8).astype(np.uint8)
+    ma = np.ones((20, 24), np.uint8)
+    K, r = 5, 2
+    w = np.array([1.0, 0.5, 2.0], np.float32)
+    for t, sidx in [(3 * 24 + 4, 10 * 24 + 12), (17 * 24 + 21, 2 * 24 + 2)]:
+        assert O.cost64_2(a, ma, a, K, t, sidx, w) == O.cost64(a, ma, K, t, sidx, w)
+    for (ty, tx), (sy, sx) in [((5, 9), (4, 7)), ((14, 27), (17, 21)), ((2, 2), (2, 2))]:
+        T = b[ty - r:ty + r + 1, tx - r:tx + r + 1].astype(np.float64)
+        km = mb[ty - r:ty + r + 1, tx - r:tx + r + 1].astype(np.float64)[..., None]
+        Pp = a[sy - r:sy + r + 1, sx - r:sx + r + 1].astype(np.float64)
+        for norm in (0, 1):
+            d = T - Pp
+            ref = float(((np.abs(d) if norm else d * d) * km * w).sum())
+            got = O.cost64_2(b, mb, a, K, ty * 30 + tx, sy * 24 + sx, w, norm)
+            assert abs(got - ref) <= 1e-12 * max(1.0, ref)
+
+
+def test_query_dict_same_grid_equals_query(small_rgb):
+    g, m, ix = small_rgb
+    t = synth.front_targets(m, 7, cap=10, cfg=2)
+    for tl in O.centres_to_lin(t, ix["ext"]):
+        r1 = O.query(ix, g, m, tl, W=12)
+        r2 = O.query_dict(ix, g, g, m, tl, 12)
+        assert r1["pick"] == r2["pick"] and r1["cost"] == r2["cost"] and np.array_equal(r1["cand"], r2["cand"])
+
+
+def test_query_dict_other_grid_full_window_is_bruteforce(small_rgb):
+    g, m, ix = small_rgb
+    g2, m2 = synth.voronoi2d(80, cfg=2, seed_sub=11)  # another image, another size
+    t = synth.front_targets(m2, 7, cap=6, cfg=2)
+    lin = O.centres_to_lin(t, O.geometry(g2)[1])
+    for tl in lin:
+        r = O.query_dict(ix, g, g2, m2, tl, ix["N"])
+        costs = np.array([O.cost64_2(g2, m2, g, 7, tl, j) for j in ix["dict"]])
+        assert r["pick"] == int(np.argmin(costs)) and r["cost"] == costs.min()
+
+
+# ----------------------------------------------------------------------------
 # SFC query with exact k-NN lists (Sec. II.D)
 # ----------------------------------------------------------------------------
 def _numpy_knn(qc, query, k):
