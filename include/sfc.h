@@ -167,6 +167,30 @@ int sfc_query_batch(const sfc_index* ix, const float* grid, const uint8_t* cur_m
  * outside the box with Tropf and Herzog's BIGMIN.  The candidates are the union
  * of the lists, rescored as above. */
 
+/* Stored indices (for a dictionary that is built once and queried many
+ * times, or from other grids).  sfc_index_save writes every array of the index
+ * and its parameters to the HOST file `path` (synchronises; projections and
+ * unsorted keys are not saved); sfc_index_load reads such a file onto the
+ * current device (synchronises `stream` at the end) -- the result answers
+ * queries exactly like the saved index.  The index does not hold its grid: the
+ * caller keeps the grid the index was built from.  Files are host byte order,
+ * with a magic and version checked on load (SFC_EINVAL when they differ or the
+ * file is truncated). */
+int sfc_index_save(const sfc_index* ix, const char* path);
+/* The scalar build parameters (pointers NULL, shifts/weights/basis not
+ * returned) and the build grid's geometry of an index; either may be NULL. */
+int sfc_index_params(const sfc_index* ix, sfc_params* p, sfc_grid* g);
+int sfc_index_load(const char* path, void* stream, sfc_index** out);
+
+/* sfc_query_batch for targets on another grid: the target patches are read
+ * from grid / cur_mask (device, geometry g: the index's ndim and ch, any
+ * extents >= K; centres in its coordinates) and the dictionary patches from
+ * dict_grid (device, the grid the index was built from).  Outputs as
+ * sfc_query_batch. */
+int sfc_query_batch_dict(const sfc_index* ix, const float* dict_grid, const float* grid, const uint8_t* cur_mask,
+                         const sfc_grid* g, const int32_t* centres, int64_t Q, int64_t* pick, float* cost,
+                         void* stream);
+
 /* Intermediate results of sfc_query_batch for checking: qkeys (Q*C uint64),
  * pos (Q*C int64 lower_bound positions; -1 for unselected indices),
  * cand (Q*C*L int32 sorted unique candidate ids, padded with -1; L = W, or k

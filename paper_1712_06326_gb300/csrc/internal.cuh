@@ -111,9 +111,16 @@ int radix_sort_pairs(const uint64_t* keys, uint64_t* skeys, uint32_t* sids, int6
                      cudaStream_t st);
 
 // k_query.cu
+// Targets on a grid other than the index's: its geometry, its patch element
+// offsets (device), and the index's grid holding the dictionary patches.
+struct TargetGrid {
+  Geo g;
+  const int* eoff;
+  const float* dict_grid;
+};
 int query_batch(const Index& ix, const float* grid, const uint8_t* cur_mask, const int32_t* centres, int64_t Q,
                 int64_t* pick, float* cost, uint64_t* qkeys, int64_t* pos, int32_t* cand, int32_t* ncand,
-                cudaStream_t st);
+                cudaStream_t st, const TargetGrid* tgt = nullptr);
 
 // k_fullscan.cu
 // cm (cost mode): bit 0 = channel weights other than 1, bit 1 = L1 norm (Sec. III.K).

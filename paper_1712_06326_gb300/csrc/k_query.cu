@@ -29,7 +29,9 @@ constexpr int kQThreads = 256;
 constexpr int kQWarps = kQThreads / 32;
 
 struct QArgs {
-  const float* grid;
+  const float* grid;   // targets (geometry g)
+  const float* dgrid;  // dictionary patches (the index's grid; = grid unless queried from another grid)
+  const int* deoff;    // element offsets of a patch in dgrid
   const uint8_t* mask;
   const int32_t* centres;
   Geo g;
@@ -503,7 +505,7 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
       float k = tm[e / ch] ? 1.0f : 0.0f;
       am[t] = k;
       mt[t] = k * tv[e];
-      eor[t] = eo[e];
+      eor[t] = a.deoff[e];
       wv[t] = WEIGHTED ? a.weights[e % ch] : 1.0f;
     } else {
       am[t] = 0.0f;
@@ -519,7 +521,7 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
 #pragma unroll
     for (int t = 0; t < MAXE; ++t) {
       if (lane + 32 * t < n) {
-        float p = __ldg(a.grid + sb + eor[t]);
+        float p = __ldg(a.dgrid + sb + eor[t]);
         float d = __fmaf_rn(-am[t], p, mt[t]);
         if (a.l1)  // L1 norm (Sec. III.K): w |d|
           acc = WEIGHTED ? __fmaf_rn(wv[t], fabsf(d), acc) : __fadd_rn(acc, fabsf(d));
@@ -563,7 +565,7 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   for (int ci = tid; ci < ncand; ci += kQThreads) {
     if (c32[ci] <= T) {
       const uint32_t j = ucand[ci];
-      const double c64 = exact_cost64(a.grid, (int64_t)a.dict[j] * ch, tv, tm, eo, P, ch, a.weights, a.l1 != 0);
+      const double c64 = exact_cost64(a.dgrid, (int64_t)a.dict[j] * ch, tv, tm, a.deoff, P, ch, a.weights, a.l1 != 0);
       if (c64 < bc || (c64 == bc && ci < bi)) {
         bc = c64;
         bi = ci;
@@ -627,7 +629,7 @@ int dispatch_q(const QArgs& a, int64_t Q, size_t shm, cudaStream_t st) {
 
 int query_batch(const Index& ix, const float* grid, const uint8_t* cur_mask, const int32_t* centres, int64_t Q,
                 int64_t* pick, float* cost, uint64_t* qkeys, int64_t* pos, int32_t* cand, int32_t* ncand,
-                cudaStream_t st) {
+                cudaStream_t st, const TargetGrid* tgt) {
   if (Q <= 0) return SFC_OK;
   if (Q > 0x7fffffffLL) {
     set_error("too many queries in one batch");
@@ -635,9 +637,11 @@ int query_batch(const Index& ix, const float* grid, const uint8_t* cur_mask, con
   }
   QArgs a;
   a.grid = grid;
+  a.dgrid = tgt ? tgt->dict_grid : grid;
+  a.deoff = ix.eoff_all;
   a.mask = cur_mask;
   a.centres = centres;
-  a.g = ix.g;
+  a.g = tgt ? tgt->g : ix.g;
   a.C = ix.C;
   a.D = ix.D;
   a.bits = ix.bits;
@@ -676,7 +680,7 @@ int query_batch(const Index& ix, const float* grid, const uint8_t* cur_mask, con
   a.shifts = ix.shifts;
   a.skeys = ix.skeys;
   a.sids = ix.sids;
-  a.eoff_all = ix.eoff_all;
+  a.eoff_all = tgt ? tgt->eoff : ix.eoff_all;
   a.weights = ix.weights;
   a.pick = pick;
   a.cost = cost;

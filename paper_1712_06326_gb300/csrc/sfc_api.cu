@@ -4,6 +4,7 @@
 #include <atomic>
 #include <array>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -315,6 +316,62 @@ int upload_patch_tables(const Geo& g, int** eoff_all, cudaStream_t st) {
   return upload(eoff_all, eo.data(), eo.size(), st);
 }
 
+// ---------------------------------------------------------------------------
+// index files: a fixed header, the parameters as int64 (and the subset
+// fraction as a double), then every array as (byte count, bytes); host byte
+// order (little-endian on every supported machine)
+// ---------------------------------------------------------------------------
+namespace {
+constexpr char kIndexMagic[8] = {'S', 'F', 'C', 'I', 'D', 'X', 'v', '1'};
+
+struct FileOut {
+  FILE* f;
+  bool ok = true;
+  void raw(const void* p, size_t n) { ok = ok && std::fwrite(p, 1, n, f) == n; }
+  void i64(int64_t v) { raw(&v, sizeof v); }
+};
+struct FileIn {
+  FILE* f;
+  bool ok = true;
+  void raw(void* p, size_t n) { ok = ok && std::fread(p, 1, n, f) == n; }
+  int64_t i64() {
+    int64_t v = 0;
+    raw(&v, sizeof v);
+    return v;
+  }
+};
+
+template <class T>
+void host_out(FileOut& o, const T* h, size_t count) {
+  o.i64((int64_t)(sizeof(T) * count));
+  o.raw(h, sizeof(T) * count);
+}
+template <class T>
+int dev_out(FileOut& o, const T* d, size_t count) {
+  std::vector<T> h(count);
+  if (count) SFC_TRY(cudaMemcpy(h.data(), d, sizeof(T) * count, cudaMemcpyDeviceToHost));
+  host_out(o, h.data(), count);
+  return SFC_OK;
+}
+template <class T>
+bool host_in(FileIn& in, std::vector<T>& h, size_t count) {
+  if (in.i64() != (int64_t)(sizeof(T) * count)) return false;
+  h.resize(count);
+  in.raw(h.data(), sizeof(T) * count);
+  return in.ok;
+}
+template <class T>
+int dev_in(FileIn& in, T** d, size_t count, cudaStream_t st) {
+  std::vector<T> h;
+  if (!host_in(in, h, count)) {
+    set_error("index file: truncated or inconsistent array");
+    return SFC_EINVAL;
+  }
+  SFC_CHECK(upload(d, h.data(), count, st));
+  return SFC_OK;
+}
+}  // namespace
+
 // Build every array of an index (shared by sfc_index_build and inpaint_run).
 int build_index(const float* grid, const uint8_t* dict_mask, const sfc_grid* gp, const sfc_params* p,
                 cudaStream_t st, Index& ix) {
@@ -575,6 +632,212 @@ int sfc_index_export(const sfc_index* h, int64_t* dict, int32_t* subsets, float*
   if (skeys) SFC_TRY(cudaMemcpy(skeys, ix.skeys, sizeof(uint64_t) * C * N, cudaMemcpyDeviceToHost));
   if (sids) SFC_TRY(cudaMemcpy(sids, ix.sids, sizeof(uint32_t) * C * N, cudaMemcpyDeviceToHost));
   return SFC_OK;
+}
+
+int sfc_index_params(const sfc_index* h, sfc_params* p, sfc_grid* g) {
+  g_err.clear();
+  if (!h) {
+    set_error("sfc_index_params: NULL index");
+    return SFC_EINVAL;
+  }
+  const Index& ix = h->ix;
+  if (p) {
+    sfc_params_default(p);
+    p->K = ix.g.K;
+    p->curves = ix.C;
+    p->dims = ix.D;
+    p->bits = ix.bits;
+    p->window = ix.W;
+    p->subset_frac = ix.frac;
+    p->select = ix.select;
+    p->pca_sample = ix.pca_sample;
+    p->knn = ix.knn;
+    p->curve = ix.curve;
+    p->cost = ix.l1 ? SFC_COST_L1 : SFC_COST_L2;
+  }
+  if (g) {
+    g->ndim = ix.g.ndim;
+    g->ch = ix.g.ch;
+    g->ext[0] = ix.g.X;
+    g->ext[1] = ix.g.Y;
+    g->ext[2] = ix.g.Z;
+  }
+  return SFC_OK;
+}
+
+int sfc_index_save(const sfc_index* h, const char* path) {
+  g_err.clear();
+  if (!h || !path) {
+    set_error("sfc_index_save: NULL index or path");
+    return SFC_EINVAL;
+  }
+  const Index& ix = h->ix;
+  SFC_TRY(cudaDeviceSynchronize());
+  FILE* f = std::fopen(path, "wb");
+  if (!f) {
+    set_error(std::string("sfc_index_save: cannot open ") + path);
+    return SFC_EINVAL;
+  }
+  FileOut o{f};
+  o.raw(kIndexMagic, sizeof kIndexMagic);
+  const int64_t head[] = {ix.g.ndim, ix.g.ch,  ix.g.K,  ix.g.X, ix.g.Y, ix.g.Z,       ix.C,         ix.D,
+                          ix.bits,   ix.bp,    ix.W,    ix.select, ix.m, ix.s,        ix.N,         ix.knn,
+                          ix.curve,  ix.l1 ? 1 : 0, ix.p_block, ix.eig_per_orth, ix.pca_sample};
+  o.i64((int64_t)(sizeof head / sizeof head[0]));
+  o.raw(head, sizeof head);
+  const double frac = ix.frac;
+  o.raw(&frac, sizeof frac);
+  const int64_t C = ix.C, N = ix.N, D = ix.D, s = ix.s, m = ix.m;
+  host_out(o, ix.subset_h.data(), ix.subset_h.size());
+  host_out(o, ix.weights_h.data(), ix.weights_h.size());
+  int rc = SFC_OK;
+  if (rc == SFC_OK) rc = dev_out(o, ix.dict, (size_t)N);
+  if (rc == SFC_OK) rc = dev_out(o, ix.eoff_all, (size_t)ix.g.n);
+  if (rc == SFC_OK) rc = dev_out(o, ix.sub_eoff, (size_t)(C * s));
+  if (rc == SFC_OK) rc = dev_out(o, ix.sub_pix, (size_t)(C * m));
+  if (rc == SFC_OK) rc = dev_out(o, ix.weights, (size_t)ix.g.ch);
+  if (rc == SFC_OK) rc = dev_out(o, ix.basis, (size_t)(C * s * D));
+  if (rc == SFC_OK) rc = dev_out(o, ix.mean, (size_t)(C * s));
+  if (rc == SFC_OK) rc = dev_out(o, ix.evals, (size_t)(C * s));
+  if (rc == SFC_OK) rc = dev_out(o, ix.lo, (size_t)(C * D));
+  if (rc == SFC_OK) rc = dev_out(o, ix.scale, (size_t)(C * D));
+  if (rc == SFC_OK) rc = dev_out(o, ix.shifts, (size_t)(C * D));
+  if (rc == SFC_OK) rc = dev_out(o, ix.skeys, (size_t)(C * N));
+  if (rc == SFC_OK) rc = dev_out(o, ix.sids, (size_t)(C * N));
+  if (rc == SFC_OK && ix.knn > 0) rc = dev_out(o, ix.sqc, (size_t)(C * N * D));
+  const bool ok = o.ok && std::fclose(f) == 0;
+  if (rc != SFC_OK) return rc;
+  if (!ok) {
+    set_error(std::string("sfc_index_save: write to ") + path + " failed");
+    return SFC_EINVAL;
+  }
+  return SFC_OK;
+}
+
+int sfc_index_load(const char* path, void* stream, sfc_index** out) {
+  g_err.clear();
+  if (!path || !out) {
+    set_error("sfc_index_load: NULL path or out");
+    return SFC_EINVAL;
+  }
+  *out = nullptr;
+  SFC_CHECK(check_device());
+  FILE* f = std::fopen(path, "rb");
+  if (!f) {
+    set_error(std::string("sfc_index_load: cannot open ") + path);
+    return SFC_EINVAL;
+  }
+  FileIn in{f};
+  char magic[8] = {};
+  in.raw(magic, sizeof magic);
+  const int64_t nhead = in.i64();
+  int64_t head[21] = {};
+  if (!in.ok || std::memcmp(magic, kIndexMagic, sizeof magic) != 0 || nhead != 21) {
+    std::fclose(f);
+    set_error("sfc_index_load: not an index file of this library version");
+    return SFC_EINVAL;
+  }
+  in.raw(head, sizeof head);
+  double frac = 0.0;
+  in.raw(&frac, sizeof frac);
+  cudaStream_t st = (cudaStream_t)stream;
+  auto* h = new sfc_index();
+  cudaGetDevice(&h->device);
+  Index& ix = h->ix;
+  sfc_grid gp;
+  gp.ndim = (int32_t)head[0];
+  gp.ch = (int32_t)head[1];
+  gp.ext[0] = head[3];
+  gp.ext[1] = head[4];
+  gp.ext[2] = head[5];
+  int rc = in.ok ? make_geo(&gp, (int)head[2], &ix.g) : SFC_EINVAL;
+  ix.C = (int)head[6];
+  ix.D = (int)head[7];
+  ix.bits = (int)head[8];
+  ix.bp = (int)head[9];
+  ix.W = (int)head[10];
+  ix.select = (int)head[11];
+  ix.m = (int)head[12];
+  ix.s = (int)head[13];
+  ix.N = head[14];
+  ix.knn = (int)head[15];
+  ix.curve = (int)head[16];
+  ix.l1 = head[17] != 0;
+  ix.p_block = (int)head[18];
+  ix.eig_per_orth = (int)head[19];
+  ix.pca_sample = head[20];
+  ix.frac = (float)frac;
+  ix.keep = false;
+  const int64_t C = ix.C, N = ix.N, D = ix.D, s = ix.s, m = ix.m;
+  if (rc == SFC_OK && (C < 1 || C > 14 || D < 1 || D > 16 || N < 1 || s != m * ix.g.ch || m < 1 || m > ix.g.P ||
+                       ix.bits < 1 || ix.bits > 21 || ix.knn < 0 || ix.knn > 128)) {
+    set_error("sfc_index_load: inconsistent index parameters");
+    rc = SFC_EINVAL;
+  }
+  if (rc == SFC_OK && !(host_in(in, ix.subset_h, (size_t)(C * m)) && host_in(in, ix.weights_h, (size_t)ix.g.ch))) {
+    set_error("sfc_index_load: truncated file");
+    rc = SFC_EINVAL;
+  }
+  if (rc == SFC_OK) rc = dev_in(in, &ix.dict, (size_t)N, st);
+  if (rc == SFC_OK) rc = dev_in(in, &ix.eoff_all, (size_t)ix.g.n, st);
+  if (rc == SFC_OK) rc = dev_in(in, &ix.sub_eoff, (size_t)(C * s), st);
+  if (rc == SFC_OK) rc = dev_in(in, &ix.sub_pix, (size_t)(C * m), st);
+  if (rc == SFC_OK) rc = dev_in(in, &ix.weights, (size_t)ix.g.ch, st);
+  if (rc == SFC_OK) rc = dev_in(in, &ix.basis, (size_t)(C * s * D), st);
+  if (rc == SFC_OK) rc = dev_in(in, &ix.mean, (size_t)(C * s), st);
+  if (rc == SFC_OK) rc = dev_in(in, &ix.evals, (size_t)(C * s), st);
+  if (rc == SFC_OK) rc = dev_in(in, &ix.lo, (size_t)(C * D), st);
+  if (rc == SFC_OK) rc = dev_in(in, &ix.scale, (size_t)(C * D), st);
+  if (rc == SFC_OK) rc = dev_in(in, &ix.shifts, (size_t)(C * D), st);
+  if (rc == SFC_OK) rc = dev_in(in, &ix.skeys, (size_t)(C * N), st);
+  if (rc == SFC_OK) rc = dev_in(in, &ix.sids, (size_t)(C * N), st);
+  if (rc == SFC_OK && ix.knn > 0) rc = dev_in(in, &ix.sqc, (size_t)(C * N * D), st);
+  if (rc == SFC_OK && (pmalloc(&ix.eig_iters, sizeof(int) * C, st) != cudaSuccess ||
+                       cudaMemsetAsync(ix.eig_iters, 0, sizeof(int) * C, st) != cudaSuccess)) {
+    cudaGetLastError();
+    set_error("sfc_index_load: out of device memory");
+    rc = SFC_ENOMEM;
+  }
+  std::fclose(f);
+  if (rc != SFC_OK) {
+    free_index(ix);
+    delete h;
+    return rc;
+  }
+  SFC_TRY(cudaStreamSynchronize(st));
+  *out = h;
+  return SFC_OK;
+}
+
+int sfc_query_batch_dict(const sfc_index* h, const float* dict_grid, const float* grid, const uint8_t* cur_mask,
+                         const sfc_grid* gp, const int32_t* centres, int64_t Q, int64_t* pick, float* cost,
+                         void* stream) {
+  g_err.clear();
+  if (!h || Q < 0) {
+    set_error("sfc_query_batch_dict: NULL index or negative Q");
+    return SFC_EINVAL;
+  }
+  if (Q == 0) return SFC_OK;
+  if (!dict_grid || !grid || !cur_mask || !centres || !pick || !cost || !gp) {
+    set_error("sfc_query_batch_dict: NULL pointer");
+    return SFC_EINVAL;
+  }
+  SFC_CHECK(check_device());
+  const Index& ix = h->ix;
+  if (gp->ndim != ix.g.ndim || gp->ch != ix.g.ch) {
+    set_error("sfc_query_batch_dict: the target grid needs the index's dimension and channel count");
+    return SFC_EINVAL;
+  }
+  TargetGrid tg;
+  SFC_CHECK(make_geo(gp, ix.g.K, &tg.g));
+  cudaStream_t st = (cudaStream_t)stream;
+  int* eo = nullptr;
+  SFC_CHECK(upload_patch_tables(tg.g, &eo, st));
+  tg.eoff = eo;
+  tg.dict_grid = dict_grid;
+  const int rc = query_batch(ix, grid, cur_mask, centres, Q, pick, cost, nullptr, nullptr, nullptr, nullptr, st, &tg);
+  cudaFreeAsync(eo, st);
+  return rc;
 }
 
 int sfc_query_batch(const sfc_index* h, const float* grid, const uint8_t* cur_mask, const int32_t* centres,

@@ -27,7 +27,7 @@ SFC_COST_L2, SFC_COST_L1 = 0, 1
 EXPORTS = ["sfc_params_default", "sfc_index_build", "sfc_index_destroy", "sfc_index_info", "sfc_index_export",
            "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "fullscan_query_batch_static",
            "sfc_tc_prescores", "inpaint_run", "sfc_status", "sfc_launch_count", "sfc_trace", "sfc_trace_read", "sfc_trace_tc_read",
-           "sfc_last_error"]
+           "sfc_last_error", "sfc_index_save", "sfc_index_load", "sfc_index_params", "sfc_query_batch_dict"]
 TRACE_PHASES = ("dictionary", "moments", "eigen", "finalize", "project_keys", "sort")
 
 
@@ -62,6 +62,10 @@ def lib():
         L.sfc_index_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)]
         L.sfc_index_export.argtypes = [vp] * 12
         L.sfc_query_batch.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
+        L.sfc_index_save.argtypes = [vp, C.c_char_p]
+        L.sfc_index_params.argtypes = [vp, C.POINTER(sfc_params), C.POINTER(sfc_grid)]
+        L.sfc_index_load.argtypes = [C.c_char_p, vp, C.POINTER(vp)]
+        L.sfc_query_batch_dict.argtypes = [vp, vp, vp, vp, C.POINTER(sfc_grid), vp, i64, vp, vp, vp]
         L.sfc_query_candidates.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp, vp]
         L.fullscan_query_batch.argtypes = [vp, vp, vp, C.POINTER(sfc_grid), C.POINTER(sfc_params), vp, i64, vp, vp,
                                            vp]
@@ -82,7 +86,8 @@ def lib():
         L.sfc_trace_tc_read.restype = C.c_int
         for name in ["sfc_index_build", "sfc_index_destroy", "sfc_index_info", "sfc_index_export",
                      "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "fullscan_query_batch_static",
-                     "sfc_tc_prescores", "inpaint_run", "sfc_status"]:
+                     "sfc_tc_prescores", "inpaint_run", "sfc_status", "sfc_index_save", "sfc_index_load",
+                     "sfc_index_params", "sfc_query_batch_dict"]:
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -182,6 +187,38 @@ def sfc_index_build(grid: torch.Tensor, dict_mask: torch.Tensor, **params) -> In
     _check(lib().sfc_index_build(_ptr(grid), _ptr(dict_mask), C.byref(g), C.byref(P.p), _stream(), C.byref(h)),
            "sfc_index_build")
     return Index(h, P, g.ndim)
+
+
+def sfc_index_save(ix: Index, path: str) -> None:
+    _check(lib().sfc_index_save(ix.h, os.fsencode(path)), "sfc_index_save")
+
+
+def sfc_index_load(path: str) -> Index:
+    h = C.c_void_p()
+    _check(lib().sfc_index_load(os.fsencode(path), _stream(), C.byref(h)), "sfc_index_load")
+    P = Params()
+    g = sfc_grid()
+    _check(lib().sfc_index_params(h, C.byref(P.p), C.byref(g)), "sfc_index_params")
+    return Index(h, P, g.ndim)
+
+
+def sfc_query_batch_dict(ix: Index, dict_grid: torch.Tensor, grid: torch.Tensor, cur_mask: torch.Tensor,
+                         centres: torch.Tensor, pick: torch.Tensor | None = None, cost: torch.Tensor | None = None):
+    """Targets on `grid` (any size, same ndim/channels), dictionary patches from
+    `dict_grid` (the grid the index was built from)."""
+    dict_grid = _dev(dict_grid, torch.float32)
+    grid = _dev(grid, torch.float32)
+    cur_mask = _dev(cur_mask, torch.uint8)
+    centres = _dev(centres, torch.int32)
+    Q = centres.shape[0]
+    g = make_grid(grid)
+    if pick is None:
+        pick = torch.empty(Q, dtype=torch.int64, device=grid.device)
+    if cost is None:
+        cost = torch.empty(Q, dtype=torch.float32, device=grid.device)
+    _check(lib().sfc_query_batch_dict(ix.h, _ptr(dict_grid), _ptr(grid), _ptr(cur_mask), C.byref(g), _ptr(centres),
+                                      Q, _ptr(pick), _ptr(cost), _stream()), "sfc_query_batch_dict")
+    return pick, cost
 
 
 def sfc_index_export(ix: Index, proj: bool = False) -> dict:
