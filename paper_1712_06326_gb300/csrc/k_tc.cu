@@ -116,7 +116,9 @@ __device__ inline void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 
 struct TcArgs {
-  int64_t Q, N;        // real rows of A / B
+  int64_t Q, N;        // real rows of A / of this launch's B (a chunk of the dictionary)
+  int64_t n0;          // first dictionary entry of the chunk (a multiple of 256)
+  int64_t Nt;          // entries of the whole dictionary (row stride of scores)
   int kblocks;         // Kp / 64
   int kb_split;        // first K-block of the second accumulator (== kblocks: none)
   int64_t mtiles;      // 128-row query tiles
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const __grid_constant
           const float v = two ? __fadd_rn(__uint_as_float(r[i]), __uint_as_float(r2[i])) : __uint_as_float(r[i]);
           if (col < a.N) {
             mn = fminf(mn, v);
-            if (a.scores && row < a.Q) a.scores[row * a.N + col] = v;
+            if (a.scores && row < a.Q) a.scores[row * a.Nt + a.n0 + col] = v;
           }
         }
         mins[c / 32] = mn;
@@ -276,7 +278,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const __grid_constant
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty)) : "memory");
       if (row < a.Q) {
-        float4* dst = reinterpret_cast<float4*>(a.submin + row * a.nsub + (int64_t)n_tile * (kBN / 32));
+        float4* dst =
+            reinterpret_cast<float4*>(a.submin + row * a.nsub + (a.n0 + (int64_t)n_tile * kBN) / 32);
         dst[0] = make_float4(mins[0], mins[1], mins[2], mins[3]);
         dst[1] = make_float4(mins[4], mins[5], mins[6], mins[7]);
       }
@@ -583,42 +586,55 @@ int tc_prescore(const Geo& g, const float* grid, const uint8_t* cur_mask, const 
   }
   const float* mu = cent;
   const float* pmax = cent + g.ch;
+  // the dictionary operand in chunks of at most kChunkBytes (one chunk for
+  // dictionaries up to ~1.9 M entries at n = 363)
+  constexpr int64_t kChunkBytes = (int64_t)8 << 30;
+  int64_t Nc = kChunkBytes / ((int64_t)Kp * 2) / kBN * kBN;
+  if (Nc < kBN) Nc = kBN;
+  if (Nc > Npad) Nc = Npad;
   SFC_TRY(pmalloc(&A, sizeof(__half) * Qpad * Kp, st));
-  SFC_TRY(pmalloc(&B, sizeof(__half) * Npad * Kp, st));
+  SFC_TRY(pmalloc(&B, sizeof(__half) * Nc * Kp, st));
   count_launch();
   k_tc_prep_A<<<(unsigned)Qpad, 256, 0, st>>>(grid, cur_mask, g, centre_lin, Q, eoff_all, weights, mu, pmax, L,
                                                A, bound);
-  count_launch();
-  k_tc_prep_B<<<152 * 32, 256, 0, st>>>(grid, dict, N, Npad, g, eoff_all, mu, L, B);
   SFC_TRY(cudaGetLastError());
-  CUtensorMap mapA, mapB;
+  CUtensorMap mapA;
   SFC_CHECK(make_map(&mapA, A, Qpad, Kp, kBM));
-  SFC_CHECK(make_map(&mapB, B, Npad, Kp, kBN));
   int* abort_all = nullptr;
   SFC_TRY(pmalloc(&abort_all, sizeof(int), st));
   SFC_TRY(cudaMemsetAsync(abort_all, 0, sizeof(int), st));
-  TcArgs a;
-  a.abort_all = abort_all;
-  a.Q = Q;
-  a.N = N;
-  a.kblocks = L.kblocks;
-  a.kb_split = L.kb_split;
-  a.mtiles = Qpad / kBM;
-  a.tiles = a.mtiles * ntiles;
-  a.nsub = (int64_t)ntiles * (kBN / 32);
-  a.submin = submin;
-  a.scores = scores;
-  a.status = status_word();
   const size_t shm = (size_t)kStages * (kStageA + kStageB) + 1024;
   SFC_TRY(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   int dev = 0, sms = 0;
   SFC_TRY(cudaGetDevice(&dev));
   SFC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const unsigned grid_x = (unsigned)std::min<int64_t>(a.tiles, std::max(sms, 1));
-  tc_trace_mark(1, st);
-  count_launch();
-  k_tc_gemm<<<grid_x, kTcThreads, shm, st>>>(mapA, mapB, a);
-  SFC_TRY(cudaGetLastError());
+  for (int64_t j0 = 0; j0 < N; j0 += Nc) {
+    const int64_t Nch = std::min(Nc, N - j0), Npch = (Nch + kBN - 1) / kBN * kBN;
+    count_launch();
+    k_tc_prep_B<<<152 * 32, 256, 0, st>>>(grid, dict + j0, Nch, Npch, g, eoff_all, mu, L, B);
+    SFC_TRY(cudaGetLastError());
+    CUtensorMap mapB;
+    SFC_CHECK(make_map(&mapB, B, Npch, Kp, kBN));
+    TcArgs a;
+    a.abort_all = abort_all;
+    a.Q = Q;
+    a.N = Nch;
+    a.n0 = j0;
+    a.Nt = N;
+    a.kblocks = L.kblocks;
+    a.kb_split = L.kb_split;
+    a.mtiles = Qpad / kBM;
+    a.tiles = a.mtiles * (Npch / kBN);
+    a.nsub = (int64_t)ntiles * (kBN / 32);
+    a.submin = submin;
+    a.scores = scores;
+    a.status = status_word();
+    const unsigned grid_x = (unsigned)std::min<int64_t>(a.tiles, std::max(sms, 1));
+    if (j0 == 0) tc_trace_mark(1, st);
+    count_launch();
+    k_tc_gemm<<<grid_x, kTcThreads, shm, st>>>(mapA, mapB, a);
+    SFC_TRY(cudaGetLastError());
+  }
   tc_trace_mark(2, st);
   cudaFreeAsync(A, st);
   cudaFreeAsync(B, st);
