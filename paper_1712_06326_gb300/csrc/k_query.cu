@@ -94,6 +94,16 @@ __device__ uint64_t warp_key(uint32_t x, int D, int bp) {
   return key;
 }
 
+// Hilbert key of the coordinates held by lanes 0..D-1 (every lane computes it
+// identically).  Kept out of line: inlined, its loops over a 16-word array
+// cost the query kernel's window path ~10 % even when the z-curve is used.
+__device__ __noinline__ uint64_t warp_hilbert_key(uint32_t x, int D, int bp) {
+  uint32_t xq[16];
+#pragma unroll
+  for (int d = 0; d < 16; ++d) xq[d] = __shfl_sync(0xffffffffu, x, d);
+  return hilbert_key(xq, D, bp);
+}
+
 // Bits of v at the positions set in m, the highest first (a software pext).
 __device__ inline uint32_t extract_bits(uint64_t v, uint64_t m) {
   uint32_t r = 0;
@@ -294,6 +304,39 @@ __device__ void warp_knn(const uint64_t* __restrict__ sk, const uint32_t* __rest
     if (s * 32 + lane < kk) out[s * 32 + lane] = li[s];
 }
 
+// FP32 costs of the candidates ucand[0..ncand), one warp per candidate (lane
+// elements lane + 32 t in registers), into c32; returns this warp's minimum.
+// L1 (Sec. III.K): w |d| instead of w d^2.
+template <int MAXE, bool WEIGHTED, bool L1>
+__device__ __forceinline__ float rescore_all(const float* __restrict__ dgrid, const uint32_t* __restrict__ dict,
+                                             const uint32_t* ucand, int ncand, int ch, int n, const float (&am)[MAXE],
+                                             const float (&mt)[MAXE], const int (&eor)[MAXE],
+                                             const float (&wv)[MAXE], float* c32) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float wmin = INFINITY;
+  for (int ci = warp; ci < ncand; ci += kQWarps) {
+    const int64_t sb = (int64_t)dict[ucand[ci]] * ch;
+    float acc = 0.0f;
+#pragma unroll
+    for (int t = 0; t < MAXE; ++t) {
+      if (lane + 32 * t < n) {
+        float p = __ldg(dgrid + sb + eor[t]);
+        float d = __fmaf_rn(-am[t], p, mt[t]);
+        if (L1)
+          acc = WEIGHTED ? __fmaf_rn(wv[t], fabsf(d), acc) : __fadd_rn(acc, fabsf(d));
+        else if (WEIGHTED)
+          acc = __fmaf_rn(__fmul_rn(wv[t], d), d, acc);
+        else
+          acc = __fmaf_rn(d, d, acc);
+      }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) c32[ci] = acc;
+    wmin = fminf(wmin, acc);
+  }
+  return wmin;
+}
+
 template <int MAXE, bool WEIGHTED, bool KNN>
 __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   const int64_t q = blockIdx.x;
@@ -306,9 +349,11 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   uint32_t* cand = reinterpret_cast<uint32_t*>(eo + n);    // L
   uint32_t* ucand = cand + a.L;                            // L
   float* c32 = reinterpret_cast<float*>(ucand + a.L);      // L
-  uint8_t* tm = reinterpret_cast<uint8_t*>(c32 + a.L);     // P
-  // k-NN region stacks, one per warp (k-NN mode only), 16-byte aligned after tm
-  KnnRegion* knn_stack = reinterpret_cast<KnnRegion*>(tm + ((g.P + 15) & ~15));
+  int* deo = reinterpret_cast<int*>(c32 + a.L);            // n (dictionary-grid offsets)
+  uint8_t* tm = reinterpret_cast<uint8_t*>(deo + n);       // P
+  // k-NN region stacks, one per warp (k-NN mode only), rounded up to a 16-byte
+  // boundary after tm (its offset 12 n + 12 L is only 4-aligned for odd n)
+  KnnRegion* knn_stack = reinterpret_cast<KnnRegion*>(((uintptr_t)(tm + g.P) + 15) & ~(uintptr_t)15);
   __shared__ int s_sel[16];
   __shared__ int s_cov[16];
   __shared__ int s_nsel, s_ncand, s_bad;
@@ -344,6 +389,7 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   for (int e = tid; e < n; e += kQThreads) {
     int o = a.eoff_all[e];
     eo[e] = o;
+    deo[e] = a.deoff[e];
     tv[e] = a.grid[tc * ch + o];
   }
   for (int pp = tid; pp < P; pp += kQThreads) tm[pp] = a.mask[tc + a.eoff_all[pp * ch] / ch];
@@ -395,15 +441,7 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
     uint32_t qk = 0;
     if (lane < a.D) qk = quantise_one(acc, a.lo[c * a.D + lane], a.scale[c * a.D + lane], a.bits) +
                          (uint32_t)a.shifts[c * a.D + lane];
-    uint64_t key;
-    if (a.curve == SFC_CURVE_HILBERT) {
-      uint32_t xq[16];
-#pragma unroll
-      for (int d = 0; d < 16; ++d) xq[d] = __shfl_sync(0xffffffffu, qk, d);
-      key = hilbert_key(xq, a.D, a.bp);  // every lane, identically
-    } else {
-      key = warp_key(qk, a.D, a.bp);
-    }
+    const uint64_t key = a.curve == SFC_CURVE_HILBERT ? warp_hilbert_key(qk, a.D, a.bp) : warp_key(qk, a.D, a.bp);
     const uint64_t* sk = a.skeys + (int64_t)c * a.N;
     int64_t pos = warp_lower_bound(sk, a.N, key);
     if (KNN) {
@@ -505,7 +543,7 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
       float k = tm[e / ch] ? 1.0f : 0.0f;
       am[t] = k;
       mt[t] = k * tv[e];
-      eor[t] = a.deoff[e];
+      eor[t] = deo[e];
       wv[t] = WEIGHTED ? a.weights[e % ch] : 1.0f;
     } else {
       am[t] = 0.0f;
@@ -514,27 +552,9 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
       wv[t] = 0.0f;
     }
   }
-  float wmin = INFINITY;
-  for (int ci = warp; ci < ncand; ci += kQWarps) {
-    const int64_t sb = (int64_t)a.dict[ucand[ci]] * ch;
-    float acc = 0.0f;
-#pragma unroll
-    for (int t = 0; t < MAXE; ++t) {
-      if (lane + 32 * t < n) {
-        float p = __ldg(a.dgrid + sb + eor[t]);
-        float d = __fmaf_rn(-am[t], p, mt[t]);
-        if (a.l1)  // L1 norm (Sec. III.K): w |d|
-          acc = WEIGHTED ? __fmaf_rn(wv[t], fabsf(d), acc) : __fadd_rn(acc, fabsf(d));
-        else if (WEIGHTED)
-          acc = __fmaf_rn(__fmul_rn(wv[t], d), d, acc);
-        else
-          acc = __fmaf_rn(d, d, acc);
-      }
-    }
-    acc = warp_sum(acc);
-    if (lane == 0) c32[ci] = acc;
-    wmin = fminf(wmin, acc);
-  }
+  // the L2 / L1 choice is uniform: one specialised loop each, no test per element
+  const float wmin = a.l1 ? rescore_all<MAXE, WEIGHTED, true>(a.dgrid, a.dict, ucand, ncand, ch, n, am, mt, eor, wv, c32)
+                          : rescore_all<MAXE, WEIGHTED, false>(a.dgrid, a.dict, ucand, ncand, ch, n, am, mt, eor, wv, c32);
   if (lane == 0) s_redf[warp] = wmin;
   __syncthreads();
   float m32 = s_redf[0];
@@ -565,7 +585,7 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   for (int ci = tid; ci < ncand; ci += kQThreads) {
     if (c32[ci] <= T) {
       const uint32_t j = ucand[ci];
-      const double c64 = exact_cost64(a.dgrid, (int64_t)a.dict[j] * ch, tv, tm, a.deoff, P, ch, a.weights, a.l1 != 0);
+      const double c64 = exact_cost64(a.dgrid, (int64_t)a.dict[j] * ch, tv, tm, deo, P, ch, a.weights, a.l1 != 0);
       if (c64 < bc || (c64 == bc && ci < bi)) {
         bc = c64;
         bi = ci;
@@ -689,8 +709,8 @@ int query_batch(const Index& ix, const float* grid, const uint8_t* cur_mask, con
   a.cand_out = cand;
   a.ncand_out = ncand;
   a.status = status_word();
-  const size_t shm = (size_t)ix.g.n * 8 + (size_t)L * 12 + (((size_t)ix.g.P + 15) & ~(size_t)15) +
-                     (ix.knn > 0 ? sizeof(KnnRegion) * kKnnStack * kQWarps : 0);
+  const size_t shm = (size_t)ix.g.n * 12 + (size_t)L * 12 + (size_t)ix.g.P +
+                     (ix.knn > 0 ? 16 + sizeof(KnnRegion) * kKnnStack * kQWarps : 0);
   bool weighted = false;
   for (float w : ix.weights_h) weighted |= (w != 1.0f);
   return weighted ? dispatch_q<true>(a, Q, shm, st) : dispatch_q<false>(a, Q, shm, st);
