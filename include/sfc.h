@@ -191,6 +191,25 @@ int sfc_query_batch_dict(const sfc_index* ix, const float* dict_grid, const floa
                          const sfc_grid* g, const int32_t* centres, int64_t Q, int64_t* pick, float* cost,
                          void* stream);
 
+/* Many images (or volumes) of uneven size, one launch: sfc_multi_create
+ * takes n indices built with the same parameters (patch, curves, dimensions,
+ * bits, window, selection, curve, cost, channel weights; shifts may differ;
+ * knn = 0) and each index's grid and current mask (device, the build
+ * geometry), and uploads a table of the images (synchronises `stream`).
+ * sfc_multi_query answers Q targets of any of the images in ONE kernel launch
+ * with no allocation and no synchronisation (so it can be captured into a
+ * CUDA graph): image[q] (device int32) is the target's image, centres (device,
+ * Q x ndim) its centre in that image; outputs as sfc_query_batch, picks being
+ * ids of that image's dictionary.  An image number outside [0, n) is treated
+ * as an invalid centre (pick -1, cost NaN, SFC_EDEVICE from sfc_status).  The
+ * object refers to the indices, grids and masks: destroy it before them. */
+typedef struct sfc_multi sfc_multi;
+int sfc_multi_create(const sfc_index* const* ix, const float* const* grids, const uint8_t* const* masks, int32_t n,
+                     void* stream, sfc_multi** out);
+int sfc_multi_query(const sfc_multi* mu, const int32_t* image, const int32_t* centres, int64_t Q, int64_t* pick,
+                    float* cost, void* stream);
+int sfc_multi_destroy(sfc_multi* mu);
+
 /* Intermediate results of sfc_query_batch for checking: qkeys (Q*C uint64),
  * pos (Q*C int64 lower_bound positions; -1 for unselected indices),
  * cand (Q*C*L int32 sorted unique candidate ids, padded with -1; L = W, or k

@@ -121,6 +121,14 @@ struct TargetGrid {
 int query_batch(const Index& ix, const float* grid, const uint8_t* cur_mask, const int32_t* centres, int64_t Q,
                 int64_t* pick, float* cost, uint64_t* qkeys, int64_t* pos, int32_t* cand, int32_t* ncand,
                 cudaStream_t st, const TargetGrid* tgt = nullptr);
+// Queries of several images in one launch (every index built with the same
+// parameters); the object keeps a device table of the images.
+struct MultiQuery;
+int multi_query_create(const Index* const* ixs, const float* const* grids, const uint8_t* const* masks, int n,
+                       cudaStream_t st, MultiQuery** out);
+void multi_query_destroy(MultiQuery* m);
+int multi_query_run(const MultiQuery* m, const int32_t* img_of, const int32_t* centres, int64_t Q, int64_t* pick,
+                    float* cost, cudaStream_t st);
 
 // k_fullscan.cu
 // cm (cost mode): bit 0 = channel weights other than 1, bit 1 = L1 norm (Sec. III.K).

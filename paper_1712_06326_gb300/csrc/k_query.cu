@@ -28,14 +28,13 @@ namespace {
 constexpr int kQThreads = 256;
 constexpr int kQWarps = kQThreads / 32;
 
-struct QArgs {
+// Everything that belongs to one image (or volume) and its index.
+struct QImg {
   const float* grid;   // targets (geometry g)
   const float* dgrid;  // dictionary patches (the index's grid; = grid unless queried from another grid)
   const int* deoff;    // element offsets of a patch in dgrid
   const uint8_t* mask;
-  const int32_t* centres;
   Geo g;
-  int C, D, bits, bp, W, select, m, s, L, maxsel, knn, capw, curve, l1;
   int64_t N;
   const uint32_t* sqc;
   const uint32_t* dict;
@@ -47,7 +46,16 @@ struct QArgs {
   const int32_t* shifts;
   const uint64_t* skeys;
   const uint32_t* sids;
-  const int* eoff_all;
+  const int* eoff_all;  // element offsets of a patch in grid
+};
+
+struct QArgs {
+  QImg img;            // the image of every query, or, with imgs: ignored
+  const QImg* imgs;    // several images: query q belongs to imgs[img_of[q]]
+  const int32_t* img_of;
+  int nimg;
+  const int32_t* centres;
+  int C, D, bits, bp, W, select, m, s, L, maxsel, knn, capw, curve, l1;
   const float* weights;
   int64_t* pick;
   float* cost;
@@ -337,10 +345,23 @@ __device__ __forceinline__ float rescore_all(const float* __restrict__ dgrid, co
   return wmin;
 }
 
-template <int MAXE, bool WEIGHTED, bool KNN>
+template <int MAXE, bool WEIGHTED, bool KNN, bool MULTI>
 __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   const int64_t q = blockIdx.x;
-  const Geo& g = a.g;
+  // this query's image: the launch's own, or (MULTI) its entry of the image
+  // table, copied to shared memory for the whole CTA
+  __shared__ QImg s_img;
+  __shared__ int s_badimg;
+  if (MULTI) {
+    if (threadIdx.x == 0) {
+      const int im = a.img_of[q];
+      s_badimg = im < 0 || im >= a.nimg;
+      s_img = a.imgs[s_badimg ? 0 : im];
+    }
+    __syncthreads();
+  }
+  const QImg& I = MULTI ? s_img : a.img;
+  const Geo& g = I.g;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = g.n, P = g.P, ch = g.ch;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -366,7 +387,7 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   if (tid == 0) {
     int64_t cx = a.centres[q * g.ndim + 0], cy = a.centres[q * g.ndim + 1];
     int64_t cz = g.ndim == 3 ? a.centres[q * g.ndim + 2] : 0;
-    s_bad = centre_ok(g, cx, cy, cz) ? 0 : 1;
+    s_bad = centre_ok(g, cx, cy, cz) && !(MULTI && s_badimg) ? 0 : 1;
     s_part[0] = (uint32_t)0;
     if (!s_bad) {
       int64_t lin = lin_of(g, cx, cy, cz);
@@ -387,19 +408,19 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   }
   const int64_t tc = s_redi[0];
   for (int e = tid; e < n; e += kQThreads) {
-    int o = a.eoff_all[e];
+    int o = I.eoff_all[e];
     eo[e] = o;
-    deo[e] = a.deoff[e];
-    tv[e] = a.grid[tc * ch + o];
+    deo[e] = I.deoff[e];
+    tv[e] = I.grid[tc * ch + o];
   }
-  for (int pp = tid; pp < P; pp += kQThreads) tm[pp] = a.mask[tc + a.eoff_all[pp * ch] / ch];
+  for (int pp = tid; pp < P; pp += kQThreads) tm[pp] = I.mask[tc + I.eoff_all[pp * ch] / ch];
   __syncthreads();
 
   // --- index selection ------------------------------------------------------
   if (a.select == SFC_SELECT_BEST) {
     for (int c = warp; c < a.C; c += kQWarps) {
       int cov = 0;
-      for (int i = lane; i < a.m; i += 32) cov += tm[a.sub_pix[c * a.m + i]] ? 1 : 0;
+      for (int i = lane; i < a.m; i += 32) cov += tm[I.sub_pix[c * a.m + i]] ? 1 : 0;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) cov += __shfl_xor_sync(0xffffffffu, cov, o);
       if (lane == 0) s_cov[c] = cov;
@@ -419,8 +440,8 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   __syncthreads();
   const int nsel = s_nsel;
   const int64_t wk = a.knn > 0 ? a.knn : a.W;
-  const int64_t len = wk < a.N ? wk : a.N;
-  int64_t maxs = a.N - a.W;
+  const int64_t len = wk < I.N ? wk : I.N;
+  int64_t maxs = I.N - a.W;
   if (maxs < 0) maxs = 0;
 
   // --- per index: project, key, search, window -------------------------------
@@ -428,9 +449,9 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
     const int c = s_sel[slot];
     float acc = 0.0f;
     if (lane < a.D) {
-      const float* B = a.basis + (int64_t)c * a.s * a.D;
-      const float* mu = a.mean + (int64_t)c * a.s;
-      const int32_t* sp = a.sub_pix + c * a.m;
+      const float* B = I.basis + (int64_t)c * a.s * a.D;
+      const float* mu = I.mean + (int64_t)c * a.s;
+      const int32_t* sp = I.sub_pix + c * a.m;
       for (int i = 0; i < a.s; ++i) {
         int pp = sp[i / ch];
         if (!tm[pp]) continue;
@@ -439,19 +460,19 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
       }
     }
     uint32_t qk = 0;
-    if (lane < a.D) qk = quantise_one(acc, a.lo[c * a.D + lane], a.scale[c * a.D + lane], a.bits) +
-                         (uint32_t)a.shifts[c * a.D + lane];
+    if (lane < a.D) qk = quantise_one(acc, I.lo[c * a.D + lane], I.scale[c * a.D + lane], a.bits) +
+                         (uint32_t)I.shifts[c * a.D + lane];
     const uint64_t key = a.curve == SFC_CURVE_HILBERT ? warp_hilbert_key(qk, a.D, a.bp) : warp_key(qk, a.D, a.bp);
-    const uint64_t* sk = a.skeys + (int64_t)c * a.N;
-    int64_t pos = warp_lower_bound(sk, a.N, key);
+    const uint64_t* sk = I.skeys + (int64_t)c * I.N;
+    int64_t pos = warp_lower_bound(sk, I.N, key);
     if (KNN) {
-      warp_knn(sk, a.sqc + (int64_t)c * a.N * a.D, a.sids + (int64_t)c * a.N, a.N, a.D, a.bp, qk, (int)len,
+      warp_knn(sk, I.sqc + (int64_t)c * I.N * a.D, I.sids + (int64_t)c * I.N, I.N, a.D, a.bp, qk, (int)len,
                cand + slot * len, knn_stack + warp * kKnnStack);
     } else {
       int64_t start = pos - a.W / 2;
       if (start > maxs) start = maxs;
       if (start < 0) start = 0;
-      const uint32_t* si = a.sids + (int64_t)c * a.N + start;
+      const uint32_t* si = I.sids + (int64_t)c * I.N + start;
       for (int64_t i = lane; i < len; i += 32) cand[slot * len + i] = si[i];
     }
     if (a.qkeys && lane == 0) {
@@ -553,8 +574,8 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
     }
   }
   // the L2 / L1 choice is uniform: one specialised loop each, no test per element
-  const float wmin = a.l1 ? rescore_all<MAXE, WEIGHTED, true>(a.dgrid, a.dict, ucand, ncand, ch, n, am, mt, eor, wv, c32)
-                          : rescore_all<MAXE, WEIGHTED, false>(a.dgrid, a.dict, ucand, ncand, ch, n, am, mt, eor, wv, c32);
+  const float wmin = a.l1 ? rescore_all<MAXE, WEIGHTED, true>(I.dgrid, I.dict, ucand, ncand, ch, n, am, mt, eor, wv, c32)
+                          : rescore_all<MAXE, WEIGHTED, false>(I.dgrid, I.dict, ucand, ncand, ch, n, am, mt, eor, wv, c32);
   if (lane == 0) s_redf[warp] = wmin;
   __syncthreads();
   float m32 = s_redf[0];
@@ -585,7 +606,7 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   for (int ci = tid; ci < ncand; ci += kQThreads) {
     if (c32[ci] <= T) {
       const uint32_t j = ucand[ci];
-      const double c64 = exact_cost64(a.dgrid, (int64_t)a.dict[j] * ch, tv, tm, deo, P, ch, a.weights, a.l1 != 0);
+      const double c64 = exact_cost64(I.dgrid, (int64_t)I.dict[j] * ch, tv, tm, deo, P, ch, a.weights, a.l1 != 0);
       if (c64 < bc || (c64 == bc && ci < bi)) {
         bc = c64;
         bi = ci;
@@ -617,24 +638,27 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   }
 }
 
-template <int MAXE, bool W, bool KNN>
+template <int MAXE, bool W, bool KNN, bool MULTI>
 int launch_q3(const QArgs& a, int64_t Q, size_t shm, cudaStream_t st) {
   if (shm > 48 * 1024)
-    SFC_TRY(cudaFuncSetAttribute(k_query<MAXE, W, KNN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    SFC_TRY(cudaFuncSetAttribute(k_query<MAXE, W, KNN, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)shm));
   count_launch();
-  k_query<MAXE, W, KNN><<<(unsigned)Q, kQThreads, shm, st>>>(a);
+  k_query<MAXE, W, KNN, MULTI><<<(unsigned)Q, kQThreads, shm, st>>>(a);
   SFC_TRY(cudaGetLastError());
   return SFC_OK;
 }
 
+// the multi-image launch runs the window search (no k-NN variant)
 template <int MAXE, bool W>
 int launch_q(const QArgs& a, int64_t Q, size_t shm, cudaStream_t st) {
-  return a.knn > 0 ? launch_q3<MAXE, W, true>(a, Q, shm, st) : launch_q3<MAXE, W, false>(a, Q, shm, st);
+  if (a.imgs) return launch_q3<MAXE, W, false, true>(a, Q, shm, st);
+  return a.knn > 0 ? launch_q3<MAXE, W, true, false>(a, Q, shm, st) : launch_q3<MAXE, W, false, false>(a, Q, shm, st);
 }
 
 template <bool W>
 int dispatch_q(const QArgs& a, int64_t Q, size_t shm, cudaStream_t st) {
-  const int need = (a.g.n + 31) / 32;
+  const int need = (a.img.g.n + 31) / 32;
   if (need <= 4) return launch_q<4, W>(a, Q, shm, st);
   if (need <= 8) return launch_q<8, W>(a, Q, shm, st);
   if (need <= 12) return launch_q<12, W>(a, Q, shm, st);
@@ -643,6 +667,78 @@ int dispatch_q(const QArgs& a, int64_t Q, size_t shm, cudaStream_t st) {
   if (need <= 32) return launch_q<32, W>(a, Q, shm, st);
   set_error("patch has more than 1024 values; not supported by the query kernel");
   return SFC_EUNSUPPORTED;
+}
+
+}  // namespace
+
+namespace {
+
+// The image descriptor of an index with its grid(s).
+QImg image_of(const Index& ix, const float* grid, const uint8_t* cur_mask, const TargetGrid* tgt) {
+  QImg I;
+  I.grid = grid;
+  I.dgrid = tgt ? tgt->dict_grid : grid;
+  I.deoff = ix.eoff_all;
+  I.mask = cur_mask;
+  I.g = tgt ? tgt->g : ix.g;
+  I.N = ix.N;
+  I.sqc = ix.sqc;
+  I.dict = ix.dict;
+  I.sub_pix = ix.sub_pix;
+  I.basis = ix.basis;
+  I.mean = ix.mean;
+  I.lo = ix.lo;
+  I.scale = ix.scale;
+  I.shifts = ix.shifts;
+  I.skeys = ix.skeys;
+  I.sids = ix.sids;
+  I.eoff_all = tgt ? tgt->eoff : ix.eoff_all;
+  return I;
+}
+
+// The fields shared by every query of a launch; maxN: the largest dictionary.
+int common_args(const Index& ix, int64_t maxN, QArgs& a) {
+  a.C = ix.C;
+  a.D = ix.D;
+  a.bits = ix.bits;
+  a.bp = ix.bp;
+  a.W = ix.W;
+  a.select = ix.select;
+  a.m = ix.m;
+  a.s = ix.s;
+  a.maxsel = ix.select == SFC_SELECT_BEST ? 1 : ix.C;
+  a.knn = ix.knn;
+  a.curve = ix.curve;
+  a.l1 = ix.l1 ? 1 : 0;
+  a.capw = ix.knn > 0 ? ix.knn : ix.W;
+  if (ix.knn > 0 && !ix.sqc) {
+    set_error("k-NN search without the index's quantised coordinates");
+    return SFC_EINVAL;
+  }
+  const int64_t wk = ix.knn > 0 ? ix.knn : ix.W;
+  const int64_t len = wk < maxN ? wk : maxN;
+  const int64_t need = len * a.maxsel;
+  int L = 2;
+  while (L < need) L <<= 1;
+  if (L > 8192) {
+    set_error("curves * window (or k) exceeds 8192 candidates per query");
+    return SFC_EINVAL;
+  }
+  a.L = L;
+  a.weights = ix.weights;
+  a.imgs = nullptr;
+  a.img_of = nullptr;
+  a.nimg = 0;
+  a.status = status_word();
+  return SFC_OK;
+}
+
+int launch_query(const Index& ix, const QArgs& a, int64_t Q, cudaStream_t st) {
+  const size_t shm = (size_t)ix.g.n * 12 + (size_t)a.L * 12 + (size_t)ix.g.P +
+                     (ix.knn > 0 ? 16 + sizeof(KnnRegion) * kKnnStack * kQWarps : 0);
+  bool weighted = false;
+  for (float w : ix.weights_h) weighted |= (w != 1.0f);
+  return weighted ? dispatch_q<true>(a, Q, shm, st) : dispatch_q<false>(a, Q, shm, st);
 }
 
 }  // namespace
@@ -656,64 +752,104 @@ int query_batch(const Index& ix, const float* grid, const uint8_t* cur_mask, con
     return SFC_EINVAL;
   }
   QArgs a;
-  a.grid = grid;
-  a.dgrid = tgt ? tgt->dict_grid : grid;
-  a.deoff = ix.eoff_all;
-  a.mask = cur_mask;
+  SFC_CHECK(common_args(ix, ix.N, a));
+  a.img = image_of(ix, grid, cur_mask, tgt);
   a.centres = centres;
-  a.g = tgt ? tgt->g : ix.g;
-  a.C = ix.C;
-  a.D = ix.D;
-  a.bits = ix.bits;
-  a.bp = ix.bp;
-  a.W = ix.W;
-  a.select = ix.select;
-  a.m = ix.m;
-  a.s = ix.s;
-  a.N = ix.N;
-  a.maxsel = ix.select == SFC_SELECT_BEST ? 1 : ix.C;
-  a.knn = ix.knn;
-  a.curve = ix.curve;
-  a.l1 = ix.l1 ? 1 : 0;
-  a.sqc = ix.sqc;
-  a.capw = ix.knn > 0 ? ix.knn : ix.W;
-  if (ix.knn > 0 && !ix.sqc) {
-    set_error("k-NN search without the index's quantised coordinates");
-    return SFC_EINVAL;
-  }
-  const int64_t wk = ix.knn > 0 ? ix.knn : ix.W;
-  int64_t len = wk < ix.N ? wk : ix.N;
-  int64_t need = len * a.maxsel;
-  int L = 2;
-  while (L < need) L <<= 1;
-  if (L > 8192) {
-    set_error("curves * window (or k) exceeds 8192 candidates per query");
-    return SFC_EINVAL;
-  }
-  a.L = L;
-  a.dict = ix.dict;
-  a.sub_pix = ix.sub_pix;
-  a.basis = ix.basis;
-  a.mean = ix.mean;
-  a.lo = ix.lo;
-  a.scale = ix.scale;
-  a.shifts = ix.shifts;
-  a.skeys = ix.skeys;
-  a.sids = ix.sids;
-  a.eoff_all = tgt ? tgt->eoff : ix.eoff_all;
-  a.weights = ix.weights;
   a.pick = pick;
   a.cost = cost;
   a.qkeys = qkeys;
   a.pos = pos;
   a.cand_out = cand;
   a.ncand_out = ncand;
-  a.status = status_word();
-  const size_t shm = (size_t)ix.g.n * 12 + (size_t)L * 12 + (size_t)ix.g.P +
-                     (ix.knn > 0 ? 16 + sizeof(KnnRegion) * kKnnStack * kQWarps : 0);
-  bool weighted = false;
-  for (float w : ix.weights_h) weighted |= (w != 1.0f);
-  return weighted ? dispatch_q<true>(a, Q, shm, st) : dispatch_q<false>(a, Q, shm, st);
+  return launch_query(ix, a, Q, st);
+}
+
+// Several images, one launch: every index built with the same parameters
+// (patch, curves, dimensions, bits, window / k, selection, curve, cost,
+// channel weights, subsets); query q belongs to image img_of[q].
+struct MultiQuery {
+  const Index* first = nullptr;  // the parameters (indices outlive the object)
+  QImg* imgs = nullptr;          // device, one per image
+  int64_t maxN = 0;
+  int n = 0;
+};
+
+int multi_query_create(const Index* const* ixs, const float* const* grids, const uint8_t* const* masks, int n,
+                       cudaStream_t st, MultiQuery** out) {
+  if (n < 1) {
+    set_error("sfc_multi_create: no images");
+    return SFC_EINVAL;
+  }
+  const Index& f = *ixs[0];
+  if (f.knn > 0) {
+    set_error("sfc_multi_create: the multi-image launch runs the window search (build with knn = 0)");
+    return SFC_EUNSUPPORTED;
+  }
+  std::vector<QImg> h(n);
+  int64_t maxN = 0;
+  for (int i = 0; i < n; ++i) {
+    const Index& x = *ixs[i];
+    const bool same = x.g.ndim == f.g.ndim && x.g.ch == f.g.ch && x.g.K == f.g.K && x.C == f.C && x.D == f.D &&
+                      x.bits == f.bits && x.bp == f.bp && x.W == f.W && x.select == f.select && x.m == f.m &&
+                      x.s == f.s && x.knn == f.knn && x.curve == f.curve && x.l1 == f.l1 &&
+                      x.weights_h == f.weights_h && x.subset_h == f.subset_h;
+    if (!same) {
+      set_error("sfc_multi_create: index " + std::to_string(i) + " was built with other parameters than index 0");
+      return SFC_EINVAL;
+    }
+    if (!grids[i] || !masks[i]) {
+      set_error("sfc_multi_create: NULL grid or mask");
+      return SFC_EINVAL;
+    }
+    h[i] = image_of(x, grids[i], masks[i], nullptr);
+    maxN = std::max(maxN, x.N);
+  }
+  auto* m = new MultiQuery();
+  m->first = &f;
+  m->n = n;
+  m->maxN = maxN;
+  if (pmalloc(&m->imgs, sizeof(QImg) * n, st) != cudaSuccess ||
+      cudaMemcpyAsync(m->imgs, h.data(), sizeof(QImg) * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    if (m->imgs) cudaFree(m->imgs);
+    delete m;
+    set_error("sfc_multi_create: out of device memory");
+    return SFC_ENOMEM;
+  }
+  *out = m;
+  return SFC_OK;
+}
+
+void multi_query_destroy(MultiQuery* m) {
+  if (!m) return;
+  cudaDeviceSynchronize();
+  if (m->imgs) cudaFreeAsync(m->imgs, nullptr);
+  cudaStreamSynchronize(nullptr);
+  delete m;
+}
+
+int multi_query_run(const MultiQuery* m, const int32_t* img_of, const int32_t* centres, int64_t Q, int64_t* pick,
+                    float* cost, cudaStream_t st) {
+  if (Q <= 0) return SFC_OK;
+  if (Q > 0x7fffffffLL) {
+    set_error("too many queries in one batch");
+    return SFC_EINVAL;
+  }
+  QArgs a;
+  SFC_CHECK(common_args(*m->first, m->maxN, a));
+  a.img = image_of(*m->first, nullptr, nullptr, nullptr);  // unused: every CTA reads imgs
+  a.imgs = m->imgs;
+  a.img_of = img_of;
+  a.nimg = m->n;
+  a.centres = centres;
+  a.pick = pick;
+  a.cost = cost;
+  a.qkeys = nullptr;
+  a.pos = nullptr;
+  a.cand_out = nullptr;
+  a.ncand_out = nullptr;
+  return launch_query(*m->first, a, Q, st);
 }
 
 }  // namespace sfc

@@ -17,6 +17,10 @@ struct sfc_index {
   int device;
 };
 
+struct sfc_multi {
+  sfc::MultiQuery* mq;
+};
+
 namespace sfc {
 
 namespace {
@@ -631,6 +635,51 @@ int sfc_index_export(const sfc_index* h, int64_t* dict, int32_t* subsets, float*
   if (keys) SFC_TRY(cudaMemcpy(keys, ix.keys, sizeof(uint64_t) * C * N, cudaMemcpyDeviceToHost));
   if (skeys) SFC_TRY(cudaMemcpy(skeys, ix.skeys, sizeof(uint64_t) * C * N, cudaMemcpyDeviceToHost));
   if (sids) SFC_TRY(cudaMemcpy(sids, ix.sids, sizeof(uint32_t) * C * N, cudaMemcpyDeviceToHost));
+  return SFC_OK;
+}
+
+int sfc_multi_create(const sfc_index* const* ix, const float* const* grids, const uint8_t* const* masks, int32_t n,
+                     void* stream, sfc_multi** out) {
+  g_err.clear();
+  if (!ix || !grids || !masks || !out || n < 1) {
+    set_error("sfc_multi_create: NULL argument or n < 1");
+    return SFC_EINVAL;
+  }
+  *out = nullptr;
+  SFC_CHECK(check_device());
+  std::vector<const Index*> v(n);
+  for (int i = 0; i < n; ++i) {
+    if (!ix[i]) {
+      set_error("sfc_multi_create: NULL index");
+      return SFC_EINVAL;
+    }
+    v[i] = &ix[i]->ix;
+  }
+  MultiQuery* mq = nullptr;
+  SFC_CHECK(multi_query_create(v.data(), grids, masks, n, (cudaStream_t)stream, &mq));
+  *out = new sfc_multi{mq};
+  return SFC_OK;
+}
+
+int sfc_multi_query(const sfc_multi* mu, const int32_t* image, const int32_t* centres, int64_t Q, int64_t* pick,
+                    float* cost, void* stream) {
+  g_err.clear();
+  if (!mu || Q < 0) {
+    set_error("sfc_multi_query: NULL object or negative Q");
+    return SFC_EINVAL;
+  }
+  if (Q == 0) return SFC_OK;
+  if (!image || !centres || !pick || !cost) {
+    set_error("sfc_multi_query: NULL pointer");
+    return SFC_EINVAL;
+  }
+  return multi_query_run(mu->mq, image, centres, Q, pick, cost, (cudaStream_t)stream);
+}
+
+int sfc_multi_destroy(sfc_multi* mu) {
+  if (!mu) return SFC_OK;
+  multi_query_destroy(mu->mq);
+  delete mu;
   return SFC_OK;
 }
 

@@ -27,7 +27,8 @@ SFC_COST_L2, SFC_COST_L1 = 0, 1
 EXPORTS = ["sfc_params_default", "sfc_index_build", "sfc_index_destroy", "sfc_index_info", "sfc_index_export",
            "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "fullscan_query_batch_static",
            "sfc_tc_prescores", "inpaint_run", "sfc_status", "sfc_launch_count", "sfc_trace", "sfc_trace_read", "sfc_trace_tc_read",
-           "sfc_last_error", "sfc_index_save", "sfc_index_load", "sfc_index_params", "sfc_query_batch_dict"]
+           "sfc_last_error", "sfc_index_save", "sfc_index_load", "sfc_index_params", "sfc_query_batch_dict",
+           "sfc_multi_create", "sfc_multi_query", "sfc_multi_destroy"]
 TRACE_PHASES = ("dictionary", "moments", "eigen", "finalize", "project_keys", "sort")
 
 
@@ -64,6 +65,9 @@ def lib():
         L.sfc_query_batch.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
         L.sfc_index_save.argtypes = [vp, C.c_char_p]
         L.sfc_index_params.argtypes = [vp, C.POINTER(sfc_params), C.POINTER(sfc_grid)]
+        L.sfc_multi_create.argtypes = [vp, vp, vp, C.c_int32, vp, C.POINTER(vp)]
+        L.sfc_multi_query.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+        L.sfc_multi_destroy.argtypes = [vp]
         L.sfc_index_load.argtypes = [C.c_char_p, vp, C.POINTER(vp)]
         L.sfc_query_batch_dict.argtypes = [vp, vp, vp, vp, C.POINTER(sfc_grid), vp, i64, vp, vp, vp]
         L.sfc_query_candidates.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp, vp]
@@ -87,7 +91,8 @@ def lib():
         for name in ["sfc_index_build", "sfc_index_destroy", "sfc_index_info", "sfc_index_export",
                      "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "fullscan_query_batch_static",
                      "sfc_tc_prescores", "inpaint_run", "sfc_status", "sfc_index_save", "sfc_index_load",
-                     "sfc_index_params", "sfc_query_batch_dict"]:
+                     "sfc_index_params", "sfc_query_batch_dict", "sfc_multi_create", "sfc_multi_query",
+                     "sfc_multi_destroy"]:
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -219,6 +224,44 @@ def sfc_query_batch_dict(ix: Index, dict_grid: torch.Tensor, grid: torch.Tensor,
     _check(lib().sfc_query_batch_dict(ix.h, _ptr(dict_grid), _ptr(grid), _ptr(cur_mask), C.byref(g), _ptr(centres),
                                       Q, _ptr(pick), _ptr(cost), _stream()), "sfc_query_batch_dict")
     return pick, cost
+
+
+class Multi:
+    """Several indices (same parameters) answered in one launch."""
+
+    def __init__(self, indices, grids, masks):
+        n = len(indices)
+        self._keep = [(_dev(gr, torch.float32), _dev(mk, torch.uint8)) for gr, mk in zip(grids, masks)]
+        self._indices = list(indices)
+        hs = (C.c_void_p * n)(*[ix.h for ix in indices])
+        gp = (C.c_void_p * n)(*[_ptr(gr) for gr, _ in self._keep])
+        mp = (C.c_void_p * n)(*[_ptr(mk) for _, mk in self._keep])
+        self.h = C.c_void_p()
+        _check(lib().sfc_multi_create(hs, gp, mp, n, _stream(), C.byref(self.h)), "sfc_multi_create")
+
+    def query(self, image: torch.Tensor, centres: torch.Tensor, pick=None, cost=None):
+        image = _dev(image, torch.int32)
+        centres = _dev(centres, torch.int32)
+        Q = centres.shape[0]
+        dev = centres.device
+        if pick is None:
+            pick = torch.empty(Q, dtype=torch.int64, device=dev)
+        if cost is None:
+            cost = torch.empty(Q, dtype=torch.float32, device=dev)
+        _check(lib().sfc_multi_query(self.h, _ptr(image), _ptr(centres), Q, _ptr(pick), _ptr(cost), _stream()),
+               "sfc_multi_query")
+        return pick, cost
+
+    def close(self):
+        if self.h:
+            lib().sfc_multi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sfc_index_export(ix: Index, proj: bool = False) -> dict:

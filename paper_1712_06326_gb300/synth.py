@@ -180,6 +180,24 @@ def spheres3d(size: int = 256, cfg: int = 3, fill: float = 0.30, block: int = 8,
 
 
 # ----------------------------------------------------------------------------
+# batched workload: many images of uneven size
+# ----------------------------------------------------------------------------
+def batch_sizes(count: int = 256, cfg: int = 4, lo: int = 256, hi: int = 2048, seed_sub: int = 0):
+    """(width, height) of ``count`` images, each side round(2^U(log2 lo, log2 hi))
+    independently (log-uniform); image i is voronoi2d(width, height, cfg,
+    seed_sub=1 + i) with its 10 % disc mask."""
+    rng = rng_for(cfg, seed_sub)
+    w = np.round(2.0 ** rng.uniform(math.log2(lo), math.log2(hi), count)).astype(int)
+    h = np.round(2.0 ** rng.uniform(math.log2(lo), math.log2(hi), count)).astype(int)
+    return [(int(a), int(b)) for a, b in zip(w, h)]
+
+
+def batch_image(i: int, size, cfg: int = 4):
+    """Image i of the batched workload (grid, mask)."""
+    return voronoi2d(size[0], size[1], cfg=cfg, seed_sub=1 + i)
+
+
+# ----------------------------------------------------------------------------
 # query centres: known pixels next to the hole (the targets a fill loop meets)
 # ----------------------------------------------------------------------------
 def front_targets(mask: np.ndarray, K: int, cap: int | None = None, cfg: int = 0, seed_sub: int = 7) -> np.ndarray:
