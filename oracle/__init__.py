@@ -74,7 +74,7 @@ def lib():
                 "or_query_knn": (None, [P, P, I32, P, I32, I32, I32, I32, I32, I32, I32, P, P, I32, P, P, P, P, P,
                                         P, I64, I64, P, P, P, P, I32]),
                 "or_inpaint": (I64, [P, P, I32, P, I32, I32, I32, I32, P, P, I64, I32, I32, I32, I32, I32, P,
-                                     I32, P, P, P, P, P, P, P, I64, P, I32]),
+                                     I32, P, P, P, P, P, P, P, I64, P, I32, I32, P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -385,9 +385,10 @@ def query_knn(ix, grid, cur_mask, target_lin, k, select=0, weights=None, norm=0)
     return dict(pick=int(pick[0]), cost=float(cost[0]), cand=cand[: int(nc[0])].copy())
 
 
-def inpaint(grid, mask, K, mode=0, prio=0, ix=None, W=64, select=0, weights=None, max_steps=0, norm=0):
+def inpaint(grid, mask, K, mode=0, prio=0, ix=None, W=64, select=0, weights=None, max_steps=0, norm=0, knn=0):
     """Fill loop (Sec. I, Fig. 1(a)); works on copies.  mode 0 = full scan,
-    1 = SFC (needs ``ix``).  -> (grid, mask, log int64 [steps, ndim+1], steps)."""
+    1 = SFC (needs ``ix``): windows of W, or with knn > 0 the exact k-NN lists
+    of Sec. II.D.  -> (grid, mask, log int64 [steps, ndim+1], steps)."""
     ndim, ext, ch = geometry(grid)
     g = np.array(grid, np.float32, copy=True)
     m = np.array(mask, np.uint8, copy=True)
@@ -402,7 +403,8 @@ def inpaint(grid, mask, K, mode=0, prio=0, ix=None, W=64, select=0, weights=None
         args = [ix["C"], ix["D"], ix["bits"], W, select, _p(ix["subset"]), ix["m"], _p(ix["basis"]),
                 _p(ix["mean"]), _p(ix["lo"]), _p(ix["scale"]), _p(ix["shifts"]), _p(ix["skeys"]), _p(ix["sids"])]
     steps = lib().or_inpaint(_p(g), _p(m), ndim, _p(ext), ch, K, mode, prio, _p(w), _p(_c(dct, np.int64)), len(dct),
-                             *args, int(max_steps), _p(log), int(norm))
+                             *args, int(max_steps), _p(log), int(norm), int(knn),
+                             _p(_c(ix["q"], np.uint32)) if (ix is not None and knn > 0) else None)
     if steps < 0:
         raise ValueError(f"oracle inpaint failed ({steps})")
     return g, m, log[:steps].copy(), int(steps)

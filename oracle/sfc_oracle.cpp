@@ -849,10 +849,11 @@ int64_t or_inpaint(float* grid, uint8_t* mask, int ndim, const int64_t* ext, int
                    const float* w, const int64_t* dict, int64_t N, int C, int D, int bits, int W, int select,
                    const int32_t* subset, int m, const float* basis, const float* mean32, const float* lo,
                    const float* scale, const int32_t* shift, const uint64_t* skeys, const uint32_t* sids,
-                   int64_t max_steps, int64_t* log, int norm) {
+                   int64_t max_steps, int64_t* log, int norm, int knn, const uint32_t* qc) {
   Geo g = make_geo(ndim, ext, ch, K);
   const int64_t npix = g.X * g.Y * g.Z;
   if (prio == 1 && ndim != 2) return -2;
+  if (mode == 1 && knn > 0 && !qc) return -3;
   std::vector<float> conf(npix);
   for (int64_t i = 0; i < npix; ++i) conf[i] = mask[i] ? 1.0f : 0.0f;
   auto known_at = [&](int64_t x, int64_t y, int64_t z) -> bool {
@@ -873,7 +874,7 @@ int64_t or_inpaint(float* grid, uint8_t* mask, int ndim, const int64_t* ext, int
   std::vector<uint8_t> is_centre(npix);
   std::vector<int64_t> cands;
   std::vector<uint64_t> qkeys(C > 0 ? C : 1);
-  std::vector<int64_t> pos(C > 0 ? C : 1), cand((size_t)(C > 0 ? C : 1) * (W > 0 ? W : 1));
+  std::vector<int64_t> pos(C > 0 ? C : 1), cand((size_t)(C > 0 ? C : 1) * std::max(W > 0 ? W : 1, knn > 0 ? knn : 1));
   while (max_steps <= 0 || steps < max_steps) {
     // front and candidate centres
     std::fill(is_centre.begin(), is_centre.end(), 0);
@@ -956,9 +957,13 @@ int64_t or_inpaint(float* grid, uint8_t* mask, int ndim, const int64_t* ext, int
       or_fullscan(grid, mask, ndim, ext, ch, K, dict, N, &bestc, 1, w, &j, &cst, norm);
     } else {
       int64_t nc;
-      or_query_curve(grid, mask, ndim, ext, ch, K, C, D, bits, W, select, w, subset, m, basis, mean32, lo, scale,
-                     shift, 0, skeys, sids, dict, N, bestc, qkeys.data(), pos.data(), cand.data(), &nc, &j, &cst,
-                     norm);
+      if (knn > 0)  // candidates = the exact k-NN lists of the query (Sec. II.D)
+        or_query_knn(grid, mask, ndim, ext, ch, K, C, D, bits, knn, select, w, subset, m, basis, mean32, lo, scale,
+                     qc, dict, N, bestc, cand.data(), &nc, &j, &cst, norm);
+      else
+        or_query_curve(grid, mask, ndim, ext, ch, K, C, D, bits, W, select, w, subset, m, basis, mean32, lo, scale,
+                       shift, 0, skeys, sids, dict, N, bestc, qkeys.data(), pos.data(), cand.data(), &nc, &j, &cst,
+                       norm);
     }
     int64_t src = dict[j];
     for (int pp = 0; pp < g.P; ++pp) {

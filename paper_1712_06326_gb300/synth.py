@@ -197,6 +197,13 @@ def batch_image(i: int, size, cfg: int = 4):
     return voronoi2d(size[0], size[1], cfg=cfg, seed_sub=1 + i)
 
 
+def batch_case(i: int, size, K: int, cap: int, cfg: int = 4):
+    """Image i of the batched workload with its queries: (grid, mask, front
+    targets capped at ``cap`` with sub-seed 100 + i)."""
+    g, m = batch_image(i, size, cfg)
+    return g, m, front_targets(m, K, cap=cap, cfg=cfg, seed_sub=100 + i)
+
+
 # ----------------------------------------------------------------------------
 # query centres: known pixels next to the hole (the targets a fill loop meets)
 # ----------------------------------------------------------------------------

@@ -122,3 +122,24 @@ def test_knn_deep_recursion_256(S):
     t = np.concatenate([synth.front_targets(m, 9, cap=24, cfg=2), synth.random_targets(m, 9, 8, cfg=2)])
     oix = run_case(S, g, m, t, 9, 8, 8, 16, 80)
     assert oix["N"] > 40_000
+
+
+@pytest.mark.parametrize("priority", [0, 1])
+def test_fill_with_the_papers_defaults_bit_identical(S, priority):
+    # the fill loop of Sec. I run with the settings of the paper's evaluation
+    # (Sec. III: K = 9, D = 10, k = 80 nearest per index, c = 0.6, byte
+    # coordinates) on the 128^2 grey image with its 24^2 hole: every step's
+    # (target, pick) and the filled image equal the oracle's
+    g, m = synth.sines2d(128)
+    K, C_, D, bits, k = 9, 8, 10, 8, 80
+    ix = S.sfc_index_build(dev(g), dev(m), K=K, curves=C_, dims=D, bits=bits, window=16, pca_sample=0, knn=k)
+    ex = S.sfc_index_export(ix)
+    ix.close()
+    oix = O.build_index(g, m, K, C_, D, bits, basis=ex["basis"], mean=ex["mean"])
+    og, om, olog, osteps = O.inpaint(g, m, K, mode=1, prio=priority, ix=oix, knn=k)
+    gd, md = dev(g), dev(m)
+    steps, log = S.inpaint_run(gd, md, mode=S.SFC_MODE_SFC, K=K, curves=C_, dims=D, bits=bits, window=16, knn=k,
+                               basis=ex["basis"], mean=ex["mean"], priority=priority)
+    assert steps == osteps and np.array_equal(log.cpu().numpy(), olog)
+    assert np.array_equal(gd.cpu().numpy(), og) and md.cpu().numpy().all()
+    assert S.sfc_status() == 0

@@ -39,17 +39,11 @@ def S():
     return sfc
 
 
-def _image(args):
-    i, size, cap = args
-    g, m = synth.batch_image(i, size)
-    t = synth.front_targets(m, K, cap=cap, cfg=4, seed_sub=100 + i)
-    return g, m, t
-
-
 def make_batch(sizes, cap):
     # a spawned pool (never forked after CUDA starts)
+    n = len(sizes)
     with cf.ProcessPoolExecutor(max_workers=16, mp_context=mp.get_context("spawn")) as ex:
-        return list(ex.map(_image, [(i, s, cap) for i, s in enumerate(sizes)]))
+        return list(ex.map(synth.batch_case, range(n), sizes, [K] * n, [cap] * n))
 
 
 def run_batch(S, imgs, prm):

@@ -739,6 +739,33 @@ def test_fill_sfc_mode_with_full_windows_equals_fullscan_mode():
     assert np.array_equal(a[2], b[2]) and np.array_equal(a[0], b[0])
 
 
+def test_fill_knn_lists_covering_dictionary_equal_fullscan_mode():
+    g, m = synth.voronoi2d(40, cfg=2, seed_sub=5)
+    ix = O.build_index(g, m, 5, 4, 4, 8, sample=0)
+    a = O.inpaint(g, m, 5, mode=0, max_steps=25)
+    b = O.inpaint(g, m, 5, mode=1, ix=ix, knn=ix["N"], max_steps=25)
+    assert np.array_equal(a[2], b[2]) and np.array_equal(a[0], b[0])
+
+
+def test_fill_knn_first_step_picks_from_the_nearest_lists():
+    # one step of the fill with k-NN lists (Sec. II.D): the pick is the exact
+    # argmin over the union of every curve's k nearest entries in quantised space
+    g, m = synth.voronoi2d(48, cfg=2, seed_sub=8)
+    K, k = 5, 7
+    ix = O.build_index(g, m, K, 4, 4, 8, sample=0)
+    _, _, log, steps = O.inpaint(g, m, K, mode=1, ix=ix, knn=k, max_steps=1)
+    assert steps == 1
+    tl = int(O.centres_to_lin(log[:1, :2], ix["ext"])[0])
+    want = set()
+    for cv in range(ix["C"]):
+        y = O.project_query(g, m, K, tl, ix["subset"][cv], ix["basis"][cv], ix["mean"][cv], ix["D"])
+        qq = O.quantise(y[None], ix["bits"], ix["lo"][cv], ix["scale"][cv])[0]
+        want |= set(_numpy_knn(ix["q"][cv], qq, k).tolist())
+    cand = sorted(want)
+    costs = [O.cost64(g, m, K, tl, ix["dict"][j]) for j in cand]
+    assert log[0, 2] == cand[int(np.argmin(costs))]
+
+
 def test_fill_criminisi_priority_runs():
     g, m = synth.voronoi2d(40, cfg=2, seed_sub=6)
     out, mo, log, steps = O.inpaint(g, m, 5, mode=0, prio=1)
