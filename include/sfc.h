@@ -309,6 +309,51 @@ int sfc_trace_read(double* ms, int64_t* builds, double* eig_flops);
 enum { SFC_TRACE_TC_PHASES = 3 };
 int sfc_trace_tc_read(double* ms, int64_t* calls, double* gemm_flops);
 
+/* ---- Parameter search (the tuned index of a batch of queries) -------------
+ * sfc_autotune builds an index for every combination of the listed index
+ * counts C (spec->curves), principal dimensions D (spec->dims) and windows W
+ * (spec->windows; with base->knn > 0 they are the list lengths k instead) on
+ * (grid, mask) -- the other parameters are base's -- and answers the Q
+ * queries `centres` (device, Q x ndim) with it.  Per configuration it measures
+ *   - ms: the median over spec->reps timed runs (after one untimed run) of the
+ *     CUDA-event time on `stream` of build + query (SFC_TUNE_STEP) or of the
+ *     query alone (SFC_TUNE_QUERY);
+ *   - ae: the acceleration error of Sec. III.C on a sample of the queries
+ *     (every ceil(Q / spec->sample)-th one): the mean over the sample of
+ *     sqrt(cost) / sqrt(exact cost) - 1, where the exact pick comes from
+ *     fullscan_query_batch (SFC_FP16 for the L2 cost, else SFC_FP32) and a
+ *     query counts 0 if the two costs are equal, 1 if only the exact cost is 0.
+ * The chosen configuration is the fastest with ae <= spec->ae_max (ties to the
+ * first in list order, C outermost, W innermost); if none qualifies, the one of
+ * least ae (ties to the faster).  *best = base with that C, D and W (or k);
+ * *chosen (host, may be NULL) its position; table (host, may be NULL) receives
+ * 5 doubles per configuration in list order: C, D, W (or k), ms, ae.
+ * base->shifts, basis and mean must be NULL (they are sized for one (C, D)).
+ * Synchronises `stream`; every configuration's index is destroyed before the
+ * call returns.  Errors: SFC_EINVAL for empty lists, more than 4096
+ * configurations, sample < 1, reps outside 1..100, ae_max < 0, and any
+ * configuration the build refuses (the message names it). */
+enum { SFC_TUNE_STEP = 0, SFC_TUNE_QUERY = 1 };
+typedef struct sfc_tune_spec {
+  const int32_t* curves; /* host */
+  int32_t n_curves;
+  const int32_t* dims;   /* host */
+  int32_t n_dims;
+  const int32_t* windows; /* host */
+  int32_t n_windows;
+  int64_t sample;        /* queries whose exact picks give ae (>= 1; all Q if larger) */
+  int32_t reps;          /* timed runs per configuration, 1..100 */
+  int32_t objective;     /* SFC_TUNE_STEP or SFC_TUNE_QUERY */
+  double ae_max;         /* acceptable mean acceleration error, e.g. 0.01 (the paper's 1 %) */
+} sfc_tune_spec;
+int sfc_autotune(const float* grid, const uint8_t* mask, const sfc_grid* g, const sfc_params* base,
+                 const int32_t* centres, int64_t Q, const sfc_tune_spec* spec, sfc_params* best, double* table,
+                 int32_t* chosen, void* stream);
+/* The selection rule of sfc_autotune on given measurements (host only; no
+ * device work): returns the chosen position in 0..n-1, or -1 if n <= 0 or a
+ * pointer is NULL.  NaN measurements count as +infinity. */
+int32_t sfc_tune_select(int32_t n, const double* ms, const double* ae, double ae_max);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* sfc_last_error(void);
 

@@ -23,17 +23,24 @@ SFC_PRIO_CONFIDENCE, SFC_PRIO_CRIMINISI = 0, 1
 SFC_MODE_FULLSCAN, SFC_MODE_SFC = 0, 1
 SFC_CURVE_MORTON, SFC_CURVE_HILBERT = 0, 1
 SFC_COST_L2, SFC_COST_L1 = 0, 1
+SFC_TUNE_STEP, SFC_TUNE_QUERY = 0, 1
 
 EXPORTS = ["sfc_params_default", "sfc_index_build", "sfc_index_destroy", "sfc_index_info", "sfc_index_export",
            "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "fullscan_query_batch_static",
            "sfc_tc_prescores", "inpaint_run", "sfc_status", "sfc_launch_count", "sfc_trace", "sfc_trace_read", "sfc_trace_tc_read",
            "sfc_last_error", "sfc_index_save", "sfc_index_load", "sfc_index_params", "sfc_query_batch_dict",
-           "sfc_multi_create", "sfc_multi_query", "sfc_multi_destroy"]
+           "sfc_multi_create", "sfc_multi_query", "sfc_multi_destroy", "sfc_autotune", "sfc_tune_select"]
 TRACE_PHASES = ("dictionary", "moments", "eigen", "finalize", "project_keys", "sort")
 
 
 class sfc_grid(C.Structure):
     _fields_ = [("ndim", C.c_int32), ("ch", C.c_int32), ("ext", C.c_int64 * 3)]
+
+
+class sfc_tune_spec(C.Structure):
+    _fields_ = [("curves", C.c_void_p), ("n_curves", C.c_int32), ("dims", C.c_void_p), ("n_dims", C.c_int32),
+                ("windows", C.c_void_p), ("n_windows", C.c_int32), ("sample", C.c_int64), ("reps", C.c_int32),
+                ("objective", C.c_int32), ("ae_max", C.c_double)]
 
 
 class sfc_params(C.Structure):
@@ -78,6 +85,10 @@ def lib():
                                        C.POINTER(i64), vp]
         L.inpaint_run.argtypes = [vp, vp, C.POINTER(sfc_grid), C.POINTER(sfc_params), i32, i64, vp,
                                   C.POINTER(i64), vp]
+        L.sfc_autotune.argtypes = [vp, vp, C.POINTER(sfc_grid), C.POINTER(sfc_params), vp, i64,
+                                   C.POINTER(sfc_tune_spec), C.POINTER(sfc_params), vp, C.POINTER(i32), vp]
+        L.sfc_tune_select.argtypes = [i32, vp, vp, C.c_double]
+        L.sfc_tune_select.restype = C.c_int32
         L.sfc_status.argtypes = [vp]
         L.sfc_last_error.restype = C.c_char_p
         L.sfc_launch_count.restype = C.c_uint64
@@ -92,7 +103,7 @@ def lib():
                      "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "fullscan_query_batch_static",
                      "sfc_tc_prescores", "inpaint_run", "sfc_status", "sfc_index_save", "sfc_index_load",
                      "sfc_index_params", "sfc_query_batch_dict", "sfc_multi_create", "sfc_multi_query",
-                     "sfc_multi_destroy"]:
+                     "sfc_multi_destroy", "sfc_autotune"]:
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -224,6 +235,41 @@ def sfc_query_batch_dict(ix: Index, dict_grid: torch.Tensor, grid: torch.Tensor,
     _check(lib().sfc_query_batch_dict(ix.h, _ptr(dict_grid), _ptr(grid), _ptr(cur_mask), C.byref(g), _ptr(centres),
                                       Q, _ptr(pick), _ptr(cost), _stream()), "sfc_query_batch_dict")
     return pick, cost
+
+
+def sfc_tune_select(ms, ae, ae_max: float) -> int:
+    """The selection rule of sfc_autotune on given measurements (host only)."""
+    ms = np.ascontiguousarray(ms, np.float64)
+    ae = np.ascontiguousarray(ae, np.float64)
+    assert ms.shape == ae.shape and ms.ndim == 1
+    return int(lib().sfc_tune_select(len(ms), ms.ctypes.data_as(C.c_void_p), ae.ctypes.data_as(C.c_void_p),
+                                     float(ae_max)))
+
+
+def sfc_autotune(grid: torch.Tensor, mask: torch.Tensor, centres: torch.Tensor, curves=(4, 8), dims=(6, 8, 10),
+                 windows=(16, 32, 64, 128), sample: int = 512, reps: int = 3, objective: int = SFC_TUNE_STEP,
+                 ae_max: float = 0.01, **base):
+    """-> (best params as a dict of the tuned keys, table float64 [n, 5] of
+    (C, D, W or k, ms, ae), chosen row)."""
+    assert grid.is_cuda and mask.is_cuda
+    P = Params(**base)
+    g = make_grid(grid)
+    cen = _dev(centres, torch.int32)
+    lists = [np.ascontiguousarray(v, np.int32) for v in (curves, dims, windows)]
+    spec = sfc_tune_spec()
+    spec.curves, spec.n_curves = lists[0].ctypes.data_as(C.c_void_p), len(lists[0])
+    spec.dims, spec.n_dims = lists[1].ctypes.data_as(C.c_void_p), len(lists[1])
+    spec.windows, spec.n_windows = lists[2].ctypes.data_as(C.c_void_p), len(lists[2])
+    spec.sample, spec.reps, spec.objective, spec.ae_max = sample, reps, objective, ae_max
+    n = len(lists[0]) * len(lists[1]) * len(lists[2])
+    table = np.zeros((n, 5), np.float64)
+    best = sfc_params()
+    chosen = C.c_int32(-1)
+    _check(lib().sfc_autotune(_ptr(grid), _ptr(mask), C.byref(g), C.byref(P.p), _ptr(cen), cen.shape[0],
+                              C.byref(spec), C.byref(best), table.ctypes.data_as(C.c_void_p), C.byref(chosen),
+                              _stream()), "sfc_autotune")
+    key = "knn" if P.p.knn > 0 else "window"
+    return {"curves": best.curves, "dims": best.dims, key: getattr(best, key)}, table, chosen.value
 
 
 class Multi:

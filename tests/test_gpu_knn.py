@@ -135,6 +135,9 @@ def test_fill_with_the_papers_defaults_bit_identical(S, priority):
     ix = S.sfc_index_build(dev(g), dev(m), K=K, curves=C_, dims=D, bits=bits, window=16, pca_sample=0, knn=k)
     ex = S.sfc_index_export(ix)
     ix.close()
+    # the image's noise leaves a flat tail of eigenvalues, so the tenth
+    # component may stop at the iteration cap (a warning, read and cleared here)
+    assert S.sfc_status() in (0, S.SFC_EDEVICE)
     oix = O.build_index(g, m, K, C_, D, bits, basis=ex["basis"], mean=ex["mean"])
     og, om, olog, osteps = O.inpaint(g, m, K, mode=1, prio=priority, ix=oix, knn=k)
     gd, md = dev(g), dev(m)
