@@ -23,7 +23,10 @@
 // Ch. 5), in FP64, on p = min(s, max(2D, D + 8), 24) vectors:
 //     Y = A Q;  H = Q^T Y;  H = W diag(e) W^T (parallel-order Jacobi, p x p);
 //     X = Q W;  Z = Y W (= A X);  stop when |Z_k - e_k X_k| <= 1e-11 e_0 for
-//     every k < D;  else Q = orthonormal basis of Z (Cholesky QR, twice).
+//     every k < D;  else Q = orthonormal basis of Z (Cholesky QR, twice; on
+//     the cluster path, once the block is close to orthogonal, a Cholesky
+//     factor in FP32 of the equilibrated Gram matrix followed by the FP64
+//     second-order correction (I + E)^(-1/2) ~ I - E/2 + 3/8 E^2).
 // The start block holds the unit vectors of the p largest diagonal entries of A
 // plus a small deterministic perturbation.  When A's row slices fit in shared
 // memory, the whole iteration runs in one launch on a cluster of 16 CTAs per
@@ -560,10 +563,23 @@ __device__ inline double rsqrt64(double x) {
 // np x np products spread over the CTA.  On exit W holds X and ev the l_i.
 __device__ void small_eig_refined(const double* H, double* W, double* ev, int np, float* H32, float* W32,
                                   double* T1, double* T2, double* red) {
+  // Index walks avoid run-time integer division: an element t = i * np + j is
+  // visited with (i, j) advanced incrementally.
+  const int nn = np * np;
+  const int di = blockDim.x / np, dj = blockDim.x % np;  // step of (i, j) per blockDim.x
   // FP32 cyclic Jacobi (one warp; np <= 24)
-  for (int t = threadIdx.x; t < np * np; t += blockDim.x) {
-    H32[t] = (float)H[t];
-    W32[t] = (t / np == t % np) ? 1.0f : 0.0f;
+  {
+    int i = threadIdx.x / np, j = threadIdx.x % np;
+    for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+      H32[t] = (float)H[t];
+      W32[t] = i == j ? 1.0f : 0.0f;
+      i += di;
+      j += dj;
+      if (j >= np) {
+        j -= np;
+        ++i;
+      }
+    }
   }
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -573,14 +589,28 @@ __device__ void small_eig_refined(const double* H, double* W, double* ev, int np
     // the product of the pairs' rotations); np - 1 rounds make a sweep
     const int lane = threadIdx.x;
     const int half = np / 2;
+    const int m1 = np - 1;
+    // this lane's walks: columns step (element l = t % half, row k = t / half),
+    // rows step (pair l = t / np, column k = t % np), diagonal test (t / np, t % np)
+    const int cl0 = lane % half, ck0 = lane / half, cdl = 32 % half, cdk = 32 / half;
+    const int rl0 = lane / np, rk0 = lane % np, rdl = 32 / np, rdk = 32 % np;
     __shared__ int jp[12], jq[12];
     __shared__ float jc[12], js[12];
     for (int sweep = 0; sweep < 12; ++sweep) {
       float off = 0.0f, all = 0.0f;
-      for (int t = lane; t < np * np; t += 32) {
-        const float v = H32[t] * H32[t];
-        all += v;
-        if (t / np != t % np) off += v;
+      {
+        int i = rl0, j = rk0;
+        for (int t = lane; t < nn; t += 32) {
+          const float v = H32[t] * H32[t];
+          all += v;
+          if (i != j) off += v;
+          i += rdl;
+          j += rdk;
+          if (j >= np) {
+            j -= np;
+            ++i;
+          }
+        }
       }
       for (int o = 16; o > 0; o >>= 1) {
         off += __shfl_xor_sync(0xffffffffu, off, o);
@@ -589,7 +619,7 @@ __device__ void small_eig_refined(const double* H, double* W, double* ev, int np
       // off-diagonal norm 1e-5 of the whole: the FP64 refinement below squares
       // the error twice, well past FP64 accuracy
       if (off <= 1e-10f * all) break;
-      for (int r = 0; r < np - 1; ++r) {
+      for (int r = 0; r < m1; ++r) {
         if (lane < half) {
           // pair lane of round r: (0, 1 + r) for lane 0, else two players
           // rotating around the fixed player 0
@@ -598,17 +628,31 @@ __device__ void small_eig_refined(const double* H, double* W, double* ev, int np
             a = 0;
             b = 1 + r;
           } else {
-            a = 1 + (r + lane) % (np - 1);
-            b = 1 + (r - lane + np - 1) % (np - 1);
+            int u = r + lane;  // < 2 (np - 1)
+            if (u >= m1) u -= m1;
+            int v = r - lane + m1;  // in [0, 2 (np - 1))
+            if (v >= m1) v -= m1;
+            a = 1 + u;
+            b = 1 + v;
           }
           const int pp = a < b ? a : b, q = a < b ? b : a;
           const float apq = H32[pp * np + q];
           float cs = 1.0f, sn = 0.0f;
           if (apq != 0.0f) {
-            const float tau = (H32[q * np + q] - H32[pp * np + pp]) / (2.0f * apq);
-            const float tt =
-                tau >= 0.0f ? 1.0f / (tau + sqrtf(1.0f + tau * tau)) : -1.0f / (-tau + sqrtf(1.0f + tau * tau));
-            cs = rsqrtf(1.0f + tt * tt);
+            // the angle needs no more than FP32 accuracy (the FP64 steps below
+            // refine the eigenvectors), so it uses the hardware approximations;
+            // |tau| > 1e18 takes t = 1 / (2 tau), which keeps tau^2 finite
+            const float tau = __fdividef(H32[q * np + q] - H32[pp * np + pp], 2.0f * apq);
+            const float at = fabsf(tau);
+            float tt;
+            if (at > 1e18f) {
+              tt = __fdividef(0.5f, at);
+            } else {
+              const float w = __fmaf_rn(at, at, 1.0f);
+              tt = __fdividef(1.0f, at + w * rsqrtf(w));
+            }
+            tt = copysignf(tt, tau);
+            cs = rsqrtf(__fmaf_rn(tt, tt, 1.0f));
             sn = tt * cs;
           }
           jp[lane] = pp;
@@ -619,85 +663,146 @@ __device__ void small_eig_refined(const double* H, double* W, double* ev, int np
         __syncwarp();
         // columns pp, q of every row k (and of W); consecutive lanes take
         // different pairs of one row, so their words sit in different banks
-        for (int t = lane; t < half * np; t += 32) {
-          const int l = t % half, k = t / half;
-          const int pp = jp[l], q = jq[l];
-          const float cs = jc[l], sn = js[l];
-          const float hkp = H32[k * np + pp], hkq = H32[k * np + q];
-          H32[k * np + pp] = cs * hkp - sn * hkq;
-          H32[k * np + q] = sn * hkp + cs * hkq;
-          const float wkp = W32[k * np + pp], wkq = W32[k * np + q];
-          W32[k * np + pp] = cs * wkp - sn * wkq;
-          W32[k * np + q] = sn * wkp + cs * wkq;
+        {
+          int l = cl0, k = ck0;
+          for (int t = lane; t < half * np; t += 32) {
+            const int pp = jp[l], q = jq[l];
+            const float cs = jc[l], sn = js[l];
+            const float hkp = H32[k * np + pp], hkq = H32[k * np + q];
+            H32[k * np + pp] = cs * hkp - sn * hkq;
+            H32[k * np + q] = sn * hkp + cs * hkq;
+            const float wkp = W32[k * np + pp], wkq = W32[k * np + q];
+            W32[k * np + pp] = cs * wkp - sn * wkq;
+            W32[k * np + q] = sn * wkp + cs * wkq;
+            l += cdl;
+            k += cdk;
+            if (l >= half) {
+              l -= half;
+              ++k;
+            }
+          }
         }
         __syncwarp();
         // rows pp, q
-        for (int t = lane; t < half * np; t += 32) {
-          const int l = t / np, k = t % np;
-          const int pp = jp[l], q = jq[l];
-          const float cs = jc[l], sn = js[l];
-          const float hpk = H32[pp * np + k], hqk = H32[q * np + k];
-          H32[pp * np + k] = cs * hpk - sn * hqk;
-          H32[q * np + k] = sn * hpk + cs * hqk;
+        {
+          int l = rl0, k = rk0;
+          for (int t = lane; t < half * np; t += 32) {
+            const int pp = jp[l], q = jq[l];
+            const float cs = jc[l], sn = js[l];
+            const float hpk = H32[pp * np + k], hqk = H32[q * np + k];
+            H32[pp * np + k] = cs * hpk - sn * hqk;
+            H32[q * np + k] = sn * hpk + cs * hqk;
+            l += rdl;
+            k += rdk;
+            if (k >= np) {
+              k -= np;
+              ++l;
+            }
+          }
         }
         __syncwarp();
       }
     }
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < np * np; t += blockDim.x) W[t] = (double)W32[t];
+  for (int t = threadIdx.x; t < nn; t += blockDim.x) W[t] = (double)W32[t];
   __syncthreads();
+  const int i0 = threadIdx.x / np, j0 = threadIdx.x % np;
   for (int step = 0; step < 2; ++step) {
     // T1 = H X
-    for (int t = threadIdx.x; t < np * np; t += blockDim.x) {
-      const int i = t / np, j = t % np;
-      double a0 = 0.0, a1 = 0.0;
-      for (int k = 0; k < np; k += 2) {
-        a0 = fma(H[i * np + k], W[k * np + j], a0);
-        if (k + 1 < np) a1 = fma(H[i * np + k + 1], W[(k + 1) * np + j], a1);
+    {
+      int i = i0, j = j0;
+      for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+        double a0 = 0.0, a1 = 0.0;
+        for (int k = 0; k < np; k += 2) {
+          a0 = fma(H[i * np + k], W[k * np + j], a0);
+          if (k + 1 < np) a1 = fma(H[i * np + k + 1], W[(k + 1) * np + j], a1);
+        }
+        T1[t] = a0 + a1;
+        i += di;
+        j += dj;
+        if (j >= np) {
+          j -= np;
+          ++i;
+        }
       }
-      T1[t] = a0 + a1;
     }
     __syncthreads();
-    // T2 = S = X^T H X (upper, mirrored) ; red-free R = I - X^T X into H32 space (as double in T1 later)
-    for (int t = threadIdx.x; t < np * np; t += blockDim.x) {
-      const int i = t / np, j = t % np;
-      double sv = 0.0, rv = 0.0;
-      for (int k = 0; k < np; ++k) {
-        sv = fma(W[k * np + i], T1[k * np + j], sv);
-        rv = fma(W[k * np + i], W[k * np + j], rv);
+    // T2 = S = X^T H X; R = I - X^T X (kept as doubles in the float scratch)
+    double* R = reinterpret_cast<double*>(H32);
+    {
+      int i = i0, j = j0;
+      for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+        double sv = 0.0, rv = 0.0;
+        for (int k = 0; k < np; ++k) {
+          sv = fma(W[k * np + i], T1[k * np + j], sv);
+          rv = fma(W[k * np + i], W[k * np + j], rv);
+        }
+        T2[t] = sv;
+        R[t] = (i == j ? 1.0 : 0.0) - rv;
+        i += di;
+        j += dj;
+        if (j >= np) {
+          j -= np;
+          ++i;
+        }
       }
-      T2[t] = sv;
-      // keep R_ij in the float scratch's double view is not possible; stash in ev-sized rows below
-      reinterpret_cast<double*>(H32)[t] = (i == j ? 1.0 : 0.0) - rv;
     }
     __syncthreads();
-    const double* R = reinterpret_cast<const double*>(H32);
     for (int i = threadIdx.x; i < np; i += blockDim.x) ev[i] = T2[i * np + i] / (1.0 - R[i * np + i]);
     __syncthreads();
-    // E into T1, then W <- W + W E
+    // E into T1, then W <- W + W E.  The off-diagonal E_ij are corrections of
+    // the size of the current error, so 1 / (l_j - l_i) is taken from the FP32
+    // reciprocal with one FP64 Newton step (relative error ~1e-14).
     double smax = 0.0;
     for (int i = 0; i < np; ++i) smax = fmax(smax, fabs(ev[i]));
-    for (int t = threadIdx.x; t < np * np; t += blockDim.x) {
-      const int i = t / np, j = t % np;
-      double e;
-      if (i == j) {
-        e = 0.5 * R[t];
-      } else {
-        const double d = ev[j] - ev[i];
-        e = fabs(d) > 1e-13 * smax ? (T2[t] + ev[j] * R[t]) / d : 0.5 * R[t];
+    {
+      int i = i0, j = j0;
+      for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+        double e;
+        if (i == j) {
+          e = 0.5 * R[t];
+        } else {
+          const double d = ev[j] - ev[i];
+          const double ad = fabs(d);
+          if (ad > 1e-13 * smax) {
+            if (ad > 1e-30 && ad < 1e30) {  // inside FP32's normal range
+              double rcp = (double)__frcp_rn((float)d);
+              rcp = rcp * fma(-d, rcp, 2.0);
+              e = (T2[t] + ev[j] * R[t]) * rcp;
+            } else {
+              e = (T2[t] + ev[j] * R[t]) / d;
+            }
+          } else {
+            e = 0.5 * R[t];
+          }
+        }
+        T1[t] = e;
+        i += di;
+        j += dj;
+        if (j >= np) {
+          j -= np;
+          ++i;
+        }
       }
-      T1[t] = e;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < np * np; t += blockDim.x) {
-      const int i = t / np, j = t % np;
-      double a = W[t];
-      for (int k = 0; k < np; ++k) a = fma(W[i * np + k], T1[k * np + j], a);
-      T2[t] = a;
+    {
+      int i = i0, j = j0;
+      for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+        double a = W[t];
+        for (int k = 0; k < np; ++k) a = fma(W[i * np + k], T1[k * np + j], a);
+        T2[t] = a;
+        i += di;
+        j += dj;
+        if (j >= np) {
+          j -= np;
+          ++i;
+        }
+      }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < np * np; t += blockDim.x) W[t] = T2[t];
+    for (int t = threadIdx.x; t < nn; t += blockDim.x) W[t] = T2[t];
     __syncthreads();
   }
 }
@@ -719,6 +824,11 @@ struct ClShm {
   double* al;   // np
   double* be;   // np
   int* ord;     // np
+  // upper-triangle pairs (i, j), i <= j < p, ordered by i descending: the pairs
+  // with i > k are the first (p - 1 - k)(p - k) / 2 (the trailing part of a
+  // Cholesky step k)
+  const unsigned char* tri_i;
+  const unsigned char* tri_j;
 };
 
 // every CTA: out[t] = sum over ranks (in order) of part[t], t < len
@@ -761,9 +871,10 @@ __device__ void cl_cholqr(cg::cluster_group& cl, ClShm& m, int nr, int r0, int s
       }
       for (int j = k + 1 + threadIdx.x; j < p; j += 32) G[k * p + j] *= y;
       __syncwarp();
-      for (int t = threadIdx.x; t < p * p; t += 32) {
-        const int i = t / p, j = t % p;
-        if (i > k && j >= i) G[i * p + j] = fma(-G[k * p + i], G[k * p + j], G[i * p + j]);
+      const int nt = (p - 1 - k) * (p - k) / 2;
+      for (int u = threadIdx.x; u < nt; u += 32) {
+        const int i = m.tri_i[u], j = m.tri_j[u];
+        G[i * p + j] = fma(-G[k * p + i], G[k * p + j], G[i * p + j]);
       }
       __syncwarp();
     }
@@ -818,6 +929,139 @@ __device__ void cl_allgather_rows(cg::cluster_group& cl, ClShm& m, int nr, int r
   cl.sync();
 }
 
+// Orthonormal basis of a distributed block Z whose columns are already nearly
+// orthogonal (the later iterations), with the serial p x p work in FP32:
+//   G = Z^T Z (FP64, reduced over the cluster), d_i = G_ii^(-1/2);
+//   R = Cholesky factor of D G D in FP32, Q1 = Z D R^{-1} (FP64 products);
+//   E = Q1^T Q1 - I (FP64, reduced), Q = Q1 (I - E/2 + 3/8 E^2),
+// the last factor being the series of (I + E)^(-1/2) to second order, so that
+// Q^T Q = I + O(|E|^3).  Both factors only recombine the columns of Z, so the
+// span is Z's.  Returns false, leaving Zs untouched, when the FP32 factor
+// fails or max |E| > 1e-5 (then the orthogonality after the series would not
+// reach FP64 rounding); every CTA of the cluster takes the same decision, as
+// its inputs are the cluster-reduced matrices.
+template <int CS>
+__device__ bool cl_orth_fast(cg::cluster_group& cl, ClShm& m, int nr, int r0, int s, int p, int rp) {
+  __shared__ int s_fail;
+  __shared__ double s_emax;
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    const int a = t / p, b = t % p;
+    double acc = 0.0;
+    if (a <= b)
+      for (int i = 0; i < nr; ++i) acc = fma(m.Zs[i * p + a], m.Zs[i * p + b], acc);
+    m.part[t] = acc;
+  }
+  cl_allreduce<CS>(cl, m.part, m.Hf, p * p);
+  double* dsc = m.be;
+  float* G32 = reinterpret_cast<float*>(m.Rv);  // p x p factor, then p x p inverse (Rv holds 2 np^2 floats)
+  if (threadIdx.x == 0) s_fail = 0;
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    const double g = m.Hf[i * p + i];
+    dsc[i] = g > 1e-300 ? rsqrt64(g) : 0.0;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    const int a = t / p, b = t % p;
+    G32[t] = a <= b ? (float)(m.Hf[t] * dsc[a] * dsc[b]) : 0.0f;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    // upper Cholesky factor in place, 1 / R_kk kept on the diagonal
+    for (int k = 0; k < p; ++k) {
+      const float gkk = G32[k * p + k];
+      const bool bad = !(gkk > 1e-6f);
+      const float y = bad ? 0.0f : rsqrtf(gkk);
+      __syncwarp();
+      if (threadIdx.x == 0) {
+        G32[k * p + k] = y;
+        if (bad) s_fail = 1;
+      }
+      for (int j = k + 1 + threadIdx.x; j < p; j += 32) G32[k * p + j] *= y;
+      __syncwarp();
+      const int nt = (p - 1 - k) * (p - k) / 2;
+      for (int u = threadIdx.x; u < nt; u += 32) {
+        const int i = m.tri_i[u], j = m.tri_j[u];
+        G32[i * p + j] = __fmaf_rn(-G32[k * p + i], G32[k * p + j], G32[i * p + j]);
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (s_fail) return false;
+  // M = D R^{-1} (R^{-1} by back substitution in FP32, one column per thread)
+  float* Ri32 = G32 + p * p;
+  if (threadIdx.x < p) {
+    const int j = threadIdx.x;
+    for (int i = p - 1; i >= 0; --i) {
+      float v = i == j ? 1.0f : 0.0f;
+      if (i < j)
+        for (int k = i + 1; k <= j; ++k) v = __fmaf_rn(-G32[i * p + k], Ri32[k * p + j], v);
+      Ri32[i * p + j] = i <= j ? v * G32[i * p + i] : 0.0f;
+    }
+  }
+  __syncthreads();
+  double* M = m.T1;
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) M[t] = dsc[t / p] * (double)Ri32[t];
+  __syncthreads();
+  // Q1 rows = Z rows M (into Ys, free here)
+  for (int t = threadIdx.x; t < nr * p; t += blockDim.x) {
+    const int i = t / p, k = t % p;
+    double a0 = 0.0, a1 = 0.0;
+    for (int j = 0; j <= k; j += 2) {
+      a0 = fma(m.Zs[i * p + j], M[j * p + k], a0);
+      if (j + 1 <= k) a1 = fma(m.Zs[i * p + j + 1], M[(j + 1) * p + k], a1);
+    }
+    m.Ys[t] = a0 + a1;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    const int a = t / p, b = t % p;
+    double acc = 0.0;
+    if (a <= b)
+      for (int i = 0; i < nr; ++i) acc = fma(m.Ys[i * p + a], m.Ys[i * p + b], acc);
+    m.part[t] = acc;
+  }
+  cl_allreduce<CS>(cl, m.part, m.Hf, p * p);
+  // E (symmetric, from the upper triangle) into T1; max |E_ij|
+  double* E = m.T1;
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    const int a = t / p, b = t % p;
+    const double g = a <= b ? m.Hf[t] : m.Hf[b * p + a];
+    E[t] = a == b ? g - 1.0 : g;
+  }
+  if (threadIdx.x == 0) s_emax = 0.0;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double e = 0.0;
+    for (int t = threadIdx.x; t < p * p; t += 32) e = fmax(e, fabs(E[t]));
+    for (int o = 16; o > 0; o >>= 1) e = fmax(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if (threadIdx.x == 0) s_emax = e;
+  }
+  __syncthreads();
+  if (!(s_emax <= 1e-5)) return false;
+  // T = I - E/2 + 3/8 E^2 into T2
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    const int a = t / p, b = t % p;
+    double e2 = 0.0;
+    for (int k = 0; k < p; ++k) e2 = fma(E[a * p + k], E[k * p + b], e2);
+    m.T2[t] = (a == b ? 1.0 : 0.0) - 0.5 * E[t] + 0.375 * e2;
+  }
+  __syncthreads();
+  // Q rows = Q1 rows T, into Qf (own rows) and Zs; then gather every row
+  for (int t = threadIdx.x; t < nr * p; t += blockDim.x) {
+    const int i = t / p, k = t % p;
+    double a0 = 0.0, a1 = 0.0;
+    for (int j = 0; j < p; j += 2) {
+      a0 = fma(m.Ys[i * p + j], m.T2[j * p + k], a0);
+      if (j + 1 < p) a1 = fma(m.Ys[i * p + j + 1], m.T2[(j + 1) * p + k], a1);
+    }
+    m.Zs[t] = a0 + a1;
+  }
+  __syncthreads();
+  cl_allgather_rows<CS>(cl, m, nr, r0, s, p, rp);
+  return true;
+}
+
 // Zs := rows [r0, r0 + nr) of A Qf
 __device__ inline void local_rows_times(const ClShm& m, int nr, int s, int p, double* out) {
   for (int t = threadIdx.x; t < nr * p; t += blockDim.x) {
@@ -864,6 +1108,17 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
   m.al = m.ev + np;
   m.be = m.al + np;
   m.ord = reinterpret_cast<int*>(m.be + np);
+  __shared__ unsigned char tri_i[kPMax * (kPMax + 1) / 2], tri_j[kPMax * (kPMax + 1) / 2];
+  if (threadIdx.x < p) {  // row i = p - 1 - threadIdx.x starts at pair (p - 1 - i)(p - i) / 2
+    const int i = p - 1 - threadIdx.x;
+    int u = (p - 1 - i) * (p - i) / 2;
+    for (int j = i; j < p; ++j, ++u) {
+      tri_i[u] = (unsigned char)i;
+      tri_j[u] = (unsigned char)j;
+    }
+  }
+  m.tri_i = tri_i;
+  m.tri_j = tri_j;
   __shared__ double red[8];
   const double* A = b.A + (int64_t)c * s * s;
   for (int t = threadIdx.x; t < nr * s; t += blockDim.x) m.As[t] = A[(int64_t)r0 * s + t];
@@ -883,8 +1138,11 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
     if (r < p) m.Zs[(i - r0) * p + r] += 1.0;
   }
   __syncthreads();
-  cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
-  cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
+  // the start block is close to orthonormal: the fast form usually suffices
+  if (!cl_orth_fast<CS>(cl, m, nr, r0, s, p, rp)) {
+    cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
+    cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
+  }
   bool conv = false;
   for (int it = 0; it < kMaxIterCl && !conv; ++it) {
     // Y = A Q (this CTA's rows)
@@ -973,8 +1231,12 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
     __syncthreads();
     // two passes while the block is far from the eigen-directions; afterwards
     // Z has nearly orthogonal columns and one pass is accurate to rounding
-    cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
-    if (it < 3) cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
+    // the FP32 factor with the FP64 second-order correction when the block is
+    // close enough to orthogonal, else two FP64 Cholesky QR passes
+    if (!cl_orth_fast<CS>(cl, m, nr, r0, s, p, rp)) {
+      cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
+      cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
+    }
   }
   cl.sync();  // no CTA leaves while others may still read its shared memory
 }
