@@ -27,6 +27,8 @@ namespace {
 
 constexpr int kQThreads = 256;
 constexpr int kQWarps = kQThreads / 32;
+// centred subset values staged per warp for the query projection
+constexpr int kXChunk = 64;
 
 // Everything that belongs to one image (or volume) and its index.
 struct QImg {
@@ -371,7 +373,8 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   uint32_t* ucand = cand + a.L;                            // L
   float* c32 = reinterpret_cast<float*>(ucand + a.L);      // L
   int* deo = reinterpret_cast<int*>(c32 + a.L);            // n (dictionary-grid offsets)
-  uint8_t* tm = reinterpret_cast<uint8_t*>(deo + n);       // P
+  float* xcb = reinterpret_cast<float*>(deo + n);          // kQWarps * kXChunk
+  uint8_t* tm = reinterpret_cast<uint8_t*>(xcb + kQWarps * kXChunk);  // P
   // k-NN region stacks, one per warp (k-NN mode only), rounded up to a 16-byte
   // boundary after tm (its offset 12 n + 12 L is only 4-aligned for odd n)
   KnnRegion* knn_stack = reinterpret_cast<KnnRegion*>(((uintptr_t)(tm + g.P) + 15) & ~(uintptr_t)15);
@@ -447,16 +450,40 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   // --- per index: project, key, search, window -------------------------------
   for (int slot = warp; slot < nsel; slot += kQWarps) {
     const int c = s_sel[slot];
+    // lane k < D runs the FMA chain of axis k over the subset values in order,
+    // known values only; the warp stages the centred values kXChunk at a time
+    // (with their known bits) so that the chain reads shared memory only
     float acc = 0.0f;
-    if (lane < a.D) {
+    {
       const float* B = I.basis + (int64_t)c * a.s * a.D;
       const float* mu = I.mean + (int64_t)c * a.s;
       const int32_t* sp = I.sub_pix + c * a.m;
-      for (int i = 0; i < a.s; ++i) {
-        int pp = sp[i / ch];
-        if (!tm[pp]) continue;
-        float xc = __fsub_rn(tv[pp * ch + i % ch], mu[i]);
-        acc = __fmaf_rn(B[(int64_t)i * a.D + lane], xc, acc);
+      float* xw = xcb + warp * kXChunk;
+      for (int i0 = 0; i0 < a.s; i0 += kXChunk) {
+        const int cnt = a.s - i0 < kXChunk ? a.s - i0 : kXChunk;
+        bool kn0 = false, kn1 = false;
+        if (lane < cnt) {
+          const int i = i0 + lane, pp = sp[i / ch];
+          kn0 = tm[pp] != 0;
+          xw[lane] = __fsub_rn(tv[pp * ch + i % ch], mu[i]);
+        }
+        if (lane + 32 < cnt) {
+          const int i = i0 + lane + 32, pp = sp[i / ch];
+          kn1 = tm[pp] != 0;
+          xw[lane + 32] = __fsub_rn(tv[pp * ch + i % ch], mu[i]);
+        }
+        const uint32_t m0 = __ballot_sync(0xffffffffu, kn0), m1 = __ballot_sync(0xffffffffu, kn1);
+        __syncwarp();
+        if (lane < a.D) {
+          const float* Bi = B + (int64_t)i0 * a.D + lane;
+#pragma unroll 4
+          for (int u = 0; u < cnt; ++u) {
+            const uint32_t mw = u < 32 ? m0 : m1;
+            const float r = __fmaf_rn(Bi[(int64_t)u * a.D], xw[u], acc);
+            acc = ((mw >> (u & 31)) & 1u) ? r : acc;
+          }
+        }
+        __syncwarp();
       }
     }
     uint32_t qk = 0;
@@ -734,7 +761,7 @@ int common_args(const Index& ix, int64_t maxN, QArgs& a) {
 }
 
 int launch_query(const Index& ix, const QArgs& a, int64_t Q, cudaStream_t st) {
-  const size_t shm = (size_t)ix.g.n * 12 + (size_t)a.L * 12 + (size_t)ix.g.P +
+  const size_t shm = (size_t)ix.g.n * 12 + (size_t)a.L * 12 + sizeof(float) * kQWarps * kXChunk + (size_t)ix.g.P +
                      (ix.knn > 0 ? 16 + sizeof(KnnRegion) * kKnnStack * kQWarps : 0);
   bool weighted = false;
   for (float w : ix.weights_h) weighted |= (w != 1.0f);
