@@ -32,6 +32,12 @@ void count_launch();
     if (r_ != SFC_OK) return r_;          \
   } while (0)
 
+// Dynamic shared memory above this size is opted into per kernel
+// (cudaFuncAttributeMaxDynamicSharedMemorySize): without the opt-in, static +
+// dynamic shared memory must stay within 48 KB, and the static part of the
+// library's kernels is below 8 KB.
+constexpr size_t kSmemOptIn = 40 * 1024;
+
 // Library-owned device status word of the current device (see ST_* bits).
 uint32_t* status_word();
 

@@ -510,7 +510,7 @@ int run_scan(const Geo& g, const float* grid, const uint8_t* cur_mask, const uin
              const int* eoff_all, const float* weights, const int64_t* lin, int64_t Q, float* tilemin,
              unsigned int* gmin, int64_t ntiles, cudaStream_t st) {
   const size_t shm = (size_t)g.n * QT * sizeof(float2) + (size_t)g.n * 8;
-  if (shm > 48 * 1024)
+  if (shm > kSmemOptIn)
     SFC_TRY(cudaFuncSetAttribute(k_fs_scan<QT, EPT, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   const int64_t qtiles = (Q + QT - 1) / QT;
   for (int64_t y0 = 0; y0 < qtiles; y0 += 65535) {
@@ -528,7 +528,7 @@ int run_band(const Geo& g, const float* grid, const uint8_t* cur_mask, const uin
              const int* eoff_all, const float* weights, const int64_t* lin, int64_t Q, const float* tilemin,
              const unsigned int* gmin, int64_t ntiles, int64_t* pick, float* cost, cudaStream_t st) {
   const size_t shm = (size_t)g.n * 20 + (size_t)g.P + 16;
-  if (shm > 48 * 1024)
+  if (shm > kSmemOptIn)
     SFC_TRY(cudaFuncSetAttribute(k_fs_band<EPT, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   count_launch();
   k_fs_band<EPT, W><<<(unsigned)Q, kFsThreads, shm, st>>>(grid, cur_mask, g, dict, N, eoff_all, weights, lin,
@@ -610,13 +610,13 @@ int fullscan_batch_tc(const Geo& g, const float* grid, const uint8_t* cur_mask, 
   SFC_CHECK(tc_prescore(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, nullptr, bound, st));
   const size_t shm = (size_t)g.n * 20 + (size_t)g.P + 16;
   if (weighted) {
-    if (shm > 48 * 1024)
+    if (shm > kSmemOptIn)
       SFC_TRY(cudaFuncSetAttribute(k_tc_select<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     count_launch();
     k_tc_select<true><<<(unsigned)Q, kFsThreads, shm, st>>>(grid, cur_mask, g, dict, N, eoff_all, weights, lin,
                                                              tilemin, nsub, bound, pick, cost, nsel);
   } else {
-    if (shm > 48 * 1024)
+    if (shm > kSmemOptIn)
       SFC_TRY(cudaFuncSetAttribute(k_tc_select<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     count_launch();
     k_tc_select<false><<<(unsigned)Q, kFsThreads, shm, st>>>(grid, cur_mask, g, dict, N, eoff_all, weights, lin,

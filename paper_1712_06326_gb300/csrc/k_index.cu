@@ -168,7 +168,7 @@ __global__ void k_sorted_coords(const float* __restrict__ proj, const uint32_t* 
 template <int D>
 int launch_project(const Index& ix, const float* grid, float* proj, uint32_t* lohi, cudaStream_t st) {
   const size_t shm = sizeof(float) * (ix.s * D + ix.s) + sizeof(int) * ix.s;
-  if (shm > 48 * 1024) SFC_TRY(cudaFuncSetAttribute(k_project<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  if (shm > kSmemOptIn) SFC_TRY(cudaFuncSetAttribute(k_project<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   dim3 grd((unsigned)((ix.N + 256 * kPE - 1) / (256 * kPE)), ix.C);
   count_launch();
   k_project<D><<<grd, 256, shm, st>>>(grid, ix.dict, ix.N, ix.g.ch, ix.s, ix.sub_eoff, ix.basis, ix.mean, proj, lohi);

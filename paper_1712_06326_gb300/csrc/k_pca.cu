@@ -1310,11 +1310,11 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
   const size_t shm_init = sizeof(double) * ((size_t)s * p + (size_t)p * p);
   const size_t shm_small = sizeof(double) * (2 * (size_t)s * p + 2 * (size_t)np * np + 3 * np) + sizeof(int) * np;
   const size_t shm_gemm = sizeof(double) * (size_t)s * p;
-  if (shm_init > 48 * 1024)
+  if (shm_init > kSmemOptIn)
     SFC_TRY(cudaFuncSetAttribute(k_si_init, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_init));
-  if (shm_small > 48 * 1024)
+  if (shm_small > kSmemOptIn)
     SFC_TRY(cudaFuncSetAttribute(k_si_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_small));
-  if (shm_gemm > 48 * 1024)
+  if (shm_gemm > kSmemOptIn)
     SFC_TRY(cudaFuncSetAttribute(k_si_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_gemm));
   // cluster path: 16 CTAs per curve when such clusters can be scheduled, else 8
   int cs = 0;

@@ -27,7 +27,8 @@ namespace {
 
 constexpr int kQThreads = 256;
 constexpr int kQWarps = kQThreads / 32;
-// centred subset values staged per warp for the query projection
+// centred subset values (and the basis rows) staged per warp for the query
+// projection, kXChunk subset values at a time
 constexpr int kXChunk = 64;
 
 // Everything that belongs to one image (or volume) and its index.
@@ -94,13 +95,18 @@ __device__ int64_t warp_lower_bound(const uint64_t* __restrict__ a, int64_t N, u
 // Morton key (top 64 bits; bit planes from the top, dimension 0 first) of the
 // coordinates held by lanes 0..D-1.
 __device__ uint64_t warp_key(uint32_t x, int D, int bp) {
+  // one ballot per bit plane gives the plane's bits with lane k at bit k; bit
+  // reversed and shifted, dimension 0 is the group's most significant bit
+  // (lanes >= D hold 0 and fall off the shift)
   uint64_t key = 0;
   int nb = 0;
-  for (int p = bp - 1; p >= 0 && nb < 64; --p)
-    for (int k = 0; k < D && nb < 64; ++k, ++nb) {
-      const uint32_t v = __shfl_sync(0xffffffffu, x, k);
-      key = (key << 1) | (uint64_t)((v >> p) & 1u);
-    }
+  for (int p = bp - 1; p >= 0 && nb < 64; --p) {
+    const uint32_t plane = __ballot_sync(0xffffffffu, (x >> p) & 1u);
+    const uint32_t grp = __brev(plane) >> (32 - D);
+    const int take = 64 - nb < D ? 64 - nb : D;
+    key = (key << take) | (uint64_t)(grp >> (D - take));
+    nb += take;
+  }
   return key;
 }
 
@@ -324,25 +330,41 @@ __device__ __forceinline__ float rescore_all(const float* __restrict__ dgrid, co
                                              const float (&wv)[MAXE], float* c32) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float wmin = INFINITY;
-  for (int ci = warp; ci < ncand; ci += kQWarps) {
+  // two candidates per pass (ci and ci + kQWarps): twice the gathers in flight;
+  // each candidate's sum keeps its order (element t per lane, then the warp sum)
+  for (int ci = warp; ci < ncand; ci += 2 * kQWarps) {
+    const int cj = ci + kQWarps;
+    const bool two = cj < ncand;
     const int64_t sb = (int64_t)dict[ucand[ci]] * ch;
-    float acc = 0.0f;
+    const int64_t sb2 = (int64_t)dict[ucand[two ? cj : ci]] * ch;
+    float acc = 0.0f, acc2 = 0.0f;
 #pragma unroll
     for (int t = 0; t < MAXE; ++t) {
       if (lane + 32 * t < n) {
-        float p = __ldg(dgrid + sb + eor[t]);
-        float d = __fmaf_rn(-am[t], p, mt[t]);
-        if (L1)
+        const float p = __ldg(dgrid + sb + eor[t]);
+        const float p2 = __ldg(dgrid + sb2 + eor[t]);
+        const float d = __fmaf_rn(-am[t], p, mt[t]);
+        const float d2 = __fmaf_rn(-am[t], p2, mt[t]);
+        if (L1) {
           acc = WEIGHTED ? __fmaf_rn(wv[t], fabsf(d), acc) : __fadd_rn(acc, fabsf(d));
-        else if (WEIGHTED)
+          acc2 = WEIGHTED ? __fmaf_rn(wv[t], fabsf(d2), acc2) : __fadd_rn(acc2, fabsf(d2));
+        } else if (WEIGHTED) {
           acc = __fmaf_rn(__fmul_rn(wv[t], d), d, acc);
-        else
+          acc2 = __fmaf_rn(__fmul_rn(wv[t], d2), d2, acc2);
+        } else {
           acc = __fmaf_rn(d, d, acc);
+          acc2 = __fmaf_rn(d2, d2, acc2);
+        }
       }
     }
     acc = warp_sum(acc);
-    if (lane == 0) c32[ci] = acc;
+    acc2 = warp_sum(acc2);
+    if (lane == 0) {
+      c32[ci] = acc;
+      if (two) c32[cj] = acc2;
+    }
     wmin = fminf(wmin, acc);
+    if (two) wmin = fminf(wmin, acc2);
   }
   return wmin;
 }
@@ -374,7 +396,8 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   float* c32 = reinterpret_cast<float*>(ucand + a.L);      // L
   int* deo = reinterpret_cast<int*>(c32 + a.L);            // n (dictionary-grid offsets)
   float* xcb = reinterpret_cast<float*>(deo + n);          // kQWarps * kXChunk
-  uint8_t* tm = reinterpret_cast<uint8_t*>(xcb + kQWarps * kXChunk);  // P
+  float* bcb = xcb + kQWarps * kXChunk;                    // kQWarps * kXChunk * D
+  uint8_t* tm = reinterpret_cast<uint8_t*>(bcb + kQWarps * kXChunk * a.D);  // P
   // k-NN region stacks, one per warp (k-NN mode only), rounded up to a 16-byte
   // boundary after tm (its offset 12 n + 12 L is only 4-aligned for odd n)
   KnnRegion* knn_stack = reinterpret_cast<KnnRegion*>(((uintptr_t)(tm + g.P) + 15) & ~(uintptr_t)15);
@@ -459,6 +482,7 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
       const float* mu = I.mean + (int64_t)c * a.s;
       const int32_t* sp = I.sub_pix + c * a.m;
       float* xw = xcb + warp * kXChunk;
+      float* bw = bcb + warp * kXChunk * a.D;
       for (int i0 = 0; i0 < a.s; i0 += kXChunk) {
         const int cnt = a.s - i0 < kXChunk ? a.s - i0 : kXChunk;
         bool kn0 = false, kn1 = false;
@@ -473,13 +497,14 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
           xw[lane + 32] = __fsub_rn(tv[pp * ch + i % ch], mu[i]);
         }
         const uint32_t m0 = __ballot_sync(0xffffffffu, kn0), m1 = __ballot_sync(0xffffffffu, kn1);
+        const float* Bc = B + (int64_t)i0 * a.D;
+        for (int u = lane; u < cnt * a.D; u += 32) bw[u] = Bc[u];
         __syncwarp();
         if (lane < a.D) {
-          const float* Bi = B + (int64_t)i0 * a.D + lane;
 #pragma unroll 4
           for (int u = 0; u < cnt; ++u) {
             const uint32_t mw = u < 32 ? m0 : m1;
-            const float r = __fmaf_rn(Bi[(int64_t)u * a.D], xw[u], acc);
+            const float r = __fmaf_rn(bw[u * a.D + lane], xw[u], acc);
             acc = ((mw >> (u & 31)) & 1u) ? r : acc;
           }
         }
@@ -667,7 +692,7 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
 
 template <int MAXE, bool W, bool KNN, bool MULTI>
 int launch_q3(const QArgs& a, int64_t Q, size_t shm, cudaStream_t st) {
-  if (shm > 48 * 1024)
+  if (shm > kSmemOptIn)
     SFC_TRY(cudaFuncSetAttribute(k_query<MAXE, W, KNN, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)shm));
   count_launch();
@@ -761,7 +786,8 @@ int common_args(const Index& ix, int64_t maxN, QArgs& a) {
 }
 
 int launch_query(const Index& ix, const QArgs& a, int64_t Q, cudaStream_t st) {
-  const size_t shm = (size_t)ix.g.n * 12 + (size_t)a.L * 12 + sizeof(float) * kQWarps * kXChunk + (size_t)ix.g.P +
+  const size_t shm = (size_t)ix.g.n * 12 + (size_t)a.L * 12 + sizeof(float) * kQWarps * kXChunk * (1 + ix.D) +
+                     (size_t)ix.g.P +
                      (ix.knn > 0 ? 16 + sizeof(KnnRegion) * kKnnStack * kQWarps : 0);
   bool weighted = false;
   for (float w : ix.weights_h) weighted |= (w != 1.0f);
