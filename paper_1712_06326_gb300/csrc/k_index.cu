@@ -54,13 +54,15 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ grid,
   // entries j0 + q * 256, q < kPE: for every subset value the warp's loads of one
   // q are 32 consecutive centres (coalesced), and one basis row serves kPE chains
   const int64_t j0 = (int64_t)blockIdx.x * blockDim.x * kPE + threadIdx.x;
-  int64_t base[kPE];
+  // one patch pointer per entry; entries past N read entry 0's patch (valid
+  // memory) and are not stored, so the loop needs no test per load
+  const float* gp[kPE];
   bool ok[kPE];
 #pragma unroll
   for (int q = 0; q < kPE; ++q) {
     const int64_t j = j0 + (int64_t)q * blockDim.x;
     ok[q] = j < N;
-    base[q] = ok[q] ? (int64_t)dict[j] * ch : 0;
+    gp[q] = grid + (int64_t)dict[ok[q] ? j : 0] * ch;
   }
   float acc[kPE][D];
 #pragma unroll
@@ -73,7 +75,7 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ grid,
     const float m = mu[i];
     float xc[kPE];
 #pragma unroll
-    for (int q = 0; q < kPE; ++q) xc[q] = __fsub_rn(ok[q] ? grid[base[q] + o] : 0.0f, m);
+    for (int q = 0; q < kPE; ++q) xc[q] = __fsub_rn(gp[q][o], m);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       const float b = B[i * D + k];

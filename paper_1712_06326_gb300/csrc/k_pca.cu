@@ -30,7 +30,11 @@
 // The start block holds the unit vectors of the p largest diagonal entries of A
 // plus a small deterministic perturbation.  When A's row slices fit in shared
 // memory, the whole iteration runs in one launch on a cluster of 16 CTAs per
-// curve (8 where 16-CTA clusters cannot be scheduled; see k_si_cluster); otherwise one launch per iteration
+// curve (8 where 16-CTA clusters cannot be scheduled; see k_si_cluster); there
+// the products are taken in FP32 (A and Q rounded, FP32 accumulation) until a
+// Rayleigh-Ritz residual reaches 1e-5 of e_0 -- the iteration is
+// self-correcting, so this only changes the start of the FP64 iterations, and
+// convergence is tested on FP64 products only; otherwise one launch per iteration
 // computes Y = A Q with every curve's rows spread over the GPU and a second (one
 // CTA per curve) does the p-sized work, a device-side flag ending the iteration
 // early.  A curve that has not converged within the iteration cap raises
@@ -543,6 +547,7 @@ __global__ void k_pca_finalize(SiBufs b, const double* __restrict__ mean, int s,
 // ----------------------------------------------------------------------------
 constexpr int kRR = 2;  // Rayleigh-Ritz every kRR iterations (of two products each)
 constexpr int kMaxIterCl = 64;
+constexpr int kLowpIters = 16;  // iterations with FP32 products at most
 
 // 1/sqrt(x) to FP64 accuracy from an FP32 seed: each Newton step
 // y (1.5 - x y^2 / 2) doubles the correct bits, 23 -> 46 -> 92 (FMAs only)
@@ -829,6 +834,8 @@ struct ClShm {
   // Cholesky step k)
   const unsigned char* tri_i;
   const unsigned char* tri_j;
+  float* As32;  // rp x s  (this CTA's rows of A rounded to FP32)
+  float* Qf32;  // s x p   (Qf rounded to FP32, for the FP32 products)
 };
 
 // every CTA: out[t] = sum over ranks (in order) of part[t], t < len
@@ -1062,6 +1069,28 @@ __device__ bool cl_orth_fast(cg::cluster_group& cl, ClShm& m, int nr, int r0, in
   return true;
 }
 
+// out := rows [r0, r0 + nr) of A Qf in FP32 (A and Q rounded to FP32, FP32
+// accumulation), widened to FP64: the early iterations only need the span
+// to move towards the eigenvectors, which this does at the FP32 pipe's rate
+__device__ inline void local_rows_times32(const ClShm& m, int nr, int s, int p, double* out) {
+  for (int t = threadIdx.x; t < s * p; t += blockDim.x) m.Qf32[t] = (float)m.Qf[t];
+  __syncthreads();
+  for (int t = threadIdx.x; t < nr * p; t += blockDim.x) {
+    const int i = t / p, k = t % p;
+    const float* ar = m.As32 + i * s;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    int j = 0;
+    for (; j + 3 < s; j += 4) {
+      a0 = __fmaf_rn(ar[j], m.Qf32[j * p + k], a0);
+      a1 = __fmaf_rn(ar[j + 1], m.Qf32[(j + 1) * p + k], a1);
+      a2 = __fmaf_rn(ar[j + 2], m.Qf32[(j + 2) * p + k], a2);
+      a3 = __fmaf_rn(ar[j + 3], m.Qf32[(j + 3) * p + k], a3);
+    }
+    for (; j < s; ++j) a0 = __fmaf_rn(ar[j], m.Qf32[j * p + k], a0);
+    out[t] = (double)((a0 + a1) + (a2 + a3));
+  }
+}
+
 // Zs := rows [r0, r0 + nr) of A Qf
 __device__ inline void local_rows_times(const ClShm& m, int nr, int s, int p, double* out) {
   for (int t = threadIdx.x; t < nr * p; t += blockDim.x) {
@@ -1081,7 +1110,7 @@ __device__ inline void local_rows_times(const ClShm& m, int nr, int s, int p, do
 }
 
 template <int CS>
-__global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int D) {
+__global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int D, int use32) {
   cg::cluster_group cl = cg::this_cluster();
   const int c = blockIdx.x / CS;
   const int me = (int)cl.block_rank();
@@ -1108,6 +1137,9 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
   m.al = m.ev + np;
   m.be = m.al + np;
   m.ord = reinterpret_cast<int*>(m.be + np);
+  // FP32 copies for the early products (only when shared memory allows)
+  m.As32 = use32 ? reinterpret_cast<float*>(((uintptr_t)(m.ord + np) + 15) & ~(uintptr_t)15) : nullptr;
+  m.Qf32 = use32 ? m.As32 + rp * s : nullptr;
   __shared__ unsigned char tri_i[kPMax * (kPMax + 1) / 2], tri_j[kPMax * (kPMax + 1) / 2];
   if (threadIdx.x < p) {  // row i = p - 1 - threadIdx.x starts at pair (p - 1 - i)(p - i) / 2
     const int i = p - 1 - threadIdx.x;
@@ -1121,7 +1153,11 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
   m.tri_j = tri_j;
   __shared__ double red[8];
   const double* A = b.A + (int64_t)c * s * s;
-  for (int t = threadIdx.x; t < nr * s; t += blockDim.x) m.As[t] = A[(int64_t)r0 * s + t];
+  for (int t = threadIdx.x; t < nr * s; t += blockDim.x) {
+    const double v = A[(int64_t)r0 * s + t];
+    m.As[t] = v;
+    if (use32) m.As32[t] = (float)v;
+  }
   // start block rows: unit vectors of the p largest diagonal entries + perturbation
   for (int t = threadIdx.x; t < nr * p; t += blockDim.x) {
     const int i = r0 + t / p, k = t % p;
@@ -1144,9 +1180,21 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
     cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
   }
   bool conv = false;
+  // products in FP32 until a Rayleigh-Ritz residual reaches 1e-5 of l_1 (or
+  // kLowpIters iterations have passed), in FP64 from then on; convergence is
+  // only accepted on FP64 products.  Every CTA of the cluster takes the same
+  // decisions (they depend on cluster-reduced values only).
+  bool lowp = use32 != 0;
+  int prod64 = 0;
   for (int it = 0; it < kMaxIterCl && !conv; ++it) {
     // Y = A Q (this CTA's rows)
-    local_rows_times(m, nr, s, p, m.Ys);
+    const bool lp1 = lowp;
+    if (lp1) {
+      local_rows_times32(m, nr, s, p, m.Ys);
+    } else {
+      local_rows_times(m, nr, s, p, m.Ys);
+      ++prod64;
+    }
     __syncthreads();
     const bool rr = (it % kRR) == kRR - 1 || it == kMaxIterCl - 1;
     if (rr) {
@@ -1209,12 +1257,13 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
       cl_allreduce<CS>(cl, m.part, m.Hf, D);
       double worst = 0.0;
       for (int k = 0; k < D; ++k) worst = fmax(worst, m.Hf[k]);
-      conv = worst <= 1e-22 * m.ev[0] * m.ev[0];
+      conv = !lp1 && worst <= 1e-22 * m.ev[0] * m.ev[0];
+      if (lowp && (worst <= 1e-10 * m.ev[0] * m.ev[0] || it >= kLowpIters)) lowp = false;
       if (conv || it == kMaxIterCl - 1) {
         if (me == 0 && threadIdx.x < p) b.e[(int64_t)c * p + threadIdx.x] = m.ev[threadIdx.x];
         if (me == 0 && threadIdx.x == 0) {
           b.done[c] = conv ? 1 : 0;
-          b.iters[c] = 2 * it + 1;  // products with A (the last iteration stops after its first)
+          b.iters[c] = prod64;  // FP64 products with A
         }
         break;
       }
@@ -1227,7 +1276,12 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
     // the block's condition stays near (l_1 / l_p)^2, inside CholeskyQR2's reach
     __syncthreads();
     cl_allgather_rows<CS>(cl, m, nr, r0, s, p, rp);
-    local_rows_times(m, nr, s, p, m.Zs);
+    if (lowp) {
+      local_rows_times32(m, nr, s, p, m.Zs);
+    } else {
+      local_rows_times(m, nr, s, p, m.Zs);
+      ++prod64;
+    }
     __syncthreads();
     // two passes while the block is far from the eigen-directions; afterwards
     // Z has nearly orthogonal columns and one pass is accurate to rounding
@@ -1241,13 +1295,14 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
   cl.sync();  // no CTA leaves while others may still read its shared memory
 }
 
-size_t cluster_shm_bytes(int s, int p, int CS) {
+size_t cluster_shm_bytes(int s, int p, int CS, bool use32) {
   const int rp = (s + CS - 1) / CS;
   const int np = p + (p & 1);
   // As, Qf, Ys, Zs, Xs, part, Hf, Wf, T1, T2, Rv (doubles); W32 (floats) + pad;
-  // ev, al, be (doubles); ord (ints)
+  // ev, al, be (doubles); ord (ints); 16-byte alignment; As32, Qf32 (floats)
   return sizeof(double) * ((size_t)rp * s + (size_t)s * p + 3 * (size_t)rp * p + 6 * (size_t)np * np + 3 * np) +
-         sizeof(float) * ((size_t)np * np + 2) + sizeof(int) * np;
+         sizeof(float) * ((size_t)np * np + 2) + sizeof(int) * np +
+         (use32 ? 16 + sizeof(float) * ((size_t)rp * s + (size_t)s * p) : 0);
 }
 
 }  // namespace
@@ -1317,10 +1372,13 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
   if (shm_gemm > kSmemOptIn)
     SFC_TRY(cudaFuncSetAttribute(k_si_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_gemm));
   // cluster path: 16 CTAs per curve when such clusters can be scheduled, else 8
-  int cs = 0;
+  int cs = 0, use32 = 0;
   size_t shm_cl = 0;
-  for (int cand : {16, 8}) {
-    const size_t need = cluster_shm_bytes(s, p, cand);
+  for (int opt = 0; opt < 4 && cs == 0; ++opt) {
+    // preference: 16-CTA clusters with the FP32 copies, without them, then 8
+    const int cand = opt < 2 ? 16 : 8;
+    const bool w32 = (opt & 1) == 0;
+    const size_t need = cluster_shm_bytes(s, p, cand, w32);
     if (need > 200 * 1024) continue;
     const void* fn = cand == 16 ? (const void*)k_si_cluster<16> : (const void*)k_si_cluster<8>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need) != cudaSuccess) continue;
@@ -1345,8 +1403,8 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
       continue;
     }
     cs = cand;
+    use32 = w32 ? 1 : 0;
     shm_cl = need;
-    break;
   }
   if (cs) {
     cudaLaunchConfig_t cfg = {};
@@ -1364,9 +1422,9 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
     ix.eig_per_orth = 2;
     count_launch();
     if (cs == 16)
-      SFC_TRY(cudaLaunchKernelEx(&cfg, k_si_cluster<16>, b, s, p, D));
+      SFC_TRY(cudaLaunchKernelEx(&cfg, k_si_cluster<16>, b, s, p, D, use32));
     else
-      SFC_TRY(cudaLaunchKernelEx(&cfg, k_si_cluster<8>, b, s, p, D));
+      SFC_TRY(cudaLaunchKernelEx(&cfg, k_si_cluster<8>, b, s, p, D, use32));
   } else {
     count_launch();
     k_si_init<<<C, 256, shm_init, st>>>(b, s, p);

@@ -60,7 +60,7 @@ __global__ void k_hist_scan(uint32_t* __restrict__ hist) {
 
 // One onesweep pass over every index's keys.  in_vals == nullptr: the values are
 // the ids (first pass).
-__global__ void __launch_bounds__(kThreads) k_onesweep(const uint64_t* __restrict__ in_keys,
+__global__ void __launch_bounds__(kThreads, 3) k_onesweep(const uint64_t* __restrict__ in_keys,
                                                        const uint32_t* __restrict__ in_vals,
                                                        uint64_t* __restrict__ out_keys,
                                                        uint32_t* __restrict__ out_vals, int64_t N, int shift,
@@ -85,27 +85,30 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(const uint64_t* __restric
   const uint64_t* ik = in_keys + (int64_t)c * N;
   const uint32_t* iv = in_vals ? in_vals + (int64_t)c * N : nullptr;
 
+  // digits are recomputed from the keys where needed (fewer registers, so
+  // three CTAs fit an SM); items past N get the singleton group 256 + lane
   uint64_t key[kItems];
   uint32_t val[kItems];
   uint32_t rnk[kItems];
-  int dig[kItems];
+  const int64_t nvalid = N - base;  // items k * 32 + lane < nvalid are valid
+#define DIG(k) (((int64_t)(k) * 32 + lane < nvalid) ? (int)((key[k] >> shift) & 255u) : 256 + lane)
 #pragma unroll
   for (int k = 0; k < kItems; ++k) {
     int64_t idx = base + k * 32 + lane;
     bool ok = idx < N;
     key[k] = ok ? ik[idx] : 0ull;
     val[k] = ok ? (iv ? iv[idx] : (uint32_t)idx) : 0u;
-    dig[k] = ok ? (int)((key[k] >> shift) & 255u) : 256 + lane;  // invalid: singleton groups, not counted
   }
   // stable rank inside the warp, items in order, lanes in order
 #pragma unroll
   for (int k = 0; k < kItems; ++k) {
-    unsigned peers = __match_any_sync(0xffffffffu, dig[k]);
+    const int dg = DIG(k);
+    unsigned peers = __match_any_sync(0xffffffffu, dg);
     unsigned before = peers & ((1u << lane) - 1u);
-    uint32_t b = dig[k] < 256 ? whist[warp][dig[k]] : 0u;
+    uint32_t b = dg < 256 ? whist[warp][dg] : 0u;
     rnk[k] = b + __popc(before);
     __syncwarp();
-    if (dig[k] < 256 && before == 0) whist[warp][dig[k]] = b + __popc(peers);
+    if (dg < 256 && before == 0) whist[warp][dg] = b + __popc(peers);
     __syncwarp();
   }
   __syncthreads();
@@ -173,12 +176,14 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(const uint64_t* __restric
   // place into shared memory in tile-sorted order
 #pragma unroll
   for (int k = 0; k < kItems; ++k) {
-    if (dig[k] < 256) {
-      uint32_t pos = tstart[dig[k]] + whist[warp][dig[k]] + rnk[k];
+    const int dg = DIG(k);
+    if (dg < 256) {
+      uint32_t pos = tstart[dg] + whist[warp][dg] + rnk[k];
       skey[pos] = key[k];
       sval[pos] = val[k];
     }
   }
+#undef DIG
   __syncthreads();
   int64_t valid = N - tile * kTileKeys;
   if (valid > kTileKeys) valid = kTileKeys;
