@@ -130,6 +130,23 @@ __device__ inline uint64_t morton_key(const uint32_t* q, int D, int bp) {
   return key;
 }
 
+// morton_key with D known at compile time (q stays in registers): each bit
+// plane's D bits form a group, dimension 0 its most significant bit.
+template <int D>
+__device__ inline uint64_t morton_key_t(const uint32_t* q, int bp) {
+  uint64_t key = 0;
+  int n = 0;
+  for (int p = bp - 1; p >= 0 && n < 64; --p) {
+    uint32_t grp = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) grp = (grp << 1) | ((q[k] >> p) & 1u);
+    const int take = 64 - n < D ? 64 - n : D;
+    key = (key << take) | (uint64_t)(grp >> (D - take));
+    n += take;
+  }
+  return key;
+}
+
 // Hilbert key (Skilling 2004, transpose method): the coordinates q[0..D) of bp
 // bits are rewritten into the transposed Hilbert index -- from the top bit
 // plane down, coordinate 0's bits below the plane are inverted where
@@ -157,6 +174,33 @@ __device__ inline uint64_t hilbert_key(uint32_t* q, int D, int bp) {
     if (q[D - 1] & plane) mask ^= plane - 1;
   for (int i = 0; i < D; ++i) q[i] ^= mask;
   return morton_key(q, D, bp);
+}
+
+// hilbert_key with D known at compile time (the same steps)
+template <int D>
+__device__ inline uint64_t hilbert_key_t(uint32_t* q, int bp) {
+  const uint32_t top = 1u << (bp - 1);
+  for (uint32_t plane = top; plane > 1; plane >>= 1) {
+    const uint32_t low = plane - 1;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      if (q[i] & plane) {
+        q[0] ^= low;
+      } else {
+        const uint32_t t = (q[0] ^ q[i]) & low;
+        q[0] ^= t;
+        q[i] ^= t;
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 1; i < D; ++i) q[i] ^= q[i - 1];
+  uint32_t mask = 0;
+  for (uint32_t plane = top; plane > 1; plane >>= 1)
+    if (q[D - 1] & plane) mask ^= plane - 1;
+#pragma unroll
+  for (int i = 0; i < D; ++i) q[i] ^= mask;
+  return morton_key_t<D>(q, bp);
 }
 
 }  // namespace sfc

@@ -140,17 +140,19 @@ __global__ void k_scale(const uint32_t* __restrict__ lohi, int n, int bits, floa
 
 namespace {
 
-__global__ void k_keys(const float* __restrict__ proj, int64_t N, int D, int bits, int bp, int curve,
+template <int D>
+__global__ void k_keys(const float* __restrict__ proj, int64_t N, int bits, int bp, int curve,
                        const float* __restrict__ lo, const float* __restrict__ scale,
                        const int32_t* __restrict__ shifts, uint64_t* __restrict__ keys) {
   const int c = blockIdx.y;
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= N) return;
-  uint32_t q[16];
+  uint32_t q[D];
   const float* y = proj + ((int64_t)c * N + j) * D;
+#pragma unroll
   for (int k = 0; k < D; ++k)
     q[k] = quantise_one(y[k], lo[c * D + k], scale[c * D + k], bits) + (uint32_t)shifts[c * D + k];
-  keys[(int64_t)c * N + j] = curve == SFC_CURVE_HILBERT ? hilbert_key(q, D, bp) : morton_key(q, D, bp);
+  keys[(int64_t)c * N + j] = curve == SFC_CURVE_HILBERT ? hilbert_key_t<D>(q, bp) : morton_key_t<D>(q, bp);
 }
 
 // sqc[c][i][k] = quantised shifted coordinate k of the entry at sorted slot i of index c
@@ -178,6 +180,15 @@ int launch_project(const Index& ix, const float* grid, float* proj, uint32_t* lo
   return SFC_OK;
 }
 
+template <int D>
+int launch_keys(const Index& ix, const float* proj, uint64_t* keys, cudaStream_t st) {
+  dim3 grd((unsigned)((ix.N + 255) / 256), ix.C);
+  count_launch();
+  k_keys<D><<<grd, 256, 0, st>>>(proj, ix.N, ix.bits, ix.bp, ix.curve, ix.lo, ix.scale, ix.shifts, keys);
+  SFC_TRY(cudaGetLastError());
+  return SFC_OK;
+}
+
 }  // namespace
 
 int project_and_key(Index& ix, const float* grid, cudaStream_t st, float* proj, uint64_t* keys) {
@@ -198,10 +209,14 @@ int project_and_key(Index& ix, const float* grid, cudaStream_t st, float* proj, 
   SFC_CHECK(rc);
   count_launch();
   k_scale<<<(n + 127) / 128, 128, 0, st>>>(lohi, n, ix.bits, ix.lo, ix.scale);
-  dim3 grd((unsigned)((ix.N + 255) / 256), ix.C);
-  count_launch();
-  k_keys<<<grd, 256, 0, st>>>(proj, ix.N, ix.D, ix.bits, ix.bp, ix.curve, ix.lo, ix.scale, ix.shifts, keys);
-  SFC_TRY(cudaGetLastError());
+  switch (ix.D) {
+#define SFC_D(d) \
+  case d: rc = launch_keys<d>(ix, proj, keys, st); break;
+    SFC_D(1) SFC_D(2) SFC_D(3) SFC_D(4) SFC_D(5) SFC_D(6) SFC_D(7) SFC_D(8)
+    SFC_D(9) SFC_D(10) SFC_D(11) SFC_D(12) SFC_D(13) SFC_D(14) SFC_D(15) SFC_D(16)
+#undef SFC_D
+  }
+  SFC_CHECK(rc);
   cudaFreeAsync(lohi, st);
   return SFC_OK;
 }
