@@ -4,7 +4,8 @@
 // Projection: y_k = chain of FP32 fused multiply-adds over the index's subset
 // values in subset order, acc = fma(B[i][k], x_i - mu_i, acc) starting at +0 with
 // x_i - mu_i rounded to FP32 (a thread runs the D chains of 4 entries of one
-// index, interleaved).  The per-axis minimum and maximum over the dictionary are
+// index, interleaved, two axes per fma.rn.f32x2: the same IEEE operation on
+// each half).  The per-axis minimum and maximum over the dictionary are
 // exact reductions (order-independent).  Quantisation: q = clamp(floor((y - lo)
 // * scale), 0, 2^b - 1) with scale = (float)(2^b / ((double)hi - (double)lo)) (0
 // if hi == lo), then q + shift.  Key: bits interleaved highest plane first,
@@ -30,17 +31,40 @@ __device__ inline float float_of(uint32_t u) {
 
 constexpr int kPE = 4;  // dictionary entries per thread (they share the basis reads)
 
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// dims paired: acc2[q][h] holds the chains of axes 2h, 2h + 1 of entry q; the
+// basis row pair (B[i][2h], B[i][2h+1]) is read as one 64-bit word and the
+// centred value is duplicated into both halves (the same IEEE FMA per half)
 template <int D>
 __global__ void __launch_bounds__(256) k_project(const float* __restrict__ grid, const uint32_t* __restrict__ dict,
                                                  int64_t N, int ch, int s, const int* __restrict__ sub_eoff,
                                                  const float* __restrict__ basis, const float* __restrict__ mean,
                                                  float* __restrict__ proj, uint32_t* __restrict__ lohi) {
+  constexpr int DP = (D + 1) / 2;
   const int c = blockIdx.y;
   extern __shared__ unsigned char smem_raw[];
-  float* B = reinterpret_cast<float*>(smem_raw);  // s*D
-  float* mu = B + s * D;                          // s
-  int* eo = reinterpret_cast<int*>(mu + s);       // s
-  for (int t = threadIdx.x; t < s * D; t += blockDim.x) B[t] = basis[(int64_t)c * s * D + t];
+  unsigned long long* B2 = reinterpret_cast<unsigned long long*>(smem_raw);  // s * DP pairs
+  float* mu = reinterpret_cast<float*>(B2 + s * DP);                         // s
+  int* eo = reinterpret_cast<int*>(mu + s);                                  // s
+  for (int t = threadIdx.x; t < s * DP; t += blockDim.x) {
+    const int i = t / DP, h = t % DP;
+    const float b0 = basis[(int64_t)c * s * D + i * D + 2 * h];
+    const float b1 = 2 * h + 1 < D ? basis[(int64_t)c * s * D + i * D + 2 * h + 1] : 0.0f;
+    B2[t] = f2_pack(b0, b1);
+  }
   for (int t = threadIdx.x; t < s; t += blockDim.x) {
     mu[t] = mean[(int64_t)c * s + t];
     eo[t] = sub_eoff[(int64_t)c * s + t];
@@ -51,11 +75,7 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ grid,
     smax[threadIdx.x] = 0u;
   }
   __syncthreads();
-  // entries j0 + q * 256, q < kPE: for every subset value the warp's loads of one
-  // q are 32 consecutive centres (coalesced), and one basis row serves kPE chains
   const int64_t j0 = (int64_t)blockIdx.x * blockDim.x * kPE + threadIdx.x;
-  // one patch pointer per entry; entries past N read entry 0's patch (valid
-  // memory) and are not stored, so the loop needs no test per load
   const float* gp[kPE];
   bool ok[kPE];
 #pragma unroll
@@ -64,25 +84,38 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ grid,
     ok[q] = j < N;
     gp[q] = grid + (int64_t)dict[ok[q] ? j : 0] * ch;
   }
-  float acc[kPE][D];
+  unsigned long long acc2[kPE][DP];
 #pragma unroll
   for (int q = 0; q < kPE; ++q)
 #pragma unroll
-    for (int k = 0; k < D; ++k) acc[q][k] = 0.0f;
+    for (int h = 0; h < DP; ++h) acc2[q][h] = 0ull;
 #pragma unroll 2
   for (int i = 0; i < s; ++i) {
     const int o = eo[i];
     const float m = mu[i];
-    float xc[kPE];
+    unsigned long long xc2[kPE];
 #pragma unroll
-    for (int q = 0; q < kPE; ++q) xc[q] = __fsub_rn(gp[q][o], m);
+    for (int q = 0; q < kPE; ++q) {
+      const float x = __fsub_rn(gp[q][o], m);
+      xc2[q] = f2_pack(x, x);
+    }
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-      const float b = B[i * D + k];
+    for (int h = 0; h < DP; ++h) {
+      const unsigned long long b2 = B2[i * DP + h];
 #pragma unroll
-      for (int q = 0; q < kPE; ++q) acc[q][k] = __fmaf_rn(b, xc[q], acc[q][k]);
+      for (int q = 0; q < kPE; ++q) acc2[q][h] = f2_fma(b2, xc2[q], acc2[q][h]);
     }
   }
+  float acc[kPE][D];
+#pragma unroll
+  for (int q = 0; q < kPE; ++q)
+#pragma unroll
+    for (int h = 0; h < DP; ++h) {
+      float lo, hi;
+      f2_unpack(acc2[q][h], lo, hi);
+      acc[q][2 * h] = lo;
+      if (2 * h + 1 < D) acc[q][2 * h + 1] = hi;
+    }
 #pragma unroll
   for (int q = 0; q < kPE; ++q)
     if (ok[q]) {
@@ -171,7 +204,7 @@ __global__ void k_sorted_coords(const float* __restrict__ proj, const uint32_t* 
 
 template <int D>
 int launch_project(const Index& ix, const float* grid, float* proj, uint32_t* lohi, cudaStream_t st) {
-  const size_t shm = sizeof(float) * (ix.s * D + ix.s) + sizeof(int) * ix.s;
+  const size_t shm = sizeof(unsigned long long) * ix.s * ((D + 1) / 2) + sizeof(float) * ix.s + sizeof(int) * ix.s;
   if (shm > kSmemOptIn) SFC_TRY(cudaFuncSetAttribute(k_project<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   dim3 grd((unsigned)((ix.N + 256 * kPE - 1) / (256 * kPE)), ix.C);
   count_launch();

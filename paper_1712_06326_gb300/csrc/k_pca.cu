@@ -94,12 +94,21 @@ __global__ void k_mean_partial(const float* __restrict__ grid, const uint32_t* _
   double acc = 0.0;
   float hi = 0.0f, lo = 0.0f;
   int k = 0;
-  for (int64_t a = a0; a < a1; ++a) {
-    df_add(grid[(int64_t)dict[a * step] * ch + eo], hi, lo);
-    if (++k == 64) {
-      acc += (double)hi + (double)lo;
-      hi = lo = 0.0f;
-      k = 0;
+  // eight samples' loads in flight, then their sums in order
+  for (int64_t a = a0; a < a1; a += 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = a + u < a1 ? grid[(int64_t)dict[(a + u) * step] * ch + eo] : 0.0f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (a + u < a1) {
+        df_add(v[u], hi, lo);
+        if (++k == 64) {
+          acc += (double)hi + (double)lo;
+          hi = lo = 0.0f;
+          k = 0;
+        }
+      }
     }
   }
   msum[(int64_t)split * n + e] = acc + ((double)hi + (double)lo);
@@ -138,20 +147,36 @@ __global__ void __launch_bounds__(256) k_cov_partial(const float* __restrict__ g
   const int64_t a0 = split * per, a1 = a0 + per < cnt ? a0 + per : cnt;
   const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;  // 16x16 threads, 2x2 outputs each
   float hi[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, lo[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-  for (int64_t ab = a0; ab < a1; ab += kChunk) {
-    for (int t = threadIdx.x; t < kChunk * kTile; t += blockDim.x) {
-      int k = t / kTile, e = t % kTile;
-      int64_t a = ab + k;
+  // the next chunk's values are loaded into registers while the current one
+  // is accumulated (each thread stages kPer (sample, value) pairs)
+  constexpr int kPer = kChunk * kTile / 256;
+  float pi[kPer], pj[kPer];
+  auto load_chunk = [&](int64_t ab) {
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int t = threadIdx.x + u * 256;
+      const int k = t / kTile, e = t % kTile;
+      const int64_t a = ab + k;
       float vi = 0.0f, vj = 0.0f;
       if (a < a1) {
-        int64_t base = (int64_t)dict[a * step] * ch;
+        const int64_t base = (int64_t)dict[a * step] * ch;
         if (i0 + e < n) vi = grid[base + eoi[e]];
         if (j0 + e < n) vj = grid[base + eoj[e]];
       }
-      xi[k][e] = vi;
-      xj[k][e] = vj;
+      pi[u] = vi;
+      pj[u] = vj;
+    }
+  };
+  if (a0 < a1) load_chunk(a0);
+  for (int64_t ab = a0; ab < a1; ab += kChunk) {
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int t = threadIdx.x + u * 256;
+      xi[t / kTile][t % kTile] = pi[u];
+      xj[t / kTile][t % kTile] = pj[u];
     }
     __syncthreads();
+    if (ab + kChunk < a1) load_chunk(ab + kChunk);
 #pragma unroll 4
     for (int k = 0; k < kChunk; ++k) {
       float a0v = xi[k][ty * 2], a1v = xi[k][ty * 2 + 1];
