@@ -293,12 +293,21 @@ uint64_t sfc_launch_count(void);
  * ms[SFC_TRACE_PHASES] the summed milliseconds of the phases -- dictionary,
  * moments (mean + covariance), eigen-solve, basis finalisation,
  * projection + keys, sort -- and *builds the number of builds summed, and
+ * (the projections, keys and sorts run pipelined over groups of curves on
+ * the library's own streams: "projection + keys" ends when every group's
+ * keys exist and includes the sorts of the earlier groups that overlap it;
+ * "sort" is the rest of the sorting) and
  * *eig_flops the summed algorithmic FP64 flops of the eigen-solves
  * (per index: 2 s^2 p per product of the covariance with the block and 4 s p^2
  * per orthonormalisation, s = subset length, p = block size).  Any output may be NULL. */
 enum { SFC_TRACE_PHASES = 6 };
 int sfc_trace(int on);
 int sfc_trace_read(double* ms, int64_t* builds, double* eig_flops);
+/* The eigen-solves' algorithmic flops split by precision: *fp64_flops as
+ * eig_flops above (FP64 products and every orthonormalisation), *fp32_flops
+ * 2 s^2 p per product taken in FP32 (the early iterations of the cluster
+ * path).  Either output may be NULL. */
+int sfc_trace_eig_read(double* fp64_flops, double* fp32_flops);
 
 /* While tracing is enabled, every fullscan_query_batch with SFC_FP16 also
  * records events around its phases -- operands (dictionary, centring, A and B

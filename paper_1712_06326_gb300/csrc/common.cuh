@@ -130,6 +130,23 @@ __device__ inline uint64_t morton_key(const uint32_t* q, int D, int bp) {
   return key;
 }
 
+// Packed pairs of FP32 values for fma.rn.f32x2 (sm_100+): each half is the
+// same IEEE round-to-nearest fused multiply-add as the scalar one (the
+// projections it computes are bit-identical to the scalar chains).
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 // morton_key with D known at compile time (q stays in registers): each bit
 // plane's D bits form a group, dimension 0 its most significant bit.
 template <int D>

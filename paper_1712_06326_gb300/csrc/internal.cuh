@@ -84,7 +84,7 @@ struct Index {
   cudaEvent_t ev[SFC_TRACE_PHASES + 1] = {};
   bool traced = false;
   int p_block = 0;             // subspace block size
-  int* eig_iters = nullptr;    // C (device): products A Q computed per index
+  int* eig_iters = nullptr;    // 2C (device): FP64 then FP32 products A Q computed per index
   int eig_per_orth = 1;        // products per orthonormalisation (2 on the cluster path)
 };
 
@@ -107,7 +107,14 @@ int dict_extract_into(const uint8_t* mask, const Geo& g, cudaStream_t st, uint8_
 int pca_build(Index& ix, const float* grid, cudaStream_t st);
 
 // k_index.cu: projection, quantisation, Morton keys.
-int project_and_key(Index& ix, const float* grid, cudaStream_t st, float* proj, uint64_t* keys);
+// Curves [c0, c0 + nc): projections (with the per-axis minima / maxima in
+// lohi, 2 words per axis of every curve, and lo / scale), then keys.
+int project_curves(Index& ix, const float* grid, float* proj, uint32_t* lohi, int c0, int nc, cudaStream_t st);
+int key_curves(Index& ix, const float* proj, uint64_t* keys, int c0, int nc, cudaStream_t st);
+// The library's auxiliary streams of the current device (k < kAuxStreams),
+// created on first use, non-blocking.
+constexpr int kAuxStreams = 3;
+cudaStream_t aux_stream(int k);
 // Quantised, shifted coordinates of the dictionary in each index's sorted order
 // (the k-NN search reads them next to the sorted keys): ix.sqc from proj.
 int sorted_coords(Index& ix, const float* proj, cudaStream_t st);

@@ -31,20 +31,6 @@ __device__ inline float float_of(uint32_t u) {
 
 constexpr int kPE = 4;  // dictionary entries per thread (they share the basis reads)
 
-__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void f2_unpack(unsigned long long v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b, unsigned long long c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-
 // dims paired: acc2[q][h] holds the chains of axes 2h, 2h + 1 of entry q; the
 // basis row pair (B[i][2h], B[i][2h+1]) is read as one 64-bit word and the
 // centred value is duplicated into both halves (the same IEEE FMA per half)
@@ -52,9 +38,9 @@ template <int D>
 __global__ void __launch_bounds__(256) k_project(const float* __restrict__ grid, const uint32_t* __restrict__ dict,
                                                  int64_t N, int ch, int s, const int* __restrict__ sub_eoff,
                                                  const float* __restrict__ basis, const float* __restrict__ mean,
-                                                 float* __restrict__ proj, uint32_t* __restrict__ lohi) {
+                                                 float* __restrict__ proj, uint32_t* __restrict__ lohi, int c0) {
   constexpr int DP = (D + 1) / 2;
-  const int c = blockIdx.y;
+  const int c = c0 + blockIdx.y;
   extern __shared__ unsigned char smem_raw[];
   unsigned long long* B2 = reinterpret_cast<unsigned long long*>(smem_raw);  // s * DP pairs
   float* mu = reinterpret_cast<float*>(B2 + s * DP);                         // s
@@ -176,8 +162,8 @@ namespace {
 template <int D>
 __global__ void k_keys(const float* __restrict__ proj, int64_t N, int bits, int bp, int curve,
                        const float* __restrict__ lo, const float* __restrict__ scale,
-                       const int32_t* __restrict__ shifts, uint64_t* __restrict__ keys) {
-  const int c = blockIdx.y;
+                       const int32_t* __restrict__ shifts, uint64_t* __restrict__ keys, int c0) {
+  const int c = c0 + blockIdx.y;
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= N) return;
   uint32_t q[D];
@@ -203,37 +189,38 @@ __global__ void k_sorted_coords(const float* __restrict__ proj, const uint32_t* 
 }
 
 template <int D>
-int launch_project(const Index& ix, const float* grid, float* proj, uint32_t* lohi, cudaStream_t st) {
+int launch_project(const Index& ix, const float* grid, float* proj, uint32_t* lohi, int c0, int nc,
+                   cudaStream_t st) {
   const size_t shm = sizeof(unsigned long long) * ix.s * ((D + 1) / 2) + sizeof(float) * ix.s + sizeof(int) * ix.s;
   if (shm > kSmemOptIn) SFC_TRY(cudaFuncSetAttribute(k_project<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-  dim3 grd((unsigned)((ix.N + 256 * kPE - 1) / (256 * kPE)), ix.C);
+  dim3 grd((unsigned)((ix.N + 256 * kPE - 1) / (256 * kPE)), nc);
   count_launch();
-  k_project<D><<<grd, 256, shm, st>>>(grid, ix.dict, ix.N, ix.g.ch, ix.s, ix.sub_eoff, ix.basis, ix.mean, proj, lohi);
+  k_project<D><<<grd, 256, shm, st>>>(grid, ix.dict, ix.N, ix.g.ch, ix.s, ix.sub_eoff, ix.basis, ix.mean, proj, lohi,
+                                      c0);
   SFC_TRY(cudaGetLastError());
   return SFC_OK;
 }
 
 template <int D>
-int launch_keys(const Index& ix, const float* proj, uint64_t* keys, cudaStream_t st) {
-  dim3 grd((unsigned)((ix.N + 255) / 256), ix.C);
+int launch_keys(const Index& ix, const float* proj, uint64_t* keys, int c0, int nc, cudaStream_t st) {
+  dim3 grd((unsigned)((ix.N + 255) / 256), nc);
   count_launch();
-  k_keys<D><<<grd, 256, 0, st>>>(proj, ix.N, ix.bits, ix.bp, ix.curve, ix.lo, ix.scale, ix.shifts, keys);
+  k_keys<D><<<grd, 256, 0, st>>>(proj, ix.N, ix.bits, ix.bp, ix.curve, ix.lo, ix.scale, ix.shifts, keys, c0);
   SFC_TRY(cudaGetLastError());
   return SFC_OK;
 }
 
 }  // namespace
 
-int project_and_key(Index& ix, const float* grid, cudaStream_t st, float* proj, uint64_t* keys) {
-  uint32_t* lohi = nullptr;
-  const int n = ix.C * ix.D;
-  SFC_TRY(pmalloc(&lohi, sizeof(uint32_t) * 2 * n, st));
+int project_curves(Index& ix, const float* grid, float* proj, uint32_t* lohi, int c0, int nc, cudaStream_t st) {
+  const int n = nc * ix.D;
+  uint32_t* lh = lohi + 2 * (size_t)c0 * ix.D;
   count_launch();
-  k_lohi_init<<<(n + 127) / 128, 128, 0, st>>>(lohi, n);
+  k_lohi_init<<<(n + 127) / 128, 128, 0, st>>>(lh, n);
   int rc = SFC_EINVAL;
   switch (ix.D) {
 #define SFC_D(d) \
-  case d: rc = launch_project<d>(ix, grid, proj, lohi, st); break;
+  case d: rc = launch_project<d>(ix, grid, proj, lohi, c0, nc, st); break;
     SFC_D(1) SFC_D(2) SFC_D(3) SFC_D(4) SFC_D(5) SFC_D(6) SFC_D(7) SFC_D(8)
     SFC_D(9) SFC_D(10) SFC_D(11) SFC_D(12) SFC_D(13) SFC_D(14) SFC_D(15) SFC_D(16)
 #undef SFC_D
@@ -241,17 +228,22 @@ int project_and_key(Index& ix, const float* grid, cudaStream_t st, float* proj, 
   }
   SFC_CHECK(rc);
   count_launch();
-  k_scale<<<(n + 127) / 128, 128, 0, st>>>(lohi, n, ix.bits, ix.lo, ix.scale);
+  k_scale<<<(n + 127) / 128, 128, 0, st>>>(lh, n, ix.bits, ix.lo + (size_t)c0 * ix.D, ix.scale + (size_t)c0 * ix.D);
+  SFC_TRY(cudaGetLastError());
+  return SFC_OK;
+}
+
+int key_curves(Index& ix, const float* proj, uint64_t* keys, int c0, int nc, cudaStream_t st) {
+  int rc = SFC_EINVAL;
   switch (ix.D) {
 #define SFC_D(d) \
-  case d: rc = launch_keys<d>(ix, proj, keys, st); break;
+  case d: rc = launch_keys<d>(ix, proj, keys, c0, nc, st); break;
     SFC_D(1) SFC_D(2) SFC_D(3) SFC_D(4) SFC_D(5) SFC_D(6) SFC_D(7) SFC_D(8)
     SFC_D(9) SFC_D(10) SFC_D(11) SFC_D(12) SFC_D(13) SFC_D(14) SFC_D(15) SFC_D(16)
 #undef SFC_D
+    default: set_error("dims must be 1..16"); return SFC_EINVAL;
   }
-  SFC_CHECK(rc);
-  cudaFreeAsync(lohi, st);
-  return SFC_OK;
+  return rc;
 }
 
 int sorted_coords(Index& ix, const float* proj, cudaStream_t st) {

@@ -237,7 +237,8 @@ struct SiBufs {
   double* X;   // C*s*p
   double* e;   // C*p
   int* done;   // C
-  int* iters;  // C: iterations used (tracing)
+  int* iters;  // C: FP64 products with A (tracing)
+  int* iters32;  // C: FP32 products with A (tracing; cluster path)
 };
 
 // Y = A Q for every curve; blockIdx.y = curve, the s*p outputs spread over
@@ -1210,12 +1211,13 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
   // only accepted on FP64 products.  Every CTA of the cluster takes the same
   // decisions (they depend on cluster-reduced values only).
   bool lowp = use32 != 0;
-  int prod64 = 0;
+  int prod64 = 0, prod32 = 0;
   for (int it = 0; it < kMaxIterCl && !conv; ++it) {
     // Y = A Q (this CTA's rows)
     const bool lp1 = lowp;
     if (lp1) {
       local_rows_times32(m, nr, s, p, m.Ys);
+      ++prod32;
     } else {
       local_rows_times(m, nr, s, p, m.Ys);
       ++prod64;
@@ -1289,6 +1291,7 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
         if (me == 0 && threadIdx.x == 0) {
           b.done[c] = conv ? 1 : 0;
           b.iters[c] = prod64;  // FP64 products with A
+          b.iters32[c] = prod32;
         }
         break;
       }
@@ -1303,6 +1306,7 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
     cl_allgather_rows<CS>(cl, m, nr, r0, s, p, rp);
     if (lowp) {
       local_rows_times32(m, nr, s, p, m.Zs);
+      ++prod32;
     } else {
       local_rows_times(m, nr, s, p, m.Zs);
       ++prod64;
@@ -1368,6 +1372,7 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
   SFC_TRY(pmalloc(&b.e, sizeof(double) * C * p, st));
   SFC_TRY(pmalloc(&b.done, sizeof(int) * C, st));
   b.iters = ix.eig_iters;
+  b.iters32 = ix.eig_iters + C;
   SFC_TRY(cudaMemsetAsync(b.iters, 0, sizeof(int) * C, st));
   SFC_TRY(cudaMemcpyAsync(pairs, pairs_h.data(), sizeof(int2) * npairs, cudaMemcpyHostToDevice, st));
 

@@ -38,6 +38,7 @@ struct TraceAcc {
   double ms[SFC_TRACE_PHASES] = {};
   int64_t builds = 0;
   double eig_flops = 0.0;
+  double eig_flops32 = 0.0;
   double tc_ms[SFC_TRACE_TC_PHASES] = {};
   int64_t tc_calls = 0;
   double tc_flops = 0.0;
@@ -92,17 +93,22 @@ static void trace_fold(Index& ix) {
   float t[SFC_TRACE_PHASES] = {};
   bool ok = true;
   for (int k = 0; k < SFC_TRACE_PHASES && ok; ++k) ok = cudaEventElapsedTime(&t[k], ix.ev[k], ix.ev[k + 1]) == cudaSuccess;
-  std::vector<int> it(ix.C, 0);
-  if (ok && ix.eig_iters) ok = cudaMemcpy(it.data(), ix.eig_iters, sizeof(int) * ix.C, cudaMemcpyDeviceToHost) == cudaSuccess;
+  std::vector<int> it(2 * ix.C, 0);
+  if (ok && ix.eig_iters)
+    ok = cudaMemcpy(it.data(), ix.eig_iters, sizeof(int) * 2 * ix.C, cudaMemcpyDeviceToHost) == cudaSuccess;
   cudaGetLastError();
   if (ok) {
     std::lock_guard<std::mutex> lk(g_trace_mu);
     for (int k = 0; k < SFC_TRACE_PHASES; ++k) g_trace.ms[k] += t[k];
     g_trace.builds += 1;
     const double s = ix.s, p = ix.p_block;
-    // per product A Q: 2 s^2 p; per orthonormalisation (Gram + Q = Z R^-1): 4 s p^2
-    for (int c = 0; c < ix.C; ++c)
-      g_trace.eig_flops += it[c] * 2.0 * s * s * p + std::ceil((double)it[c] / ix.eig_per_orth) * 4.0 * s * p * p;
+    // per product A Q: 2 s^2 p (FP64 or FP32); per orthonormalisation (Gram +
+    // Q = Z R^-1, FP64): 4 s p^2
+    for (int c = 0; c < ix.C; ++c) {
+      const int i64 = it[c], i32 = it[ix.C + c];
+      g_trace.eig_flops += i64 * 2.0 * s * s * p + std::ceil((double)(i64 + i32) / ix.eig_per_orth) * 4.0 * s * p * p;
+      g_trace.eig_flops32 += i32 * 2.0 * s * s * p;
+    }
   }
   for (auto& e : ix.ev)
     if (e) {
@@ -160,6 +166,22 @@ cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st) {
   }
   if (pool) return cudaMallocFromPoolAsync(p, bytes, pool, st);
   return cudaMallocAsync(p, bytes, st);
+}
+
+namespace {
+std::mutex g_aux_mu;
+cudaStream_t g_aux[128][kAuxStreams] = {};
+}  // namespace
+
+cudaStream_t aux_stream(int k) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128 || k < 0 || k >= kAuxStreams) return nullptr;
+  std::lock_guard<std::mutex> lk(g_aux_mu);
+  if (!g_aux[dev][k] && cudaStreamCreateWithFlags(&g_aux[dev][k], cudaStreamNonBlocking) != cudaSuccess) {
+    g_aux[dev][k] = nullptr;
+    cudaGetLastError();
+  }
+  return g_aux[dev][k];
 }
 
 int fill_loop(const Geo& g, float* grid, uint8_t* mask, int prio, int mode, const Index* ix, const uint32_t* dict,
@@ -376,6 +398,74 @@ int dev_in(FileIn& in, T** d, size_t count, cudaStream_t st) {
 }
 }  // namespace
 
+// Projection, keys and sort of every curve, pipelined over groups of curves:
+// group g runs on its own stream (group 0 on st), its projection starts once
+// group g - 1's projection is done, so that the sorts of the earlier groups
+// (latency-bound) overlap the projections of the later ones (FP32-bound).
+// Phase 5 of the trace is marked once every group's keys exist, phase 6 (by
+// the caller) once every sort is done.  st waits for all groups, also on an
+// error, so nothing the caller frees next is still in use.
+int project_sort_pipelined(Index& ix, const float* grid, float* proj, uint64_t* keys, uint32_t* lohi,
+                           cudaStream_t st) {
+  const int C = ix.C;
+  const int64_t N = ix.N;
+  const int key_bits = std::min(64, ix.D * ix.bp);
+  int G = C < kAuxStreams + 1 ? C : kAuxStreams + 1;
+  cudaStream_t sg[kAuxStreams + 1] = {st};
+  for (int g = 1; g < G; ++g) {
+    sg[g] = aux_stream(g - 1);
+    if (!sg[g]) G = g;  // no stream: fewer groups
+  }
+  const int per = (C + G - 1) / G;
+  G = (C + per - 1) / per;
+  cudaEvent_t ev_fork = nullptr, ev_proj[kAuxStreams + 1] = {}, ev_keys[kAuxStreams + 1] = {},
+              ev_done[kAuxStreams + 1] = {};
+  int rc = SFC_OK;
+  auto mk = [&](cudaEvent_t* e) {
+    if (rc == SFC_OK && cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) {
+      set_error("cudaEventCreateWithFlags failed");
+      rc = SFC_ECUDA;
+    }
+  };
+  mk(&ev_fork);
+  for (int g = 0; g < G; ++g) {
+    mk(&ev_proj[g]);
+    mk(&ev_keys[g]);
+    mk(&ev_done[g]);
+  }
+  if (rc == SFC_OK && cudaEventRecord(ev_fork, st) != cudaSuccess) rc = SFC_ECUDA;
+  int launched = 0;
+  for (int g = 0; g < G && rc == SFC_OK; ++g) {
+    const int c0 = g * per, nc = std::min(per, C - c0);
+    cudaStream_t s = sg[g];
+    if (g > 0 && (cudaStreamWaitEvent(s, ev_fork, 0) != cudaSuccess ||
+                  cudaStreamWaitEvent(s, ev_proj[g - 1], 0) != cudaSuccess)) {
+      rc = SFC_ECUDA;
+      break;
+    }
+    launched = g + 1;
+    rc = project_curves(ix, grid, proj, lohi, c0, nc, s);
+    if (rc == SFC_OK && cudaEventRecord(ev_proj[g], s) != cudaSuccess) rc = SFC_ECUDA;
+    if (rc == SFC_OK) rc = key_curves(ix, proj, keys, c0, nc, s);
+    if (rc == SFC_OK && cudaEventRecord(ev_keys[g], s) != cudaSuccess) rc = SFC_ECUDA;
+    if (rc == SFC_OK)
+      rc = radix_sort_pairs(keys + (size_t)c0 * N, ix.skeys + (size_t)c0 * N, ix.sids + (size_t)c0 * N, N, nc,
+                            key_bits, s);
+    if (cudaEventRecord(ev_done[g], s) != cudaSuccess && rc == SFC_OK) rc = SFC_ECUDA;
+  }
+  if (rc == SFC_OK) {
+    for (int g = 1; g < launched; ++g) cudaStreamWaitEvent(st, ev_keys[g], 0);
+    trace_mark(ix, 5, st);
+  }
+  for (int g = 1; g < launched; ++g) cudaStreamWaitEvent(st, ev_done[g], 0);
+  for (cudaEvent_t e : {ev_fork}) if (e) cudaEventDestroy(e);
+  for (int g = 0; g < G; ++g)
+    for (cudaEvent_t e : {ev_proj[g], ev_keys[g], ev_done[g]})
+      if (e) cudaEventDestroy(e);
+  if (rc == SFC_ECUDA && sfc_last_error()[0] == 0) set_error(std::string("pipelined build: ") + cudaGetErrorString(cudaGetLastError()));
+  return rc;
+}
+
 // Build every array of an index (shared by sfc_index_build and inpaint_run).
 int build_index(const float* grid, const uint8_t* dict_mask, const sfc_grid* gp, const sfc_params* p,
                 cudaStream_t st, Index& ix) {
@@ -465,8 +555,8 @@ int build_index(const float* grid, const uint8_t* dict_mask, const sfc_grid* gp,
     for (auto& e : ix.ev) SFC_TRY(cudaEventCreate(&e));
     trace_mark(ix, 0, st);
   }
-  SFC_TRY(pmalloc(&ix.eig_iters, sizeof(int) * ix.C, st));
-  SFC_TRY(cudaMemsetAsync(ix.eig_iters, 0, sizeof(int) * ix.C, st));
+  SFC_TRY(pmalloc(&ix.eig_iters, sizeof(int) * 2 * ix.C, st));
+  SFC_TRY(cudaMemsetAsync(ix.eig_iters, 0, sizeof(int) * 2 * ix.C, st));
   SFC_CHECK(dict_extract(dict_mask, g, st, &ix.dict, &ix.N));
   trace_mark(ix, 1, st);
   if (ix.N <= 0) {
@@ -494,12 +584,12 @@ int build_index(const float* grid, const uint8_t* dict_mask, const sfc_grid* gp,
   trace_mark(ix, 4, st);
   float* proj = nullptr;
   uint64_t* keys = nullptr;
+  uint32_t* lohi = nullptr;
   SFC_TRY(pmalloc(&proj, sizeof(float) * C * N * D, st));
   SFC_TRY(pmalloc(&keys, sizeof(uint64_t) * C * N, st));
-  SFC_CHECK(project_and_key(ix, grid, st, proj, keys));
-  trace_mark(ix, 5, st);
-  const int key_bits = std::min(64, D * ix.bp);
-  SFC_CHECK(radix_sort_pairs(keys, ix.skeys, ix.sids, N, C, key_bits, st));
+  SFC_TRY(pmalloc(&lohi, sizeof(uint32_t) * 2 * C * D, st));
+  SFC_CHECK(project_sort_pipelined(ix, grid, proj, keys, lohi, st));
+  cudaFreeAsync(lohi, st);
   if (ix.knn > 0) SFC_CHECK(sorted_coords(ix, proj, st));
   trace_mark(ix, 6, st);
   if (ix.keep) {
@@ -551,6 +641,13 @@ int sfc_trace_tc_read(double* ms, int64_t* calls, double* gemm_flops) {
     for (int k = 0; k < SFC_TRACE_TC_PHASES; ++k) ms[k] = g_trace.tc_ms[k];
   if (calls) *calls = g_trace.tc_calls;
   if (gemm_flops) *gemm_flops = g_trace.tc_flops;
+  return SFC_OK;
+}
+
+int sfc_trace_eig_read(double* fp64_flops, double* fp32_flops) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  if (fp64_flops) *fp64_flops = g_trace.eig_flops;
+  if (fp32_flops) *fp32_flops = g_trace.eig_flops32;
   return SFC_OK;
 }
 
@@ -841,8 +938,8 @@ int sfc_index_load(const char* path, void* stream, sfc_index** out) {
   if (rc == SFC_OK) rc = dev_in(in, &ix.skeys, (size_t)(C * N), st);
   if (rc == SFC_OK) rc = dev_in(in, &ix.sids, (size_t)(C * N), st);
   if (rc == SFC_OK && ix.knn > 0) rc = dev_in(in, &ix.sqc, (size_t)(C * N * D), st);
-  if (rc == SFC_OK && (pmalloc(&ix.eig_iters, sizeof(int) * C, st) != cudaSuccess ||
-                       cudaMemsetAsync(ix.eig_iters, 0, sizeof(int) * C, st) != cudaSuccess)) {
+  if (rc == SFC_OK && (pmalloc(&ix.eig_iters, sizeof(int) * 2 * C, st) != cudaSuccess ||
+                       cudaMemsetAsync(ix.eig_iters, 0, sizeof(int) * 2 * C, st) != cudaSuccess)) {
     cudaGetLastError();
     set_error("sfc_index_load: out of device memory");
     rc = SFC_ENOMEM;

@@ -29,7 +29,7 @@ EXPORTS = ["sfc_params_default", "sfc_index_build", "sfc_index_destroy", "sfc_in
            "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "fullscan_query_batch_static",
            "sfc_tc_prescores", "inpaint_run", "sfc_status", "sfc_launch_count", "sfc_trace", "sfc_trace_read", "sfc_trace_tc_read",
            "sfc_last_error", "sfc_index_save", "sfc_index_load", "sfc_index_params", "sfc_query_batch_dict",
-           "sfc_multi_create", "sfc_multi_query", "sfc_multi_destroy", "sfc_autotune", "sfc_tune_select"]
+           "sfc_multi_create", "sfc_multi_query", "sfc_multi_destroy", "sfc_autotune", "sfc_tune_select", "sfc_trace_eig_read"]
 TRACE_PHASES = ("dictionary", "moments", "eigen", "finalize", "project_keys", "sort")
 
 
@@ -97,6 +97,8 @@ def lib():
         L.sfc_trace.restype = C.c_int
         L.sfc_trace_read.argtypes = [vp, vp, vp]
         L.sfc_trace_read.restype = C.c_int
+        L.sfc_trace_eig_read.argtypes = [vp, vp]
+        L.sfc_trace_eig_read.restype = C.c_int
         L.sfc_trace_tc_read.argtypes = [vp, vp, vp]
         L.sfc_trace_tc_read.restype = C.c_int
         for name in ["sfc_index_build", "sfc_index_destroy", "sfc_index_info", "sfc_index_export",
@@ -446,7 +448,12 @@ def sfc_trace_read() -> dict:
     fl = np.zeros(1, np.float64)
     _check(lib().sfc_trace_read(ms.ctypes.data_as(C.c_void_p), builds.ctypes.data_as(C.c_void_p),
                                 fl.ctypes.data_as(C.c_void_p)), "sfc_trace_read")
-    return dict(ms=dict(zip(TRACE_PHASES, ms.tolist())), builds=int(builds[0]), eig_flops=float(fl[0]))
+    f64 = np.zeros(1, np.float64)
+    f32 = np.zeros(1, np.float64)
+    _check(lib().sfc_trace_eig_read(f64.ctypes.data_as(C.c_void_p), f32.ctypes.data_as(C.c_void_p)),
+           "sfc_trace_eig_read")
+    return dict(ms=dict(zip(TRACE_PHASES, ms.tolist())), builds=int(builds[0]), eig_flops=float(fl[0]),
+                eig_flops32=float(f32[0]))
 
 
 TRACE_TC_PHASES = ("operands", "gemm", "exact")
