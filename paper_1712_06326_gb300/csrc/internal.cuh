@@ -120,8 +120,11 @@ cudaStream_t aux_stream(int k);
 int sorted_coords(Index& ix, const float* proj, cudaStream_t st);
 
 // k_sort.cu: stable LSD radix sort (onesweep) of (key, id) per index.
+// scratch: radix_sort_scratch_bytes(N, C, key_bits) bytes of device memory
+// usable on st, or nullptr (then allocated and freed on st).
 int radix_sort_pairs(const uint64_t* keys, uint64_t* skeys, uint32_t* sids, int64_t N, int C, int key_bits,
-                     cudaStream_t st);
+                     cudaStream_t st, void* scratch = nullptr);
+size_t radix_sort_scratch_bytes(int64_t N, int C, int key_bits);
 
 // k_query.cu
 // Targets on a grid other than the index's: its geometry, its patch element

@@ -204,26 +204,59 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const uint64_t* __rest
 
 }  // namespace
 
+namespace {
+struct SortLayout {
+  int npass;
+  int64_t ntiles;
+  size_t hist, status, ctr, tk, tv, goffs, total;  // byte offsets / size
+};
+SortLayout sort_layout(int64_t N, int C, int key_bits) {
+  SortLayout L;
+  L.npass = (key_bits + 7) / 8;
+  if (L.npass < 1) L.npass = 1;
+  if (L.npass > 8) L.npass = 8;
+  L.ntiles = (N + kTileKeys - 1) / kTileKeys;
+  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  size_t o = 0;
+  L.hist = o;
+  o += up(sizeof(uint32_t) * C * 8 * 256);
+  L.status = o;
+  o += up(sizeof(uint32_t) * (size_t)L.npass * C * L.ntiles * 256);
+  L.ctr = o;
+  o += up(sizeof(uint32_t) * L.npass * C);
+  L.tk = o;
+  o += up(sizeof(uint64_t) * C * N);
+  L.tv = o;
+  o += up(sizeof(uint32_t) * C * N);
+  L.goffs = o;
+  o += up(sizeof(uint32_t) * L.npass * C * 256);
+  L.total = o;
+  return L;
+}
+}  // namespace
+
+size_t radix_sort_scratch_bytes(int64_t N, int C, int key_bits) { return N > 0 ? sort_layout(N, C, key_bits).total : 0; }
+
 int radix_sort_pairs(const uint64_t* keys, uint64_t* skeys, uint32_t* sids, int64_t N, int C, int key_bits,
-                     cudaStream_t st) {
+                     cudaStream_t st, void* scratch) {
   if (N <= 0) return SFC_OK;
   if (N >= (int64_t)kValMask) {
     set_error("dictionary too large for the radix sort (>= 2^30 entries per index)");
     return SFC_EINVAL;
   }
-  int npass = (key_bits + 7) / 8;
-  if (npass < 1) npass = 1;
-  if (npass > 8) npass = 8;
-  const int64_t ntiles = (N + kTileKeys - 1) / kTileKeys;
-  uint32_t *hist = nullptr, *status = nullptr, *ctr = nullptr;
-  uint64_t* tk = nullptr;
-  uint32_t* tv = nullptr;
+  const SortLayout L = sort_layout(N, C, key_bits);
+  const int npass = L.npass;
+  const int64_t ntiles = L.ntiles;
+  unsigned char* ws = static_cast<unsigned char*>(scratch);
+  const bool own = ws == nullptr;
+  if (own) SFC_TRY(pmalloc(&ws, L.total, st));
+  uint32_t* hist = reinterpret_cast<uint32_t*>(ws + L.hist);
+  uint32_t* status = reinterpret_cast<uint32_t*>(ws + L.status);
+  uint32_t* ctr = reinterpret_cast<uint32_t*>(ws + L.ctr);
+  uint64_t* tk = reinterpret_cast<uint64_t*>(ws + L.tk);
+  uint32_t* tv = reinterpret_cast<uint32_t*>(ws + L.tv);
+  uint32_t* goffs = reinterpret_cast<uint32_t*>(ws + L.goffs);
   const size_t status_words = (size_t)npass * C * ntiles * 256;
-  SFC_TRY(pmalloc(&hist, sizeof(uint32_t) * C * 8 * 256, st));
-  SFC_TRY(pmalloc(&status, sizeof(uint32_t) * status_words, st));
-  SFC_TRY(pmalloc(&ctr, sizeof(uint32_t) * npass * C, st));
-  SFC_TRY(pmalloc(&tk, sizeof(uint64_t) * C * N, st));
-  SFC_TRY(pmalloc(&tv, sizeof(uint32_t) * C * N, st));
   SFC_TRY(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * C * 8 * 256, st));
   SFC_TRY(cudaMemsetAsync(status, 0, sizeof(uint32_t) * status_words, st));
   SFC_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t) * npass * C, st));
@@ -235,8 +268,6 @@ int radix_sort_pairs(const uint64_t* keys, uint64_t* skeys, uint32_t* sids, int6
   k_hist_scan<<<dim3(npass, C), 256, 0, st>>>(hist);
   SFC_TRY(cudaGetLastError());
   // hist is laid out [C][8][256]; pass p needs the [C][256] slice of every index
-  uint32_t* goffs = nullptr;
-  SFC_TRY(pmalloc(&goffs, sizeof(uint32_t) * npass * C * 256, st));
   for (int p = 0; p < npass; ++p)
     SFC_TRY(cudaMemcpy2DAsync(goffs + (size_t)p * C * 256, 256 * sizeof(uint32_t), hist + (size_t)p * 256,
                               8 * 256 * sizeof(uint32_t), 256 * sizeof(uint32_t), C, cudaMemcpyDeviceToDevice, st));
@@ -255,12 +286,7 @@ int radix_sort_pairs(const uint64_t* keys, uint64_t* skeys, uint32_t* sids, int6
     ink = ok_;
     inv = ov;
   }
-  cudaFreeAsync(hist, st);
-  cudaFreeAsync(status, st);
-  cudaFreeAsync(ctr, st);
-  cudaFreeAsync(tk, st);
-  cudaFreeAsync(tv, st);
-  cudaFreeAsync(goffs, st);
+  if (own) cudaFreeAsync(ws, st);
   return SFC_OK;
 }
 

@@ -418,6 +418,11 @@ int project_sort_pipelined(Index& ix, const float* grid, float* proj, uint64_t* 
   }
   const int per = (C + G - 1) / G;
   G = (C + per - 1) / per;
+  // every group's sort scratch is taken on st before the fork and returned
+  // after the join, so no memory moves between the streams' pool queues
+  const size_t ws_bytes = radix_sort_scratch_bytes(N, per, key_bits);
+  unsigned char* ws = nullptr;
+  SFC_TRY(pmalloc(&ws, ws_bytes * G, st));
   cudaEvent_t ev_fork = nullptr, ev_proj[kAuxStreams + 1] = {}, ev_keys[kAuxStreams + 1] = {},
               ev_done[kAuxStreams + 1] = {};
   int rc = SFC_OK;
@@ -450,7 +455,7 @@ int project_sort_pipelined(Index& ix, const float* grid, float* proj, uint64_t* 
     if (rc == SFC_OK && cudaEventRecord(ev_keys[g], s) != cudaSuccess) rc = SFC_ECUDA;
     if (rc == SFC_OK)
       rc = radix_sort_pairs(keys + (size_t)c0 * N, ix.skeys + (size_t)c0 * N, ix.sids + (size_t)c0 * N, N, nc,
-                            key_bits, s);
+                            key_bits, s, ws + ws_bytes * g);
     if (cudaEventRecord(ev_done[g], s) != cudaSuccess && rc == SFC_OK) rc = SFC_ECUDA;
   }
   if (rc == SFC_OK) {
@@ -458,6 +463,7 @@ int project_sort_pipelined(Index& ix, const float* grid, float* proj, uint64_t* 
     trace_mark(ix, 5, st);
   }
   for (int g = 1; g < launched; ++g) cudaStreamWaitEvent(st, ev_done[g], 0);
+  cudaFreeAsync(ws, st);
   for (cudaEvent_t e : {ev_fork}) if (e) cudaEventDestroy(e);
   for (int g = 0; g < G; ++g)
     for (cudaEvent_t e : {ev_proj[g], ev_keys[g], ev_done[g]})
