@@ -32,7 +32,7 @@
 // memory, the whole iteration runs in one launch on a cluster of 16 CTAs per
 // curve (8 where 16-CTA clusters cannot be scheduled; see k_si_cluster); there
 // the products are taken in FP32 (A and Q rounded, FP32 accumulation) until a
-// Rayleigh-Ritz residual reaches 1e-5 of e_0 -- the iteration is
+// Rayleigh-Ritz residual reaches 3.2e-6 of e_0 -- the iteration is
 // self-correcting, so this only changes the start of the FP64 iterations, and
 // convergence is tested on FP64 products only; otherwise one launch per iteration
 // computes Y = A Q with every curve's rows spread over the GPU and a second (one
@@ -571,7 +571,7 @@ __global__ void k_pca_finalize(SiBufs b, const double* __restrict__ mean, int s,
 // cluster barriers between phases.  Rayleigh-Ritz and the convergence test run
 // every kRR-th iteration (the subspace converges at the same rate without it).
 // ----------------------------------------------------------------------------
-constexpr int kRR = 2;  // Rayleigh-Ritz every kRR iterations (of two products each)
+constexpr int kRR = 3;  // Rayleigh-Ritz every kRR iterations (of two products each)
 constexpr int kMaxIterCl = 64;
 constexpr int kLowpIters = 16;  // iterations with FP32 products at most
 
@@ -1206,7 +1206,7 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
     cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
   }
   bool conv = false;
-  // products in FP32 until a Rayleigh-Ritz residual reaches 1e-5 of l_1 (or
+  // products in FP32 until a Rayleigh-Ritz residual reaches 3.2e-6 of l_1 (or
   // kLowpIters iterations have passed), in FP64 from then on; convergence is
   // only accepted on FP64 products.  Every CTA of the cluster takes the same
   // decisions (they depend on cluster-reduced values only).
@@ -1285,7 +1285,7 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
       double worst = 0.0;
       for (int k = 0; k < D; ++k) worst = fmax(worst, m.Hf[k]);
       conv = !lp1 && worst <= 1e-22 * m.ev[0] * m.ev[0];
-      if (lowp && (worst <= 1e-10 * m.ev[0] * m.ev[0] || it >= kLowpIters)) lowp = false;
+      if (lowp && (worst <= 1e-11 * m.ev[0] * m.ev[0] || it >= kLowpIters)) lowp = false;
       if (conv || it == kMaxIterCl - 1) {
         if (me == 0 && threadIdx.x < p) b.e[(int64_t)c * p + threadIdx.x] = m.ev[threadIdx.x];
         if (me == 0 && threadIdx.x == 0) {

@@ -320,18 +320,19 @@ __device__ void warp_knn(const uint64_t* __restrict__ sk, const uint32_t* __rest
     if (s * 32 + lane < kk) out[s * 32 + lane] = li[s];
 }
 
-// FP32 costs of the candidates ucand[0..ncand), one warp per candidate (lane
-// elements lane + 32 t in registers), into c32; returns this warp's minimum.
+// FP32 costs of the candidates ucand[0..ncand), one warp per candidate (the
+// target's nk known elements, compacted: lane holds known elements lane + 32 t
+// in registers), into c32; returns this warp's minimum.
 // L1 (Sec. III.K): w |d| instead of w d^2.
 template <int MAXE, bool WEIGHTED, bool L1>
 __device__ __forceinline__ float rescore_all(const float* __restrict__ dgrid, const uint32_t* __restrict__ dict,
-                                             const uint32_t* ucand, int ncand, int ch, int n, const float (&am)[MAXE],
-                                             const float (&mt)[MAXE], const int (&eor)[MAXE],
-                                             const float (&wv)[MAXE], float* c32) {
+                                             const uint32_t* ucand, int ncand, int ch, int nk, const float (&tr)[MAXE],
+                                             const int (&eor)[MAXE], const float (&wv)[MAXE], float* c32) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float wmin = INFINITY;
   // two candidates per pass (ci and ci + kQWarps): twice the gathers in flight;
-  // each candidate's sum keeps its order (element t per lane, then the warp sum)
+  // each candidate's sum keeps its order (known element t per lane, then the
+  // warp sum)
   for (int ci = warp; ci < ncand; ci += 2 * kQWarps) {
     const int cj = ci + kQWarps;
     const bool two = cj < ncand;
@@ -340,11 +341,11 @@ __device__ __forceinline__ float rescore_all(const float* __restrict__ dgrid, co
     float acc = 0.0f, acc2 = 0.0f;
 #pragma unroll
     for (int t = 0; t < MAXE; ++t) {
-      if (lane + 32 * t < n) {
+      if (lane + 32 * t < nk) {
         const float p = __ldg(dgrid + sb + eor[t]);
         const float p2 = __ldg(dgrid + sb2 + eor[t]);
-        const float d = __fmaf_rn(-am[t], p, mt[t]);
-        const float d2 = __fmaf_rn(-am[t], p2, mt[t]);
+        const float d = __fsub_rn(tr[t], p);
+        const float d2 = __fsub_rn(tr[t], p2);
         if (L1) {
           acc = WEIGHTED ? __fmaf_rn(wv[t], fabsf(d), acc) : __fadd_rn(acc, fabsf(d));
           acc2 = WEIGHTED ? __fmaf_rn(wv[t], fabsf(d2), acc2) : __fadd_rn(acc2, fabsf(d2));
@@ -390,14 +391,16 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   const int n = g.n, P = g.P, ch = g.ch;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* tv = reinterpret_cast<float*>(smem_raw);          // n
-  int* eo = reinterpret_cast<int*>(tv + n);                // n
-  uint32_t* cand = reinterpret_cast<uint32_t*>(eo + n);    // L
+  int* ceo = reinterpret_cast<int*>(tv + n);               // n: known elements' dictionary-grid offsets
+  uint32_t* cand = reinterpret_cast<uint32_t*>(ceo + n);   // L
   uint32_t* ucand = cand + a.L;                            // L
   float* c32 = reinterpret_cast<float*>(ucand + a.L);      // L
   int* deo = reinterpret_cast<int*>(c32 + a.L);            // n (dictionary-grid offsets)
   float* xcb = reinterpret_cast<float*>(deo + n);          // kQWarps * kXChunk
   float* bcb = xcb + kQWarps * kXChunk;                    // kQWarps * kXChunk * D
-  uint8_t* tm = reinterpret_cast<uint8_t*>(bcb + kQWarps * kXChunk * a.D);  // P
+  float* ct = bcb + kQWarps * kXChunk * a.D;               // n: known elements' target values
+  float* cw = ct + n;                                      // n: their channel weights
+  uint8_t* tm = reinterpret_cast<uint8_t*>(cw + n);        // P
   // k-NN region stacks, one per warp (k-NN mode only), rounded up to a 16-byte
   // boundary after tm (its offset 12 n + 12 L is only 4-aligned for odd n)
   KnnRegion* knn_stack = reinterpret_cast<KnnRegion*>(((uintptr_t)(tm + g.P) + 15) & ~(uintptr_t)15);
@@ -435,7 +438,6 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   const int64_t tc = s_redi[0];
   for (int e = tid; e < n; e += kQThreads) {
     int o = I.eoff_all[e];
-    eo[e] = o;
     deo[e] = I.deoff[e];
     tv[e] = I.grid[tc * ch + o];
   }
@@ -607,27 +609,42 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   if (!a.pick) return;
 
   // --- FP32 rescore --------------------------------------------------------
-  float am[MAXE], mt[MAXE], wv[MAXE];
+  // the known elements of the target, compacted in patch order: unknown ones
+  // add exactly 0 to a cost, so only known values are gathered
+  int nk = 0;
+  for (int r0 = 0; r0 < n; r0 += kQThreads) {
+    const int e = r0 + tid;
+    const bool kn = e < n && tm[e / ch] != 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, kn);
+    if (lane == 0) s_part[warp] = (uint32_t)__popc(bal);
+    __syncthreads();
+    int off = nk, tot = 0;
+    for (int w = 0; w < kQWarps; ++w) {
+      if (w < warp) off += (int)s_part[w];
+      tot += (int)s_part[w];
+    }
+    if (kn) {
+      const int at = off + __popc(bal & ((1u << lane) - 1u));
+      ceo[at] = deo[e];
+      ct[at] = tv[e];
+      cw[at] = WEIGHTED ? a.weights[e % ch] : 1.0f;
+    }
+    __syncthreads();
+    nk += tot;
+  }
+  float tr[MAXE], wv[MAXE];
   int eor[MAXE];
 #pragma unroll
   for (int t = 0; t < MAXE; ++t) {
-    int e = lane + 32 * t;
-    if (e < n) {
-      float k = tm[e / ch] ? 1.0f : 0.0f;
-      am[t] = k;
-      mt[t] = k * tv[e];
-      eor[t] = deo[e];
-      wv[t] = WEIGHTED ? a.weights[e % ch] : 1.0f;
-    } else {
-      am[t] = 0.0f;
-      mt[t] = 0.0f;
-      eor[t] = 0;
-      wv[t] = 0.0f;
-    }
+    const int e = lane + 32 * t;
+    const bool in = e < nk;
+    tr[t] = in ? ct[e] : 0.0f;
+    eor[t] = in ? ceo[e] : 0;
+    wv[t] = in ? cw[e] : 0.0f;
   }
   // the L2 / L1 choice is uniform: one specialised loop each, no test per element
-  const float wmin = a.l1 ? rescore_all<MAXE, WEIGHTED, true>(I.dgrid, I.dict, ucand, ncand, ch, n, am, mt, eor, wv, c32)
-                          : rescore_all<MAXE, WEIGHTED, false>(I.dgrid, I.dict, ucand, ncand, ch, n, am, mt, eor, wv, c32);
+  const float wmin = a.l1 ? rescore_all<MAXE, WEIGHTED, true>(I.dgrid, I.dict, ucand, ncand, ch, nk, tr, eor, wv, c32)
+                          : rescore_all<MAXE, WEIGHTED, false>(I.dgrid, I.dict, ucand, ncand, ch, nk, tr, eor, wv, c32);
   if (lane == 0) s_redf[warp] = wmin;
   __syncthreads();
   float m32 = s_redf[0];
@@ -786,7 +803,7 @@ int common_args(const Index& ix, int64_t maxN, QArgs& a) {
 }
 
 int launch_query(const Index& ix, const QArgs& a, int64_t Q, cudaStream_t st) {
-  const size_t shm = (size_t)ix.g.n * 12 + (size_t)a.L * 12 + sizeof(float) * kQWarps * kXChunk * (1 + ix.D) +
+  const size_t shm = (size_t)ix.g.n * 20 + (size_t)a.L * 12 + sizeof(float) * kQWarps * kXChunk * (1 + ix.D) +
                      (size_t)ix.g.P +
                      (ix.knn > 0 ? 16 + sizeof(KnnRegion) * kKnnStack * kQWarps : 0);
   bool weighted = false;
