@@ -120,6 +120,7 @@ __global__ void k_mean_reduce(const double* __restrict__ msum, int n, int nsplit
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
   double t = 0.0;
+#pragma unroll 8
   for (int sp = 0; sp < nsplit; ++sp) t += msum[(int64_t)sp * n + e];
   mean[e] = t / (double)cnt;
 }
@@ -1355,13 +1356,18 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
   int nsplit = (int)((cnt + 511) / 512);
   if (nsplit > 64) nsplit = 64;
   if (nsplit < 1) nsplit = 1;
+  // the mean is a cheap sum per value: more, shorter splits (64 samples each)
+  // keep more of its gathers in flight
+  int msplit = (int)((cnt + 63) / 64);
+  if (msplit > 256) msplit = 256;
+  if (msplit < 1) msplit = 1;
 
   double *mean = nullptr, *mean_c = nullptr, *msum = nullptr, *partial = nullptr, *M = nullptr;
   int2* pairs = nullptr;
   SiBufs b;
   SFC_TRY(pmalloc(&mean, sizeof(double) * n, st));
   SFC_TRY(pmalloc(&mean_c, sizeof(double) * C * s, st));
-  SFC_TRY(pmalloc(&msum, sizeof(double) * nsplit * n, st));
+  SFC_TRY(pmalloc(&msum, sizeof(double) * msplit * n, st));
   SFC_TRY(pmalloc(&partial, sizeof(double) * nsplit * npairs * kTile * kTile, st));
   SFC_TRY(pmalloc(&M, sizeof(double) * n * n, st));
   SFC_TRY(pmalloc(&pairs, sizeof(int2) * npairs, st));
@@ -1377,10 +1383,10 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
   SFC_TRY(cudaMemcpyAsync(pairs, pairs_h.data(), sizeof(int2) * npairs, cudaMemcpyHostToDevice, st));
 
   count_launch();
-  k_mean_partial<<<dim3((n + 127) / 128, nsplit), 128, 0, st>>>(grid, ix.dict, step, cnt, ix.eoff_all, n, ix.g.ch,
-                                                                  nsplit, msum);
+  k_mean_partial<<<dim3((n + 127) / 128, msplit), 128, 0, st>>>(grid, ix.dict, step, cnt, ix.eoff_all, n, ix.g.ch,
+                                                                  msplit, msum);
   count_launch();
-  k_mean_reduce<<<(n + 127) / 128, 128, 0, st>>>(msum, n, nsplit, cnt, mean);
+  k_mean_reduce<<<(n + 127) / 128, 128, 0, st>>>(msum, n, msplit, cnt, mean);
   count_launch();
   k_cov_partial<<<dim3(npairs, nsplit), 256, 0, st>>>(grid, ix.dict, step, cnt, ix.eoff_all, n, ix.g.ch, nsplit,
                                                       pairs, npairs, partial);
