@@ -10,7 +10,9 @@ batch is every fill-front target of the initial mask (3,597; a seeded cap of
 One step = sfc_index_build (dictionary, PCA, projection, keys, radix sort) +
 sfc_query_batch over the batch, i.e. every row of the hot path but the full scan
 and the fill loop, which are timed in the same run and reported beside it
-("fullscan", "inpaint").  value = queries per second of whole steps.
+("fullscan", "inpaint"), as are the k-NN and Hilbert variants of the step and
+the batched configuration of 256 images ("batch_256", skipped by --no-batch).
+value = queries per second of whole steps.
 Inputs are resident in HBM when a step starts; the L2 is flushed (a 512 MB
 write) between timed steps, outside the timed interval.
 
