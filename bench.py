@@ -63,6 +63,14 @@ def workload_inputs(width=WORKLOAD["width"]):
     return g, m, t
 
 
+def arm_config(Q: int, N: int, world: int) -> dict:
+    """The workload description both arms print (ours and --impl reference)."""
+    return {"workload": "voronoi2d 1024x1024 RGB, 10% disc holes, K=11 (d=363), SFC C=8 D=8 b=16 W=64",
+            "queries_per_step": Q, "dictionary": N, "pca_sample": WORKLOAD["pca_sample"],
+            "step": "sfc_index_build + sfc_query_batch", "l2": "flushed (512 MB write) between steps",
+            "parallelism": f"replica x{world}"}
+
+
 def index_params():
     return dict(K=WORKLOAD["K"], curves=WORKLOAD["curves"], dims=WORKLOAD["dims"], bits=WORKLOAD["bits"],
                 window=WORKLOAD["window"], pca_sample=WORKLOAD["pca_sample"])
@@ -104,6 +112,13 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    import oracle as O
+
+    # the workload's own sizes for the config line (the timed work is the
+    # bounded sample below)
+    g, m, t = workload_inputs()
+    O.build()
+    N = len(O.dict_extract(m, WORKLOAD["K"]))
     for _ in range(args.warmup):
         oracle_sample(crop=64, y0=768, x0=512)
     times, qs = [], []
@@ -116,7 +131,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "voronoi2d 1024x1024 RGB, K=11, C=8, D=8, b=16, W=64 (oracle on a crop)"},
+            "config": arm_config(len(t), N, 1),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -632,10 +647,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "voronoi2d 1024x1024 RGB, 10% disc holes, K=11 (d=363), SFC C=8 D=8 b=16 W=64",
-                       "queries_per_step": Q, "dictionary": N, "pca_sample": WORKLOAD["pca_sample"],
-                       "step": "sfc_index_build + sfc_query_batch", "l2": "flushed (512 MB write) between steps",
-                       "parallelism": f"replica x{world}"},
+            "config": arm_config(Q, N, world),
             "roofline": roofline, "gpu_launches": int(launches), "e2e": e2e, "clocks": clk,
             "query_only": {"qps": query_only_qps, "ms": q_ms_mean},
             "index_build_ms": tot_ms / args.steps - q_ms_mean, "phases_ms": phases_ms,
