@@ -12,10 +12,12 @@
 //     or, with knn = k, find the exact k nearest entries in the quantised space
 //     (Sec. II.D; warp_knn below);
 //  4. bitonic sort + de-duplication of the candidate union in shared memory;
-//  5. filter-and-refine (Fig. 1(d)): FP32 masked-L2 cost of every candidate, one
-//     warp per candidate, each lane holding its patch elements' known flag,
-//     target value and grid offset in registers, gathered reads of the source
-//     patch rows, warp-shuffle sum; block minimum; a single candidate inside
+//  5. filter-and-refine (Fig. 1(d)): FP32 masked-L2 cost of every candidate
+//     over the target's known elements only (compacted in patch order: the
+//     unknown ones add exactly zero), one warp per candidate and two candidates
+//     per pass, each lane holding its elements' target value and grid offset in
+//     registers, gathered reads of the source patch, warp-shuffle sum; block
+//     minimum; a single candidate inside
 //     the FP32 error band is the exact argmin, several (near-ties) are rescored
 //     with the exact FP64 sequential cost and the argmin over (cost, id) taken.
 //     The reported cost is the FP32 cost of the pick.
