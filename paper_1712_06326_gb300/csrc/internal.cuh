@@ -111,10 +111,12 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st);
 // lohi, 2 words per axis of every curve, and lo / scale), then keys.
 int project_curves(Index& ix, const float* grid, float* proj, uint32_t* lohi, int c0, int nc, cudaStream_t st);
 int key_curves(Index& ix, const float* proj, uint64_t* keys, int c0, int nc, cudaStream_t st);
-// The library's auxiliary streams of the current device (k < kAuxStreams),
-// created on first use, non-blocking.
+// The library's auxiliary streams of the current device (k < kAuxStreams,
+// default priority) and one of the highest priority, created on first use,
+// non-blocking; nullptr if a stream cannot be created.
 constexpr int kAuxStreams = 3;
 cudaStream_t aux_stream(int k);
+cudaStream_t aux_stream_hi();
 // Quantised, shifted coordinates of the dictionary in each index's sorted order
 // (the k-NN search reads them next to the sorted keys): ix.sqc from proj.
 int sorted_coords(Index& ix, const float* proj, cudaStream_t st);

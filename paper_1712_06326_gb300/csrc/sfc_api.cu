@@ -171,7 +171,23 @@ cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st) {
 namespace {
 std::mutex g_aux_mu;
 cudaStream_t g_aux[128][kAuxStreams] = {};
+cudaStream_t g_aux_hi[128] = {};
 }  // namespace
+
+cudaStream_t aux_stream_hi() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return nullptr;
+  std::lock_guard<std::mutex> lk(g_aux_mu);
+  if (!g_aux_hi[dev]) {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&g_aux_hi[dev], cudaStreamNonBlocking, greatest) != cudaSuccess) {
+      g_aux_hi[dev] = nullptr;
+      cudaGetLastError();
+    }
+  }
+  return g_aux_hi[dev];
+}
 
 cudaStream_t aux_stream(int k) {
   int dev = 0;
@@ -399,23 +415,30 @@ int dev_in(FileIn& in, T** d, size_t count, cudaStream_t st) {
 }  // namespace
 
 // Projection, keys and sort of every curve, pipelined over groups of curves:
-// group g runs on its own stream (group 0 on st), its projection starts once
-// group g - 1's projection is done, so that the sorts of the earlier groups
-// (latency-bound) overlap the projections of the later ones (FP32-bound).
-// Phase 5 of the trace is marked once every group's keys exist, phase 6 (by
-// the caller) once every sort is done.  st waits for all groups, also on an
-// error, so nothing the caller frees next is still in use.
+// the groups' projections and keys run in order on a high-priority library
+// stream, and each group's sort on one of the library's default-priority
+// streams as soon as its keys exist, so the sorts (latency-bound) fill the SMs
+// around the projections (issue-bound) without holding them up.  Phase 5 of
+// the trace is marked once every group's keys exist, phase 6 (by the caller)
+// once every sort is done.  st waits for all of it, also on an error, so
+// nothing the caller frees next is still in use.
 int project_sort_pipelined(Index& ix, const float* grid, float* proj, uint64_t* keys, uint32_t* lohi,
                            cudaStream_t st) {
   const int C = ix.C;
   const int64_t N = ix.N;
   const int key_bits = std::min(64, ix.D * ix.bp);
-  int G = C < kAuxStreams + 1 ? C : kAuxStreams + 1;
-  cudaStream_t sg[kAuxStreams + 1] = {st};
-  for (int g = 1; g < G; ++g) {
-    sg[g] = aux_stream(g - 1);
-    if (!sg[g]) G = g;  // no stream: fewer groups
+  cudaStream_t hi = aux_stream_hi();
+  cudaStream_t lo[kAuxStreams];
+  int nlo = 0;
+  while (nlo < kAuxStreams && (lo[nlo] = aux_stream(nlo)) != nullptr) ++nlo;
+  if (!hi || nlo == 0) {  // no library streams: everything in order on st
+    SFC_CHECK(project_curves(ix, grid, proj, lohi, 0, C, st));
+    SFC_CHECK(key_curves(ix, proj, keys, 0, C, st));
+    trace_mark(ix, 5, st);
+    return radix_sort_pairs(keys, ix.skeys, ix.sids, N, C, key_bits, st);
   }
+  constexpr int kGroups = 4;
+  int G = C < kGroups ? C : kGroups;
   const int per = (C + G - 1) / G;
   G = (C + per - 1) / per;
   // every group's sort scratch is taken on st before the fork and returned
@@ -423,8 +446,7 @@ int project_sort_pipelined(Index& ix, const float* grid, float* proj, uint64_t* 
   const size_t ws_bytes = radix_sort_scratch_bytes(N, per, key_bits);
   unsigned char* ws = nullptr;
   SFC_TRY(pmalloc(&ws, ws_bytes * G, st));
-  cudaEvent_t ev_fork = nullptr, ev_proj[kAuxStreams + 1] = {}, ev_keys[kAuxStreams + 1] = {},
-              ev_done[kAuxStreams + 1] = {};
+  cudaEvent_t ev_fork = nullptr, ev_hi = nullptr, ev_keys[kGroups] = {}, ev_done[kGroups] = {};
   int rc = SFC_OK;
   auto mk = [&](cudaEvent_t* e) {
     if (rc == SFC_OK && cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) {
@@ -433,42 +455,47 @@ int project_sort_pipelined(Index& ix, const float* grid, float* proj, uint64_t* 
     }
   };
   mk(&ev_fork);
+  mk(&ev_hi);
   for (int g = 0; g < G; ++g) {
-    mk(&ev_proj[g]);
     mk(&ev_keys[g]);
     mk(&ev_done[g]);
   }
-  if (rc == SFC_OK && cudaEventRecord(ev_fork, st) != cudaSuccess) rc = SFC_ECUDA;
-  int launched = 0;
+  bool forked = false;
+  if (rc == SFC_OK && cudaEventRecord(ev_fork, st) == cudaSuccess && cudaStreamWaitEvent(hi, ev_fork, 0) == cudaSuccess)
+    forked = true;
+  else if (rc == SFC_OK)
+    rc = SFC_ECUDA;
+  int sorted = 0;  // groups whose sort stream recorded ev_done
   for (int g = 0; g < G && rc == SFC_OK; ++g) {
     const int c0 = g * per, nc = std::min(per, C - c0);
-    cudaStream_t s = sg[g];
-    if (g > 0 && (cudaStreamWaitEvent(s, ev_fork, 0) != cudaSuccess ||
-                  cudaStreamWaitEvent(s, ev_proj[g - 1], 0) != cudaSuccess)) {
+    rc = project_curves(ix, grid, proj, lohi, c0, nc, hi);
+    if (rc == SFC_OK) rc = key_curves(ix, proj, keys, c0, nc, hi);
+    if (rc == SFC_OK && cudaEventRecord(ev_keys[g], hi) != cudaSuccess) rc = SFC_ECUDA;
+    if (rc != SFC_OK) break;
+    cudaStream_t s = lo[g % nlo];
+    if (cudaStreamWaitEvent(s, ev_keys[g], 0) != cudaSuccess) {
       rc = SFC_ECUDA;
       break;
     }
-    launched = g + 1;
-    rc = project_curves(ix, grid, proj, lohi, c0, nc, s);
-    if (rc == SFC_OK && cudaEventRecord(ev_proj[g], s) != cudaSuccess) rc = SFC_ECUDA;
-    if (rc == SFC_OK) rc = key_curves(ix, proj, keys, c0, nc, s);
-    if (rc == SFC_OK && cudaEventRecord(ev_keys[g], s) != cudaSuccess) rc = SFC_ECUDA;
-    if (rc == SFC_OK)
-      rc = radix_sort_pairs(keys + (size_t)c0 * N, ix.skeys + (size_t)c0 * N, ix.sids + (size_t)c0 * N, N, nc,
-                            key_bits, s, ws + ws_bytes * g);
-    if (cudaEventRecord(ev_done[g], s) != cudaSuccess && rc == SFC_OK) rc = SFC_ECUDA;
+    rc = radix_sort_pairs(keys + (size_t)c0 * N, ix.skeys + (size_t)c0 * N, ix.sids + (size_t)c0 * N, N, nc,
+                          key_bits, s, ws + ws_bytes * g);
+    if (cudaEventRecord(ev_done[g], s) == cudaSuccess)
+      sorted = g + 1;
+    else if (rc == SFC_OK)
+      rc = SFC_ECUDA;
   }
-  if (rc == SFC_OK) {
-    for (int g = 1; g < launched; ++g) cudaStreamWaitEvent(st, ev_keys[g], 0);
-    trace_mark(ix, 5, st);
-  }
-  for (int g = 1; g < launched; ++g) cudaStreamWaitEvent(st, ev_done[g], 0);
+  // join: the high-priority stream's end, then every sort
+  if (forked && cudaEventRecord(ev_hi, hi) == cudaSuccess) cudaStreamWaitEvent(st, ev_hi, 0);
+  if (rc == SFC_OK) trace_mark(ix, 5, st);
+  for (int g = 0; g < sorted; ++g) cudaStreamWaitEvent(st, ev_done[g], 0);
   cudaFreeAsync(ws, st);
-  for (cudaEvent_t e : {ev_fork}) if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : {ev_fork, ev_hi})
+    if (e) cudaEventDestroy(e);
   for (int g = 0; g < G; ++g)
-    for (cudaEvent_t e : {ev_proj[g], ev_keys[g], ev_done[g]})
+    for (cudaEvent_t e : {ev_keys[g], ev_done[g]})
       if (e) cudaEventDestroy(e);
-  if (rc == SFC_ECUDA && sfc_last_error()[0] == 0) set_error(std::string("pipelined build: ") + cudaGetErrorString(cudaGetLastError()));
+  if (rc == SFC_ECUDA && sfc_last_error()[0] == 0)
+    set_error(std::string("pipelined build: ") + cudaGetErrorString(cudaGetLastError()));
   return rc;
 }
 
