@@ -583,6 +583,56 @@ def main():
                    "acceleration_error_mean": float((torch.sqrt(hc_[sel].double()) /
                                                      torch.sqrt(fc.double()).clamp_min(1e-30) - 1.0).mean().item())}
 
+    # ---- the same step with the L1 cost (Sec. III.K) --------------------------
+    l1_prm = dict(prm, cost=sfc.SFC_COST_L1)
+    l1_ms = []
+    for r in range(4):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ixl = sfc.sfc_index_build(gd, md, **l1_prm)
+        sfc.sfc_query_batch(ixl, gd, md, td)
+        b.record(stream)
+        b.synchronize()
+        if r > 0:
+            l1_ms.append(a.elapsed_time(b))
+        ixl.close()
+    sfc_l1 = {"qps": Q / (statistics.mean(l1_ms) / 1000.0), "ms_per_step": statistics.mean(l1_ms)}
+
+    # ---- a stored index: save, load, query (the index built once, reused) ----
+    import tempfile
+
+    st_ms = {"save": [], "load": [], "query": []}
+    with tempfile.TemporaryDirectory() as tmpd:
+        path = os.path.join(tmpd, "index.sfc")
+        ixs = sfc.sfc_index_build(gd, md, **prm)
+        for r in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sfc.sfc_index_save(ixs, path)
+            t1 = time.perf_counter()
+            ixr = sfc.sfc_index_load(path)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lp, lc = sfc.sfc_query_batch(ixr, gd, md, td)
+            b.record(stream)
+            b.synchronize()
+            if r > 0:
+                st_ms["save"].append(1000 * (t1 - t0))
+                st_ms["load"].append(1000 * (t2 - t1))
+                st_ms["query"].append(a.elapsed_time(b))
+            ixr.close()
+        file_mb = os.path.getsize(path) / 1e6
+        ixs.close()
+    stored = {"file_mb": file_mb, "save_ms": statistics.mean(st_ms["save"]),
+              "load_ms": statistics.mean(st_ms["load"]), "query_ms": statistics.mean(st_ms["query"]),
+              "query_qps": Q / (statistics.mean(st_ms["query"]) / 1000.0),
+              "picks_equal_built_index": bool(torch.equal(lp, pick))}
+
     # ---- end to end through the C-ABI with host buffers ----------------------
     gh = torch.from_numpy(g).pin_memory()
     mh = torch.from_numpy(m).pin_memory()
@@ -651,7 +701,8 @@ def main():
             "roofline": roofline, "gpu_launches": int(launches), "e2e": e2e, "clocks": clk,
             "query_only": {"qps": query_only_qps, "ms": q_ms_mean},
             "index_build_ms": tot_ms / args.steps - q_ms_mean, "phases_ms": phases_ms,
-            "fullscan": fullscan, "sfc_knn": sfc_knn, "sfc_hilbert": sfc_hilbert, "inpaint_128x128": inp,
+            "fullscan": fullscan, "sfc_knn": sfc_knn, "sfc_hilbert": sfc_hilbert, "sfc_l1": sfc_l1,
+            "stored_index": stored, "inpaint_128x128": inp,
             "batch_256": batch}
     if rank == 0:
         if not args.no_cpu_baseline:
