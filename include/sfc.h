@@ -249,12 +249,15 @@ int sfc_tc_prescores(const float* grid, const uint8_t* dict_mask, const uint8_t*
  * forbids libraries from allocating behind its back, or a latency-critical
  * caller that cannot afford the implicit synchronisation an allocation may
  * cause.  Arguments, results and errors are those of fullscan_query_batch; the
- * caller still passes every input and output.  All scratch lives in one
+ * caller still passes every input and output.  With SFC_FP16 this entry point
+ * runs the FP32 scan, whose picks and costs the tensor-core form reproduces
+ * bit for bit anyway (its operands would not fit the static array).  All scratch lives in one
  * library-owned static device array of 16 MiB (held by every GPU that loads the
  * library until the process exits); a call whose grid and batch would need more
  * -- about 2 bytes per pixel + 4 bytes per valid centre + 13 bytes per query +
  * 4 bytes per query per 1,024 valid centres -- is rejected with SFC_EINVAL
- * before any device work.  The first call on a device looks up that array's
+ * before any device work (so is any single size beyond the array: more pixels
+ * than bytes, or more than 16 MiB / 13 queries).  The first call on a device looks up that array's
  * device address; make that first call before any stream capture.  All calls
  * share the array and it keeps the last call's contents, so calls that overlap
  * on the GPU (concurrent streams or host threads) race: serialise them.

@@ -504,21 +504,25 @@ void or_keys(const uint32_t* q, int64_t N, int D, int bits, const int32_t* shift
   or_keys_curve(q, N, D, bits, shift, 0, keys);
 }
 
-// The paper's comparator (Sec. II.C listing), with its two typos fixed (the
-// dimension count is passed in; the loop variable is the dimension): the
-// dimension holding the most significant differing bit decides.
-static inline bool less_msb(uint32_t a, uint32_t b) { return a < b && a < (a ^ b); }
+// z-order comparison of two quantised points without forming their keys
+// (Sec. II.C).  The curve reads bit planes from the top and, inside a plane,
+// dimension 0 first, so the first bit at which the two interleaved keys differ
+// is owned by the dimension whose coordinate difference reaches the highest
+// bit position; among dimensions that reach the same position the lowest one
+// is read first.  That dimension's coordinates decide the order.
 int or_zless(const uint32_t* a, const uint32_t* b, int D) {
-  uint32_t so_far = 0;
-  int best = 0;
+  int owner = -1, top = -1;
   for (int d = 0; d < D; ++d) {
-    uint32_t diff = a[d] ^ b[d];
-    if (less_msb(so_far, diff)) {
-      so_far = diff;
-      best = d;
+    const uint32_t x = a[d] ^ b[d];
+    if (x == 0) continue;
+    const int h = 31 - __builtin_clz(x);  // highest differing bit of this axis
+    if (h > top) {                        // strictly higher: ties keep the lower axis
+      top = h;
+      owner = d;
     }
   }
-  return a[best] < b[best] ? 1 : 0;
+  if (owner < 0) return 0;  // equal points
+  return a[owner] < b[owner] ? 1 : 0;
 }
 
 // Sort of the dictionary by z-order (Sec. II.C).  Reading: a stable sort of the

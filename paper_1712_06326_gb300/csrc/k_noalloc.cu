@@ -88,16 +88,36 @@ extern "C" int fullscan_query_batch_static(const float* grid, const uint8_t* dic
       }
       weighted |= v != 1.0f;
     }
+  if (p->precision != SFC_FP32 && p->precision != SFC_FP16) {
+    set_error("fullscan_query_batch_static: precision must be SFC_FP32 or SFC_FP16");
+    return SFC_EUNSUPPORTED;
+  }
   if (p->cost != SFC_COST_L2 && p->cost != SFC_COST_L1) {
     set_error("cost must be SFC_COST_L2 or SFC_COST_L1");
     return SFC_EINVAL;
   }
+  if (p->precision == SFC_FP16 && p->cost != SFC_COST_L2) {
+    set_error("the tensor-core pre-score (SFC_FP16) is an L2 expansion; use SFC_FP32 with SFC_COST_L1");
+    return SFC_EUNSUPPORTED;
+  }
+  // SFC_FP16 runs the FP32 scan here: the tensor-core form's picks and costs
+  // are the FP32 scan's by construction, and its operands would not fit the
+  // static array.
   const int cm = (weighted ? 1 : 0) | (p->cost == SFC_COST_L1 ? 2 : 0);
   // scratch layout (every piece 256-byte aligned), sized by the largest
   // possible dictionary (every valid centre)
   const int64_t npix = g.X * g.Y * g.Z;
   const int64_t nmax = (g.X - g.K + 1) * (g.Y - g.K + 1) * (g.ndim == 3 ? g.Z - g.K + 1 : 1);
   const int64_t ntiles_max = (nmax + 1023) / 1024;
+  // Each factor is bounded by the array size before any product is formed, so
+  // the offsets below cannot wrap around.
+  if (npix > (int64_t)kScratchBytes || nmax > (int64_t)(kScratchBytes / 4) || Q > (int64_t)(kScratchBytes / 13) ||
+      g.n > (int64_t)(kScratchBytes / 4)) {
+    set_error("fullscan_query_batch_static: the grid or the batch is larger than the " +
+              std::to_string(kScratchBytes) + "-byte static scratch allows (use fullscan_query_batch, or fewer "
+              "queries per call)");
+    return SFC_EINVAL;
+  }
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;

@@ -398,14 +398,15 @@ def sfc_tc_prescores(grid: torch.Tensor, dict_mask: torch.Tensor, cur_mask: torc
 
 
 def fullscan_query_batch_static(grid: torch.Tensor, dict_mask: torch.Tensor, cur_mask: torch.Tensor,
-                                centres: torch.Tensor, K: int, ch_weights=None, pick=None, cost=None):
+                                centres: torch.Tensor, K: int, ch_weights=None, pick=None, cost=None,
+                                norm: int = SFC_COST_L2):
     """As fullscan_query_batch, through the entry point that allocates no device memory."""
     grid = _dev(grid, torch.float32)
     dict_mask = _dev(dict_mask, torch.uint8)
     cur_mask = _dev(cur_mask, torch.uint8)
     centres = _dev(centres, torch.int32)
     Q = centres.shape[0]
-    P = Params(K=K, ch_weights=ch_weights)
+    P = Params(K=K, ch_weights=ch_weights, cost=norm)
     g = make_grid(grid)
     if pick is None:
         pick = torch.empty(Q, dtype=torch.int64, device=grid.device)

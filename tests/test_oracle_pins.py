@@ -415,9 +415,9 @@ def test_morton_shift_adds_a_bit():
     assert int(k[0]) == O.morton(np.array([2, 3], np.uint32), 3)
 
 
-def test_paper_comparator_orders_like_morton_keys():
-    # Sec. II.C: comparing via the most significant differing bit is the same
-    # order as comparing full z-addresses
+def test_zorder_comparison_orders_like_morton_keys():
+    # Sec. II.C: deciding by the axis with the highest differing bit gives the
+    # same order as comparing full z-addresses
     rng = np.random.default_rng(11)
     for D in [1, 2, 3, 5, 8]:
         q = rng.integers(0, 256, (300, D)).astype(np.uint32)
