@@ -73,6 +73,7 @@ def lib():
                                          P, P, I32, P, P, P, I64, I64, P, P, P, P, I32]),
                 "or_query_knn": (None, [P, P, I32, P, I32, I32, I32, I32, I32, I32, I32, P, P, I32, P, P, P, P, P,
                                         P, I64, I64, P, P, P, P, I32]),
+                "or_priority": (I32, [P, P, P, I32, P, I32, I32, I64, I32, P]),
                 "or_inpaint": (I64, [P, P, I32, P, I32, I32, I32, I32, P, P, I64, I32, I32, I32, I32, I32, P,
                                      I32, P, P, P, P, P, P, P, I64, P, I32, I32, P]),
             }
@@ -383,6 +384,20 @@ def query_knn(ix, grid, cur_mask, target_lin, k, select=0, weights=None, norm=0)
                        _p(_c(ix["scale"], np.float32)), _p(_c(ix["q"], np.uint32)), _p(_c(ix["dict"], np.int64)),
                        ix["N"], int(target_lin), _p(cand), _p(nc), _p(pick), _p(cost), int(norm))
     return dict(pick=int(pick[0]), cost=float(cost[0]), cand=cand[: int(nc[0])].copy())
+
+
+def priority(grid, mask, K, centre_xy, prio=1, conf=None):
+    """Fill-order terms of one centre (the Criminisi priority the paper defers
+    to, Sec. I) -> dict C, gx, gy, nx, ny, D, P (all float32 values)."""
+    ndim, ext, ch = geometry(grid)
+    terms = np.zeros(7, np.float32)
+    lin = int(centres_to_lin(np.array([centre_xy]), ext)[0])
+    cf = None if conf is None else _c(conf, np.float32)
+    rc = lib().or_priority(_p(_c(grid, np.float32)), _p(_c(mask, np.uint8)), _p(cf), ndim, _p(ext), ch, K, lin,
+                           int(prio), _p(terms))
+    if rc != 0:
+        raise ValueError(f"or_priority: {rc}")
+    return dict(zip(("C", "gx", "gy", "nx", "ny", "D", "P"), (float(v) for v in terms)))
 
 
 def inpaint(grid, mask, K, mode=0, prio=0, ix=None, W=64, select=0, weights=None, max_steps=0, norm=0, knn=0):

@@ -21,7 +21,7 @@
 //   * PCA per index, first D components                      -- Sec. II.A
 //   * quantised coordinates, Morton/z-address, MSB first,
 //     dimension 0 first, highest-variance dimension first   -- Sec. II.C
-//   * z-order comparator via the most significant differing bit -- Sec. II.C
+//   * z-order comparison: the axis with the highest differing bit -- Sec. II.C
 //   * sort by z-order, binary search on the sorted array     -- Sec. II.B, II.C
 //   * filter-and-refine: candidates rescored in image space  -- Fig. 1(d)
 //   * fill front, search area, target area, best index       -- Fig. 1(a)-(c)
@@ -824,6 +824,104 @@ void or_query_dict(const float* dgrid, const int64_t* dext, const float* tgrid, 
   *cost = best;
 }
 
+// Priority of a candidate centre c (reading of the fill order that the paper
+// takes from Criminisi et al., Sec. I and Sec. II.G).  terms[0] = confidence
+// C(p): the patch's confidence values summed one by one in patch raster order
+// (FP32), divided by K^dim.  With prio == 1 (2-D only) the data term follows:
+// terms[1], terms[2] = the grey gradient (g_x, g_y), grey = channel mean (summed
+// left to right, divided by ch); each component is the central difference
+// 0.5 (I(+1) - I(-1)) when both axis neighbours are known, the one-sided
+// difference towards the known neighbour when only one is known and the centre
+// itself is known, else 0 (out of the grid counts as unknown).  terms[3],
+// terms[4] = the unit normal n of the fill front: the central-difference
+// gradient of the mask as 0/1 (out of the grid counts as 1 = known), divided by
+// its IEEE sqrtf norm, or (0, 0) when the norm is 0.  terms[5] = the data term
+// D(p) = |(-g_y) n_x + g_x n_y| (the isophote, the gradient turned by 90
+// degrees, against the normal; alpha = 1).  terms[6] = the priority: C(p) for
+// prio == 0, C(p) (D(p) + 0.001) for prio == 1.  Every product and sum is
+// rounded separately (no fused multiply-add).
+static void prio_terms(const Geo& g, const float* grid, const uint8_t* mask, const float* conf, int64_t c, int prio,
+                       float* terms) {
+  float sum = 0.0f;
+  for (int pp = 0; pp < g.P; ++pp) sum = sum + conf[patch_pixel(g, c, pp)];
+  const float Ct = sum / (float)g.P;
+  for (int i = 0; i < 7; ++i) terms[i] = 0.0f;
+  terms[0] = Ct;
+  terms[6] = Ct;
+  if (prio != 1) return;
+  auto known_at = [&](int64_t x, int64_t y) -> bool {
+    if (x < 0 || y < 0 || x >= g.X || y >= g.Y) return false;
+    return mask[lin_of(g, x, y, 0)] != 0;
+  };
+  auto gray = [&](int64_t q) -> float {
+    if (g.ch == 1) return grid[q];
+    float acc = grid[q * g.ch];
+    for (int k = 1; k < g.ch; ++k) acc = acc + grid[q * g.ch + k];
+    return acc / (float)g.ch;
+  };
+  auto mval = [&](int64_t x, int64_t y) -> float {
+    if (x < 0 || y < 0 || x >= g.X || y >= g.Y) return 1.0f;
+    return mask[lin_of(g, x, y, 0)] ? 1.0f : 0.0f;
+  };
+  int64_t cc[3];
+  coords_of(g, c, cc);
+  const int64_t x = cc[0], y = cc[1];
+  const bool kc = mask[c] != 0;
+  float gxy[2];
+  for (int a = 0; a < 2; ++a) {
+    const int64_t x0 = x - (a == 0), y0 = y - (a == 1), x1 = x + (a == 0), y1 = y + (a == 1);
+    const bool k0 = known_at(x0, y0), k1 = known_at(x1, y1);
+    float gv = 0.0f;
+    if (k0 && k1)
+      gv = 0.5f * (gray(lin_of(g, x1, y1, 0)) - gray(lin_of(g, x0, y0, 0)));
+    else if (kc && k1)
+      gv = gray(lin_of(g, x1, y1, 0)) - gray(c);
+    else if (kc && k0)
+      gv = gray(c) - gray(lin_of(g, x0, y0, 0));
+    gxy[a] = gv;
+  }
+  const float mx = 0.5f * (mval(x + 1, y) - mval(x - 1, y));
+  const float my = 0.5f * (mval(x, y + 1) - mval(x, y - 1));
+  const float mx2 = mx * mx;
+  const float my2 = my * my;
+  const float nrm = std::sqrt(mx2 + my2);
+  float nx = 0.0f, ny = 0.0f;
+  if (nrm > 0.0f) {
+    nx = mx / nrm;
+    ny = my / nrm;
+  }
+  const float t1 = (-gxy[1]) * nx;
+  const float t2 = gxy[0] * ny;
+  const float Dt = std::fabs(t1 + t2);
+  terms[1] = gxy[0];
+  terms[2] = gxy[1];
+  terms[3] = nx;
+  terms[4] = ny;
+  terms[5] = Dt;
+  terms[6] = Ct * (Dt + 0.001f);
+}
+
+// The priority terms of one centre, exposed for tests (conf: npix floats, or
+// NULL = 1 on known pixels and 0 on unknown ones).  Returns -1 for an invalid
+// centre and -2 for prio == 1 outside 2-D.
+int or_priority(const float* grid, const uint8_t* mask, const float* conf, int ndim, const int64_t* ext, int ch,
+                int K, int64_t centre, int prio, float* terms) {
+  Geo g = make_geo(ndim, ext, ch, K);
+  if (prio == 1 && ndim != 2) return -2;
+  if (centre < 0 || centre >= g.X * g.Y * g.Z) return -1;
+  int64_t cc[3];
+  coords_of(g, centre, cc);
+  if (!centre_valid(g, cc[0], cc[1], cc[2])) return -1;
+  std::vector<float> own;
+  if (!conf) {
+    own.resize(g.X * g.Y * g.Z);
+    for (size_t i = 0; i < own.size(); ++i) own[i] = mask[i] ? 1.0f : 0.0f;
+    conf = own.data();
+  }
+  prio_terms(g, grid, mask, conf, centre, prio, terms);
+  return 0;
+}
+
 // ----------------------------------------------------------------------------
 // Inpainting loop (Sec. I; Fig. 1(a)).  Readings:
 //  * fill front: known pixels with an unknown axis-neighbour (4-/6-connected);
@@ -860,20 +958,6 @@ int64_t or_inpaint(float* grid, uint8_t* mask, int ndim, const int64_t* ext, int
   if (mode == 1 && knn > 0 && !qc) return -3;
   std::vector<float> conf(npix);
   for (int64_t i = 0; i < npix; ++i) conf[i] = mask[i] ? 1.0f : 0.0f;
-  auto known_at = [&](int64_t x, int64_t y, int64_t z) -> bool {
-    if (x < 0 || y < 0 || z < 0 || x >= g.X || y >= g.Y || z >= g.Z) return false;
-    return mask[lin_of(g, x, y, z)] != 0;
-  };
-  auto gray = [&](int64_t q) -> float {
-    if (ch == 1) return grid[q];
-    float acc = grid[q * ch];
-    for (int c = 1; c < ch; ++c) acc = acc + grid[q * ch + c];
-    return acc / (float)ch;
-  };
-  auto mval = [&](int64_t x, int64_t y) -> float {
-    if (x < 0 || y < 0 || x >= g.X || y >= g.Y) return 1.0f;
-    return mask[lin_of(g, x, y, 0)] ? 1.0f : 0.0f;
-  };
   int64_t steps = 0;
   std::vector<uint8_t> is_centre(npix);
   std::vector<int64_t> cands;
@@ -912,47 +996,13 @@ int64_t or_inpaint(float* grid, uint8_t* mask, int ndim, const int64_t* ext, int
     float bestC = 0.0f;
     for (int64_t c = 0; c < npix; ++c) {
       if (!is_centre[c]) continue;
-      float sum = 0.0f;
-      for (int pp = 0; pp < g.P; ++pp) sum = sum + conf[patch_pixel(g, c, pp)];
-      float Ct = sum / (float)g.P;
-      float P = Ct;
-      if (prio == 1) {
-        int64_t cc[3];
-        coords_of(g, c, cc);
-        int64_t x = cc[0], y = cc[1];
-        bool kc = mask[c] != 0;
-        float gxy[2];
-        for (int a = 0; a < 2; ++a) {
-          int64_t x0 = x - (a == 0), y0 = y - (a == 1), x1 = x + (a == 0), y1 = y + (a == 1);
-          bool k0 = known_at(x0, y0, 0), k1 = known_at(x1, y1, 0);
-          float gv = 0.0f;
-          if (k0 && k1)
-            gv = 0.5f * (gray(lin_of(g, x1, y1, 0)) - gray(lin_of(g, x0, y0, 0)));
-          else if (kc && k1)
-            gv = gray(lin_of(g, x1, y1, 0)) - gray(c);
-          else if (kc && k0)
-            gv = gray(c) - gray(lin_of(g, x0, y0, 0));
-          gxy[a] = gv;
-        }
-        float mx = 0.5f * (mval(x + 1, y) - mval(x - 1, y));
-        float my = 0.5f * (mval(x, y + 1) - mval(x, y - 1));
-        float mx2 = mx * mx;
-        float my2 = my * my;
-        float nrm = std::sqrt(mx2 + my2);
-        float nx = 0.0f, ny = 0.0f;
-        if (nrm > 0.0f) {
-          nx = mx / nrm;
-          ny = my / nrm;
-        }
-        float t1 = (-gxy[1]) * nx;
-        float t2 = gxy[0] * ny;
-        float Dt = std::fabs(t1 + t2);
-        P = Ct * (Dt + 0.001f);
-      }
+      float terms[7];
+      prio_terms(g, grid, mask, conf.data(), c, prio, terms);
+      const float P = terms[6];
       if (P > bestP) {
         bestP = P;
         bestc = c;
-        bestC = Ct;
+        bestC = terms[0];
       }
     }
     int64_t j;

@@ -384,6 +384,32 @@ def test_projection_selector_basis_is_exact_and_query_skips_unknown():
     assert y[1] == 0.0 and y[0] == np.float32(g[5, 5, 0] - np.float32(0.5))
 
 
+def test_projection_is_a_fused_multiply_add_chain_in_subset_order():
+    # Reading r7 of the projection arithmetic (Sec. II.A leaves it open): the
+    # accumulator is updated by one fused multiply-add per subset value, in
+    # subset order.  Values chosen so that the three plausible readings differ:
+    # B0 = -1, x0 = 1 + 2^-11 gives acc = -(1 + 2^-11) exactly; then
+    # B1 = x1 = 1 + 2^-12, whose exact product 1 + 2^-11 + 2^-24 is not a float.
+    #   fused:            acc + B1 x1 rounded once          = 2^-24
+    #   separate rounding: fl(B1 x1) = 1 + 2^-11 (tie to even) -> 0
+    #   reversed order:   fl(B1 x1) first, then -(1 + 2^-11) -> 0
+    a = np.float32(1 + 2.0 ** -11)
+    b = np.float32(1 + 2.0 ** -12)
+    assert np.float32(b * b) == a  # the product alone rounds to 1 + 2^-11
+    g = np.full((5, 5, 1), 0.5, np.float32)
+    g[1, 1, 0] = a  # patch pixel 0 of the centre (2, 2)
+    g[1, 2, 0] = b  # patch pixel 1
+    m = np.ones((5, 5), np.uint8)
+    sub = np.arange(9, dtype=np.int32)
+    B = np.zeros((9, 1), np.float32)
+    B[0, 0] = -1.0
+    B[1, 0] = b
+    mu = np.zeros(9, np.float32)
+    want = np.float32(2.0 ** -24)
+    assert O.project_query(g, m, 3, 2 * 5 + 2, sub, B, mu, 1)[0] == want
+    assert O.project(g, 3, np.array([2 * 5 + 2]), sub, B, mu, 1)[0, 0] == want
+
+
 def test_quantise_closed_forms():
     y = np.array([[0.0], [1.0], [0.5], [0.25], [-3.0], [9.0]], np.float32)
     lo, sc = O.quant_params(y[:2], 8)
@@ -770,6 +796,88 @@ def test_fill_criminisi_priority_runs():
     g, m = synth.voronoi2d(40, cfg=2, seed_sub=6)
     out, mo, log, steps = O.inpaint(g, m, 5, mode=0, prio=1)
     assert mo.all() and steps > 0
+
+
+def _prio_grid(name, X=16, Y=16):
+    y, x = np.mgrid[0:Y, 0:X].astype(np.float64)
+    if name == "quad":
+        v = x * x / 256 + y / 32
+    else:
+        v = x / 64 + y / 32
+    if name == "ramp_rgb":
+        return np.stack([v + 0.25, v, v - 0.25], -1).astype(np.float32)
+    return v[..., None].astype(np.float32)
+
+
+def _prio_mask(name, X=16, Y=16):
+    y, x = np.mgrid[0:Y, 0:X]
+    unknown = {"vcol10": x >= 10, "diag14": x + y >= 14, "cols8_10": (x == 8) | (x == 10),
+               "col2": (x == 2) & (y >= 4) & (y < 8)}[name]
+    return (~unknown).astype(np.uint8)
+
+
+def _frac(t):
+    s = 1 / np.sqrt(2.0)
+    neg = t.startswith("-")
+    t = t.lstrip("-")
+    if t == "s":
+        v = s
+    elif t.endswith("s/256") or t.endswith("s/64"):
+        num, den = t.split("s/")
+        v = float(num or 1) * s / float(den)
+    elif "/" in t:
+        a, b = t.split("/")
+        v = float(a) / float(b)
+    else:
+        v = float(t)
+    return -v if neg else v
+
+
+def test_criminisi_priority_terms_hand_worked():
+    # Each term of the fill order (Sec. I, Sec. II.G: Criminisi's priority) at
+    # hand-worked pixels: the one-sided difference from the known side, a zero
+    # difference when both neighbours (or the centre) are unknown, the mask
+    # normal of straight and diagonal edges, the channel mean, and D(p) as the
+    # isophote (not the gradient) against the normal.
+    n = 0
+    for line in open(os.path.join(GOLD, "criminisi_priority.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        gname, mname, K, cx, cy, *vals = line.strip().split(";")
+        t = O.priority(_prio_grid(gname), _prio_mask(mname), int(K), (int(cx), int(cy)), prio=1)
+        for key, want in zip(("C", "gx", "gy", "nx", "ny", "D"), vals):
+            assert t[key] == pytest.approx(_frac(want), rel=1e-6, abs=1e-12), (line, key)
+        assert t["P"] == pytest.approx(t["C"] * (t["D"] + 0.001), rel=1e-6)
+        # the confidence-only priority is C(p) alone
+        assert O.priority(_prio_grid(gname), _prio_mask(mname), int(K), (int(cx), int(cy)), prio=0)["P"] == t["C"]
+        n += 1
+    assert n >= 6
+
+
+def test_criminisi_first_target_differs_from_confidence():
+    # 24 x 24 ramp I = x/64 + y/32, square hole [10, 14)^2, K = 3.  Front
+    # centres: top/bottom rows (x = 10..13, y = 9 / 14) and left/right columns
+    # (x = 9 / 14, y = 10..13).  Confidence: 7/9 at the four ends of each side
+    # (two unknown pixels in the patch), 6/9 in between.  CONFIDENCE takes the
+    # lowest linear index among the 7/9 centres: (10, 9).  The data term is
+    # |g_x| = 1/64 on the top and bottom sides (normal (0, -+1)) and |g_y| = 1/32
+    # on the left and right sides (normal (-+1, 0)), so CRIMINISI takes the
+    # lowest linear index among the left/right ends: (9, 10).  (The gradient
+    # instead of the isophote would swap the two sides and pick (10, 9).)
+    g = _prio_grid("ramp", 24, 24)
+    m = np.ones((24, 24), np.uint8)
+    m[10:14, 10:14] = 0
+    _, _, log_c, _ = O.inpaint(g, m, 3, mode=0, prio=0, max_steps=1)
+    _, _, log_k, _ = O.inpaint(g, m, 3, mode=0, prio=1, max_steps=1)
+    assert tuple(log_c[0, :2]) == (10, 9)
+    assert tuple(log_k[0, :2]) == (9, 10)
+    ends = {(10, 9), (13, 9), (10, 14), (13, 14), (9, 10), (9, 13), (14, 10), (14, 13)}
+    for c in ends:
+        t = O.priority(g, m, 3, c, prio=1)
+        assert t["C"] == pytest.approx(7 / 9, rel=1e-7)
+        assert t["D"] == (1 / 32 if c[0] in (9, 14) else 1 / 64)
+    for c in [(11, 9), (9, 11), (12, 14), (14, 12)]:
+        assert O.priority(g, m, 3, c, prio=1)["C"] == pytest.approx(6 / 9, rel=1e-7)
 
 
 def test_empty_dictionary_is_an_error():
