@@ -688,8 +688,6 @@ def main():
         torch.cuda.synchronize()
         if r > 0:
             times.append(1000 * (time.perf_counter() - t0))
-    # (status: SFC_EDEVICE = the eigen-solve's iteration-cap warning on the
-    # flat noise tail of this image's spectrum; the fill itself is unaffected)
     inp["sfc_knn80_paper_settings"] = {"ms": statistics.mean(times), "steps": steps, "status": sfc.sfc_status()}
     ix.close()
     batch = None if args.no_batch else run_batch(sfc, torch, dev, flush, stream)

@@ -58,7 +58,8 @@ enum {
   SFC_ECUDA = -3,        /* a CUDA runtime call failed */
   SFC_ETIMEOUT = -4,     /* a bounded device-side wait gave up */
   SFC_EUNSUPPORTED = -5, /* device is not sm_103 / feature not built */
-  SFC_EDEVICE = -6       /* a kernel flagged invalid data (e.g. a centre outside the grid) */
+  SFC_EDEVICE = -6,      /* a kernel flagged invalid data (e.g. a centre outside the grid) */
+  SFC_ENOCONV = -7       /* a PCA eigen-solve of sfc_index_build did not converge */
 };
 
 enum { SFC_SELECT_ALL = 0, SFC_SELECT_BEST = 1 };
@@ -122,8 +123,13 @@ void sfc_params_default(sfc_params* p);
  * given, FP32 projection, per-axis
  * quantisation to b bits, Morton keys (top 64 bits), and a stable radix sort of
  * (key, id) per index.  grid/dict_mask: device, layout above.  On success *out
- * owns device memory until sfc_index_destroy.  Synchronises `stream` once (to
- * learn the dictionary size).  SFC_EINVAL if the dictionary is empty. */
+ * owns device memory until sfc_index_destroy.  Synchronises `stream` once to
+ * learn the dictionary size and, when it computes the PCA, once more at the
+ * end to confirm that every eigen-solve converged.  Subsets of up to 64 values
+ * are solved completely by FP64 Jacobi; longer ones by subspace iteration,
+ * taken over by Jacobi (up to 112 values) where the iteration stalls.
+ * SFC_EINVAL if the dictionary is empty; SFC_ENOCONV (no index is returned) if
+ * an eigen-solve did not converge. */
 int sfc_index_build(const float* grid, const uint8_t* dict_mask, const sfc_grid* g, const sfc_params* p,
                     void* stream, sfc_index** out);
 
@@ -280,8 +286,7 @@ int inpaint_run(float* grid, uint8_t* mask, const sfc_grid* g, const sfc_params*
 
 /* Read and clear the library's device-side status flags (synchronises stream):
  * SFC_OK, SFC_ETIMEOUT (a bounded wait gave up), or SFC_EDEVICE (an invalid
- * centre was seen, a PCA eigen-solve hit its iteration cap, or a fill step made
- * no progress). */
+ * centre was seen, or a fill step made no progress). */
 int sfc_status(void* stream);
 
 /* Number of kernels the library has launched in this process so far (all host

@@ -8,7 +8,7 @@
 namespace sfc {
 
 // Device-side status bits (ORed into a library-owned word, read by sfc_status).
-enum : uint32_t { ST_BAD_CENTRE = 1u, ST_TIMEOUT = 2u, ST_OVERFLOW = 4u, ST_NOCONV = 8u };
+enum : uint32_t { ST_BAD_CENTRE = 1u, ST_TIMEOUT = 2u, ST_OVERFLOW = 4u };
 
 // Upper bound of the spin iterations of any wait on another CTA's flag.
 constexpr long long kSpinLimit = 1ll << 24;

@@ -86,6 +86,7 @@ struct Index {
   int p_block = 0;             // subspace block size
   int* eig_iters = nullptr;    // 2C (device): FP64 then FP32 products A Q computed per index
   int eig_per_orth = 1;        // products per orthonormalisation (2 on the cluster path)
+  int* pca_done = nullptr;     // C (device): 1 where the eigen-solve converged (PCA builds only)
 };
 
 // Record phase boundary k of a traced build (no-op otherwise).

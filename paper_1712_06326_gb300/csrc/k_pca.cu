@@ -37,8 +37,10 @@
 // convergence is tested on FP64 products only; otherwise one launch per iteration
 // computes Y = A Q with every curve's rows spread over the GPU and a second (one
 // CTA per curve) does the p-sized work, a device-side flag ending the iteration
-// early.  A curve that has not converged within the iteration cap raises
-// ST_NOCONV.  Jacobi rotation angles are taken in FP32 and the
+// early.  For s <= kSJacobi the whole s x s problem is solved by Jacobi
+// instead (k_eig_full), and for s <= kSFull Jacobi also takes over every curve
+// the iteration left unconverged; a curve that is still unconverged is
+// reported by the build (SFC_ENOCONV).  Jacobi rotation angles are taken in FP32 and the
 // rotation made orthogonal to FP64 precision by a Newton step for
 // 1/sqrt(1 + t^2) (no FP64 division or square root in the loop).  Eigenvectors
 // are ordered by descending eigenvalue and signed so that the component of
@@ -561,7 +563,64 @@ __global__ void k_pca_finalize(SiBufs b, const double* __restrict__ mean, int s,
     const double sg = X[(int64_t)imax * p + k] < 0.0 ? -1.0 : 1.0;
     for (int i = 0; i < s; ++i) basis[((int64_t)c * s + i) * D + k] = (float)(sg * X[(int64_t)i * p + k]);
   }
-  if (threadIdx.x == 0 && !b.done[c]) atomicOr(status, ST_NOCONV);
+}
+
+// Full eigen-decomposition of each index's s x s covariance (s <= kSFull) by
+// the parallel-order Jacobi method above, one CTA per curve, everything in
+// shared memory.  Used instead of the subspace iteration when s <= kSJacobi
+// (the cost, ~s^3 per sweep, is then below the iteration's), and after it for
+// kSJacobi < s <= kSFull on the curves the iteration left unconverged
+// (only_unconverged = 1): a flat tail of the spectrum (a noise floor, where
+// l_{p+1} / l_D is close to 1) stalls the iteration but not Jacobi.  Writes the
+// leading p eigenpairs (descending; ties to the lower column) into X and e and
+// done[c] = 1 when the off-diagonal norm fell below 1e-14 of the whole.
+constexpr int kSJacobi = 64;
+constexpr int kSFull = 112;
+
+__global__ void __launch_bounds__(256) k_eig_full(SiBufs b, int s, int p, int only_unconverged) {
+  const int c = blockIdx.x;
+  if (only_unconverged && b.done[c]) return;
+  const int np = s + (s & 1);
+  extern __shared__ double sm[];
+  double* H = sm;            // np*np
+  double* W = H + np * np;   // np*np
+  double* al = W + np * np;  // np
+  double* be = al + np;      // np
+  int* ord = reinterpret_cast<int*>(be + np);  // np
+  __shared__ double red[8];
+  const double* A = b.A + (int64_t)c * s * s;
+  for (int t = threadIdx.x; t < np * np; t += blockDim.x) {
+    const int i = t / np, j = t % np;
+    H[t] = (i < s && j < s) ? A[(int64_t)i * s + j] : 0.0;
+  }
+  __syncthreads();
+  small_jacobi(H, W, np, al, be, red);
+  double off = 0.0, all = 0.0;
+  for (int t = threadIdx.x; t < np * np; t += blockDim.x) {
+    const double v = H[t] * H[t];
+    all += v;
+    if (t / np != t % np) off += v;
+  }
+  off = block_sum(off, red);
+  all = block_sum(all, red);
+  // order the s eigenvalues descending (the zero padding column excluded)
+  for (int k = threadIdx.x; k < s; k += blockDim.x) {
+    const double ek = H[k * np + k];
+    int r = 0;
+    for (int j = 0; j < s; ++j) {
+      const double ej = H[j * np + j];
+      if (ej > ek || (ej == ek && j < k)) ++r;
+    }
+    ord[r] = k;
+  }
+  __syncthreads();
+  double* X = b.X + (int64_t)c * s * p;
+  for (int t = threadIdx.x; t < s * p; t += blockDim.x) {
+    const int i = t / p, k = t % p;
+    X[t] = W[i * np + ord[k]];
+  }
+  if (threadIdx.x < p) b.e[(int64_t)c * p + threadIdx.x] = H[ord[threadIdx.x] * np + ord[threadIdx.x]];
+  if (threadIdx.x == 0) b.done[c] = (off <= 1e-28 * all || off == 0.0) ? 1 : 0;
 }
 
 // ----------------------------------------------------------------------------
@@ -1407,10 +1466,14 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
     SFC_TRY(cudaFuncSetAttribute(k_si_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_small));
   if (shm_gemm > kSmemOptIn)
     SFC_TRY(cudaFuncSetAttribute(k_si_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_gemm));
+  const int npf = s + (s & 1);
+  const size_t shm_full = sizeof(double) * (2 * (size_t)npf * npf + 2 * npf) + sizeof(int) * npf;
+  if (s <= kSFull && shm_full > kSmemOptIn)
+    SFC_TRY(cudaFuncSetAttribute(k_eig_full, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_full));
   // cluster path: 16 CTAs per curve when such clusters can be scheduled, else 8
   int cs = 0, use32 = 0;
   size_t shm_cl = 0;
-  for (int opt = 0; opt < 4 && cs == 0; ++opt) {
+  for (int opt = 0; opt < 4 && cs == 0 && s > kSJacobi; ++opt) {
     // preference: 16-CTA clusters with the FP32 copies, without them, then 8
     const int cand = opt < 2 ? 16 : 8;
     const bool w32 = (opt & 1) == 0;
@@ -1442,7 +1505,10 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
     use32 = w32 ? 1 : 0;
     shm_cl = need;
   }
-  if (cs) {
+  if (s <= kSJacobi) {
+    count_launch();
+    k_eig_full<<<C, 256, shm_full, st>>>(b, s, p, 0);
+  } else if (cs) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C * cs);
     cfg.blockDim = dim3(256);
@@ -1474,6 +1540,11 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
       k_si_small<<<C, 256, shm_small, st>>>(b, s, p, D);
     }
   }
+  if (s > kSJacobi && s <= kSFull) {
+    // the curves the iteration left unconverged (returns at once for the others)
+    count_launch();
+    k_eig_full<<<C, 256, shm_full, st>>>(b, s, p, 1);
+  }
   SFC_TRY(cudaGetLastError());
   trace_mark(ix, 3, st);
   count_launch();
@@ -1490,7 +1561,7 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
   cudaFreeAsync(b.Y, st);
   cudaFreeAsync(b.X, st);
   cudaFreeAsync(b.e, st);
-  cudaFreeAsync(b.done, st);
+  ix.pca_done = b.done;  // read by the build once the device is done with it
   return SFC_OK;
 }
 

@@ -326,8 +326,9 @@ int upload(T** dst, const T* src, size_t count, cudaStream_t st) {
 void free_index(Index& ix) {
   cudaDeviceSynchronize();
   trace_fold(ix);
-  void* ptrs[] = {ix.dict,  ix.eoff_all, ix.sub_eoff, ix.sub_pix, ix.weights, ix.basis, ix.mean, ix.evals,
-                  ix.lo,    ix.scale,    ix.shifts,   ix.proj,    ix.keys,    ix.skeys, ix.sids, ix.sqc};
+  void* ptrs[] = {ix.dict,  ix.eoff_all, ix.sub_eoff, ix.sub_pix, ix.weights, ix.basis, ix.mean,      ix.evals,
+                  ix.lo,    ix.scale,    ix.shifts,   ix.proj,    ix.keys,    ix.skeys, ix.sids,       ix.sqc,
+                  ix.eig_iters, ix.pca_done};
   cudaDeviceSynchronize();
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, nullptr);
@@ -633,6 +634,19 @@ int build_index(const float* grid, const uint8_t* dict_mask, const sfc_grid* gp,
     cudaFreeAsync(keys, st);
   }
   SFC_TRY(cudaGetLastError());
+  if (ix.pca_done) {
+    // every eigen-solve must have converged: wait for the build, then read the flags
+    std::vector<int> done(C, 0);
+    SFC_TRY(cudaMemcpyAsync(done.data(), ix.pca_done, sizeof(int) * C, cudaMemcpyDeviceToHost, st));
+    SFC_TRY(cudaStreamSynchronize(st));
+    for (int c = 0; c < C; ++c)
+      if (!done[c]) {
+        set_error("the PCA eigen-solve of index " + std::to_string(c) + " (subset length " + std::to_string(s) +
+                  ", D = " + std::to_string(D) + ") did not converge: the covariance spectrum is too flat "
+                  "beyond the D-th eigenvalue for the iteration; give a basis, or fewer dimensions");
+        return SFC_ENOCONV;
+      }
+  }
   return SFC_OK;
 }
 
@@ -1225,10 +1239,6 @@ int sfc_status(void* stream) {
   if (v & ST_TIMEOUT) {
     set_error("a bounded device-side wait timed out");
     return SFC_ETIMEOUT;
-  }
-  if (v & ST_NOCONV) {
-    set_error("a PCA eigen-solve stopped before its residual test passed (basis less accurate)");
-    return SFC_EDEVICE;
   }
   if (v & ST_OVERFLOW) {
     set_error("the fill loop stopped: a step filled no pixel");

@@ -16,7 +16,8 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libsfc.so")
 
-SFC_OK, SFC_EINVAL, SFC_ENOMEM, SFC_ECUDA, SFC_ETIMEOUT, SFC_EUNSUPPORTED, SFC_EDEVICE = 0, -1, -2, -3, -4, -5, -6
+SFC_OK, SFC_EINVAL, SFC_ENOMEM, SFC_ECUDA, SFC_ETIMEOUT, SFC_EUNSUPPORTED, SFC_EDEVICE, SFC_ENOCONV = (
+    0, -1, -2, -3, -4, -5, -6, -7)
 SFC_SELECT_ALL, SFC_SELECT_BEST = 0, 1
 SFC_FP32, SFC_BF16, SFC_FP16 = 0, 1, 2
 SFC_PRIO_CONFIDENCE, SFC_PRIO_CRIMINISI = 0, 1

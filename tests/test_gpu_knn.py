@@ -124,6 +124,13 @@ def test_knn_deep_recursion_256(S):
     assert oix["N"] > 40_000
 
 
+def principal_sin_max(B1, B2):
+    """sin of the largest principal angle between the column spaces of B1 and B2."""
+    Q1 = np.linalg.qr(np.asarray(B1, np.float64))[0]
+    Q2 = np.linalg.qr(np.asarray(B2, np.float64))[0]
+    return np.linalg.norm(Q2 - Q1 @ (Q1.T @ Q2), 2)
+
+
 @pytest.mark.parametrize("priority", [0, 1])
 def test_fill_with_the_papers_defaults_bit_identical(S, priority):
     # the fill loop of Sec. I run with the settings of the paper's evaluation
@@ -135,9 +142,15 @@ def test_fill_with_the_papers_defaults_bit_identical(S, priority):
     ix = S.sfc_index_build(dev(g), dev(m), K=K, curves=C_, dims=D, bits=bits, window=16, pca_sample=0, knn=k)
     ex = S.sfc_index_export(ix)
     ix.close()
-    # the image's noise leaves a flat tail of eigenvalues, so the tenth
-    # component may stop at the iteration cap (a warning, read and cleared here)
-    assert S.sfc_status() in (0, S.SFC_EDEVICE)
+    assert S.sfc_status() == 0
+    # the image's noise leaves a flat tail of eigenvalues (l_11 / l_10 ~ 0.99):
+    # the basis is still the oracle's -- eigenvalues within 1e-10 relative and
+    # every principal angle between the D-dimensional subspaces below 1e-6
+    d = ex["dict"]
+    for cv in range(C_):
+        B, mu, ev, cov = O.pca(g, K, d, ex["subsets"][cv], 0, D)
+        assert np.allclose(ex["evals"][cv][:D], ev[:D], rtol=1e-10, atol=0)
+        assert principal_sin_max(ex["basis"][cv], B) < 1e-6
     oix = O.build_index(g, m, K, C_, D, bits, basis=ex["basis"], mean=ex["mean"])
     og, om, olog, osteps = O.inpaint(g, m, K, mode=1, prio=priority, ix=oix, knn=k)
     gd, md = dev(g), dev(m)

@@ -268,7 +268,7 @@ def test_query_exact_ties_and_constant_grid(S):
     m = np.ones((40, 40), np.uint8)
     N = len(O.dict_extract(m, 5))
     ix = S.sfc_index_build(dev(g), dev(m), K=5, curves=2, dims=3, bits=8, window=N, pca_sample=0)
-    S.sfc_status()  # white-noise data has no eigen-gap: a PCA cap warning is expected here
+    assert S.sfc_status() == 0  # white noise has no eigen-gap; the 15-value subsets are solved by Jacobi
     t = np.array([[32, 32], [4, 22], [5, 5], [20, 20]], np.int32)
     pk, cs = S.sfc_query_batch(ix, dev(g), dev(m), dev(t))
     d = O.dict_extract(m, 5)
