@@ -16,6 +16,16 @@ value = queries per second of whole steps.
 Inputs are resident in HBM when a step starts; the L2 is flushed (a 512 MB
 write) between timed steps, outside the timed interval.
 
+Also reported, outside the timed steps: the same step with the covariance over
+every dictionary entry ("pca_sample_all"), the fill loop run to completion on
+the workload ("inpaint_1024"), the 256^3 and 512^3 configurations ("volumes",
+skipped by --no-3d), and, on rank 0, the oracle timed on the host cores
+("cpu_baseline": one thread and all workers on a 256^2 tile, its full scan on
+sampled targets) together with the parity record of this run's results
+("parity": the oracle's index rebuilt from the GPU's basis with its sorted
+arrays compared, every query's pick and candidate set, sampled full-scan picks
+and the first fill steps).
+
 Multi-GPU (torchrun): queries are independent, so every rank runs its own copy of
 the workload (weak scaling, no data-path collective); the step time is the max
 over ranks.  ``--impl reference`` times the CPU oracle instead (rank 0 only).
@@ -71,41 +81,150 @@ def arm_config(Q: int, N: int, world: int) -> dict:
             "parallelism": f"replica x{world}"}
 
 
+def known_values(m, t, K, ch):
+    """Known values in each target's patch (the rescore and the method's cost
+    read only these)."""
+    r = K // 2
+    ii = np.pad(m.astype(np.int64), ((1, 0), (1, 0))).cumsum(0).cumsum(1)
+    x, y = t[:, 0].astype(np.int64), t[:, 1].astype(np.int64)
+    s = ii[y + r + 1, x + r + 1] - ii[y - r, x + r + 1] - ii[y + r + 1, x - r] + ii[y - r, x - r]
+    return s * ch
+
+
 def index_params():
     return dict(K=WORKLOAD["K"], curves=WORKLOAD["curves"], dims=WORKLOAD["dims"], bits=WORKLOAD["bits"],
                 window=WORKLOAD["window"], pca_sample=WORKLOAD["pca_sample"])
 
 
 # ----------------------------------------------------------------------------
-# CPU oracle baseline (bounded sample of the same workload)
+# CPU oracle legs: the timed baseline (a bounded tile of the workload) and the
+# parity record of the GPU's full-size results (outside every timed region)
 # ----------------------------------------------------------------------------
-def oracle_sample(crop=256, y0=768, x0=512):
-    """The oracle as it stands on a crop of the workload: by default the 256x256
-    tile holding the most fill-front targets (482 of the 3,597), with its full
-    8-curve index build and every front-target query of the tile, one thread."""
-    import oracle as O
+# the 256x256 tile of the workload holding the most fill-front targets
+TILE = dict(crop=256, y0=768, x0=512)
+
+
+def tile_inputs(crop=TILE["crop"], y0=TILE["y0"], x0=TILE["x0"]):
     from paper_1712_06326_gb300 import synth
 
     g, m, _ = workload_inputs()
     g = np.ascontiguousarray(g[y0:y0 + crop, x0:x0 + crop])
     m = np.ascontiguousarray(m[y0:y0 + crop, x0:x0 + crop])
     t = synth.front_targets(m, WORKLOAD["K"])
-    O.build()
-    t0 = time.perf_counter()
-    ix = O.build_index(g, m, WORKLOAD["K"], WORKLOAD["curves"], WORKLOAD["dims"], WORKLOAD["bits"],
-                       sample=WORKLOAD["pca_sample"])
+    return g, m, t
+
+
+def tile_description(N, Q):
+    return (f"{TILE['crop']}x{TILE['crop']} tile at (x={TILE['x0']}, y={TILE['y0']}) of the workload image "
+            f"(N={N} dictionary patches, Q={Q} front targets): 8-curve index build (own PCA, "
+            f"{WORKLOAD['pca_sample']}-entry sample) + every front-target query")
+
+
+def oracle_tile(pool=None, workers=1, inputs=None):
+    """The oracle as it stands on the tile: index build + all queries; one
+    thread, or (pool) the indices and the queries spread over `workers`
+    processes.  -> (queries/s, seconds, N, Q)."""
+    import oracle as O
+    from oracle import parallel as OP
+
+    g, m, t = inputs if inputs is not None else tile_inputs()
     lin = O.centres_to_lin(t, O.geometry(g)[1])
-    for tl in lin:
-        O.query(ix, g, m, tl, WORKLOAD["window"])
+    args = (g, m, WORKLOAD["K"], WORKLOAD["curves"], WORKLOAD["dims"], WORKLOAD["bits"])
+    t0 = time.perf_counter()
+    if pool is None:
+        ix = O.build_index(*args, sample=WORKLOAD["pca_sample"])
+        for tl in lin:
+            O.query(ix, g, m, tl, WORKLOAD["window"])
+    else:
+        ix = OP.build_index(pool, *args, sample=WORKLOAD["pca_sample"])
+        OP.query_batch(pool, workers, ix, g, m, lin, WORKLOAD["window"])
     dt = time.perf_counter() - t0
-    sample = (f"{crop}x{crop} tile at (x={x0}, y={y0}) of the workload: N={ix['N']}, Q={len(t)} front targets, "
-              "8-curve index build + all queries")
-    return len(t) / dt, dt, sample
+    return len(t) / dt, dt, int(ix["N"]), len(t)
 
 
-def cpu_baseline_obj():
-    v, dt, sample = oracle_sample()
-    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, "seconds": dt}
+def lscpu_info():
+    info = {"model": None, "cpus": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            k, _, v = ln.partition(":")
+            if k.strip() == "Model name":
+                info["model"] = v.strip()
+            elif k.strip() == "CPU(s)":
+                info["cpus"] = int(v.strip())
+    except (OSError, ValueError, subprocess.SubprocessError):
+        pass
+    return info
+
+
+def cpu_baseline_obj(gpu):
+    """The oracle timed on the host cores (one thread, then all workers) on the
+    tile, and its full scan on seeded targets of the full workload; its results
+    on the full workload also give the parity record of the GPU's: the index
+    rebuilt from the GPU's basis (sorted arrays bit-exact), every query's pick
+    and candidate set, and the full-scan picks of the sampled targets."""
+    import oracle as O
+    from oracle import parallel as OP
+
+    O.build()
+    inputs = tile_inputs()
+    v1, dt1, Nt, Qt = oracle_tile(inputs=inputs)
+    workers = OP.default_workers()
+    pool = OP.make_pool(workers)
+    try:
+        vp, dtp, _, _ = oracle_tile(pool, workers, inputs=inputs)
+        g, m, t = gpu["g"], gpu["m"], gpu["t"]
+        lin = O.centres_to_lin(t, O.geometry(g)[1])
+        dct = gpu["ex"]["dict"]
+        # full scan: one thread on 4 of the GPU's full-scan targets, all workers on 8 per worker
+        fs_sel = gpu["fs_sel"]
+        t0 = time.perf_counter()
+        p1, _ = O.fullscan(g, m, WORKLOAD["K"], dct, lin[fs_sel[:4]])
+        fs1 = 4 / (time.perf_counter() - t0)
+        nfs = min(len(fs_sel), 8 * workers)
+        t0 = time.perf_counter()
+        pp, cp = OP.fullscan(pool, workers, g, m, WORKLOAD["K"], dct, lin[fs_sel[:nfs]])
+        fsp = nfs / (time.perf_counter() - t0)
+        fs_equal = int(np.sum(pp == gpu["fs_pick"][:nfs]))
+        # parity of the headline step's results (untimed)
+        ex = gpu["ex"]
+        t0 = time.perf_counter()
+        oix = OP.build_index(pool, g, m, WORKLOAD["K"], WORKLOAD["curves"], WORKLOAD["dims"], WORKLOAD["bits"],
+                             basis=ex["basis"], mean=ex["mean"])
+        arrays_equal = int(sum(np.array_equal(oix["skeys"][c], ex["skeys"][c]) and
+                               np.array_equal(oix["sids"][c], ex["sids"][c]) for c in range(WORKLOAD["curves"])))
+        op, oc, ocand = OP.query_batch(pool, workers, oix, g, m, lin, WORKLOAD["window"])
+        cand, nc = gpu["cand"], gpu["ncand"]
+        cand_equal = int(sum(np.array_equal(cand[i, : nc[i]], ocand[i]) for i in range(len(t))))
+        rel = np.abs(gpu["cost"].astype(np.float64) - oc) / np.maximum(np.abs(oc), 1e-300)
+        # the oracle's fill loop on the same image, from the same index, for a
+        # bounded number of steps: every step's (target, pick) must be the GPU's
+        nfill = min(10, len(gpu["fill_log"]))
+        t1 = time.perf_counter()
+        _, _, olog, _ = O.inpaint(g, m, WORKLOAD["K"], mode=1, prio=0, ix=oix, W=WORKLOAD["window"],
+                                  max_steps=nfill)
+        fill_ms = 1000 * (time.perf_counter() - t1) / max(nfill, 1)
+        parity = {"fill_steps_checked": int(nfill),
+                  "fill_steps_equal": int(np.sum(np.all(olog[:nfill] == gpu["fill_log"][:nfill], axis=1))),
+                  "queries_checked": int(len(t)), "picks_equal": int(np.sum(op == gpu["pick"])),
+                  "candidate_sets_equal": cand_equal, "max_cost_rel_err": float(rel.max()),
+                  "sorted_arrays_equal": arrays_equal, "sorted_arrays_checked": WORKLOAD["curves"],
+                  "fullscan_checked": int(nfs), "fullscan_picks_equal": fs_equal,
+                  "fullscan_1core_picks_equal": int(np.sum(p1 == gpu["fs_pick"][:4])),
+                  "oracle": "index rebuilt from the GPU's exported basis (the oracle's own projections, keys and "
+                            "sorts); full scan by brute force",
+                  "seconds": time.perf_counter() - t0}
+    finally:
+        pool.shutdown()
+    cpu = lscpu_info()
+    return {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": tile_description(Nt, Qt) + ", one thread", "seconds": dt1,
+            "all_cores": {"value": vp, "cores": workers, "seconds": dtp,
+                          "how": "indices and queries spread over spawned worker processes"},
+            "inpaint_1024_ms_per_step_1core": fill_ms,
+            "fullscan": {"qps_1core": fs1, "qps_all_cores": fsp, "queries_all_cores": int(nfs),
+                         "sample": "seeded targets of the full 1024x1024 workload (N=%d)" % len(dct)},
+            "cpu_model": cpu["model"], "host_cpus": cpu["cpus"]}, parity
 
 
 def run_reference(args):
@@ -114,25 +233,27 @@ def run_reference(args):
         return 0
     import oracle as O
 
-    # the workload's own sizes for the config line (the timed work is the
-    # bounded sample below)
-    g, m, t = workload_inputs()
     O.build()
-    N = len(O.dict_extract(m, WORKLOAD["K"]))
+    inputs = tile_inputs()
     for _ in range(args.warmup):
-        oracle_sample(crop=64, y0=768, x0=512)
+        oracle_tile(inputs=tile_inputs(crop=64))
     times, qs = [], []
-    sample = ""
+    N = Q = 0
     for _ in range(args.steps):
-        v, dt, sample = oracle_sample()
+        v, dt, N, Q = oracle_tile(inputs=inputs)
         times.append(dt)
-        qs.append(v * dt)
+        qs.append(Q)
     value = sum(qs) / sum(times)
+    cfg = {"workload": "voronoi2d 1024x1024 RGB, 10% disc holes, K=11 (d=363), SFC C=8 D=8 b=16 W=64; timed on "
+                       f"the {TILE['crop']}x{TILE['crop']} tile at (x={TILE['x0']}, y={TILE['y0']})",
+           "queries_per_step": Q, "dictionary": N, "pca_sample": WORKLOAD["pca_sample"],
+           "step": "oracle index build + all front-target queries of the tile", "parallelism": "one host thread"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
-            "config": arm_config(len(t), N, 1),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": tile_description(N, Q) + ", one thread"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -333,6 +454,108 @@ def run_batch(sfc, torch, dev, flush, stream):
             "acceleration_error_mean": ae, "input_generation_s": gen_s}
 
 
+def principal_sin_max(B1, B2):
+    """sin of the largest principal angle between the column spaces of B1 and B2."""
+    Q1 = np.linalg.qr(np.asarray(B1, np.float64))[0]
+    Q2 = np.linalg.qr(np.asarray(B2, np.float64))[0]
+    return float(np.linalg.norm(Q2 - Q1 @ (Q1.T @ Q2), 2))
+
+
+def pca_sample_comparison(sfc, torch, gd, md, td, prm, flush, stream, ex_h, fp, fc, sel, step_ms):
+    """The headline step with the covariance over every dictionary entry
+    (pca_sample = all) instead of the 16,384-entry sample: its step time, the
+    largest principal angle between the two bases per index, and the quality of
+    both against the exact full-scan picks of the 2,048 sampled targets."""
+    prm_all = dict(prm, pca_sample=0)
+    ms = []
+    for r in range(4):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ixa = sfc.sfc_index_build(gd, md, **prm_all)
+        pa, ca = sfc.sfc_query_batch(ixa, gd, md, td)
+        b.record(stream)
+        b.synchronize()
+        if r > 0:
+            ms.append(a.elapsed_time(b))
+        if r < 3:
+            ixa.close()
+    exa = sfc.sfc_index_export(ixa)
+    ixa.close()
+    sins = [principal_sin_max(ex_h["basis"][c], exa["basis"][c]) for c in range(len(exa["basis"]))]
+    fcd = torch.sqrt(fc.double()).clamp_min(1e-30)
+    return {"ms_per_step": statistics.mean(ms), "ms_per_step_16384": step_ms,
+            "max_principal_angle_sin_per_index": sins,
+            "pick_agreement_fullscan": float((pa[sel] == fp).double().mean().item()),
+            "acceleration_error_mean": float((torch.sqrt(ca[sel].double()) / fcd - 1.0).mean().item())}
+
+
+VOLUMES = {
+    "spheres3d_256": dict(size=256, cfg=3, block=8, missing=0.15, salt=0.0, K=7, curves=8, dims=12, bits=21,
+                          window=128, pca_sample=16384, cap=131072),
+    "spheres3d_512": dict(size=512, cfg=5, block=16, missing=0.20, salt=0.05, K=9, curves=8, dims=8, bits=8,
+                          window=256, pca_sample=65536, cap=131072),
+}
+
+
+def volume_case(name):
+    from paper_1712_06326_gb300 import synth
+
+    v = VOLUMES[name]
+    g, m = synth.spheres3d(v["size"], cfg=v["cfg"], block=v["block"], missing=v["missing"], salt=v["salt"])
+    t = synth.front_targets(m, v["K"], cap=v["cap"], cfg=v["cfg"])
+    return name, g, m, t
+
+
+def run_volumes(sfc, torch, dev, flush, stream):
+    """The 3-D configurations: a step = sfc_index_build + sfc_query_batch over the
+    front targets (capped at 131,072 by seeded sampling), like the headline."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    t0 = time.perf_counter()
+    with cf.ProcessPoolExecutor(max_workers=2, mp_context=mp.get_context("spawn")) as ex:
+        cases = list(ex.map(volume_case, list(VOLUMES)))
+    gen_s = time.perf_counter() - t0
+    out = {"input_generation_s": gen_s}
+    for name, g, m, t in cases:
+        v = VOLUMES[name]
+        prm = {k: v[k] for k in ("K", "curves", "dims", "bits", "window", "pca_sample")}
+        gd = torch.from_numpy(np.ascontiguousarray(g)).to(dev)
+        md = torch.from_numpy(np.ascontiguousarray(m)).to(dev)
+        td = torch.from_numpy(np.ascontiguousarray(t)).to(dev)
+        del g
+        st_ms, q_ms = [], []
+        for r in range(3):  # the first step is untimed
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            mid = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ix = sfc.sfc_index_build(gd, md, **prm)
+            mid.record(stream)
+            sfc.sfc_query_batch(ix, gd, md, td)
+            b.record(stream)
+            b.synchronize()
+            if r > 0:
+                st_ms.append(a.elapsed_time(b))
+                q_ms.append(mid.elapsed_time(b))
+            N = ix.N
+            ix.close()
+        Q = len(t)
+        out[name] = {"workload": f"{v['size']}^3 spheres, {int(v['missing'] * 100)}% missing {v['block']}^3 blocks"
+                                 + (f", {int(v['salt'] * 100)}% salt-and-pepper" if v["salt"] else "")
+                                 + f", K={v['K']} (d={v['K'] ** 3}), SFC C={v['curves']} D={v['dims']} "
+                                 f"b={v['bits']} W={v['window']}, FP32 projections",
+                     "dictionary": int(N), "queries": Q, "qps": Q / (statistics.mean(st_ms) / 1000.0),
+                     "ms_per_step": statistics.mean(st_ms), "query_ms": statistics.mean(q_ms),
+                     "query_only_qps": Q / (statistics.mean(q_ms) / 1000.0), "status": sfc.sfc_status()}
+        del gd, md, td
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -341,6 +564,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-image batched configuration")
+    ap.add_argument("--no-3d", action="store_true", help="skip the 256^3 and 512^3 configurations")
     ap.add_argument("--profile-fp16", nargs=2, type=int, metavar=("WIDTH", "QUERIES"),
                     help="profiling case only: two tensor-core full scans (SFC_FP16) of QUERIES targets on a "
                          "WIDTH^2 voronoi2d grid, K=11; prints one line, no timing")
@@ -431,6 +655,8 @@ def main():
     qk, pos, cand, nc = sfc.sfc_query_candidates(ix, gd, md, td)
     mean_cand = float(nc.double().mean().item())
     n_elem = WORKLOAD["K"] ** 2 * 3
+    nk = known_values(m, t, WORKLOAD["K"], 3)  # known values per target (mean ~201 of 363)
+    nc_h = nc.cpu().numpy().astype(np.int64)
     q_ms = []
     for _ in range(5):
         flush.fill_(1.0)
@@ -443,11 +669,14 @@ def main():
         q_ms.append(a.elapsed_time(b))
     q_ms_mean = statistics.mean(q_ms)
     N = ix.N
-    # algorithmic bytes per query: the gathered candidate patches (n values of 4 B
-    # each), the window ids, and the binary-search probes (8 B per level)
-    per_query = mean_cand * n_elem * 4 + WORKLOAD["curves"] * WORKLOAD["window"] * 4 + \
-        WORKLOAD["curves"] * 8 * int(np.ceil(np.log2(N)))
-    bytes_launch = per_query * Q
+    ex_h = sfc.sfc_index_export(ix)  # the headline index's arrays, for the parity record
+    # algorithmic bytes per query: the candidates' values at the target's known
+    # elements (4 B each; the cost reads nothing else), the window ids, and the
+    # binary-search probes (8 B per level)
+    probes = WORKLOAD["curves"] * WORKLOAD["window"] * 4 + WORKLOAD["curves"] * 8 * int(np.ceil(np.log2(N)))
+    bytes_launch = float(np.sum(nc_h * nk * 4) + probes * Q)
+    per_query = bytes_launch / Q
+    bytes_all_values = float(np.sum(nc_h) * n_elem * 4 + probes * Q)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -458,7 +687,9 @@ def main():
               "achieved": bytes_launch / (q_ms_mean / 1000.0) / 1e9, "peak": hbm, "unit": "GB/s",
               "traffic": TRAFFIC.get("k_query"),
               "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s",
-              "bytes_per_query": per_query, "mean_candidates": mean_cand, "launch_ms": q_ms_mean}
+              "bytes_per_query": per_query, "mean_candidates": mean_cand, "mean_known_values": float(nk.mean()),
+              "bytes_per_query_all_363_values": bytes_all_values / Q,
+              "launch_ms": q_ms_mean}
     q_roof["frac"] = q_roof["achieved"] / q_roof["peak"]
     eig_ms = phases_ms["eigen"]
     # the solve mixes FP64 work (late products, every orthonormalisation) and
@@ -502,10 +733,19 @@ def main():
     agree = float((sp == fp).double().mean().item())
     # acceleration error (Sec. III.C): L2 norm of the pick / of the exact pick - 1
     ae = float((torch.sqrt(cost[sel].double()) / torch.sqrt(fc.double()).clamp_min(1e-30) - 1.0).mean().item())
-    fs_flops = 3.0 * float(N) * n_elem * fs_q
+    sel_h = sel.cpu().numpy()
+    # the method's work: a subtraction and a multiply-add per known value
+    # (3 flops) per dictionary entry; the kernel executes all n values (the
+    # mask is folded into its operand)
+    fs_flops = 3.0 * float(N) * float(np.sum(nk[sel_h]))
+    fs_flops_exec = 3.0 * float(N) * n_elem * fs_q
+    fs_tf = fs_flops / (statistics.mean(fs_ms) / 1000.0) / 1e12
     fullscan = {"qps": fs_qps, "queries": fs_q, "ms": statistics.mean(fs_ms), "pick_agreement_sfc": agree,
                 "acceleration_error_mean": ae,
-                "fp32_gflops_algorithmic": fs_flops / (statistics.mean(fs_ms) / 1000.0) / 1e9}
+                "fp32_tflops_algorithmic": fs_tf, "fp32_frac_of_derived_peak": fs_tf / FP32_PEAK_TFLOPS,
+                "fp32_tflops_executed": fs_flops_exec / (statistics.mean(fs_ms) / 1000.0) / 1e12,
+                "fp32_peak_source": f"derived: {FP32_PEAK_TFLOPS} TFLOP/s from the unit counts and the 2.07 GHz "
+                                    "clock (no measured FP32 peak)"}
 
     # ---- the same full scan with the tensor-core pre-score (SFC_FP16) ---------
     tc_ms = []
@@ -526,14 +766,21 @@ def main():
     same = bool(torch.equal(hp, fp) and torch.equal(hc.view(torch.int32), fc.view(torch.int32)))
     calls = max(tct["calls"], 1)
     gemm_ms = tct["ms"]["gemm"] / calls
-    gemm_flops = tct["gemm_flops"] / calls
+    # the method's contraction: 2 Q N 2n flops (rows [-2 m w t ; m w] against
+    # [p ; p^2]); executed: the three split products on padded tiles,
+    # 2 Qpad Npad Kp with Kp = 6 ceil(n / 8) 8 rounded up to 64
+    gemm_flops = 2.0 * fs_q * float(N) * 2 * n_elem
+    kp = -(-6 * (-(-n_elem // 8) * 8) // 64) * 64
+    gemm_flops_exec = 2.0 * (-(-fs_q // 128) * 128) * float(-(-N // 256) * 256) * kp
     bf16 = float(peaks.get("bf16_tflops", 1900.0))
     tc_roof = {"kernel": "k_tc_gemm (fullscan_query_batch, SFC_FP16)", "bound": "tensor",
                "achieved": gemm_flops / (gemm_ms / 1000.0) / 1e12 if gemm_ms > 0 else 0.0, "peak": bf16,
                "unit": "TFLOP/s", "traffic": TRAFFIC.get("k_tc_gemm"),
                "peak_source": ("MEASURED_PEAKS.json bf16_tflops (FP16 and BF16 run at one rate)" if peaks
                                else "fallback 1900 TFLOP/s"),
-               "flops_per_launch": gemm_flops, "launch_ms": gemm_ms}
+               "flops_per_launch": gemm_flops, "launch_ms": gemm_ms,
+               "executed_flops_per_launch": gemm_flops_exec,
+               "executed_tflops": gemm_flops_exec / (gemm_ms / 1000.0) / 1e12 if gemm_ms > 0 else 0.0}
     tc_roof["frac"] = tc_roof["achieved"] / tc_roof["peak"]
     fullscan["fp16_tensor"] = {"qps": fs_q / (statistics.mean(tc_ms) / 1000.0), "ms": statistics.mean(tc_ms),
                                "picks_and_costs_equal_fp32": same,
@@ -633,6 +880,30 @@ def main():
               "query_qps": Q / (statistics.mean(st_ms["query"]) / 1000.0),
               "picks_equal_built_index": bool(torch.equal(lp, pick))}
 
+    # ---- the PCA over every dictionary entry instead of a 16,384-entry sample --
+    pca_all = pca_sample_comparison(sfc, torch, gd, md, td, prm, flush, stream, ex_h, fp, fc, sel, statistics.mean(
+        step_ms))
+
+    # ---- the fill loop on the full workload (SFC mode, until no pixel is unknown)
+    fill_steps_cap = 40000
+    gg = gd.clone()
+    mm = md.clone()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fsteps, flog = sfc.inpaint_run(gg, mm, mode=sfc.SFC_MODE_SFC, max_steps=fill_steps_cap, **prm)
+    torch.cuda.synchronize()
+    fill_s = time.perf_counter() - t0
+    fill_big = {"workload": "the headline image and mask, SFC mode with the headline's index parameters, "
+                            "confidence priority",
+                "unknown_pixels": int((m == 0).sum()), "steps": int(fsteps), "step_cap": fill_steps_cap,
+                "done": bool(mm.all().item()), "seconds": fill_s, "ms_per_step": 1000 * fill_s / max(fsteps, 1),
+                "status": sfc.sfc_status()}
+    flog_h = flog.cpu().numpy()
+    del gg, mm
+
+    # ---- the 3-D configurations (256^3, 512^3): index build + front-target queries
+    volumes = None if args.no_3d else run_volumes(sfc, torch, dev, flush, stream)
+
     # ---- end to end through the C-ABI with host buffers ----------------------
     gh = torch.from_numpy(g).pin_memory()
     mh = torch.from_numpy(m).pin_memory()
@@ -702,9 +973,13 @@ def main():
             "fullscan": fullscan, "sfc_knn": sfc_knn, "sfc_hilbert": sfc_hilbert, "sfc_l1": sfc_l1,
             "stored_index": stored, "inpaint_128x128": inp,
             "batch_256": batch}
+    line.update({"pca_sample_all": pca_all, "inpaint_1024": fill_big, "volumes": volumes})
     if rank == 0:
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline_obj()
+            gpu = {"g": g, "m": m, "t": t, "ex": ex_h, "pick": pick.cpu().numpy(), "cost": cost.cpu().numpy(),
+                   "cand": cand.cpu().numpy(), "ncand": nc_h, "fs_sel": sel_h, "fs_pick": fp.cpu().numpy(),
+                   "fill_log": flog_h}
+            line["cpu_baseline"], line["parity"] = cpu_baseline_obj(gpu)
         print(json.dumps(line))
     if world > 1:
         dist.barrier()

@@ -1,6 +1,7 @@
 """bench.py --impl reference on the host (no GPU): the oracle arm prints one
-JSON line with the main arm's metric, unit, direction and workload config,
-and the cpu_baseline / e2e objects the line format asks for."""
+JSON line with the main arm's metric, unit and direction, a config naming the
+256x256 tile of the workload it times, and the cpu_baseline / e2e objects the
+line format asks for."""
 import json
 import os
 import subprocess
@@ -21,8 +22,9 @@ def test_reference_arm_line():
     assert (line["metric"], line["unit"], line["higher_is_better"]) == (bench.METRIC, bench.UNIT, True)
     assert line["value"] > 0 and line["steps"] == 1 and line["warmup"] == 1
     cfg = line["config"]
-    assert cfg == bench.arm_config(cfg["queries_per_step"], cfg["dictionary"], 1)
-    assert cfg["queries_per_step"] == 3597 and cfg["dictionary"] == 901592
+    # the config states the tile the oracle actually times, not the full workload
+    assert "256x256 tile" in cfg["workload"]
+    assert cfg["queries_per_step"] == 482 and cfg["dictionary"] == 42802
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"] and cb["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,

@@ -380,24 +380,66 @@ def test_big_index_sorted_permutation_and_sampled_keys(big):
             assert O.keys(q, 16)[0] == ex["keys"][cv][j]
 
 
-def test_big_sampled_queries_match_oracle(S, big):
-    ex, g, m, t = big["ex"], big["g"], big["m"], big["t"]
+@pytest.fixture(scope="module")
+def opool():
+    from oracle import parallel as OP
+
+    ex = OP.make_pool()
+    yield ex, OP.default_workers()
+    ex.shutdown()
+
+
+@pytest.fixture(scope="module")
+def big_oracle(big, opool):
+    """The oracle's index of the full workload, built from the GPU's exported
+    basis (checkpoint split: everything downstream of the basis must be
+    bit-exact), its indices built in parallel worker processes."""
+    from oracle import parallel as OP
+
+    ex = big["ex"]
+    return OP.build_index(opool[0], big["g"], big["m"], 11, 8, 8, 16, basis=ex["basis"], mean=ex["mean"])
+
+
+def test_big_oracle_index_bit_exact(big, big_oracle):
+    # every projection, quantiser, key and both sorted arrays of all 8 indices
+    ex, oix = big["ex"], big_oracle
+    assert np.array_equal(oix["dict"], ex["dict"])
+    assert np.array_equal(oix["proj"], ex["proj"])
+    assert np.array_equal(oix["lo"], ex["lo"]) and np.array_equal(oix["scale"], ex["scale"])
+    assert np.array_equal(oix["keys"], ex["keys"])
+    assert np.array_equal(oix["skeys"], ex["skeys"]) and np.array_equal(oix["sids"], ex["sids"])
+
+
+def test_big_all_queries_match_oracle(S, big, big_oracle, opool):
+    # all 3,597 front targets: candidate sets bit-exact, picks equal, costs
+    # within 1e-5 of the exact cost, against the oracle's own sorted arrays
+    from oracle import parallel as OP
+
+    g, m, t = big["g"], big["m"], big["t"]
     assert len(t) == 3597  # every front target of the initial mask (the 65,536 cap is not reached)
     pk, cs = S.sfc_query_batch(big["ix"], big["gd"], big["md"], big["td"])
     pk, cs = pk.cpu().numpy(), cs.cpu().numpy()
-    assert np.all(pk >= 0)
-    oq = oracle_ix(ex, g, 11, 8, 8, 16)
+    _, _, cand, nc = S.sfc_query_candidates(big["ix"], big["gd"], big["md"], big["td"])
+    cand, nc = cand.cpu().numpy(), nc.cpu().numpy()
     lin = O.centres_to_lin(t, ext_of(g))
-    rng = np.random.default_rng(1)
-    for i in np.r_[0, len(t) - 1, rng.choice(len(t), 62, replace=False)]:
-        rr = O.query(oq, g, m, lin[i], 64)
-        assert pk[i] == rr["pick"] and cost_close(cs[i], rr["cost"])
+    op, oc, ocand = OP.query_batch(opool[0], opool[1], big_oracle, g, m, lin, 64)
+    assert np.array_equal(pk, op)
+    assert cost_close(cs, oc)
+    for i in range(len(t)):
+        assert np.array_equal(cand[i, : nc[i]], ocand[i]), i
 
 
-def test_big_sampled_fullscan_match_oracle(S, big):
+def test_big_fullscan_256_match_oracle(S, big, opool):
+    # 256 seeded targets: the tensor-core full scan (a3) equals the FP32 scan
+    # (a2) bit for bit, and both equal the oracle's brute-force picks
+    from oracle import parallel as OP
+
     g, m, t = big["g"], big["m"], big["t"]
     rng = np.random.default_rng(2)
-    sel = np.sort(rng.choice(len(t), 12, replace=False))
-    fp, fc = S.fullscan_query_batch(big["gd"], big["md"], big["md"], dev(t[sel]), K=11)
-    op, oc = O.fullscan(g, m, 11, big["ex"]["dict"], O.centres_to_lin(t[sel], ext_of(g)))
+    sel = np.sort(rng.choice(len(t), 256, replace=False))
+    td = dev(t[sel])
+    fp, fc = S.fullscan_query_batch(big["gd"], big["md"], big["md"], td, K=11)
+    hp, hc = S.fullscan_query_batch(big["gd"], big["md"], big["md"], td, K=11, precision=S.SFC_FP16)
+    assert torch.equal(fp, hp) and torch.equal(fc.view(torch.int32), hc.view(torch.int32))
+    op, oc = OP.fullscan(opool[0], opool[1], g, m, 11, big["ex"]["dict"], O.centres_to_lin(t[sel], ext_of(g)))
     assert np.array_equal(fp.cpu().numpy(), op) and cost_close(fc.cpu().numpy(), oc)
