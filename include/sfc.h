@@ -371,6 +371,27 @@ int sfc_autotune(const float* grid, const uint8_t* mask, const sfc_grid* g, cons
  * pointer is NULL.  NaN measurements count as +infinity. */
 int32_t sfc_tune_select(int32_t n, const double* ms, const double* ae, double ae_max);
 
+/* ---- Failure injection for tests ------------------------------------------
+ * The paper has no counterpart: these hooks let tests drive the library's
+ * failure paths without faulting the GPU.
+ *
+ * sfc_debug_fail_alloc(n): the n-th library device allocation from now on
+ * fails as if the device were out of memory (n <= 0: off); the entry point
+ * that made it returns SFC_ENOMEM and releases everything it had taken.
+ * sfc_debug_alloc_count(): library device allocations made so far (process).
+ * sfc_debug_pool_used(bytes): synchronises the device, then *bytes (host) = the
+ * bytes currently allocated from the library's memory pool on this device.
+ * sfc_debug_lookback(spin_limit, stall): the radix sort's decoupled look-back
+ * gives up after spin_limit polls (<= 0: the default 2^24), and with stall = 1
+ * every look-back polls a word nothing writes -- so every sort tile after the
+ * first gives up, the sort's output is garbage and sfc_status() reports
+ * SFC_ETIMEOUT (writes stay inside the output arrays; the GPU stays usable).
+ * Reset with sfc_debug_lookback(0, 0). */
+int sfc_debug_fail_alloc(int64_t n);
+int64_t sfc_debug_alloc_count(void);
+int sfc_debug_pool_used(uint64_t* bytes);
+int sfc_debug_lookback(int64_t spin_limit, int32_t stall);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* sfc_last_error(void);
 

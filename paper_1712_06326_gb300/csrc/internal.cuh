@@ -50,6 +50,40 @@ inline cudaError_t pmalloc(T** p, size_t bytes, cudaStream_t st) {
   return pool_malloc(reinterpret_cast<void**>(p), bytes, st);
 }
 
+// The stream-ordered allocations of one call: each is freed on the stream
+// (cudaFreeAsync) when the guard goes out of scope, unless ownership was passed
+// on with keep() -- so an early error return frees everything taken so far.
+class Scratch {
+ public:
+  explicit Scratch(cudaStream_t st) : st_(st) {}
+  Scratch(const Scratch&) = delete;
+  Scratch& operator=(const Scratch&) = delete;
+  ~Scratch() {
+    for (void* p : ptrs_)
+      if (p) cudaFreeAsync(p, st_);
+  }
+  template <typename T>
+  cudaError_t alloc(T** p, size_t bytes) {
+    *p = nullptr;
+    cudaError_t e = pool_malloc(reinterpret_cast<void**>(p), bytes, st_);
+    if (e == cudaSuccess) ptrs_.push_back(*p);
+    return e;
+  }
+  // p, allocated elsewhere on the same stream, is freed by the guard too
+  void adopt(void* p) {
+    if (p) ptrs_.push_back(p);
+  }
+  // ownership of p moves to the caller's object (not freed by the guard)
+  void keep(const void* p) {
+    for (void*& q : ptrs_)
+      if (q == p) q = nullptr;
+  }
+
+ private:
+  cudaStream_t st_;
+  std::vector<void*> ptrs_;
+};
+
 // Per-index state (host struct, device arrays).
 struct Index {
   Geo g;
@@ -128,6 +162,10 @@ int sorted_coords(Index& ix, const float* proj, cudaStream_t st);
 int radix_sort_pairs(const uint64_t* keys, uint64_t* skeys, uint32_t* sids, int64_t N, int C, int key_bits,
                      cudaStream_t st, void* scratch = nullptr);
 size_t radix_sort_scratch_bytes(int64_t N, int C, int key_bits);
+// Failure injection (tests): the onesweep look-back's poll limit (<= 0: the
+// default kSpinLimit) and, with stall = 1, look-backs that poll a word nothing
+// writes, so every tile after the first gives up after spin_limit polls.
+void sort_lookback_test(long long spin_limit, int stall);
 
 // k_query.cu
 // Targets on a grid other than the index's: its geometry, its patch element

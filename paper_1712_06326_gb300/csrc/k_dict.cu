@@ -113,10 +113,12 @@ int dict_extract(const uint8_t* mask, const Geo& g, cudaStream_t st, uint32_t** 
   uint32_t* counts = nullptr;
   int64_t* dtotal = nullptr;
   const int64_t ntiles = (npix + kTile - 1) / kTile;
-  SFC_TRY(pmalloc(&a, npix, st));
-  SFC_TRY(pmalloc(&b, npix, st));
-  SFC_TRY(pmalloc(&counts, ntiles * sizeof(uint32_t), st));
-  SFC_TRY(pmalloc(&dtotal, sizeof(int64_t), st));
+  *dict = nullptr;
+  Scratch scr(st);
+  SFC_TRY(scr.alloc(&a, npix));
+  SFC_TRY(scr.alloc(&b, npix));
+  SFC_TRY(scr.alloc(&counts, ntiles * sizeof(uint32_t)));
+  SFC_TRY(scr.alloc(&dtotal, sizeof(int64_t)));
   int grid = (int)((npix + 255) / 256 < 152 * 64 ? (npix + 255) / 256 : 152 * 64);
   count_launch();
   k_window_all<<<grid, 256, 0, st>>>(mask, a, npix, g.X, g.Y, 0, g.X, g.r);
@@ -137,15 +139,12 @@ int dict_extract(const uint8_t* mask, const Geo& g, cudaStream_t st, uint32_t** 
   SFC_TRY(cudaStreamSynchronize(st));
   uint32_t* out = nullptr;
   if (total > 0) {
-    SFC_TRY(pmalloc(&out, total * sizeof(uint32_t), st));
+    SFC_TRY(scr.alloc(&out, total * sizeof(uint32_t)));
     count_launch();
     k_tile_emit<<<(unsigned)ntiles, 256, 0, st>>>(flag, npix, counts, out);
   }
   SFC_TRY(cudaGetLastError());
-  cudaFreeAsync(a, st);
-  cudaFreeAsync(b, st);
-  cudaFreeAsync(counts, st);
-  cudaFreeAsync(dtotal, st);
+  scr.keep(out);
   *dict = out;
   *N = total;
   return SFC_OK;

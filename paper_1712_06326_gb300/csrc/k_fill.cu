@@ -266,20 +266,21 @@ int fill_loop(const Geo& g, float* grid, uint8_t* mask, int prio, int mode, cons
   float* tilemin = nullptr;
   unsigned int* gmin = nullptr;
   const int64_t ntiles = (N + 1023) / 1024;
-  SFC_TRY(pmalloc(&s.key, sizeof(unsigned long long) * npix, st));
-  SFC_TRY(pmalloc(&s.conf, sizeof(float) * npix, st));
-  SFC_TRY(pmalloc(&s.cterm, sizeof(float) * npix, st));
-  SFC_TRY(pmalloc(&s.best, sizeof(unsigned long long), st));
-  SFC_TRY(pmalloc(&s.sel_lin, sizeof(int64_t), st));
-  SFC_TRY(pmalloc(&s.sel_xyz, sizeof(int32_t) * 4, st));
-  SFC_TRY(pmalloc(&s.sel_cterm, sizeof(float), st));
-  SFC_TRY(pmalloc(&s.pick, sizeof(int64_t), st));
-  SFC_TRY(pmalloc(&s.cost, sizeof(float), st));
-  SFC_TRY(pmalloc(&s.done, sizeof(int), st));
-  SFC_TRY(pmalloc(&s.steps, sizeof(int64_t), st));
-  SFC_TRY(pmalloc(&unknown, sizeof(int64_t), st));
-  SFC_TRY(pmalloc(&tilemin, sizeof(float) * (ntiles > 0 ? ntiles : 1), st));
-  SFC_TRY(pmalloc(&gmin, sizeof(unsigned int), st));
+  Scratch scr(st);  // the loop's state, freed on every return
+  SFC_TRY(scr.alloc(&s.key, sizeof(unsigned long long) * npix));
+  SFC_TRY(scr.alloc(&s.conf, sizeof(float) * npix));
+  SFC_TRY(scr.alloc(&s.cterm, sizeof(float) * npix));
+  SFC_TRY(scr.alloc(&s.best, sizeof(unsigned long long)));
+  SFC_TRY(scr.alloc(&s.sel_lin, sizeof(int64_t)));
+  SFC_TRY(scr.alloc(&s.sel_xyz, sizeof(int32_t) * 4));
+  SFC_TRY(scr.alloc(&s.sel_cterm, sizeof(float)));
+  SFC_TRY(scr.alloc(&s.pick, sizeof(int64_t)));
+  SFC_TRY(scr.alloc(&s.cost, sizeof(float)));
+  SFC_TRY(scr.alloc(&s.done, sizeof(int)));
+  SFC_TRY(scr.alloc(&s.steps, sizeof(int64_t)));
+  SFC_TRY(scr.alloc(&unknown, sizeof(int64_t)));
+  SFC_TRY(scr.alloc(&tilemin, sizeof(float) * (ntiles > 0 ? ntiles : 1)));
+  SFC_TRY(scr.alloc(&gmin, sizeof(unsigned int)));
   SFC_TRY(cudaMemsetAsync(unknown, 0, sizeof(int64_t), st));
   SFC_TRY(cudaMemsetAsync(s.key, 0, sizeof(unsigned long long) * npix, st));
   SFC_TRY(cudaMemsetAsync(s.cterm, 0, sizeof(float) * npix, st));
@@ -343,20 +344,6 @@ int fill_loop(const Geo& g, float* grid, uint8_t* mask, int prio, int mode, cons
   SFC_TRY(cudaMemcpyAsync(&steps, s.steps, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   SFC_TRY(cudaStreamSynchronize(st));
   *steps_done = steps;
-  cudaFreeAsync(s.key, st);
-  cudaFreeAsync(s.conf, st);
-  cudaFreeAsync(s.cterm, st);
-  cudaFreeAsync(s.best, st);
-  cudaFreeAsync(s.sel_lin, st);
-  cudaFreeAsync(s.sel_xyz, st);
-  cudaFreeAsync(s.sel_cterm, st);
-  cudaFreeAsync(s.pick, st);
-  cudaFreeAsync(s.cost, st);
-  cudaFreeAsync(s.done, st);
-  cudaFreeAsync(s.steps, st);
-  cudaFreeAsync(unknown, st);
-  cudaFreeAsync(tilemin, st);
-  cudaFreeAsync(gmin, st);
   return rc;
 }
 

@@ -593,15 +593,16 @@ int fullscan_batch_tc(const Geo& g, const float* grid, const uint8_t* cur_mask, 
                       const int* eoff_all, const float* weights, bool weighted, const int32_t* centres, int64_t Q,
                       int64_t* pick, float* cost, int* nsel, cudaStream_t st) {
   if (Q <= 0) return SFC_OK;
+  Scratch scr(st);  // freed on every return
   const int64_t nsub = tc_subs(N);
   int64_t* lin = nullptr;
   uint8_t* bad = nullptr;
   float* tilemin = nullptr;
   double* bound = nullptr;
-  SFC_TRY(pmalloc(&lin, sizeof(int64_t) * Q, st));
-  SFC_TRY(pmalloc(&bad, Q, st));
-  SFC_TRY(pmalloc(&tilemin, sizeof(float) * Q * nsub, st));
-  SFC_TRY(pmalloc(&bound, sizeof(double) * Q, st));
+  SFC_TRY(scr.alloc(&lin, sizeof(int64_t) * Q));
+  SFC_TRY(scr.alloc(&bad, Q));
+  SFC_TRY(scr.alloc(&tilemin, sizeof(float) * Q * nsub));
+  SFC_TRY(scr.alloc(&bound, sizeof(double) * Q));
   const unsigned qb = (unsigned)((Q + 255) / 256);
   count_launch();
   k_centre_lin<<<qb, 256, 0, st>>>(centres, Q, g, lin, status_word());
@@ -626,10 +627,6 @@ int fullscan_batch_tc(const Geo& g, const float* grid, const uint8_t* cur_mask, 
   k_mark_bad<<<qb, 256, 0, st>>>(bad, Q, pick, cost);
   SFC_TRY(cudaGetLastError());
   tc_trace_mark(3, st);
-  cudaFreeAsync(lin, st);
-  cudaFreeAsync(bad, st);
-  cudaFreeAsync(tilemin, st);
-  cudaFreeAsync(bound, st);
   tc_trace_end(2.0 * (double)Q * (double)N * 6.0 * g.n);
   return SFC_OK;
 }
@@ -639,22 +636,20 @@ int tc_prescores_all(const Geo& g, const float* grid, const uint8_t* cur_mask, c
                      const int* eoff_all, const float* weights, const int32_t* centres, int64_t Q, float* scores,
                      double* bound, cudaStream_t st) {
   if (Q <= 0) return SFC_OK;
+  Scratch scr(st);  // freed on every return
   const int64_t nsub = tc_subs(N);
   int64_t* lin = nullptr;
   uint8_t* bad = nullptr;
   float* tilemin = nullptr;
-  SFC_TRY(pmalloc(&lin, sizeof(int64_t) * Q, st));
-  SFC_TRY(pmalloc(&bad, Q, st));
-  SFC_TRY(pmalloc(&tilemin, sizeof(float) * Q * nsub, st));
+  SFC_TRY(scr.alloc(&lin, sizeof(int64_t) * Q));
+  SFC_TRY(scr.alloc(&bad, Q));
+  SFC_TRY(scr.alloc(&tilemin, sizeof(float) * Q * nsub));
   const unsigned qb = (unsigned)((Q + 255) / 256);
   count_launch();
   k_centre_lin<<<qb, 256, 0, st>>>(centres, Q, g, lin, status_word());
   count_launch();
   k_centre_fix<<<qb, 256, 0, st>>>(lin, Q, g, bad);
   SFC_CHECK(tc_prescore(g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, scores, bound, st));
-  cudaFreeAsync(lin, st);
-  cudaFreeAsync(bad, st);
-  cudaFreeAsync(tilemin, st);
   return SFC_OK;
 }
 
@@ -662,23 +657,24 @@ int fullscan_batch(const Geo& g, const float* grid, const uint8_t* cur_mask, con
                    const int* eoff_all, const float* weights, int cm, const int32_t* centres,
                    const int64_t* centre_lin, int64_t Q, int64_t* pick, float* cost, cudaStream_t st) {
   if (Q <= 0) return SFC_OK;
+  Scratch scr(st);  // freed on every return
   constexpr int EPT = 4;
   const int64_t ntiles = (N + kFsThreads * EPT - 1) / (kFsThreads * EPT);
   int64_t* lin = nullptr;
   uint8_t* bad = nullptr;
   float* tilemin = nullptr;
   unsigned int* gmin = nullptr;
-  SFC_TRY(pmalloc(&tilemin, sizeof(float) * Q * ntiles, st));
-  SFC_TRY(pmalloc(&gmin, sizeof(unsigned int) * Q, st));
-  SFC_TRY(pmalloc(&bad, Q, st));
+  SFC_TRY(scr.alloc(&tilemin, sizeof(float) * Q * ntiles));
+  SFC_TRY(scr.alloc(&gmin, sizeof(unsigned int) * Q));
+  SFC_TRY(scr.alloc(&bad, Q));
   const int64_t* L = centre_lin;
   if (!L) {
-    SFC_TRY(pmalloc(&lin, sizeof(int64_t) * Q, st));
+    SFC_TRY(scr.alloc(&lin, sizeof(int64_t) * Q));
     count_launch();
     k_centre_lin<<<(unsigned)((Q + 255) / 256), 256, 0, st>>>(centres, Q, g, lin, status_word());
     L = lin;
   } else {
-    SFC_TRY(pmalloc(&lin, sizeof(int64_t) * Q, st));
+    SFC_TRY(scr.alloc(&lin, sizeof(int64_t) * Q));
     SFC_TRY(cudaMemcpyAsync(lin, centre_lin, sizeof(int64_t) * Q, cudaMemcpyDeviceToDevice, st));
     L = lin;
   }
@@ -694,10 +690,6 @@ int fullscan_batch(const Geo& g, const float* grid, const uint8_t* cur_mask, con
   count_launch();
   k_mark_bad<<<(unsigned)((Q + 255) / 256), 256, 0, st>>>(bad, Q, pick, cost);
   SFC_TRY(cudaGetLastError());
-  cudaFreeAsync(tilemin, st);
-  cudaFreeAsync(gmin, st);
-  cudaFreeAsync(bad, st);
-  cudaFreeAsync(lin, st);
   return SFC_OK;
 }
 

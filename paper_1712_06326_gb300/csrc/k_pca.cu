@@ -1424,18 +1424,19 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
   double *mean = nullptr, *mean_c = nullptr, *msum = nullptr, *partial = nullptr, *M = nullptr;
   int2* pairs = nullptr;
   SiBufs b;
-  SFC_TRY(pmalloc(&mean, sizeof(double) * n, st));
-  SFC_TRY(pmalloc(&mean_c, sizeof(double) * C * s, st));
-  SFC_TRY(pmalloc(&msum, sizeof(double) * msplit * n, st));
-  SFC_TRY(pmalloc(&partial, sizeof(double) * nsplit * npairs * kTile * kTile, st));
-  SFC_TRY(pmalloc(&M, sizeof(double) * n * n, st));
-  SFC_TRY(pmalloc(&pairs, sizeof(int2) * npairs, st));
-  SFC_TRY(pmalloc(&b.A, sizeof(double) * C * s * s, st));
-  SFC_TRY(pmalloc(&b.Q, sizeof(double) * C * s * p, st));
-  SFC_TRY(pmalloc(&b.Y, sizeof(double) * C * s * p, st));
-  SFC_TRY(pmalloc(&b.X, sizeof(double) * C * s * p, st));
-  SFC_TRY(pmalloc(&b.e, sizeof(double) * C * p, st));
-  SFC_TRY(pmalloc(&b.done, sizeof(int) * C, st));
+  Scratch scr(st);
+  SFC_TRY(scr.alloc(&mean, sizeof(double) * n));
+  SFC_TRY(scr.alloc(&mean_c, sizeof(double) * C * s));
+  SFC_TRY(scr.alloc(&msum, sizeof(double) * msplit * n));
+  SFC_TRY(scr.alloc(&partial, sizeof(double) * nsplit * npairs * kTile * kTile));
+  SFC_TRY(scr.alloc(&M, sizeof(double) * n * n));
+  SFC_TRY(scr.alloc(&pairs, sizeof(int2) * npairs));
+  SFC_TRY(scr.alloc(&b.A, sizeof(double) * C * s * s));
+  SFC_TRY(scr.alloc(&b.Q, sizeof(double) * C * s * p));
+  SFC_TRY(scr.alloc(&b.Y, sizeof(double) * C * s * p));
+  SFC_TRY(scr.alloc(&b.X, sizeof(double) * C * s * p));
+  SFC_TRY(scr.alloc(&b.e, sizeof(double) * C * p));
+  SFC_TRY(scr.alloc(&b.done, sizeof(int) * C));
   b.iters = ix.eig_iters;
   b.iters32 = ix.eig_iters + C;
   SFC_TRY(cudaMemsetAsync(b.iters, 0, sizeof(int) * C, st));
@@ -1550,19 +1551,9 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
   count_launch();
   k_pca_finalize<<<C, 256, 0, st>>>(b, mean_c, s, p, D, ix.basis, ix.mean, ix.evals, status_word());
   SFC_TRY(cudaGetLastError());
-  cudaFreeAsync(mean, st);
-  cudaFreeAsync(mean_c, st);
-  cudaFreeAsync(msum, st);
-  cudaFreeAsync(M, st);
-  cudaFreeAsync(partial, st);
-  cudaFreeAsync(pairs, st);
-  cudaFreeAsync(b.A, st);
-  cudaFreeAsync(b.Q, st);
-  cudaFreeAsync(b.Y, st);
-  cudaFreeAsync(b.X, st);
-  cudaFreeAsync(b.e, st);
+  scr.keep(b.done);
   ix.pca_done = b.done;  // read by the build once the device is done with it
-  return SFC_OK;
+  return SFC_OK;  // the guard frees the rest on the stream
 }
 
 }  // namespace sfc

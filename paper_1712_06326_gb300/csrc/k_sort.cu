@@ -11,11 +11,19 @@
 // digit run are contiguous.  Look-back spins are bounded (kSpinLimit): on
 // timeout the CTA raises ST_TIMEOUT in the status word and carries on, so the
 // device never hangs.  Only the passes covering the key bits in use run.
+#include <atomic>
+
 #include "internal.cuh"
 
 namespace sfc {
 
 namespace {
+
+// Failure injection for tests (sfc_debug_lookback): the look-back's poll limit,
+// and a switch that makes every look-back poll a word nothing ever writes.
+std::atomic<long long> g_spin_limit{kSpinLimit};
+std::atomic<int> g_stall{0};
+__device__ uint32_t g_never_set[256];  // zero, never written
 
 constexpr int kThreads = 256;
 constexpr int kItems = 12;
@@ -67,7 +75,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const uint64_t* __rest
                                                        const uint32_t* __restrict__ goffs,  // [C][256] this pass
                                                        uint32_t* __restrict__ status,       // [C][ntiles][256]
                                                        uint32_t* __restrict__ tile_ctr,     // [C]
-                                                       int64_t ntiles, uint32_t* __restrict__ err) {
+                                                       int64_t ntiles, uint32_t* __restrict__ err,
+                                                       long long spin_limit, int stall) {
   const int c = blockIdx.y;
   __shared__ uint32_t s_tile;
   __shared__ uint32_t whist[kWarps][256];  // per-warp counts -> per-warp exclusive offsets
@@ -132,9 +141,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const uint64_t* __rest
       int64_t j = tile - 1;
       long long spins = 0;
       while (j >= 0) {
-        uint32_t v = *((volatile uint32_t*)&st[j * 256 + d]);
+        const uint32_t v = stall ? *((volatile uint32_t*)&g_never_set[d]) : *((volatile uint32_t*)&st[j * 256 + d]);
         if (v == 0) {
-          if (++spins > kSpinLimit) {
+          if (++spins > spin_limit) {
             atomicOr(err, ST_TIMEOUT);
             break;
           }
@@ -235,6 +244,11 @@ SortLayout sort_layout(int64_t N, int C, int key_bits) {
 }
 }  // namespace
 
+void sort_lookback_test(long long spin_limit, int stall) {
+  g_spin_limit.store(spin_limit > 0 ? spin_limit : kSpinLimit);
+  g_stall.store(stall ? 1 : 0);
+}
+
 size_t radix_sort_scratch_bytes(int64_t N, int C, int key_bits) { return N > 0 ? sort_layout(N, C, key_bits).total : 0; }
 
 int radix_sort_pairs(const uint64_t* keys, uint64_t* skeys, uint32_t* sids, int64_t N, int C, int key_bits,
@@ -248,8 +262,8 @@ int radix_sort_pairs(const uint64_t* keys, uint64_t* skeys, uint32_t* sids, int6
   const int npass = L.npass;
   const int64_t ntiles = L.ntiles;
   unsigned char* ws = static_cast<unsigned char*>(scratch);
-  const bool own = ws == nullptr;
-  if (own) SFC_TRY(pmalloc(&ws, L.total, st));
+  Scratch scr(st);  // frees the sort's own scratch (if it takes one) on return
+  if (!ws) SFC_TRY(scr.alloc(&ws, L.total));
   uint32_t* hist = reinterpret_cast<uint32_t*>(ws + L.hist);
   uint32_t* status = reinterpret_cast<uint32_t*>(ws + L.status);
   uint32_t* ctr = reinterpret_cast<uint32_t*>(ws + L.ctr);
@@ -281,12 +295,12 @@ int radix_sort_pairs(const uint64_t* keys, uint64_t* skeys, uint32_t* sids, int6
     k_onesweep<<<dim3((unsigned)ntiles, C), kThreads, 0, st>>>(ink, inv, ok_, ov, N, 8 * p,
                                                                goffs + (size_t)p * C * 256,
                                                                status + (size_t)p * C * ntiles * 256, ctr + p * C,
-                                                               ntiles, status_word());
+                                                               ntiles, status_word(), g_spin_limit.load(),
+                                                               g_stall.load());
     SFC_TRY(cudaGetLastError());
     ink = ok_;
     inv = ov;
   }
-  if (own) cudaFreeAsync(ws, st);
   return SFC_OK;
 }
 

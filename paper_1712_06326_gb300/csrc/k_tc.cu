@@ -543,8 +543,9 @@ int tc_prescore(const Geo& g, const float* grid, const uint8_t* cur_mask, const 
   __half *A = nullptr, *B = nullptr;
   unsigned* rng = nullptr;
   float* cent = nullptr;
-  SFC_TRY(pmalloc(&rng, sizeof(unsigned) * 2 * g.ch, st));
-  SFC_TRY(pmalloc(&cent, sizeof(float) * 2 * g.ch, st));
+  Scratch scr(st);  // freed on every return
+  SFC_TRY(scr.alloc(&rng, sizeof(unsigned) * 2 * g.ch));
+  SFC_TRY(scr.alloc(&cent, sizeof(float) * 2 * g.ch));
   SFC_TRY(cudaMemsetAsync(rng, 0xFF, sizeof(unsigned) * g.ch, st));
   SFC_TRY(cudaMemsetAsync(rng + g.ch, 0, sizeof(unsigned) * g.ch, st));
   count_launch();
@@ -576,8 +577,6 @@ int tc_prescore(const Geo& g, const float* grid, const uint8_t* cur_mask, const 
            2.0f * wh[c] * pm < 30000.0f;
     }
     if (!ok) {
-      cudaFreeAsync(rng, st);
-      cudaFreeAsync(cent, st);
       set_error("grid values or weights out of range for the FP16 tensor-core pre-score (need finite values, "
                 "max |value - mid-range| < 128, weights and 2 w |value - mid-range| < 30000; use SFC_FP32)");
       return SFC_EINVAL;
@@ -592,8 +591,8 @@ int tc_prescore(const Geo& g, const float* grid, const uint8_t* cur_mask, const 
   int64_t Nc = kChunkBytes / ((int64_t)Kp * 2) / kBN * kBN;
   if (Nc < kBN) Nc = kBN;
   if (Nc > Npad) Nc = Npad;
-  SFC_TRY(pmalloc(&A, sizeof(__half) * Qpad * Kp, st));
-  SFC_TRY(pmalloc(&B, sizeof(__half) * Nc * Kp, st));
+  SFC_TRY(scr.alloc(&A, sizeof(__half) * Qpad * Kp));
+  SFC_TRY(scr.alloc(&B, sizeof(__half) * Nc * Kp));
   count_launch();
   k_tc_prep_A<<<(unsigned)Qpad, 256, 0, st>>>(grid, cur_mask, g, centre_lin, Q, eoff_all, weights, mu, pmax, L,
                                                A, bound);
@@ -601,7 +600,7 @@ int tc_prescore(const Geo& g, const float* grid, const uint8_t* cur_mask, const 
   CUtensorMap mapA;
   SFC_CHECK(make_map(&mapA, A, Qpad, Kp, kBM));
   int* abort_all = nullptr;
-  SFC_TRY(pmalloc(&abort_all, sizeof(int), st));
+  SFC_TRY(scr.alloc(&abort_all, sizeof(int)));
   SFC_TRY(cudaMemsetAsync(abort_all, 0, sizeof(int), st));
   const size_t shm = (size_t)kStages * (kStageA + kStageB) + 1024;
   SFC_TRY(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
@@ -636,11 +635,6 @@ int tc_prescore(const Geo& g, const float* grid, const uint8_t* cur_mask, const 
     SFC_TRY(cudaGetLastError());
   }
   tc_trace_mark(2, st);
-  cudaFreeAsync(A, st);
-  cudaFreeAsync(B, st);
-  cudaFreeAsync(rng, st);
-  cudaFreeAsync(cent, st);
-  cudaFreeAsync(abort_all, st);
   return SFC_OK;
 }
 

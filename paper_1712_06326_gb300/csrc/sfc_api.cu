@@ -141,7 +141,17 @@ cudaMemPool_t g_pool[128] = {};
 bool g_pool_tried[128] = {};
 }  // namespace
 
+namespace {
+std::atomic<int64_t> g_fail_alloc{0};  // > 0: the g_fail_alloc-th next allocation fails (tests)
+std::atomic<int64_t> g_alloc_count{0};
+}  // namespace
+
 cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st) {
+  if (g_fail_alloc.load() > 0 && g_fail_alloc.fetch_sub(1) == 1) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  g_alloc_count.fetch_add(1);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -316,10 +326,22 @@ std::vector<int32_t> subsets_host(int ndim, int K, int C, int m) {
   return out;
 }
 
+// *dst = a new device copy of count host values (nullptr on failure: nothing
+// is left allocated)
 template <typename T>
 int upload(T** dst, const T* src, size_t count, cudaStream_t st) {
-  SFC_TRY(pmalloc(dst, sizeof(T) * (count ? count : 1), st));
-  if (count) SFC_TRY(cudaMemcpyAsync(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice, st));
+  *dst = nullptr;
+  T* d = nullptr;
+  SFC_TRY(pmalloc(&d, sizeof(T) * (count ? count : 1), st));
+  if (count) {
+    const cudaError_t e = cudaMemcpyAsync(d, src, sizeof(T) * count, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(d, st);
+      set_error(std::string("upload: ") + cudaGetErrorString(e));
+      return SFC_ECUDA;
+    }
+  }
+  *dst = d;
   return SFC_OK;
 }
 
@@ -619,19 +641,20 @@ int build_index(const float* grid, const uint8_t* dict_mask, const sfc_grid* gp,
   float* proj = nullptr;
   uint64_t* keys = nullptr;
   uint32_t* lohi = nullptr;
-  SFC_TRY(pmalloc(&proj, sizeof(float) * C * N * D, st));
-  SFC_TRY(pmalloc(&keys, sizeof(uint64_t) * C * N, st));
-  SFC_TRY(pmalloc(&lohi, sizeof(uint32_t) * 2 * C * D, st));
-  SFC_CHECK(project_sort_pipelined(ix, grid, proj, keys, lohi, st));
-  cudaFreeAsync(lohi, st);
-  if (ix.knn > 0) SFC_CHECK(sorted_coords(ix, proj, st));
-  trace_mark(ix, 6, st);
-  if (ix.keep) {
-    ix.proj = proj;
-    ix.keys = keys;
-  } else {
-    cudaFreeAsync(proj, st);
-    cudaFreeAsync(keys, st);
+  {
+    Scratch scr(st);
+    SFC_TRY(scr.alloc(&proj, sizeof(float) * C * N * D));
+    SFC_TRY(scr.alloc(&keys, sizeof(uint64_t) * C * N));
+    SFC_TRY(scr.alloc(&lohi, sizeof(uint32_t) * 2 * C * D));
+    SFC_CHECK(project_sort_pipelined(ix, grid, proj, keys, lohi, st));
+    if (ix.knn > 0) SFC_CHECK(sorted_coords(ix, proj, st));
+    trace_mark(ix, 6, st);
+    if (ix.keep) {
+      scr.keep(proj);
+      scr.keep(keys);
+      ix.proj = proj;
+      ix.keys = keys;
+    }
   }
   SFC_TRY(cudaGetLastError());
   if (ix.pca_done) {
@@ -1107,20 +1130,19 @@ int fullscan_query_batch(const float* grid, const uint8_t* dict_mask, const uint
   int64_t N = 0;
   int* eo = nullptr;
   float* wd = nullptr;
+  Scratch scr(st);  // dictionary and tables, freed on every return
   SFC_CHECK(dict_extract(dict_mask, g, st, &dict, &N));
+  scr.adopt(dict);
   if (N <= 0) {
-    if (dict) cudaFreeAsync(dict, st);
     set_error("the dictionary is empty (no fully known patch)");
     return SFC_EINVAL;
   }
   SFC_CHECK(upload_patch_tables(g, &eo, st));
+  scr.adopt(eo);
   SFC_CHECK(upload(&wd, w.data(), w.size(), st));
-  const int rc = tc ? fullscan_batch_tc(g, grid, cur_mask, dict, N, eo, wd, weighted, centres, Q, pick, cost, nullptr, st)
-                    : fullscan_batch(g, grid, cur_mask, dict, N, eo, wd, cm, centres, nullptr, Q, pick, cost, st);
-  cudaFreeAsync(dict, st);
-  cudaFreeAsync(eo, st);
-  cudaFreeAsync(wd, st);
-  return rc;
+  scr.adopt(wd);
+  return tc ? fullscan_batch_tc(g, grid, cur_mask, dict, N, eo, wd, weighted, centres, Q, pick, cost, nullptr, st)
+            : fullscan_batch(g, grid, cur_mask, dict, N, eo, wd, cm, centres, nullptr, Q, pick, cost, st);
 }
 
 int sfc_tc_prescores(const float* grid, const uint8_t* dict_mask, const uint8_t* cur_mask, const sfc_grid* gp,
@@ -1145,20 +1167,19 @@ int sfc_tc_prescores(const float* grid, const uint8_t* dict_mask, const uint8_t*
   int64_t N = 0;
   int* eo = nullptr;
   float* wd = nullptr;
+  Scratch scr(st);
   SFC_CHECK(dict_extract(dict_mask, g, st, &dict, &N));
+  scr.adopt(dict);
   *N_out = N;
   if (N <= 0) {
-    if (dict) cudaFreeAsync(dict, st);
     set_error("the dictionary is empty (no fully known patch)");
     return SFC_EINVAL;
   }
   SFC_CHECK(upload_patch_tables(g, &eo, st));
+  scr.adopt(eo);
   SFC_CHECK(upload(&wd, w.data(), w.size(), st));
-  int rc = tc_prescores_all(g, grid, cur_mask, dict, N, eo, wd, centres, Q, scores, bound, st);
-  cudaFreeAsync(dict, st);
-  cudaFreeAsync(eo, st);
-  cudaFreeAsync(wd, st);
-  return rc;
+  scr.adopt(wd);
+  return tc_prescores_all(g, grid, cur_mask, dict, N, eo, wd, centres, Q, scores, bound, st);
 }
 
 int inpaint_run(float* grid, uint8_t* mask, const sfc_grid* gp, const sfc_params* p, int32_t mode, int64_t max_steps,
@@ -1210,23 +1231,53 @@ int inpaint_run(float* grid, uint8_t* mask, const sfc_grid* gp, const sfc_params
     N = ix.N;
     eo = ix.eoff_all;
     wd = ix.weights;
-  } else {
-    SFC_CHECK(dict_extract(mask, g, st, &dict, &N));
-    SFC_CHECK(upload_patch_tables(g, &eo, st));
-    SFC_CHECK(upload(&wd, w.data(), w.size(), st));
-  }
-  rc = fill_loop(g, grid, mask, p->priority, mode, mode == SFC_MODE_SFC ? &ix : nullptr, dict, N, eo, wd, cm,
-                 max_steps, log, steps_done, st);
-  if (mode == SFC_MODE_SFC) {
+    rc = fill_loop(g, grid, mask, p->priority, mode, &ix, dict, N, eo, wd, cm, max_steps, log, steps_done, st);
     free_index(ix);
-  } else {
-    cudaStreamSynchronize(st);
-    if (dict) cudaFreeAsync(dict, st);
-    cudaFreeAsync(eo, st);
-    cudaFreeAsync(wd, st);
-    cudaStreamSynchronize(st);
+    return rc;
   }
+  {
+    Scratch scr(st);  // dictionary and tables of the full-scan mode
+    SFC_CHECK(dict_extract(mask, g, st, &dict, &N));
+    scr.adopt(dict);
+    SFC_CHECK(upload_patch_tables(g, &eo, st));
+    scr.adopt(eo);
+    SFC_CHECK(upload(&wd, w.data(), w.size(), st));
+    scr.adopt(wd);
+    rc = fill_loop(g, grid, mask, p->priority, mode, nullptr, dict, N, eo, wd, cm, max_steps, log, steps_done, st);
+  }
+  cudaStreamSynchronize(st);
   return rc;
+}
+
+int sfc_debug_fail_alloc(int64_t n) {
+  g_fail_alloc.store(n > 0 ? n : 0);
+  return SFC_OK;
+}
+
+int64_t sfc_debug_alloc_count(void) { return g_alloc_count.load(); }
+
+int sfc_debug_pool_used(uint64_t* bytes) {
+  g_err.clear();
+  if (!bytes) {
+    set_error("sfc_debug_pool_used: NULL pointer");
+    return SFC_EINVAL;
+  }
+  *bytes = 0;
+  int dev = 0;
+  SFC_TRY(cudaGetDevice(&dev));
+  SFC_TRY(cudaDeviceSynchronize());
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (dev >= 0 && dev < 128) pool = g_pool[dev];
+  }
+  if (pool) SFC_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, bytes));
+  return SFC_OK;
+}
+
+int sfc_debug_lookback(int64_t spin_limit, int32_t stall) {
+  sort_lookback_test(spin_limit, stall);
+  return SFC_OK;
 }
 
 int sfc_status(void* stream) {

@@ -30,7 +30,8 @@ EXPORTS = ["sfc_params_default", "sfc_index_build", "sfc_index_destroy", "sfc_in
            "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "fullscan_query_batch_static",
            "sfc_tc_prescores", "inpaint_run", "sfc_status", "sfc_launch_count", "sfc_trace", "sfc_trace_read", "sfc_trace_tc_read",
            "sfc_last_error", "sfc_index_save", "sfc_index_load", "sfc_index_params", "sfc_query_batch_dict",
-           "sfc_multi_create", "sfc_multi_query", "sfc_multi_destroy", "sfc_autotune", "sfc_tune_select", "sfc_trace_eig_read"]
+           "sfc_multi_create", "sfc_multi_query", "sfc_multi_destroy", "sfc_autotune", "sfc_tune_select", "sfc_trace_eig_read",
+           "sfc_debug_fail_alloc", "sfc_debug_alloc_count", "sfc_debug_pool_used", "sfc_debug_lookback"]
 TRACE_PHASES = ("dictionary", "moments", "eigen", "finalize", "project_keys", "sort")
 
 
@@ -102,6 +103,14 @@ def lib():
         L.sfc_trace_eig_read.restype = C.c_int
         L.sfc_trace_tc_read.argtypes = [vp, vp, vp]
         L.sfc_trace_tc_read.restype = C.c_int
+        L.sfc_debug_fail_alloc.argtypes = [i64]
+        L.sfc_debug_fail_alloc.restype = C.c_int
+        L.sfc_debug_alloc_count.argtypes = []
+        L.sfc_debug_alloc_count.restype = i64
+        L.sfc_debug_pool_used.argtypes = [vp]
+        L.sfc_debug_pool_used.restype = C.c_int
+        L.sfc_debug_lookback.argtypes = [i64, i32]
+        L.sfc_debug_lookback.restype = C.c_int
         for name in ["sfc_index_build", "sfc_index_destroy", "sfc_index_info", "sfc_index_export",
                      "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "fullscan_query_batch_static",
                      "sfc_tc_prescores", "inpaint_run", "sfc_status", "sfc_index_save", "sfc_index_load",
@@ -472,3 +481,23 @@ def sfc_trace_tc_read() -> dict:
 
 def sfc_status() -> int:
     return lib().sfc_status(_stream())
+
+
+def sfc_debug_fail_alloc(n: int) -> None:
+    """Failure injection (tests): the n-th library allocation from now on fails (0: off)."""
+    _check(lib().sfc_debug_fail_alloc(int(n)), "sfc_debug_fail_alloc")
+
+
+def sfc_debug_alloc_count() -> int:
+    return int(lib().sfc_debug_alloc_count())
+
+
+def sfc_debug_pool_used() -> int:
+    v = C.c_uint64()
+    _check(lib().sfc_debug_pool_used(C.byref(v)), "sfc_debug_pool_used")
+    return int(v.value)
+
+
+def sfc_debug_lookback(spin_limit: int = 0, stall: bool = False) -> None:
+    """Failure injection (tests): the radix sort's look-back poll limit and stall switch."""
+    _check(lib().sfc_debug_lookback(int(spin_limit), 1 if stall else 0), "sfc_debug_lookback")
