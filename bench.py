@@ -880,6 +880,31 @@ def main():
               "query_qps": Q / (statistics.mean(st_ms["query"]) / 1000.0),
               "picks_equal_built_index": bool(torch.equal(lp, pick))}
 
+    # ---- several GPUs: the full scan of the same targets with the dictionary
+    # split over the ranks (one all-reduce-min + one all-gather per batch) ----
+    split = None
+    if world > 1:
+        try:
+            from paper_1712_06326_gb300 import shard as SH
+
+            sp_ms = []
+            for r in range(3):
+                barrier()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                spk, spc = SH.fullscan_dict_split(gd, md, md, tsub, K=WORKLOAD["K"])
+                torch.cuda.synchronize()
+                if r > 0:
+                    sp_ms.append(1000 * (time.perf_counter() - t0))
+            sp_ms_max = max_over_ranks(statistics.mean(sp_ms), dev)
+            split = {"ranks": world, "queries": fs_q, "ms": sp_ms_max, "qps": fs_q / (sp_ms_max / 1000.0),
+                     "scaling": "strong (one batch, the dictionary shared out)",
+                     "picks_and_costs_equal_single_gpu": bool(torch.equal(spk, fp) and
+                                                              torch.equal(spc.view(torch.int32),
+                                                                          fc.view(torch.int32)))}
+        except Exception as e:  # reported, not fatal: the headline does not depend on it
+            split = {"error": f"{type(e).__name__}: {e}"}
+
     # ---- the PCA over every dictionary entry instead of a 16,384-entry sample --
     pca_all = pca_sample_comparison(sfc, torch, gd, md, td, prm, flush, stream, ex_h, fp, fc, sel, statistics.mean(
         step_ms))
@@ -974,6 +999,8 @@ def main():
             "stored_index": stored, "inpaint_128x128": inp,
             "batch_256": batch}
     line.update({"pca_sample_all": pca_all, "inpaint_1024": fill_big, "volumes": volumes})
+    if split is not None:
+        line["fullscan_dict_split"] = split
     if rank == 0:
         if not args.no_cpu_baseline:
             gpu = {"g": g, "m": m, "t": t, "ex": ex_h, "pick": pick.cpu().numpy(), "cost": cost.cpu().numpy(),

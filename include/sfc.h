@@ -272,6 +272,41 @@ int fullscan_query_batch_static(const float* grid, const uint8_t* dict_mask, con
                                 const sfc_grid* g, const sfc_params* p, const int32_t* centres, int64_t Q,
                                 int64_t* pick, float* cost, void* stream);
 
+/* ---- The full scan split over dictionary shards (several GPUs) ------------
+ * One exact full scan (Sec. I) over a dictionary shared out among S shards,
+ * e.g. one per GPU: shard s owns the dictionary ids [floor(s N / S),
+ * floor((s + 1) N / S)).  Per query batch:
+ *   sfc_shard_scan  -- the shard's FP32 scan; min32 (device, Q uint32) gets the
+ *                      shard's minimum FP32 cost as float bits (+inf bits for
+ *                      an empty shard; costs are >= 0, so the bits order like
+ *                      the values);
+ *   (caller)        -- gmin32 = the element-wise minimum of min32 over all
+ *                      shards (e.g. an all-reduce-min);
+ *   sfc_shard_band  -- every shard entry inside the FP32 error band of gmin32
+ *                      rescored with the exact FP64 cost; cost64 (device, Q
+ *                      doubles), id (device, Q int64, ids of the whole
+ *                      dictionary) and cost32 (device, Q floats) get the
+ *                      shard's (cost64, id) minimum and its FP32 cost, or
+ *                      (+inf, -1, +inf) if the shard holds no band entry;
+ *   (caller)        -- the pick is the (cost64, id) minimum over the shards
+ *                      (e.g. an all-gather of 20 bytes per query and shard),
+ *                      its cost the FP32 cost reported with it.
+ * The result equals fullscan_query_batch's picks and costs (SFC_FP32 only).  An
+ * invalid centre gives (NaN, -1, NaN) on every shard (and SFC_EDEVICE from
+ * sfc_status()).  sfc_shard_create extracts the dictionary (synchronises
+ * `stream` once), keeps the centres' indices and the scan's scratch; the shard
+ * refers to grid and cur_mask (device, the caller keeps them alive) and must be
+ * used on the device it was created on.  sfc_shard_range reports N and the
+ * shard's [j0, j1); any output may be NULL. */
+typedef struct sfc_shard sfc_shard;
+int sfc_shard_create(const float* grid, const uint8_t* dict_mask, const uint8_t* cur_mask, const sfc_grid* g,
+                     const sfc_params* p, const int32_t* centres, int64_t Q, int32_t shard, int32_t nshards,
+                     void* stream, sfc_shard** out);
+int sfc_shard_range(const sfc_shard* s, int64_t* N, int64_t* j0, int64_t* j1);
+int sfc_shard_scan(sfc_shard* s, uint32_t* min32, void* stream);
+int sfc_shard_band(sfc_shard* s, const uint32_t* gmin32, double* cost64, int64_t* id, float* cost32, void* stream);
+int sfc_shard_destroy(sfc_shard* s);
+
 /* Exemplar-based inpainting loop (Sec. I; Fig. 1(a)): repeat { find the fill
  * front (known pixels with an unknown axis neighbour; centres moved inside the
  * valid range), take the centre of highest priority (ties: lowest linear

@@ -205,6 +205,17 @@ int fullscan_batch_into(const Geo& g, const float* grid, const uint8_t* cur_mask
                         int64_t* pick, float* cost, int64_t* lin, uint8_t* bad, unsigned int* gmin, float* tilemin,
                         cudaStream_t st);
 
+// Dictionary split of the full scan (one shard's part; see k_fullscan.cu).
+int64_t fullscan_range_tiles(int64_t n);
+int fullscan_range_scan(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t n,
+                        const int* eoff_all, const float* weights, int cm, const int64_t* lin, int64_t Q,
+                        float* tilemin, unsigned int* gmin, cudaStream_t st);
+int fullscan_range_band(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t n,
+                        const int* eoff_all, const float* weights, int cm, const int64_t* lin, int64_t Q,
+                        const uint8_t* bad, const float* tilemin, const unsigned int* gmin, int64_t id_base,
+                        int64_t* id, float* cost32, double* cost64, cudaStream_t st);
+int centres_to_lin(const Geo& g, const int32_t* centres, int64_t Q, int64_t* lin, uint8_t* bad, cudaStream_t st);
+
 // helpers (sfc_api.cu)
 int upload_patch_tables(const Geo& g, int** eoff_all, cudaStream_t st);
 int check_device();

@@ -132,7 +132,13 @@ __device__ inline float cost32_one(const float* __restrict__ grid, int64_t sb, c
   return acc;
 }
 
-template <int EPT, int CM>
+// RANGE: the band pass of one shard of a dictionary split (the entries dict[0,
+// N) are ids id_base + [0, N) of the whole dictionary, gmin is the minimum over
+// every shard): every in-band entry of the shard is rescored in FP64 (no
+// single-entry shortcut, since other shards may hold band entries too) and the
+// shard's (FP64 cost, id, FP32 cost) minimum is written to cost64 / pick / cost
+// (+inf, -1, +inf when the shard holds no band entry).
+template <int EPT, int CM, bool RANGE = false>
 __global__ void __launch_bounds__(kFsThreads) k_fs_band(const float* __restrict__ grid,
                                                         const uint8_t* __restrict__ mask, Geo g,
                                                         const uint32_t* __restrict__ dict, int64_t N,
@@ -141,7 +147,8 @@ __global__ void __launch_bounds__(kFsThreads) k_fs_band(const float* __restrict_
                                                         const int64_t* __restrict__ centre_lin,
                                                         const float* __restrict__ tilemin,
                                                         const unsigned int* __restrict__ gmin, int64_t ntiles,
-                                                        int64_t* __restrict__ pick, float* __restrict__ cost) {
+                                                        int64_t* __restrict__ pick, float* __restrict__ cost,
+                                                        double* __restrict__ cost64 = nullptr, int64_t id_base = 0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = g.n, ch = g.ch, P = g.P;
   float2* am = reinterpret_cast<float2*>(smem_raw);
@@ -187,7 +194,7 @@ __global__ void __launch_bounds__(kFsThreads) k_fs_band(const float* __restrict_
   }
   __syncthreads();
   const int cnt = s_cnt;
-  if (cnt == 1) {
+  if (!RANGE && cnt == 1) {
     if (threadIdx.x == 0) {
       pick[q] = s_j[0];
       cost[q] = s_c[0];
@@ -254,7 +261,12 @@ __global__ void __launch_bounds__(kFsThreads) k_fs_band(const float* __restrict_
         bj = si[w];
         bc32 = sf[w];
       }
-    if (bj == INT64_MAX) {
+    if (RANGE) {
+      const bool none = bj == INT64_MAX;
+      pick[q] = none ? -1 : id_base + bj;
+      cost[q] = none ? __int_as_float(0x7f800000) : bc32;
+      cost64[q] = none ? __longlong_as_double(0x7ff0000000000000ll) : bc;
+    } else if (bj == INT64_MAX) {
       pick[q] = -1;
       cost[q] = __int_as_float(0x7fc00000);
     } else {
@@ -562,7 +574,104 @@ int band_cm(int cm, const Geo& g, const float* grid, const uint8_t* cur_mask, co
   }
 }
 
+template <int EPT, int W>
+int run_band_range(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
+                   const int* eoff_all, const float* weights, const int64_t* lin, int64_t Q, const float* tilemin,
+                   const unsigned int* gmin, int64_t ntiles, int64_t id_base, int64_t* id, float* cost32,
+                   double* cost64, cudaStream_t st) {
+  const size_t shm = (size_t)g.n * 20 + (size_t)g.P + 16;
+  if (shm > kSmemOptIn)
+    SFC_TRY(cudaFuncSetAttribute(k_fs_band<EPT, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  count_launch();
+  k_fs_band<EPT, W, true><<<(unsigned)Q, kFsThreads, shm, st>>>(grid, cur_mask, g, dict, N, eoff_all, weights, lin,
+                                                                tilemin, gmin, ntiles, id, cost32, cost64, id_base);
+  SFC_TRY(cudaGetLastError());
+  return SFC_OK;
+}
+
+// shard outputs of the queries whose centre is invalid: id -1, costs NaN
+__global__ void k_mark_bad_range(const uint8_t* bad, int64_t Q, int64_t* id, float* cost32, double* cost64) {
+  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q < Q && bad[q]) {
+    id[q] = -1;
+    cost32[q] = __int_as_float(0x7fc00000);
+    cost64[q] = __longlong_as_double(0x7ff8000000000000ll);
+  }
+}
+
+__global__ void k_fill_range_empty(int64_t Q, int64_t* id, float* cost32, double* cost64) {
+  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q < Q) {
+    id[q] = -1;
+    cost32[q] = __int_as_float(0x7f800000);
+    cost64[q] = __longlong_as_double(0x7ff0000000000000ll);
+  }
+}
+
 }  // namespace
+
+constexpr int kRangeEPT = 4;
+int64_t fullscan_range_tiles(int64_t n) { return (n + kFsThreads * kRangeEPT - 1) / (kFsThreads * kRangeEPT); }
+
+// Shard scan of a dictionary split: the FP32 pass over dict[0, n) (one shard's
+// entries) for Q valid centres `lin`; gmin (Q words) receives the shard's
+// per-query minimum FP32 cost as float bits (+inf for an empty shard); tilemin
+// (Q * fullscan_range_tiles(n) floats) keeps the tile minima for the band pass.
+int fullscan_range_scan(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t n,
+                        const int* eoff_all, const float* weights, int cm, const int64_t* lin, int64_t Q,
+                        float* tilemin, unsigned int* gmin, cudaStream_t st) {
+  if (Q <= 0) return SFC_OK;
+  count_launch();
+  k_fill_u32<<<(unsigned)((Q + 255) / 256), 256, 0, st>>>(gmin, Q, 0x7f800000u);
+  SFC_TRY(cudaGetLastError());
+  if (n <= 0) return SFC_OK;
+  const int64_t ntiles = fullscan_range_tiles(n);
+  return Q >= 8 ? scan_cm<8, kRangeEPT>(cm, g, grid, cur_mask, dict, n, eoff_all, weights, lin, Q, tilemin, gmin,
+                                        ntiles, st)
+                : scan_cm<1, kRangeEPT>(cm, g, grid, cur_mask, dict, n, eoff_all, weights, lin, Q, tilemin, gmin,
+                                        ntiles, st);
+}
+
+// Shard band pass: gmin = the minimum over all shards; writes the shard's
+// (cost64, id, cost32) minimum over its in-band entries, ids offset by id_base.
+int fullscan_range_band(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t n,
+                        const int* eoff_all, const float* weights, int cm, const int64_t* lin, int64_t Q,
+                        const uint8_t* bad, const float* tilemin, const unsigned int* gmin, int64_t id_base,
+                        int64_t* id, float* cost32, double* cost64, cudaStream_t st) {
+  if (Q <= 0) return SFC_OK;
+  const unsigned qb = (unsigned)((Q + 255) / 256);
+  if (n <= 0) {
+    count_launch();
+    k_fill_range_empty<<<qb, 256, 0, st>>>(Q, id, cost32, cost64);
+  } else {
+    const int64_t ntiles = fullscan_range_tiles(n);
+    int rc;
+    switch (cm & 3) {
+      case 0: rc = run_band_range<kRangeEPT, 0>(g, grid, cur_mask, dict, n, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, id_base, id, cost32, cost64, st); break;
+      case 1: rc = run_band_range<kRangeEPT, 1>(g, grid, cur_mask, dict, n, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, id_base, id, cost32, cost64, st); break;
+      case 2: rc = run_band_range<kRangeEPT, 2>(g, grid, cur_mask, dict, n, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, id_base, id, cost32, cost64, st); break;
+      default: rc = run_band_range<kRangeEPT, 3>(g, grid, cur_mask, dict, n, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, id_base, id, cost32, cost64, st); break;
+    }
+    SFC_CHECK(rc);
+  }
+  count_launch();
+  k_mark_bad_range<<<qb, 256, 0, st>>>(bad, Q, id, cost32, cost64);
+  SFC_TRY(cudaGetLastError());
+  return SFC_OK;
+}
+
+// Centre rows -> linear indices for a shard (invalid centres: a stand-in index
+// and bad[q] = 1; the status word is flagged as for every full scan).
+int centres_to_lin(const Geo& g, const int32_t* centres, int64_t Q, int64_t* lin, uint8_t* bad, cudaStream_t st) {
+  if (Q <= 0) return SFC_OK;
+  const unsigned qb = (unsigned)((Q + 255) / 256);
+  count_launch();
+  k_centre_lin<<<qb, 256, 0, st>>>(centres, Q, g, lin, status_word());
+  count_launch();
+  k_centre_fix<<<qb, 256, 0, st>>>(lin, Q, g, bad);
+  SFC_TRY(cudaGetLastError());
+  return SFC_OK;
+}
 
 // One query whose centre (linear index) is already on the device and valid; the
 // caller owns the tile-minimum buffer (ceil(N / 1024) floats) and gmin.

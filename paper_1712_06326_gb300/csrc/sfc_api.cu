@@ -174,8 +174,9 @@ cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st) {
     }
     pool = g_pool[dev];
   }
-  if (pool) return cudaMallocFromPoolAsync(p, bytes, pool, st);
-  return cudaMallocAsync(p, bytes, st);
+  const cudaError_t e2 = pool ? cudaMallocFromPoolAsync(p, bytes, pool, st) : cudaMallocAsync(p, bytes, st);
+  if (e2 != cudaSuccess) *p = nullptr;
+  return e2;
 }
 
 namespace {

@@ -31,7 +31,8 @@ EXPORTS = ["sfc_params_default", "sfc_index_build", "sfc_index_destroy", "sfc_in
            "sfc_tc_prescores", "inpaint_run", "sfc_status", "sfc_launch_count", "sfc_trace", "sfc_trace_read", "sfc_trace_tc_read",
            "sfc_last_error", "sfc_index_save", "sfc_index_load", "sfc_index_params", "sfc_query_batch_dict",
            "sfc_multi_create", "sfc_multi_query", "sfc_multi_destroy", "sfc_autotune", "sfc_tune_select", "sfc_trace_eig_read",
-           "sfc_debug_fail_alloc", "sfc_debug_alloc_count", "sfc_debug_pool_used", "sfc_debug_lookback"]
+           "sfc_debug_fail_alloc", "sfc_debug_alloc_count", "sfc_debug_pool_used", "sfc_debug_lookback",
+           "sfc_shard_create", "sfc_shard_range", "sfc_shard_scan", "sfc_shard_band", "sfc_shard_destroy"]
 TRACE_PHASES = ("dictionary", "moments", "eigen", "finalize", "project_keys", "sort")
 
 
@@ -111,6 +112,14 @@ def lib():
         L.sfc_debug_pool_used.restype = C.c_int
         L.sfc_debug_lookback.argtypes = [i64, i32]
         L.sfc_debug_lookback.restype = C.c_int
+        L.sfc_shard_create.argtypes = [vp, vp, vp, C.POINTER(sfc_grid), C.POINTER(sfc_params), vp, i64, i32, i32, vp,
+                                       C.POINTER(vp)]
+        L.sfc_shard_range.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+        L.sfc_shard_scan.argtypes = [vp, vp, vp]
+        L.sfc_shard_band.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.sfc_shard_destroy.argtypes = [vp]
+        for name in ["sfc_shard_create", "sfc_shard_range", "sfc_shard_scan", "sfc_shard_band", "sfc_shard_destroy"]:
+            getattr(L, name).restype = C.c_int
         for name in ["sfc_index_build", "sfc_index_destroy", "sfc_index_info", "sfc_index_export",
                      "sfc_query_batch", "sfc_query_candidates", "fullscan_query_batch", "fullscan_query_batch_static",
                      "sfc_tc_prescores", "inpaint_run", "sfc_status", "sfc_index_save", "sfc_index_load",
