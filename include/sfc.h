@@ -98,7 +98,9 @@ typedef struct sfc_params {
   const float* basis;     /* host, curves*s*D FP32 basis (row i = subset value i), or NULL = PCA */
   const float* mean;      /* host, curves*s FP32 means (required with basis) */
   int32_t select;         /* SFC_SELECT_ALL or SFC_SELECT_BEST (Fig. 1(b)) */
-  int32_t precision;      /* SFC_FP32; fullscan_query_batch also takes SFC_FP16 (tensor-core pre-score) */
+  int32_t precision;      /* SFC_FP32; fullscan_query_batch also takes SFC_FP16 (tensor-core pre-score);
+                             sfc_index_build also takes SFC_BF16 (the precision tier: dictionary projections
+                             on tensor cores, stored in BF16) */
   int64_t pca_sample;     /* dictionary entries used for the covariance; <= 0: all */
   int32_t priority;       /* fill order: SFC_PRIO_CONFIDENCE or SFC_PRIO_CRIMINISI (2-D) */
   int32_t keep_intermediates; /* 1: keep projections and unsorted keys for sfc_index_export */
@@ -129,7 +131,16 @@ void sfc_params_default(sfc_params* p);
  * are solved completely by FP64 Jacobi; longer ones by subspace iteration,
  * taken over by Jacobi (up to 112 values) where the iteration stalls.
  * SFC_EINVAL if the dictionary is empty; SFC_ENOCONV (no index is returned) if
- * an eigen-solve did not converge. */
+ * an eigen-solve did not converge.
+ *
+ * Precision tier (p->precision = SFC_BF16): the dictionary's projections are
+ * one tensor-core GEMM for every index at once (tcgen05, BF16 operands, FP32
+ * accumulation): the whole patch, centred per element by its mean and rounded
+ * to BF16, times the indices' basis columns in BF16 (zero outside each index's
+ * subset), rounded to BF16 -- the stored projections (exported widened to
+ * FP32).  The quantiser's range and the keys come from these values; queries
+ * still project in FP32 and every pick is rescored exactly, so only the
+ * candidate windows differ from the FP32 index.  Requires curves * dims <= 256. */
 int sfc_index_build(const float* grid, const uint8_t* dict_mask, const sfc_grid* g, const sfc_params* p,
                     void* stream, sfc_index** out);
 

@@ -121,6 +121,7 @@ struct Index {
   int* eig_iters = nullptr;    // 2C (device): FP64 then FP32 products A Q computed per index
   int eig_per_orth = 1;        // products per orthonormalisation (2 on the cluster path)
   int* pca_done = nullptr;     // C (device): 1 where the eigen-solve converged (PCA builds only)
+  bool bf16 = false;           // precision tier: projections on tensor cores, stored as BF16 (proj holds BF16)
 };
 
 // Record phase boundary k of a traced build (no-op otherwise).
@@ -146,6 +147,13 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st);
 // lohi, 2 words per axis of every curve, and lo / scale), then keys.
 int project_curves(Index& ix, const float* grid, float* proj, uint32_t* lohi, int c0, int nc, cudaStream_t st);
 int key_curves(Index& ix, const float* proj, uint64_t* keys, int c0, int nc, cudaStream_t st);
+// lohi (2 words per axis of every curve) reset, and lo / scale of every curve from it
+int lohi_init(uint32_t* lohi, int n, cudaStream_t st);
+int lohi_to_scale(Index& ix, const uint32_t* lohi, cudaStream_t st);
+// k_proj_tc.cu: the BF16 tier -- every curve's projections (proj as BF16
+// [C][N][D]) by one tensor-core GEMM, with the per-axis minima / maxima in lohi
+// (initialised here) and lo / scale; keys then come from key_curves.
+int project_bf16(Index& ix, const float* grid, void* proj, uint32_t* lohi, cudaStream_t st);
 // The library's auxiliary streams of the current device (k < kAuxStreams,
 // default priority) and one of the highest priority, created on first use,
 // non-blocking; nullptr if a stream cannot be created.

@@ -11,6 +11,8 @@
 // if hi == lo), then q + shift.  Key: bits interleaved highest plane first,
 // dimension 0 first inside a plane (the highest-variance axis first, Sec. II.C);
 // the top 64 bits when D * b' > 64.
+#include <cuda_bf16.h>
+
 #include "internal.cuh"
 
 namespace sfc {
@@ -159,23 +161,28 @@ __global__ void k_scale(const uint32_t* __restrict__ lohi, int n, int bits, floa
 
 namespace {
 
-template <int D>
-__global__ void k_keys(const float* __restrict__ proj, int64_t N, int bits, int bp, int curve,
+// projections are FP32, or BF16 (the precision tier) widened exactly to FP32
+__device__ inline float proj_f(float v) { return v; }
+__device__ inline float proj_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <int D, typename T>
+__global__ void k_keys(const T* __restrict__ proj, int64_t N, int bits, int bp, int curve,
                        const float* __restrict__ lo, const float* __restrict__ scale,
                        const int32_t* __restrict__ shifts, uint64_t* __restrict__ keys, int c0) {
   const int c = c0 + blockIdx.y;
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= N) return;
   uint32_t q[D];
-  const float* y = proj + ((int64_t)c * N + j) * D;
+  const T* y = proj + ((int64_t)c * N + j) * D;
 #pragma unroll
   for (int k = 0; k < D; ++k)
-    q[k] = quantise_one(y[k], lo[c * D + k], scale[c * D + k], bits) + (uint32_t)shifts[c * D + k];
+    q[k] = quantise_one(proj_f(y[k]), lo[c * D + k], scale[c * D + k], bits) + (uint32_t)shifts[c * D + k];
   keys[(int64_t)c * N + j] = curve == SFC_CURVE_HILBERT ? hilbert_key_t<D>(q, bp) : morton_key_t<D>(q, bp);
 }
 
 // sqc[c][i][k] = quantised shifted coordinate k of the entry at sorted slot i of index c
-__global__ void k_sorted_coords(const float* __restrict__ proj, const uint32_t* __restrict__ sids, int64_t N, int D,
+template <typename T>
+__global__ void k_sorted_coords(const T* __restrict__ proj, const uint32_t* __restrict__ sids, int64_t N, int D,
                                 int bits, const float* __restrict__ lo, const float* __restrict__ scale,
                                 const int32_t* __restrict__ shifts, uint32_t* __restrict__ sqc) {
   const int c = blockIdx.y;
@@ -184,7 +191,7 @@ __global__ void k_sorted_coords(const float* __restrict__ proj, const uint32_t* 
   const int64_t i = t / D;
   const int k = (int)(t - i * D);
   const int64_t j = sids[(int64_t)c * N + i];
-  const float y = proj[((int64_t)c * N + j) * D + k];
+  const float y = proj_f(proj[((int64_t)c * N + j) * D + k]);
   sqc[(int64_t)c * N * D + t] = quantise_one(y, lo[c * D + k], scale[c * D + k], bits) + (uint32_t)shifts[c * D + k];
 }
 
@@ -205,7 +212,12 @@ template <int D>
 int launch_keys(const Index& ix, const float* proj, uint64_t* keys, int c0, int nc, cudaStream_t st) {
   dim3 grd((unsigned)((ix.N + 255) / 256), nc);
   count_launch();
-  k_keys<D><<<grd, 256, 0, st>>>(proj, ix.N, ix.bits, ix.bp, ix.curve, ix.lo, ix.scale, ix.shifts, keys, c0);
+  if (ix.bf16)
+    k_keys<D, __nv_bfloat16><<<grd, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(proj), ix.N, ix.bits,
+                                                   ix.bp, ix.curve, ix.lo, ix.scale, ix.shifts, keys, c0);
+  else
+    k_keys<D, float><<<grd, 256, 0, st>>>(proj, ix.N, ix.bits, ix.bp, ix.curve, ix.lo, ix.scale, ix.shifts, keys,
+                                          c0);
   SFC_TRY(cudaGetLastError());
   return SFC_OK;
 }
@@ -233,6 +245,21 @@ int project_curves(Index& ix, const float* grid, float* proj, uint32_t* lohi, in
   return SFC_OK;
 }
 
+int lohi_init(uint32_t* lohi, int n, cudaStream_t st) {
+  count_launch();
+  k_lohi_init<<<(n + 127) / 128, 128, 0, st>>>(lohi, n);
+  SFC_TRY(cudaGetLastError());
+  return SFC_OK;
+}
+
+int lohi_to_scale(Index& ix, const uint32_t* lohi, cudaStream_t st) {
+  const int n = ix.C * ix.D;
+  count_launch();
+  k_scale<<<(n + 127) / 128, 128, 0, st>>>(lohi, n, ix.bits, ix.lo, ix.scale);
+  SFC_TRY(cudaGetLastError());
+  return SFC_OK;
+}
+
 int key_curves(Index& ix, const float* proj, uint64_t* keys, int c0, int nc, cudaStream_t st) {
   int rc = SFC_EINVAL;
   switch (ix.D) {
@@ -250,7 +277,12 @@ int sorted_coords(Index& ix, const float* proj, cudaStream_t st) {
   SFC_TRY(pmalloc(&ix.sqc, sizeof(uint32_t) * ix.C * ix.N * ix.D, st));
   dim3 grd((unsigned)((ix.N * ix.D + 255) / 256), ix.C);
   count_launch();
-  k_sorted_coords<<<grd, 256, 0, st>>>(proj, ix.sids, ix.N, ix.D, ix.bits, ix.lo, ix.scale, ix.shifts, ix.sqc);
+  if (ix.bf16)
+    k_sorted_coords<__nv_bfloat16><<<grd, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(proj), ix.sids, ix.N,
+                                                        ix.D, ix.bits, ix.lo, ix.scale, ix.shifts, ix.sqc);
+  else
+    k_sorted_coords<float><<<grd, 256, 0, st>>>(proj, ix.sids, ix.N, ix.D, ix.bits, ix.lo, ix.scale, ix.shifts,
+                                                ix.sqc);
   SFC_TRY(cudaGetLastError());
   return SFC_OK;
 }

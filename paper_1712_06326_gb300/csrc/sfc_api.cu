@@ -456,7 +456,10 @@ int project_sort_pipelined(Index& ix, const float* grid, float* proj, uint64_t* 
   int nlo = 0;
   while (nlo < kAuxStreams && (lo[nlo] = aux_stream(nlo)) != nullptr) ++nlo;
   if (!hi || nlo == 0) {  // no library streams: everything in order on st
-    SFC_CHECK(project_curves(ix, grid, proj, lohi, 0, C, st));
+    if (ix.bf16)
+      SFC_CHECK(project_bf16(ix, grid, proj, lohi, st));
+    else
+      SFC_CHECK(project_curves(ix, grid, proj, lohi, 0, C, st));
     SFC_CHECK(key_curves(ix, proj, keys, 0, C, st));
     trace_mark(ix, 5, st);
     return radix_sort_pairs(keys, ix.skeys, ix.sids, N, C, key_bits, st);
@@ -492,7 +495,11 @@ int project_sort_pipelined(Index& ix, const float* grid, float* proj, uint64_t* 
   int sorted = 0;  // groups whose sort stream recorded ev_done
   for (int g = 0; g < G && rc == SFC_OK; ++g) {
     const int c0 = g * per, nc = std::min(per, C - c0);
-    rc = project_curves(ix, grid, proj, lohi, c0, nc, hi);
+    // (BF16 tier: one tensor-core launch projects every curve, before the first group's keys)
+    if (!ix.bf16)
+      rc = project_curves(ix, grid, proj, lohi, c0, nc, hi);
+    else if (g == 0)
+      rc = project_bf16(ix, grid, proj, lohi, hi);
     if (rc == SFC_OK) rc = key_curves(ix, proj, keys, c0, nc, hi);
     if (rc == SFC_OK && cudaEventRecord(ev_keys[g], hi) != cudaSuccess) rc = SFC_ECUDA;
     if (rc != SFC_OK) break;
@@ -552,10 +559,12 @@ int build_index(const float* grid, const uint8_t* dict_mask, const sfc_grid* gp,
     set_error("the k-NN search (knn > 0) runs on the z-curve (SFC_CURVE_MORTON) only");
     return SFC_EUNSUPPORTED;
   }
-  if (p->precision != SFC_FP32) {
-    set_error("the index path computes in FP32 (precision must be SFC_FP32)");
+  if (p->precision != SFC_FP32 && p->precision != SFC_BF16) {
+    set_error("the index path takes SFC_FP32 (exact FMA-chain projections) or SFC_BF16 (tensor-core projections, "
+              "stored in BF16)");
     return SFC_EUNSUPPORTED;
   }
+  ix.bf16 = p->precision == SFC_BF16;
   ix.C = p->curves;
   ix.D = p->dims;
   ix.bits = p->bits;
@@ -644,7 +653,7 @@ int build_index(const float* grid, const uint8_t* dict_mask, const sfc_grid* gp,
   uint32_t* lohi = nullptr;
   {
     Scratch scr(st);
-    SFC_TRY(scr.alloc(&proj, sizeof(float) * C * N * D));
+    SFC_TRY(scr.alloc(&proj, (ix.bf16 ? 2 : sizeof(float)) * C * N * D));
     SFC_TRY(scr.alloc(&keys, sizeof(uint64_t) * C * N));
     SFC_TRY(scr.alloc(&lohi, sizeof(uint32_t) * 2 * C * D));
     SFC_CHECK(project_sort_pipelined(ix, grid, proj, keys, lohi, st));
@@ -799,7 +808,15 @@ int sfc_index_export(const sfc_index* h, int64_t* dict, int32_t* subsets, float*
   if (evals) SFC_TRY(cudaMemcpy(evals, ix.evals, sizeof(double) * C * s, cudaMemcpyDeviceToHost));
   if (lo) SFC_TRY(cudaMemcpy(lo, ix.lo, sizeof(float) * C * D, cudaMemcpyDeviceToHost));
   if (scale) SFC_TRY(cudaMemcpy(scale, ix.scale, sizeof(float) * C * D, cudaMemcpyDeviceToHost));
-  if (proj) SFC_TRY(cudaMemcpy(proj, ix.proj, sizeof(float) * C * N * D, cudaMemcpyDeviceToHost));
+  if (proj && !ix.bf16) SFC_TRY(cudaMemcpy(proj, ix.proj, sizeof(float) * C * N * D, cudaMemcpyDeviceToHost));
+  if (proj && ix.bf16) {  // stored in BF16: widened exactly to FP32
+    std::vector<uint16_t> h((size_t)C * N * D);
+    SFC_TRY(cudaMemcpy(h.data(), ix.proj, sizeof(uint16_t) * h.size(), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < h.size(); ++i) {
+      const uint32_t u = (uint32_t)h[i] << 16;
+      std::memcpy(&proj[i], &u, sizeof(float));
+    }
+  }
   if (keys) SFC_TRY(cudaMemcpy(keys, ix.keys, sizeof(uint64_t) * C * N, cudaMemcpyDeviceToHost));
   if (skeys) SFC_TRY(cudaMemcpy(skeys, ix.skeys, sizeof(uint64_t) * C * N, cudaMemcpyDeviceToHost));
   if (sids) SFC_TRY(cudaMemcpy(sids, ix.sids, sizeof(uint32_t) * C * N, cudaMemcpyDeviceToHost));
@@ -871,6 +888,7 @@ int sfc_index_params(const sfc_index* h, sfc_params* p, sfc_grid* g) {
     p->knn = ix.knn;
     p->curve = ix.curve;
     p->cost = ix.l1 ? SFC_COST_L1 : SFC_COST_L2;
+    p->precision = ix.bf16 ? SFC_BF16 : SFC_FP32;
   }
   if (g) {
     g->ndim = ix.g.ndim;
@@ -899,7 +917,8 @@ int sfc_index_save(const sfc_index* h, const char* path) {
   o.raw(kIndexMagic, sizeof kIndexMagic);
   const int64_t head[] = {ix.g.ndim, ix.g.ch,  ix.g.K,  ix.g.X, ix.g.Y, ix.g.Z,       ix.C,         ix.D,
                           ix.bits,   ix.bp,    ix.W,    ix.select, ix.m, ix.s,        ix.N,         ix.knn,
-                          ix.curve,  ix.l1 ? 1 : 0, ix.p_block, ix.eig_per_orth, ix.pca_sample};
+                          ix.curve,  ix.l1 ? 1 : 0, ix.p_block, ix.eig_per_orth, ix.pca_sample,
+                          ix.bf16 ? SFC_BF16 : SFC_FP32};
   o.i64((int64_t)(sizeof head / sizeof head[0]));
   o.raw(head, sizeof head);
   const double frac = ix.frac;
@@ -948,13 +967,13 @@ int sfc_index_load(const char* path, void* stream, sfc_index** out) {
   char magic[8] = {};
   in.raw(magic, sizeof magic);
   const int64_t nhead = in.i64();
-  int64_t head[21] = {};
-  if (!in.ok || std::memcmp(magic, kIndexMagic, sizeof magic) != 0 || nhead != 21) {
+  int64_t head[22] = {};  // 21 entries in files written before the precision was recorded (FP32)
+  if (!in.ok || std::memcmp(magic, kIndexMagic, sizeof magic) != 0 || (nhead != 21 && nhead != 22)) {
     std::fclose(f);
     set_error("sfc_index_load: not an index file of this library version");
     return SFC_EINVAL;
   }
-  in.raw(head, sizeof head);
+  in.raw(head, sizeof(int64_t) * nhead);
   double frac = 0.0;
   in.raw(&frac, sizeof frac);
   cudaStream_t st = (cudaStream_t)stream;
@@ -983,6 +1002,7 @@ int sfc_index_load(const char* path, void* stream, sfc_index** out) {
   ix.p_block = (int)head[18];
   ix.eig_per_orth = (int)head[19];
   ix.pca_sample = head[20];
+  ix.bf16 = nhead > 21 && head[21] == SFC_BF16;
   ix.frac = (float)frac;
   ix.keep = false;
   const int64_t C = ix.C, N = ix.N, D = ix.D, s = ix.s, m = ix.m;
