@@ -122,6 +122,8 @@ struct Index {
   int eig_per_orth = 1;        // products per orthonormalisation (2 on the cluster path)
   int* pca_done = nullptr;     // C (device): 1 where the eigen-solve converged (PCA builds only)
   bool bf16 = false;           // precision tier: projections on tensor cores, stored as BF16 (proj holds BF16)
+  cudaEvent_t ev_proj[2] = {};  // traced BF16 builds: around the tensor-core projection launch
+  double proj_flops = 0.0, proj_bytes = 0.0;  // its algorithmic work (set by project_bf16)
 };
 
 // Record phase boundary k of a traced build (no-op otherwise).

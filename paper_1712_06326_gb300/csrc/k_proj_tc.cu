@@ -44,6 +44,9 @@ constexpr int kPK = 64;              // elements per K-block (128 bytes of BF16)
 constexpr int kPStages = 3;          // A ring stages
 constexpr int kPThreads = 256;
 constexpr uint32_t kPStageBytes = kPM * kPK * 2;  // 16 KB
+// element-offset table entry of a K position no index reads (offsets relative
+// to the patch centre are negative before the centre, so -1 cannot mark it)
+constexpr int kNoElem = INT32_MIN;
 
 // D = F32, A = B = BF16, both K-major, M = 128, N = nb
 __device__ inline uint32_t idesc_bf16(int nb) {
@@ -75,7 +78,7 @@ struct PtArgs {
   int64_t N;
   int ch, kblocks, nb, CD, D, C;
   int64_t tiles;
-  const int* eo;                // kblocks * 64 element offsets (-1: padding or no subset uses it)
+  const int* eo;                // kblocks * 64 element offsets (kNoElem: padding or no subset uses it)
   const float* cm;              // kblocks * 64 centring values
   const __nv_bfloat16* Bg;      // nb x (kblocks * 64), K-major
   const float* beta;            // C D
@@ -162,8 +165,8 @@ __global__ void __launch_bounds__(kPThreads) k_proj_tc(PtArgs a) {
         const int64_t b = s_base[r];
         float v0 = 0.0f, v1 = 0.0f;
         if (b >= 0) {
-          if (o0 >= 0) v0 = __fsub_rn(__ldg(a.grid + b + o0), m0);
-          if (o1 >= 0) v1 = __fsub_rn(__ldg(a.grid + b + o1), m1);
+          if (o0 != kNoElem) v0 = __fsub_rn(__ldg(a.grid + b + o0), m0);
+          if (o1 != kNoElem) v1 = __fsub_rn(__ldg(a.grid + b + o1), m1);
         }
         const __nv_bfloat162 pk = __floats2bfloat162_rn(v0, v1);  // v0 at the lower address
         *reinterpret_cast<__nv_bfloat162*>(stage + sw128_off(r, 2 * lane)) = pk;
@@ -289,9 +292,9 @@ int project_bf16(Index& ix, const float* grid, void* proj, uint32_t* lohi, cudaS
     return SFC_EUNSUPPORTED;
   }
   // host tables: the patch element of every subset value, the first (index,
-  // value) using each element, and the element offsets the gather reads (-1:
-  // padding, or an element no subset uses)
-  std::vector<int> elem((size_t)C * s), first(Kp, -1), eo(Kp, -1);
+  // value) using each element, and the element offsets the gather reads
+  // (kNoElem: padding, or an element no subset uses)
+  std::vector<int> elem((size_t)C * s), first(Kp, -1), eo(Kp, kNoElem);
   for (int c = 0; c < C; ++c)
     for (int i = 0; i < s; ++i) {
       const int e = ix.subset_h[(size_t)c * m + i / ch] * ch + i % ch;
@@ -354,11 +357,17 @@ int project_bf16(Index& ix, const float* grid, void* proj, uint32_t* lohi, cudaS
   while (cols < (uint32_t)nb) cols <<= 1;
   a.tmem_cols = cols;
   const int64_t grid_n = std::min<int64_t>(a.tiles, (int64_t)sms * per_sm);
+  // the method's work: N C s D multiply-adds; its bytes: the patch values
+  // gathered (N n FP32) and the BF16 projections written
+  ix.proj_flops = 2.0 * (double)ix.N * C * s * D;
+  ix.proj_bytes = (double)ix.N * n * 4.0 + (double)ix.N * CD * 2.0;
+  if (ix.ev_proj[0]) cudaEventRecord(ix.ev_proj[0], st);
   if (grid_n > 0) {
     count_launch();
     k_proj_tc<<<(unsigned)grid_n, kPThreads, shm, st>>>(a);
     SFC_TRY(cudaGetLastError());
   }
+  if (ix.ev_proj[1]) cudaEventRecord(ix.ev_proj[1], st);
   return lohi_to_scale(ix, lohi, st);
 }
 

@@ -42,6 +42,8 @@ struct TraceAcc {
   double tc_ms[SFC_TRACE_TC_PHASES] = {};
   int64_t tc_calls = 0;
   double tc_flops = 0.0;
+  double proj_ms = 0.0, proj_flops = 0.0, proj_bytes = 0.0;  // BF16 tensor-core projections
+  int64_t proj_calls = 0;
 } g_trace;
 std::mutex g_trace_mu;
 // events of the tensor-core full scan in flight on this host thread
@@ -110,7 +112,23 @@ static void trace_fold(Index& ix) {
       g_trace.eig_flops32 += i32 * 2.0 * s * s * p;
     }
   }
+  if (ix.ev_proj[0] && ix.ev_proj[1]) {
+    float pm = 0.0f;
+    if (cudaEventElapsedTime(&pm, ix.ev_proj[0], ix.ev_proj[1]) == cudaSuccess) {
+      std::lock_guard<std::mutex> lk(g_trace_mu);
+      g_trace.proj_ms += pm;
+      g_trace.proj_calls += 1;
+      g_trace.proj_flops += ix.proj_flops;
+      g_trace.proj_bytes += ix.proj_bytes;
+    }
+    cudaGetLastError();
+  }
   for (auto& e : ix.ev)
+    if (e) {
+      cudaEventDestroy(e);
+      e = nullptr;
+    }
+  for (auto& e : ix.ev_proj)
     if (e) {
       cudaEventDestroy(e);
       e = nullptr;
@@ -619,6 +637,8 @@ int build_index(const float* grid, const uint8_t* dict_mask, const sfc_grid* gp,
   }
   if (ix.traced) {
     for (auto& e : ix.ev) SFC_TRY(cudaEventCreate(&e));
+    if (p->precision == SFC_BF16)
+      for (auto& e : ix.ev_proj) SFC_TRY(cudaEventCreate(&e));
     trace_mark(ix, 0, st);
   }
   SFC_TRY(pmalloc(&ix.eig_iters, sizeof(int) * 2 * ix.C, st));
@@ -728,6 +748,15 @@ int sfc_trace_eig_read(double* fp64_flops, double* fp32_flops) {
   std::lock_guard<std::mutex> lk(g_trace_mu);
   if (fp64_flops) *fp64_flops = g_trace.eig_flops;
   if (fp32_flops) *fp32_flops = g_trace.eig_flops32;
+  return SFC_OK;
+}
+
+int sfc_trace_proj_read(double* ms, int64_t* calls, double* flops, double* bytes) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  if (ms) *ms = g_trace.proj_ms;
+  if (calls) *calls = g_trace.proj_calls;
+  if (flops) *flops = g_trace.proj_flops;
+  if (bytes) *bytes = g_trace.proj_bytes;
   return SFC_OK;
 }
 

@@ -32,7 +32,8 @@ EXPORTS = ["sfc_params_default", "sfc_index_build", "sfc_index_destroy", "sfc_in
            "sfc_last_error", "sfc_index_save", "sfc_index_load", "sfc_index_params", "sfc_query_batch_dict",
            "sfc_multi_create", "sfc_multi_query", "sfc_multi_destroy", "sfc_autotune", "sfc_tune_select", "sfc_trace_eig_read",
            "sfc_debug_fail_alloc", "sfc_debug_alloc_count", "sfc_debug_pool_used", "sfc_debug_lookback",
-           "sfc_shard_create", "sfc_shard_range", "sfc_shard_scan", "sfc_shard_band", "sfc_shard_destroy"]
+           "sfc_shard_create", "sfc_shard_range", "sfc_shard_scan", "sfc_shard_band", "sfc_shard_destroy",
+           "sfc_trace_proj_read"]
 TRACE_PHASES = ("dictionary", "moments", "eigen", "finalize", "project_keys", "sort")
 
 
@@ -104,6 +105,8 @@ def lib():
         L.sfc_trace_eig_read.restype = C.c_int
         L.sfc_trace_tc_read.argtypes = [vp, vp, vp]
         L.sfc_trace_tc_read.restype = C.c_int
+        L.sfc_trace_proj_read.argtypes = [vp, vp, vp, vp]
+        L.sfc_trace_proj_read.restype = C.c_int
         L.sfc_debug_fail_alloc.argtypes = [i64]
         L.sfc_debug_fail_alloc.restype = C.c_int
         L.sfc_debug_alloc_count.argtypes = []
@@ -490,6 +493,14 @@ def sfc_trace_tc_read() -> dict:
 
 def sfc_status() -> int:
     return lib().sfc_status(_stream())
+
+
+def sfc_trace_proj_read() -> dict:
+    """Summed time, launches and algorithmic work of the traced BF16 projections."""
+    ms, fl, by = C.c_double(), C.c_double(), C.c_double()
+    calls = C.c_int64()
+    _check(lib().sfc_trace_proj_read(C.byref(ms), C.byref(calls), C.byref(fl), C.byref(by)), "sfc_trace_proj_read")
+    return {"ms": ms.value, "calls": calls.value, "flops": fl.value, "bytes": by.value}
 
 
 def sfc_debug_fail_alloc(n: int) -> None:
