@@ -491,11 +491,60 @@ def pca_sample_comparison(sfc, torch, gd, md, td, prm, flush, stream, ex_h, fp, 
             "acceleration_error_mean": float((torch.sqrt(ca[sel].double()) / fcd - 1.0).mean().item())}
 
 
+def run_bf16_tier(sfc, torch, gd, md, td, prm, flush, stream, fp, fc, sel, pick32, cost32, peaks, Q):
+    """The headline step with the index's projections as one tcgen05 BF16 GEMM
+    (stored in BF16): step time, the projection launch's time and rates, and
+    the quality against the exact full-scan picks beside the FP32 index's."""
+    bprm = dict(prm, precision=sfc.SFC_BF16)
+    ms = []
+    sfc.sfc_trace(True)
+    for r in range(4):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ix = sfc.sfc_index_build(gd, md, **bprm)
+        pb, cb = sfc.sfc_query_batch(ix, gd, md, td)
+        b.record(stream)
+        b.synchronize()
+        if r == 0:
+            ix.close()
+            sfc.sfc_trace(True)  # drop the first (untimed) build's phases
+            continue
+        ms.append(a.elapsed_time(b))
+        ix.close()
+    pt = sfc.sfc_trace_proj_read()
+    tr = sfc.sfc_trace_read()
+    sfc.sfc_trace(False)
+    assert sfc.sfc_status() == 0
+    calls = max(pt["calls"], 1)
+    pms = pt["ms"] / calls
+    flops, byts = pt["flops"] / calls, pt["bytes"] / calls
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    fcd = torch.sqrt(fc.double()).clamp_min(1e-30)
+    return {"workload": "the headline step with precision SFC_BF16 (projections: one tcgen05 BF16 GEMM over every "
+                        "curve, stored in BF16; query projections FP32; every pick rescored exactly)",
+            "qps": Q / (statistics.mean(ms) / 1000.0), "ms_per_step": statistics.mean(ms),
+            "phases_ms": {k: v / max(tr["builds"], 1) for k, v in tr["ms"].items()},
+            "projection_kernel": {"kernel": "k_proj_tc", "launch_ms": pms, "method_flops": flops,
+                                  "tensor_tflops": flops / (pms / 1000.0) / 1e12 if pms > 0 else 0.0,
+                                  "tensor_frac_of_measured_bf16": (flops / (pms / 1000.0) / 1e12) / bf16_peak
+                                  if pms > 0 else 0.0,
+                                  "gathered_and_written_bytes": byts,
+                                  "gather_GBps": byts / (pms / 1000.0) / 1e9 if pms > 0 else 0.0,
+                                  "note": "bound by the patch gather from the L2-resident grid, not the tensor pipe"},
+            "pick_agreement_fullscan": float((pb[sel] == fp).double().mean().item()),
+            "acceleration_error_mean": float((torch.sqrt(cb[sel].double()) / fcd - 1.0).mean().item()),
+            "fp32_index_pick_agreement_fullscan": float((pick32[sel] == fp).double().mean().item()),
+            "fp32_index_acceleration_error_mean": float((torch.sqrt(cost32[sel].double()) / fcd - 1.0).mean().item()),
+            "picks_equal_fp32_index": float((pb == pick32).double().mean().item())}
+
+
 VOLUMES = {
     "spheres3d_256": dict(size=256, cfg=3, block=8, missing=0.15, salt=0.0, K=7, curves=8, dims=12, bits=21,
                           window=128, pca_sample=16384, cap=131072),
     "spheres3d_512": dict(size=512, cfg=5, block=16, missing=0.20, salt=0.05, K=9, curves=8, dims=8, bits=8,
-                          window=256, pca_sample=65536, cap=131072),
+                          window=256, pca_sample=65536, cap=131072, precisions=("bf16", "fp32")),
 }
 
 
@@ -526,31 +575,38 @@ def run_volumes(sfc, torch, dev, flush, stream):
         md = torch.from_numpy(np.ascontiguousarray(m)).to(dev)
         td = torch.from_numpy(np.ascontiguousarray(t)).to(dev)
         del g
-        st_ms, q_ms = [], []
-        for r in range(3):  # the first step is untimed
-            flush.fill_(1.0)
-            a = torch.cuda.Event(enable_timing=True)
-            mid = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            ix = sfc.sfc_index_build(gd, md, **prm)
-            mid.record(stream)
-            sfc.sfc_query_batch(ix, gd, md, td)
-            b.record(stream)
-            b.synchronize()
-            if r > 0:
-                st_ms.append(a.elapsed_time(b))
-                q_ms.append(mid.elapsed_time(b))
-            N = ix.N
-            ix.close()
         Q = len(t)
-        out[name] = {"workload": f"{v['size']}^3 spheres, {int(v['missing'] * 100)}% missing {v['block']}^3 blocks"
-                                 + (f", {int(v['salt'] * 100)}% salt-and-pepper" if v["salt"] else "")
-                                 + f", K={v['K']} (d={v['K'] ** 3}), SFC C={v['curves']} D={v['dims']} "
-                                 f"b={v['bits']} W={v['window']}, FP32 projections",
-                     "dictionary": int(N), "queries": Q, "qps": Q / (statistics.mean(st_ms) / 1000.0),
-                     "ms_per_step": statistics.mean(st_ms), "query_ms": statistics.mean(q_ms),
-                     "query_only_qps": Q / (statistics.mean(q_ms) / 1000.0), "status": sfc.sfc_status()}
+        res = {}
+        for prec in v.get("precisions", ("fp32",)):
+            pp = dict(prm, precision=sfc.SFC_BF16 if prec == "bf16" else sfc.SFC_FP32)
+            st_ms, q_ms = [], []
+            for r in range(3):  # the first step is untimed
+                flush.fill_(1.0)
+                a = torch.cuda.Event(enable_timing=True)
+                mid = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ix = sfc.sfc_index_build(gd, md, **pp)
+                mid.record(stream)
+                sfc.sfc_query_batch(ix, gd, md, td)
+                b.record(stream)
+                b.synchronize()
+                if r > 0:
+                    st_ms.append(a.elapsed_time(b))
+                    q_ms.append(mid.elapsed_time(b))
+                N = ix.N
+                ix.close()
+            res[prec] = {"workload": f"{v['size']}^3 spheres, {int(v['missing'] * 100)}% missing {v['block']}^3 "
+                                     "blocks" + (f", {int(v['salt'] * 100)}% salt-and-pepper" if v["salt"] else "")
+                                     + f", K={v['K']} (d={v['K'] ** 3}), SFC C={v['curves']} D={v['dims']} "
+                                     f"b={v['bits']} W={v['window']}, {prec.upper()} projections",
+                         "dictionary": int(N), "queries": Q, "qps": Q / (statistics.mean(st_ms) / 1000.0),
+                         "ms_per_step": statistics.mean(st_ms), "query_ms": statistics.mean(q_ms),
+                         "query_only_qps": Q / (statistics.mean(q_ms) / 1000.0), "status": sfc.sfc_status()}
+        out[name] = res[v.get("precisions", ("fp32",))[0]]
+        for prec, r_ in res.items():
+            if prec != v.get("precisions", ("fp32",))[0]:
+                out[name][prec + "_projections"] = r_
         del gd, md, td
         torch.cuda.empty_cache()
     return out
@@ -786,6 +842,9 @@ def main():
                                "picks_and_costs_equal_fp32": same,
                                "phases_ms": {k: v / calls for k, v in tct["ms"].items()}, "roofline": tc_roof}
 
+    # ---- the BF16 precision tier: dictionary projections on tensor cores -----
+    bf16 = run_bf16_tier(sfc, torch, gd, md, td, prm, flush, stream, fp, fc, sel, pick, cost, peaks, Q)
+
     # ---- the paper's exact k-NN lists (Sec. II.D, k = 80) instead of windows ---
     knn_prm = dict(prm, knn=80)
     kn_ms, kq_ms = [], []
@@ -996,7 +1055,7 @@ def main():
             "query_only": {"qps": query_only_qps, "ms": q_ms_mean},
             "index_build_ms": tot_ms / args.steps - q_ms_mean, "phases_ms": phases_ms,
             "fullscan": fullscan, "sfc_knn": sfc_knn, "sfc_hilbert": sfc_hilbert, "sfc_l1": sfc_l1,
-            "stored_index": stored, "inpaint_128x128": inp,
+            "stored_index": stored, "inpaint_128x128": inp, "bf16_index": bf16,
             "batch_256": batch}
     line.update({"pca_sample_all": pca_all, "inpaint_1024": fill_big, "volumes": volumes})
     if split is not None:

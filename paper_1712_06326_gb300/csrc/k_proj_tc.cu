@@ -86,15 +86,20 @@ struct PtArgs {
   uint32_t* lohi;               // 2 C D ordered words
   uint32_t* status;
   uint32_t tmem_cols;           // power of two >= nb
+  int b_streamed;               // 1: B does not fit shared memory whole; each stage carries its K-block of B
 };
 
 __global__ void __launch_bounds__(kPThreads) k_proj_tc(PtArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int Kp = a.kblocks * kPK;
-  unsigned char* sB = base;                                      // kblocks x (nb rows x 128 B)
-  unsigned char* sA = sB + (size_t)a.kblocks * a.nb * 128;       // kPStages x 16 KB
-  int* s_eo = reinterpret_cast<int*>(sA + kPStages * kPStageBytes);  // Kp
+  // resident B: kblocks x (nb rows x 128 B), then the stages (A: 16 KB each);
+  // streamed B: no resident copy, each stage holds A (16 KB) then its B block
+  const uint32_t bblk = (uint32_t)a.nb * 128u;
+  const uint32_t stage_bytes = kPStageBytes + (a.b_streamed ? bblk : 0u);
+  unsigned char* sB = base;
+  unsigned char* sA = sB + (a.b_streamed ? 0 : (size_t)a.kblocks * bblk);
+  int* s_eo = reinterpret_cast<int*>(sA + (size_t)kPStages * stage_bytes);  // Kp
   float* s_cm = reinterpret_cast<float*>(s_eo + Kp);                 // Kp
   float* s_beta = s_cm + Kp;                                         // CD
   uint32_t* s_min = reinterpret_cast<uint32_t*>(s_beta + a.CD);      // CD
@@ -105,7 +110,7 @@ __global__ void __launch_bounds__(kPThreads) k_proj_tc(PtArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   // B operand (swizzled like the A blocks), element tables, ranges
-  for (int t = threadIdx.x; t < a.kblocks * a.nb * 8; t += kPThreads) {
+  for (int t = threadIdx.x; t < (a.b_streamed ? 0 : a.kblocks * a.nb * 8); t += kPThreads) {
     const int kb = t / (a.nb * 8), rem = t % (a.nb * 8), row = rem / 8, chunk = rem % 8;
     const uint4 v = *reinterpret_cast<const uint4*>(a.Bg + (size_t)row * Kp + kb * kPK + chunk * 8);
     *reinterpret_cast<uint4*>(sB + (size_t)kb * a.nb * 128 + sw128_off(row, chunk * 8)) = v;
@@ -155,7 +160,14 @@ __global__ void __launch_bounds__(kPThreads) k_proj_tc(PtArgs a) {
         break;
       }
       // gather: warp -> rows warp, warp + 8, ...; lane -> elements 2 lane, 2 lane + 1
-      unsigned char* stage = sA + (size_t)s * kPStageBytes;
+      unsigned char* stage = sA + (size_t)s * stage_bytes;
+      unsigned char* bstage = a.b_streamed ? stage + kPStageBytes : sB + (size_t)kb * bblk;
+      if (a.b_streamed)
+        for (int t2 = threadIdx.x; t2 < a.nb * 8; t2 += kPThreads) {
+          const int row = t2 / 8, chunk = t2 % 8;
+          const uint4 v = *reinterpret_cast<const uint4*>(a.Bg + (size_t)row * Kp + kb * kPK + chunk * 8);
+          *reinterpret_cast<uint4*>(bstage + sw128_off(row, chunk * 8)) = v;
+        }
       const int e0 = kb * kPK + 2 * lane;
       const int o0 = s_eo[e0], o1 = s_eo[e0 + 1];
       const float m0 = s_cm[e0], m1 = s_cm[e0 + 1];
@@ -175,7 +187,7 @@ __global__ void __launch_bounds__(kPThreads) k_proj_tc(PtArgs a) {
       __syncthreads();
       if (threadIdx.x == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t a0 = smem_u32(stage), b0 = smem_u32(sB + (size_t)kb * a.nb * 128);
+        const uint32_t a0 = smem_u32(stage), b0 = smem_u32(bstage);
 #pragma unroll
         for (int kk = 0; kk < kPK / 16; ++kk)
           mma_bf16(tmem, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), idesc,
@@ -322,8 +334,13 @@ int project_bf16(Index& ix, const float* grid, void* proj, uint32_t* lohi, cudaS
   SFC_TRY(cudaGetLastError());
   SFC_CHECK(lohi_init(lohi, CD, st));
   // launch: one or two CTAs per SM (by shared memory), persistent over tiles
-  const size_t shm = 1024 + (size_t)kblocks * nb * 128 + (size_t)kPStages * kPStageBytes + (size_t)Kp * 8 +
-                     (size_t)CD * 12 + 8 + kPM * 8;
+  const size_t tables = (size_t)Kp * 8 + (size_t)CD * 12 + 8 + kPM * 8;
+  size_t shm = 1024 + (size_t)kblocks * nb * 128 + (size_t)kPStages * kPStageBytes + tables;
+  int streamed = 0;
+  if (shm > 227 * 1024) {  // B streamed through the stages with A
+    streamed = 1;
+    shm = 1024 + (size_t)kPStages * (kPStageBytes + (size_t)nb * 128) + tables;
+  }
   if (shm > 227 * 1024) {
     set_error("the BF16 projection's operands do not fit shared memory (patch too large)");
     return SFC_EUNSUPPORTED;
@@ -356,6 +373,7 @@ int project_bf16(Index& ix, const float* grid, void* proj, uint32_t* lohi, cudaS
   uint32_t cols = 32;
   while (cols < (uint32_t)nb) cols <<= 1;
   a.tmem_cols = cols;
+  a.b_streamed = streamed;
   const int64_t grid_n = std::min<int64_t>(a.tiles, (int64_t)sms * per_sm);
   // the method's work: N C s D multiply-adds; its bytes: the patch values
   // gathered (N n FP32) and the BF16 projections written
