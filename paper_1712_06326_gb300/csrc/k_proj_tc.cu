@@ -171,17 +171,22 @@ __global__ void __launch_bounds__(kPThreads) k_proj_tc(PtArgs a) {
       const int e0 = kb * kPK + 2 * lane;
       const int o0 = s_eo[e0], o1 = s_eo[e0 + 1];
       const float m0 = s_cm[e0], m1 = s_cm[e0 + 1];
-#pragma unroll 4
+      const bool u0 = o0 != kNoElem, u1 = o1 != kNoElem;
+      // rows warp + 8 i share r & 7, hence the swizzled chunk: one offset per thread
+      unsigned char* dst0 = stage + sw128_off(warp, 2 * lane);
+      float v0[kPM / 8], v1[kPM / 8];
+#pragma unroll
+      for (int i = 0; i < kPM / 8; ++i) {  // every load of the block in flight at once
+        const int64_t b = s_base[warp + 8 * i];
+        v0[i] = (b >= 0 && u0) ? __ldg(a.grid + b + o0) : 0.0f;
+        v1[i] = (b >= 0 && u1) ? __ldg(a.grid + b + o1) : 0.0f;
+      }
+#pragma unroll
       for (int i = 0; i < kPM / 8; ++i) {
-        const int r = warp + 8 * i;
-        const int64_t b = s_base[r];
-        float v0 = 0.0f, v1 = 0.0f;
-        if (b >= 0) {
-          if (o0 != kNoElem) v0 = __fsub_rn(__ldg(a.grid + b + o0), m0);
-          if (o1 != kNoElem) v1 = __fsub_rn(__ldg(a.grid + b + o1), m1);
-        }
-        const __nv_bfloat162 pk = __floats2bfloat162_rn(v0, v1);  // v0 at the lower address
-        *reinterpret_cast<__nv_bfloat162*>(stage + sw128_off(r, 2 * lane)) = pk;
+        const int64_t b = s_base[warp + 8 * i];
+        const float x0 = (b >= 0 && u0) ? __fsub_rn(v0[i], m0) : 0.0f;
+        const float x1 = (b >= 0 && u1) ? __fsub_rn(v1[i], m1) : 0.0f;
+        *reinterpret_cast<__nv_bfloat162*>(dst0 + i * 1024) = __floats2bfloat162_rn(x0, x1);  // x0 at the lower address
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
@@ -204,43 +209,79 @@ __global__ void __launch_bounds__(kPThreads) k_proj_tc(PtArgs a) {
       break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
-    // 2 x [128 rows][33] floats in the free A ring (the odd row stride keeps
-    // the row-per-lane writes and the column reads free of bank conflicts)
+    // The columns are taken in groups of whole curves (cpg curves, at most 64
+    // columns): warp w reads TMEM lanes 32 (w % 4) .. and 32 of the group's
+    // columns into [128 rows][65] floats in the free A ring (the odd row
+    // stride keeps row-per-lane writes and column reads free of bank
+    // conflicts); then thread (curve slot, row) writes that curve's D values
+    // of the row as BF16 and the warps reduce the per-axis minima / maxima of
+    // their 32 rows.
     float* stg = reinterpret_cast<float*>(sA);
-    constexpr int kRS = 33;
+    constexpr int kRS = 65;
     const int quarter = warp & 3, half = warp >> 2;
     const int64_t row0 = t * kPM;
     const int nrow = (int)(a.N - row0 < kPM ? a.N - row0 : kPM);
-    for (int c0 = 0; c0 < a.nb; c0 += 64) {
-      {
+    const int cpg = 64 / a.D;  // curves per group (D <= 16: at least 4)
+    for (int cur0 = 0; cur0 < a.C; cur0 += cpg) {
+      const int col0 = cur0 * a.D;
+      const int ncur = min(cpg, a.C - cur0);
+      if ((uint32_t)(col0 + 32 * half) < a.tmem_cols) {  // warp-uniform
         uint32_t v[32];
-        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(c0 + 32 * half), v);
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(col0 + 32 * half), v);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        float* dst = stg + (size_t)half * kPM * kRS + (size_t)(quarter * 32 + lane) * kRS;
+        float* dst = stg + (size_t)(quarter * 32 + lane) * kRS + 32 * half;
 #pragma unroll
         for (int i = 0; i < 32; ++i) dst[i] = __uint_as_float(v[i]);
       }
       __syncthreads();
-      // y = bf16(acc + beta): the columns' ranges, then the stores
-      const int ncol = min(64, a.CD - c0);
-      if (threadIdx.x < ncol) {
-        const int cc = threadIdx.x, col = c0 + cc;
-        const float* src = stg + (size_t)(cc >> 5) * kPM * kRS + (cc & 31);
-        uint32_t lo = s_min[col], hi = s_max[col];
-        for (int r = 0; r < nrow; ++r) {
-          const float y = __bfloat162float(__float2bfloat16_rn(__fadd_rn(src[(size_t)r * kRS], s_beta[col])));
-          const uint32_t u = ord_of_f(y);
-          lo = min(lo, u);
-          hi = max(hi, u);
+      for (int pidx = threadIdx.x; pidx < ncur * kPM; pidx += kPThreads) {
+        const int slot = pidx / kPM, r = pidx % kPM;  // kPM = 128: shifts
+        const int curve = cur0 + slot, cb = curve * a.D;
+        const float* src = stg + (size_t)r * kRS + slot * a.D;
+        const bool valid = r < nrow;
+        __nv_bfloat16 yb[16];
+        float yf[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+          if (k < a.D) {
+            yb[k] = __float2bfloat16_rn(__fadd_rn(src[k], s_beta[cb + k]));
+            yf[k] = __bfloat162float(yb[k]);
+          }
+        if (valid) {
+          __nv_bfloat16* out = a.proj + ((int64_t)curve * a.N + row0 + r) * a.D;
+          if ((a.D & 7) == 0) {
+#pragma unroll
+            for (int k = 0; k < 16; k += 8)
+              if (k < a.D) {
+                uint4 u;
+                u.x = (uint32_t)__bfloat16_as_ushort(yb[k]) | ((uint32_t)__bfloat16_as_ushort(yb[k + 1]) << 16);
+                u.y = (uint32_t)__bfloat16_as_ushort(yb[k + 2]) | ((uint32_t)__bfloat16_as_ushort(yb[k + 3]) << 16);
+                u.z = (uint32_t)__bfloat16_as_ushort(yb[k + 4]) | ((uint32_t)__bfloat16_as_ushort(yb[k + 5]) << 16);
+                u.w = (uint32_t)__bfloat16_as_ushort(yb[k + 6]) | ((uint32_t)__bfloat16_as_ushort(yb[k + 7]) << 16);
+                *reinterpret_cast<uint4*>(out + k) = u;
+              }
+          } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+              if (k < a.D) out[k] = yb[k];
+          }
         }
-        s_min[col] = lo;
-        s_max[col] = hi;
-      }
-      for (int u = threadIdx.x; u < ncol * nrow; u += kPThreads) {
-        const int cc = u % ncol, r = u / ncol, col = c0 + cc;
-        const float acc = stg[(size_t)(cc >> 5) * kPM * kRS + (size_t)r * kRS + (cc & 31)];
-        const int curve = col / a.D, k = col - curve * a.D;
-        a.proj[((int64_t)curve * a.N + row0 + r) * a.D + k] = __float2bfloat16_rn(__fadd_rn(acc, s_beta[col]));
+        // per-axis range of the warp's 32 rows (a warp holds one curve slot:
+        // 128 rows per slot, 32 rows per warp)
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+          if (k < a.D) {
+            uint32_t lo = valid ? ord_of_f(yf[k]) : 0xffffffffu, hi = valid ? ord_of_f(yf[k]) : 0u;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+              hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            }
+            if (lane == 0) {
+              atomicMin(&s_min[cb + k], lo);
+              atomicMax(&s_max[cb + k], hi);
+            }
+          }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncthreads();
@@ -346,6 +387,7 @@ int project_bf16(Index& ix, const float* grid, void* proj, uint32_t* lohi, cudaS
     return SFC_EUNSUPPORTED;
   }
   SFC_TRY(cudaFuncSetAttribute(k_proj_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  SFC_TRY(cudaFuncSetAttribute(k_proj_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   int dev = 0, sms = 0, per_sm = 0;
   SFC_TRY(cudaGetDevice(&dev));
   SFC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -370,9 +412,18 @@ int project_bf16(Index& ix, const float* grid, void* proj, uint32_t* lohi, cudaS
   a.proj = static_cast<__nv_bfloat16*>(proj);
   a.lohi = lohi;
   a.status = status_word();
+  // TMEM columns: the accumulator (nb) and every 64-column read of the
+  // epilogue's curve groups (a group starts at a multiple of D)
+  int need = nb;
+  for (int c0 = 0, cpg = 64 / D; c0 < C; c0 += cpg) need = std::max(need, c0 * D + 64);
   uint32_t cols = 32;
-  while (cols < (uint32_t)nb) cols <<= 1;
+  while (cols < (uint32_t)need) cols <<= 1;
+  if (cols > 512) {
+    set_error("the BF16 projection needs more than 512 TMEM columns (curves * dims too large)");
+    return SFC_EUNSUPPORTED;
+  }
   a.tmem_cols = cols;
+  per_sm = std::min(per_sm, (int)(512 / cols));  // every CTA on an SM holds its columns at once
   a.b_streamed = streamed;
   const int64_t grid_n = std::min<int64_t>(a.tiles, (int64_t)sms * per_sm);
   // the method's work: N C s D multiply-adds; its bytes: the patch values
