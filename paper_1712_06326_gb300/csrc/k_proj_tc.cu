@@ -100,20 +100,22 @@ __global__ void __launch_bounds__(kPThreads) k_proj_tc(PtArgs a) {
   unsigned char* sB = base;
   unsigned char* sA = sB + (a.b_streamed ? 0 : (size_t)a.kblocks * bblk);
   int* s_eo = reinterpret_cast<int*>(sA + (size_t)kPStages * stage_bytes);  // Kp
-  float* s_cm = reinterpret_cast<float*>(s_eo + Kp);                 // Kp
-  float* s_beta = s_cm + Kp;                                         // CD
-  uint32_t* s_min = reinterpret_cast<uint32_t*>(s_beta + a.CD);      // CD
-  uint32_t* s_max = s_min + a.CD;                                    // CD
-  int64_t* s_base = reinterpret_cast<int64_t*>(((uintptr_t)(s_max + a.CD) + 7) & ~(uintptr_t)7);  // kPM
-  __shared__ uint64_t empty_bar[kPStages], acc_full, final_bar;
+  float* s_cm = reinterpret_cast<float*>(s_eo + Kp);                        // Kp
+  float* s_beta = s_cm + Kp;                                                // CD
+  uint32_t* s_min = reinterpret_cast<uint32_t*>(s_beta + a.CD);             // CD
+  uint32_t* s_max = s_min + a.CD;                                           // CD
+  int* s_cur = reinterpret_cast<int*>(s_max + a.CD);                        // CD: curve of a column
+  int* s_k = s_cur + a.CD;                                                  // CD: axis of a column
+  int64_t* s_base = reinterpret_cast<int64_t*>(((uintptr_t)(s_k + a.CD) + 7) & ~(uintptr_t)7);  // kPM
+  __shared__ uint64_t empty_bar[kPStages], acc_full[2], final_bar;
   __shared__ uint32_t tmem_base;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  // B operand (swizzled like the A blocks), element tables, ranges
+  // B operand (swizzled like the A blocks), element tables, column tables, ranges
   for (int t = threadIdx.x; t < (a.b_streamed ? 0 : a.kblocks * a.nb * 8); t += kPThreads) {
     const int kb = t / (a.nb * 8), rem = t % (a.nb * 8), row = rem / 8, chunk = rem % 8;
     const uint4 v = *reinterpret_cast<const uint4*>(a.Bg + (size_t)row * Kp + kb * kPK + chunk * 8);
-    *reinterpret_cast<uint4*>(sB + (size_t)kb * a.nb * 128 + sw128_off(row, chunk * 8)) = v;
+    *reinterpret_cast<uint4*>(sB + (size_t)kb * bblk + sw128_off(row, chunk * 8)) = v;
   }
   for (int t = threadIdx.x; t < Kp; t += kPThreads) {
     s_eo[t] = a.eo[t];
@@ -123,10 +125,13 @@ __global__ void __launch_bounds__(kPThreads) k_proj_tc(PtArgs a) {
     s_beta[t] = a.beta[t];
     s_min[t] = 0xffffffffu;
     s_max[t] = 0u;
+    s_cur[t] = t / a.D;
+    s_k[t] = t % a.D;
   }
   if (threadIdx.x == 0) {
     for (int s = 0; s < kPStages; ++s) mbar_init(&empty_bar[s], 1);
-    mbar_init(&acc_full, 1);
+    mbar_init(&acc_full[0], 1);
+    mbar_init(&acc_full[1], 1);
     mbar_init(&final_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -142,150 +147,175 @@ __global__ void __launch_bounds__(kPThreads) k_proj_tc(PtArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = idesc_bf16(a.nb);
+  const int nchunks = (a.CD + 31) / 32;
+  const bool vec = 32 % a.D == 0;  // every 32-column chunk holds whole curves
   bool ok = true;
   long long it = 0;  // A ring position over all tiles
-  int local = 0;     // tiles of this CTA (phase of acc_full)
-  for (int64_t t = blockIdx.x; t < a.tiles && ok; t += gridDim.x, ++local) {
-    for (int r = threadIdx.x; r < kPM; r += kPThreads) {
-      const int64_t j = t * kPM + r;
-      s_base[r] = j < a.N ? (int64_t)a.dict[j] * a.ch : -1;
+  // Software pipeline over this CTA's tiles: iteration L gathers tile L into
+  // accumulator buffer L & 1 and issues its MMAs, then drains tile L - 1 (whose
+  // MMAs ran during the gather) -- so the MMA latency hides behind the gather.
+  for (int L = 0;; ++L) {
+    const int64_t t = blockIdx.x + (int64_t)L * gridDim.x;
+    const bool have = ok && t < a.tiles;
+    if (have) {
+      const uint32_t tacc = tmem + (uint32_t)((L & 1) * a.nb);
+      for (int r = threadIdx.x; r < kPM; r += kPThreads) {
+        const int64_t j = t * kPM + r;
+        s_base[r] = j < a.N ? (int64_t)a.dict[j] * a.ch : -1;
+      }
+      __syncthreads();
+      for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
+        const int s = (int)(it % kPStages);
+        bool w = true;
+        if (it >= kPStages) w = mbar_wait(&empty_bar[s], (uint32_t)((it / kPStages) - 1) & 1u);
+        if (!__syncthreads_and(w)) {
+          ok = false;
+          break;
+        }
+        unsigned char* stage = sA + (size_t)s * stage_bytes;
+        unsigned char* bstage = a.b_streamed ? stage + kPStageBytes : sB + (size_t)kb * bblk;
+        if (a.b_streamed)
+          for (int t2 = threadIdx.x; t2 < a.nb * 8; t2 += kPThreads) {
+            const int row = t2 / 8, chunk = t2 % 8;
+            const uint4 v = *reinterpret_cast<const uint4*>(a.Bg + (size_t)row * Kp + kb * kPK + chunk * 8);
+            *reinterpret_cast<uint4*>(bstage + sw128_off(row, chunk * 8)) = v;
+          }
+        // gather: warp -> rows warp, warp + 8, ...; lane -> elements 2 lane, 2 lane + 1
+        const int e0 = kb * kPK + 2 * lane;
+        const int o0 = s_eo[e0], o1 = s_eo[e0 + 1];
+        const float m0 = s_cm[e0], m1 = s_cm[e0 + 1];
+        const bool u0 = o0 != kNoElem, u1 = o1 != kNoElem;
+        // rows warp + 8 i share r & 7, hence the swizzled chunk: one offset per thread
+        unsigned char* dst0 = stage + sw128_off(warp, 2 * lane);
+        float v0[kPM / 8], v1[kPM / 8];
+#pragma unroll
+        for (int i = 0; i < kPM / 8; ++i) {  // every load of the block in flight at once
+          const int64_t b = s_base[warp + 8 * i];
+          v0[i] = (b >= 0 && u0) ? __ldg(a.grid + b + o0) : 0.0f;
+          v1[i] = (b >= 0 && u1) ? __ldg(a.grid + b + o1) : 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < kPM / 8; ++i) {
+          const int64_t b = s_base[warp + 8 * i];
+          const float x0 = (b >= 0 && u0) ? __fsub_rn(v0[i], m0) : 0.0f;
+          const float x1 = (b >= 0 && u1) ? __fsub_rn(v1[i], m1) : 0.0f;
+          *reinterpret_cast<__nv_bfloat162*>(dst0 + i * 1024) = __floats2bfloat162_rn(x0, x1);  // x0 first
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t a0 = smem_u32(stage), b0 = smem_u32(bstage);
+#pragma unroll
+          for (int kk = 0; kk < kPK / 16; ++kk)
+            mma_bf16(tacc, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), idesc,
+                     (kb > 0 || kk > 0) ? 1u : 0u);
+          tc_commit(&empty_bar[s]);
+          if (kb == a.kblocks - 1) tc_commit(&acc_full[L & 1]);
+        }
+      }
     }
-    __syncthreads();
-    for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
-      const int s = (int)(it % kPStages);
-      bool w = true;
-      if (it >= kPStages) w = mbar_wait(&empty_bar[s], (uint32_t)((it / kPStages) - 1) & 1u);
+    // drain the previous tile: TMEM -> BF16 projections, per-axis ranges
+    const int P = L - 1;
+    const int64_t tp = blockIdx.x + (int64_t)P * gridDim.x;
+    if (ok && P >= 0 && tp < a.tiles) {
+      const bool w = mbar_wait(&acc_full[P & 1], (uint32_t)(P >> 1) & 1u);
       if (!__syncthreads_and(w)) {
         ok = false;
-        break;
-      }
-      // gather: warp -> rows warp, warp + 8, ...; lane -> elements 2 lane, 2 lane + 1
-      unsigned char* stage = sA + (size_t)s * stage_bytes;
-      unsigned char* bstage = a.b_streamed ? stage + kPStageBytes : sB + (size_t)kb * bblk;
-      if (a.b_streamed)
-        for (int t2 = threadIdx.x; t2 < a.nb * 8; t2 += kPThreads) {
-          const int row = t2 / 8, chunk = t2 % 8;
-          const uint4 v = *reinterpret_cast<const uint4*>(a.Bg + (size_t)row * Kp + kb * kPK + chunk * 8);
-          *reinterpret_cast<uint4*>(bstage + sw128_off(row, chunk * 8)) = v;
-        }
-      const int e0 = kb * kPK + 2 * lane;
-      const int o0 = s_eo[e0], o1 = s_eo[e0 + 1];
-      const float m0 = s_cm[e0], m1 = s_cm[e0 + 1];
-      const bool u0 = o0 != kNoElem, u1 = o1 != kNoElem;
-      // rows warp + 8 i share r & 7, hence the swizzled chunk: one offset per thread
-      unsigned char* dst0 = stage + sw128_off(warp, 2 * lane);
-      float v0[kPM / 8], v1[kPM / 8];
-#pragma unroll
-      for (int i = 0; i < kPM / 8; ++i) {  // every load of the block in flight at once
-        const int64_t b = s_base[warp + 8 * i];
-        v0[i] = (b >= 0 && u0) ? __ldg(a.grid + b + o0) : 0.0f;
-        v1[i] = (b >= 0 && u1) ? __ldg(a.grid + b + o1) : 0.0f;
-      }
-#pragma unroll
-      for (int i = 0; i < kPM / 8; ++i) {
-        const int64_t b = s_base[warp + 8 * i];
-        const float x0 = (b >= 0 && u0) ? __fsub_rn(v0[i], m0) : 0.0f;
-        const float x1 = (b >= 0 && u1) ? __fsub_rn(v1[i], m1) : 0.0f;
-        *reinterpret_cast<__nv_bfloat162*>(dst0 + i * 1024) = __floats2bfloat162_rn(x0, x1);  // x0 at the lower address
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (threadIdx.x == 0) {
+      } else {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t a0 = smem_u32(stage), b0 = smem_u32(bstage);
+        const int q = warp & 3;  // TMEM lanes 32 q .. 32 q + 31 = rows of the tile
+        const int64_t row = tp * kPM + q * 32 + lane;
+        const bool valid = row < a.N;
+        const uint32_t tbuf = tmem + (uint32_t)((P & 1) * a.nb) + ((uint32_t)(q * 32) << 16);
+        for (int j = warp >> 2; j < nchunks; j += 2) {  // warp-uniform
+          uint32_t v[32];
+          tmem_ld32(tbuf + 32 * j, v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          const int col0 = 32 * j;
+          uint32_t yb[16];  // the 32 columns' BF16 results, in pairs
 #pragma unroll
-        for (int kk = 0; kk < kPK / 16; ++kk)
-          mma_bf16(tmem, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), idesc,
-                   (kb > 0 || kk > 0) ? 1u : 0u);
-        tc_commit(&empty_bar[s]);
-        if (kb == a.kblocks - 1) tc_commit(&acc_full);
-      }
-    }
-    if (!ok) break;
-    // epilogue: the accumulators of this tile
-    const bool w = mbar_wait(&acc_full, (uint32_t)local & 1u);
-    if (!__syncthreads_and(w)) {
-      ok = false;
-      break;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    // The columns are taken in groups of whole curves (cpg curves, at most 64
-    // columns): warp w reads TMEM lanes 32 (w % 4) .. and 32 of the group's
-    // columns into [128 rows][65] floats in the free A ring (the odd row
-    // stride keeps row-per-lane writes and column reads free of bank
-    // conflicts); then thread (curve slot, row) writes that curve's D values
-    // of the row as BF16 and the warps reduce the per-axis minima / maxima of
-    // their 32 rows.
-    float* stg = reinterpret_cast<float*>(sA);
-    constexpr int kRS = 65;
-    const int quarter = warp & 3, half = warp >> 2;
-    const int64_t row0 = t * kPM;
-    const int nrow = (int)(a.N - row0 < kPM ? a.N - row0 : kPM);
-    const int cpg = 64 / a.D;  // curves per group (D <= 16: at least 4)
-    for (int cur0 = 0; cur0 < a.C; cur0 += cpg) {
-      const int col0 = cur0 * a.D;
-      const int ncur = min(cpg, a.C - cur0);
-      if ((uint32_t)(col0 + 32 * half) < a.tmem_cols) {  // warp-uniform
-        uint32_t v[32];
-        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(col0 + 32 * half), v);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        float* dst = stg + (size_t)(quarter * 32 + lane) * kRS + 32 * half;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) dst[i] = __uint_as_float(v[i]);
-      }
-      __syncthreads();
-      for (int pidx = threadIdx.x; pidx < ncur * kPM; pidx += kPThreads) {
-        const int slot = pidx / kPM, r = pidx % kPM;  // kPM = 128: shifts
-        const int curve = cur0 + slot, cb = curve * a.D;
-        const float* src = stg + (size_t)r * kRS + slot * a.D;
-        const bool valid = r < nrow;
-        __nv_bfloat16 yb[16];
-        float yf[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k)
-          if (k < a.D) {
-            yb[k] = __float2bfloat16_rn(__fadd_rn(src[k], s_beta[cb + k]));
-            yf[k] = __bfloat162float(yb[k]);
+          for (int i = 0; i < 32; i += 2) {
+            const int c = col0 + i;
+            const float f0 = c < a.CD ? __fadd_rn(__uint_as_float(v[i]), s_beta[c]) : 0.0f;
+            const float f1 = c + 1 < a.CD ? __fadd_rn(__uint_as_float(v[i + 1]), s_beta[c + 1]) : 0.0f;
+            const __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
+            yb[i / 2] = *reinterpret_cast<const uint32_t*>(&h);
           }
-        if (valid) {
-          __nv_bfloat16* out = a.proj + ((int64_t)curve * a.N + row0 + r) * a.D;
-          if ((a.D & 7) == 0) {
+          if (valid) {
+            if (vec) {
+              // whole curves: vector stores of each curve's D values
+#define SFC_OUT(cs) (a.proj + ((int64_t)s_cur[col0 + (cs) * a.D] * a.N + row) * a.D)
+              switch (a.D) {
+                case 16:
 #pragma unroll
-            for (int k = 0; k < 16; k += 8)
-              if (k < a.D) {
-                uint4 u;
-                u.x = (uint32_t)__bfloat16_as_ushort(yb[k]) | ((uint32_t)__bfloat16_as_ushort(yb[k + 1]) << 16);
-                u.y = (uint32_t)__bfloat16_as_ushort(yb[k + 2]) | ((uint32_t)__bfloat16_as_ushort(yb[k + 3]) << 16);
-                u.z = (uint32_t)__bfloat16_as_ushort(yb[k + 4]) | ((uint32_t)__bfloat16_as_ushort(yb[k + 5]) << 16);
-                u.w = (uint32_t)__bfloat16_as_ushort(yb[k + 6]) | ((uint32_t)__bfloat16_as_ushort(yb[k + 7]) << 16);
-                *reinterpret_cast<uint4*>(out + k) = u;
+                  for (int cs = 0; cs < 2; ++cs)
+                    if (col0 + cs * 16 < a.CD) {
+                      uint4* o = reinterpret_cast<uint4*>(SFC_OUT(cs));
+                      o[0] = make_uint4(yb[8 * cs], yb[8 * cs + 1], yb[8 * cs + 2], yb[8 * cs + 3]);
+                      o[1] = make_uint4(yb[8 * cs + 4], yb[8 * cs + 5], yb[8 * cs + 6], yb[8 * cs + 7]);
+                    }
+                  break;
+                case 8:
+#pragma unroll
+                  for (int cs = 0; cs < 4; ++cs)
+                    if (col0 + cs * 8 < a.CD)
+                      *reinterpret_cast<uint4*>(SFC_OUT(cs)) =
+                          make_uint4(yb[4 * cs], yb[4 * cs + 1], yb[4 * cs + 2], yb[4 * cs + 3]);
+                  break;
+                case 4:
+#pragma unroll
+                  for (int cs = 0; cs < 8; ++cs)
+                    if (col0 + cs * 4 < a.CD) *reinterpret_cast<uint2*>(SFC_OUT(cs)) = make_uint2(yb[2 * cs], yb[2 * cs + 1]);
+                  break;
+                case 2:
+#pragma unroll
+                  for (int cs = 0; cs < 16; ++cs)
+                    if (col0 + cs * 2 < a.CD) *reinterpret_cast<uint32_t*>(SFC_OUT(cs)) = yb[cs];
+                  break;
+                default:  // D == 1
+#pragma unroll
+                  for (int cs = 0; cs < 32; ++cs)
+                    if (col0 + cs < a.CD)
+                      *reinterpret_cast<unsigned short*>(SFC_OUT(cs)) = (unsigned short)(yb[cs / 2] >> (16 * (cs & 1)));
+                  break;
               }
-          } else {
+#undef SFC_OUT
+            } else {
 #pragma unroll
-            for (int k = 0; k < 16; ++k)
-              if (k < a.D) out[k] = yb[k];
+              for (int i = 0; i < 32; ++i) {
+                const int c = col0 + i;
+                if (c < a.CD)
+                  *reinterpret_cast<unsigned short*>(a.proj + ((int64_t)s_cur[c] * a.N + row) * a.D + s_k[c]) =
+                      (unsigned short)(yb[i / 2] >> (16 * (i & 1)));
+              }
+            }
+          }
+          // the columns' ranges over the warp's 32 rows
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int c = col0 + i;
+            if (c < a.CD) {  // warp-uniform
+              const float y = __uint_as_float((i & 1) ? (yb[i / 2] & 0xffff0000u) : (yb[i / 2] << 16));
+              const uint32_t u = ord_of_f(y);
+              uint32_t lo = valid ? u : 0xffffffffu, hi = valid ? u : 0u;
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) {
+                lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+              }
+              if (lane == 0) {
+                atomicMin(&s_min[c], lo);
+                atomicMax(&s_max[c], hi);
+              }
+            }
           }
         }
-        // per-axis range of the warp's 32 rows (a warp holds one curve slot:
-        // 128 rows per slot, 32 rows per warp)
-#pragma unroll
-        for (int k = 0; k < 16; ++k)
-          if (k < a.D) {
-            uint32_t lo = valid ? ord_of_f(yf[k]) : 0xffffffffu, hi = valid ? ord_of_f(yf[k]) : 0u;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-              lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-              hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-            }
-            if (lane == 0) {
-              atomicMin(&s_min[cb + k], lo);
-              atomicMax(&s_max[cb + k], hi);
-            }
-          }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
       }
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();
     }
+    if (!have) break;
   }
   // ranges of this CTA
   if (ok)
@@ -375,7 +405,7 @@ int project_bf16(Index& ix, const float* grid, void* proj, uint32_t* lohi, cudaS
   SFC_TRY(cudaGetLastError());
   SFC_CHECK(lohi_init(lohi, CD, st));
   // launch: one or two CTAs per SM (by shared memory), persistent over tiles
-  const size_t tables = (size_t)Kp * 8 + (size_t)CD * 12 + 8 + kPM * 8;
+  const size_t tables = (size_t)Kp * 8 + (size_t)CD * 20 + 8 + kPM * 8;
   size_t shm = 1024 + (size_t)kblocks * nb * 128 + (size_t)kPStages * kPStageBytes + tables;
   int streamed = 0;
   if (shm > 227 * 1024) {  // B streamed through the stages with A
@@ -391,9 +421,9 @@ int project_bf16(Index& ix, const float* grid, void* proj, uint32_t* lohi, cudaS
   int dev = 0, sms = 0, per_sm = 0;
   SFC_TRY(cudaGetDevice(&dev));
   SFC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  SFC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_proj_tc, kPThreads, shm));
-  if (per_sm < 1) per_sm = 1;
-  if (per_sm > 2) per_sm = 2;  // TMEM: at most 2 x 256 columns per SM here
+  // two CTAs per SM when their shared memory fits (one CTA's gather then
+  // overlaps the other's waits); TMEM below
+  per_sm = 2 * (shm + 2048) <= 233472 ? 2 : 1;
   PtArgs a;
   a.grid = grid;
   a.dict = ix.dict;
@@ -412,16 +442,10 @@ int project_bf16(Index& ix, const float* grid, void* proj, uint32_t* lohi, cudaS
   a.proj = static_cast<__nv_bfloat16*>(proj);
   a.lohi = lohi;
   a.status = status_word();
-  // TMEM columns: the accumulator (nb) and every 64-column read of the
-  // epilogue's curve groups (a group starts at a multiple of D)
-  int need = nb;
-  for (int c0 = 0, cpg = 64 / D; c0 < C; c0 += cpg) need = std::max(need, c0 * D + 64);
+  // TMEM columns: two accumulator buffers of nb columns (the epilogue reads
+  // 32-column chunks below round_up(C D, 32) <= nb of a buffer)
   uint32_t cols = 32;
-  while (cols < (uint32_t)need) cols <<= 1;
-  if (cols > 512) {
-    set_error("the BF16 projection needs more than 512 TMEM columns (curves * dims too large)");
-    return SFC_EUNSUPPORTED;
-  }
+  while (cols < (uint32_t)(2 * nb)) cols <<= 1;
   a.tmem_cols = cols;
   per_sm = std::min(per_sm, (int)(512 / cols));  // every CTA on an SM holds its columns at once
   a.b_streamed = streamed;
