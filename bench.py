@@ -970,13 +970,16 @@ def main():
 
     # ---- the fill loop on the full workload (SFC mode, until no pixel is unknown)
     fill_steps_cap = 40000
-    gg = gd.clone()
-    mm = md.clone()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    fsteps, flog = sfc.inpaint_run(gg, mm, mode=sfc.SFC_MODE_SFC, max_steps=fill_steps_cap, **prm)
-    torch.cuda.synchronize()
-    fill_s = time.perf_counter() - t0
+    fill_times = []
+    for r in range(2):  # the first run is untimed
+        gg = gd.clone()
+        mm = md.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fsteps, flog = sfc.inpaint_run(gg, mm, mode=sfc.SFC_MODE_SFC, max_steps=fill_steps_cap, **prm)
+        torch.cuda.synchronize()
+        fill_times.append(time.perf_counter() - t0)
+    fill_s = fill_times[-1]
     fill_big = {"workload": "the headline image and mask, SFC mode with the headline's index parameters, "
                             "confidence priority",
                 "unknown_pixels": int((m == 0).sum()), "steps": int(fsteps), "step_cap": fill_steps_cap,
