@@ -924,6 +924,29 @@ struct ClShm {
   float* Qf32;  // s x p   (Qf rounded to FP32, for the FP32 products)
 };
 
+// every CTA: the rows of Qf held by the other CTAs of the cluster (row i by
+// rank i / rp), read through distributed shared memory; 16-byte reads where
+// the rows pair up and the array is aligned
+template <int CS>
+__device__ void cl_gather_qf(cg::cluster_group& cl, ClShm& m, int s, int p, int rp) {
+  const int me = (int)cl.block_rank();
+  if ((p & 1) == 0 && (((uintptr_t)m.Qf) & 15) == 0) {
+    const int half = p / 2;
+    double2* q2 = reinterpret_cast<double2*>(m.Qf);
+#pragma unroll 8
+    for (int t = threadIdx.x; t < s * half; t += blockDim.x) {
+      const int rk = (t / half) / rp;
+      if (rk != me) q2[t] = cl.map_shared_rank(q2, rk)[t];
+    }
+  } else {
+#pragma unroll 4
+    for (int t = threadIdx.x; t < s * p; t += blockDim.x) {
+      const int rk = (t / p) / rp;
+      if (rk != me) m.Qf[t] = cl.map_shared_rank(m.Qf, rk)[t];
+    }
+  }
+}
+
 // every CTA: out[t] = sum over ranks (in order) of part[t], t < len
 template <int CS>
 __device__ void cl_allreduce(cg::cluster_group& cl, double* part, double* out, int len) {
@@ -999,12 +1022,7 @@ __device__ void cl_cholqr(cg::cluster_group& cl, ClShm& m, int nr, int r0, int s
   __syncthreads();
   for (int t = threadIdx.x; t < nr * p; t += blockDim.x) m.Zs[t] = m.Qf[(r0 + t / p) * p + t % p];
   cl.sync();
-  const int me = (int)cl.block_rank();
-#pragma unroll 4
-  for (int t = threadIdx.x; t < s * p; t += blockDim.x) {
-    const int rk = (t / p) / rp;
-    if (rk != me) m.Qf[t] = cl.map_shared_rank(m.Qf, rk)[t];
-  }
+  cl_gather_qf<CS>(cl, m, s, p, rp);
   cl.sync();
 }
 
@@ -1013,12 +1031,7 @@ template <int CS>
 __device__ void cl_allgather_rows(cg::cluster_group& cl, ClShm& m, int nr, int r0, int s, int p, int rp) {
   for (int t = threadIdx.x; t < nr * p; t += blockDim.x) m.Qf[(r0 + t / p) * p + t % p] = m.Zs[t];
   cl.sync();
-  const int me = (int)cl.block_rank();
-#pragma unroll 4
-  for (int t = threadIdx.x; t < s * p; t += blockDim.x) {
-    const int rk = (t / p) / rp;
-    if (rk != me) m.Qf[t] = cl.map_shared_rank(m.Qf, rk)[t];
-  }
+  cl_gather_qf<CS>(cl, m, s, p, rp);
   cl.sync();
 }
 
@@ -1263,7 +1276,7 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
   // the start block is close to orthonormal: the fast form usually suffices
   if (!cl_orth_fast<CS>(cl, m, nr, r0, s, p, rp)) {
     cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
-    cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
+    if (!cl_orth_fast<CS>(cl, m, nr, r0, s, p, rp)) cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
   }
   bool conv = false;
   // products in FP32 until a Rayleigh-Ritz residual reaches 3.2e-6 of l_1 (or
@@ -1376,9 +1389,11 @@ __global__ void __launch_bounds__(256) k_si_cluster(SiBufs b, int s, int p, int 
     // Z has nearly orthogonal columns and one pass is accurate to rounding
     // the FP32 factor with the FP64 second-order correction when the block is
     // close enough to orthogonal, else two FP64 Cholesky QR passes
+    // (after one FP64 pass the block is close to orthonormal, so the second
+    // pass is the fast form whenever its FP32 factor succeeds)
     if (!cl_orth_fast<CS>(cl, m, nr, r0, s, p, rp)) {
       cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
-      cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
+      if (!cl_orth_fast<CS>(cl, m, nr, r0, s, p, rp)) cl_cholqr<CS>(cl, m, nr, r0, s, p, rp);
     }
   }
   cl.sync();  // no CTA leaves while others may still read its shared memory
