@@ -14,6 +14,7 @@ void set_error(const std::string& msg);
 
 // Host-side count of kernel launches made by the library (diagnostics).
 void count_launch();
+void count_launches(int64_t n);  // n kernels launched at once (a graph), or -n captured but not run
 
 // Evaluate a CUDA runtime call; on failure record the message and return SFC_ECUDA
 // (SFC_ENOMEM for allocation failures) from the enclosing function.

@@ -305,37 +305,81 @@ int fill_loop(const Geo& g, float* grid, uint8_t* mask, int prio, int mode, cons
   }
   // every step fills >= 1 unknown pixel, so `left` steps always suffice
   const int64_t log_cap = max_steps > 0 ? (max_steps < left ? max_steps : left) : left;
-  int64_t enqueued = 0;
-  int chunk = 8;
-  int done = 0;
-  int rc = SFC_OK;
-  int64_t first = 1;
-  while (!done && rc == SFC_OK) {
-    for (int k = 0; k < chunk; ++k) {
-      if (!first) {
-        count_launch();
-        k_prio<<<bg, 256, 0, st>>>(grid, mask, g, prio, s, 0);
-      }
-      first = 0;
+  // One step: the priorities around the last insert (the first step has the
+  // whole map just computed), the target, the search, the insert.
+  auto step = [&](bool update) -> int {
+    if (update) {
       count_launch();
-      k_argmax<<<ag, 256, 0, st>>>(s.key, npix, s);
-      count_launch();
-      k_select<<<1, 1, 0, st>>>(g, s, max_steps);
-      if (mode == SFC_MODE_SFC)
-        rc = query_batch(*ix, grid, mask, s.sel_xyz, 1, s.pick, s.cost, nullptr, nullptr, nullptr, nullptr, st);
-      else
-        rc = fullscan_single(g, grid, mask, dict, N, eoff_all, weights, cm, s.sel_lin, s.pick, s.cost, tilemin,
-                             gmin, st);
-      if (rc != SFC_OK) break;
-      count_launch();
-      k_insert<<<1, 256, 0, st>>>(grid, mask, g, dict, s, log, log_cap, unknown, status_word());
-      ++enqueued;
+      k_prio<<<bg, 256, 0, st>>>(grid, mask, g, prio, s, 0);
     }
-    SFC_TRY(cudaGetLastError());
+    count_launch();
+    k_argmax<<<ag, 256, 0, st>>>(s.key, npix, s);
+    count_launch();
+    k_select<<<1, 1, 0, st>>>(g, s, max_steps);
+    const int r = mode == SFC_MODE_SFC
+                      ? query_batch(*ix, grid, mask, s.sel_xyz, 1, s.pick, s.cost, nullptr, nullptr, nullptr, nullptr,
+                                    st)
+                      : fullscan_single(g, grid, mask, dict, N, eoff_all, weights, cm, s.sel_lin, s.pick, s.cost,
+                                        tilemin, gmin, st);
+    if (r != SFC_OK) return r;
+    count_launch();
+    k_insert<<<1, 256, 0, st>>>(grid, mask, g, dict, s, log, log_cap, unknown, status_word());
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      set_error(std::string("inpaint_run: ") + cudaGetErrorString(e));
+      return SFC_ECUDA;
+    }
+    return SFC_OK;
+  };
+  // After the first step (eager), the loop runs as a CUDA graph of kGraphSteps
+  // steps replayed between completion checks: every kernel of a step reads its
+  // inputs from device state and returns at once after the last step, so a
+  // replay past the end does nothing but a search on the last target.  If the
+  // capture cannot be made, the same steps are enqueued one by one.
+  constexpr int kGraphSteps = 8;
+  struct GraphHold {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    ~GraphHold() {
+      if (x) cudaGraphExecDestroy(x);
+      if (g) cudaGraphDestroy(g);
+    }
+  } gh;
+  int64_t enqueued = 0;
+  int done = 0;
+  int rc = step(false);
+  ++enqueued;
+  bool graph_ok = false;
+  uint64_t per_graph = 0;
+  if (rc == SFC_OK && cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    const uint64_t l0 = sfc_launch_count();
+    int r = SFC_OK;
+    for (int k = 0; k < kGraphSteps && r == SFC_OK; ++k) r = step(true);
+    const cudaError_t e = cudaStreamEndCapture(st, &gh.g);
+    per_graph = sfc_launch_count() - l0;
+    count_launches(-(int64_t)per_graph);  // captured, not run yet
+    graph_ok = r == SFC_OK && e == cudaSuccess && gh.g && cudaGraphInstantiate(&gh.x, gh.g, 0) == cudaSuccess;
+    if (!graph_ok) {
+      cudaGetLastError();
+      set_error("");
+    }
+  }
+  int reps = 1;
+  while (!done && rc == SFC_OK) {
+    for (int k = 0; k < reps && rc == SFC_OK; ++k) {
+      if (graph_ok) {
+        SFC_TRY(cudaGraphLaunch(gh.x, st));
+        count_launches((int64_t)per_graph);
+        enqueued += kGraphSteps;
+      } else {
+        for (int u = 0; u < kGraphSteps && rc == SFC_OK; ++u, ++enqueued) rc = step(true);
+      }
+    }
+    if (rc != SFC_OK) break;
     SFC_TRY(cudaMemcpyAsync(&done, s.done, sizeof(int), cudaMemcpyDeviceToHost, st));
     SFC_TRY(cudaStreamSynchronize(st));
-    if (chunk < 256) chunk *= 2;
-    if (!done && enqueued > left + 1) {
+    if (reps < 32) reps *= 2;
+    if (!done && enqueued > left + kGraphSteps) {
       set_error("inpaint_run: the loop did not finish within one step per unknown pixel");
       rc = SFC_EDEVICE;
     }
