@@ -351,7 +351,33 @@ int fill_loop(const Geo& g, float* grid, uint8_t* mask, int prio, int mode, cons
   ++enqueued;
   bool graph_ok = false;
   uint64_t per_graph = 0;
-  if (rc == SFC_OK && cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+  // The steps run on the library's own stream (a capture needs a stream other
+  // than the legacy default one), ordered after `st` by an event and joined
+  // back into it at the end.
+  // (joined on every return, before the scratch guard frees on `st`)
+  struct Join {
+    cudaStream_t caller = nullptr, own = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    ~Join() {
+      if (own && ev_out && cudaEventRecord(ev_out, own) == cudaSuccess) cudaStreamWaitEvent(caller, ev_out, 0);
+      if (ev_in) cudaEventDestroy(ev_in);
+      if (ev_out) cudaEventDestroy(ev_out);
+    }
+  } jn;
+  const cudaStream_t caller = st;
+  jn.caller = st;
+  if (cudaStream_t own = aux_stream(0)) {
+    if (cudaEventCreateWithFlags(&jn.ev_in, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&jn.ev_out, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventRecord(jn.ev_in, caller) == cudaSuccess && cudaStreamWaitEvent(own, jn.ev_in, 0) == cudaSuccess) {
+      jn.own = own;
+      st = own;
+    }
+  }
+  cudaGetLastError();
+  if (rc == SFC_OK && st != caller) {
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) cudaGetLastError();
+    else {
     const uint64_t l0 = sfc_launch_count();
     int r = SFC_OK;
     for (int k = 0; k < kGraphSteps && r == SFC_OK; ++k) r = step(true);
@@ -362,6 +388,7 @@ int fill_loop(const Geo& g, float* grid, uint8_t* mask, int prio, int mode, cons
     if (!graph_ok) {
       cudaGetLastError();
       set_error("");
+    }
     }
   }
   int reps = 1;
@@ -383,6 +410,11 @@ int fill_loop(const Geo& g, float* grid, uint8_t* mask, int prio, int mode, cons
       set_error("inpaint_run: the loop did not finish within one step per unknown pixel");
       rc = SFC_EDEVICE;
     }
+  }
+  if (jn.own) {  // join the caller's stream now (the rest runs on it)
+    if (cudaEventRecord(jn.ev_out, jn.own) == cudaSuccess) cudaStreamWaitEvent(caller, jn.ev_out, 0);
+    jn.own = nullptr;
+    st = caller;
   }
   int64_t steps = 0;
   SFC_TRY(cudaMemcpyAsync(&steps, s.steps, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
