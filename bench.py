@@ -360,6 +360,53 @@ def run_profile_fp16(width: int, queries: int):
     return 0 if st == 0 else 1
 
 
+def run_profile_step(precision: str, steps: int):
+    """The headline step (index build + every front-target query) STEPS times
+    on the workload, for ncu launch lists and captures; prints one line, no
+    timing."""
+    import torch
+
+    import __graft_entry__
+    import paper_1712_06326_gb300.sfc as sfc
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    g, m, t = workload_inputs()
+    gd, md, td = (torch.from_numpy(a).cuda() for a in (g, m, t))
+    prm = dict(index_params(), precision=sfc.SFC_BF16 if precision == "bf16" else sfc.SFC_FP32)
+    for _ in range(steps):
+        ix = sfc.sfc_index_build(gd, md, **prm)
+        sfc.sfc_query_batch(ix, gd, md, td)
+        ix.close()
+    torch.cuda.synchronize()
+    st = sfc.sfc_status()
+    print(json.dumps({"profile_step": {"precision": precision, "steps": steps, "queries": int(len(t)), "status": st}}))
+    return 0 if st == 0 else 1
+
+
+def run_profile_fill(steps: int):
+    """The fill loop (SFC mode, the workload's index parameters) for STEPS
+    steps on the workload, twice, for ncu; prints one line, no timing."""
+    import torch
+
+    import __graft_entry__
+    import paper_1712_06326_gb300.sfc as sfc
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    g, m, _ = workload_inputs()
+    prm = {k: WORKLOAD[k] for k in ("K", "curves", "dims", "bits", "window", "pca_sample")}
+    done = []
+    for _ in range(2):
+        gd, md = torch.from_numpy(g).cuda(), torch.from_numpy(m).cuda()
+        n, _ = sfc.inpaint_run(gd, md, mode=sfc.SFC_MODE_SFC, max_steps=steps, **prm)
+        done.append(int(n))
+    torch.cuda.synchronize()
+    st = sfc.sfc_status()
+    print(json.dumps({"profile_fill": {"steps": done, "status": st}}))
+    return 0 if st == 0 else 1
+
+
 def batch_inputs():
     import concurrent.futures as cf
     import multiprocessing as mp
@@ -624,11 +671,24 @@ def main():
     ap.add_argument("--profile-fp16", nargs=2, type=int, metavar=("WIDTH", "QUERIES"),
                     help="profiling case only: two tensor-core full scans (SFC_FP16) of QUERIES targets on a "
                          "WIDTH^2 voronoi2d grid, K=11; prints one line, no timing")
+    ap.add_argument("--profile-step", nargs=2, metavar=("PRECISION", "STEPS"),
+                    help="profiling case only: STEPS headline steps (index build with fp32 or bf16 projections "
+                         "+ every front-target query) on the workload; prints one line, no timing")
+    ap.add_argument("--profile-fill", type=int, metavar="STEPS",
+                    help="profiling case only: the fill loop on the workload (SFC mode) for STEPS steps, twice; "
+                         "prints one line, no timing")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_fp16:
         return run_profile_fp16(*args.profile_fp16)
+    if args.profile_step:
+        prec, n = args.profile_step
+        if prec not in ("fp32", "bf16"):
+            ap.error("--profile-step PRECISION must be fp32 or bf16")
+        return run_profile_step(prec, int(n))
+    if args.profile_fill:
+        return run_profile_fill(args.profile_fill)
 
     import torch
     import torch.distributed as dist

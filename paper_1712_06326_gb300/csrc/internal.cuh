@@ -186,9 +186,23 @@ struct TargetGrid {
   const int* eoff;
   const float* dict_grid;
 };
+// Device buffers for the split form of a small batch (up to qmax queries of up
+// to cap candidates each): the candidate ids, their number and their FP32 costs.
+struct QSplit {
+  int32_t* cand = nullptr;  // qmax * cap
+  int32_t* ncand = nullptr; // qmax
+  float* c32 = nullptr;     // qmax * cap
+  int64_t cap = 0, qmax = 0;
+};
+// Candidates per query of an index (C * window, or C * k): the size of a QSplit.
+int64_t query_split_cap(const Index& ix);
+// Batches of up to 32 queries with picks run in the split form (the rescore
+// spread over many CTAs; same picks and costs), in `split` if given and large
+// enough, else in stream-ordered scratch (the one-CTA form while `st` is being
+// captured).
 int query_batch(const Index& ix, const float* grid, const uint8_t* cur_mask, const int32_t* centres, int64_t Q,
                 int64_t* pick, float* cost, uint64_t* qkeys, int64_t* pos, int32_t* cand, int32_t* ncand,
-                cudaStream_t st, const TargetGrid* tgt = nullptr);
+                cudaStream_t st, const TargetGrid* tgt = nullptr, const QSplit* split = nullptr);
 // Queries of several images in one launch (every index built with the same
 // parameters); the object keeps a device table of the images.
 struct MultiQuery;

@@ -281,6 +281,14 @@ int fill_loop(const Geo& g, float* grid, uint8_t* mask, int prio, int mode, cons
   SFC_TRY(scr.alloc(&unknown, sizeof(int64_t)));
   SFC_TRY(scr.alloc(&tilemin, sizeof(float) * (ntiles > 0 ? ntiles : 1)));
   SFC_TRY(scr.alloc(&gmin, sizeof(unsigned int)));
+  QSplit qs;  // the search's buffers (SFC mode): the split form of one query
+  if (mode == SFC_MODE_SFC && ix) {
+    qs.cap = query_split_cap(*ix);
+    qs.qmax = 1;
+    SFC_TRY(scr.alloc(&qs.cand, sizeof(int32_t) * qs.cap));
+    SFC_TRY(scr.alloc(&qs.ncand, sizeof(int32_t)));
+    SFC_TRY(scr.alloc(&qs.c32, sizeof(float) * qs.cap));
+  }
   SFC_TRY(cudaMemsetAsync(unknown, 0, sizeof(int64_t), st));
   SFC_TRY(cudaMemsetAsync(s.key, 0, sizeof(unsigned long long) * npix, st));
   SFC_TRY(cudaMemsetAsync(s.cterm, 0, sizeof(float) * npix, st));
@@ -318,7 +326,7 @@ int fill_loop(const Geo& g, float* grid, uint8_t* mask, int prio, int mode, cons
     k_select<<<1, 1, 0, st>>>(g, s, max_steps);
     const int r = mode == SFC_MODE_SFC
                       ? query_batch(*ix, grid, mask, s.sel_xyz, 1, s.pick, s.cost, nullptr, nullptr, nullptr, nullptr,
-                                    st)
+                                    st, nullptr, &qs)
                       : fullscan_single(g, grid, mask, dict, N, eoff_all, weights, cm, s.sel_lin, s.pick, s.cost,
                                         tilemin, gmin, st);
     if (r != SFC_OK) return r;

@@ -68,6 +68,7 @@ struct QArgs {
   int64_t* pos;
   int32_t* cand_out;
   int32_t* ncand_out;
+  float* c32_out;  // split form: FP32 cost of every candidate slot (stride C * capw)
   uint32_t* status;
 };
 
@@ -326,6 +327,64 @@ __device__ void warp_knn(const uint64_t* __restrict__ sk, const uint32_t* __rest
 // target's nk known elements, compacted: lane holds known elements lane + 32 t
 // in registers), into c32; returns this warp's minimum.
 // L1 (Sec. III.K): w |d| instead of w d^2.
+// The target patch of centre tc in shared memory: tv[e] its values, deo[e]
+// the element offsets in the dictionary grid, tm[pp] its known flags.
+__device__ __forceinline__ void stage_target(const QImg& I, int64_t tc, float* tv, int* deo, uint8_t* tm) {
+  const Geo& g = I.g;
+  for (int e = threadIdx.x; e < g.n; e += kQThreads) {
+    deo[e] = I.deoff[e];
+    tv[e] = I.grid[tc * g.ch + I.eoff_all[e]];
+  }
+  for (int pp = threadIdx.x; pp < g.P; pp += kQThreads) tm[pp] = I.mask[tc + I.eoff_all[pp * g.ch] / g.ch];
+}
+
+// The known elements of the staged target, compacted in patch order (unknown
+// ones add exactly 0 to a cost, so only known values are gathered): ceo their
+// dictionary-grid offsets, ct their values, cw their channel weights.  Returns
+// their number; the whole CTA calls it.
+template <bool WEIGHTED>
+__device__ int compact_known(int n, int ch, const uint8_t* tm, const int* deo, const float* tv,
+                             const float* __restrict__ weights, int* ceo, float* ct, float* cw, uint32_t* s_part) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int nk = 0;
+  for (int r0 = 0; r0 < n; r0 += kQThreads) {
+    const int e = r0 + tid;
+    const bool kn = e < n && tm[e / ch] != 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, kn);
+    if (lane == 0) s_part[warp] = (uint32_t)__popc(bal);
+    __syncthreads();
+    int off = nk, tot = 0;
+    for (int w = 0; w < kQWarps; ++w) {
+      if (w < warp) off += (int)s_part[w];
+      tot += (int)s_part[w];
+    }
+    if (kn) {
+      const int at = off + __popc(bal & ((1u << lane) - 1u));
+      ceo[at] = deo[e];
+      ct[at] = tv[e];
+      cw[at] = WEIGHTED ? weights[e % ch] : 1.0f;
+    }
+    __syncthreads();
+    nk += tot;
+  }
+  return nk;
+}
+
+// Lane registers of the compacted elements lane + 32 t.
+template <int MAXE>
+__device__ __forceinline__ void lane_elems(int nk, const int* ceo, const float* ct, const float* cw, float (&tr)[MAXE],
+                                           int (&eor)[MAXE], float (&wv)[MAXE]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int t = 0; t < MAXE; ++t) {
+    const int e = lane + 32 * t;
+    const bool in = e < nk;
+    tr[t] = in ? ct[e] : 0.0f;
+    eor[t] = in ? ceo[e] : 0;
+    wv[t] = in ? cw[e] : 0.0f;
+  }
+}
+
 template <int MAXE, bool WEIGHTED, bool L1>
 __device__ __forceinline__ float rescore_all(const float* __restrict__ dgrid, const uint32_t* __restrict__ dict,
                                              const uint32_t* ucand, int ncand, int ch, int nk, const float (&tr)[MAXE],
@@ -438,12 +497,7 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
     return;
   }
   const int64_t tc = s_redi[0];
-  for (int e = tid; e < n; e += kQThreads) {
-    int o = I.eoff_all[e];
-    deo[e] = I.deoff[e];
-    tv[e] = I.grid[tc * ch + o];
-  }
-  for (int pp = tid; pp < P; pp += kQThreads) tm[pp] = I.mask[tc + I.eoff_all[pp * ch] / ch];
+  stage_target(I, tc, tv, deo, tm);
   __syncthreads();
 
   // --- index selection ------------------------------------------------------
@@ -611,39 +665,10 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
   if (!a.pick) return;
 
   // --- FP32 rescore --------------------------------------------------------
-  // the known elements of the target, compacted in patch order: unknown ones
-  // add exactly 0 to a cost, so only known values are gathered
-  int nk = 0;
-  for (int r0 = 0; r0 < n; r0 += kQThreads) {
-    const int e = r0 + tid;
-    const bool kn = e < n && tm[e / ch] != 0;
-    const unsigned bal = __ballot_sync(0xffffffffu, kn);
-    if (lane == 0) s_part[warp] = (uint32_t)__popc(bal);
-    __syncthreads();
-    int off = nk, tot = 0;
-    for (int w = 0; w < kQWarps; ++w) {
-      if (w < warp) off += (int)s_part[w];
-      tot += (int)s_part[w];
-    }
-    if (kn) {
-      const int at = off + __popc(bal & ((1u << lane) - 1u));
-      ceo[at] = deo[e];
-      ct[at] = tv[e];
-      cw[at] = WEIGHTED ? a.weights[e % ch] : 1.0f;
-    }
-    __syncthreads();
-    nk += tot;
-  }
+  const int nk = compact_known<WEIGHTED>(n, ch, tm, deo, tv, a.weights, ceo, ct, cw, s_part);
   float tr[MAXE], wv[MAXE];
   int eor[MAXE];
-#pragma unroll
-  for (int t = 0; t < MAXE; ++t) {
-    const int e = lane + 32 * t;
-    const bool in = e < nk;
-    tr[t] = in ? ct[e] : 0.0f;
-    eor[t] = in ? ceo[e] : 0;
-    wv[t] = in ? cw[e] : 0.0f;
-  }
+  lane_elems<MAXE>(nk, ceo, ct, cw, tr, eor, wv);
   // the L2 / L1 choice is uniform: one specialised loop each, no test per element
   const float wmin = a.l1 ? rescore_all<MAXE, WEIGHTED, true>(I.dgrid, I.dict, ucand, ncand, ch, nk, tr, eor, wv, c32)
                           : rescore_all<MAXE, WEIGHTED, false>(I.dgrid, I.dict, ucand, ncand, ch, nk, tr, eor, wv, c32);
@@ -704,6 +729,143 @@ __global__ void __launch_bounds__(kQThreads) k_query(QArgs a) {
       a.cost[q] = __int_as_float(0x7fc00000);
     } else {
       a.pick[q] = ucand[i];
+      a.cost[q] = c32[i];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Split form for small batches (a few queries; the fill loop asks one per
+// step).  One CTA per query leaves most SMs idle while it rescores its C * W
+// candidates two per warp at a time; here the rescore is spread out:
+//   k_query with pick == nullptr writes each query's de-duplicated candidates;
+//   k_qs_rescore: CTA (b, q) rescores slots [b S, (b + 1) S) of query q with
+//     rescore_all, i.e. per candidate the same FP32 operations in the same
+//     order as the one-CTA kernel (the costs are bit-identical);
+//   k_qs_pick: the FP32 minimum, the band and the FP64 decision over (cost,
+//     slot) exactly as the one-CTA kernel takes them.
+constexpr int kQsSlice = 2 * kQWarps;  // candidates per rescoring CTA: one pass of rescore_all
+constexpr int64_t kQsMaxQ = 32;        // batches up to this size take the split form
+
+template <int MAXE, bool WEIGHTED, bool L1>
+__global__ void __launch_bounds__(kQThreads) k_qs_rescore(QArgs a) {
+  const int64_t q = blockIdx.y;
+  const int cap = a.C * a.capw;
+  const int nc = a.ncand_out[q];  // 0: invalid centre
+  const int c0 = blockIdx.x * kQsSlice;
+  if (c0 >= nc) return;
+  const QImg& I = a.img;
+  const Geo& g = I.g;
+  const int n = g.n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* tv = reinterpret_cast<float*>(smem_raw);  // n
+  int* deo = reinterpret_cast<int*>(tv + n);       // n
+  int* ceo = deo + n;                              // n
+  float* ct = reinterpret_cast<float*>(ceo + n);   // n
+  float* cw = ct + n;                              // n
+  uint8_t* tm = reinterpret_cast<uint8_t*>(cw + n);  // P
+  __shared__ uint32_t s_part[kQWarps];
+  const int64_t cx = a.centres[q * g.ndim + 0], cy = a.centres[q * g.ndim + 1];
+  const int64_t cz = g.ndim == 3 ? a.centres[q * g.ndim + 2] : 0;
+  stage_target(I, lin_of(g, cx, cy, cz), tv, deo, tm);
+  __syncthreads();
+  const int nk = compact_known<WEIGHTED>(n, g.ch, tm, deo, tv, a.weights, ceo, ct, cw, s_part);
+  float tr[MAXE], wv[MAXE];
+  int eor[MAXE];
+  lane_elems<MAXE>(nk, ceo, ct, cw, tr, eor, wv);
+  const int cnt = nc - c0 < kQsSlice ? nc - c0 : kQsSlice;
+  rescore_all<MAXE, WEIGHTED, L1>(I.dgrid, I.dict, reinterpret_cast<const uint32_t*>(a.cand_out) + q * cap + c0, cnt,
+                                  g.ch, nk, tr, eor, wv, a.c32_out + q * cap + c0);
+}
+
+__global__ void __launch_bounds__(kQThreads) k_qs_pick(QArgs a) {
+  const int64_t q = blockIdx.x;
+  const int cap = a.C * a.capw;
+  const int nc = a.ncand_out[q];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (nc == 0) {  // invalid centre (k_query raised ST_BAD_CENTRE)
+    if (tid == 0) {
+      a.pick[q] = -1;
+      a.cost[q] = __int_as_float(0x7fc00000);
+    }
+    return;
+  }
+  const QImg& I = a.img;
+  const Geo& g = I.g;
+  const float* c32 = a.c32_out + q * cap;
+  const uint32_t* uc = reinterpret_cast<const uint32_t*>(a.cand_out) + q * cap;
+  __shared__ float s_redf[kQWarps];
+  __shared__ int s_cnt[kQWarps];
+  __shared__ double s_redd[kQWarps];
+  __shared__ int64_t s_redi[kQWarps];
+  float m = INFINITY;
+  for (int ci = tid; ci < nc; ci += kQThreads) m = fminf(m, c32[ci]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) s_redf[warp] = m;
+  __syncthreads();
+  float m32 = s_redf[0];
+  for (int w = 1; w < kQWarps; ++w) m32 = fminf(m32, s_redf[w]);
+  const float T = band_limit32(m32, g.n);
+  int nband = 0, mine = -1;
+  for (int ci = tid; ci < nc; ci += kQThreads)
+    if (c32[ci] <= T) {
+      ++nband;
+      mine = ci;
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nband += __shfl_xor_sync(0xffffffffu, nband, o);
+  if (lane == 0) s_cnt[warp] = nband;
+  __syncthreads();
+  int total = 0;
+  for (int w = 0; w < kQWarps; ++w) total += s_cnt[w];
+  if (total == 1) {
+    if (mine >= 0) {
+      a.pick[q] = uc[mine];
+      a.cost[q] = c32[mine];
+    }
+    return;
+  }
+  // near-ties: the exact FP64 cost of every band member, (cost, slot) minimum
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* tv = reinterpret_cast<float*>(smem_raw);    // n
+  int* deo = reinterpret_cast<int*>(tv + g.n);       // n
+  uint8_t* tm = reinterpret_cast<uint8_t*>(deo + g.n);  // P
+  const int64_t cx = a.centres[q * g.ndim + 0], cy = a.centres[q * g.ndim + 1];
+  const int64_t cz = g.ndim == 3 ? a.centres[q * g.ndim + 2] : 0;
+  stage_target(I, lin_of(g, cx, cy, cz), tv, deo, tm);
+  __syncthreads();
+  double bc = INFINITY;
+  int64_t bi = INT64_MAX;
+  for (int ci = tid; ci < nc; ci += kQThreads) {
+    if (c32[ci] <= T) {
+      const double c64 = exact_cost64(I.dgrid, (int64_t)I.dict[uc[ci]] * g.ch, tv, tm, deo, g.P, g.ch, a.weights,
+                                      a.l1 != 0);
+      if (c64 < bc || (c64 == bc && ci < bi)) {
+        bc = c64;
+        bi = ci;
+      }
+    }
+  }
+  warp_argmin64(bc, bi);
+  if (lane == 0) {
+    s_redd[warp] = bc;
+    s_redi[warp] = bi;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double c = s_redd[0];
+    int64_t i = s_redi[0];
+    for (int w = 1; w < kQWarps; ++w)
+      if (s_redd[w] < c || (s_redd[w] == c && s_redi[w] < i)) {
+        c = s_redd[w];
+        i = s_redi[w];
+      }
+    if (i == INT64_MAX) {
+      a.pick[q] = -1;
+      a.cost[q] = __int_as_float(0x7fc00000);
+    } else {
+      a.pick[q] = uc[i];
       a.cost[q] = c32[i];
     }
   }
@@ -800,24 +962,76 @@ int common_args(const Index& ix, int64_t maxN, QArgs& a) {
   a.imgs = nullptr;
   a.img_of = nullptr;
   a.nimg = 0;
+  a.c32_out = nullptr;
   a.status = status_word();
   return SFC_OK;
+}
+
+bool index_weighted(const Index& ix) {
+  bool weighted = false;
+  for (float w : ix.weights_h) weighted |= (w != 1.0f);
+  return weighted;
 }
 
 int launch_query(const Index& ix, const QArgs& a, int64_t Q, cudaStream_t st) {
   const size_t shm = (size_t)ix.g.n * 20 + (size_t)a.L * 12 + sizeof(float) * kQWarps * kXChunk * (1 + ix.D) +
                      (size_t)ix.g.P +
                      (ix.knn > 0 ? 16 + sizeof(KnnRegion) * kKnnStack * kQWarps : 0);
-  bool weighted = false;
-  for (float w : ix.weights_h) weighted |= (w != 1.0f);
-  return weighted ? dispatch_q<true>(a, Q, shm, st) : dispatch_q<false>(a, Q, shm, st);
+  return index_weighted(ix) ? dispatch_q<true>(a, Q, shm, st) : dispatch_q<false>(a, Q, shm, st);
+}
+
+template <int MAXE>
+void launch_qs_rescore(const QArgs& a, bool weighted, dim3 grd, size_t shm, cudaStream_t st) {
+  if (weighted)
+    a.l1 ? k_qs_rescore<MAXE, true, true><<<grd, kQThreads, shm, st>>>(a)
+         : k_qs_rescore<MAXE, true, false><<<grd, kQThreads, shm, st>>>(a);
+  else
+    a.l1 ? k_qs_rescore<MAXE, false, true><<<grd, kQThreads, shm, st>>>(a)
+         : k_qs_rescore<MAXE, false, false><<<grd, kQThreads, shm, st>>>(a);
+}
+
+// The split form (kernels above) of a batch of Q <= kQsMaxQ queries with
+// picks; cand / ncand / c32: Q * (C * capw), Q, Q * (C * capw) device words.
+int launch_query_split(const Index& ix, const QArgs& a, int64_t Q, int32_t* cand, int32_t* ncand, float* c32,
+                       cudaStream_t st) {
+  QArgs a1 = a;
+  a1.pick = nullptr;
+  a1.cost = nullptr;
+  a1.cand_out = cand;
+  a1.ncand_out = ncand;
+  SFC_CHECK(launch_query(ix, a1, Q, st));
+  QArgs a2 = a;
+  a2.qkeys = nullptr;
+  a2.pos = nullptr;
+  a2.cand_out = cand;
+  a2.ncand_out = ncand;
+  a2.c32_out = c32;
+  const int n = ix.g.n, P = ix.g.P, need = (n + 31) / 32;
+  const int cap = a.C * a.capw;
+  const dim3 grd((unsigned)((cap + kQsSlice - 1) / kQsSlice), (unsigned)Q);
+  const size_t shm_r = (size_t)n * 20 + (size_t)P;
+  const bool w = index_weighted(ix);
+  count_launch();
+  if (need <= 4) launch_qs_rescore<4>(a2, w, grd, shm_r, st);
+  else if (need <= 8) launch_qs_rescore<8>(a2, w, grd, shm_r, st);
+  else if (need <= 12) launch_qs_rescore<12>(a2, w, grd, shm_r, st);
+  else if (need <= 16) launch_qs_rescore<16>(a2, w, grd, shm_r, st);
+  else if (need <= 24) launch_qs_rescore<24>(a2, w, grd, shm_r, st);
+  else launch_qs_rescore<32>(a2, w, grd, shm_r, st);  // n <= 1024: checked by launch_query
+  SFC_TRY(cudaGetLastError());
+  count_launch();
+  k_qs_pick<<<(unsigned)Q, kQThreads, (size_t)n * 8 + (size_t)P, st>>>(a2);
+  SFC_TRY(cudaGetLastError());
+  return SFC_OK;
 }
 
 }  // namespace
 
+int64_t query_split_cap(const Index& ix) { return (int64_t)ix.C * (ix.knn > 0 ? ix.knn : ix.W); }
+
 int query_batch(const Index& ix, const float* grid, const uint8_t* cur_mask, const int32_t* centres, int64_t Q,
                 int64_t* pick, float* cost, uint64_t* qkeys, int64_t* pos, int32_t* cand, int32_t* ncand,
-                cudaStream_t st, const TargetGrid* tgt) {
+                cudaStream_t st, const TargetGrid* tgt, const QSplit* split) {
   if (Q <= 0) return SFC_OK;
   if (Q > 0x7fffffffLL) {
     set_error("too many queries in one batch");
@@ -833,6 +1047,25 @@ int query_batch(const Index& ix, const float* grid, const uint8_t* cur_mask, con
   a.pos = pos;
   a.cand_out = cand;
   a.ncand_out = ncand;
+  a.c32_out = nullptr;
+  if (pick && !cand && Q <= kQsMaxQ) {
+    // a small batch: the split form, in the caller's buffers or in stream-ordered
+    // scratch (not while the stream is being captured: then the one-CTA form)
+    const int64_t cap = (int64_t)a.C * a.capw;
+    if (split && split->cap >= cap && split->qmax >= Q)
+      return launch_query_split(ix, a, Q, split->cand, split->ncand, split->c32, st);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusActive;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+      Scratch scr(st);
+      int32_t *sc = nullptr, *sn = nullptr;
+      float* sf = nullptr;
+      SFC_TRY(scr.alloc(&sc, sizeof(int32_t) * Q * cap));
+      SFC_TRY(scr.alloc(&sn, sizeof(int32_t) * Q));
+      SFC_TRY(scr.alloc(&sf, sizeof(float) * Q * cap));
+      return launch_query_split(ix, a, Q, sc, sn, sf, st);
+    }
+    cudaGetLastError();
+  }
   return launch_query(ix, a, Q, st);
 }
 
