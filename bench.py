@@ -18,8 +18,9 @@ write) between timed steps, outside the timed interval.
 
 Also reported, outside the timed steps: the same step with the covariance over
 every dictionary entry ("pca_sample_all"), the fill loop run to completion on
-the workload ("inpaint_1024"), the 256^3 and 512^3 configurations ("volumes",
-skipped by --no-3d), and, on rank 0, the oracle timed on the host cores
+the workload ("inpaint_1024"), the parameter search over (C, D, W) against the
+acceleration-error bound ("autotune"), the 256^3 and 512^3 configurations
+("volumes", skipped by --no-3d), and, on rank 0, the oracle timed on the host cores
 ("cpu_baseline": one thread and all workers on a 256^2 tile, its full scan on
 sampled targets) together with the parity record of this run's results
 ("parity": the oracle's index rebuilt from the GPU's basis with its sorted
@@ -418,6 +419,30 @@ def batch_inputs():
     # a spawned pool: never forked from a process that has started CUDA
     with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1), mp_context=mp.get_context("spawn")) as ex:
         return list(ex.map(synth.batch_case, range(n), sizes, [BATCH["K"]] * n, [BATCH["cap"]] * n))
+
+
+def run_autotune(sfc, torch, gd, md, td):
+    """sfc_autotune on the headline workload: every (C, D, W) of a grid built
+    and queried through the public entry points (step time = build + all
+    front-target queries, median of 2), acceleration error (Sec. III.C) on 512
+    sampled targets against the full scan's exact picks; the fastest within
+    ae_max = 0.01, or, when none reaches it, the most accurate (the tuner's
+    rule)."""
+    ae_max = 0.01
+    curves, dims, windows = (4, 8, 16), (6, 8, 10), (64, 256, 512)
+    base = {k: WORKLOAD[k] for k in ("K", "bits", "pca_sample")}
+    t0 = time.perf_counter()
+    best, table, chosen = sfc.sfc_autotune(gd, md, td, curves=curves, dims=dims, windows=windows, sample=512,
+                                           reps=2, objective=sfc.SFC_TUNE_STEP, ae_max=ae_max, **base)
+    wall = time.perf_counter() - t0
+    rows = [{"curves": int(r[0]), "dims": int(r[1]), "window": int(r[2]), "step_ms": float(r[3]),
+             "acceleration_error": float(r[4])} for r in table]
+    within = [r for r in rows if r["acceleration_error"] <= ae_max]
+    return {"workload": "the headline image, mask and targets; grid C x D x W = "
+                        f"{list(curves)} x {list(dims)} x {list(windows)}, sample 512, objective build + query",
+            "ae_max": ae_max, "chosen": rows[chosen], "configs_within_ae_max": len(within),
+            "min_acceleration_error": min(r["acceleration_error"] for r in rows), "table": rows,
+            "tuner_seconds": wall, "status": sfc.sfc_status()}
 
 
 def run_batch(sfc, torch, dev, flush, stream):
@@ -1048,6 +1073,9 @@ def main():
     flog_h = flog.cpu().numpy()
     del gg, mm
 
+    # ---- the parameter search on the workload (acceleration error vs time) -----
+    tune = run_autotune(sfc, torch, gd, md, td)
+
     # ---- the 3-D configurations (256^3, 512^3): index build + front-target queries
     volumes = None if args.no_3d else run_volumes(sfc, torch, dev, flush, stream)
 
@@ -1120,7 +1148,7 @@ def main():
             "fullscan": fullscan, "sfc_knn": sfc_knn, "sfc_hilbert": sfc_hilbert, "sfc_l1": sfc_l1,
             "stored_index": stored, "inpaint_128x128": inp, "bf16_index": bf16,
             "batch_256": batch}
-    line.update({"pca_sample_all": pca_all, "inpaint_1024": fill_big, "volumes": volumes})
+    line.update({"pca_sample_all": pca_all, "inpaint_1024": fill_big, "volumes": volumes, "autotune": tune})
     if split is not None:
         line["fullscan_dict_split"] = split
     if rank == 0:

@@ -440,11 +440,18 @@ int32_t sfc_tune_select(int32_t n, const double* ms, const double* ae, double ae
  * every look-back polls a word nothing writes -- so every sort tile after the
  * first gives up, the sort's output is garbage and sfc_status() reports
  * SFC_ETIMEOUT (writes stay inside the output arrays; the GPU stays usable).
- * Reset with sfc_debug_lookback(0, 0). */
+ * Reset with sfc_debug_lookback(0, 0).
+ * sfc_debug_sort(force_lsd, bucket_cap): index builds with up to 2^20
+ * dictionary entries sort each index by a sample sort; force_lsd = 1 makes them
+ * take the LSD radix sort (the one the look-back hook above acts on), and
+ * bucket_cap in 1..4095 lowers the sample sort's bucket capacity so that an
+ * index whose largest bucket exceeds it is sorted again by the LSD sort (its
+ * fallback path).  Same sorted arrays either way.  Reset with (0, 0). */
 int sfc_debug_fail_alloc(int64_t n);
 int64_t sfc_debug_alloc_count(void);
 int sfc_debug_pool_used(uint64_t* bytes);
 int sfc_debug_lookback(int64_t spin_limit, int32_t stall);
+int sfc_debug_sort(int32_t force_lsd, int32_t bucket_cap);
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char* sfc_last_error(void);

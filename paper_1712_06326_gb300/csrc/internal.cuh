@@ -177,6 +177,18 @@ size_t radix_sort_scratch_bytes(int64_t N, int C, int key_bits);
 // default kSpinLimit) and, with stall = 1, look-backs that poll a word nothing
 // writes, so every tile after the first gives up after spin_limit polls.
 void sort_lookback_test(long long spin_limit, int stall);
+// k_sort.cu: sample sort of (key, id) per index for N <= 2^20 (the same order
+// as the LSD sort).  ovf: C device ints, set to 1 for an index whose pairs were
+// not sorted (a bucket above the shared-memory capacity): the caller sorts
+// that index with radix_sort_pairs.  scratch as for radix_sort_pairs.
+bool sample_sort_fits(int64_t N);
+int sample_sort_pairs(const uint64_t* keys, uint64_t* skeys, uint32_t* sids, int64_t N, int C, int* ovf,
+                      cudaStream_t st, void* scratch = nullptr);
+size_t sample_sort_scratch_bytes(int64_t N, int C);
+// Tests: force the LSD sort (force_lsd = 1), or lower the bucket capacity
+// (cap > 0) so that indices overflow and take the LSD sort after the sample
+// sort; (0, 0) restores the defaults.
+void sample_sort_test(int force_lsd, int cap);
 
 // k_query.cu
 // Targets on a grid other than the index's: its geometry, its patch element

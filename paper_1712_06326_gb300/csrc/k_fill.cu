@@ -90,8 +90,20 @@ __device__ void prio_one(const Geo& g, const float* __restrict__ grid, const uin
     key[c] = 0ull;
     return;
   }
+  // the confidence sum in raster order, a patch row at a time (the row's loads
+  // are independent of the running sum, so they are issued ahead of it)
   float sum = 0.0f;
-  for (int pp = 0; pp < g.P; ++pp) sum = __fadd_rn(sum, conf[c + patch_off(g, pp)]);
+  const int K = g.K, nz = g.ndim == 3 ? K : 1;
+  for (int dz = 0; dz < nz; ++dz)
+    for (int dy = 0; dy < K; ++dy) {
+      const float* row = conf + c + ((int64_t)(g.ndim == 3 ? dz - g.r : 0) * g.Y + (dy - g.r)) * g.X - g.r;
+      int dx = 0;
+      for (; dx + 4 <= K; dx += 4) {
+        const float a0 = row[dx], a1 = row[dx + 1], a2 = row[dx + 2], a3 = row[dx + 3];
+        sum = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(sum, a0), a1), a2), a3);
+      }
+      for (; dx < K; ++dx) sum = __fadd_rn(sum, row[dx]);
+    }
   const float Ct = __fdiv_rn(sum, (float)g.P);
   float P = Ct;
   if (prio == SFC_PRIO_CRIMINISI) {

@@ -461,15 +461,23 @@ int dev_in(FileIn& in, T** d, size_t count, cudaStream_t st) {
 // the groups' projections and keys run in order on a high-priority library
 // stream, and each group's sort on one of the library's default-priority
 // streams as soon as its keys exist, so the sorts (latency-bound) fill the SMs
-// around the projections (issue-bound) without holding them up.  Phase 5 of
+// around the projections (issue-bound) without holding them up.  With the
+// sample sort (ss) there is one group: the sort follows the projections.  Phase 5 of
 // the trace is marked once every group's keys exist, phase 6 (by the caller)
 // once every sort is done.  st waits for all of it, also on an error, so
 // nothing the caller frees next is still in use.
-int project_sort_pipelined(Index& ix, const float* grid, float* proj, uint64_t* keys, uint32_t* lohi,
-                           cudaStream_t st) {
+int project_sort_pipelined(Index& ix, const float* grid, float* proj, uint64_t* keys, uint32_t* lohi, int* ovf,
+                           bool ss, cudaStream_t st) {
   const int C = ix.C;
   const int64_t N = ix.N;
   const int key_bits = std::min(64, ix.D * ix.bp);
+  // the sort of curves [c0, c0 + nc): the sample sort (ss) or the LSD sort
+  auto sort_group = [&](int c0, int nc, cudaStream_t s, void* ws) -> int {
+    return ss ? sample_sort_pairs(keys + (size_t)c0 * N, ix.skeys + (size_t)c0 * N, ix.sids + (size_t)c0 * N, N,
+                                  nc, ovf + c0, s, ws)
+              : radix_sort_pairs(keys + (size_t)c0 * N, ix.skeys + (size_t)c0 * N, ix.sids + (size_t)c0 * N, N, nc,
+                                 key_bits, s, ws);
+  };
   cudaStream_t hi = aux_stream_hi();
   cudaStream_t lo[kAuxStreams];
   int nlo = 0;
@@ -481,15 +489,20 @@ int project_sort_pipelined(Index& ix, const float* grid, float* proj, uint64_t* 
       SFC_CHECK(project_curves(ix, grid, proj, lohi, 0, C, st));
     SFC_CHECK(key_curves(ix, proj, keys, 0, C, st));
     trace_mark(ix, 5, st);
-    return radix_sort_pairs(keys, ix.skeys, ix.sids, N, C, key_bits, st);
+    return sort_group(0, C, st, nullptr);
   }
+  // groups of curves: the sample sort gains more from sorting every curve in
+  // one set of launches than from overlapping smaller sorts with the
+  // projections (1,024² workload: step 3.52 ms with one group, 3.55 with two,
+  // 3.57 with four); the LSD sort of larger dictionaries overlaps, in four
   constexpr int kGroups = 4;
   int G = C < kGroups ? C : kGroups;
+  if (ss) G = 1;
   const int per = (C + G - 1) / G;
   G = (C + per - 1) / per;
   // every group's sort scratch is taken on st before the fork and returned
   // after the join, so no memory moves between the streams' pool queues
-  const size_t ws_bytes = radix_sort_scratch_bytes(N, per, key_bits);
+  const size_t ws_bytes = ss ? sample_sort_scratch_bytes(N, per) : radix_sort_scratch_bytes(N, per, key_bits);
   unsigned char* ws = nullptr;
   SFC_TRY(pmalloc(&ws, ws_bytes * G, st));
   cudaEvent_t ev_fork = nullptr, ev_hi = nullptr, ev_keys[kGroups] = {}, ev_done[kGroups] = {};
@@ -527,8 +540,7 @@ int project_sort_pipelined(Index& ix, const float* grid, float* proj, uint64_t* 
       rc = SFC_ECUDA;
       break;
     }
-    rc = radix_sort_pairs(keys + (size_t)c0 * N, ix.skeys + (size_t)c0 * N, ix.sids + (size_t)c0 * N, N, nc,
-                          key_bits, s, ws + ws_bytes * g);
+    rc = sort_group(c0, nc, s, ws + ws_bytes * g);
     if (cudaEventRecord(ev_done[g], s) == cudaSuccess)
       sorted = g + 1;
     else if (rc == SFC_OK)
@@ -672,12 +684,30 @@ int build_index(const float* grid, const uint8_t* dict_mask, const sfc_grid* gp,
   float* proj = nullptr;
   uint64_t* keys = nullptr;
   uint32_t* lohi = nullptr;
+  int* ovf = nullptr;
+  std::vector<int> done(C, 1);
   {
     Scratch scr(st);
     SFC_TRY(scr.alloc(&proj, (ix.bf16 ? 2 : sizeof(float)) * C * N * D));
     SFC_TRY(scr.alloc(&keys, sizeof(uint64_t) * C * N));
     SFC_TRY(scr.alloc(&lohi, sizeof(uint32_t) * 2 * C * D));
-    SFC_CHECK(project_sort_pipelined(ix, grid, proj, keys, lohi, st));
+    SFC_TRY(scr.alloc(&ovf, sizeof(int) * C));
+    SFC_TRY(cudaMemsetAsync(ovf, 0, sizeof(int) * C, st));
+    const bool ss = sample_sort_fits(N);
+    SFC_CHECK(project_sort_pipelined(ix, grid, proj, keys, lohi, ovf, ss, st));
+    // one wait for the flags: the eigen-solves' convergence and the indices the
+    // sample sort left to the LSD sort (sorted now, from the keys)
+    if (ss || ix.pca_done) {
+      std::vector<int> ov(C, 0);
+      if (ss) SFC_TRY(cudaMemcpyAsync(ov.data(), ovf, sizeof(int) * C, cudaMemcpyDeviceToHost, st));
+      if (ix.pca_done) SFC_TRY(cudaMemcpyAsync(done.data(), ix.pca_done, sizeof(int) * C, cudaMemcpyDeviceToHost, st));
+      SFC_TRY(cudaStreamSynchronize(st));
+      const int key_bits = std::min(64, ix.D * ix.bp);
+      for (int c = 0; c < C; ++c)
+        if (ov[c])
+          SFC_CHECK(radix_sort_pairs(keys + (size_t)c * N, ix.skeys + (size_t)c * N, ix.sids + (size_t)c * N, N, 1,
+                                     key_bits, st));
+    }
     if (ix.knn > 0) SFC_CHECK(sorted_coords(ix, proj, st));
     trace_mark(ix, 6, st);
     if (ix.keep) {
@@ -689,10 +719,7 @@ int build_index(const float* grid, const uint8_t* dict_mask, const sfc_grid* gp,
   }
   SFC_TRY(cudaGetLastError());
   if (ix.pca_done) {
-    // every eigen-solve must have converged: wait for the build, then read the flags
-    std::vector<int> done(C, 0);
-    SFC_TRY(cudaMemcpyAsync(done.data(), ix.pca_done, sizeof(int) * C, cudaMemcpyDeviceToHost, st));
-    SFC_TRY(cudaStreamSynchronize(st));
+    // every eigen-solve must have converged (flags read above)
     for (int c = 0; c < C; ++c)
       if (!done[c]) {
         set_error("the PCA eigen-solve of index " + std::to_string(c) + " (subset length " + std::to_string(s) +
@@ -1328,6 +1355,11 @@ int sfc_debug_pool_used(uint64_t* bytes) {
 
 int sfc_debug_lookback(int64_t spin_limit, int32_t stall) {
   sort_lookback_test(spin_limit, stall);
+  return SFC_OK;
+}
+
+int sfc_debug_sort(int32_t force_lsd, int32_t bucket_cap) {
+  sample_sort_test(force_lsd, bucket_cap);
   return SFC_OK;
 }
 

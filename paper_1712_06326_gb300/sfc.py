@@ -31,7 +31,7 @@ EXPORTS = ["sfc_params_default", "sfc_index_build", "sfc_index_destroy", "sfc_in
            "sfc_tc_prescores", "inpaint_run", "sfc_status", "sfc_launch_count", "sfc_trace", "sfc_trace_read", "sfc_trace_tc_read",
            "sfc_last_error", "sfc_index_save", "sfc_index_load", "sfc_index_params", "sfc_query_batch_dict",
            "sfc_multi_create", "sfc_multi_query", "sfc_multi_destroy", "sfc_autotune", "sfc_tune_select", "sfc_trace_eig_read",
-           "sfc_debug_fail_alloc", "sfc_debug_alloc_count", "sfc_debug_pool_used", "sfc_debug_lookback",
+           "sfc_debug_fail_alloc", "sfc_debug_alloc_count", "sfc_debug_pool_used", "sfc_debug_lookback", "sfc_debug_sort",
            "sfc_shard_create", "sfc_shard_range", "sfc_shard_scan", "sfc_shard_band", "sfc_shard_destroy",
            "sfc_trace_proj_read"]
 TRACE_PHASES = ("dictionary", "moments", "eigen", "finalize", "project_keys", "sort")
@@ -115,6 +115,8 @@ def lib():
         L.sfc_debug_pool_used.restype = C.c_int
         L.sfc_debug_lookback.argtypes = [i64, i32]
         L.sfc_debug_lookback.restype = C.c_int
+        L.sfc_debug_sort.argtypes = [i32, i32]
+        L.sfc_debug_sort.restype = C.c_int
         L.sfc_shard_create.argtypes = [vp, vp, vp, C.POINTER(sfc_grid), C.POINTER(sfc_params), vp, i64, i32, i32, vp,
                                        C.POINTER(vp)]
         L.sfc_shard_range.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
@@ -521,3 +523,9 @@ def sfc_debug_pool_used() -> int:
 def sfc_debug_lookback(spin_limit: int = 0, stall: bool = False) -> None:
     """Failure injection (tests): the radix sort's look-back poll limit and stall switch."""
     _check(lib().sfc_debug_lookback(int(spin_limit), 1 if stall else 0), "sfc_debug_lookback")
+
+
+def sfc_debug_sort(force_lsd: bool = False, bucket_cap: int = 0) -> None:
+    """Builds sort with the LSD radix sort (force_lsd), or the sample sort with
+    a lowered bucket capacity (its LSD fallback); (False, 0) resets."""
+    _check(lib().sfc_debug_sort(1 if force_lsd else 0, int(bucket_cap)), "sfc_debug_sort")

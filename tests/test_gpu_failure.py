@@ -34,6 +34,7 @@ def S():
     sfc.sfc_status()
     yield sfc
     sfc.sfc_debug_lookback(0, False)
+    sfc.sfc_debug_sort(False, 0)
     sfc.sfc_debug_fail_alloc(0)
 
 
@@ -60,6 +61,7 @@ def test_sort_lookback_timeout_is_reported_and_the_gpu_recovers(S):
     K, C_, D, bits, W = 9, 4, 6, 10, 32
     assert len(O.dict_extract(m, K)) > 8 * 3072  # several sort tiles per index
     assert S.sfc_status() == 0
+    S.sfc_debug_sort(True, 0)  # the LSD radix sort (dictionaries this small take the sample sort)
     S.sfc_debug_lookback(2000, True)
     try:
         ix = S.sfc_index_build(dev(g), dev(m), K=K, curves=C_, dims=D, bits=bits, window=W, pca_sample=0)
@@ -67,6 +69,7 @@ def test_sort_lookback_timeout_is_reported_and_the_gpu_recovers(S):
         ix.close()
     finally:
         S.sfc_debug_lookback(0, False)
+        S.sfc_debug_sort(False, 0)
     assert S.sfc_status() == 0  # read and cleared
     # the same context: a normal build sorts correctly and answers like the oracle
     check_queries_match_oracle(S, g, m, t, K, C_, D, bits, W)
