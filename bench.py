@@ -429,7 +429,7 @@ def run_autotune(sfc, torch, gd, md, td):
     ae_max = 0.01, or, when none reaches it, the most accurate (the tuner's
     rule)."""
     ae_max = 0.01
-    curves, dims, windows = (4, 8, 16), (6, 8, 10), (64, 256, 512)
+    curves, dims, windows = (4, 8), (6, 8, 10), (64, 256, 1024)  # 2-D indices: at most 8 curves
     base = {k: WORKLOAD[k] for k in ("K", "bits", "pca_sample")}
     t0 = time.perf_counter()
     best, table, chosen = sfc.sfc_autotune(gd, md, td, curves=curves, dims=dims, windows=windows, sample=512,

@@ -371,6 +371,7 @@ namespace {
 constexpr int kSsOver = 8;              // samples per bucket
 constexpr int kSsRun = 1024;            // sampled pairs per sorting CTA
 constexpr int kSsCap = 2048;            // pairs per bucket sorted in shared memory
+constexpr int kSsBucketE = 4;           // pairs per thread and chunk in the bucket sort
 constexpr int kSsTile = 256 * 16;       // pairs per CTA of the count / place passes
 constexpr int64_t kSsMaxN = 1ll << 20;  // larger dictionaries: the LSD sort
 std::atomic<int> g_ss_force_lsd{0};
@@ -434,13 +435,30 @@ __device__ __forceinline__ void sp_put(const SPairs& a, int i, uint64_t k, uint3
   a.id[p] = v;
 }
 
+// Batcher's odd-even merge network on E = 4 or 8 pairs in registers.
+template <int E>
+__device__ __forceinline__ void sort_net(uint64_t (&k)[E], uint32_t (&v)[E]) {
+#define CE(i, j) ce_pair(k[i], v[i], k[j], v[j])
+  if (E == 4) {
+    CE(0, 1); CE(2, 3); CE(0, 2); CE(1, 3); CE(1, 2);
+  } else {
+    CE(0, 1); CE(2, 3); CE(4, 5); CE(6, 7);
+    CE(0, 2); CE(1, 3); CE(4, 6); CE(5, 7);
+    CE(1, 2); CE(5, 6);
+    CE(0, 4); CE(1, 5); CE(2, 6); CE(3, 7);
+    CE(2, 4); CE(3, 5);
+    CE(1, 2); CE(3, 4); CE(5, 6);
+  }
+#undef CE
+}
+
 // Merge sort of n pairs by (key, id) in shared memory, by the whole CTA: runs
-// of 4 sorted in registers, then merge passes of doubling width, each thread
-// producing 4 outputs per chunk from its merge-path split (a binary search on
+// of E sorted in registers, then merge passes of doubling width, each thread
+// producing E outputs per chunk from its merge-path split (a binary search on
 // the output diagonal).  a holds the input; b is a second buffer.  Returns true
 // if the result is in b.  The pairs are distinct, so no tie rule is needed.
+template <int E>
 __device__ bool merge_sort_pairs(const SPairs& a, const SPairs& b, int n) {
-  constexpr int E = 4;
   const int T = blockDim.x;
   for (int o0 = threadIdx.x * E; o0 < n; o0 += T * E) {
     const int r = n - o0 < E ? n - o0 : E;
@@ -454,11 +472,7 @@ __device__ bool merge_sort_pairs(const SPairs& a, const SPairs& b, int n) {
         v[e] = ~0u;
       }
     }
-    ce_pair(k[0], v[0], k[1], v[1]);
-    ce_pair(k[2], v[2], k[3], v[3]);
-    ce_pair(k[0], v[0], k[2], v[2]);
-    ce_pair(k[1], v[1], k[3], v[3]);
-    ce_pair(k[1], v[1], k[2], v[2]);
+    sort_net<E>(k, v);
 #pragma unroll
     for (int e = 0; e < E; ++e)
       if (e < r) sp_put(a, o0 + e, k[e], v[e]);
@@ -524,7 +538,7 @@ __global__ void __launch_bounds__(256) k_ss_sample(const uint64_t* __restrict__ 
     sp_put(pa, t, k[j], (uint32_t)j);
   }
   __syncthreads();
-  const SPairs& r = merge_sort_pairs(pa, pb, n) ? pb : pa;
+  const SPairs& r = merge_sort_pairs<4>(pa, pb, n) ? pb : pa;
   for (int t = threadIdx.x; t < n; t += blockDim.x) {
     uint64_t kk;
     uint32_t vv;
@@ -716,7 +730,7 @@ __global__ void __launch_bounds__(256) k_ss_bucket(const uint64_t* __restrict__ 
   const SPairs pa = spairs(sm, M), pb = spairs(sm + 3 * sw_len(M), M);  // two buffers of the bucket
   for (int t = threadIdx.x; t < M; t += blockDim.x) sp_put(pa, t, tk[base + t], tv[base + t]);
   __syncthreads();
-  const SPairs& r = merge_sort_pairs(pa, pb, M) ? pb : pa;
+  const SPairs& r = merge_sort_pairs<kSsBucketE>(pa, pb, M) ? pb : pa;
   for (int t = threadIdx.x; t < M; t += blockDim.x) {
     uint64_t kk;
     uint32_t vv;
