@@ -18,7 +18,8 @@ write) between timed steps, outside the timed interval.
 
 Also reported, outside the timed steps: the same step with the covariance over
 every dictionary entry ("pca_sample_all"), the fill loop run to completion on
-the workload ("inpaint_1024"), the parameter search over (C, D, W) against the
+the workload ("inpaint_1024"), the fill loops of 16 images one by one and all at
+once ("inpaint_multi"), the parameter search over (C, D, W) against the
 acceleration-error bound ("autotune"), the 256^3 and 512^3 configurations
 ("volumes", skipped by --no-3d), and, on rank 0, the oracle timed on the host cores
 ("cpu_baseline": one thread and all workers on a 256^2 tile, its full scan on
@@ -443,6 +444,43 @@ def run_autotune(sfc, torch, gd, md, td):
             "ae_max": ae_max, "chosen": rows[chosen], "configs_within_ae_max": len(within),
             "min_acceleration_error": min(r["acceleration_error"] for r in rows), "table": rows,
             "tuner_seconds": wall, "status": sfc.sfc_status()}
+
+
+def run_fill_multi(sfc, torch, dev):
+    """The fill loops of 16 images (512^2 voronoi2d, the headline's index
+    parameters, SFC mode, to completion): one inpaint_run per image against
+    one inpaint_run_multi for all of them (every round one step of every image;
+    the same results, checked here image by image)."""
+    from paper_1712_06326_gb300 import synth
+
+    n = 16
+    imgs = [synth.voronoi2d(512, cfg=2, seed_sub=100 + i) for i in range(n)]
+    prm = {k: WORKLOAD[k] for k in ("K", "curves", "dims", "bits", "window", "pca_sample")}
+    res = {}
+    for rep in range(2):  # the first pass warms up both paths
+        gs = [torch.from_numpy(g).to(dev) for g, _ in imgs]
+        ms = [torch.from_numpy(m).to(dev) for _, m in imgs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        one = [sfc.inpaint_run(g_, m_, mode=sfc.SFC_MODE_SFC, **prm) for g_, m_ in zip(gs, ms)]
+        torch.cuda.synchronize()
+        t_one = time.perf_counter() - t0
+        gm = [torch.from_numpy(g).to(dev) for g, _ in imgs]
+        mm = [torch.from_numpy(m).to(dev) for _, m in imgs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps, logs = sfc.inpaint_run_multi(gm, mm, **prm)
+        torch.cuda.synchronize()
+        t_multi = time.perf_counter() - t0
+        same = all(torch.equal(a, b) and torch.equal(c, d) and s1 == s2 and torch.equal(l1, l2)
+                   for a, b, c, d, s1, s2, l1, l2 in zip(gs, gm, ms, mm, [o[0] for o in one], steps,
+                                                         [o[1] for o in one], logs))
+        res = {"workload": f"{n} voronoi2d 512x512 RGB images (10% disc holes), the headline's index parameters, "
+                           "SFC mode, each filled to completion (index build included)",
+               "images": n, "steps_total": int(sum(steps)), "max_steps_one_image": int(max(steps)),
+               "one_by_one_s": t_one, "multi_s": t_multi, "speedup": t_one / t_multi,
+               "results_equal": bool(same), "status": sfc.sfc_status()}
+    return res
 
 
 def run_batch(sfc, torch, dev, flush, stream):
@@ -1076,6 +1114,9 @@ def main():
     # ---- the parameter search on the workload (acceleration error vs time) -----
     tune = run_autotune(sfc, torch, gd, md, td)
 
+    # ---- the fill loops of many images at once --------------------------------
+    fill_multi = run_fill_multi(sfc, torch, dev)
+
     # ---- the 3-D configurations (256^3, 512^3): index build + front-target queries
     volumes = None if args.no_3d else run_volumes(sfc, torch, dev, flush, stream)
 
@@ -1148,7 +1189,8 @@ def main():
             "fullscan": fullscan, "sfc_knn": sfc_knn, "sfc_hilbert": sfc_hilbert, "sfc_l1": sfc_l1,
             "stored_index": stored, "inpaint_128x128": inp, "bf16_index": bf16,
             "batch_256": batch}
-    line.update({"pca_sample_all": pca_all, "inpaint_1024": fill_big, "volumes": volumes, "autotune": tune})
+    line.update({"pca_sample_all": pca_all, "inpaint_1024": fill_big, "volumes": volumes, "autotune": tune,
+                 "inpaint_multi": fill_multi})
     if split is not None:
         line["fullscan_dict_split"] = split
     if rank == 0:

@@ -330,6 +330,20 @@ int sfc_shard_destroy(sfc_shard* s);
 int inpaint_run(float* grid, uint8_t* mask, const sfc_grid* g, const sfc_params* p, int32_t mode, int64_t max_steps,
                 int64_t* log, int64_t* steps_done, void* stream);
 
+/* The inpainting loop of n images at once (the batched configuration; the
+ * paper runs one image at a time): each image gets the index of its initial
+ * image (sfc_index_build with p, SFC mode, knn = 0), then every round takes one
+ * step of every image whose loop is not done -- priorities, target, one
+ * multi-image query launch for all images, insert -- until every image is done
+ * or has max_steps (> 0) steps.  Each image ends exactly as inpaint_run(mode =
+ * SFC_MODE_SFC) leaves it: same grid, mask and log.  grids, masks, logs: HOST
+ * arrays of n DEVICE pointers (logs: NULL, or each image's log as for
+ * inpaint_run); gs: host array of n grids (same dimension and channels, any
+ * extents); steps_done: host int64[n].  SFC_EUNSUPPORTED for knn > 0.
+ * Synchronises `stream`. */
+int inpaint_run_multi(float* const* grids, uint8_t* const* masks, const sfc_grid* gs, int32_t n, const sfc_params* p,
+                      int64_t max_steps, int64_t* const* logs, int64_t* steps_done, void* stream);
+
 /* Read and clear the library's device-side status flags (synchronises stream):
  * SFC_OK, SFC_ETIMEOUT (a bounded wait gave up), or SFC_EDEVICE (an invalid
  * centre was seen, or a fill step made no progress). */

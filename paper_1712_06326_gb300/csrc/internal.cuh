@@ -221,8 +221,15 @@ struct MultiQuery;
 int multi_query_create(const Index* const* ixs, const float* const* grids, const uint8_t* const* masks, int n,
                        cudaStream_t st, MultiQuery** out);
 void multi_query_destroy(MultiQuery* m);
+// split: buffers for the split form (used when Q <= 32 and they are large enough).
 int multi_query_run(const MultiQuery* m, const int32_t* img_of, const int32_t* centres, int64_t Q, int64_t* pick,
-                    float* cost, cudaStream_t st);
+                    float* cost, cudaStream_t st, const QSplit* split = nullptr);
+// k_fill.cu: the fill loops of n images in SFC mode, every round one step of
+// every image not done (ixs: each image's index of its initial image, built
+// with the same parameters; grids / masks: device, updated in place; logs:
+// NULL or n device logs; steps_done: host int64[n]).  Synchronises st.
+int fill_loop_multi(const Index* const* ixs, float* const* grids, uint8_t* const* masks, int n, int prio,
+                    int64_t max_steps, int64_t* const* logs, int64_t* steps_done, cudaStream_t st);
 
 // k_fullscan.cu
 // cm (cost mode): bit 0 = channel weights other than 1, bit 1 = L1 norm (Sec. III.K).

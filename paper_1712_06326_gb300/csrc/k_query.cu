@@ -754,7 +754,7 @@ __global__ void __launch_bounds__(kQThreads) k_qs_rescore(QArgs a) {
   const int nc = a.ncand_out[q];  // 0: invalid centre
   const int c0 = blockIdx.x * kQsSlice;
   if (c0 >= nc) return;
-  const QImg& I = a.img;
+  const QImg& I = a.imgs ? a.imgs[a.img_of[q]] : a.img;  // nc > 0: a valid image
   const Geo& g = I.g;
   const int n = g.n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -790,7 +790,7 @@ __global__ void __launch_bounds__(kQThreads) k_qs_pick(QArgs a) {
     }
     return;
   }
-  const QImg& I = a.img;
+  const QImg& I = a.imgs ? a.imgs[a.img_of[q]] : a.img;  // nc > 0: a valid image
   const Geo& g = I.g;
   const float* c32 = a.c32_out + q * cap;
   const uint32_t* uc = reinterpret_cast<const uint32_t*>(a.cand_out) + q * cap;
@@ -1135,7 +1135,7 @@ void multi_query_destroy(MultiQuery* m) {
 }
 
 int multi_query_run(const MultiQuery* m, const int32_t* img_of, const int32_t* centres, int64_t Q, int64_t* pick,
-                    float* cost, cudaStream_t st) {
+                    float* cost, cudaStream_t st, const QSplit* split) {
   if (Q <= 0) return SFC_OK;
   if (Q > 0x7fffffffLL) {
     set_error("too many queries in one batch");
@@ -1154,6 +1154,10 @@ int multi_query_run(const MultiQuery* m, const int32_t* img_of, const int32_t* c
   a.pos = nullptr;
   a.cand_out = nullptr;
   a.ncand_out = nullptr;
+  // the split form only in the caller's buffers (the public entry point is one
+  // launch with no allocation)
+  if (split && Q <= kQsMaxQ && split->cap >= (int64_t)a.C * a.capw && split->qmax >= Q)
+    return launch_query_split(*m->first, a, Q, split->cand, split->ncand, split->c32, st);
   return launch_query(*m->first, a, Q, st);
 }
 

@@ -1327,6 +1327,59 @@ int inpaint_run(float* grid, uint8_t* mask, const sfc_grid* gp, const sfc_params
   return rc;
 }
 
+int inpaint_run_multi(float* const* grids, uint8_t* const* masks, const sfc_grid* gs, int32_t n, const sfc_params* p,
+                      int64_t max_steps, int64_t* const* logs, int64_t* steps_done, void* stream) {
+  g_err.clear();
+  if (n < 1 || !grids || !masks || !gs || !p || !steps_done) {
+    set_error("inpaint_run_multi: NULL pointer or n < 1");
+    return SFC_EINVAL;
+  }
+  for (int i = 0; i < n; ++i) {
+    steps_done[i] = 0;
+    if (!grids[i] || !masks[i]) {
+      set_error("inpaint_run_multi: NULL grid or mask of image " + std::to_string(i));
+      return SFC_EINVAL;
+    }
+  }
+  SFC_CHECK(check_device());
+  if (p->priority != SFC_PRIO_CONFIDENCE && p->priority != SFC_PRIO_CRIMINISI) {
+    set_error("inpaint_run_multi: unknown priority");
+    return SFC_EINVAL;
+  }
+  if (p->priority == SFC_PRIO_CRIMINISI && gs[0].ndim != 2) {
+    set_error("inpaint_run_multi: the Criminisi priority is defined for 2-D grids");
+    return SFC_EINVAL;
+  }
+  if (p->knn > 0) {
+    set_error("inpaint_run_multi: the multi-image search runs the window search (knn = 0)");
+    return SFC_EUNSUPPORTED;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // every image's index of its initial image (released on every return)
+  std::vector<Index> ixs(n);
+  struct Free {
+    std::vector<Index>& v;
+    int built = 0;
+    ~Free() {
+      for (int i = 0; i < built; ++i) free_index(v[i]);
+    }
+  } fr{ixs};
+  for (int i = 0; i < n; ++i) {
+    if (gs[i].ndim != gs[0].ndim || gs[i].ch != gs[0].ch) {
+      set_error("inpaint_run_multi: every image needs image 0's dimension and channel count");
+      return SFC_EINVAL;
+    }
+    const int rc = build_index(grids[i], masks[i], &gs[i], p, st, ixs[i]);
+    fr.built = i + 1;
+    if (rc != SFC_OK) return rc;
+  }
+  std::vector<const Index*> ptr(n);
+  for (int i = 0; i < n; ++i) ptr[i] = &ixs[i];
+  const int rc = fill_loop_multi(ptr.data(), grids, masks, n, p->priority, max_steps, logs, steps_done, st);
+  cudaStreamSynchronize(st);
+  return rc;
+}
+
 int sfc_debug_fail_alloc(int64_t n) {
   g_fail_alloc.store(n > 0 ? n : 0);
   return SFC_OK;

@@ -33,7 +33,7 @@ EXPORTS = ["sfc_params_default", "sfc_index_build", "sfc_index_destroy", "sfc_in
            "sfc_multi_create", "sfc_multi_query", "sfc_multi_destroy", "sfc_autotune", "sfc_tune_select", "sfc_trace_eig_read",
            "sfc_debug_fail_alloc", "sfc_debug_alloc_count", "sfc_debug_pool_used", "sfc_debug_lookback", "sfc_debug_sort",
            "sfc_shard_create", "sfc_shard_range", "sfc_shard_scan", "sfc_shard_band", "sfc_shard_destroy",
-           "sfc_trace_proj_read"]
+           "sfc_trace_proj_read", "inpaint_run_multi"]
 TRACE_PHASES = ("dictionary", "moments", "eigen", "finalize", "project_keys", "sort")
 
 
@@ -89,6 +89,8 @@ def lib():
                                        C.POINTER(i64), vp]
         L.inpaint_run.argtypes = [vp, vp, C.POINTER(sfc_grid), C.POINTER(sfc_params), i32, i64, vp,
                                   C.POINTER(i64), vp]
+        L.inpaint_run_multi.argtypes = [vp, vp, vp, i32, C.POINTER(sfc_params), i64, vp, vp, vp]
+        L.inpaint_run_multi.restype = C.c_int
         L.sfc_autotune.argtypes = [vp, vp, C.POINTER(sfc_grid), C.POINTER(sfc_params), vp, i64,
                                    C.POINTER(sfc_tune_spec), C.POINTER(sfc_params), vp, C.POINTER(i32), vp]
         L.sfc_tune_select.argtypes = [i32, vp, vp, C.c_double]
@@ -457,6 +459,32 @@ def inpaint_run(grid: torch.Tensor, mask: torch.Tensor, mode: int = SFC_MODE_FUL
                              C.byref(steps), _stream()), "inpaint_run")
     n = steps.value
     return n, (lg[:n] if lg is not None else None)
+
+
+def inpaint_run_multi(grids, masks, max_steps: int = 0, log: bool = True, **params):
+    """The fill loops of several images at once (SFC mode), in place on the
+    (device) grids and masks.  -> (steps per image, logs: list of int64
+    [steps, ndim+1] or None)."""
+    n = len(grids)
+    assert n == len(masks) and n >= 1
+    for g_, m_ in zip(grids, masks):
+        assert g_.is_cuda and m_.is_cuda and g_.is_contiguous() and m_.is_contiguous()
+        assert g_.dtype == torch.float32 and m_.dtype == torch.uint8
+    P = Params(**params)
+    gs = (sfc_grid * n)(*[make_grid(g_) for g_ in grids])
+    logs = []
+    for g_, m_ in zip(grids, masks):
+        unknown = int((m_ == 0).sum().item())
+        cap = unknown if max_steps <= 0 else max_steps
+        nd = gs[0].ndim
+        logs.append(torch.zeros((max(cap, 1), nd + 1), dtype=torch.int64, device=g_.device) if log else None)
+    gp = (C.c_void_p * n)(*[_ptr(g_) for g_ in grids])
+    mp = (C.c_void_p * n)(*[_ptr(m_) for m_ in masks])
+    lp = (C.c_void_p * n)(*[_ptr(l_) for l_ in logs]) if log else None
+    steps = np.zeros(n, np.int64)
+    _check(lib().inpaint_run_multi(gp, mp, gs, n, C.byref(P.p), max_steps, lp, steps.ctypes.data_as(C.c_void_p),
+                                   _stream()), "inpaint_run_multi")
+    return steps.tolist(), ([l_[:k] for l_, k in zip(logs, steps)] if log else None)
 
 
 def sfc_launch_count() -> int:
