@@ -896,6 +896,8 @@ def main():
     fs_q = 2048
     sel = torch.from_numpy(np.sort(np.random.default_rng(5).choice(Q, fs_q, replace=False))).to(dev)
     tsub = td[sel].contiguous()
+    # the scan's tile shape, tuned on 256 of these queries (same picks for every shape)
+    tile_table, tile_chosen = sfc.sfc_tune_tiles(gd, md, md, tsub[:256].contiguous(), reps=2, K=WORKLOAD["K"])
     fs_ms = []
     for r in range(3):
         flush.fill_(1.0)
@@ -924,7 +926,12 @@ def main():
                 "fp32_tflops_algorithmic": fs_tf, "fp32_frac_of_derived_peak": fs_tf / FP32_PEAK_TFLOPS,
                 "fp32_tflops_executed": fs_flops_exec / (statistics.mean(fs_ms) / 1000.0) / 1e12,
                 "fp32_peak_source": f"derived: {FP32_PEAK_TFLOPS} TFLOP/s from the unit counts and the 2.07 GHz "
-                                    "clock (no measured FP32 peak)"}
+                                    "clock (no measured FP32 peak)",
+                "tile_shapes": {"tuned_on": "256 of the queries, median of 2 timed calls per shape",
+                                "table": [{"queries_per_tile": int(r_[0]), "entries_per_thread": int(r_[1]),
+                                           "ms": float(r_[2])} for r_ in tile_table],
+                                "chosen": {"queries_per_tile": int(tile_table[tile_chosen][0]),
+                                           "entries_per_thread": int(tile_table[tile_chosen][1])}}}
 
     # ---- the same full scan with the tensor-core pre-score (SFC_FP16) ---------
     tc_ms = []

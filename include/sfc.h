@@ -123,11 +123,14 @@ void sfc_params_default(sfc_params* p);
  * of Fig. 2, a PCA per index (covariance of a deterministic sample accumulated to FP64
  * accuracy, leading eigenvectors by FP64 subspace iteration) unless p->basis is
  * given, FP32 projection, per-axis
- * quantisation to b bits, Morton keys (top 64 bits), and a stable radix sort of
- * (key, id) per index.  grid/dict_mask: device, layout above.  On success *out
- * owns device memory until sfc_index_destroy.  Synchronises `stream` once to
- * learn the dictionary size and, when it computes the PCA, once more at the
- * end to confirm that every eigen-solve converged.  Subsets of up to 64 values
+ * quantisation to b bits, Morton keys (top 64 bits), and a sort of (key, id)
+ * per index in key order, ties by id (a sample sort for up to 2^20 dictionary
+ * entries, an LSD radix sort above).  grid/dict_mask: device, layout above.  On
+ * success *out owns device memory until sfc_index_destroy.  Synchronises
+ * `stream` once to learn the dictionary size and, when it computes the PCA or
+ * takes the sample sort, once more near the end to read the eigen-solves'
+ * convergence and the sort's flags (an index whose sample sort overflowed a
+ * bucket is sorted again by the radix sort).  Subsets of up to 64 values
  * are solved completely by FP64 Jacobi; longer ones by subspace iteration,
  * taken over by Jacobi (up to 112 values) where the iteration stalls.
  * SFC_EINVAL if the dictionary is empty; SFC_ENOCONV (no index is returned) if
@@ -438,6 +441,25 @@ int sfc_autotune(const float* grid, const uint8_t* mask, const sfc_grid* g, cons
  * device work): returns the chosen position in 0..n-1, or -1 if n <= 0 or a
  * pointer is NULL.  NaN measurements count as +infinity. */
 int32_t sfc_tune_select(int32_t n, const double* ms, const double* ae, double ae_max);
+
+/* Tile shapes of the FP32 full scan (the paper's full scan is a CPU loop; the
+ * shapes are this library's): the scan has compiled variants of (queries per
+ * CTA tile, dictionary entries per thread) -- (8, 4), (8, 2), (16, 2), (4, 4),
+ * (4, 8), (16, 4), (32, 2) -- that compute the same FP32 cost of every (query, entry) pair and
+ * so give the same picks and costs.  sfc_tune_tiles times fullscan_query_batch
+ * (precision SFC_FP32; same arguments as there) with each shape (median of
+ * reps timed calls after one untimed, CUDA events on `stream`), checks that
+ * every shape returns shape 0's picks and cost bits (SFC_EDEVICE if not), and
+ * makes the fastest the shape of every later FP32 full scan in this process.
+ * table: HOST double [7][3] (queries per tile, entries per thread, ms) or NULL;
+ * chosen: the shape taken, or NULL.  sfc_tile_shape(shape) sets the shape
+ * (0..6; any other value only reads it) and returns the one in use.
+ * fullscan_query_batch_static always takes shape 0 (its scratch is sized for
+ * it). */
+int sfc_tune_tiles(const float* grid, const uint8_t* dict_mask, const uint8_t* cur_mask, const sfc_grid* g,
+                   const sfc_params* p, const int32_t* centres, int64_t Q, int32_t reps, double* table,
+                   int32_t* chosen, void* stream);
+int32_t sfc_tile_shape(int32_t shape);
 
 /* ---- Failure injection for tests ------------------------------------------
  * The paper has no counterpart: these hooks let tests drive the library's

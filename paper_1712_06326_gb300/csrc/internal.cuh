@@ -236,6 +236,12 @@ int fill_loop_multi(const Index* const* ixs, float* const* grids, uint8_t* const
 int fullscan_batch(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
                    const int* eoff_all, const float* weights, int cm, const int32_t* centres,
                    const int64_t* centre_lin, int64_t Q, int64_t* pick, float* cost, cudaStream_t st);
+// The FP32 scan's tile shapes: their number, with (queries per tile, entries
+// per thread) into qt / ept (either may be NULL; arrays of at least 8).
+int fullscan_tile_shapes(int* qt, int* ept);
+// The shape fullscan_batch uses (process-wide): shape in range sets it; returns
+// the one in use.
+int fullscan_tile_shape(int shape);
 
 int fullscan_batch_tc(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
                       const int* eoff_all, const float* weights, bool weighted, const int32_t* centres, int64_t Q,

@@ -15,6 +15,8 @@
 // sequential cost and the argmin over (cost, id) taken.  The reported cost is
 // the FP32 cost of the pick.  Costs are non-negative, so float bit patterns order
 // like their values.
+#include <atomic>
+
 #include "internal.cuh"
 
 namespace sfc {
@@ -762,12 +764,24 @@ int tc_prescores_all(const Geo& g, const float* grid, const uint8_t* cur_mask, c
   return SFC_OK;
 }
 
-int fullscan_batch(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
+// Tile shapes of the FP32 scan (queries per CTA tile, dictionary entries per
+// thread): every shape computes the same FP32 cost of every (query, entry) pair
+// (the sum over the patch elements in order) and the same band, so the picks
+// and costs do not depend on it; the fastest one for a workload is found by
+// measurement (sfc_tune_tiles) and kept for the process.
+namespace {
+struct FsShape {
+  int qt, ept;
+};
+constexpr FsShape kFsShapes[] = {{8, 4}, {8, 2}, {16, 2}, {4, 4}, {4, 8}, {16, 4}, {32, 2}};
+constexpr int kFsNShapes = sizeof(kFsShapes) / sizeof(kFsShapes[0]);
+std::atomic<int> g_fs_shape{0};
+
+template <int QT, int EPT>
+int fullscan_shape(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
                    const int* eoff_all, const float* weights, int cm, const int32_t* centres,
                    const int64_t* centre_lin, int64_t Q, int64_t* pick, float* cost, cudaStream_t st) {
-  if (Q <= 0) return SFC_OK;
   Scratch scr(st);  // freed on every return
-  constexpr int EPT = 4;
   const int64_t ntiles = (N + kFsThreads * EPT - 1) / (kFsThreads * EPT);
   int64_t* lin = nullptr;
   uint8_t* bad = nullptr;
@@ -776,30 +790,56 @@ int fullscan_batch(const Geo& g, const float* grid, const uint8_t* cur_mask, con
   SFC_TRY(scr.alloc(&tilemin, sizeof(float) * Q * ntiles));
   SFC_TRY(scr.alloc(&gmin, sizeof(unsigned int) * Q));
   SFC_TRY(scr.alloc(&bad, Q));
-  const int64_t* L = centre_lin;
-  if (!L) {
-    SFC_TRY(scr.alloc(&lin, sizeof(int64_t) * Q));
+  SFC_TRY(scr.alloc(&lin, sizeof(int64_t) * Q));
+  if (!centre_lin) {
     count_launch();
     k_centre_lin<<<(unsigned)((Q + 255) / 256), 256, 0, st>>>(centres, Q, g, lin, status_word());
-    L = lin;
   } else {
-    SFC_TRY(scr.alloc(&lin, sizeof(int64_t) * Q));
     SFC_TRY(cudaMemcpyAsync(lin, centre_lin, sizeof(int64_t) * Q, cudaMemcpyDeviceToDevice, st));
-    L = lin;
   }
   count_launch();
   k_centre_fix<<<(unsigned)((Q + 255) / 256), 256, 0, st>>>(lin, Q, g, bad);
   count_launch();
   k_fill_u32<<<(unsigned)((Q + 255) / 256), 256, 0, st>>>(gmin, Q, 0x7f800000u);
-  int rc = Q >= 8 ? scan_cm<8, EPT>(cm, g, grid, cur_mask, dict, N, eoff_all, weights, L, Q, tilemin, gmin, ntiles, st)
-                   : scan_cm<1, EPT>(cm, g, grid, cur_mask, dict, N, eoff_all, weights, L, Q, tilemin, gmin, ntiles, st);
+  int rc = Q >= QT ? scan_cm<QT, EPT>(cm, g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, st)
+                   : scan_cm<1, EPT>(cm, g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, st);
   SFC_CHECK(rc);
-  rc = band_cm<EPT>(cm, g, grid, cur_mask, dict, N, eoff_all, weights, L, Q, tilemin, gmin, ntiles, pick, cost, st);
+  rc = band_cm<EPT>(cm, g, grid, cur_mask, dict, N, eoff_all, weights, lin, Q, tilemin, gmin, ntiles, pick, cost, st);
   SFC_CHECK(rc);
   count_launch();
   k_mark_bad<<<(unsigned)((Q + 255) / 256), 256, 0, st>>>(bad, Q, pick, cost);
   SFC_TRY(cudaGetLastError());
   return SFC_OK;
+}
+}  // namespace
+
+int fullscan_tile_shapes(int* qt, int* ept) {
+  for (int i = 0; i < kFsNShapes; ++i) {
+    if (qt) qt[i] = kFsShapes[i].qt;
+    if (ept) ept[i] = kFsShapes[i].ept;
+  }
+  return kFsNShapes;
+}
+
+int fullscan_tile_shape(int shape) {
+  if (shape >= 0 && shape < kFsNShapes) g_fs_shape.store(shape);
+  return g_fs_shape.load();
+}
+
+int fullscan_batch(const Geo& g, const float* grid, const uint8_t* cur_mask, const uint32_t* dict, int64_t N,
+                   const int* eoff_all, const float* weights, int cm, const int32_t* centres,
+                   const int64_t* centre_lin, int64_t Q, int64_t* pick, float* cost, cudaStream_t st) {
+  if (Q <= 0) return SFC_OK;
+  switch (g_fs_shape.load()) {
+#define SFC_SHAPE(i, qt, ept) \
+  case i: return fullscan_shape<qt, ept>(g, grid, cur_mask, dict, N, eoff_all, weights, cm, centres, centre_lin, Q, pick, cost, st);
+    SFC_SHAPE(1, 8, 2) SFC_SHAPE(2, 16, 2) SFC_SHAPE(3, 4, 4) SFC_SHAPE(4, 4, 8) SFC_SHAPE(5, 16, 4)
+    SFC_SHAPE(6, 32, 2)
+#undef SFC_SHAPE
+    default:
+      return fullscan_shape<8, 4>(g, grid, cur_mask, dict, N, eoff_all, weights, cm, centres, centre_lin, Q, pick,
+                                  cost, st);
+  }
 }
 
 // The batched full scan into caller-provided scratch (no allocation): lin: Q

@@ -7,6 +7,7 @@
 // one, averaged over a sample of the queries.  The exact picks are those of the
 // full scan (Sec. I), whose picks equal the definition's.
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -186,6 +187,79 @@ int sfc_autotune(const float* grid, const uint8_t* mask, const sfc_grid* g, cons
   const int32_t k = sfc_tune_select((int32_t)n_cfg, ms_all.data(), ae_all.data(), spec->ae_max);
   *best = cfg[k];
   if (chosen) *chosen = k;
+  return SFC_OK;
+}
+
+int32_t sfc_tile_shape(int32_t shape) { return fullscan_tile_shape(shape); }
+
+int sfc_tune_tiles(const float* grid, const uint8_t* dict_mask, const uint8_t* cur_mask, const sfc_grid* g,
+                   const sfc_params* p, const int32_t* centres, int64_t Q, int32_t reps, double* table,
+                   int32_t* chosen, void* stream) {
+  if (!grid || !dict_mask || !cur_mask || !g || !p || !centres || Q < 1 || reps < 1 || reps > 100) {
+    set_error("sfc_tune_tiles: NULL argument, Q < 1 or reps outside 1..100");
+    return SFC_EINVAL;
+  }
+  if (p->precision != SFC_FP32) {
+    set_error("sfc_tune_tiles: the tile shapes are the FP32 full scan's (precision SFC_FP32)");
+    return SFC_EUNSUPPORTED;
+  }
+  SFC_CHECK(check_device());
+  cudaStream_t st = (cudaStream_t)stream;
+  int qt[8], ept[8];
+  const int ns = fullscan_tile_shapes(qt, ept);
+  const int prev = fullscan_tile_shape(-1);
+  DevBuf d_pick, d_cost;
+  SFC_TRY(cudaMalloc(&d_pick.p, sizeof(int64_t) * Q));
+  SFC_TRY(cudaMalloc(&d_cost.p, sizeof(float) * Q));
+  std::vector<int64_t> pick0(Q), pk(Q);
+  std::vector<float> cost0(Q), cs(Q);
+  Events ev;
+  for (auto& e : ev.e) SFC_TRY(cudaEventCreate(&e));
+  std::vector<double> ms(ns);
+  int rc = SFC_OK;
+  for (int k = 0; k < ns && rc == SFC_OK; ++k) {
+    fullscan_tile_shape(k);
+    std::vector<double> t;
+    for (int r = 0; r <= reps && rc == SFC_OK; ++r) {  // r = 0 warms up, untimed
+      cudaEventRecord(ev.e[0], st);
+      rc = fullscan_query_batch(grid, dict_mask, cur_mask, g, p, centres, Q, (int64_t*)d_pick.p, (float*)d_cost.p,
+                                stream);
+      cudaEventRecord(ev.e[1], st);
+      if (rc == SFC_OK && cudaEventSynchronize(ev.e[1]) != cudaSuccess) rc = SFC_ECUDA;
+      float v = 0.0f;
+      if (rc == SFC_OK && r > 0 && cudaEventElapsedTime(&v, ev.e[0], ev.e[1]) == cudaSuccess) t.push_back(v);
+    }
+    if (rc != SFC_OK) break;
+    std::sort(t.begin(), t.end());
+    ms[k] = t[t.size() / 2];
+    // every shape must give the same picks and cost bits
+    if (cudaMemcpy(k == 0 ? pick0.data() : pk.data(), d_pick.p, sizeof(int64_t) * Q, cudaMemcpyDeviceToHost) !=
+            cudaSuccess ||
+        cudaMemcpy(k == 0 ? cost0.data() : cs.data(), d_cost.p, sizeof(float) * Q, cudaMemcpyDeviceToHost) !=
+            cudaSuccess) {
+      rc = SFC_ECUDA;
+      break;
+    }
+    if (k > 0 && (pk != pick0 || std::memcmp(cs.data(), cost0.data(), sizeof(float) * Q) != 0)) {
+      set_error("sfc_tune_tiles: tile shape " + std::to_string(k) + " gave other picks or costs than shape 0");
+      rc = SFC_EDEVICE;
+    }
+  }
+  if (rc != SFC_OK) {
+    fullscan_tile_shape(prev);
+    return rc;
+  }
+  int best = 0;
+  for (int k = 1; k < ns; ++k)
+    if (ms[k] < ms[best]) best = k;
+  fullscan_tile_shape(best);
+  if (table)
+    for (int k = 0; k < ns; ++k) {
+      table[3 * k + 0] = qt[k];
+      table[3 * k + 1] = ept[k];
+      table[3 * k + 2] = ms[k];
+    }
+  if (chosen) *chosen = best;
   return SFC_OK;
 }
 

@@ -33,7 +33,7 @@ EXPORTS = ["sfc_params_default", "sfc_index_build", "sfc_index_destroy", "sfc_in
            "sfc_multi_create", "sfc_multi_query", "sfc_multi_destroy", "sfc_autotune", "sfc_tune_select", "sfc_trace_eig_read",
            "sfc_debug_fail_alloc", "sfc_debug_alloc_count", "sfc_debug_pool_used", "sfc_debug_lookback", "sfc_debug_sort",
            "sfc_shard_create", "sfc_shard_range", "sfc_shard_scan", "sfc_shard_band", "sfc_shard_destroy",
-           "sfc_trace_proj_read", "inpaint_run_multi"]
+           "sfc_trace_proj_read", "inpaint_run_multi", "sfc_tune_tiles", "sfc_tile_shape"]
 TRACE_PHASES = ("dictionary", "moments", "eigen", "finalize", "project_keys", "sort")
 
 
@@ -91,6 +91,11 @@ def lib():
                                   C.POINTER(i64), vp]
         L.inpaint_run_multi.argtypes = [vp, vp, vp, i32, C.POINTER(sfc_params), i64, vp, vp, vp]
         L.inpaint_run_multi.restype = C.c_int
+        L.sfc_tune_tiles.argtypes = [vp, vp, vp, C.POINTER(sfc_grid), C.POINTER(sfc_params), vp, i64, i32, vp, vp,
+                                     vp]
+        L.sfc_tune_tiles.restype = C.c_int
+        L.sfc_tile_shape.argtypes = [i32]
+        L.sfc_tile_shape.restype = C.c_int32
         L.sfc_autotune.argtypes = [vp, vp, C.POINTER(sfc_grid), C.POINTER(sfc_params), vp, i64,
                                    C.POINTER(sfc_tune_spec), C.POINTER(sfc_params), vp, C.POINTER(i32), vp]
         L.sfc_tune_select.argtypes = [i32, vp, vp, C.c_double]
@@ -459,6 +464,29 @@ def inpaint_run(grid: torch.Tensor, mask: torch.Tensor, mode: int = SFC_MODE_FUL
                              C.byref(steps), _stream()), "inpaint_run")
     n = steps.value
     return n, (lg[:n] if lg is not None else None)
+
+
+def sfc_tune_tiles(grid, dict_mask, cur_mask, centres, reps: int = 3, **params):
+    """Times the FP32 full scan with each tile shape and keeps the fastest.
+    -> (table float64 [shapes, 3] of (queries per tile, entries per thread,
+    ms), chosen shape)."""
+    grid = _dev(grid, torch.float32)
+    dict_mask = _dev(dict_mask, torch.uint8)
+    cur_mask = _dev(cur_mask, torch.uint8)
+    centres = _dev(centres, torch.int32)
+    P = Params(**params)
+    g = make_grid(grid)
+    table = np.zeros((7, 3), np.float64)
+    chosen = C.c_int32(-1)
+    _check(lib().sfc_tune_tiles(_ptr(grid), _ptr(dict_mask), _ptr(cur_mask), C.byref(g), C.byref(P.p),
+                                _ptr(centres), centres.shape[0], reps, table.ctypes.data_as(C.c_void_p),
+                                C.byref(chosen), _stream()), "sfc_tune_tiles")
+    return table, chosen.value
+
+
+def sfc_tile_shape(shape: int = -1) -> int:
+    """Sets the FP32 full scan's tile shape (0..6; other values only read it)."""
+    return int(lib().sfc_tile_shape(int(shape)))
 
 
 def inpaint_run_multi(grids, masks, max_steps: int = 0, log: bool = True, **params):
