@@ -50,11 +50,11 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(width=1024, K=11, curves=8, dims=8, bits=16, window=64, pca_sample=16384, cap=65536)
 # DRAM bytes (read + write) per launch from one ncu capture of `python bench.py
-# --steps 1 --warmup 1` (profiles/); None once the kernel changed since.
+# --profile-step fp32 2` (profiles/); None once the kernel changed since.
 # k_tc_gemm: captured on the 512^2 case (N = 210,944, Q = 1,024: 949.8 MB read,
 # 27.8 MB written) and scaled to the bench's full scan (N = 901,632, Q = 2,048):
 # the reads (the B operand, read once) by N, the writes (group minima) by Q N.
-TRAFFIC = {"k_query": 21.35e6, "k_si_cluster": 3.31e6, "k_tc_gemm": 949.8e6 * 901632 / 210944 + 27.8e6 * 8.548}
+TRAFFIC = {"k_query": 21.35e6, "k_si_cluster": 3.342e6, "k_tc_gemm": 949.8e6 * 901632 / 210944 + 27.8e6 * 8.548}
 FP64_PEAK_TFLOPS = 1.26  # 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 80.5  # 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz
 METRIC = "patch queries/s: SFC index vs full-scan masked-L2, 1 GB300, oracle-equal picks"
