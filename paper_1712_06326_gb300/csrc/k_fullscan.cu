@@ -47,28 +47,55 @@ __global__ void __launch_bounds__(kFsThreads) k_fs_scan(const float* __restrict_
                                                         unsigned int* __restrict__ gmin, int64_t ntiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = g.n, ch = g.ch;
-  float2* am = reinterpret_cast<float2*>(smem_raw);  // [n][QT]: (known, known * t)
+  float2* am = reinterpret_cast<float2*>(smem_raw);  // [ne][QT]: (known, known * t)
   int* eo = reinterpret_cast<int*>(am + (size_t)n * QT);
-  float* we = reinterpret_cast<float*>(eo + n);       // [n] weights (WEIGHTED)
+  float* we = reinterpret_cast<float*>(eo + n);       // [ne] weights (WEIGHTED)
+  __shared__ int s_wcnt[kFsThreads / 32];
   const int64_t q0 = qbase + (int64_t)blockIdx.y * QT;
-  for (int e = threadIdx.x; e < n; e += kFsThreads) {
-    int o = eoff_all[e];
-    eo[e] = o;
-    if (CM & 1) we[e] = weights[e % ch];
-    const int pixo = eoff_all[e - e % ch] / ch;
+  // the elements known to at least one query of the tile, in patch order: an
+  // element unknown to every query adds exactly 0 to every cost, so it is left out
+  const int lane0 = threadIdx.x & 31, warp0 = threadIdx.x >> 5;
+  int ne = 0;
+  for (int r0 = 0; r0 < n; r0 += kFsThreads) {
+    const int e = r0 + threadIdx.x;
+    int o = 0, pixo = 0;
+    bool any = false;
+    if (e < n) {
+      o = eoff_all[e];
+      pixo = eoff_all[e - e % ch] / ch;
 #pragma unroll
-    for (int qi = 0; qi < QT; ++qi) {
-      int64_t q = q0 + qi;
-      float2 v = make_float2(0.0f, 0.0f);
-      if (q < Q) {
-        int64_t tc = centre_lin[q];
-        float k = mask[tc + pixo] ? 1.0f : 0.0f;
-        v = make_float2(k, k * grid[tc * ch + o]);
+      for (int qi = 0; qi < QT; ++qi) {
+        const int64_t q = q0 + qi;
+        if (q < Q) any |= mask[centre_lin[q] + pixo] != 0;
       }
-      am[(size_t)e * QT + qi] = v;
     }
+    const unsigned bal = __ballot_sync(0xffffffffu, any);
+    if (lane0 == 0) s_wcnt[warp0] = __popc(bal);
+    __syncthreads();
+    int off = ne, tot = 0;
+    for (int w = 0; w < kFsThreads / 32; ++w) {
+      if (w < warp0) off += s_wcnt[w];
+      tot += s_wcnt[w];
+    }
+    if (any) {
+      const int at = off + __popc(bal & ((1u << lane0) - 1u));
+      eo[at] = o;
+      if (CM & 1) we[at] = weights[e % ch];
+#pragma unroll
+      for (int qi = 0; qi < QT; ++qi) {
+        const int64_t q = q0 + qi;
+        float2 v = make_float2(0.0f, 0.0f);
+        if (q < Q) {
+          const int64_t tc = centre_lin[q];
+          const float k = mask[tc + pixo] ? 1.0f : 0.0f;
+          v = make_float2(k, k * grid[tc * ch + o]);
+        }
+        am[(size_t)at * QT + qi] = v;
+      }
+    }
+    __syncthreads();
+    ne += tot;
   }
-  __syncthreads();
   const int64_t j0 = (int64_t)blockIdx.x * kFsThreads * EPT + threadIdx.x;
   int64_t sb[EPT];
 #pragma unroll
@@ -81,7 +108,7 @@ __global__ void __launch_bounds__(kFsThreads) k_fs_scan(const float* __restrict_
   for (int k = 0; k < EPT; ++k)
 #pragma unroll
     for (int qi = 0; qi < QT; ++qi) acc[k][qi] = 0.0f;
-  for (int e = 0; e < n; ++e) {
+  for (int e = 0; e < ne; ++e) {
     const int o = eo[e];
     float p[EPT];
 #pragma unroll

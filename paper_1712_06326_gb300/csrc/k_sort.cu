@@ -372,6 +372,7 @@ constexpr int kSsOver = 8;              // samples per bucket
 constexpr int kSsRun = 1024;            // sampled pairs per sorting CTA
 constexpr int kSsCap = 2048;            // pairs per bucket sorted in shared memory
 constexpr int kSsBucketE = 4;           // pairs per thread and chunk in the bucket sort
+constexpr int kSsBucketThreads = 256;   // threads of a bucket-sorting CTA
 constexpr int kSsTile = 256 * 16;       // pairs per CTA of the count / place passes
 constexpr int64_t kSsMaxN = 1ll << 20;  // larger dictionaries: the LSD sort
 std::atomic<int> g_ss_force_lsd{0};
@@ -707,7 +708,7 @@ __global__ void __launch_bounds__(256) k_ss_place(const uint64_t* __restrict__ k
     }
 }
 
-__global__ void __launch_bounds__(256) k_ss_bucket(const uint64_t* __restrict__ tk, const uint32_t* __restrict__ tv,
+__global__ void __launch_bounds__(kSsBucketThreads) k_ss_bucket(const uint64_t* __restrict__ tk, const uint32_t* __restrict__ tv,
                                                    int64_t N, int B, const uint32_t* __restrict__ start,
                                                    const int* __restrict__ ovf, uint64_t* __restrict__ skeys,
                                                    uint32_t* __restrict__ sids) {
@@ -831,7 +832,7 @@ int sample_sort_pairs(const uint64_t* keys, uint64_t* skeys, uint32_t* sids, int
   if (shm_b > kSmemOptIn)
     SFC_TRY(cudaFuncSetAttribute(k_ss_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_b));
   count_launch();
-  k_ss_bucket<<<dim3((unsigned)B, C), 256, shm_b, st>>>(tk, tv, N, B, start, ovf, skeys, sids);
+  k_ss_bucket<<<dim3((unsigned)B, C), kSsBucketThreads, shm_b, st>>>(tk, tv, N, B, start, ovf, skeys, sids);
   SFC_TRY(cudaGetLastError());
   return SFC_OK;
 }
