@@ -82,6 +82,16 @@ def test_multi_criminisi_step_cap_and_a_full_image(S):
     assert S.sfc_status() == 0
 
 
+def test_multi_more_images_than_the_split_form_takes(S):
+    # 36 images: each round's search is the one-CTA multi-image launch
+    images = [synth.voronoi2d(40 + 4 * (i % 5), cfg=2, seed_sub=60 + i) for i in range(36)]
+    params = dict(K=5, curves=4, dims=4, bits=10, window=8, pca_sample=0)
+    ref = one_by_one(S, images, max_steps=25, **params)
+    got = all_at_once(S, images, max_steps=25, **params)
+    check_same(ref, got)
+    assert S.sfc_status() == 0
+
+
 def test_multi_3d(S):
     images = [synth.spheres3d(20, block=4, missing=0.05, seed_sub=46),
               synth.spheres3d(24, block=4, missing=0.05, seed_sub=47)]

@@ -105,3 +105,19 @@ def test_sort_all_keys_equal(S):
     ex = check_all_modes(S, g, m, K=7, curves=2, dims=4, bits=10, window=8, basis=ex0["basis"], mean=ex0["mean"])
     assert np.all(ex["keys"] == ex["keys"][:, :1])
     assert np.array_equal(ex["sids"], np.tile(np.arange(len(ex["dict"]), dtype=np.uint32), (2, 1)))
+
+
+def test_sort_at_the_sample_sort_limit(S):
+    # 2^20 dictionary entries take the sample sort, more the LSD sort; both give
+    # the oracle's sort (grey noise images, every patch known, K = 7)
+    for X, Y in ((1030, 1030), (1031, 1030)):
+        g = np.random.default_rng(X).random((Y, X, 1)).astype(np.float32)
+        m = np.ones((Y, X), np.uint8)
+        ix = S.sfc_index_build(dev(g), dev(m), K=7, curves=1, dims=4, bits=12, window=8, pca_sample=4096,
+                               keep_intermediates=1)
+        ex = S.sfc_index_export(ix, proj=True)
+        ix.close()
+        assert len(ex["dict"]) == (X - 6) * (Y - 6)
+        sk, si = O.sort(ex["keys"][0])
+        assert np.array_equal(sk, ex["skeys"][0]) and np.array_equal(si, ex["sids"][0])
+    assert S.sfc_status() == 0
