@@ -364,10 +364,11 @@ uint64_t sfc_launch_count(void);
  * ms[SFC_TRACE_PHASES] the summed milliseconds of the phases -- dictionary,
  * moments (mean + covariance), eigen-solve, basis finalisation,
  * projection + keys, sort -- and *builds the number of builds summed, and
- * (the projections, keys and sorts run pipelined over groups of curves on
- * the library's own streams: "projection + keys" ends when every group's
- * keys exist and includes the sorts of the earlier groups that overlap it;
- * "sort" is the rest of the sorting) and
+ * (the projections, keys and sorts run on the library's own streams; with
+ * the radix sort of dictionaries above 2^20 entries they are pipelined over
+ * groups of curves, and "projection + keys" ends when every group's keys exist
+ * and includes the sorts of the earlier groups that overlap it; "sort" is the
+ * rest of the sorting, with the sample sort all of it) and
  * *eig_flops the summed algorithmic FP64 flops of the eigen-solves
  * (per index: 2 s^2 p per product of the covariance with the block and 4 s p^2
  * per orthonormalisation, s = subset length, p = block size).  Any output may be NULL. */
