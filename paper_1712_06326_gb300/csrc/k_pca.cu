@@ -82,58 +82,15 @@ __device__ inline void df_acc_prod(float a, float b, float& hi, float& lo) {
   hi = t;
 }
 
-// Partial sums of every patch value over one split of the sample (double-float,
-// folded to FP64 every 64 samples): msum[split][e], fixed order.
-__global__ void k_mean_partial(const float* __restrict__ grid, const uint32_t* __restrict__ dict, int64_t step,
-                               int64_t cnt, const int* __restrict__ eoff, int n, int ch, int nsplit,
-                               double* __restrict__ msum) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  const int split = blockIdx.y;
-  if (e >= n) return;
-  const int64_t per = (cnt + nsplit - 1) / nsplit;
-  const int64_t a0 = split * per, a1 = a0 + per < cnt ? a0 + per : cnt;
-  const int eo = eoff[e];
-  double acc = 0.0;
-  float hi = 0.0f, lo = 0.0f;
-  int k = 0;
-  // eight samples' loads in flight, then their sums in order
-  for (int64_t a = a0; a < a1; a += 8) {
-    float v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = a + u < a1 ? grid[(int64_t)dict[(a + u) * step] * ch + eo] : 0.0f;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      if (a + u < a1) {
-        df_add(v[u], hi, lo);
-        if (++k == 64) {
-          acc += (double)hi + (double)lo;
-          hi = lo = 0.0f;
-          k = 0;
-        }
-      }
-    }
-  }
-  msum[(int64_t)split * n + e] = acc + ((double)hi + (double)lo);
-}
-
-// mean[e] = (sum over splits in order) / cnt
-__global__ void k_mean_reduce(const double* __restrict__ msum, int n, int nsplit, int64_t cnt,
-                              double* __restrict__ mean) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  double t = 0.0;
-#pragma unroll 8
-  for (int sp = 0; sp < nsplit; ++sp) t += msum[(int64_t)sp * n + e];
-  mean[e] = t / (double)cnt;
-}
-
 // Partial raw second moments sum_a x_i x_j of the whole patch (n values), tile
 // (ti, tj), ti <= tj, over one split of the sample: partial layout
-// [split][pair][32][32] (FP64, folded from double-float).
+// [split][pair][32][32] (FP64, folded from double-float).  The CTAs of the
+// diagonal tiles (ti == tj) also sum the values themselves, sample by sample
+// in order (double-float): msum[split][e], the mean's partial sums.
 __global__ void __launch_bounds__(256) k_cov_partial(const float* __restrict__ grid, const uint32_t* __restrict__ dict,
                                                      int64_t step, int64_t cnt, const int* __restrict__ eoff, int n,
                                                      int ch, int nsplit, const int2* __restrict__ pairs, int npairs,
-                                                     double* __restrict__ partial) {
+                                                     double* __restrict__ partial, double* __restrict__ msum) {
   const int split = blockIdx.y, pr = blockIdx.x;
   const int2 tp = pairs[pr];
   const int i0 = tp.x * kTile, j0 = tp.y * kTile;
@@ -150,6 +107,8 @@ __global__ void __launch_bounds__(256) k_cov_partial(const float* __restrict__ g
   const int64_t a0 = split * per, a1 = a0 + per < cnt ? a0 + per : cnt;
   const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;  // 16x16 threads, 2x2 outputs each
   float hi[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, lo[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  const bool msums = tp.x == tp.y && tx == 0;  // this thread also sums rows ty*2, ty*2+1
+  float mh[2] = {0.f, 0.f}, ml[2] = {0.f, 0.f};
   // the next chunk's values are loaded into registers while the current one
   // is accumulated (each thread stages kPer (sample, value) pairs)
   constexpr int kPer = kChunk * kTile / 256;
@@ -188,17 +147,31 @@ __global__ void __launch_bounds__(256) k_cov_partial(const float* __restrict__ g
       df_acc_prod(a0v, b1v, hi[0][1], lo[0][1]);
       df_acc_prod(a1v, b0v, hi[1][0], lo[1][0]);
       df_acc_prod(a1v, b1v, hi[1][1], lo[1][1]);
+      if (msums) {
+        df_add(a0v, mh[0], ml[0]);
+        df_add(a1v, mh[1], ml[1]);
+      }
     }
     __syncthreads();
   }
+  if (msums)
+    for (int a = 0; a < 2; ++a)
+      if (i0 + ty * 2 + a < n) msum[(int64_t)split * n + i0 + ty * 2 + a] = (double)mh[a] + (double)ml[a];
   double* out = partial + ((int64_t)split * npairs + pr) * kTile * kTile;
   for (int a = 0; a < 2; ++a)
     for (int b = 0; b < 2; ++b) out[(ty * 2 + a) * kTile + tx * 2 + b] = (double)hi[a][b] + (double)lo[a][b];
 }
 
-// Full-patch second moments M[e][f] (n x n, both triangles) = sum over splits.
+// Full-patch second moments M[e][f] (n x n, both triangles) = sum over splits;
+// mean[e] = (the splits' sums of value e, in order) / cnt.
 __global__ void k_cov_reduce(const double* __restrict__ partial, int nsplit, int npairs, int n,
-                             double* __restrict__ M) {
+                             double* __restrict__ M, const double* __restrict__ msum, int64_t cnt,
+                             double* __restrict__ mean) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double t = 0.0;
+    for (int sp = 0; sp < nsplit; ++sp) t += msum[(int64_t)sp * n + e];
+    mean[e] = t / (double)cnt;
+  }
   const int T = (n + kTile - 1) / kTile;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * n;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -1430,11 +1403,6 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
   int nsplit = (int)((cnt + 511) / 512);
   if (nsplit > 64) nsplit = 64;
   if (nsplit < 1) nsplit = 1;
-  // the mean is a cheap sum per value: more, shorter splits (64 samples each)
-  // keep more of its gathers in flight
-  int msplit = (int)((cnt + 63) / 64);
-  if (msplit > 256) msplit = 256;
-  if (msplit < 1) msplit = 1;
 
   double *mean = nullptr, *mean_c = nullptr, *msum = nullptr, *partial = nullptr, *M = nullptr;
   int2* pairs = nullptr;
@@ -1442,7 +1410,7 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
   Scratch scr(st);
   SFC_TRY(scr.alloc(&mean, sizeof(double) * n));
   SFC_TRY(scr.alloc(&mean_c, sizeof(double) * C * s));
-  SFC_TRY(scr.alloc(&msum, sizeof(double) * msplit * n));
+  SFC_TRY(scr.alloc(&msum, sizeof(double) * nsplit * n));
   SFC_TRY(scr.alloc(&partial, sizeof(double) * nsplit * npairs * kTile * kTile));
   SFC_TRY(scr.alloc(&M, sizeof(double) * n * n));
   SFC_TRY(scr.alloc(&pairs, sizeof(int2) * npairs));
@@ -1458,15 +1426,10 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
   SFC_TRY(cudaMemcpyAsync(pairs, pairs_h.data(), sizeof(int2) * npairs, cudaMemcpyHostToDevice, st));
 
   count_launch();
-  k_mean_partial<<<dim3((n + 127) / 128, msplit), 128, 0, st>>>(grid, ix.dict, step, cnt, ix.eoff_all, n, ix.g.ch,
-                                                                  msplit, msum);
-  count_launch();
-  k_mean_reduce<<<(n + 127) / 128, 128, 0, st>>>(msum, n, msplit, cnt, mean);
-  count_launch();
   k_cov_partial<<<dim3(npairs, nsplit), 256, 0, st>>>(grid, ix.dict, step, cnt, ix.eoff_all, n, ix.g.ch, nsplit,
-                                                      pairs, npairs, partial);
+                                                      pairs, npairs, partial, msum);
   count_launch();
-  k_cov_reduce<<<128, 256, 0, st>>>(partial, nsplit, npairs, n, M);
+  k_cov_reduce<<<128, 256, 0, st>>>(partial, nsplit, npairs, n, M, msum, cnt, mean);
   count_launch();
   k_cov_extract<<<dim3(64, C), 256, 0, st>>>(M, mean, n, ix.g.ch, cnt, ix.sub_pix, ix.m, s, b.A, mean_c);
   SFC_TRY(cudaGetLastError());
