@@ -106,7 +106,9 @@ __global__ void __launch_bounds__(kPThreads) k_proj_tc(PtArgs a) {
   uint32_t* s_max = s_min + a.CD;                                           // CD
   int* s_cur = reinterpret_cast<int*>(s_max + a.CD);                        // CD: curve of a column
   int* s_k = s_cur + a.CD;                                                  // CD: axis of a column
-  int64_t* s_base = reinterpret_cast<int64_t*>(((uintptr_t)(s_k + a.CD) + 7) & ~(uintptr_t)7);  // kPM
+  // each row's patch centre in the grid (rows past N take entry 0's: their
+  // results are never stored or ranged)
+  const float** s_rowp = reinterpret_cast<const float**>(((uintptr_t)(s_k + a.CD) + 7) & ~(uintptr_t)7);  // kPM
   __shared__ uint64_t empty_bar[kPStages], acc_full[2], final_bar;
   __shared__ uint32_t tmem_base;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(kPThreads) k_proj_tc(PtArgs a) {
       const uint32_t tacc = tmem + (uint32_t)((L & 1) * a.nb);
       for (int r = threadIdx.x; r < kPM; r += kPThreads) {
         const int64_t j = t * kPM + r;
-        s_base[r] = j < a.N ? (int64_t)a.dict[j] * a.ch : -1;
+        s_rowp[r] = a.grid + (int64_t)a.dict[j < a.N ? j : 0] * a.ch;
       }
       __syncthreads();
       for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
@@ -182,23 +184,23 @@ __global__ void __launch_bounds__(kPThreads) k_proj_tc(PtArgs a) {
           }
         // gather: warp -> rows warp, warp + 8, ...; lane -> elements 2 lane, 2 lane + 1
         const int e0 = kb * kPK + 2 * lane;
-        const int o0 = s_eo[e0], o1 = s_eo[e0 + 1];
+        const int oe0 = s_eo[e0], oe1 = s_eo[e0 + 1];
         const float m0 = s_cm[e0], m1 = s_cm[e0 + 1];
-        const bool u0 = o0 != kNoElem, u1 = o1 != kNoElem;
+        const bool u0 = oe0 != kNoElem, u1 = oe1 != kNoElem;
+        const int o0 = u0 ? oe0 : 0, o1 = u1 ? oe1 : 0;  // unused elements read the centre, then give 0
         // rows warp + 8 i share r & 7, hence the swizzled chunk: one offset per thread
         unsigned char* dst0 = stage + sw128_off(warp, 2 * lane);
         float v0[kPM / 8], v1[kPM / 8];
 #pragma unroll
         for (int i = 0; i < kPM / 8; ++i) {  // every load of the block in flight at once
-          const int64_t b = s_base[warp + 8 * i];
-          v0[i] = (b >= 0 && u0) ? __ldg(a.grid + b + o0) : 0.0f;
-          v1[i] = (b >= 0 && u1) ? __ldg(a.grid + b + o1) : 0.0f;
+          const float* rp = s_rowp[warp + 8 * i];
+          v0[i] = __ldg(rp + o0);
+          v1[i] = __ldg(rp + o1);
         }
 #pragma unroll
         for (int i = 0; i < kPM / 8; ++i) {
-          const int64_t b = s_base[warp + 8 * i];
-          const float x0 = (b >= 0 && u0) ? __fsub_rn(v0[i], m0) : 0.0f;
-          const float x1 = (b >= 0 && u1) ? __fsub_rn(v1[i], m1) : 0.0f;
+          const float x0 = u0 ? __fsub_rn(v0[i], m0) : 0.0f;
+          const float x1 = u1 ? __fsub_rn(v1[i], m1) : 0.0f;
           *reinterpret_cast<__nv_bfloat162*>(dst0 + i * 1024) = __floats2bfloat162_rn(x0, x1);  // x0 first
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
