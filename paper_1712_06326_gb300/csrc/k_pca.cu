@@ -1449,13 +1449,16 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
   const size_t shm_full = sizeof(double) * (2 * (size_t)npf * npf + 2 * npf) + sizeof(int) * npf;
   if (s <= kSFull && shm_full > kSmemOptIn)
     SFC_TRY(cudaFuncSetAttribute(k_eig_full, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_full));
-  // cluster path: 16 CTAs per curve when such clusters can be scheduled, else 8
-  int cs = 0, use32 = 0;
+  // cluster path: the first of (16 CTAs, FP32 copies), (8, FP32 copies),
+  // (16, none), (8, none) whose clusters for every curve can all run at once
+  // (a second wave of clusters costs about as much as the first: 16-CTA
+  // clusters at one CTA per SM measured 1.27 against 0.80 ms); if none can,
+  // the schedulable one with the most clusters at once
+  int cs = 0, use32 = 0, best_n = 0;
   size_t shm_cl = 0;
-  for (int opt = 0; opt < 4 && cs == 0 && s > kSJacobi; ++opt) {
-    // preference: 16-CTA clusters with the FP32 copies, without them, then 8
-    const int cand = opt < 2 ? 16 : 8;
-    const bool w32 = (opt & 1) == 0;
+  for (int opt = 0; opt < 4 && s > kSJacobi; ++opt) {
+    const int cand = (opt & 1) == 0 ? 16 : 8;
+    const bool w32 = opt < 2;
     const size_t need = cluster_shm_bytes(s, p, cand, w32);
     if (need > 200 * 1024) continue;
     const void* fn = cand == 16 ? (const void*)k_si_cluster<16> : (const void*)k_si_cluster<8>;
@@ -1480,9 +1483,17 @@ int pca_build(Index& ix, const float* grid, cudaStream_t st) {
       cudaGetLastError();
       continue;
     }
-    cs = cand;
-    use32 = w32 ? 1 : 0;
-    shm_cl = need;
+    if (nclusters > best_n) {
+      best_n = nclusters;
+      cs = cand;
+      use32 = w32 ? 1 : 0;
+      shm_cl = need;
+    }
+    if (nclusters >= C) break;  // one wave
+  }
+  if (cs) {  // the chosen kernel's shared-memory size (a later candidate may have set another)
+    const void* fn = cs == 16 ? (const void*)k_si_cluster<16> : (const void*)k_si_cluster<8>;
+    SFC_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_cl));
   }
   if (s <= kSJacobi) {
     count_launch();
