@@ -390,12 +390,16 @@ int sfc_trace_eig_read(double* fp64_flops, double* fp32_flops);
 enum { SFC_TRACE_TC_PHASES = 3 };
 int sfc_trace_tc_read(double* ms, int64_t* calls, double* gemm_flops);
 
-/* While tracing is enabled, every SFC_BF16 build also records events around
- * its tensor-core projection launch; when the index is destroyed the launch's
- * time is added up.  sfc_trace_proj_read gives the summed milliseconds, the
- * number of launches, and the summed algorithmic work: 2 N C s D flops and
- * N n 4 + N C D 2 bytes (patch values gathered, BF16 projections written).
- * Any output may be NULL. */
+/* While tracing is enabled, every build also records events around its
+ * projection launches (SFC_BF16: the tensor-core launch; SFC_FP32: from the
+ * first curve's FMA-chain launch to the last one's, which with the radix sort
+ * of dictionaries above 2^20 entries also spans the keys of the earlier
+ * curve groups); when the index is destroyed that time is added up.
+ * sfc_trace_proj_read gives the summed milliseconds, the number of builds
+ * counted, and the summed algorithmic work: 2 N C s D flops and N n 4 + N C D 2
+ * bytes (SFC_BF16: patch values gathered, BF16 projections written) or
+ * N C s 4 + N C D 4 bytes (SFC_FP32: subset values gathered per curve, FP32
+ * projections written).  Any output may be NULL. */
 int sfc_trace_proj_read(double* ms, int64_t* calls, double* flops, double* bytes);
 
 /* ---- Parameter search (the tuned index of a batch of queries) -------------

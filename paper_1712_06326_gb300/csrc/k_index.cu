@@ -196,15 +196,23 @@ __global__ void k_sorted_coords(const T* __restrict__ proj, const uint32_t* __re
 }
 
 template <int D>
-int launch_project(const Index& ix, const float* grid, float* proj, uint32_t* lohi, int c0, int nc,
+int launch_project(Index& ix, const float* grid, float* proj, uint32_t* lohi, int c0, int nc,
                    cudaStream_t st) {
   const size_t shm = sizeof(unsigned long long) * ix.s * ((D + 1) / 2) + sizeof(float) * ix.s + sizeof(int) * ix.s;
   if (shm > kSmemOptIn) SFC_TRY(cudaFuncSetAttribute(k_project<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   dim3 grd((unsigned)((ix.N + 256 * kPE - 1) / (256 * kPE)), nc);
+  // traced builds: events around the projection launches (from the first
+  // curve's to the last one's), and the launches' algorithmic work
+  if (c0 == 0 && ix.ev_proj[0]) {
+    ix.proj_flops = 2.0 * (double)ix.N * ix.C * ix.s * D;
+    ix.proj_bytes = (double)ix.N * ix.C * ix.s * 4.0 + (double)ix.N * ix.C * D * 4.0;
+    cudaEventRecord(ix.ev_proj[0], st);
+  }
   count_launch();
   k_project<D><<<grd, 256, shm, st>>>(grid, ix.dict, ix.N, ix.g.ch, ix.s, ix.sub_eoff, ix.basis, ix.mean, proj, lohi,
                                       c0);
   SFC_TRY(cudaGetLastError());
+  if (c0 + nc == ix.C && ix.ev_proj[1]) cudaEventRecord(ix.ev_proj[1], st);
   return SFC_OK;
 }
 

@@ -650,8 +650,7 @@ int build_index(const float* grid, const uint8_t* dict_mask, const sfc_grid* gp,
   }
   if (ix.traced) {
     for (auto& e : ix.ev) SFC_TRY(cudaEventCreate(&e));
-    if (p->precision == SFC_BF16)
-      for (auto& e : ix.ev_proj) SFC_TRY(cudaEventCreate(&e));
+    for (auto& e : ix.ev_proj) SFC_TRY(cudaEventCreate(&e));
     trace_mark(ix, 0, st);
   }
   SFC_TRY(pmalloc(&ix.eig_iters, sizeof(int) * 2 * ix.C, st));
