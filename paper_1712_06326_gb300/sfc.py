@@ -554,7 +554,7 @@ def sfc_status() -> int:
 
 
 def sfc_trace_proj_read() -> dict:
-    """Summed time, launches and algorithmic work of the traced BF16 projections."""
+    """Summed time, builds counted and algorithmic work of the traced projection launches."""
     ms, fl, by = C.c_double(), C.c_double(), C.c_double()
     calls = C.c_int64()
     _check(lib().sfc_trace_proj_read(C.byref(ms), C.byref(calls), C.byref(fl), C.byref(by)), "sfc_trace_proj_read")

@@ -12,7 +12,8 @@ Bars:
   bit-exact: the quantiser's lo / scale, the keys, the sorted keys and ids, the
   queries' keys, candidate sets, picks and costs (the oracle's index built from
   the exported projections);
-* the k-NN lists, a 3-D volume with K = 9 (n = 729), and a stored BF16 index.
+* the k-NN lists, a 3-D volume with K = 9 (n = 729), a stored BF16 index, and
+  the trace counters of the projection launches (FP32 and BF16 builds).
 """
 import numpy as np
 import pytest
@@ -165,4 +166,20 @@ def test_bf16_stored_index_round_trip(S, tmp_path):
     assert ix2.params.precision == S.SFC_BF16
     ix.close()
     ix2.close()
+    assert S.sfc_status() == 0
+
+
+def test_projection_trace_fp32_and_bf16(S):
+    # the trace's projection work counters: 2 N C s D flops per build, either tier
+    g, m = synth.voronoi2d(96, cfg=2, seed_sub=14)
+    for prec in (S.SFC_FP32, S.SFC_BF16):
+        S.sfc_trace(True)
+        ix = S.sfc_index_build(dev(g), dev(m), K=7, curves=4, dims=6, bits=12, window=16, pca_sample=0,
+                               precision=prec)
+        N, s = ix.N, ix.s
+        ix.close()
+        pt = S.sfc_trace_proj_read()
+        S.sfc_trace(False)
+        assert pt["calls"] == 1 and pt["ms"] > 0
+        assert pt["flops"] == 2.0 * N * 4 * s * 6
     assert S.sfc_status() == 0
