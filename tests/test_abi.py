@@ -65,6 +65,14 @@ def test_invalid_arguments_rejected_on_host(L):
     assert L.inpaint_run(None, None, C.byref(g), C.byref(p), 0, 0, None, C.byref(steps), None) == sfc.SFC_EINVAL
     assert L.sfc_index_destroy(None) == 0
     assert len(L.sfc_last_error()) > 0
+    # the many-image fill loop and the tile-shape tuner check their arguments first
+    st = (C.c_int64 * 2)()
+    assert L.inpaint_run_multi(None, None, None, 0, C.byref(p), 0, None, st, None) == sfc.SFC_EINVAL
+    assert L.inpaint_run_multi(None, None, C.byref(g), 2, C.byref(p), 0, None, st, None) == sfc.SFC_EINVAL
+    table = (C.c_double * 21)()
+    assert L.sfc_tune_tiles(None, None, None, C.byref(g), C.byref(p), None, 4, 2, table, None, None) == sfc.SFC_EINVAL
+    # reading the full scan's tile shape touches no device
+    assert L.sfc_tile_shape(-1) == 0
 
 
 def test_library_has_no_cpu_fallback_symbols(L):
