@@ -293,20 +293,32 @@ class Clocks:
         self.index = index
         self.proc = None
         self.lines = []
+        self.first = threading.Event()
+        self.t0 = 0  # lines read before the timed region
 
     def start(self):
+        """Start sampling every 100 ms and wait (up to 10 s) for the first
+        sample: nvidia-smi's start-up stalls this process's driver calls for a
+        few milliseconds (one 3.5 ms step measured 5.4 ms when the sampler was
+        started with the timed region), so it must be done before the region."""
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            self.first.wait(10.0)
         except OSError:
             self.proc = None
+
+    def begin(self):
+        """Mark the start of the timed region: later samples are the region's."""
+        self.t0 = len(self.lines)
 
     def _read(self):
         for ln in self.proc.stdout:
             self.lines.append(ln.strip())
+            self.first.set()
 
     def stop(self):
         if not self.proc:
@@ -318,7 +330,9 @@ class Clocks:
             self.proc.kill()
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        # the timed region's samples; the last one before it if the region was shorter than the interval
+        region = self.lines[self.t0:] or self.lines[max(self.t0 - 1, 0):self.t0]
+        for ln in region:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -332,7 +346,8 @@ class Clocks:
                     reasons.add(nm)
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm),
+                "interval_ms": 100, "in_timed_region": len(self.lines) > self.t0}
 
 
 # ----------------------------------------------------------------------------
@@ -725,7 +740,8 @@ def run_volumes(sfc, torch, dev, flush, stream):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 100; 5 with --impl reference, whose steps take seconds each)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -741,6 +757,8 @@ def main():
                     help="profiling case only: the fill loop on the workload (SFC mode) for STEPS steps, twice; "
                          "prints one line, no timing")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 5 if args.impl == "reference" else 100
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_fp16:
@@ -804,6 +822,7 @@ def main():
     sfc.sfc_trace(True)
     barrier()
     torch.cuda.synchronize()
+    clocks.begin()
     l0 = sfc.sfc_launch_count()
     ev = []
     live = []
