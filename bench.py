@@ -54,7 +54,10 @@ WORKLOAD = dict(width=1024, K=11, curves=8, dims=8, bits=16, window=64, pca_samp
 # k_tc_gemm: captured on the 512^2 case (N = 210,944, Q = 1,024: 949.8 MB read,
 # 27.8 MB written) and scaled to the bench's full scan (N = 901,632, Q = 2,048):
 # the reads (the B operand, read once) by N, the writes (group minima) by Q N.
-TRAFFIC = {"k_query": 21.35e6, "k_si_cluster": 3.342e6, "k_tc_gemm": 949.8e6 * 901632 / 210944 + 27.8e6 * 8.548}
+# k_project: 17.3 MB read + 170.3 MB written (the 231 MB of projections partly
+# still in L2 when the launch ends).
+TRAFFIC = {"k_query": 21.35e6, "k_si_cluster": 3.342e6, "k_project": 187.6e6,
+           "k_tc_gemm": 949.8e6 * 901632 / 210944 + 27.8e6 * 8.548}
 FP64_PEAK_TFLOPS = 1.26  # 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 80.5  # 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz
 METRIC = "patch queries/s: SFC index vs full-scan masked-L2, 1 GB300, oracle-equal picks"
@@ -913,7 +916,7 @@ def main():
     p_ms = ptrace["ms"] / pcalls
     p_tf = (ptrace["flops"] / pcalls) / (p_ms / 1000.0) / 1e12 if p_ms > 0 else 0.0
     p_roof = {"kernel": "k_project (FP32 projection in sfc_index_build)", "bound": "alu", "achieved": p_tf,
-              "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": p_tf / FP32_PEAK_TFLOPS, "traffic": None,
+              "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": p_tf / FP32_PEAK_TFLOPS, "traffic": TRAFFIC["k_project"],
               "peak_source": f"derived: FP32 {FP32_PEAK_TFLOPS} TFLOP/s from the unit counts and the 2.07 GHz clock",
               "launch_ms": p_ms, "flops_per_launch": ptrace["flops"] / pcalls,
               "gathered_and_written_bytes": ptrace["bytes"] / pcalls}
