@@ -82,6 +82,21 @@ __device__ inline void df_acc_prod(float a, float b, float& hi, float& lo) {
   hi = t;
 }
 
+// (hi, lo) += a * b for hi >= 0 and a, b >= 0: the product p >= 0, so the
+// larger of hi and p is also the one of larger magnitude and Fast2Sum on the
+// ordered pair gives the same rounded sum and the same exact error as the
+// two-sum above (both are error-free transformations): three additions and
+// two max/min instead of six additions.
+__device__ inline void df_acc_prod_nonneg(float a, float b, float& hi, float& lo) {
+  float p = __fmul_rn(a, b);
+  float e = __fmaf_rn(a, b, -p);
+  float big = fmaxf(hi, p), small = fminf(hi, p);
+  float t = __fadd_rn(big, small);
+  float err = __fsub_rn(small, __fsub_rn(t, big));
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+  hi = t;
+}
+
 // Partial raw second moments sum_a x_i x_j of the whole patch (n values), tile
 // (ti, tj), ti <= tj, over one split of the sample: partial layout
 // [split][pair][32][32] (FP64, folded from double-float).  The CTAs of the
@@ -129,27 +144,49 @@ __global__ void __launch_bounds__(256) k_cov_partial(const float* __restrict__ g
       pj[u] = vj;
     }
   };
+  // while every staged value so far is >= 0 (pixel data), the sums take the
+  // shorter non-negative form; the first negative or NaN value in any chunk
+  // switches this block to the general two-sum for good (same results either way)
+  bool general = false;
   if (a0 < a1) load_chunk(a0);
   for (int64_t ab = a0; ab < a1; ab += kChunk) {
+    bool neg = false;
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
       const int t = threadIdx.x + u * 256;
       xi[t / kTile][t % kTile] = pi[u];
       xj[t / kTile][t % kTile] = pj[u];
+      neg |= !(pi[u] >= 0.0f) | !(pj[u] >= 0.0f);
     }
-    __syncthreads();
+    general |= __syncthreads_or(neg) != 0;
     if (ab + kChunk < a1) load_chunk(ab + kChunk);
+    if (general) {
 #pragma unroll 4
-    for (int k = 0; k < kChunk; ++k) {
-      float a0v = xi[k][ty * 2], a1v = xi[k][ty * 2 + 1];
-      float b0v = xj[k][tx * 2], b1v = xj[k][tx * 2 + 1];
-      df_acc_prod(a0v, b0v, hi[0][0], lo[0][0]);
-      df_acc_prod(a0v, b1v, hi[0][1], lo[0][1]);
-      df_acc_prod(a1v, b0v, hi[1][0], lo[1][0]);
-      df_acc_prod(a1v, b1v, hi[1][1], lo[1][1]);
-      if (msums) {
-        df_add(a0v, mh[0], ml[0]);
-        df_add(a1v, mh[1], ml[1]);
+      for (int k = 0; k < kChunk; ++k) {
+        float a0v = xi[k][ty * 2], a1v = xi[k][ty * 2 + 1];
+        float b0v = xj[k][tx * 2], b1v = xj[k][tx * 2 + 1];
+        df_acc_prod(a0v, b0v, hi[0][0], lo[0][0]);
+        df_acc_prod(a0v, b1v, hi[0][1], lo[0][1]);
+        df_acc_prod(a1v, b0v, hi[1][0], lo[1][0]);
+        df_acc_prod(a1v, b1v, hi[1][1], lo[1][1]);
+        if (msums) {
+          df_add(a0v, mh[0], ml[0]);
+          df_add(a1v, mh[1], ml[1]);
+        }
+      }
+    } else {
+#pragma unroll 4
+      for (int k = 0; k < kChunk; ++k) {
+        float a0v = xi[k][ty * 2], a1v = xi[k][ty * 2 + 1];
+        float b0v = xj[k][tx * 2], b1v = xj[k][tx * 2 + 1];
+        df_acc_prod_nonneg(a0v, b0v, hi[0][0], lo[0][0]);
+        df_acc_prod_nonneg(a0v, b1v, hi[0][1], lo[0][1]);
+        df_acc_prod_nonneg(a1v, b0v, hi[1][0], lo[1][0]);
+        df_acc_prod_nonneg(a1v, b1v, hi[1][1], lo[1][1]);
+        if (msums) {
+          df_add(a0v, mh[0], ml[0]);
+          df_add(a1v, mh[1], ml[1]);
+        }
       }
     }
     __syncthreads();

@@ -157,6 +157,24 @@ def test_index_pca_basis_close_to_oracle(rgb_index):
                 assert np.abs(ex["basis"][cv][:, k] - B[:, k]).max() < 2e-6
 
 
+@pytest.mark.parametrize("shift", [0.5, 0.2])
+def test_index_pca_with_negative_values(S, shift):
+    # grid values shifted below zero (all of them around 0.5, some at 0.2): the
+    # moments then take the general two-sum path, from the first chunk or from
+    # a later one on, and the eigenpairs still match the oracle's
+    g, m = synth.voronoi2d(80, cfg=2, seed_sub=5)
+    g = (g - np.float32(shift)).astype(np.float32)
+    K, C_, D = 7, 4, 6
+    ix = S.sfc_index_build(dev(g), dev(m), K=K, curves=C_, dims=D, bits=12, window=16, pca_sample=0)
+    ex = S.sfc_index_export(ix)
+    ix.close()
+    assert S.sfc_status() == 0
+    for cv in range(C_):
+        B, mu, ev, _ = O.pca(g, K, ex["dict"], ex["subsets"][cv], 0, D)
+        assert np.allclose(ex["evals"][cv][:D], ev[:D], rtol=1e-9, atol=1e-12 * ev[0])
+        assert np.all(np.abs(ex["mean"][cv] - mu) <= np.spacing(np.abs(mu)))
+
+
 def test_index_keys_bit_exact_from_common_basis(rgb_index):
     r = rgb_index
     ex = r["ex"]
