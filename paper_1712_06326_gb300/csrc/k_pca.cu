@@ -97,6 +97,17 @@ __device__ inline void df_acc_prod_nonneg(float a, float b, float& hi, float& lo
   hi = t;
 }
 
+// (hi, lo) += a * b when a * b <= hi is known beforehand (hi >= 0): Fast2Sum
+// in the given order, the same rounded sum and exact error as the two-sum
+__device__ inline void df_acc_prod_dominated(float a, float b, float& hi, float& lo) {
+  float p = __fmul_rn(a, b);
+  float e = __fmaf_rn(a, b, -p);
+  float t = __fadd_rn(hi, p);
+  float err = __fsub_rn(p, __fsub_rn(t, hi));
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+  hi = t;
+}
+
 // Partial raw second moments sum_a x_i x_j of the whole patch (n values), tile
 // (ti, tj), ti <= tj, over one split of the sample: partial layout
 // [split][pair][32][32] (FP64, folded from double-float).  The CTAs of the
@@ -146,21 +157,54 @@ __global__ void __launch_bounds__(256) k_cov_partial(const float* __restrict__ g
   };
   // while every staged value so far is >= 0 (pixel data), the sums take the
   // shorter non-negative form; the first negative or NaN value in any chunk
-  // switches this block to the general two-sum for good (same results either way)
+  // switches this block to the general two-sum for good (same results either
+  // way).  In the non-negative form, a warp whose every accumulator is already
+  // at least the square of the chunk's largest value skips the ordering: no
+  // product of the chunk can exceed an accumulator, which only grows.
+  __shared__ uint32_t s_wmax[8];
   bool general = false;
   if (a0 < a1) load_chunk(a0);
   for (int64_t ab = a0; ab < a1; ab += kChunk) {
     bool neg = false;
+    float vmax = 0.0f;
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
       const int t = threadIdx.x + u * 256;
       xi[t / kTile][t % kTile] = pi[u];
       xj[t / kTile][t % kTile] = pj[u];
       neg |= !(pi[u] >= 0.0f) | !(pj[u] >= 0.0f);
+      vmax = fmaxf(vmax, fmaxf(pi[u], pj[u]));
     }
+    // non-negative floats order like their bit patterns
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, __float_as_uint(vmax));
+    if ((threadIdx.x & 31) == 0) s_wmax[threadIdx.x >> 5] = wmax;
     general |= __syncthreads_or(neg) != 0;
     if (ab + kChunk < a1) load_chunk(ab + kChunk);
-    if (general) {
+    bool dominated = false;
+    if (!general) {
+      uint32_t bm = s_wmax[0];
+#pragma unroll
+      for (int w = 1; w < 8; ++w) bm = max(bm, s_wmax[w]);
+      const float m = __uint_as_float(bm);
+      const float m2 = __fmul_rn(m, m);  // >= every rounded product of the chunk
+      const float hmin = fminf(fminf(hi[0][0], hi[0][1]), fminf(hi[1][0], hi[1][1]));
+      dominated = __all_sync(0xffffffffu, hmin >= m2);
+    }
+    if (dominated) {
+#pragma unroll 4
+      for (int k = 0; k < kChunk; ++k) {
+        float a0v = xi[k][ty * 2], a1v = xi[k][ty * 2 + 1];
+        float b0v = xj[k][tx * 2], b1v = xj[k][tx * 2 + 1];
+        df_acc_prod_dominated(a0v, b0v, hi[0][0], lo[0][0]);
+        df_acc_prod_dominated(a0v, b1v, hi[0][1], lo[0][1]);
+        df_acc_prod_dominated(a1v, b0v, hi[1][0], lo[1][0]);
+        df_acc_prod_dominated(a1v, b1v, hi[1][1], lo[1][1]);
+        if (msums) {
+          df_add(a0v, mh[0], ml[0]);
+          df_add(a1v, mh[1], ml[1]);
+        }
+      }
+    } else if (general) {
 #pragma unroll 4
       for (int k = 0; k < kChunk; ++k) {
         float a0v = xi[k][ty * 2], a1v = xi[k][ty * 2 + 1];
