@@ -147,10 +147,32 @@ __device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsig
   return d;
 }
 
+// morton_key for D = 8: the key is the top min(bp, 8) bit planes of the eight
+// coordinates, one byte per plane (dimension 0 its most significant bit), i.e.
+// the transpose of the 8 x 8 bit matrix whose row 7 - k holds coordinate k's
+// top eight bits.  The transpose is the three-step swap of 1 x 1, 2 x 2 and
+// 4 x 4 blocks across the diagonal (Hacker's Delight, Sec. 7-3).
+__host__ __device__ inline uint64_t morton_key8(const uint32_t* q, int bp) {
+  const int sh = bp > 8 ? bp - 8 : 0;
+  const uint32_t m = bp >= 8 ? 0xffu : (1u << bp) - 1u;
+  uint64_t x = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x |= (uint64_t)((q[k] >> sh) & m) << (8 * (7 - k));
+  uint64_t t;
+  t = (x ^ (x >> 7)) & 0x00AA00AA00AA00AAull;
+  x ^= t ^ (t << 7);
+  t = (x ^ (x >> 14)) & 0x0000CCCC0000CCCCull;
+  x ^= t ^ (t << 14);
+  t = (x ^ (x >> 28)) & 0x00000000F0F0F0F0ull;
+  x ^= t ^ (t << 28);
+  return x;
+}
+
 // morton_key with D known at compile time (q stays in registers): each bit
 // plane's D bits form a group, dimension 0 its most significant bit.
 template <int D>
 __device__ inline uint64_t morton_key_t(const uint32_t* q, int bp) {
+  if constexpr (D == 8) return morton_key8(q, bp);
   uint64_t key = 0;
   int n = 0;
   for (int p = bp - 1; p >= 0 && n < 64; --p) {
